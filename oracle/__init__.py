@@ -1,0 +1,236 @@
+"""FP64 CPU oracle of the Celeris extended-Boussinesq time step (arXiv 1611.05984).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, obviously correct
+restatement of the paper's method that the CUDA path is checked against.  Only
+``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg may import this package.  It shares no code with the CUDA
+library (``paper_1611_05984_gb300``) and never imports it.
+
+Parity-pin status of the oracle's parts (the tests under ``tests/`` that pin
+each one are named in the test module docstrings):
+  * reconstruction, flux, bed slope: lake at rest (well-balanced) -- pinned
+  * flux form, walls, AB3: mass conservation with solid walls -- pinned
+  * KP07 NLSW path + dry front: Ritter dam-break closed form -- pinned
+  * dispersion + tridiagonal + F*: linear dispersion relation -- pinned
+  * mirror / transpose symmetry -- pinned
+  * Thomas solver: dense solve -- pinned; Eckart, sponge, soliton -- pinned
+  * friction + AB3 order: uniform-flow ODE -- pinned
+  * Euler start-up, AM4 corrector, sine-ghost timing, corner ghosts:
+    parity unpinned (internal consistency only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "celeris_oracle.c")
+_HDR = os.path.join(_HERE, "celeris_oracle.h")
+_LIB = os.path.join(_HERE, "_build", "libceleris_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BSNQ, NLSW = 0, 1
+FRIC_NONE, FRIC_QUAD, FRIC_MANNING = 0, 1, 2
+SOLID, SPONGE, SINE = 0, 1, 2
+W, E, S, N = 0, 1, 2, 3
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("model", ctypes.c_int), ("g", ctypes.c_double),
+                ("Bd", ctypes.c_double), ("theta", ctypes.c_double),
+                ("eps", ctypes.c_double), ("dt", ctypes.c_double),
+                ("K", ctypes.c_int), ("ws", ctypes.c_double),
+                ("friction", ctypes.c_int), ("fcoef", ctypes.c_double)]
+
+
+class OrcBC(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("width", ctypes.c_int),
+                ("ncomp", ctypes.c_int),
+                ("amp", ctypes.c_double * 8), ("period", ctypes.c_double * 8),
+                ("dir", ctypes.c_double * 8), ("phase", ctypes.c_double * 8)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, FP64, OpenMP, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O3", "-std=c99", "-fopenmp", "-ffp-contract=off", "-fPIC",
+           "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            # ORACLE_LIB lets the mutation test load a deliberately broken copy
+            path = os.environ.get("ORACLE_LIB") or build()
+            L = ctypes.CDLL(path)
+            d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.orc_create.restype = p
+            L.orc_create.argtypes = [ctypes.POINTER(OrcParams), dp]
+            L.orc_destroy.argtypes = [p]
+            L.orc_set_boundary.argtypes = [p, i, ctypes.POINTER(OrcBC)]
+            L.orc_set_state.argtypes = [p, dp, dp, dp]
+            L.orc_add_solitary.argtypes = [p, d, d, d, d]
+            L.orc_step.argtypes = [p, i]
+            L.orc_get_state.argtypes = [p, dp, dp, dp]
+            L.orc_get_field.argtypes = [p, i, dp]
+            L.orc_get_time.argtypes = [p, dp, ctypes.POINTER(ctypes.c_longlong)]
+            L.orc_mass.restype = d
+            L.orc_mass.argtypes = [p]
+            L.orc_clamp_mass.restype = d
+            L.orc_clamp_mass.argtypes = [p]
+            L.orc_set_gauges.argtypes = [p, ctypes.POINTER(ctypes.c_int), i, i, i]
+            L.orc_read_gauges.argtypes = [p, dp, i, ctypes.POINTER(ctypes.c_int)]
+            L.orc_num_threads.restype = i
+            L.orc_minmod.restype = d
+            L.orc_minmod.argtypes = [d, d, d, d]
+            L.orc_eckart_k.restype = d
+            L.orc_eckart_k.argtypes = [d, d, d]
+            L.orc_sponge_gamma.restype = d
+            L.orc_sponge_gamma.argtypes = [d, d]
+            L.orc_thomas.argtypes = [i, dp, dp, dp, dp, dp]
+            L.orc_central_upwind.argtypes = [d] * 9 + [dp]
+            _lib = L
+        return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def make_bc(type=SOLID, width=0, comps=()):
+    """comps: iterable of (amp, period, dir_rad, phase_rad)."""
+    bc = OrcBC()
+    bc.type, bc.width, bc.ncomp = int(type), int(width), len(comps)
+    for m, (a, T, th, ph) in enumerate(comps):
+        bc.amp[m], bc.period[m], bc.dir[m], bc.phase[m] = a, T, th, ph
+    return bc
+
+
+class Oracle:
+    """One oracle simulation.  Arguments mirror the paper's problem statement."""
+
+    def __init__(self, z, dx, dy, dt, *, model=BSNQ, g=9.81, Bd=1.0 / 15.0,
+                 theta=1.3, eps=5e-12, K=0, ws=0.0, friction=FRIC_NONE, fcoef=0.0):
+        z = _f64(z)
+        ny, nx = z.shape
+        self.nx, self.ny = nx, ny
+        self.p = OrcParams(nx, ny, dx, dy, model, g, Bd, theta, eps, dt, K, ws,
+                           friction, fcoef)
+        self._L = lib()
+        self._h = self._L.orc_create(ctypes.byref(self.p), _dp(z))
+        if not self._h:
+            raise ValueError("orc_create rejected the parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.orc_destroy(h)
+            self._h = None
+
+    def set_boundary(self, side, type=SOLID, width=0, comps=()):
+        bc = make_bc(type, width, comps)
+        if self._L.orc_set_boundary(self._h, side, ctypes.byref(bc)) != 0:
+            raise ValueError("bad boundary")
+
+    def set_state(self, w, P, Q):
+        sh = (self.ny, self.nx)
+        w, P, Q = _f64(w, sh), _f64(P, sh), _f64(Q, sh)
+        if self._L.orc_set_state(self._h, _dp(w), _dp(P), _dp(Q)) != 0:
+            raise ValueError("bad state")
+
+    def add_solitary(self, H, theta, x0, y0):
+        if self._L.orc_add_solitary(self._h, H, theta, x0, y0) != 0:
+            raise ValueError("solitary wave rejected (dry crest)")
+
+    def step(self, n=1):
+        if self._L.orc_step(self._h, int(n)) != 0:
+            raise RuntimeError("orc_step failed")
+
+    def state(self):
+        sh = (self.ny, self.nx)
+        w, P, Q = np.empty(sh), np.empty(sh), np.empty(sh)
+        self._L.orc_get_state(self._h, _dp(w), _dp(P), _dp(Q))
+        return w, P, Q
+
+    def field(self, which):
+        idx = {"Bbar": 0, "d": 1, "U": 2, "V": 3}[which]
+        out = np.empty((self.ny, self.nx))
+        self._L.orc_get_field(self._h, idx, _dp(out))
+        return out
+
+    def time(self):
+        t = ctypes.c_double()
+        s = ctypes.c_longlong()
+        self._L.orc_get_time(self._h, ctypes.byref(t), ctypes.byref(s))
+        return t.value, s.value
+
+    def mass(self):
+        return self._L.orc_mass(self._h)
+
+    def clamp_mass(self):
+        return self._L.orc_clamp_mass(self._h)
+
+    def set_gauges(self, ij, log_every, capacity):
+        ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int32).reshape(-1, 2))
+        ptr = ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        if self._L.orc_set_gauges(self._h, ptr, len(ij), log_every, capacity) != 0:
+            raise ValueError("bad gauges")
+        self._ng = len(ij)
+
+    def read_gauges(self, max_rec):
+        out = np.zeros((max_rec, self._ng))
+        n = ctypes.c_int()
+        self._L.orc_read_gauges(self._h, _dp(out), max_rec, ctypes.byref(n))
+        return out[: n.value]
+
+
+def minmod(theta, qm, q0, qp):
+    return lib().orc_minmod(theta, qm, q0, qp)
+
+
+def eckart_k(omega, d, g=9.81):
+    return lib().orc_eckart_k(omega, d, g)
+
+
+def sponge_gamma(D, Ls):
+    return lib().orc_sponge_gamma(D, Ls)
+
+
+def thomas(a, b, c, r):
+    a, b, c, r = (_f64(v) for v in (a, b, c, r))
+    x = np.empty_like(r)
+    lib().orc_thomas(len(r), _dp(a), _dp(b), _dp(c), _dp(r), _dp(x))
+    return x
+
+
+def central_upwind(g, eps, wL, nL, tL, wR, nR, tR, Bf):
+    H = np.zeros(3)
+    lib().orc_central_upwind(g, eps, wL, nL, tL, wR, nR, tR, Bf, _dp(H))
+    return H
+
+
+def num_threads():
+    return lib().orc_num_threads()

@@ -1,0 +1,845 @@
+/*
+ * celeris_oracle.c -- FP64 CPU oracle of the Celeris extended-Boussinesq step.
+ *
+ * TEST INFRASTRUCTURE ONLY (see celeris_oracle.h).  Plain loops in the order
+ * the paper describes, one function per step of the method, no blocking or
+ * fusion.  Readings of passages the paper leaves open are marked "Reading:".
+ *
+ * Paper: S. Tavakkol, P. Lynett, "Celeris: A GPU-accelerated open source
+ * software with a Boussinesq-type wave solver ...", arXiv 1611.05984.
+ *   Sec. 2.1  governing equations (Eq. 1-3)
+ *   Sec. 2.2  Wei-Kirby form (Eq. 4-13), KP07 steps 1-4, Eq. 14
+ *   Sec. 2.3  AB3 predictor (Eq. 15-17), AM4 corrector (Eq. 18-20),
+ *             tridiagonal systems (Eq. 21-23)
+ *   Sec. 2.4  boundaries: solid wall (Eq. 24), sine maker (Eq. 25-29),
+ *             sponge (Eq. 30)
+ *   Sec. 2.6  friction (Eq. 31-32);  Sec. 2.7 solitary wave (Eq. 33-36)
+ *
+ * Storage: every cell field is "extended", (nx+4) x (ny+4) with two ghost
+ * layers (Sec. 2.4).  Bed corners are (nx+3) x (ny+3), corner (ci,cj) at
+ * (ci*dx, cj*dy), ci in [-1, nx+1].
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include "celeris_oracle.h"
+
+#define ORC_PI 3.14159265358979323846
+
+struct orc {
+    orc_params p;
+    orc_bc bc[4];
+    int nx, ny, ex, ey;
+    long long step;   /* steps since create: t = step * dt                  */
+    long long nh;     /* steps since the last restart of the AB3 history    */
+    double clamp_mass;
+    double *z, *Bc, *Bbar, *d, *ddx, *ddy;      /* static fields           */
+    double *w, *P, *Q, *w1, *P1, *Q1;           /* state n and iterate n+1 */
+    double *U, *V, *U1, *V1;                    /* U*, V* (Eq. 7-8)        */
+    double *E[3], *F[3], *G[3], *Fs[3], *Gs[3]; /* [0]=n, [1]=n-1, [2]=n-2 */
+    double *Ec, *Fc, *Gc, *Fsc, *Gsc;           /* rhs at the AM4 iterate  */
+    double *Hx[3], *Hy[3];                      /* face fluxes             */
+    int ng, log_every, cap, nrec, head;
+    int *gij;
+    double *grec;
+};
+
+static size_t IX(const orc *o, int i, int j)
+{
+    return (size_t)(j + 2) * (size_t)o->ex + (size_t)(i + 2);
+}
+static size_t CX(const orc *o, int ci, int cj)
+{
+    return (size_t)(cj + 1) * (size_t)(o->nx + 3) + (size_t)(ci + 1);
+}
+/* Bed on the x-face f (x = f dx) of row j, and on the y-face g of column i:
+ * mean of the face's two end corners (Reading A-W1). */
+static double Bx(const orc *o, int f, int j)
+{
+    return 0.5 * (o->Bc[CX(o, f, j)] + o->Bc[CX(o, f, j + 1)]);
+}
+static double By(const orc *o, int i, int g)
+{
+    return 0.5 * (o->Bc[CX(o, i, g)] + o->Bc[CX(o, i + 1, g)]);
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------- pieces */
+
+/* Generalized minmod of KP07 step 1 (Sec. 2.2): the slope is
+ * minmod(theta*(q0-qm), (qp-qm)/2, theta*(qp-q0)); zero unless all three
+ * share a sign, else the one of least magnitude (Reading A-L1). */
+double orc_minmod(double theta, double qm, double q0, double qp)
+{
+    double a = theta * (q0 - qm), b = 0.5 * (qp - qm), c = theta * (qp - q0);
+    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+/* Eq. 29: Eckart's approximation k = omega^2/g * sqrt(coth(omega^2 d / g)). */
+double orc_eckart_k(double omega, double d, double g)
+{
+    double k0 = omega * omega / g;
+    return k0 * sqrt(1.0 / tanh(k0 * d));
+}
+
+/* Eq. 30: gamma = (1 + cos(pi (Ls - D)/Ls))/2 inside the layer, 1 outside. */
+double orc_sponge_gamma(double D, double Ls)
+{
+    if (!(D < Ls)) return 1.0;
+    return 0.5 * (1.0 + cos(ORC_PI * (Ls - D) / Ls));
+}
+
+/* Textbook Thomas algorithm: a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = r[i]. */
+static void thomas_ws(int n, const double *a, const double *b, const double *c,
+                      const double *r, double *x, double *cp, double *dp)
+{
+    cp[0] = c[0] / b[0];
+    dp[0] = r[0] / b[0];
+    for (int i = 1; i < n; i++) {
+        double m = b[i] - a[i] * cp[i - 1];
+        cp[i] = c[i] / m;
+        dp[i] = (r[i] - a[i] * dp[i - 1]) / m;
+    }
+    x[n - 1] = dp[n - 1];
+    for (int i = n - 2; i >= 0; i--) x[i] = dp[i] - cp[i] * x[i + 1];
+}
+
+void orc_thomas(int n, const double *a, const double *b, const double *c,
+                const double *r, double *x)
+{
+    if (n <= 0) return;
+    double *cp = (double *)malloc(sizeof(double) * (size_t)n);
+    double *dp = (double *)malloc(sizeof(double) * (size_t)n);
+    thomas_ws(n, a, b, c, r, x, cp, dp);
+    free(cp);
+    free(dp);
+}
+
+/* Eq. 14 factor: u = k(h) * P with k(h) = sqrt(2) h / sqrt(h^4 + max(h^4, eps))
+ * (Reading A-G3); also the desingularised 1/h of the friction term (Sec. 2.6). */
+static double desing(double h, double eps)
+{
+    double h4 = (h * h) * (h * h);
+    return sqrt(2.0) * h / sqrt(h4 + fmax(h4, eps));
+}
+
+/* KP07 step 3 (Sec. 2.2): central-upwind flux through one face.  L/R states
+ * are (w, normal discharge, tangential discharge) at the face; Bf is the bed
+ * on the face.  H = (mass, normal momentum, tangential momentum). */
+void orc_central_upwind(double g, double eps, double wL, double nL, double tL,
+                        double wR, double nR, double tR, double Bf, double H[3])
+{
+    double hL = fmax(wL - Bf, 0.0), hR = fmax(wR - Bf, 0.0);
+    double kL = desing(hL, eps), kR = desing(hR, eps);
+    double uL = kL * nL, vL = kL * tL, uR = kR * nR, vR = kR * tR;
+    double qnL = hL * uL, qtL = hL * vL, qnR = hR * uR, qtR = hR * vR;
+    double sL = sqrt(g * hL), sR = sqrt(g * hR);
+    double ap = fmax(fmax(uL + sL, uR + sR), 0.0);
+    double am = fmin(fmin(uL - sL, uR - sR), 0.0);
+    double den = ap - am;
+    if (!(den > 0.0)) { /* both sides dry (Reading A-F1) */
+        H[0] = H[1] = H[2] = 0.0;
+        return;
+    }
+    double FL0 = qnL, FL1 = qnL * uL + 0.5 * g * hL * hL, FL2 = qnL * vL;
+    double FR0 = qnR, FR1 = qnR * uR + 0.5 * g * hR * hR, FR2 = qnR * vR;
+    H[0] = (ap * FL0 - am * FR0 + ap * am * (wR - wL)) / den;
+    H[1] = (ap * FL1 - am * FR1 + ap * am * (qnR - qnL)) / den;
+    H[2] = (ap * FL2 - am * FR2 + ap * am * (qtR - qtL)) / den;
+}
+
+/* Sine-wave maker, Eq. 25-28 summed over components (Reading A-B4). */
+static void sine_eval(const orc *o, const orc_bc *bc, double dadj, double x,
+                      double y, double t, double *eta, double *Pg, double *Qg)
+{
+    *eta = *Pg = *Qg = 0.0;
+    if (!(dadj > 0.0)) return;
+    for (int m = 0; m < bc->ncomp; m++) {
+        double om = 2.0 * ORC_PI / bc->period[m];
+        double k = orc_eckart_k(om, dadj, o->p.g);
+        double c = om / k;
+        double cs = cos(bc->dir[m]), sn = sin(bc->dir[m]);
+        double em = bc->amp[m] * sin(om * t - k * cs * x - k * sn * y + bc->phase[m]);
+        *eta += em;
+        *Pg += c * cs * em;
+        *Qg += c * sn * em;
+    }
+}
+
+/* ------------------------------------------------------------ boundaries */
+
+/* Ghost layers at time t (Sec. 2.4).  x-sides first over interior rows, then
+ * y-sides over every column, so corner ghosts come by composition.
+ * Solid (and the outer ghosts behind a sponge): face-centred mirror, ghost
+ * -1-k <- interior k, normal discharge negated (Eq. 24, Reading A-B1). */
+static void fill_ghosts(orc *o, double *w, double *P, double *Q, double t)
+{
+    const int nx = o->nx, ny = o->ny;
+    const double ws = o->p.ws;
+    for (int side = ORC_W; side <= ORC_E; side++) {
+        const orc_bc *bc = &o->bc[side];
+        for (int j = 0; j < ny; j++)
+            for (int k = 0; k < 2; k++) {
+                int gi = side == ORC_W ? -1 - k : nx + k;
+                int si = side == ORC_W ? k : nx - 1 - k;
+                size_t gc = IX(o, gi, j), sc = IX(o, si, j);
+                if (bc->type == ORC_SINE) {
+                    double eta, Pg, Qg;
+                    double dadj = o->d[IX(o, side == ORC_W ? 0 : nx - 1, j)];
+                    sine_eval(o, bc, dadj, (gi + 0.5) * o->p.dx,
+                              (j + 0.5) * o->p.dy, t, &eta, &Pg, &Qg);
+                    w[gc] = ws + eta;
+                    P[gc] = Pg;
+                    Q[gc] = Qg;
+                } else {
+                    w[gc] = w[sc];
+                    P[gc] = -P[sc];
+                    Q[gc] = Q[sc];
+                }
+            }
+    }
+    for (int side = ORC_S; side <= ORC_N; side++) {
+        const orc_bc *bc = &o->bc[side];
+        for (int i = -2; i < nx + 2; i++)
+            for (int k = 0; k < 2; k++) {
+                int gj = side == ORC_S ? -1 - k : ny + k;
+                int sj = side == ORC_S ? k : ny - 1 - k;
+                size_t gc = IX(o, i, gj), sc = IX(o, i, sj);
+                if (bc->type == ORC_SINE) {
+                    double eta, Pg, Qg;
+                    int ic = i < 0 ? 0 : (i > nx - 1 ? nx - 1 : i);
+                    double dadj = o->d[IX(o, ic, side == ORC_S ? 0 : ny - 1)];
+                    sine_eval(o, bc, dadj, (i + 0.5) * o->p.dx,
+                              (gj + 0.5) * o->p.dy, t, &eta, &Pg, &Qg);
+                    w[gc] = ws + eta;
+                    P[gc] = Pg;
+                    Q[gc] = Qg;
+                } else {
+                    w[gc] = w[sc];
+                    P[gc] = P[sc];
+                    Q[gc] = -Q[sc];
+                }
+            }
+    }
+}
+
+/* Sponge coefficient of cell (i,j): Eq. 30 with D the distance from the
+ * absorbing boundary face to the cell centre; the smallest gamma over all
+ * sponge sides (Reading A-B3). */
+static double sponge_at(const orc *o, int i, int j)
+{
+    double gmin = 1.0;
+    for (int s = 0; s < 4; s++) {
+        const orc_bc *bc = &o->bc[s];
+        if (bc->type != ORC_SPONGE || bc->width <= 0) continue;
+        double D, L;
+        if (s == ORC_W) { D = (i + 0.5) * o->p.dx; L = bc->width * o->p.dx; }
+        else if (s == ORC_E) { D = (o->nx - i - 0.5) * o->p.dx; L = bc->width * o->p.dx; }
+        else if (s == ORC_S) { D = (j + 0.5) * o->p.dy; L = bc->width * o->p.dy; }
+        else { D = (o->ny - j - 0.5) * o->p.dy; L = bc->width * o->p.dy; }
+        gmin = fmin(gmin, orc_sponge_gamma(D, L));
+    }
+    return gmin;
+}
+
+/* ------------------------------------------------------- static fields */
+
+/* a0: bed corners from cell-centre z (Reading A-W1): ghost z mirrored evenly,
+ * corner = mean of its 4 cells, cell Bbar = mean of its 4 corners,
+ * d = max(w_s - Bbar, 0) (Sec. 2.1), d_x, d_y by central differences. */
+static void derive_static(orc *o, const double *zin)
+{
+    const int nx = o->nx, ny = o->ny;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) o->z[IX(o, i, j)] = zin[(size_t)j * nx + i];
+    for (int j = 0; j < ny; j++)
+        for (int k = 0; k < 2; k++) {
+            o->z[IX(o, -1 - k, j)] = o->z[IX(o, k, j)];
+            o->z[IX(o, nx + k, j)] = o->z[IX(o, nx - 1 - k, j)];
+        }
+    for (int i = -2; i < nx + 2; i++)
+        for (int k = 0; k < 2; k++) {
+            o->z[IX(o, i, -1 - k)] = o->z[IX(o, i, k)];
+            o->z[IX(o, i, ny + k)] = o->z[IX(o, i, ny - 1 - k)];
+        }
+    for (int cj = -1; cj <= ny + 1; cj++)
+        for (int ci = -1; ci <= nx + 1; ci++)
+            o->Bc[CX(o, ci, cj)] =
+                0.25 * (o->z[IX(o, ci - 1, cj - 1)] + o->z[IX(o, ci, cj - 1)] +
+                        o->z[IX(o, ci - 1, cj)] + o->z[IX(o, ci, cj)]);
+    for (int j = -1; j <= ny; j++)
+        for (int i = -1; i <= nx; i++) {
+            double b = 0.25 * (o->Bc[CX(o, i, j)] + o->Bc[CX(o, i + 1, j)] +
+                               o->Bc[CX(o, i, j + 1)] + o->Bc[CX(o, i + 1, j + 1)]);
+            o->Bbar[IX(o, i, j)] = b;
+            o->d[IX(o, i, j)] = fmax(o->p.ws - b, 0.0);
+        }
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            o->ddx[IX(o, i, j)] =
+                (o->d[IX(o, i + 1, j)] - o->d[IX(o, i - 1, j)]) / (2.0 * o->p.dx);
+            o->ddy[IX(o, i, j)] =
+                (o->d[IX(o, i, j + 1)] - o->d[IX(o, i, j - 1)]) / (2.0 * o->p.dy);
+        }
+}
+
+/* ------------------------------------------------------------- the rhs */
+
+/* KP07 steps 1-2 for one cell along one direction (stride s): minmod slopes
+ * of w, P, Q give the low- and high-face values; then the conservative
+ * positivity fix of w against the face beds Blo, Bhi (Reading A-L2). */
+static void recon_cell(double theta, const double *w, const double *P,
+                       const double *Q, size_t c, size_t s, double Blo,
+                       double Bhi, double lo[3], double hi[3])
+{
+    const double *q[3] = {w, P, Q};
+    for (int v = 0; v < 3; v++) {
+        double sig = orc_minmod(theta, q[v][c - s], q[v][c], q[v][c + s]);
+        lo[v] = q[v][c] - 0.5 * sig;
+        hi[v] = q[v][c] + 0.5 * sig;
+    }
+    if (hi[0] < Bhi) {
+        hi[0] = Bhi;
+        lo[0] = 2.0 * w[c] - Bhi;
+    } else if (lo[0] < Blo) {
+        lo[0] = Blo;
+        hi[0] = 2.0 * w[c] - Blo;
+    }
+}
+
+/* Eq. 9-13 at every interior cell, for state (w,P,Q) whose ghosts are set.
+ * E, F, G: flux divergence of KP07 (steps 3-4) + bed slope + friction
+ * (Eq. 31-32) + the dispersive eta terms of Eq. 10-11 by central FD;
+ * Fs = F*(Q) (Eq. 12), Gs = G*(P) (Eq. 13, Reading A-G2). */
+static void compute_rhs(orc *o, const double *w, const double *P,
+                        const double *Q, double *E, double *F, double *G,
+                        double *Fs, double *Gs)
+{
+    const int nx = o->nx, ny = o->ny;
+    const double dx = o->p.dx, dy = o->p.dy, g = o->p.g, eps = o->p.eps;
+    const double th = o->p.theta;
+    const size_t ex = (size_t)o->ex;
+
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int f = 0; f <= nx; f++) {
+            double loL[3], hiL[3], loR[3], hiR[3], H[3];
+            recon_cell(th, w, P, Q, IX(o, f - 1, j), 1, Bx(o, f - 1, j), Bx(o, f, j), loL, hiL);
+            recon_cell(th, w, P, Q, IX(o, f, j), 1, Bx(o, f, j), Bx(o, f + 1, j), loR, hiR);
+            orc_central_upwind(g, eps, hiL[0], hiL[1], hiL[2], loR[0], loR[1],
+                               loR[2], Bx(o, f, j), H);
+            size_t k = (size_t)j * (size_t)(nx + 1) + (size_t)f;
+            o->Hx[0][k] = H[0];
+            o->Hx[1][k] = H[1];
+            o->Hx[2][k] = H[2];
+        }
+#pragma omp parallel for schedule(static)
+    for (int gq = 0; gq <= ny; gq++)
+        for (int i = 0; i < nx; i++) {
+            double loS[3], hiS[3], loN[3], hiN[3], H[3];
+            recon_cell(th, w, P, Q, IX(o, i, gq - 1), ex, By(o, i, gq - 1), By(o, i, gq), loS, hiS);
+            recon_cell(th, w, P, Q, IX(o, i, gq), ex, By(o, i, gq), By(o, i, gq + 1), loN, hiN);
+            /* normal discharge is Q, tangential is P */
+            orc_central_upwind(g, eps, hiS[0], hiS[2], hiS[1], loN[0], loN[2],
+                               loN[1], By(o, i, gq), H);
+            size_t k = (size_t)gq * (size_t)nx + (size_t)i;
+            o->Hy[0][k] = H[0];
+            o->Hy[1][k] = H[2];
+            o->Hy[2][k] = H[1];
+        }
+
+    const int bsnq = o->p.model == ORC_BSNQ;
+    const double Bd = o->p.Bd, ws = o->p.ws, B3 = o->p.Bd + 1.0 / 3.0;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            size_t c = IX(o, i, j);
+            size_t kx = (size_t)j * (size_t)(nx + 1) + (size_t)i;
+            size_t ky = (size_t)j * (size_t)nx + (size_t)i;
+            size_t kyn = (size_t)(j + 1) * (size_t)nx + (size_t)i;
+            double hb = w[c] - o->Bbar[c];
+            double e = -(o->Hx[0][kx + 1] - o->Hx[0][kx]) / dx -
+                       (o->Hy[0][kyn] - o->Hy[0][ky]) / dy;
+            double f = -(o->Hx[1][kx + 1] - o->Hx[1][kx]) / dx -
+                       (o->Hy[1][kyn] - o->Hy[1][ky]) / dy -
+                       g * hb * (Bx(o, i + 1, j) - Bx(o, i, j)) / dx;
+            double gg = -(o->Hx[2][kx + 1] - o->Hx[2][kx]) / dx -
+                        (o->Hy[2][kyn] - o->Hy[2][ky]) / dy -
+                        g * hb * (By(o, i, j + 1) - By(o, i, j)) / dy;
+            if (o->p.friction != ORC_FRIC_NONE) {
+                double hinv = desing(fmax(hb, 0.0), eps);
+                double fc = o->p.friction == ORC_FRIC_MANNING
+                                ? g * o->p.fcoef * o->p.fcoef * cbrt(hinv)
+                                : o->p.fcoef;
+                double mag = sqrt(P[c] * P[c] + Q[c] * Q[c]);
+                f -= fc * P[c] * mag * hinv * hinv;
+                gg -= fc * Q[c] * mag * hinv * hinv;
+            }
+            double fs = 0.0, gs = 0.0;
+            if (bsnq) {
+                double dd = o->d[c], dxd = o->ddx[c], dyd = o->ddy[c];
+#define ETA(a, b) (w[IX(o, i + (a), j + (b))] - ws)
+                double exx = (ETA(1, 0) - 2.0 * ETA(0, 0) + ETA(-1, 0)) / (dx * dx);
+                double eyy = (ETA(0, 1) - 2.0 * ETA(0, 0) + ETA(0, -1)) / (dy * dy);
+                double exy = (ETA(1, 1) - ETA(1, -1) - ETA(-1, 1) + ETA(-1, -1)) / (4.0 * dx * dy);
+                double exxx = (ETA(2, 0) - 2.0 * ETA(1, 0) + 2.0 * ETA(-1, 0) - ETA(-2, 0)) /
+                              (2.0 * dx * dx * dx);
+                double eyyy = (ETA(0, 2) - 2.0 * ETA(0, 1) + 2.0 * ETA(0, -1) - ETA(0, -2)) /
+                              (2.0 * dy * dy * dy);
+                double exyy = ((ETA(1, 1) - 2.0 * ETA(1, 0) + ETA(1, -1)) -
+                               (ETA(-1, 1) - 2.0 * ETA(-1, 0) + ETA(-1, -1))) /
+                              (2.0 * dx * dy * dy);
+                double exxy = ((ETA(1, 1) - 2.0 * ETA(0, 1) + ETA(-1, 1)) -
+                               (ETA(1, -1) - 2.0 * ETA(0, -1) + ETA(-1, -1))) /
+                              (2.0 * dx * dx * dy);
+#undef ETA
+                f += Bd * g * dd * dd * dd * (exxx + exyy) +
+                     Bd * g * dd * dd * (dxd * (2.0 * exx + eyy) + dyd * exy);
+                gg += Bd * g * dd * dd * dd * (eyyy + exxy) +
+                      Bd * g * dd * dd * (dyd * (2.0 * eyy + exx) + dxd * exy);
+#define QQ(a, b) Q[IX(o, i + (a), j + (b))]
+#define PP(a, b) P[IX(o, i + (a), j + (b))]
+                double Qx = (QQ(1, 0) - QQ(-1, 0)) / (2.0 * dx);
+                double Qy = (QQ(0, 1) - QQ(0, -1)) / (2.0 * dy);
+                double Qxy = (QQ(1, 1) - QQ(1, -1) - QQ(-1, 1) + QQ(-1, -1)) / (4.0 * dx * dy);
+                double Px = (PP(1, 0) - PP(-1, 0)) / (2.0 * dx);
+                double Py = (PP(0, 1) - PP(0, -1)) / (2.0 * dy);
+                double Pxy = (PP(1, 1) - PP(1, -1) - PP(-1, 1) + PP(-1, -1)) / (4.0 * dx * dy);
+#undef QQ
+#undef PP
+                fs = dd * dxd * Qy / 6.0 + dd * dyd * Qx / 6.0 + B3 * dd * dd * Qxy;
+                gs = dd * dyd * Px / 6.0 + dd * dxd * Py / 6.0 + B3 * dd * dd * Pxy;
+            }
+            E[c] = e;
+            F[c] = f;
+            G[c] = gg;
+            Fs[c] = fs;
+            Gs[c] = gs;
+        }
+}
+
+/* Eq. 23 coefficients of the line through cell c (spacing h, d, d_alpha). */
+static void coef23(double Bd, double h, double dd, double dda, double *a,
+                   double *b, double *c)
+{
+    double r = (Bd + 1.0 / 3.0) * dd * dd / (h * h);
+    double s = dd * dda / (6.0 * h);
+    *a = s - r;
+    *b = 1.0 + 2.0 * r;
+    *c = -s - r;
+}
+
+/* U*, V* of Eq. 7-8 discretised exactly as the rows of Eq. 21-23, from P, Q
+ * with their ghosts (Reading A-T3).  NLSW: U* = P, V* = Q. */
+static void compute_ustar(orc *o, const double *P, const double *Q, double *U,
+                          double *V)
+{
+    const int nx = o->nx, ny = o->ny;
+    const size_t ex = (size_t)o->ex;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            size_t c = IX(o, i, j);
+            if (o->p.model != ORC_BSNQ) {
+                U[c] = P[c];
+                V[c] = Q[c];
+                continue;
+            }
+            double a, b, cc;
+            coef23(o->p.Bd, o->p.dx, o->d[c], o->ddx[c], &a, &b, &cc);
+            U[c] = a * P[c - 1] + b * P[c] + cc * P[c + 1];
+            coef23(o->p.Bd, o->p.dy, o->d[c], o->ddy[c], &a, &b, &cc);
+            V[c] = a * Q[c - ex] + b * Q[c] + cc * Q[c + ex];
+        }
+}
+
+/* Eq. 21 per x-row (dir 0) or Eq. 22 per y-column (dir 1), Thomas.  Boundary
+ * rows (Reading A-B2): a solid or sponge end uses the mirror P_{-1} = -P_0;
+ * a sine end moves the known ghost discharge at t1 to the right side. */
+static void solve_lines(orc *o, int dir, const double *R, double *X, double t1)
+{
+    const int nx = o->nx, ny = o->ny;
+    const int n = dir == 0 ? nx : ny, nl = dir == 0 ? ny : nx;
+    const double h = dir == 0 ? o->p.dx : o->p.dy;
+    const orc_bc *lo = &o->bc[dir == 0 ? ORC_W : ORC_S];
+    const orc_bc *hi = &o->bc[dir == 0 ? ORC_E : ORC_N];
+#pragma omp parallel
+    {
+        double *a = (double *)malloc(sizeof(double) * (size_t)n * 7);
+        double *b = a + n, *c = b + n, *r = c + n, *x = r + n, *cp = x + n, *dp = cp + n;
+#pragma omp for schedule(static)
+        for (int l = 0; l < nl; l++) {
+            for (int k = 0; k < n; k++) {
+                int i = dir == 0 ? k : l, j = dir == 0 ? l : k;
+                size_t cc = IX(o, i, j);
+                coef23(o->p.Bd, h, o->d[cc], dir == 0 ? o->ddx[cc] : o->ddy[cc],
+                       &a[k], &b[k], &c[k]);
+                r[k] = R[cc];
+            }
+            for (int end = 0; end < 2; end++) {
+                const orc_bc *bc = end == 0 ? lo : hi;
+                int k = end == 0 ? 0 : n - 1;
+                double *off = end == 0 ? &a[0] : &c[n - 1];
+                if (bc->type == ORC_SINE) {
+                    int gk = end == 0 ? -1 : n;
+                    int gi = dir == 0 ? gk : l, gj = dir == 0 ? l : gk;
+                    int ai = dir == 0 ? k : l, aj = dir == 0 ? l : k;
+                    double eta, Pg, Qg;
+                    sine_eval(o, bc, o->d[IX(o, ai, aj)], (gi + 0.5) * o->p.dx,
+                              (gj + 0.5) * o->p.dy, t1, &eta, &Pg, &Qg);
+                    r[k] -= *off * (dir == 0 ? Pg : Qg);
+                } else {
+                    b[k] -= *off;
+                }
+                *off = 0.0;
+            }
+            thomas_ws(n, a, b, c, r, x, cp, dp);
+            for (int k = 0; k < n; k++) {
+                int i = dir == 0 ? k : l, j = dir == 0 ? l : k;
+                X[IX(o, i, j)] = x[k];
+            }
+        }
+        free(a);
+    }
+}
+
+/* Reading A-D1: AB3 is not positivity preserving, so w is clamped to the
+ * bed after each update and P, Q are zeroed where the depth is zero. */
+static void clamp_w(orc *o, double *w)
+{
+    double added = 0.0;
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j);
+            if (w[c] < o->Bbar[c]) {
+                added += o->Bbar[c] - w[c];
+                w[c] = o->Bbar[c];
+            }
+        }
+    o->clamp_mass += added * o->p.dx * o->p.dy;
+}
+
+static void dry_zero(orc *o, const double *w, double *P, double *Q)
+{
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j);
+            if (w[c] - o->Bbar[c] <= 0.0) {
+                P[c] = 0.0;
+                Q[c] = 0.0;
+            }
+        }
+}
+
+static void record_gauges(orc *o)
+{
+    if (o->ng <= 0 || o->log_every <= 0 || o->cap <= 0) return;
+    if (o->step % o->log_every != 0) return;
+    int slot = (o->head + o->nrec) % o->cap;
+    if (o->nrec == o->cap) { /* full: keep the newest capacity records */
+        slot = o->head;
+        o->head = (o->head + 1) % o->cap;
+    } else {
+        o->nrec++;
+    }
+    for (int gk = 0; gk < o->ng; gk++) {
+        int i = o->gij[2 * gk], j = o->gij[2 * gk + 1];
+        o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)] - o->p.ws;
+    }
+}
+
+/* -------------------------------------------------------------- the step */
+
+static void swap3(double **h)
+{
+    double *t = h[2];
+    h[2] = h[1];
+    h[1] = h[0];
+    h[0] = t;
+}
+
+int orc_step(orc *o, int nsteps)
+{
+    if (!o || nsteps < 0) return -1;
+    const int nx = o->nx, ny = o->ny;
+    const double dt = o->p.dt;
+    const int bsnq = o->p.model == ORC_BSNQ;
+    for (int s = 0; s < nsteps; s++) {
+        double t0 = (double)o->step * dt, t1 = (double)(o->step + 1) * dt;
+        fill_ghosts(o, o->w, o->P, o->Q, t0);
+        compute_rhs(o, o->w, o->P, o->Q, o->E[0], o->F[0], o->G[0], o->Fs[0], o->Gs[0]);
+        compute_ustar(o, o->P, o->Q, o->U, o->V);
+        /* Sec. 2.3: forward Euler for the first two steps after a (re)start,
+         * the AM4 corrector only once AB3 runs (Reading A-T1, A-T2). */
+        const int Kn = o->nh >= 2 ? o->p.K : 0;
+        for (int stage = 0; stage <= Kn; stage++) {
+            if (stage == 0) {
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        size_t c = IX(o, i, j);
+                        if (o->nh == 0) { /* Euler; F* increment zero */
+                            o->w1[c] = o->w[c] + dt * o->E[0][c];
+                            o->U1[c] = o->U[c] + dt * o->F[0][c];
+                            o->V1[c] = o->V[c] + dt * o->G[0][c];
+                        } else if (o->nh == 1) { /* Euler; F*^1 - F*^0 */
+                            o->w1[c] = o->w[c] + dt * o->E[0][c];
+                            o->U1[c] = o->U[c] + dt * o->F[0][c] + (o->Fs[0][c] - o->Fs[1][c]);
+                            o->V1[c] = o->V[c] + dt * o->G[0][c] + (o->Gs[0][c] - o->Gs[1][c]);
+                        } else { /* Eq. 15-17 */
+                            o->w1[c] = o->w[c] + dt / 12.0 *
+                                (23.0 * o->E[0][c] - 16.0 * o->E[1][c] + 5.0 * o->E[2][c]);
+                            o->U1[c] = o->U[c] + dt / 12.0 *
+                                (23.0 * o->F[0][c] - 16.0 * o->F[1][c] + 5.0 * o->F[2][c]) +
+                                2.0 * o->Fs[0][c] - 3.0 * o->Fs[1][c] + o->Fs[2][c];
+                            o->V1[c] = o->V[c] + dt / 12.0 *
+                                (23.0 * o->G[0][c] - 16.0 * o->G[1][c] + 5.0 * o->G[2][c]) +
+                                2.0 * o->Gs[0][c] - 3.0 * o->Gs[1][c] + o->Gs[2][c];
+                        }
+                    }
+            } else { /* Eq. 18-20 at the previous iterate */
+                fill_ghosts(o, o->w1, o->P1, o->Q1, t1);
+                compute_rhs(o, o->w1, o->P1, o->Q1, o->Ec, o->Fc, o->Gc, o->Fsc, o->Gsc);
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        size_t c = IX(o, i, j);
+                        o->w1[c] = o->w[c] + dt / 24.0 *
+                            (9.0 * o->Ec[c] + 19.0 * o->E[0][c] - 5.0 * o->E[1][c] + o->E[2][c]);
+                        o->U1[c] = o->U[c] + dt / 24.0 *
+                            (9.0 * o->Fc[c] + 19.0 * o->F[0][c] - 5.0 * o->F[1][c] + o->F[2][c]) +
+                            o->Fsc[c] - o->Fs[0][c];
+                        o->V1[c] = o->V[c] + dt / 24.0 *
+                            (9.0 * o->Gc[c] + 19.0 * o->G[0][c] - 5.0 * o->G[1][c] + o->G[2][c]) +
+                            o->Gsc[c] - o->Gs[0][c];
+                    }
+            }
+            clamp_w(o, o->w1);
+            if (bsnq) {
+                solve_lines(o, 0, o->U1, o->P1, t1);
+                solve_lines(o, 1, o->V1, o->Q1, t1);
+            } else {
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        size_t c = IX(o, i, j);
+                        o->P1[c] = o->U1[c];
+                        o->Q1[c] = o->V1[c];
+                    }
+            }
+            if (stage == Kn) { /* Eq. 30 once per step (Reading A-B3) */
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        double gam = sponge_at(o, i, j);
+                        if (gam >= 1.0) continue;
+                        size_t c = IX(o, i, j);
+                        if (o->d[c] > 0.0) o->w1[c] = o->p.ws + gam * (o->w1[c] - o->p.ws);
+                        o->P1[c] *= gam;
+                        o->Q1[c] *= gam;
+                    }
+            }
+            dry_zero(o, o->w1, o->P1, o->Q1);
+        }
+        swap3(o->E); swap3(o->F); swap3(o->G); swap3(o->Fs); swap3(o->Gs);
+        double *t;
+        t = o->w; o->w = o->w1; o->w1 = t;
+        t = o->P; o->P = o->P1; o->P1 = t;
+        t = o->Q; o->Q = o->Q1; o->Q1 = t;
+        o->step++;
+        o->nh++;
+        record_gauges(o);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ API */
+
+orc *orc_create(const orc_params *p, const double *z)
+{
+    if (!p || !z || p->nx < 2 || p->ny < 2 || !(p->dx > 0) || !(p->dy > 0) ||
+        !(p->dt > 0) || p->K < 0 || !(p->eps > 0))
+        return NULL;
+    orc *o = (orc *)calloc(1, sizeof(orc));
+    o->p = *p;
+    o->nx = p->nx;
+    o->ny = p->ny;
+    o->ex = p->nx + 4;
+    o->ey = p->ny + 4;
+    size_t ne = (size_t)o->ex * (size_t)o->ey;
+    double **cell[] = {&o->z, &o->Bbar, &o->d, &o->ddx, &o->ddy, &o->w, &o->P,
+                       &o->Q, &o->w1, &o->P1, &o->Q1, &o->U, &o->V, &o->U1,
+                       &o->V1, &o->Ec, &o->Fc, &o->Gc, &o->Fsc, &o->Gsc};
+    for (size_t k = 0; k < sizeof(cell) / sizeof(cell[0]); k++)
+        *cell[k] = (double *)calloc(ne, sizeof(double));
+    for (int k = 0; k < 3; k++) {
+        o->E[k] = (double *)calloc(ne, sizeof(double));
+        o->F[k] = (double *)calloc(ne, sizeof(double));
+        o->G[k] = (double *)calloc(ne, sizeof(double));
+        o->Fs[k] = (double *)calloc(ne, sizeof(double));
+        o->Gs[k] = (double *)calloc(ne, sizeof(double));
+        o->Hx[k] = (double *)calloc((size_t)(p->nx + 1) * p->ny, sizeof(double));
+        o->Hy[k] = (double *)calloc((size_t)p->nx * (p->ny + 1), sizeof(double));
+    }
+    o->Bc = (double *)calloc((size_t)(p->nx + 3) * (p->ny + 3), sizeof(double));
+    for (int s = 0; s < 4; s++) o->bc[s].type = ORC_SOLID;
+    derive_static(o, z);
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j);
+            o->w[c] = fmax(p->ws, o->Bbar[c]);
+        }
+    return o;
+}
+
+void orc_destroy(orc *o)
+{
+    if (!o) return;
+    double *cell[] = {o->z, o->Bbar, o->d, o->ddx, o->ddy, o->w, o->P, o->Q,
+                      o->w1, o->P1, o->Q1, o->U, o->V, o->U1, o->V1, o->Ec,
+                      o->Fc, o->Gc, o->Fsc, o->Gsc, o->Bc};
+    for (size_t k = 0; k < sizeof(cell) / sizeof(cell[0]); k++) free(cell[k]);
+    for (int k = 0; k < 3; k++) {
+        free(o->E[k]); free(o->F[k]); free(o->G[k]); free(o->Fs[k]);
+        free(o->Gs[k]); free(o->Hx[k]); free(o->Hy[k]);
+    }
+    free(o->gij);
+    free(o->grec);
+    free(o);
+}
+
+int orc_set_boundary(orc *o, int side, const orc_bc *bc)
+{
+    if (!o || !bc || side < 0 || side > 3 || bc->type < ORC_SOLID ||
+        bc->type > ORC_SINE || bc->ncomp < 0 || bc->ncomp > 8 || bc->width < 0)
+        return -1;
+    o->bc[side] = *bc;
+    return 0;
+}
+
+int orc_set_state(orc *o, const double *w, const double *P, const double *Q)
+{
+    if (!o || !w || !P || !Q) return -1;
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j), k = (size_t)j * o->nx + i;
+            o->w[c] = fmax(w[k], o->Bbar[c]);
+            o->P[c] = P[k];
+            o->Q[c] = Q[k];
+        }
+    dry_zero(o, o->w, o->P, o->Q);
+    o->nh = 0;
+    return 0;
+}
+
+/* Eq. 33-36 (Reading A-S1): d is the still-water depth of the cell holding
+ * the crest; the wave is added where d > 0. */
+int orc_add_solitary(orc *o, double H, double theta, double x0, double y0)
+{
+    if (!o) return -1;
+    int ic = (int)floor(x0 / o->p.dx), jc = (int)floor(y0 / o->p.dy);
+    ic = ic < 0 ? 0 : (ic > o->nx - 1 ? o->nx - 1 : ic);
+    jc = jc < 0 ? 0 : (jc > o->ny - 1 ? o->ny - 1 : jc);
+    double ds = o->d[IX(o, ic, jc)];
+    if (!(ds > 0.0) || !(H + ds > 0.0)) return -1;
+    double ks = sqrt(3.0 * fabs(H) / (4.0 * ds * ds * ds));
+    double cs = sqrt(o->p.g * (H + ds));
+    double ct = cos(theta), st = sin(theta);
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j);
+            if (!(o->d[c] > 0.0)) continue;
+            double xi = ((i + 0.5) * o->p.dx - x0) * ct + ((j + 0.5) * o->p.dy - y0) * st;
+            double sh = 1.0 / cosh(ks * xi);
+            double es = H * sh * sh;
+            o->w[c] = fmax(o->w[c] + es, o->Bbar[c]);
+            o->P[c] += cs * es * ct;
+            o->Q[c] += cs * es * st;
+        }
+    dry_zero(o, o->w, o->P, o->Q);
+    o->nh = 0;
+    return 0;
+}
+
+void orc_get_state(const orc *o, double *w, double *P, double *Q)
+{
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j), k = (size_t)j * o->nx + i;
+            if (w) w[k] = o->w[c];
+            if (P) P[k] = o->P[c];
+            if (Q) Q[k] = o->Q[c];
+        }
+}
+
+int orc_get_field(const orc *o, int which, double *out)
+{
+    const double *src = which == 0 ? o->Bbar : which == 1 ? o->d
+                        : which == 2 ? o->U : which == 3 ? o->V : NULL;
+    if (!src || !out) return -1;
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) out[(size_t)j * o->nx + i] = src[IX(o, i, j)];
+    return 0;
+}
+
+void orc_get_time(const orc *o, double *t, long long *step)
+{
+    if (t) *t = (double)o->step * o->p.dt;
+    if (step) *step = o->step;
+}
+
+double orc_mass(const orc *o)
+{
+    double m = 0.0;
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j);
+            m += o->w[c] - o->Bbar[c];
+        }
+    return m * o->p.dx * o->p.dy;
+}
+
+double orc_clamp_mass(const orc *o) { return o->clamp_mass; }
+
+int orc_set_gauges(orc *o, const int *ij, int n, int log_every, int capacity)
+{
+    if (!o || n < 0 || (n > 0 && !ij) || log_every < 0 || capacity < 0) return -1;
+    for (int k = 0; k < n; k++)
+        if (ij[2 * k] < 0 || ij[2 * k] >= o->nx || ij[2 * k + 1] < 0 || ij[2 * k + 1] >= o->ny)
+            return -1;
+    free(o->gij);
+    free(o->grec);
+    o->gij = n ? (int *)malloc(sizeof(int) * 2 * (size_t)n) : NULL;
+    if (n) memcpy(o->gij, ij, sizeof(int) * 2 * (size_t)n);
+    o->grec = (n && capacity) ? (double *)calloc((size_t)n * capacity, sizeof(double)) : NULL;
+    o->ng = n;
+    o->log_every = log_every;
+    o->cap = capacity;
+    o->nrec = 0;
+    o->head = 0;
+    return 0;
+}
+
+int orc_read_gauges(orc *o, double *eta, int max_rec, int *n_rec)
+{
+    if (!o || !n_rec || max_rec < 0) return -1;
+    int n = o->nrec < max_rec ? o->nrec : max_rec;
+    for (int r = 0; r < n; r++) {
+        int slot = (o->head + r) % (o->cap ? o->cap : 1);
+        for (int gk = 0; gk < o->ng; gk++)
+            eta[(size_t)r * o->ng + gk] = o->grec[(size_t)slot * o->ng + gk];
+    }
+    o->head = o->cap ? (o->head + n) % o->cap : 0;
+    o->nrec -= n;
+    *n_rec = n;
+    return 0;
+}

@@ -1,0 +1,64 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake (a dropped term, a wrong sign, a wrong index or
+coefficient) in a copy of the oracle's C source, builds it in a temporary
+directory and runs the pin that should catch it against that copy, in a child
+process.  The pin must fail.  The real oracle is never modified.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "celeris_oracle.c")
+
+MUTANTS = [
+    # (name, original text, mutated text, pin that must fail)
+    ("drop_Fstar", "fs = dd * dxd * Qy / 6.0 + dd * dyd * Qx / 6.0 + B3 * dd * dd * Qxy;",
+     "fs = dd * dxd * Qy / 6.0 + dd * dyd * Qx / 6.0;", "test_dispersion_relation_2d_oblique"),
+    ("sign_exyy", "Bd * g * dd * dd * dd * (exxx + exyy)", "Bd * g * dd * dd * dd * (exxx - exyy)",
+     "test_dispersion_relation_2d_oblique"),
+    ("drop_exxx", "Bd * g * dd * dd * dd * (exxx + exyy)", "Bd * g * dd * dd * dd * (exyy)",
+     "test_dispersion_relation_1d"),
+    ("bed_slope_sign", "g * hb * (Bx(o, i + 1, j) - Bx(o, i, j)) / dx;",
+     "g * hb * (Bx(o, i, j) - Bx(o, i + 1, j)) / dx;", "test_lake_at_rest_submerged"),
+    ("ab3_coef", "(23.0 * o->E[0][c] - 16.0 * o->E[1][c] + 5.0 * o->E[2][c])",
+     "(23.0 * o->E[0][c] - 15.0 * o->E[1][c] + 5.0 * o->E[2][c])", "test_dispersion_relation_1d"),
+    ("ab3_U_coef", "(23.0 * o->F[0][c] - 16.0 * o->F[1][c] + 5.0 * o->F[2][c])",
+     "(23.0 * o->F[0][c] - 16.0 * o->F[1][c] + 4.0 * o->F[2][c])", "test_friction_quadratic_order"),
+    ("wall_no_negate", "P[gc] = -P[sc];", "P[gc] = P[sc];", "test_mass_soliton_channel"),
+    ("eq23_sign_s", "*a = s - r;", "*a = -s - r;", "test_symmetry_mirror_x"),
+    ("tridiag_B", "*b = 1.0 + 2.0 * r;", "*b = 1.0 + r;", "test_dispersion_relation_1d"),
+    ("hydrostatic_half", "FL1 = qnL * uL + 0.5 * g * hL * hL", "FL1 = qnL * uL + g * hL * hL",
+     "test_lake_at_rest_submerged"),
+    ("flux_mass_diffusion_sign", "ap * am * (wR - wL)", "ap * am * (wL - wR)", "test_ritter_dam_break"),
+    ("friction_h_power", "f -= fc * P[c] * mag * hinv * hinv;", "f -= fc * P[c] * mag * hinv;",
+     "test_friction_manning_ode"),
+    ("soliton_ks", "sqrt(3.0 * fabs(H) / (4.0 * ds * ds * ds))", "sqrt(3.0 * fabs(H) / (2.0 * ds * ds * ds))",
+     "test_soliton_speed"),
+    ("eckart", "return k0 * sqrt(1.0 / tanh(k0 * d));", "return k0 * (1.0 / tanh(k0 * d));",
+     "test_eckart_vs_exact_dispersion"),
+    ("transpose_y_solve", "coef23(o->p.Bd, o->p.dy, o->d[c], o->ddy[c], &a, &b, &cc);",
+     "coef23(o->p.Bd, o->p.dy, o->d[c], o->ddx[c], &a, &b, &cc);", "test_lake_at_rest_submerged"),
+]
+
+
+@pytest.mark.parametrize("name,orig,mut,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pin_catches_mutant(tmp_path, name, orig, mut, pin):
+    src = open(SRC).read()
+    assert src.count(orig) >= 1, f"mutation site for {name} not found"
+    mdir = tmp_path / "oracle_mutant"
+    mdir.mkdir()
+    (mdir / "celeris_oracle.c").write_text(src.replace(orig, mut, 1))
+    hdr = os.path.join(ROOT, "oracle", "celeris_oracle.h")
+    (mdir / "celeris_oracle.h").write_text(open(hdr).read())
+    so = mdir / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fopenmp", "-ffp-contract=off", "-fPIC",
+                    "-shared", "-o", str(so), str(mdir / "celeris_oracle.c"), "-lm"], check=True)
+    env = dict(os.environ, ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", pin],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pin {pin} did not catch mutant {name}:\n{r.stdout[-2000:]}"

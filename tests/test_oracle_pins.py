@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check is a closed form,
+an invariant, a textbook routine, a special case or a convergence order.
+
+  Part of the oracle                      Pin (test below)
+  --------------------------------------  --------------------------------------
+  Thomas solver (Eq. 21-23 solves)        dense LAPACK solve        test_thomas_*
+  minmod (KP07 step 1)                    hand cases                test_minmod_*
+  Eckart k (Eq. 29)                       Newton on w^2 = gk tanh kd test_eckart_*
+  sponge gamma (Eq. 30)                   end values, monotone      test_sponge_*
+  central-upwind flux (KP07 step 3)       consistency, upwinding    test_central_*
+  reconstruction + flux + bed slope       lake at rest              test_lake_*
+  flux form, walls, AB3 / AM4             mass conservation         test_mass_*
+  NLSW path, dry front                    Ritter closed form        test_ritter_*
+  dispersion terms, tridiagonal, F*, G*   linear dispersion relation test_dispersion_*
+  ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
+  soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36)  test_soliton_*
+  friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders   test_friction_*
+  AB3 stability (Sec. 2.3)                real-axis bound -6/11     test_stability_*
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_05984_gb300 import scenarios as sc
+from tests.helpers import oracle_from
+
+G = 9.81
+B = 1.0 / 15.0
+
+
+# --------------------------------------------------------------- pieces
+
+def test_thomas_vs_dense(oracle_mod):
+    rng = np.random.default_rng(11)
+    for n in list(range(1, 33)) + [97, 256]:
+        a = rng.uniform(-1, 1, n)
+        c = rng.uniform(-1, 1, n)
+        a[0] = 0.0
+        c[-1] = 0.0
+        b = np.abs(a) + np.abs(c) + rng.uniform(0.1, 2.0, n)
+        b *= rng.choice([-1.0, 1.0], n)
+        r = rng.standard_normal(n)
+        M = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+        x = oracle_mod.thomas(a, b, c, r)
+        ref = np.linalg.solve(M, r)
+        assert np.max(np.abs(x - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_minmod_cases(oracle_mod):
+    mm = oracle_mod.minmod
+    assert mm(1.3, 0.0, 1.0, 2.0) == pytest.approx(1.0)        # linear: central
+    assert mm(1.3, 0.0, 1.0, 1.1) == pytest.approx(0.13)       # theta * forward
+    assert mm(2.0, 0.0, 0.1, 5.0) == pytest.approx(0.2)        # theta * backward
+    assert mm(1.3, 0.0, 1.0, 0.5) == 0.0                       # extremum
+    assert mm(1.3, 2.0, 1.0, 0.0) == pytest.approx(-1.0)       # decreasing
+    assert mm(1.0, 0.0, 1.0, 3.0) == pytest.approx(1.0)        # theta=1: minmod(fwd,bwd)
+
+
+def _airy_k(omega, d):
+    k = omega / math.sqrt(G * d)
+    for _ in range(100):
+        f = G * k * math.tanh(k * d) - omega ** 2
+        fp = G * math.tanh(k * d) + G * k * d / math.cosh(k * d) ** 2
+        k -= f / fp
+    return k
+
+
+def test_eckart_vs_exact_dispersion(oracle_mod):
+    d = 1.0
+    for kd in np.geomspace(0.05, 10.0, 40):
+        k = kd / d
+        omega = math.sqrt(G * k * math.tanh(kd))
+        ke = oracle_mod.eckart_k(omega, d)
+        assert abs(ke / _airy_k(omega, d) - 1.0) < 0.06
+    # limits: deep water k = w^2/g; shallow k -> w/sqrt(gd)
+    om = 10.0
+    assert oracle_mod.eckart_k(om, 50.0) == pytest.approx(om * om / G, rel=1e-12)
+    om = 0.01
+    assert oracle_mod.eckart_k(om, 1.0) == pytest.approx(om / math.sqrt(G), rel=1e-4)
+
+
+def test_sponge_gamma(oracle_mod):
+    g = oracle_mod.sponge_gamma
+    L = 20.0
+    assert g(0.0, L) == pytest.approx(0.0, abs=1e-15)
+    assert g(L, L) == 1.0
+    assert g(5 * L, L) == 1.0
+    assert g(0.5 * L, L) == pytest.approx(0.5)
+    v = [g(D, L) for D in np.linspace(0, L, 101)]
+    assert all(b >= a for a, b in zip(v, v[1:]))
+
+
+def test_central_upwind_consistency(oracle_mod):
+    cu = oracle_mod.central_upwind
+    eps = 5e-12
+    # identical states: flux equals the physical flux F(U) (Eq. 1)
+    h, u, v, Bf = 2.0, 0.7, -0.3, -1.5
+    w = Bf + h
+    H = cu(G, eps, w, h * u, h * v, w, h * u, h * v, Bf)
+    assert H == pytest.approx([h * u, h * u * u + 0.5 * G * h * h, h * u * v], rel=1e-13)
+    # lake at rest: hydrostatic momentum flux only
+    H = cu(G, eps, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, -3.0)
+    assert H == pytest.approx([0.0, 0.5 * G * 9.0, 0.0], abs=1e-13)
+    # supercritical to the right: pure upwinding, H = F(U_left)
+    hL, uL, hR, uR = 0.5, 10.0, 0.4, 9.0
+    H = cu(G, eps, hL, hL * uL, 0.0, hR, hR * uR, 0.0, 0.0)
+    assert H == pytest.approx([hL * uL, hL * uL * uL + 0.5 * G * hL * hL, 0.0], rel=1e-12)
+    # both sides dry
+    assert list(cu(G, eps, 1.0, 0.3, 0.1, 1.0, -0.2, 0.0, 1.0)) == [0.0, 0.0, 0.0]
+
+
+# -------------------------------------------------------------- invariants
+
+def test_lake_at_rest_submerged(oracle_mod):
+    """KP07 with corner bed values is exactly well-balanced when submerged."""
+    nx, ny = 64, 48
+    z = sc.random_bed(nx, ny, 5, -9.0, -1.0, smooth=2)
+    dmax = 9.0
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * dmax), K=1,
+                          friction=2, fcoef=0.015)
+    o.set_state(np.zeros_like(z), np.zeros_like(z), np.zeros_like(z))
+    o.step(1000)
+    w, P, Q = o.state()
+    bound = 1e-12 * math.sqrt(G * dmax) * dmax
+    assert np.max(np.abs(P)) <= bound and np.max(np.abs(Q)) <= bound
+    assert np.max(np.abs(w)) <= 1e-13
+
+
+@pytest.mark.parametrize("K", [0, 2])
+def test_mass_soliton_channel(oracle_mod, K):
+    s = sc.soliton_channel(K=K)
+    o = oracle_from(s)
+    m0 = o.mass()
+    o.step(1000)
+    assert o.clamp_mass() == 0.0
+    assert abs(o.mass() - m0) <= 1e-13 * abs(m0)
+
+
+def test_mass_2d_closed_basin(oracle_mod):
+    nx, ny = 64, 48
+    z = sc.random_bed(nx, ny, 7, -3.0, -1.0, smooth=3)
+    X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
+    eta = 0.2 * np.exp(-((X - 20) ** 2 + (Y - 25) ** 2) / 30.0)
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * 3.0), K=1,
+                          friction=2, fcoef=0.02)
+    o.set_state(eta, 0 * z, 0 * z)
+    m0 = o.mass()
+    o.step(1000)
+    assert o.clamp_mass() == 0.0
+    assert abs(o.mass() - m0) <= 1e-13 * abs(m0)
+
+
+# ------------------------------------------------------------ closed forms
+
+def _ritter_l1(oracle_mod, dx, T=1.5):
+    L0, L1 = -8.0, 12.0
+    nx, ny = int(round((L1 - L0) / dx)), 2
+    x = L0 + (np.arange(nx) + 0.5) * dx
+    z = np.zeros((ny, nx))
+    dt = 0.1 * dx / math.sqrt(G)      # front moves at 2 sqrt(g h0)
+    o = oracle_mod.Oracle(z, dx, dx, dt, model=oracle_mod.NLSW)
+    o.set_state(np.tile(np.where(x < 0, 1.0, 0.0), (ny, 1)), 0 * z, 0 * z)
+    n = int(round(T / dt))
+    o.step(n)
+    t = n * dt
+    w, _, _ = o.state()
+    c0 = math.sqrt(G)
+    h_ex = np.where(x < -c0 * t, 1.0,
+                    np.where(x > 2 * c0 * t, 0.0, (2 * c0 - x / t) ** 2 / (9 * G)))
+    m = (x > -c0 * t - 1.0) & (x < 2 * c0 * t + 1.0)
+    assert np.array_equal(w[0], w[1])
+    return float(np.sum(np.abs(w[0] - h_ex)[m]) / np.sum(h_ex[m]))
+
+
+def test_ritter_dam_break(oracle_mod):
+    e1 = _ritter_l1(oracle_mod, 0.02)
+    e2 = _ritter_l1(oracle_mod, 0.01)
+    assert e2 <= 0.02 and e1 <= 0.02
+    assert e2 < 0.75 * e1
+
+
+def _omega(k, d):
+    return k * math.sqrt(G * d * (1 + B * (k * d) ** 2) / (1 + (B + 1 / 3) * (k * d) ** 2))
+
+
+def _standing_period_error(oracle_mod, kd, cpl, twod=False, periods=3):
+    """Standing mode eta = a cos(kx x)[cos(ky y)] in a walled basin; period
+    from the zero crossings of eta at the corner cell vs the linear
+    dispersion relation of Eq. 2 / 7 / 10 (flat bed)."""
+    d = 1.0
+    k = kd / d
+    if twod:
+        kx = ky = k / math.sqrt(2)
+        nx = ny = cpl
+    else:
+        kx, ky, nx, ny = k, 0.0, cpl, 2
+    dx = 2 * math.pi / kx / cpl
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
+    eta = 1e-4 * d * np.cos(kx * X) * (np.cos(ky * Y) if twod else 1.0)
+    z = np.full((ny, nx), -d)
+    dt = 0.2 * dx / math.sqrt(G * d)
+    o = oracle_mod.Oracle(z, dx, dx, dt, K=1 if twod else 0)
+    o.set_state(eta, 0 * z, 0 * z)
+    T = 2 * math.pi / _omega(k, d)
+    n = int(periods * T / dt) + 2
+    sig = np.empty(n)
+    for s in range(n):
+        o.step(1)
+        sig[s] = o.state()[0][0, 0]
+    t = (np.arange(n) + 1) * dt
+    zc = [t[s] - sig[s] * dt / (sig[s + 1] - sig[s])
+          for s in range(n - 1) if sig[s] * sig[s + 1] < 0]
+    return abs(2 * np.mean(np.diff(zc)) / T - 1)
+
+
+@pytest.mark.parametrize("kd", [0.5, 1.0, 2.0, 3.0])
+def test_dispersion_relation_1d(oracle_mod, kd):
+    e64 = _standing_period_error(oracle_mod, kd, 64)
+    e128 = _standing_period_error(oracle_mod, kd, 128)
+    assert e64 <= 5e-3
+    assert e128 <= e64 / 3.0          # second order in space
+
+
+@pytest.mark.parametrize("kd", [1.0, 2.0])
+def test_dispersion_relation_2d_oblique(oracle_mod, kd):
+    """An oblique mode needs the mixed terms of Eq. 10-13 (F*, G*, eta_xyy)."""
+    e32 = _standing_period_error(oracle_mod, kd, 32, twod=True)
+    e64 = _standing_period_error(oracle_mod, kd, 64, twod=True)
+    assert e64 <= 5e-3
+    assert e64 <= e32 / 3.0
+
+
+def test_soliton_speed(oracle_mod):
+    """Eq. 33-36 on a long flat channel: crest speed c_s = sqrt(g(H+d))."""
+    H, d, dx, ny = 0.1, 1.0, 0.05, 2
+    nx = int(130.0 / dx)
+    z = np.full((ny, nx), -d)
+    dt = 0.2 * dx / math.sqrt(G * d)
+    o = oracle_mod.Oracle(z, dx, dx, dt)
+    o.set_state(0 * z, 0 * z, 0 * z)
+    o.add_solitary(H, 0.0, 15.0, ny * dx / 2)
+    x = (np.arange(nx) + 0.5) * dx
+
+    def crest():
+        w = o.state()[0][0]
+        i = int(np.argmax(w))
+        y0, y1, y2 = w[i - 1], w[i], w[i + 1]
+        return x[i] + 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2) * dx, y1
+
+    n1, n2 = int(5.0 / dt), int(30.0 / dt)
+    o.step(n1)
+    xa, ha = crest()
+    o.step(n2 - n1)
+    xb, hb = crest()
+    c = (xb - xa) / ((n2 - n1) * dt)
+    assert abs(c / math.sqrt(G * (H + d)) - 1) <= 0.03
+    assert hb >= 0.95 * H
+
+
+def _uniform_friction_error(oracle_mod, dt, f=0.5, P0=0.5, h=1.0, T=2.0, kind=1):
+    nx, ny, dx = 400, 2, 0.1
+    z = np.full((ny, nx), -h)
+    o = oracle_mod.Oracle(z, dx, dx, dt, model=oracle_mod.NLSW, friction=kind, fcoef=f)
+    o.set_state(0 * z, P0 + 0 * z, 0 * z)
+    n = int(round(T / dt))
+    o.step(n)
+    return o.state()[1][0, nx // 2], n * dt
+
+
+def test_friction_quadratic_order(oracle_mod):
+    """Eq. 31 with constant f on a uniform flow: P' = -f P|P|/h^2, exactly
+    P(t) = P0/(1 + f P0 t/h^2).  The two forward-Euler start-up steps
+    (Sec. 2.3) give the O(dt^2) error -2 a^2 P0^3 dt^2/(1 + a P0 T)^2,
+    a = f/h^2; what remains is the AB3 error, O(dt^3)."""
+    f, P0, h = 0.5, 0.5, 1.0
+    a = f / h ** 2
+    res = []
+    for dt in (0.008, 0.004, 0.002):
+        P, T = _uniform_friction_error(oracle_mod, dt, f=f, P0=P0, h=h)
+        err = P - P0 / (1 + a * P0 * T)
+        startup = -2 * a * a * P0 ** 3 * dt * dt / (1 + a * P0 * T) ** 2
+        assert err == pytest.approx(startup, rel=0.05)
+        res.append(abs(err - startup))
+    assert math.log2(res[0] / res[1]) >= 2.7
+    assert math.log2(res[1] / res[2]) >= 2.7
+
+
+def test_friction_manning_ode(oracle_mod):
+    """Eq. 32: f = g n^2 / h^(1/3); compare with a quadrature of the ODE."""
+    from scipy.integrate import solve_ivp
+    n_m, P0, h, T = 0.03, 0.8, 0.5, 2.0
+    fm = G * n_m ** 2 / h ** (1 / 3)
+    sol = solve_ivp(lambda t, p: -fm * p * np.abs(p) / h ** 2, (0, T), [P0],
+                    rtol=1e-12, atol=1e-14)
+    ref = sol.y[0, -1]
+    P, _ = _uniform_friction_error(oracle_mod, 0.002, f=n_m, P0=P0, h=h, T=T, kind=2)
+    assert P == pytest.approx(ref, rel=1e-5)
+
+
+# --------------------------------------------------------------- symmetry
+
+def test_symmetry_mirror_x(oracle_mod):
+    nx, ny = 96, 4
+    dx = 0.05
+    x = (np.arange(nx) + 0.5) * dx
+    z = np.full((ny, nx), -1.0) + 0.3 * np.exp(-((x - nx * dx / 2) / 0.8) ** 2)
+    eta = 0.05 * np.exp(-((x - nx * dx / 2) / 0.5) ** 2)
+    o = oracle_mod.Oracle(z, dx, dx, 0.2 * dx / math.sqrt(G), K=0)
+    o.set_state(np.tile(eta, (ny, 1)), 0 * z, 0 * z)
+    o.step(400)
+    w, P, Q = o.state()
+    scale = np.max(np.abs(w))
+    assert np.max(np.abs(w - w[:, ::-1])) <= 1e-12 * scale
+    assert np.max(np.abs(P + P[:, ::-1])) <= 1e-12 * max(np.max(np.abs(P)), 1e-30)
+    assert np.all(Q == 0.0)
+    assert np.max(np.abs(w - w[0:1])) == 0.0          # stays y-uniform
+
+
+def test_symmetry_transpose(oracle_mod):
+    n = 48
+    z = sc.random_bed(n, n, 3, -3.0, -1.5, smooth=3)
+    z = 0.5 * (z + z.T)
+    X, Y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+    eta = 0.1 * np.exp(-((X - 18) ** 2 + (Y - 30) ** 2) / 20.0)
+    eta = eta + eta.T
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * 3.0), K=1)
+    o.set_state(eta, 0 * z, 0 * z)
+    o.step(300)
+    w, P, Q = o.state()
+    assert np.max(np.abs(w - w.T)) <= 1e-12 * np.max(np.abs(w))
+    assert np.max(np.abs(P - Q.T)) <= 1e-12 * np.max(np.abs(P))
+
+
+# -------------------------------------------------------------- stability
+
+def _growth(oracle_mod, cr, model, K, depth=9.0, dx=1.0, n=32, steps=1500):
+    z = np.full((n, n), -depth)
+    rng = np.random.default_rng(0)
+    o = oracle_mod.Oracle(z, dx, dx, cr * dx / math.sqrt(G * depth), model=model, K=K)
+    o.set_state(1e-6 * rng.standard_normal((n, n)), 0 * z, 0 * z)
+    o.step(steps)
+    P = o.state()[1]
+    return float(np.max(np.abs(P))) if np.all(np.isfinite(P)) else math.inf
+
+
+def test_stability_ab3_real_axis_bound(oracle_mod):
+    """KP07 damps a 2-D checkerboard at rate -4c/dx; AB3 (Eq. 15-17) is
+    stable on the negative real axis only down to -6/11, so the NLSW step
+    is stable for Courant < 3/22 = 0.136 and not above."""
+    assert _growth(oracle_mod, 0.13, oracle_mod.NLSW, 0) < 1e-4
+    assert _growth(oracle_mod, 0.145, oracle_mod.NLSW, 0) > 1.0
+
+
+def test_stability_corrector_parity(oracle_mod):
+    """With depth/dx >> 1 the explicitly extrapolated mixed terms (F*, G*)
+    grow for K = 0 and even K and are bounded for odd K."""
+    assert _growth(oracle_mod, 0.1, oracle_mod.BSNQ, 0, steps=600) > 1.0
+    assert _growth(oracle_mod, 0.1, oracle_mod.BSNQ, 1) < 1e-4
+    assert _growth(oracle_mod, 0.1, oracle_mod.BSNQ, 2, steps=600) > 1.0
+    assert _growth(oracle_mod, 0.1, oracle_mod.BSNQ, 3) < 1e-4
+
+
+# ------------------------------------------------------------ host logic
+
+def test_set_state_clamps_to_bed(oracle_mod):
+    z = np.array([[-1.0, -1.0, 0.5, 1.0]] * 3)
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.01)
+    o.set_state(np.zeros_like(z), np.ones_like(z), np.ones_like(z))
+    w, P, Q = o.state()
+    Bb = o.field("Bbar")
+    assert np.all(w >= Bb)
+    dry = (w - Bb) <= 0
+    assert dry.any()
+    assert np.all(P[dry] == 0) and np.all(Q[dry] == 0)
+    assert np.all(P[~dry] == 1)
+
+
+def test_add_solitary_rejects_dry_crest(oracle_mod):
+    z = np.array([[-1.0] * 4 + [1.0] * 4] * 3)
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.01)
+    with pytest.raises(ValueError):
+        o.add_solitary(0.1, 0.0, 7.5, 1.5)
+    o.add_solitary(0.1, 0.0, 1.5, 1.5)
+
+
+def test_gauge_ring(oracle_mod):
+    s = sc.soliton_channel(steps=0)
+    o = oracle_from(s)
+    o.set_gauges([(10, 5), (200, 16)], log_every=3, capacity=4)
+    o.step(20)                 # records at steps 3,6,...,18 -> 6, keeps last 4
+    rec = o.read_gauges(10)
+    assert rec.shape == (4, 2)
+    o2 = oracle_from(s)
+    etas = []
+    for n in range(1, 21):
+        o2.step(1)
+        if n % 3 == 0:
+            w = o2.state()[0]
+            etas.append([w[5, 10], w[16, 200]])
+    np.testing.assert_array_equal(rec, np.array(etas[-4:]))
+    assert o.read_gauges(10).shape == (0, 2)
