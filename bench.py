@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the Celeris extended-Boussinesq step on GB300.
+
+Metric: cell-updates/s (interior cells x time steps / second) of the full
+time step (stencil + update, x-line and y-line tridiagonal solves, for the
+AB3 predictor and the AM4 corrector stage) on the 2048 x 2048 beach-and-shoal
+workload (FP32, seeded synthetic bed: 1:30 beach, 8 Gaussian shoals, sine
+maker on the west, 50-cell sponges north and south, Manning n = 0.015).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  N > 1 runs N independent replicas (the single-grid
+step has no natural shard: every step couples whole rows and columns through
+the tridiagonal solves), one per GPU, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic values moved per cell by one launch of each kernel (see the
+# kernel notes): the stencil predictor of an AB3 step with the AM4 carries
+# reads w, P, Q, bed corners and 12 carries and writes w, U*, V* and 15
+# carries; the corrector stencil reads w, P, Q, corners, 3 bases and writes
+# w, U*, V*; a line solve reads its right side and depth and writes P or Q.
+VALUES = {"stencil_pred_k": 16 + 18, "stencil_pred_0": 10 + 9, "stencil_corr": 7 + 3, "lines": 3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="beach2048", choices=["beach2048", "beach8192", "beach512"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1611_05984_gb300 import scenarios as sc
+    if name == "beach2048":
+        return sc.beach(nx=2048, ny=2048)
+    if name == "beach8192":
+        return sc.beach_directional(nx=8192, ny=8192)
+    return sc.beach(nx=512, ny=512, sponge=20)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _oracle_for(s):
+    import oracle
+    o = oracle.Oracle(s.z, s.dx, s.dy, s.dt, model=s.model, g=s.g, Bd=s.Bd, theta=s.theta, eps=s.eps,
+                      K=s.K, ws=s.ws, friction=s.friction, fcoef=s.fcoef)
+    for side, sd in s.sides.items():
+        o.set_boundary(side, sd.type, sd.width, sd.comps)
+    o.set_state(*s.initial_state())
+    return o
+
+
+def _row_crop(s, rows):
+    """The first `rows` rows of the same bed and boundaries: the cross-shore
+    profile (sine maker, shoals, beach, wall) is kept, the alongshore extent cut."""
+    import copy
+    if rows >= s.ny:
+        return s
+    c = copy.copy(s)
+    c.z = s.z[:rows].copy()
+    c.ny = rows
+    c.sides = dict(s.sides)
+    c.name = f"{s.name}[rows 0:{rows}]"
+    return c
+
+
+def _sample_rows(s, seconds_per_step):
+    """Rows of a crop whose oracle step takes about seconds_per_step."""
+    import time as _t
+    probe = _row_crop(s, min(s.ny, 64))
+    o = _oracle_for(probe)
+    o.step(3)
+    t0 = _t.perf_counter()
+    o.step(2)
+    per_row = (_t.perf_counter() - t0) / 2 / probe.ny
+    return max(16, min(s.ny, int(seconds_per_step / max(per_row, 1e-9))))
+
+
+def cpu_baseline(s, seconds):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded sample of
+    the same workload (a row crop if a full step is too slow), timed after the
+    two Euler start-up steps, about `seconds` of CPU work."""
+    import oracle
+    rows = _sample_rows(s, seconds / 4)
+    c = _row_crop(s, rows)
+    o = _oracle_for(c)
+    o.step(2)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 50:
+            break
+    return {"value": c.cells * n / el, "unit": "cell-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{c.name}, FP64, {n} AB3+AM4 steps after the 2 Euler start-up steps, {el:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on this host (rank 0 only), each step one
+    oracle step on a row crop of the workload sized to keep the run to about
+    two minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    s = workload(args.workload)
+    rows = _sample_rows(s, 120.0 / (args.steps + args.warmup + 2))
+    c = _row_crop(s, rows)
+    o = _oracle_for(c)
+    o.step(2 + args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = c.cells * args.steps / el
+    line = {"impl": "reference", "metric": "cell-updates/s", "value": v, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": s.name, "nx": s.nx, "ny": s.ny, "cells": s.cells,
+                       "corrector_iters": s.K, "dt": s.dt, "sample_rows": rows},
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{c.name}, FP64, {args.steps} timed steps after "
+                                       f"{args.warmup + 2} untimed"},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1611_05984_gb300 import celeris
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    dtype = torch.float32 if args.precision == "f32" else torch.float64
+    es = 4 if args.precision == "f32" else 8
+    s = workload(args.workload)
+    sol = celeris.from_scenario(s, dtype=dtype)
+    stream = sol.stream
+    sol.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, inputs resident in HBM
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.4)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sol.profile_enable(4 * (s.K + 1) * args.steps + 16)
+    e0.record(stream)
+    sol.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = sol.last_launch_count()
+    prof = sol.profile_read()
+    sol.profile_disable()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * s.cells * args.steps / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (bytes per launch / event time)
+    peak, peak_src = peaks()
+    st_ms, st_n = prof["stencil"]
+    nstages_corr = s.K * args.steps
+    nstages_pred = args.steps
+    pred_vals = VALUES["stencil_pred_k"] if s.K > 0 else VALUES["stencil_pred_0"]
+    st_bytes = s.cells * es * (nstages_pred * pred_vals + nstages_corr * VALUES["stencil_corr"])
+    kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()}
+    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    line_bytes = s.cells * es * VALUES["lines"] * (nstages_pred + nstages_corr)
+    bytes_of = {"stencil": st_bytes, "xlines": line_bytes, "ylines": line_bytes}
+    dk = kernels[dominant]
+    achieved = bytes_of[dominant] / (dk["ms_total"] / 1e3) / 1e9 if dk["ms_total"] > 0 else 0.0
+    for k in kernels:
+        kk = kernels[k]
+        kk["gbs_algorithmic"] = bytes_of[k] / (kk["ms_total"] / 1e3) / 1e9 if kk["ms_total"] > 0 else None
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tj = json.load(f)
+        ent = tj.get(f"{dominant}:{args.workload}:{args.precision}")
+        if ent and ent.get("source_hash") == celeris_source_hash():
+            traffic = ent["bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "per_kernel": kernels,
+                "step_bytes_algorithmic": (st_bytes + 2 * line_bytes) / args.steps,
+                "step_gbs_algorithmic": (st_bytes + 2 * line_bytes) / (ms / 1e3) / 1e9 / world}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(s, dtype, es, args.steps, celeris, torch, world, barrier)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": s.name, "nx": s.nx, "ny": s.ny, "cells": s.cells,
+                           "corrector_iters": s.K, "dt": s.dt, "courant": 0.1,
+                           "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (workspace %.0f MB > 129 MB)"
+                                 % (sol.workspace.numel() / 1e6)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def celeris_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("celeris_kernels.cu", "celeris_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1611_05984_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def end_to_end(s, dtype, es, steps, celeris, torch, world, barrier):
+    """Same metric through the public calls a user makes, with host buffers:
+    bed and initial state copied from pinned host memory, the solver created,
+    then every step followed by a synchronising read of the gauge record
+    (16 gauges, device -> host); the final free surface is copied back."""
+    import numpy as np
+    npdt = np.float32 if es == 4 else np.float64
+    z_h = torch.from_numpy(s.z.astype(npdt)).pin_memory()
+    w0, P0, Q0 = (torch.from_numpy(a.astype(npdt)).pin_memory() for a in s.initial_state())
+    eta_h = torch.empty((s.ny, s.nx), dtype=dtype).pin_memory()
+    rng = np.random.default_rng(17)
+    gij = np.stack([rng.integers(0, s.nx // 2, 16), rng.integers(0, s.ny, 16)], 1)
+    stream = torch.cuda.current_stream()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    z_d = z_h.to("cuda", non_blocking=True)
+    sol = celeris.Solver(z_d, s.dx, s.dy, s.dt, dtype=dtype, model=s.model, g=s.g, Bd=s.Bd, theta=s.theta,
+                         eps=s.eps, K=s.K, ws=s.ws, friction=s.friction, fcoef=s.fcoef)
+    for side, sd in s.sides.items():
+        sol.set_boundary(side, sd.type, sd.width, sd.comps)
+    sol.set_state(w0.to("cuda", non_blocking=True), P0.to("cuda", non_blocking=True),
+                  Q0.to("cuda", non_blocking=True))
+    sol.set_gauges(gij, 1, 4)
+    got = 0
+    for _ in range(steps):
+        sol.step(1)
+        got += len(sol.read_gauges(4))
+    w, _, _ = sol.state()
+    eta_h.copy_(w, non_blocking=True)
+    stream.synchronize()
+    el = time.perf_counter() - t0
+    barrier()
+    assert got == steps
+    h2d = 4 * s.cells * es
+    d2h = steps * 16 * es + s.cells * es
+    return {"value": world * s.cells * steps / el, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "what": "bed + state H2D, create, per-step gauge read (sync), final eta D2H"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * celeris_gb.h -- C ABI of the GB300 time-step library for the extended
+ * Boussinesq equations of Madsen & Sorensen in the conservative form used by
+ * Celeris (Tavakkol & Lynett, arXiv 1611.05984).
+ *
+ * One step advances U = [h, P, Q] (unknowns [w, P, Q], w = h + z) by:
+ *   KP07 generalized-minmod reconstruction, positivity fix and desingularised
+ *   velocities (Sec. 2.2, Eq. 14); central-upwind fluxes; bed-slope, friction
+ *   (Sec. 2.6, Eq. 31-32) and dispersive terms (Eq. 10-13); the AB3 predictor
+ *   (Eq. 15-17) with K iterations of the AM4 corrector (Eq. 18-20), Euler for
+ *   the first two steps; the tridiagonal solves of Eq. 21-23 per x-row and
+ *   per y-column; boundaries (Sec. 2.4, Eq. 24-30).
+ *
+ * Conventions (every call):
+ *   - SI units.  Cell (i,j) has its centre at ((i+1/2) dx, (j+1/2) dy).
+ *   - Field arrays passed in or out are interior only, dense, row-major
+ *     [ny][nx], of the grid's real type (real_bytes = 4: float, 8: double),
+ *     in DEVICE memory unless a parameter says "host".
+ *   - Memory ownership: the caller owns all device memory (workspace, arrays,
+ *     checkpoints, gauge buffers).  The library never allocates device memory;
+ *     the handle holds host metadata and pointers into caller memory only.
+ *   - Streams: calls are asynchronous on the handle's stream unless marked
+ *     "synchronises".  A handle must not be used from two threads at once.
+ *   - Errors: every call returns a cel_status; nothing throws across the ABI.
+ *     NULL pointers and bad sizes give CEL_ERR_INVALID_ARG; a CUDA error gives
+ *     CEL_ERR_CUDA and its text is kept for cel_last_error().
+ */
+#ifndef CELERIS_GB_H
+#define CELERIS_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cel_solver cel_solver; /* opaque, owned by the library (host) */
+
+typedef enum {
+    CEL_OK = 0,
+    CEL_ERR_INVALID_ARG = 1,
+    CEL_ERR_WORKSPACE_TOO_SMALL = 2,
+    CEL_ERR_CUDA = 3,
+    CEL_ERR_NONFINITE = 4,
+    CEL_ERR_TIMEOUT = 5,
+    CEL_ERR_NOT_IMPLEMENTED = 6
+} cel_status;
+
+enum { CEL_BSNQ = 0, CEL_NLSW = 1 };                 /* model, Sec. 3.2       */
+enum { CEL_FRIC_NONE = 0, CEL_FRIC_QUADRATIC = 1, CEL_FRIC_MANNING = 2 }; /* Sec. 2.6 */
+enum { CEL_SOLID = 0, CEL_SPONGE = 1, CEL_SINE = 2 }; /* boundary, Sec. 2.4    */
+enum { CEL_WEST = 0, CEL_EAST = 1, CEL_SOUTH = 2, CEL_NORTH = 3 };
+enum { CEL_FIELD_BBAR = 0, CEL_FIELD_D = 1, CEL_FIELD_USTAR = 2, CEL_FIELD_VSTAR = 3 };
+
+/* Maximum line lengths of the tridiagonal solves (one thread block per line). */
+#define CEL_MAX_LINE_F32 16384
+#define CEL_MAX_LINE_F64 8192
+
+typedef struct {
+    int32_t nx, ny;       /* interior cells, 2 <= n <= CEL_MAX_LINE_*          */
+    double dx, dy;        /* cell sizes [m]                                    */
+    int32_t real_bytes;   /* 4 (FP32) or 8 (FP64): type of state and arithmetic */
+} cel_grid;
+
+typedef struct {
+    int32_t model;        /* CEL_BSNQ or CEL_NLSW (Sec. 3.2)                   */
+    double g;             /* gravity, 9.81                                     */
+    double Bdisp;         /* dispersion calibration B of Eq. 2, 1/15           */
+    double theta;         /* generalized-minmod parameter of KP07, in [1, 2]   */
+    double eps;           /* desingularisation tolerance of Eq. 14 (5e-12)     */
+    double dt;            /* fixed time step [s]                               */
+    int32_t corrector_iters; /* K >= 0 AM4 iterations per step (Sec. 2.3)      */
+    double still_water;   /* w_s                                               */
+    int32_t friction;     /* CEL_FRIC_*                                        */
+    double fric_coef;     /* f (quadratic, Eq. 31) or Manning n (Eq. 32)       */
+} cel_params;
+
+typedef struct {
+    int32_t type;         /* CEL_SOLID | CEL_SPONGE | CEL_SINE (Sec. 2.4)       */
+    int32_t width_cells;  /* sponge width L_s in cells (Eq. 30)                */
+    int32_t ncomp;        /* sine components summed, 0..8 (Eq. 25-28)          */
+    double amp[8];        /* a [m]                                             */
+    double period[8];     /* T [s]                                             */
+    double theta[8];      /* direction [rad] from +x                           */
+    double phase[8];      /* phase added inside the sine [rad]                 */
+} cel_bc;
+
+/* Bytes of device workspace a solver of this grid/params needs.  Host only;
+ * INVALID_ARG on bad sizes (n < 2, n above the line limit, real_bytes). */
+cel_status cel_workspace_bytes(const cel_grid *grid, const cel_params *params,
+                               size_t *bytes);
+
+/* Create a solver.  z_dev: bed elevation at cell centres (Sec. 3.2 "bathymetry
+ * file"), [ny][nx] real, device, read during the call only.  workspace_dev:
+ * caller-owned device memory of at least cel_workspace_bytes, 256-byte
+ * aligned, kept until cel_destroy.  cuda_stream: a cudaStream_t (NULL = the
+ * legacy default stream).  The state starts at rest: w = max(w_s, Bbar),
+ * P = Q = 0, all sides CEL_SOLID, t = 0.  Asynchronous on the stream. */
+cel_status cel_create(const cel_grid *grid, const cel_params *params,
+                      const void *z_dev, void *workspace_dev, size_t ws_bytes,
+                      void *cuda_stream, cel_solver **out);
+
+/* Boundary of one side (CEL_WEST..CEL_NORTH), Sec. 2.4: solid wall (Eq. 24),
+ * sponge layer (Eq. 30; the ghosts behind it are solid) or sine-wave maker
+ * (Eq. 25-29, components summed).  Host only; takes effect at the next step. */
+cel_status cel_set_boundary(cel_solver *s, int32_t side, const cel_bc *bc);
+
+/* Hot start (Sec. 3.2): copy w, P, Q ([ny][nx] real, device).  w is raised to
+ * the cell bed where below it and P = Q = 0 where the depth is zero.  Restarts
+ * the AB3 history (the next two steps are Euler, Sec. 2.3).  Asynchronous. */
+cel_status cel_set_state(cel_solver *s, const void *w, const void *P,
+                         const void *Q);
+
+/* Superpose a solitary wave (Sec. 2.7, Eq. 33-36) of height H [m] (negative:
+ * depression), direction theta [rad], crest at (x0, y0) [m], where the still
+ * water depth d > 0.  d in Eq. 35-36 is that of the cell holding the crest;
+ * INVALID_ARG if it is dry or H + d <= 0.  Restarts the AB3 history.
+ * Synchronises (reads the crest depth). */
+cel_status cel_add_solitary(cel_solver *s, double H, double theta, double x0,
+                            double y0);
+
+/* Replace the bed (runtime terrain edit, Sec. 1) and re-derive the static
+ * fields; w is raised to the new bed; restarts the AB3 history.  Async. */
+cel_status cel_set_bathymetry(cel_solver *s, const void *z_dev);
+
+/* Advance nsteps >= 0 time steps.  Asynchronous on the handle's stream. */
+cel_status cel_step(cel_solver *s, int32_t nsteps);
+
+/* Copy the current w, P, Q into [ny][nx] device arrays (any may be NULL).
+ * Asynchronous. */
+cel_status cel_get_state(cel_solver *s, void *w, void *P, void *Q);
+
+/* Diagnostic fields into a [ny][nx] device array: CEL_FIELD_BBAR (cell bed),
+ * CEL_FIELD_D (still-water depth), CEL_FIELD_USTAR / _VSTAR (the increments
+ * of U*, V* of Eq. 7-8 over the last stage, the right sides of the last line
+ * solves, which are solved for P^{n+1} - P^n).  Asynchronous. */
+cel_status cel_get_field(cel_solver *s, int32_t which, void *dst);
+
+/* Gauges (Sec. 3.2 "logData"): record eta = w - w_s at n cells (ij_host =
+ * [i0,j0,i1,j1,...], host) every log_every steps into a ring of `capacity`
+ * records kept in gauge_buf_dev (caller device memory of cel_gauge_bytes).
+ * When full, the oldest record is overwritten.  Host + one async copy. */
+cel_status cel_gauge_bytes(int32_t n, int32_t capacity, int32_t real_bytes,
+                           size_t *bytes);
+cel_status cel_set_gauges(cel_solver *s, const int32_t *ij_host, int32_t n,
+                          int32_t log_every, int32_t capacity,
+                          void *gauge_buf_dev, size_t buf_bytes);
+/* Move up to max_rec oldest records into eta_host ([rec][n] real, host) and
+ * drop them from the ring; *n_rec = records written.  Synchronises. */
+cel_status cel_read_gauges(cel_solver *s, void *eta_host, int32_t max_rec,
+                           int32_t *n_rec);
+
+/* Simulated time t = step * dt and the step count since create.  Host only. */
+cel_status cel_get_time(cel_solver *s, double *t, int64_t *step);
+
+/* Device reduction over w, P, Q: CEL_ERR_NONFINITE if any value is NaN/Inf
+ * (the first offending cell index goes into cel_last_error).  Synchronises. */
+cel_status cel_check_finite(cel_solver *s);
+
+/* Checkpoint: state, AB3/AM4 history, step count and time, enough for a
+ * bit-exact resume.  Device buffer of cel_checkpoint_bytes.  Asynchronous
+ * (save) / synchronises (load reads the header). */
+cel_status cel_checkpoint_bytes(const cel_solver *s, size_t *bytes);
+cel_status cel_save_checkpoint(cel_solver *s, void *dst_dev, size_t bytes);
+cel_status cel_load_checkpoint(cel_solver *s, const void *src_dev, size_t bytes);
+
+/* Kernel launches issued by the most recent cel_step call. */
+cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+ * each launch of the three step kernels (0: stencil + update, 1: x-line
+ * solves, 2: y-line solves).  cel_profile_enable creates `capacity` event
+ * pairs (host-side CUDA resources; no device memory) and starts recording;
+ * launches beyond capacity are not timed.  cel_profile_read synchronises and
+ * returns the summed milliseconds and launch counts per kernel, then resets
+ * the counters.  cel_profile_disable destroys the events. */
+cel_status cel_profile_enable(cel_solver *s, int32_t capacity);
+cel_status cel_profile_read(cel_solver *s, double ms[3], int64_t count[3]);
+cel_status cel_profile_disable(cel_solver *s);
+
+const char *cel_status_string(cel_status st);
+const char *cel_last_error(const cel_solver *s);  /* "" if none; never NULL */
+/* Release the handle (not the caller's memory).  Does not synchronise. */
+void cel_destroy(cel_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

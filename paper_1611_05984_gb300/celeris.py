@@ -1,0 +1,301 @@
+"""Python binding of the Celeris GB300 step library (ctypes over the C ABI).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``libceleris_gb.so``.  PyTorch supplies the device memory (the workspace,
+gauge ring and checkpoint buffers are torch tensors the binding keeps alive)
+and the CUDA stream (``torch.cuda.current_stream()`` by default).  There is no
+CPU fallback: constructing a Solver without a CUDA device or without the
+compiled library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+CEL_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA error",
+          4: "non-finite value", 5: "timeout", 6: "not implemented"}
+BSNQ, NLSW = 0, 1
+FRIC_NONE, FRIC_QUADRATIC, FRIC_MANNING = 0, 1, 2
+SOLID, SPONGE, SINE = 0, 1, 2
+WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
+FIELDS = {"Bbar": 0, "d": 1, "U": 2, "V": 3}
+
+EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_state",
+           "cel_add_solitary", "cel_set_bathymetry", "cel_step", "cel_get_state", "cel_get_field",
+           "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
+           "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
+           "cel_load_checkpoint", "cel_last_launch_count", "cel_profile_enable",
+           "cel_profile_read", "cel_profile_disable", "cel_status_string",
+           "cel_last_error", "cel_destroy"]
+
+
+class CelGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("real_bytes", ctypes.c_int32)]
+
+
+class CelParams(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("g", ctypes.c_double), ("Bdisp", ctypes.c_double),
+                ("theta", ctypes.c_double), ("eps", ctypes.c_double), ("dt", ctypes.c_double),
+                ("corrector_iters", ctypes.c_int32), ("still_water", ctypes.c_double),
+                ("friction", ctypes.c_int32), ("fric_coef", ctypes.c_double)]
+
+
+class CelBC(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("width_cells", ctypes.c_int32),
+                ("ncomp", ctypes.c_int32), ("amp", ctypes.c_double * 8),
+                ("period", ctypes.c_double * 8), ("theta", ctypes.c_double * 8),
+                ("phase", ctypes.c_double * 8)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libceleris_gb.so (building it with nvcc when absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path}")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        d = ctypes.c_double
+        L.cel_workspace_bytes.argtypes = [ctypes.POINTER(CelGrid), ctypes.POINTER(CelParams), ctypes.POINTER(sz)]
+        L.cel_create.argtypes = [ctypes.POINTER(CelGrid), ctypes.POINTER(CelParams), vp, vp, sz, vp,
+                                 ctypes.POINTER(vp)]
+        L.cel_set_boundary.argtypes = [vp, i32, ctypes.POINTER(CelBC)]
+        L.cel_set_state.argtypes = [vp, vp, vp, vp]
+        L.cel_add_solitary.argtypes = [vp, d, d, d, d]
+        L.cel_set_bathymetry.argtypes = [vp, vp]
+        L.cel_step.argtypes = [vp, i32]
+        L.cel_get_state.argtypes = [vp, vp, vp, vp]
+        L.cel_get_field.argtypes = [vp, i32, vp]
+        L.cel_gauge_bytes.argtypes = [i32, i32, i32, ctypes.POINTER(sz)]
+        L.cel_set_gauges.argtypes = [vp, ctypes.POINTER(i32), i32, i32, i32, vp, sz]
+        L.cel_read_gauges.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+        L.cel_get_time.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
+        L.cel_check_finite.argtypes = [vp]
+        L.cel_checkpoint_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+        L.cel_save_checkpoint.argtypes = [vp, vp, sz]
+        L.cel_load_checkpoint.argtypes = [vp, vp, sz]
+        L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+        L.cel_profile_enable.argtypes = [vp, i32]
+        L.cel_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
+        L.cel_profile_disable.argtypes = [vp]
+        L.cel_status_string.restype = ctypes.c_char_p
+        L.cel_status_string.argtypes = [ctypes.c_int]
+        L.cel_last_error.restype = ctypes.c_char_p
+        L.cel_last_error.argtypes = [vp]
+        L.cel_destroy.argtypes = [vp]
+        L.cel_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("cel_status_string", "cel_last_error", "cel_destroy"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+class CelerisError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def make_bc(type: int = SOLID, width: int = 0, comps: Sequence = ()) -> CelBC:
+    """comps: (amp [m], period [s], direction [rad], phase [rad]) per component."""
+    bc = CelBC()
+    bc.type, bc.width_cells, bc.ncomp = int(type), int(width), len(comps)
+    for m, (a, T, th, ph) in enumerate(comps):
+        bc.amp[m], bc.period[m], bc.theta[m], bc.phase[m] = a, T, th, ph
+    return bc
+
+
+class Solver:
+    """One simulation on one GPU.  Arrays in and out are torch tensors (ny, nx)."""
+
+    def __init__(self, z, dx: float, dy: float, dt: float, *, dtype=None, model: int = BSNQ,
+                 g: float = 9.81, Bd: float = 1.0 / 15.0, theta: float = 1.3, eps: float = 5e-12,
+                 K: int = 0, ws: float = 0.0, friction: int = FRIC_NONE, fcoef: float = 0.0,
+                 device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the Celeris GB300 solver needs a CUDA device")
+        self.torch = torch
+        self.dtype = dtype or torch.float32
+        if self.dtype not in (torch.float32, torch.float64):
+            raise ValueError("dtype must be float32 or float64")
+        self.device = torch.device(device or "cuda")
+        self.L = load()
+        zt = torch.as_tensor(z).to(device=self.device, dtype=self.dtype).contiguous()
+        self.ny, self.nx = zt.shape
+        self.es = 4 if self.dtype == torch.float32 else 8
+        self.grid = CelGrid(self.nx, self.ny, dx, dy, self.es)
+        self.params = CelParams(model, g, Bd, theta, eps, dt, K, ws, friction, fcoef)
+        nb = ctypes.c_size_t()
+        self._check(self.L.cel_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.params),
+                                               ctypes.byref(nb)), "workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        self._h = None
+        st = self.L.cel_create(ctypes.byref(self.grid), ctypes.byref(self.params), zt.data_ptr(),
+                               self._ws_ptr, nb.value, self.stream.cuda_stream, ctypes.byref(h))
+        if st != CEL_OK:
+            raise CelerisError(st, "cel_create failed")
+        self._h = h
+        self._z = zt
+        self._gauge_buf = None
+        self.ng = 0
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, st: int, what: str):
+        if st != CEL_OK:
+            msg = ""
+            if getattr(self, "_h", None):
+                msg = self.L.cel_last_error(self._h).decode()
+            raise CelerisError(st, f"{what}: {msg}")
+
+    def _arr(self, a):
+        t = self.torch.as_tensor(a).to(device=self.device, dtype=self.dtype).contiguous()
+        if t.shape != (self.ny, self.nx):
+            raise ValueError(f"expected shape {(self.ny, self.nx)}, got {tuple(t.shape)}")
+        return t
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self.L.cel_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- calls
+    def set_boundary(self, side: int, type: int = SOLID, width: int = 0, comps: Sequence = ()):
+        bc = make_bc(type, width, comps)
+        self._check(self.L.cel_set_boundary(self._h, side, ctypes.byref(bc)), "set_boundary")
+
+    def set_state(self, w, P, Q):
+        w, P, Q = self._arr(w), self._arr(P), self._arr(Q)
+        self._check(self.L.cel_set_state(self._h, w.data_ptr(), P.data_ptr(), Q.data_ptr()), "set_state")
+        self.stream.synchronize()
+
+    def add_solitary(self, H: float, theta: float, x0: float, y0: float):
+        self._check(self.L.cel_add_solitary(self._h, H, theta, x0, y0), "add_solitary")
+
+    def set_bathymetry(self, z):
+        zt = self._arr(z)
+        self._check(self.L.cel_set_bathymetry(self._h, zt.data_ptr()), "set_bathymetry")
+        self.stream.synchronize()
+
+    def step(self, n: int = 1):
+        self._check(self.L.cel_step(self._h, int(n)), "step")
+
+    def state(self) -> Tuple:
+        t = self.torch
+        w = t.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
+        P, Q = t.empty_like(w), t.empty_like(w)
+        self._check(self.L.cel_get_state(self._h, w.data_ptr(), P.data_ptr(), Q.data_ptr()), "get_state")
+        self.stream.synchronize()
+        return w, P, Q
+
+    def field(self, name: str):
+        out = self.torch.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
+        self._check(self.L.cel_get_field(self._h, FIELDS[name], out.data_ptr()), "get_field")
+        self.stream.synchronize()
+        return out
+
+    def set_gauges(self, ij, log_every: int, capacity: int):
+        ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int32).reshape(-1, 2))
+        nb = ctypes.c_size_t()
+        self._check(self.L.cel_gauge_bytes(len(ij), capacity, self.es, ctypes.byref(nb)), "gauge_bytes")
+        buf = self.torch.empty(nb.value + 256, dtype=self.torch.uint8, device=self.device)
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        self._check(self.L.cel_set_gauges(self._h, ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          len(ij), log_every, capacity, ptr, nb.value), "set_gauges")
+        self.stream.synchronize()
+        self._gauge_buf = buf
+        self.ng = len(ij)
+
+    def read_gauges(self, max_rec: int) -> np.ndarray:
+        out = np.zeros((max_rec, self.ng), dtype=np.float32 if self.es == 4 else np.float64)
+        n = ctypes.c_int32()
+        self._check(self.L.cel_read_gauges(self._h, out.ctypes.data, max_rec, ctypes.byref(n)), "read_gauges")
+        return out[: n.value]
+
+    def time(self):
+        t, s = ctypes.c_double(), ctypes.c_int64()
+        self._check(self.L.cel_get_time(self._h, ctypes.byref(t), ctypes.byref(s)), "get_time")
+        return t.value, s.value
+
+    def check_finite(self) -> bool:
+        st = self.L.cel_check_finite(self._h)
+        if st == 4:
+            return False
+        self._check(st, "check_finite")
+        return True
+
+    def checkpoint(self):
+        nb = ctypes.c_size_t()
+        self._check(self.L.cel_checkpoint_bytes(self._h, ctypes.byref(nb)), "checkpoint_bytes")
+        buf = self.torch.empty(nb.value, dtype=self.torch.uint8, device=self.device)
+        self._check(self.L.cel_save_checkpoint(self._h, buf.data_ptr(), nb.value), "save_checkpoint")
+        self.stream.synchronize()
+        return buf
+
+    def restore(self, buf):
+        self._check(self.L.cel_load_checkpoint(self._h, buf.data_ptr(), buf.numel()), "load_checkpoint")
+        self.stream.synchronize()
+
+    def profile_enable(self, capacity: int):
+        self._check(self.L.cel_profile_enable(self._h, int(capacity)), "profile_enable")
+
+    def profile_read(self):
+        """{kernel: (total ms, launches)} since enable or the last read."""
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int64 * 3)()
+        self._check(self.L.cel_profile_read(self._h, ms, cnt), "profile_read")
+        return {name: (ms[k], cnt[k]) for k, name in enumerate(("stencil", "xlines", "ylines"))}
+
+    def profile_disable(self):
+        self._check(self.L.cel_profile_disable(self._h), "profile_disable")
+
+    def last_launch_count(self) -> int:
+        n = ctypes.c_int64()
+        self._check(self.L.cel_last_launch_count(self._h, ctypes.byref(n)), "last_launch_count")
+        return n.value
+
+
+def from_scenario(s, dtype=None, K: Optional[int] = None, **kw) -> Solver:
+    """A Solver set up with a scenario's bed, boundaries, state and solitons."""
+    sol = Solver(s.z, s.dx, s.dy, s.dt, dtype=dtype, model=s.model, g=s.g, Bd=s.Bd, theta=s.theta,
+                 eps=s.eps, K=s.K if K is None else K, ws=s.ws, friction=s.friction, fcoef=s.fcoef, **kw)
+    for side, sd in s.sides.items():
+        sol.set_boundary(side, sd.type, sd.width, sd.comps)
+    sol.set_state(*s.initial_state())
+    for (H, th, x0, y0) in s.solitons:
+        sol.add_solitary(H, th, x0, y0)
+    return sol

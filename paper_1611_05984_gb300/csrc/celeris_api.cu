@@ -1,0 +1,753 @@
+// C ABI of the Celeris step library (declared in include/celeris_gb.h).
+//
+// The handle keeps host metadata and pointers into the caller's workspace;
+// the library never allocates device memory.  Every call returns a status and
+// records the text of the last error in the handle.
+#include "celeris_gb.h"
+#include "celeris_internal.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+using namespace cel;
+
+namespace {
+
+constexpr double kPiD = 3.14159265358979323846;
+constexpr uint64_t kCkptMagic = 0x43454c4b50543031ull;   // "CELKPT01"
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
+
+struct Layout {
+    size_t w[2], P[2], U, dr, a[3], b[3][2], Y[3], q[3], e[3];
+    size_t Qc[2], Vc, dc, Bc, mr, mc, flag;
+    size_t total;
+    size_t row_bytes, col_bytes;
+};
+
+Geo make_geo(const cel_grid &g)
+{
+    Geo G;
+    G.nx = g.nx;
+    G.ny = g.ny;
+    G.px = round_up_i(g.nx, 32);
+    G.py = round_up_i(g.ny, 32);
+    G.pc = round_up_i(g.nx + 3, 32);
+    G.nwx = (g.nx + 31) / 32;
+    G.nwy = (g.ny + 31) / 32;
+    G.dx = g.dx;
+    G.dy = g.dy;
+    return G;
+}
+
+Layout make_layout(const Geo &G, int es, int K)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    size_t cur = 0;
+    auto take = [&](size_t b) {
+        size_t o = cur;
+        cur += align256(b);
+        return o;
+    };
+    L.row_bytes = (size_t)G.ny * G.px * es;
+    L.col_bytes = (size_t)G.nx * G.py * es;
+    L.w[0] = take(L.row_bytes);
+    L.w[1] = take(L.row_bytes);
+    L.P[0] = take(L.row_bytes);
+    L.P[1] = take(L.row_bytes);
+    L.U = take(L.row_bytes);
+    L.dr = take(L.row_bytes);
+    for (int v = 0; v < 3; v++) {
+        L.a[v] = take(L.row_bytes);
+        L.b[v][0] = take(L.row_bytes);
+        L.b[v][1] = take(L.row_bytes);
+    }
+    if (K > 0)
+        for (int v = 0; v < 3; v++) {
+            L.Y[v] = take(L.row_bytes);
+            L.q[v] = take(L.row_bytes);
+            L.e[v] = take(L.row_bytes);
+        }
+    L.Qc[0] = take(L.col_bytes);
+    L.Qc[1] = take(L.col_bytes);
+    L.Vc = take(L.col_bytes);
+    L.dc = take(L.col_bytes);
+    L.Bc = take((size_t)(G.ny + 3) * G.pc * es);
+    L.mr = take((size_t)G.ny * G.nwx * 4);
+    L.mc = take((size_t)G.nx * G.nwy * 4);
+    L.flag = take(256);
+    L.total = cur;
+    return L;
+}
+
+bool grid_ok(const cel_grid *g)
+{
+    if (!g) return false;
+    if (g->real_bytes != 4 && g->real_bytes != 8) return false;
+    int mx = g->real_bytes == 4 ? CEL_MAX_LINE_F32 : CEL_MAX_LINE_F64;
+    if (g->nx < 2 || g->ny < 2 || g->nx > mx || g->ny > mx) return false;
+    if (!(g->dx > 0) || !(g->dy > 0) || !isfinite(g->dx) || !isfinite(g->dy)) return false;
+    return true;
+}
+
+bool params_ok(const cel_params *p)
+{
+    if (!p) return false;
+    if (p->model != CEL_BSNQ && p->model != CEL_NLSW) return false;
+    if (p->friction < CEL_FRIC_NONE || p->friction > CEL_FRIC_MANNING) return false;
+    if (!(p->g > 0) || !(p->dt > 0) || !(p->eps > 0) || !(p->Bdisp >= 0)) return false;
+    if (!(p->theta >= 0 && p->theta <= 2.0)) return false;
+    if (p->corrector_iters < 0 || p->corrector_iters > 64) return false;
+    if (!isfinite(p->still_water) || !(p->fric_coef >= 0)) return false;
+    return true;
+}
+
+}  // namespace
+
+struct cel_solver {
+    cel_grid grid;
+    cel_params params;
+    Geo geo;
+    Phys phy;
+    Bnd bnd;
+    Layout lay;
+    int es;
+    cudaStream_t stream;
+    unsigned char *ws;
+    int cur;      // w buffer of the state (w alternates per stage)
+    int pcur;     // P / Q buffer of the state (alternates per step)
+    int64_t step, nh;
+    int nseg_x, nseg_y;
+    // gauges
+    int32_t *gij;
+    unsigned char *gring;
+    int ng, log_every, cap, nrec, head;
+    int64_t launches;
+    std::string err;
+    // optional per-kernel event timing
+    cudaEvent_t *ev_beg, *ev_end;
+    int *ev_kind;
+    int ev_cap, ev_used;
+
+    template <typename T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+};
+
+namespace {
+
+cel_status fail(cel_solver *s, cel_status st, const std::string &msg)
+{
+    if (s) s->err = msg;
+    return st;
+}
+
+cel_status cuda_fail(cel_solver *s, cudaError_t e, const char *where)
+{
+    return fail(s, CEL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CEL_CUDA(s, expr, where)                       \
+    do {                                               \
+        cudaError_t e_ = (expr);                       \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, where); \
+    } while (0)
+
+int prof_begin(cel_solver *s, int kind)
+{
+    if (!s->ev_cap || s->ev_used >= s->ev_cap) return -1;
+    int k = s->ev_used++;
+    s->ev_kind[k] = kind;
+    cudaEventRecord(s->ev_beg[k], s->stream);
+    return k;
+}
+
+void prof_end(cel_solver *s, int k)
+{
+    if (k >= 0) cudaEventRecord(s->ev_end[k], s->stream);
+}
+
+void prof_free(cel_solver *s)
+{
+    for (int k = 0; k < s->ev_cap; k++) {
+        cudaEventDestroy(s->ev_beg[k]);
+        cudaEventDestroy(s->ev_end[k]);
+    }
+    delete[] s->ev_beg;
+    delete[] s->ev_end;
+    delete[] s->ev_kind;
+    s->ev_beg = s->ev_end = nullptr;
+    s->ev_kind = nullptr;
+    s->ev_cap = s->ev_used = 0;
+}
+
+template <typename real>
+cel_status derive_static(cel_solver *s, const void *z)
+{
+    CEL_CUDA(s, launch_corners<real>(s->geo, (const real *)z, s->at<real>(s->lay.Bc), s->stream), "corners");
+    CEL_CUDA(s, launch_static_cells<real>(s->geo, s->phy, s->at<real>(s->lay.Bc), s->at<real>(s->lay.dr),
+                                          s->at<real>(s->lay.dc), s->stream), "static cells");
+    return CEL_OK;
+}
+
+template <typename real>
+cel_status set_state_t(cel_solver *s, const void *w, const void *P, const void *Q, int rest)
+{
+    s->cur = 0;
+    s->pcur = 0;
+    CEL_CUDA(s, launch_set_state<real>(s->geo, s->phy, s->at<real>(s->lay.Bc), (const real *)w,
+                                       (const real *)P, (const real *)Q, s->at<real>(s->lay.w[0]),
+                                       s->at<real>(s->lay.P[s->pcur]), s->at<real>(s->lay.Qc[s->pcur]), rest, s->stream),
+             "set_state");
+    s->nh = 0;
+    return CEL_OK;
+}
+
+template <typename real>
+cel_status step_t(cel_solver *s, int nsteps)
+{
+    const Layout &L = s->lay;
+    const int K = s->params.corrector_iters;
+    int64_t launches = 0;
+    for (int it = 0; it < nsteps; it++) {
+        const int kind0 = s->nh == 0 ? kEuler0 : (s->nh == 1 ? kEuler1 : kAB3);
+        const int Kn = s->nh >= 2 ? K : 0;
+        const double t0 = (double)s->step * s->params.dt, t1 = (double)(s->step + 1) * s->params.dt;
+        const int slot = (int)(s->nh & 1);
+        for (int stage = 0; stage <= Kn; stage++) {
+            StencilArgs<real> a;
+            a.geo = s->geo;
+            a.phy = s->phy;
+            a.bnd = s->bnd;
+            a.Bc = s->at<real>(L.Bc);
+            a.w_in = s->at<real>(L.w[(s->cur + stage) & 1]);
+            a.w_out = s->at<real>(L.w[(s->cur + stage + 1) & 1]);
+            a.P_in = s->at<real>(L.P[stage == 0 ? s->pcur : 1 - s->pcur]);
+            a.Qc_in = s->at<real>(L.Qc[stage == 0 ? s->pcur : 1 - s->pcur]);
+            a.U_out = s->at<real>(L.U);
+            a.Vc_out = s->at<real>(L.Vc);
+            for (int v = 0; v < 3; v++) {
+                a.a[v] = s->at<real>(L.a[v]);
+                a.b[v] = s->at<real>(L.b[v][slot]);
+                a.Y[v] = K > 0 ? s->at<real>(L.Y[v]) : nullptr;
+                a.q[v] = K > 0 ? s->at<real>(L.q[v]) : nullptr;
+                a.e[v] = K > 0 ? s->at<real>(L.e[v]) : nullptr;
+            }
+            a.mask_r = s->at<uint32_t>(L.mr);
+            a.mask_c = s->at<uint32_t>(L.mc);
+            a.kind = stage == 0 ? kind0 : kAM4;
+            a.keepK = K > 0;
+            a.final_stage = stage == Kn;
+            a.t = stage == 0 ? t0 : t1;
+            int pe = prof_begin(s, 0);
+            CEL_CUDA(s, launch_stencil<real>(a, s->stream), "stencil");
+            prof_end(s, pe);
+            for (int dir = 0; dir < 2; dir++) {
+                LineArgs<real> l;
+                l.geo = s->geo;
+                l.phy = s->phy;
+                l.bnd = s->bnd;
+                l.rhs = s->at<real>(dir == 0 ? L.U : L.Vc);
+                l.d = s->at<real>(dir == 0 ? L.dr : L.dc);
+                l.mask = s->at<uint32_t>(dir == 0 ? L.mr : L.mc);
+                l.base = s->at<real>(dir == 0 ? L.P[s->pcur] : L.Qc[s->pcur]);
+                l.sol = s->at<real>(dir == 0 ? L.P[1 - s->pcur] : L.Qc[1 - s->pcur]);
+                l.dir = dir;
+                l.n = dir == 0 ? s->geo.nx : s->geo.ny;
+                l.nlines = dir == 0 ? s->geo.ny : s->geo.nx;
+                l.pitch = dir == 0 ? s->geo.px : s->geo.py;
+                l.nwords = dir == 0 ? s->geo.nwx : s->geo.nwy;
+                l.nseg = dir == 0 ? s->nseg_x : s->nseg_y;
+                l.final_stage = stage == Kn;
+                l.identity = s->params.model == CEL_NLSW;
+                l.t0 = t0;
+                l.t1 = t1;
+                int pl = prof_begin(s, 1 + dir);
+                CEL_CUDA(s, launch_lines<real>(l, s->stream), dir == 0 ? "x-lines" : "y-lines");
+                prof_end(s, pl);
+            }
+            launches += 3;
+        }
+        s->cur = (s->cur + Kn + 1) & 1;
+        s->pcur = 1 - s->pcur;
+        s->step++;
+        s->nh++;
+        if (s->ng > 0 && s->log_every > 0 && s->cap > 0 && s->step % s->log_every == 0) {
+            int slotg;
+            if (s->nrec < s->cap) {
+                slotg = (s->head + s->nrec) % s->cap;
+                s->nrec++;
+            } else {
+                slotg = s->head;
+                s->head = (s->head + 1) % s->cap;
+            }
+            real *dst = reinterpret_cast<real *>(s->gring) + (size_t)slotg * s->ng;
+            CEL_CUDA(s, launch_gauges<real>(s->geo, s->phy, s->at<real>(L.w[s->cur]), s->gij, s->ng, dst,
+                                            s->stream), "gauges");
+            launches += 1;
+        }
+    }
+    s->launches = launches;
+    return CEL_OK;
+}
+
+struct CkptHeader {
+    uint64_t magic;
+    int32_t nx, ny, es, K;
+    int64_t step, nh;
+    uint64_t bytes;
+    uint64_t pad[2];
+};
+
+struct CkptPart {
+    size_t off_ws, bytes;
+};
+
+int ckpt_parts(const cel_solver *s, CkptPart *parts)
+{
+    const Layout &L = s->lay;
+    int n = 0;
+    parts[n++] = {L.w[s->cur], L.row_bytes};
+    parts[n++] = {L.P[s->pcur], L.row_bytes};
+    parts[n++] = {L.Qc[s->pcur], L.col_bytes};
+    for (int v = 0; v < 3; v++) {
+        parts[n++] = {L.a[v], L.row_bytes};
+        parts[n++] = {L.b[v][0], L.row_bytes};
+        parts[n++] = {L.b[v][1], L.row_bytes};
+    }
+    if (s->params.corrector_iters > 0)
+        for (int v = 0; v < 3; v++) {
+            parts[n++] = {L.Y[v], L.row_bytes};
+            parts[n++] = {L.q[v], L.row_bytes};
+            parts[n++] = {L.e[v], L.row_bytes};
+        }
+    return n;
+}
+
+size_t ckpt_total(const cel_solver *s)
+{
+    CkptPart parts[32];
+    int n = ckpt_parts(s, parts);
+    size_t t = align256(sizeof(CkptHeader));
+    for (int k = 0; k < n; k++) t += align256(parts[k].bytes);
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cel_status_string(cel_status st)
+{
+    switch (st) {
+    case CEL_OK: return "ok";
+    case CEL_ERR_INVALID_ARG: return "invalid argument";
+    case CEL_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case CEL_ERR_CUDA: return "CUDA error";
+    case CEL_ERR_NONFINITE: return "non-finite value in the state";
+    case CEL_ERR_TIMEOUT: return "timeout";
+    case CEL_ERR_NOT_IMPLEMENTED: return "not implemented";
+    }
+    return "unknown status";
+}
+
+const char *cel_last_error(const cel_solver *s) { return s ? s->err.c_str() : ""; }
+
+cel_status cel_workspace_bytes(const cel_grid *grid, const cel_params *params, size_t *bytes)
+{
+    if (!grid_ok(grid) || !params_ok(params) || !bytes) return CEL_ERR_INVALID_ARG;
+    Geo G = make_geo(*grid);
+    *bytes = make_layout(G, grid->real_bytes, params->corrector_iters).total;
+    return CEL_OK;
+}
+
+cel_status cel_create(const cel_grid *grid, const cel_params *params, const void *z_dev,
+                      void *workspace_dev, size_t ws_bytes, void *cuda_stream, cel_solver **out)
+{
+    if (!out) return CEL_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid_ok(grid) || !params_ok(params) || !z_dev || !workspace_dev) return CEL_ERR_INVALID_ARG;
+    if (((uintptr_t)workspace_dev & 255) != 0) return CEL_ERR_INVALID_ARG;
+    Geo G = make_geo(*grid);
+    Layout L = make_layout(G, grid->real_bytes, params->corrector_iters);
+    if (ws_bytes < L.total) return CEL_ERR_WORKSPACE_TOO_SMALL;
+    cel_solver *s = new cel_solver();
+    s->grid = *grid;
+    s->params = *params;
+    s->geo = G;
+    s->lay = L;
+    s->es = grid->real_bytes;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->ws = (unsigned char *)workspace_dev;
+    s->phy.model = params->model;
+    s->phy.friction = params->friction;
+    s->phy.K = params->corrector_iters;
+    s->phy.g = params->g;
+    s->phy.Bd = params->Bdisp;
+    s->phy.theta = params->theta;
+    s->phy.eps = params->eps;
+    s->phy.dt = params->dt;
+    s->phy.ws = params->still_water;
+    s->phy.fcoef = params->fric_coef;
+    memset(&s->bnd, 0, sizeof(s->bnd));
+    for (int k = 0; k < 4; k++) s->bnd.s[k].type = kSolid;
+    s->nseg_x = line_segments(G.nx, s->es);
+    s->nseg_y = line_segments(G.ny, s->es);
+    s->gij = nullptr;
+    s->gring = nullptr;
+    s->ng = s->log_every = s->cap = s->nrec = s->head = 0;
+    s->launches = 0;
+    s->step = 0;
+    s->cur = s->pcur = 0;
+    s->ev_beg = s->ev_end = nullptr;
+    s->ev_kind = nullptr;
+    s->ev_cap = s->ev_used = 0;
+    cudaError_t e = cudaMemsetAsync(workspace_dev, 0, L.total, s->stream);
+    if (e != cudaSuccess) {
+        delete s;
+        return CEL_ERR_CUDA;
+    }
+    cel_status st = s->es == 4 ? derive_static<float>(s, z_dev) : derive_static<double>(s, z_dev);
+    if (st == CEL_OK)
+        st = s->es == 4 ? set_state_t<float>(s, nullptr, nullptr, nullptr, 1)
+                        : set_state_t<double>(s, nullptr, nullptr, nullptr, 1);
+    if (st != CEL_OK) {
+        delete s;
+        return st;
+    }
+    *out = s;
+    return CEL_OK;
+}
+
+void cel_destroy(cel_solver *s)
+{
+    if (!s) return;
+    prof_free(s);
+    delete s;
+}
+
+cel_status cel_set_boundary(cel_solver *s, int32_t side, const cel_bc *bc)
+{
+    if (!s || !bc || side < 0 || side > 3) return fail(s, CEL_ERR_INVALID_ARG, "bad side or NULL bc");
+    if (bc->type < CEL_SOLID || bc->type > CEL_SINE || bc->ncomp < 0 || bc->ncomp > 8 || bc->width_cells < 0)
+        return fail(s, CEL_ERR_INVALID_ARG, "bad boundary type, ncomp or width");
+    if (bc->type == CEL_SINE)
+        for (int m = 0; m < bc->ncomp; m++)
+            if (!(bc->period[m] > 0) || !isfinite(bc->amp[m]) || !isfinite(bc->theta[m]) ||
+                !isfinite(bc->phase[m]))
+                return fail(s, CEL_ERR_INVALID_ARG, "bad sine component");
+    Side &S = s->bnd.s[side];
+    memset(&S, 0, sizeof(S));
+    S.type = bc->type;
+    S.width = bc->width_cells;
+    S.L = bc->width_cells * (side < 2 ? s->grid.dx : s->grid.dy);
+    S.ncomp = bc->type == CEL_SINE ? bc->ncomp : 0;
+    for (int m = 0; m < S.ncomp; m++) {
+        S.amp[m] = bc->amp[m];
+        S.omega[m] = 2.0 * kPiD / bc->period[m];
+        S.cdir[m] = cos(bc->theta[m]);
+        S.sdir[m] = sin(bc->theta[m]);
+        S.phase[m] = bc->phase[m];
+    }
+    return CEL_OK;
+}
+
+cel_status cel_set_state(cel_solver *s, const void *w, const void *P, const void *Q)
+{
+    if (!s || !w || !P || !Q) return fail(s, CEL_ERR_INVALID_ARG, "NULL state array");
+    return s->es == 4 ? set_state_t<float>(s, w, P, Q, 0) : set_state_t<double>(s, w, P, Q, 0);
+}
+
+cel_status cel_add_solitary(cel_solver *s, double H, double theta, double x0, double y0)
+{
+    if (!s || !isfinite(H) || !isfinite(theta) || !isfinite(x0) || !isfinite(y0))
+        return fail(s, CEL_ERR_INVALID_ARG, "bad solitary-wave arguments");
+    int ic = (int)floor(x0 / s->grid.dx), jc = (int)floor(y0 / s->grid.dy);
+    ic = ic < 0 ? 0 : (ic > s->grid.nx - 1 ? s->grid.nx - 1 : ic);
+    jc = jc < 0 ? 0 : (jc > s->grid.ny - 1 ? s->grid.ny - 1 : jc);
+    double ds;
+    const size_t off = s->lay.dr + ((size_t)jc * s->geo.px + ic) * s->es;
+    if (s->es == 4) {
+        float v;
+        CEL_CUDA(s, cudaMemcpyAsync(&v, s->ws + off, 4, cudaMemcpyDeviceToHost, s->stream), "read depth");
+        CEL_CUDA(s, cudaStreamSynchronize(s->stream), "read depth");
+        ds = v;
+    } else {
+        CEL_CUDA(s, cudaMemcpyAsync(&ds, s->ws + off, 8, cudaMemcpyDeviceToHost, s->stream), "read depth");
+        CEL_CUDA(s, cudaStreamSynchronize(s->stream), "read depth");
+    }
+    if (!(ds > 0.0) || !(H + ds > 0.0)) return fail(s, CEL_ERR_INVALID_ARG, "dry crest or H + d <= 0");
+    double ks = sqrt(3.0 * fabs(H) / (4.0 * ds * ds * ds));
+    double cs = sqrt(s->params.g * (H + ds));
+    double ct = cos(theta), st = sin(theta);
+    cudaError_t e;
+    if (s->es == 4)
+        e = launch_add_solitary<float>(s->geo, s->phy, s->at<float>(s->lay.Bc), s->at<float>(s->lay.w[s->cur]),
+                                       s->at<float>(s->lay.P[s->pcur]), s->at<float>(s->lay.Qc[s->pcur]), H, ct, st, x0, y0, ks, cs,
+                                       s->stream);
+    else
+        e = launch_add_solitary<double>(s->geo, s->phy, s->at<double>(s->lay.Bc),
+                                        s->at<double>(s->lay.w[s->cur]), s->at<double>(s->lay.P[s->pcur]),
+                                        s->at<double>(s->lay.Qc[s->pcur]), H, ct, st, x0, y0, ks, cs, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "add_solitary");
+    s->nh = 0;
+    return CEL_OK;
+}
+
+cel_status cel_set_bathymetry(cel_solver *s, const void *z_dev)
+{
+    if (!s || !z_dev) return fail(s, CEL_ERR_INVALID_ARG, "NULL bathymetry");
+    cel_status st = s->es == 4 ? derive_static<float>(s, z_dev) : derive_static<double>(s, z_dev);
+    if (st != CEL_OK) return st;
+    // raise w to the new bed in place, zero the discharge where now dry
+    cudaError_t e = s->es == 4
+                        ? launch_clamp_state<float>(s->geo, s->phy, s->at<float>(s->lay.Bc),
+                                                    s->at<float>(s->lay.w[s->cur]), s->at<float>(s->lay.P[s->pcur]),
+                                                    s->at<float>(s->lay.Qc[s->pcur]), s->stream)
+                        : launch_clamp_state<double>(s->geo, s->phy, s->at<double>(s->lay.Bc),
+                                                     s->at<double>(s->lay.w[s->cur]), s->at<double>(s->lay.P[s->pcur]),
+                                                     s->at<double>(s->lay.Qc[s->pcur]), s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set_bathymetry");
+    s->nh = 0;
+    return CEL_OK;
+}
+
+cel_status cel_step(cel_solver *s, int32_t nsteps)
+{
+    if (!s || nsteps < 0) return fail(s, CEL_ERR_INVALID_ARG, "bad step count");
+    return s->es == 4 ? step_t<float>(s, nsteps) : step_t<double>(s, nsteps);
+}
+
+cel_status cel_get_state(cel_solver *s, void *w, void *P, void *Q)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    cudaError_t e;
+    if (s->es == 4)
+        e = launch_get_state<float>(s->geo, s->at<float>(s->lay.w[s->cur]), s->at<float>(s->lay.P[s->pcur]),
+                                    s->at<float>(s->lay.Qc[s->pcur]), (float *)w, (float *)P, (float *)Q, s->stream);
+    else
+        e = launch_get_state<double>(s->geo, s->at<double>(s->lay.w[s->cur]), s->at<double>(s->lay.P[s->pcur]),
+                                     s->at<double>(s->lay.Qc[s->pcur]), (double *)w, (double *)P, (double *)Q, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "get_state");
+    return CEL_OK;
+}
+
+cel_status cel_get_field(cel_solver *s, int32_t which, void *dst)
+{
+    if (!s || !dst || which < 0 || which > 3) return fail(s, CEL_ERR_INVALID_ARG, "bad field");
+    cudaError_t e;
+    if (s->es == 4)
+        e = launch_get_field<float>(s->geo, s->phy, which, s->at<float>(s->lay.Bc), s->at<float>(s->lay.dr),
+                                    s->at<float>(s->lay.U), s->at<float>(s->lay.Vc), (float *)dst, s->stream);
+    else
+        e = launch_get_field<double>(s->geo, s->phy, which, s->at<double>(s->lay.Bc), s->at<double>(s->lay.dr),
+                                     s->at<double>(s->lay.U), s->at<double>(s->lay.Vc), (double *)dst,
+                                     s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "get_field");
+    return CEL_OK;
+}
+
+cel_status cel_gauge_bytes(int32_t n, int32_t capacity, int32_t real_bytes, size_t *bytes)
+{
+    if (!bytes || n < 0 || capacity < 0 || (real_bytes != 4 && real_bytes != 8)) return CEL_ERR_INVALID_ARG;
+    *bytes = align256((size_t)n * 2 * sizeof(int32_t)) + (size_t)n * capacity * real_bytes;
+    return CEL_OK;
+}
+
+cel_status cel_set_gauges(cel_solver *s, const int32_t *ij_host, int32_t n, int32_t log_every, int32_t capacity,
+                          void *gauge_buf_dev, size_t buf_bytes)
+{
+    if (!s || n < 0 || log_every < 0 || capacity < 0 || (n > 0 && (!ij_host || !gauge_buf_dev)))
+        return fail(s, CEL_ERR_INVALID_ARG, "bad gauge arguments");
+    for (int k = 0; k < n; k++)
+        if (ij_host[2 * k] < 0 || ij_host[2 * k] >= s->grid.nx || ij_host[2 * k + 1] < 0 ||
+            ij_host[2 * k + 1] >= s->grid.ny)
+            return fail(s, CEL_ERR_INVALID_ARG, "gauge outside the grid");
+    size_t need;
+    cel_gauge_bytes(n, capacity, s->es, &need);
+    if (n > 0 && buf_bytes < need) return fail(s, CEL_ERR_WORKSPACE_TOO_SMALL, "gauge buffer too small");
+    if (n > 0 && ((uintptr_t)gauge_buf_dev & 255) != 0) return fail(s, CEL_ERR_INVALID_ARG, "gauge buffer alignment");
+    s->ng = n;
+    s->log_every = log_every;
+    s->cap = capacity;
+    s->nrec = s->head = 0;
+    s->gij = n ? (int32_t *)gauge_buf_dev : nullptr;
+    s->gring = n ? (unsigned char *)gauge_buf_dev + align256((size_t)n * 2 * sizeof(int32_t)) : nullptr;
+    if (n > 0)
+        CEL_CUDA(s, cudaMemcpyAsync(s->gij, ij_host, (size_t)n * 2 * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    s->stream), "gauge indices");
+    return CEL_OK;
+}
+
+cel_status cel_read_gauges(cel_solver *s, void *eta_host, int32_t max_rec, int32_t *n_rec)
+{
+    if (!s || !n_rec || max_rec < 0 || (max_rec > 0 && !eta_host)) return fail(s, CEL_ERR_INVALID_ARG, "bad read");
+    int n = s->nrec < max_rec ? s->nrec : max_rec;
+    size_t rec = (size_t)s->ng * s->es;
+    for (int r = 0; r < n; r++) {
+        int slot = (s->head + r) % s->cap;
+        CEL_CUDA(s, cudaMemcpyAsync((unsigned char *)eta_host + (size_t)r * rec, s->gring + (size_t)slot * rec, rec,
+                                    cudaMemcpyDeviceToHost, s->stream), "read gauges");
+    }
+    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "read gauges");
+    if (s->cap) s->head = (s->head + n) % s->cap;
+    s->nrec -= n;
+    *n_rec = n;
+    return CEL_OK;
+}
+
+cel_status cel_get_time(cel_solver *s, double *t, int64_t *step)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    if (t) *t = (double)s->step * s->params.dt;
+    if (step) *step = s->step;
+    return CEL_OK;
+}
+
+cel_status cel_check_finite(cel_solver *s)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    unsigned long long *flag = s->at<unsigned long long>(s->lay.flag);
+    CEL_CUDA(s, cudaMemsetAsync(flag, 0xff, sizeof(unsigned long long), s->stream), "check_finite");
+    cudaError_t e = s->es == 4
+                        ? launch_check_finite<float>(s->geo, s->at<float>(s->lay.w[s->cur]), s->at<float>(s->lay.P[s->pcur]),
+                                                     s->at<float>(s->lay.Qc[s->pcur]), flag, s->stream)
+                        : launch_check_finite<double>(s->geo, s->at<double>(s->lay.w[s->cur]),
+                                                      s->at<double>(s->lay.P[s->pcur]), s->at<double>(s->lay.Qc[s->pcur]), flag,
+                                                      s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "check_finite");
+    unsigned long long v = 0;
+    CEL_CUDA(s, cudaMemcpyAsync(&v, flag, sizeof(v), cudaMemcpyDeviceToHost, s->stream), "check_finite");
+    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "check_finite");
+    if (v != ~0ull) {
+        char buf[128];
+        snprintf(buf, sizeof(buf), "non-finite value at cell i=%llu j=%llu", v % (unsigned long long)s->grid.nx,
+                 v / (unsigned long long)s->grid.nx);
+        return fail(s, CEL_ERR_NONFINITE, buf);
+    }
+    return CEL_OK;
+}
+
+cel_status cel_checkpoint_bytes(const cel_solver *s, size_t *bytes)
+{
+    if (!s || !bytes) return CEL_ERR_INVALID_ARG;
+    *bytes = ckpt_total(s);
+    return CEL_OK;
+}
+
+cel_status cel_save_checkpoint(cel_solver *s, void *dst_dev, size_t bytes)
+{
+    if (!s || !dst_dev) return fail(s, CEL_ERR_INVALID_ARG, "NULL checkpoint buffer");
+    size_t need = ckpt_total(s);
+    if (bytes < need) return fail(s, CEL_ERR_WORKSPACE_TOO_SMALL, "checkpoint buffer too small");
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kCkptMagic;
+    h.nx = s->grid.nx;
+    h.ny = s->grid.ny;
+    h.es = s->es;
+    h.K = s->params.corrector_iters;
+    h.step = s->step;
+    h.nh = s->nh;
+    h.bytes = need;
+    unsigned char *dst = (unsigned char *)dst_dev;
+    CEL_CUDA(s, cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream), "checkpoint header");
+    // the header copy reads pageable host memory: finish it before h goes away
+    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "checkpoint header");
+    CkptPart parts[32];
+    int np = ckpt_parts(s, parts);
+    size_t off = align256(sizeof(CkptHeader));
+    for (int k = 0; k < np; k++) {
+        CEL_CUDA(s, cudaMemcpyAsync(dst + off, s->ws + parts[k].off_ws, parts[k].bytes, cudaMemcpyDeviceToDevice,
+                                    s->stream), "checkpoint");
+        off += align256(parts[k].bytes);
+    }
+    return CEL_OK;
+}
+
+cel_status cel_load_checkpoint(cel_solver *s, const void *src_dev, size_t bytes)
+{
+    if (!s || !src_dev) return fail(s, CEL_ERR_INVALID_ARG, "NULL checkpoint buffer");
+    CkptHeader h;
+    if (bytes < sizeof(h)) return fail(s, CEL_ERR_INVALID_ARG, "checkpoint too small");
+    CEL_CUDA(s, cudaMemcpyAsync(&h, src_dev, sizeof(h), cudaMemcpyDeviceToHost, s->stream), "checkpoint header");
+    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "checkpoint header");
+    if (h.magic != kCkptMagic || h.nx != s->grid.nx || h.ny != s->grid.ny || h.es != s->es ||
+        h.K != s->params.corrector_iters)
+        return fail(s, CEL_ERR_INVALID_ARG, "checkpoint does not match this solver");
+    s->cur = 0;
+    s->pcur = 0;
+    size_t need = ckpt_total(s);
+    if (bytes < need || h.bytes != need) return fail(s, CEL_ERR_INVALID_ARG, "checkpoint size mismatch");
+    CkptPart parts[32];
+    int np = ckpt_parts(s, parts);
+    size_t off = align256(sizeof(CkptHeader));
+    const unsigned char *src = (const unsigned char *)src_dev;
+    for (int k = 0; k < np; k++) {
+        CEL_CUDA(s, cudaMemcpyAsync(s->ws + parts[k].off_ws, src + off, parts[k].bytes, cudaMemcpyDeviceToDevice,
+                                    s->stream), "checkpoint");
+        off += align256(parts[k].bytes);
+    }
+    s->step = h.step;
+    s->nh = h.nh;
+    return CEL_OK;
+}
+
+cel_status cel_profile_enable(cel_solver *s, int32_t capacity)
+{
+    if (!s || capacity < 1 || capacity > (1 << 20)) return fail(s, CEL_ERR_INVALID_ARG, "bad profile capacity");
+    prof_free(s);
+    s->ev_beg = new cudaEvent_t[capacity];
+    s->ev_end = new cudaEvent_t[capacity];
+    s->ev_kind = new int[capacity];
+    for (int k = 0; k < capacity; k++) {
+        cudaError_t e1 = cudaEventCreate(&s->ev_beg[k]);
+        cudaError_t e2 = cudaEventCreate(&s->ev_end[k]);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            s->ev_cap = k + (e1 == cudaSuccess && e2 == cudaSuccess);
+            prof_free(s);
+            return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "profile events");
+        }
+    }
+    s->ev_cap = capacity;
+    s->ev_used = 0;
+    return CEL_OK;
+}
+
+cel_status cel_profile_read(cel_solver *s, double ms[3], int64_t count[3])
+{
+    if (!s || !ms || !count) return CEL_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; k++) {
+        ms[k] = 0.0;
+        count[k] = 0;
+    }
+    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "profile read");
+    for (int k = 0; k < s->ev_used; k++) {
+        float t = 0.f;
+        CEL_CUDA(s, cudaEventElapsedTime(&t, s->ev_beg[k], s->ev_end[k]), "profile elapsed");
+        ms[s->ev_kind[k]] += t;
+        count[s->ev_kind[k]] += 1;
+    }
+    s->ev_used = 0;
+    return CEL_OK;
+}
+
+cel_status cel_profile_disable(cel_solver *s)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    prof_free(s);
+    return CEL_OK;
+}
+
+cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches)
+{
+    if (!s || !launches) return CEL_ERR_INVALID_ARG;
+    *launches = s->launches;
+    return CEL_OK;
+}
+
+}  // extern "C"

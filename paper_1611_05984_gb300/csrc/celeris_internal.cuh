@@ -1,0 +1,134 @@
+// Internal declarations shared by the kernels and the C-ABI host code.
+//
+// Data layout in device memory (all arrays carved from the caller's workspace):
+//   * x-family fields (w, P, dU*, and every per-cell history value) are
+//     row-major [ny][px], px = nx rounded up to 32 elements, so an x-row is a
+//     contiguous line (the x tridiagonal solves of Eq. 21 read whole rows);
+//   * y-family fields (Q, dV*) are column-major [nx][py], py = ny rounded up
+//     to 32, so a y-column is a contiguous line (the y solves of Eq. 22);
+//   * the static bed is stored once, as corner values (nx+3) x (ny+3): corner
+//     (ci, cj) at (ci dx, cj dy), ci in [-1, nx+1], at [(cj+1)*pc + ci+1];
+//   * the still-water depth d is stored twice, row-major for the x solves and
+//     column-major for the y solves (static, derived at create);
+//   * dry-cell bit masks, one bit per cell, row-major words for the x solves
+//     and column-major words for the y solves.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cel {
+
+constexpr int kTile = 32;          // stencil tile edge (cells)
+constexpr int kHalo = 2;           // ghost layers (Sec. 2.4)
+constexpr int kTileIn = kTile + 2 * kHalo;   // 36
+constexpr int kStride = kTileIn + 1;         // padded smem row of the state tile
+constexpr int kCorner = kTile + 3;           // 35 corners per tile edge
+constexpr int kCornerStride = kCorner + 1;
+constexpr int kDcell = kTile + 2;            // 34 cells of d per tile edge
+constexpr int kDStride = kDcell + 1;
+constexpr int kStencilThreads = 256;
+
+enum { kSolid = 0, kSponge = 1, kSine = 2 };
+enum { kBsnq = 0, kNlsw = 1 };
+enum { kFricNone = 0, kFricQuad = 1, kFricManning = 2 };
+// Stage kinds of one step (Sec. 2.3).
+enum { kEuler0 = 0, kEuler1 = 1, kAB3 = 2, kAM4 = 3 };
+
+struct Side {
+    int type;            // kSolid | kSponge | kSine
+    int width;           // sponge width in cells
+    int ncomp;
+    double L;            // sponge width in metres
+    double amp[8], omega[8], cdir[8], sdir[8], phase[8];
+};
+
+struct Geo {
+    int nx, ny;
+    int px, py, pc;      // pitches (elements): row-major, column-major, corners
+    int nwx, nwy;        // mask words per row / per column
+    double dx, dy;
+};
+
+struct Phys {
+    int model, friction, K;
+    double g, Bd, theta, eps, dt, ws, fcoef;
+};
+
+struct Bnd {
+    Side s[4];           // west, east, south, north
+};
+
+template <typename real>
+struct StencilArgs {
+    Geo geo;
+    Phys phy;
+    Bnd bnd;
+    const real *Bc;
+    const real *w_in, *P_in, *Qc_in;     // state (or AM4 iterate) at time t
+    real *w_out, *U_out, *Vc_out;        // w^{n+1}, and the increments of U*, V*
+    real *a[3], *b[3];                   // AB3 carries (w, U, V), b = this slot
+    real *Y[3], *q[3], *e[3];            // AM4 carries (K > 0)
+    uint32_t *mask_r, *mask_c;
+    int kind;                            // kEuler0 | kEuler1 | kAB3 | kAM4
+    int keepK;                           // maintain the AM4 carries
+    int final_stage;                     // last stage of the step: sponge on w
+    double t;                            // time of the state read (ghosts)
+};
+
+template <typename real>
+struct LineArgs {
+    Geo geo;
+    Phys phy;
+    Bnd bnd;
+    const real *rhs;       // increment of U* (x-lines) or V* (y-lines), line-major
+    const real *d;         // still-water depth, line-major
+    const uint32_t *mask;  // dry bits, line-major words
+    const real *base;      // P^n or Q^n, line-major
+    real *sol;             // P^{n+1} = P^n + solution, line-major
+    int dir;               // 0: x-lines (rows), 1: y-lines (columns)
+    int n, nlines, pitch, nwords;
+    int nseg;              // segments per line (threads doing sweeps)
+    int final_stage;       // apply the sponge
+    int identity;          // NLSW model: no dispersive solve, P = U*, Q = V*
+    double t0, t1;         // times of the ghost discharge on sine sides
+};
+
+// Launchers (celeris_kernels.cu).  All return cudaGetLastError().
+template <typename real>
+cudaError_t launch_corners(const Geo &g, const real *z, real *Bc, cudaStream_t st);
+template <typename real>
+cudaError_t launch_static_cells(const Geo &g, const Phys &p, const real *Bc, real *d_r,
+                                real *d_c, cudaStream_t st);
+template <typename real>
+cudaError_t launch_set_state(const Geo &g, const Phys &p, const real *Bc, const real *w_in,
+                             const real *P_in, const real *Q_in, real *w, real *P, real *Qc,
+                             int rest, cudaStream_t st);
+template <typename real>
+cudaError_t launch_clamp_state(const Geo &g, const Phys &p, const real *Bc, real *w, real *P,
+                               real *Qc, cudaStream_t st);
+template <typename real>
+cudaError_t launch_get_state(const Geo &g, const real *w, const real *P, const real *Qc,
+                             real *w_out, real *P_out, real *Q_out, cudaStream_t st);
+template <typename real>
+cudaError_t launch_get_field(const Geo &g, const Phys &p, int which, const real *Bc,
+                             const real *d_r, const real *U, const real *Vc, real *out,
+                             cudaStream_t st);
+template <typename real>
+cudaError_t launch_add_solitary(const Geo &g, const Phys &p, const real *Bc, real *w, real *P,
+                                real *Qc, double H, double ct, double st_, double x0,
+                                double y0, double ks, double cs, cudaStream_t st);
+template <typename real>
+cudaError_t launch_gauges(const Geo &g, const Phys &p, const real *w, const int32_t *ij,
+                          int n, real *slot, cudaStream_t st);
+template <typename real>
+cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, const real *Qc,
+                                unsigned long long *first_bad, cudaStream_t st);
+template <typename real>
+cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st);
+template <typename real>
+cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st);
+template <typename real>
+size_t line_smem_bytes(int n, int nseg);
+int line_segments(int n, int real_bytes);
+
+}  // namespace cel

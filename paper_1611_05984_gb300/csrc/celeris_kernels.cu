@@ -1,0 +1,1009 @@
+// CUDA kernels of the Celeris extended-Boussinesq step for GB300 (sm_103a).
+//
+// Paper: Tavakkol & Lynett, "Celeris", arXiv 1611.05984.
+//   Sec. 2.1  Eq. 1-3 (governing equations); Sec. 2.2 Eq. 4-14 (Wei-Kirby
+//   form, KP07 steps 1-4); Sec. 2.3 Eq. 15-23 (AB3 / AM4, tridiagonal
+//   systems); Sec. 2.4 Eq. 24-30 (boundaries); Sec. 2.6 Eq. 31-32 (friction);
+//   Sec. 2.7 Eq. 33-36 (solitary wave).
+//
+// Per step and per stage (predictor, then K corrector iterations) three
+// kernels run:
+//   k_stencil  one 32x32 tile per thread block: stages w, P, Q (+2 ghost
+//              layers produced in shared memory from the boundary rules) and
+//              the bed corners, computes every face flux once, then per cell
+//              E, F, G, F*, G*, friction and the time update; writes w^{n+1},
+//              the increments of U* (row-major) and V* (column-major,
+//              transposed through shared memory) and the dry-cell bits.
+//   k_lines    one thread block per line, x-rows then y-columns: a
+//              partitioned tridiagonal solve of Eq. 21/22 for the increment
+//              P^{n+1} - P^n (each thread eliminates its own segment, the
+//              2-per-segment interface system is solved by parallel cyclic
+//              reduction), then P^n + increment, sponge and dry-cell epilogue.
+#include "celeris_internal.cuh"
+
+#include <math.h>
+
+namespace cel {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+__device__ __forceinline__ int mirror_index(int i, int n)
+{
+    return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
+}
+
+// Eq. 14: u = k(h) P with k(h) = sqrt(2) h / sqrt(h^4 + max(h^4, eps)).
+template <typename real>
+__device__ __forceinline__ real desing(real h, real eps)
+{
+    real h2 = h * h;
+    real h4 = h2 * h2;
+    return real(1.4142135623730951) * h / sqrt(h4 + fmax(h4, eps));
+}
+
+// KP07 step 1: generalized minmod of the three one-sided / central slopes.
+template <typename real>
+__device__ __forceinline__ real minmod3(real th, real qm, real q0, real qp)
+{
+    real a = th * (q0 - qm), b = real(0.5) * (qp - qm), c = th * (qp - q0);
+    if (a > real(0) && b > real(0) && c > real(0)) return fmin(a, fmin(b, c));
+    if (a < real(0) && b < real(0) && c < real(0)) return fmax(a, fmax(b, c));
+    return real(0);
+}
+
+// KP07 steps 1-2 for one cell along one direction: face values of (w, P, Q)
+// at the low and high faces, then the positivity fix of w.
+template <typename real>
+__device__ __forceinline__ void recon(real th, const real wq[3], const real Pq[3],
+                                      const real Qq[3], real Blo, real Bhi, real lo[3],
+                                      real hi[3])
+{
+    real sw = minmod3(th, wq[0], wq[1], wq[2]);
+    real sP = minmod3(th, Pq[0], Pq[1], Pq[2]);
+    real sQ = minmod3(th, Qq[0], Qq[1], Qq[2]);
+    lo[0] = wq[1] - real(0.5) * sw;
+    hi[0] = wq[1] + real(0.5) * sw;
+    lo[1] = Pq[1] - real(0.5) * sP;
+    hi[1] = Pq[1] + real(0.5) * sP;
+    lo[2] = Qq[1] - real(0.5) * sQ;
+    hi[2] = Qq[1] + real(0.5) * sQ;
+    if (hi[0] < Bhi) {
+        hi[0] = Bhi;
+        lo[0] = real(2) * wq[1] - Bhi;
+    } else if (lo[0] < Blo) {
+        lo[0] = Blo;
+        hi[0] = real(2) * wq[1] - Blo;
+    }
+}
+
+// KP07 step 3: central-upwind flux.  States are (w, normal, tangential
+// discharge); H = (mass, normal momentum, tangential momentum).
+template <typename real>
+__device__ __forceinline__ void cu_flux(real g, real eps, real wL, real nL, real tL, real wR,
+                                        real nR, real tR, real Bf, real H[3])
+{
+    real hL = fmax(wL - Bf, real(0)), hR = fmax(wR - Bf, real(0));
+    real kL = desing(hL, eps), kR = desing(hR, eps);
+    real uL = kL * nL, vL = kL * tL, uR = kR * nR, vR = kR * tR;
+    real qnL = hL * uL, qtL = hL * vL, qnR = hR * uR, qtR = hR * vR;
+    real sL = sqrt(g * hL), sR = sqrt(g * hR);
+    real ap = fmax(fmax(uL + sL, uR + sR), real(0));
+    real am = fmin(fmin(uL - sL, uR - sR), real(0));
+    real den = ap - am;
+    if (!(den > real(0))) {
+        H[0] = H[1] = H[2] = real(0);
+        return;
+    }
+    real inv = real(1) / den, apam = ap * am;
+    real FL1 = qnL * uL + real(0.5) * g * hL * hL, FR1 = qnR * uR + real(0.5) * g * hR * hR;
+    H[0] = (ap * qnL - am * qnR + apam * (wR - wL)) * inv;
+    H[1] = (ap * FL1 - am * FR1 + apam * (qnR - qnL)) * inv;
+    H[2] = (ap * (qnL * vL) - am * (qnR * vR) + apam * (qtR - qtL)) * inv;
+}
+
+// Sine-wave maker, Eq. 25-29, summed over components; double precision.
+__device__ inline void sine_ghost(const Side &s, double g, double dadj, double x, double y,
+                                  double t, double &eta, double &Pg, double &Qg)
+{
+    eta = Pg = Qg = 0.0;
+    if (!(dadj > 0.0)) return;
+    for (int m = 0; m < s.ncomp; m++) {
+        double om = s.omega[m];
+        double k0 = om * om / g;
+        double k = k0 * sqrt(1.0 / tanh(k0 * dadj));
+        double c = om / k;
+        double em = s.amp[m] * sin(om * t - k * s.cdir[m] * x - k * s.sdir[m] * y + s.phase[m]);
+        eta += em;
+        Pg += c * s.cdir[m] * em;
+        Qg += c * s.sdir[m] * em;
+    }
+}
+
+// Eq. 30 with D the distance from the absorbing face to the cell centre;
+// the smallest gamma over the sponge sides.
+template <typename real>
+__device__ __forceinline__ real sponge_gamma(const Bnd &b, const Geo &g, int i, int j)
+{
+    real gm = real(1);
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        if (b.s[s].type != kSponge || b.s[s].width <= 0) continue;
+        double D = s == 0   ? (i + 0.5) * g.dx
+                   : s == 1 ? (g.nx - i - 0.5) * g.dx
+                   : s == 2 ? (j + 0.5) * g.dy
+                            : (g.ny - j - 0.5) * g.dy;
+        double L = b.s[s].L;
+        if (D < L) {
+            real v = real(0.5) * (real(1) + cos(real(kPi * (L - D) / L)));
+            gm = fmin(gm, v);
+        }
+    }
+    return gm;
+}
+
+template <typename real>
+__device__ __forceinline__ real cell_bbar(real c00, real c10, real c01, real c11)
+{
+    return real(0.25) * (((c00 + c10) + c01) + c11);
+}
+
+// ------------------------------------------------------------ static fields
+
+// a0 (Reading A-W1): corner bed = mean of the 4 cells around it, with the
+// cell-centre bed mirrored evenly into the two ghost layers.
+template <typename real>
+__global__ void k_corners(Geo g, const real *__restrict__ z, real *__restrict__ Bc)
+{
+    int ci = blockIdx.x * blockDim.x + threadIdx.x - 1;
+    int cj = blockIdx.y * blockDim.y + threadIdx.y - 1;
+    if (ci > g.nx + 1 || cj > g.ny + 1) return;
+    int i0 = mirror_index(ci - 1, g.nx), i1 = mirror_index(ci, g.nx);
+    int j0 = mirror_index(cj - 1, g.ny), j1 = mirror_index(cj, g.ny);
+    real z00 = z[(size_t)j0 * g.nx + i0], z10 = z[(size_t)j0 * g.nx + i1];
+    real z01 = z[(size_t)j1 * g.nx + i0], z11 = z[(size_t)j1 * g.nx + i1];
+    Bc[(size_t)(cj + 1) * g.pc + (ci + 1)] = real(0.25) * (((z00 + z10) + z01) + z11);
+}
+
+template <typename real>
+__device__ __forceinline__ real corner(const real *Bc, const Geo &g, int ci, int cj)
+{
+    return Bc[(size_t)(cj + 1) * g.pc + (ci + 1)];
+}
+
+template <typename real>
+__device__ __forceinline__ real bbar_at(const real *Bc, const Geo &g, int i, int j)
+{
+    return cell_bbar(corner(Bc, g, i, j), corner(Bc, g, i + 1, j), corner(Bc, g, i, j + 1),
+                     corner(Bc, g, i + 1, j + 1));
+}
+
+template <typename real>
+__global__ void k_static_cells(Geo g, Phys p, const real *__restrict__ Bc, real *__restrict__ d_r,
+                               real *__restrict__ d_c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    real d = fmax(real(p.ws) - bbar_at(Bc, g, i, j), real(0));
+    d_r[(size_t)j * g.px + i] = d;
+    d_c[(size_t)i * g.py + j] = d;
+}
+
+// Hot start (or rest): w >= Bbar, P = Q = 0 where the depth is zero.
+template <typename real>
+__global__ void k_set_state(Geo g, Phys p, const real *__restrict__ Bc, const real *w_in,
+                            const real *P_in, const real *Q_in, real *w, real *P, real *Qc,
+                            int rest)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    size_t k = (size_t)j * g.nx + i;
+    real Bb = bbar_at(Bc, g, i, j);
+    real wv = rest ? real(p.ws) : w_in[k];
+    real Pv = rest ? real(0) : P_in[k];
+    real Qv = rest ? real(0) : Q_in[k];
+    wv = fmax(wv, Bb);
+    if (wv - Bb <= real(0)) {
+        Pv = real(0);
+        Qv = real(0);
+    }
+    w[(size_t)j * g.px + i] = wv;
+    P[(size_t)j * g.px + i] = Pv;
+    Qc[(size_t)i * g.py + j] = Qv;
+}
+
+template <typename real>
+__global__ void k_clamp_state(Geo g, Phys p, const real *__restrict__ Bc, real *w, real *P, real *Qc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    size_t kr = (size_t)j * g.px + i, kc = (size_t)i * g.py + j;
+    real Bb = bbar_at(Bc, g, i, j);
+    real wv = fmax(w[kr], Bb);
+    w[kr] = wv;
+    if (wv - Bb <= real(0)) {
+        P[kr] = real(0);
+        Qc[kc] = real(0);
+    }
+}
+
+template <typename real>
+__global__ void k_get_state(Geo g, const real *w, const real *P, const real *Qc, real *w_out,
+                            real *P_out, real *Q_out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    size_t k = (size_t)j * g.nx + i;
+    if (w_out) w_out[k] = w[(size_t)j * g.px + i];
+    if (P_out) P_out[k] = P[(size_t)j * g.px + i];
+    if (Q_out) Q_out[k] = Qc[(size_t)i * g.py + j];
+}
+
+template <typename real>
+__global__ void k_get_field(Geo g, Phys p, int which, const real *Bc, const real *d_r,
+                            const real *U, const real *Vc, real *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    real v;
+    if (which == 0) v = bbar_at(Bc, g, i, j);
+    else if (which == 1) v = d_r[(size_t)j * g.px + i];
+    else if (which == 2) v = U[(size_t)j * g.px + i];
+    else v = Vc[(size_t)i * g.py + j];
+    out[(size_t)j * g.nx + i] = v;
+}
+
+// Eq. 33-36 (Reading A-S1), evaluated in double, added where d > 0.
+template <typename real>
+__global__ void k_add_solitary(Geo g, Phys p, const real *Bc, real *w, real *P, real *Qc,
+                               double H, double ct, double st, double x0, double y0, double ks,
+                               double cs)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    size_t kr = (size_t)j * g.px + i, kc = (size_t)i * g.py + j;
+    real Bb = bbar_at(Bc, g, i, j);
+    real d = fmax(real(p.ws) - Bb, real(0));
+    real wv = w[kr], Pv = P[kr], Qv = Qc[kc];
+    if (d > real(0)) {
+        double xi = ((i + 0.5) * g.dx - x0) * ct + ((j + 0.5) * g.dy - y0) * st;
+        double sh = 1.0 / cosh(ks * xi);
+        double es = H * sh * sh;
+        wv = (real)fmax((double)wv + es, (double)Bb);
+        Pv = (real)((double)Pv + cs * es * ct);
+        Qv = (real)((double)Qv + cs * es * st);
+    }
+    if (wv - Bb <= real(0)) {
+        Pv = real(0);
+        Qv = real(0);
+    }
+    w[kr] = wv;
+    P[kr] = Pv;
+    Qc[kc] = Qv;
+}
+
+template <typename real>
+__global__ void k_gauges(Geo g, Phys p, const real *w, const int32_t *ij, int n, real *slot)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = ij[2 * k], j = ij[2 * k + 1];
+    slot[k] = w[(size_t)j * g.px + i] - real(p.ws);
+}
+
+template <typename real>
+__global__ void k_check_finite(Geo g, const real *w, const real *P, const real *Qc,
+                               unsigned long long *first_bad)
+{
+    size_t n = (size_t)g.nx * g.ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(k % g.nx), j = (int)(k / g.nx);
+        real a = w[(size_t)j * g.px + i], b = P[(size_t)j * g.px + i], c = Qc[(size_t)i * g.py + j];
+        if (!isfinite(a) || !isfinite(b) || !isfinite(c)) atomicMin(first_bad, (unsigned long long)k);
+    }
+}
+
+// ------------------------------------------------------------ the stencil
+
+template <typename real>
+struct StencilSmem {
+    real w[kTileIn * kStride];
+    real P[kTileIn * kStride];
+    real Q[kTileIn * kStride];
+    real Bc[kCorner * kCornerStride];
+    real d[kDcell * kDStride];
+    real Fx[3][kTile][kTile + 1];    // x-faces: [component][row][face]
+    real Fy[3][kTile + 1][kTile];    // y-faces: [component][face][column]
+    real Vout[kTile][kTile + 1];     // V*^{n+1} staged for the transposed store
+    uint32_t colbits[kTile];
+};
+
+// Update of one unknown (w, U* or V*) with right side R and mixed term Phi
+// (0 for w), Sec. 2.3, returned as the increment X^{n+1} - X^n.  Carries
+// (per cell, row-major):
+//   a = -16 (dt/12) R^{n-1} - 3 Phi^{n-1}       (in place)
+//   b = 5 (dt/12) R^{n-2} + Phi^{n-2}           (two slots, by step parity)
+// so that Eq. 15-17 read X^{n+1} - X^n = 23 (dt/12) R^n + 2 Phi^n + a + b.
+// The first two steps are forward Euler; the second adds Phi^1 - Phi^0,
+// for which `a` holds Phi^0 after the first.  With K > 0 also
+//   q = (dt/24)(-5 R^{n-1} + R^{n-2}),  e = (dt/24) R^{n-1},
+//   Y = X0 + 19 (dt/24) R^n - Phi^n + q         (corrector base),
+// so that Eq. 18-20 read X^{n+1} - X0 = Y - X0 + 9 (dt/24) R^{n+1} + Phi^{n+1}
+// (the AM4 stage returns Y + 9 (dt/24) R + Phi).  For w, X0 = w^n, so the
+// corrector returns w^{n+1} itself.  U* and V* are carried as increments
+// only (X0 = 0): the line solves find P^{n+1} - P^n from the increment of U*,
+// which equals recomputing U*^n from P^n by Eq. 23 but keeps the rounding
+// relative to the increment instead of to P.
+template <typename real>
+__device__ __forceinline__ real advance(int kind, int keepK, real X0, real R, real Phi, real dt, size_t k,
+                                        real *a, real *b, real *Y, real *q, real *e)
+{
+    const real c12 = dt / real(12), c24 = dt / real(24);
+    if (kind == kAM4) return Y[k] + real(9) * c24 * R + Phi;
+    real D;
+    if (kind == kEuler0) {
+        D = dt * R;
+        a[k] = Phi;
+        b[k] = real(5) * c12 * R + Phi;
+        if (keepK) e[k] = c24 * R;
+    } else if (kind == kEuler1) {
+        D = dt * R + (Phi - a[k]);
+        a[k] = real(-16) * c12 * R - real(3) * Phi;
+        b[k] = real(5) * c12 * R + Phi;
+        if (keepK) {
+            q[k] = real(-5) * c24 * R + e[k];
+            e[k] = c24 * R;
+        }
+    } else {
+        D = real(23) * c12 * R + real(2) * Phi + (a[k] + b[k]);
+        if (keepK) {
+            Y[k] = X0 + real(19) * c24 * R - Phi + q[k];
+            q[k] = real(-5) * c24 * R + e[k];
+            e[k] = c24 * R;
+        }
+        a[k] = real(-16) * c12 * R - real(3) * Phi;
+        b[k] = real(5) * c12 * R + Phi;
+    }
+    return D;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StencilSmem<real> &sm = *reinterpret_cast<StencilSmem<real> *>(smem_raw);
+    const Geo &G = A.geo;
+    const int nx = G.nx, ny = G.ny;
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const int tid = threadIdx.x;
+    const real ws = real(A.phy.ws), g = real(A.phy.g), eps = real(A.phy.eps);
+    const real th = real(A.phy.theta);
+
+    // ---- 1. stage the state tile (+2 halo) and the bed corners
+    for (int k = tid; k < kTileIn * kTileIn; k += kStencilThreads) {
+        int ty = k / kTileIn, tx = k % kTileIn;
+        int gx = x0 - kHalo + tx, gy = y0 - kHalo + ty;
+        bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        size_t r = (size_t)gy * G.px + gx;
+        sm.w[ty * kStride + tx] = in ? A.w_in[r] : real(0);
+        sm.P[ty * kStride + tx] = in ? A.P_in[r] : real(0);
+    }
+    for (int k = tid; k < kTileIn * kTileIn; k += kStencilThreads) {
+        int tx = k / kTileIn, ty = k % kTileIn;   // column-major: y fastest
+        int gx = x0 - kHalo + tx, gy = y0 - kHalo + ty;
+        bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        sm.Q[ty * kStride + tx] = in ? A.Qc_in[(size_t)gx * G.py + gy] : real(0);
+    }
+    for (int k = tid; k < kCorner * kCorner; k += kStencilThreads) {
+        int cy = k / kCorner, cx = k % kCorner;
+        int ax = min(x0 + cx, nx + 2), ay = min(y0 + cy, ny + 2);   // array index = corner + 1
+        sm.Bc[cy * kCornerStride + cx] = A.Bc[(size_t)ay * G.pc + ax];
+    }
+    if (tid < kTile) sm.colbits[tid] = 0u;
+    __syncthreads();
+
+    auto cell_d = [&](int cx, int cy) -> real {   // cell whose SW corner is tile corner (cx,cy)
+        const real *c = sm.Bc;
+        real Bb = cell_bbar(c[cy * kCornerStride + cx], c[cy * kCornerStride + cx + 1],
+                            c[(cy + 1) * kCornerStride + cx], c[(cy + 1) * kCornerStride + cx + 1]);
+        return fmax(ws - Bb, real(0));
+    };
+
+    // ---- 2. ghost layers (Sec. 2.4): x-sides over interior rows, then
+    //         y-sides over every column, so corners come by composition.
+    const bool westT = x0 == 0, eastT = x0 + kTile + kHalo > nx;
+    const bool southT = y0 == 0, northT = y0 + kTile + kHalo > ny;
+    if (westT || eastT) {
+        for (int k = tid; k < 4 * (kTileIn - 2); k += kStencilThreads) {
+            int ty = 1 + k % (kTileIn - 2), which = k / (kTileIn - 2);   // ty in [1, 35)
+            int gy = y0 - kHalo + ty;
+            if (gy < 0 || gy >= ny) continue;
+            int side = which < 2 ? 0 : 1, kk = which & 1;
+            if ((side == 0 && !westT) || (side == 1 && !eastT)) continue;
+            int gx = side == 0 ? -1 - kk : nx + kk;
+            int tx = gx - x0 + kHalo;
+            if (tx < 0 || tx >= kTileIn) continue;
+            int sx = side == 0 ? kk : nx - 1 - kk;
+            int stx = sx - x0 + kHalo;
+            const Side &S = A.bnd.s[side];
+            int gi = ty * kStride + tx, si = ty * kStride + stx;
+            if (S.type == kSine) {
+                int ia = side == 0 ? 0 : nx - 1;
+                double dadj = (double)cell_d(ia - x0 + 1, gy - y0 + 1);
+                double eta, Pg, Qg;
+                sine_ghost(S, A.phy.g, dadj, (gx + 0.5) * G.dx, (gy + 0.5) * G.dy, A.t, eta, Pg, Qg);
+                sm.w[gi] = real(A.phy.ws + eta);
+                sm.P[gi] = real(Pg);
+                sm.Q[gi] = real(Qg);
+            } else {
+                sm.w[gi] = sm.w[si];
+                sm.P[gi] = -sm.P[si];
+                sm.Q[gi] = sm.Q[si];
+            }
+        }
+    }
+    __syncthreads();
+    if (southT || northT) {
+        for (int k = tid; k < 4 * (kTileIn - 2); k += kStencilThreads) {
+            int tx = 1 + k % (kTileIn - 2), which = k / (kTileIn - 2);
+            int gx = x0 - kHalo + tx;
+            int side = which < 2 ? 2 : 3, kk = which & 1;
+            if ((side == 2 && !southT) || (side == 3 && !northT)) continue;
+            int gy = side == 2 ? -1 - kk : ny + kk;
+            int ty = gy - y0 + kHalo;
+            if (ty < 0 || ty >= kTileIn) continue;
+            int sy = side == 2 ? kk : ny - 1 - kk;
+            int sty = sy - y0 + kHalo;
+            const Side &S = A.bnd.s[side];
+            int gi = ty * kStride + tx, si = sty * kStride + tx;
+            if (S.type == kSine) {
+                int ia = min(max(gx, 0), nx - 1), ja = side == 2 ? 0 : ny - 1;
+                double dadj = (double)cell_d(ia - x0 + 1, ja - y0 + 1);
+                double eta, Pg, Qg;
+                sine_ghost(S, A.phy.g, dadj, (gx + 0.5) * G.dx, (gy + 0.5) * G.dy, A.t, eta, Pg, Qg);
+                sm.w[gi] = real(A.phy.ws + eta);
+                sm.P[gi] = real(Pg);
+                sm.Q[gi] = real(Qg);
+            } else {
+                sm.w[gi] = sm.w[si];
+                sm.P[gi] = sm.P[si];
+                sm.Q[gi] = -sm.Q[si];
+            }
+        }
+    }
+    // ---- 3. still-water depth d (Sec. 2.1) on the tile + 1 ring
+    for (int k = tid; k < kDcell * kDcell; k += kStencilThreads) {
+        int cy = k / kDcell, cx = k % kDcell;
+        sm.d[cy * kDStride + cx] = cell_d(cx, cy);
+    }
+    __syncthreads();
+
+    // ---- 4. fluxes through every face of the tile, each computed once
+    for (int k = tid; k < 2 * kTile * (kTile + 1); k += kStencilThreads) {
+        real H[3];
+        if (k < kTile * (kTile + 1)) {   // x-face fx (x = (x0+fx) dx) of row r
+            int r = k / (kTile + 1), fx = k % (kTile + 1);
+            int ty = r + kHalo, txL = fx + 1;   // left cell's tile column
+            const real *cb = sm.Bc + (r + 1) * kCornerStride;
+            real B0 = real(0.5) * (cb[fx] + cb[fx + kCornerStride]);
+            real B1 = real(0.5) * (cb[fx + 1] + cb[fx + 1 + kCornerStride]);
+            real B2 = real(0.5) * (cb[fx + 2] + cb[fx + 2 + kCornerStride]);
+            const int o = ty * kStride + txL;
+            real wL[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
+            real PL[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
+            real QL[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
+            real wR[3] = {sm.w[o], sm.w[o + 1], sm.w[o + 2]};
+            real PR[3] = {sm.P[o], sm.P[o + 1], sm.P[o + 2]};
+            real QR[3] = {sm.Q[o], sm.Q[o + 1], sm.Q[o + 2]};
+            real loL[3], hiL[3], loR[3], hiR[3];
+            recon(th, wL, PL, QL, B0, B1, loL, hiL);
+            recon(th, wR, PR, QR, B1, B2, loR, hiR);
+            cu_flux(g, eps, hiL[0], hiL[1], hiL[2], loR[0], loR[1], loR[2], B1, H);
+            sm.Fx[0][r][fx] = H[0];
+            sm.Fx[1][r][fx] = H[1];
+            sm.Fx[2][r][fx] = H[2];
+        } else {                          // y-face gy of column c
+            int kk = k - kTile * (kTile + 1);
+            int gy = kk / kTile, c = kk % kTile;
+            int tx = c + kHalo, tyS = gy + 1;
+            const real *cb = sm.Bc + c + 1;
+            real B0 = real(0.5) * (cb[gy * kCornerStride] + cb[gy * kCornerStride + 1]);
+            real B1 = real(0.5) * (cb[(gy + 1) * kCornerStride] + cb[(gy + 1) * kCornerStride + 1]);
+            real B2 = real(0.5) * (cb[(gy + 2) * kCornerStride] + cb[(gy + 2) * kCornerStride + 1]);
+            const int o = tyS * kStride + tx;
+            real wS[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
+            real PS[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
+            real QS[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
+            real wN[3] = {sm.w[o], sm.w[o + kStride], sm.w[o + 2 * kStride]};
+            real PN[3] = {sm.P[o], sm.P[o + kStride], sm.P[o + 2 * kStride]};
+            real QN[3] = {sm.Q[o], sm.Q[o + kStride], sm.Q[o + 2 * kStride]};
+            real loS[3], hiS[3], loN[3], hiN[3];
+            recon(th, wS, PS, QS, B0, B1, loS, hiS);
+            recon(th, wN, PN, QN, B1, B2, loN, hiN);
+            // normal discharge is Q, tangential is P
+            cu_flux(g, eps, hiS[0], hiS[2], hiS[1], loN[0], loN[2], loN[1], B1, H);
+            sm.Fy[0][gy][c] = H[0];
+            sm.Fy[1][gy][c] = H[2];
+            sm.Fy[2][gy][c] = H[1];
+        }
+    }
+    __syncthreads();
+
+    // ---- 5. per cell: Eq. 9-13, friction, U*, V*, update
+    const real dt = real(A.phy.dt);
+    const real rdx = real(1.0 / G.dx), rdy = real(1.0 / G.dy);
+    const real rdx2 = real(1.0 / (G.dx * G.dx)), rdy2 = real(1.0 / (G.dy * G.dy));
+    const real rdxdy4 = real(1.0 / (4.0 * G.dx * G.dy));
+    const real rdx3h = real(1.0 / (2.0 * G.dx * G.dx * G.dx)), rdy3h = real(1.0 / (2.0 * G.dy * G.dy * G.dy));
+    const real rdxdy2h = real(1.0 / (2.0 * G.dx * G.dy * G.dy)), rdx2dyh = real(1.0 / (2.0 * G.dx * G.dx * G.dy));
+    const real Bd = real(A.phy.Bd), B3 = real(A.phy.Bd + 1.0 / 3.0);
+    const real sixth = real(1.0 / 6.0);
+    const bool bsnq = A.phy.model == kBsnq;
+    const int lane = tid & 31;
+    for (int rr = 0; rr < kTile / (kStencilThreads / 32); rr++) {
+        const int cx = lane, cy = (tid >> 5) + rr * (kStencilThreads / 32);
+        const int i = x0 + cx, j = y0 + cy;
+        const bool valid = i < nx && j < ny;
+        const int o = (cy + kHalo) * kStride + cx + kHalo;
+        const real *cb = sm.Bc + (cy + 1) * kCornerStride + cx + 1;
+        real c00 = cb[0], c10 = cb[1], c01 = cb[kCornerStride], c11 = cb[kCornerStride + 1];
+        real Bb = cell_bbar(c00, c10, c01, c11);
+        real BxW = real(0.5) * (c00 + c01), BxE = real(0.5) * (c10 + c11);
+        real ByS = real(0.5) * (c00 + c10), ByN = real(0.5) * (c01 + c11);
+        real w0 = sm.w[o], P0 = sm.P[o], Q0 = sm.Q[o];
+        real hb = w0 - Bb;
+        real E = -(sm.Fx[0][cy][cx + 1] - sm.Fx[0][cy][cx]) * rdx - (sm.Fy[0][cy + 1][cx] - sm.Fy[0][cy][cx]) * rdy;
+        real F = -(sm.Fx[1][cy][cx + 1] - sm.Fx[1][cy][cx]) * rdx - (sm.Fy[1][cy + 1][cx] - sm.Fy[1][cy][cx]) * rdy -
+                 g * hb * (BxE - BxW) * rdx;
+        real Gq = -(sm.Fx[2][cy][cx + 1] - sm.Fx[2][cy][cx]) * rdx - (sm.Fy[2][cy + 1][cx] - sm.Fy[2][cy][cx]) * rdy -
+                  g * hb * (ByN - ByS) * rdy;
+        if (A.phy.friction != kFricNone) {   // Eq. 31-32 with the Eq. 14 device
+            real hinv = desing(fmax(hb, real(0)), eps);
+            real fc = A.phy.friction == kFricManning ? real(A.phy.g * A.phy.fcoef * A.phy.fcoef) * cbrt(hinv)
+                                                     : real(A.phy.fcoef);
+            real mag = sqrt(P0 * P0 + Q0 * Q0);
+            F -= fc * P0 * mag * hinv * hinv;
+            Gq -= fc * Q0 * mag * hinv * hinv;
+        }
+        real Fs = real(0), Gs = real(0);
+        const int od = (cy + 1) * kDStride + cx + 1;
+        const real dd = sm.d[od];
+        if (bsnq) {
+            const real ddx = (sm.d[od + 1] - sm.d[od - 1]) * (real(0.5) * rdx);
+            const real ddy = (sm.d[od + kDStride] - sm.d[od - kDStride]) * (real(0.5) * rdy);
+            const real *W = sm.w + o;
+            const int S1 = kStride, S2 = 2 * kStride;
+            real e00 = W[0] - ws;
+            real eE = W[1] - ws, eW = W[-1] - ws, eN = W[S1] - ws, eS = W[-S1] - ws;
+            real eEE = W[2] - ws, eWW = W[-2] - ws, eNN = W[S2] - ws, eSS = W[-S2] - ws;
+            real eNE = W[S1 + 1] - ws, eNW = W[S1 - 1] - ws, eSE = W[-S1 + 1] - ws, eSW = W[-S1 - 1] - ws;
+            real exx = (eE - real(2) * e00 + eW) * rdx2;
+            real eyy = (eN - real(2) * e00 + eS) * rdy2;
+            real exy = (eNE - eSE - eNW + eSW) * rdxdy4;
+            real exxx = (eEE - real(2) * eE + real(2) * eW - eWW) * rdx3h;
+            real eyyy = (eNN - real(2) * eN + real(2) * eS - eSS) * rdy3h;
+            real exyy = ((eNE - real(2) * eE + eSE) - (eNW - real(2) * eW + eSW)) * rdxdy2h;
+            real exxy = ((eNE - real(2) * eN + eNW) - (eSE - real(2) * eS + eSW)) * rdx2dyh;
+            F += Bd * g * dd * dd * dd * (exxx + exyy) + Bd * g * dd * dd * (ddx * (real(2) * exx + eyy) + ddy * exy);
+            Gq += Bd * g * dd * dd * dd * (eyyy + exxy) + Bd * g * dd * dd * (ddy * (real(2) * eyy + exx) + ddx * exy);
+            const real *Pt = sm.P + o, *Qt = sm.Q + o;
+            real Qx = (Qt[1] - Qt[-1]) * (real(0.5) * rdx), Qy = (Qt[S1] - Qt[-S1]) * (real(0.5) * rdy);
+            real Qxy = (Qt[S1 + 1] - Qt[-S1 + 1] - Qt[S1 - 1] + Qt[-S1 - 1]) * rdxdy4;
+            real Px = (Pt[1] - Pt[-1]) * (real(0.5) * rdx), Py = (Pt[S1] - Pt[-S1]) * (real(0.5) * rdy);
+            real Pxy = (Pt[S1 + 1] - Pt[-S1 + 1] - Pt[S1 - 1] + Pt[-S1 - 1]) * rdxdy4;
+            Fs = dd * ddx * Qy * sixth + dd * ddy * Qx * sixth + B3 * dd * dd * Qxy;
+            Gs = dd * ddy * Px * sixth + dd * ddx * Py * sixth + B3 * dd * dd * Pxy;
+        }
+        real w1 = w0, dU = real(0), dV = real(0);
+        if (valid) {
+            const size_t kr = (size_t)j * G.px + i;
+            real dw = advance(A.kind, A.keepK, w0, E, real(0), dt, kr, A.a[0], A.b[0], A.Y[0], A.q[0], A.e[0]);
+            w1 = A.kind == kAM4 ? dw : w0 + dw;   // the AM4 base of w holds w^n
+            dU = advance(A.kind, A.keepK, real(0), F, Fs, dt, kr, A.a[1], A.b[1], A.Y[1], A.q[1], A.e[1]);
+            dV = advance(A.kind, A.keepK, real(0), Gq, Gs, dt, kr, A.a[2], A.b[2], A.Y[2], A.q[2], A.e[2]);
+            if (w1 < Bb) w1 = Bb;   // Reading A-D1
+            if (A.final_stage) {
+                real gam = sponge_gamma<real>(A.bnd, G, i, j);
+                if (gam < real(1) && dd > real(0)) w1 = ws + gam * (w1 - ws);
+            }
+            A.w_out[kr] = w1;
+            A.U_out[kr] = dU;
+        }
+        const bool dry = valid && (w1 - Bb <= real(0));
+        unsigned bits = __ballot_sync(0xffffffffu, dry);
+        if (lane == 0 && j < ny) A.mask_r[(size_t)j * G.nwx + (x0 >> 5)] = bits;
+        if (dry) atomicOr(&sm.colbits[cx], 1u << cy);
+        sm.Vout[cy][cx] = dV;
+    }
+    __syncthreads();
+    for (int k = tid; k < kTile * kTile; k += kStencilThreads) {
+        int c = k / kTile, r = k % kTile;
+        int i = x0 + c, j = y0 + r;
+        if (i < nx && j < ny) A.Vc_out[(size_t)i * G.py + j] = sm.Vout[r][c];
+    }
+    if (tid < kTile && x0 + tid < nx) A.mask_c[(size_t)(x0 + tid) * G.nwy + (y0 >> 5)] = sm.colbits[tid];
+}
+
+// ------------------------------------------------------------ line solves
+
+// Change of the sine-maker ghost discharge (P for x-lines, Q for y-lines)
+// from t0 to t1: the ghost term of the boundary row of Eq. 21/22 written for
+// the increment P^{n+1} - P^n.
+template <typename real>
+__device__ inline double ghost_increment(const Side &S, const LineArgs<real> &A, double dadj, double x,
+                                         double y)
+{
+    double eta, P1, Q1, P0, Q0;
+    sine_ghost(S, A.phy.g, dadj, x, y, A.t1, eta, P1, Q1);
+    sine_ghost(S, A.phy.g, dadj, x, y, A.t0, eta, P0, Q0);
+    return A.dir == 0 ? P1 - P0 : Q1 - Q0;
+}
+
+// Eq. 23 coefficients of line element k.
+template <typename real>
+__device__ __forceinline__ void coef23(real B3, real rh, real rh2, real dd, real dm, real dp,
+                                       real &a, real &b, real &c)
+{
+    real dda = (dp - dm) * (real(0.5) * rh);
+    real r = B3 * dd * dd * rh2;
+    real s = dd * dda * (real(1.0 / 6.0) * rh);
+    a = s - r;
+    b = real(1) + real(2) * r;
+    c = -s - r;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = A.n, S = A.nseg, N2 = 2 * S;
+    real *sA = reinterpret_cast<real *>(smem_raw);   // d, then alpha / alpha-hat
+    real *sC = sA + n;                               // gamma / gamma-hat
+    real *sR = sC + n;                               // rhs -> rho -> rho-hat -> x
+    real *ra = sR + n, *rb = ra + N2, *rc = rb + N2, *rr = rc + N2;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const Geo &G = A.geo;
+    const double h = A.dir == 0 ? G.dx : G.dy;
+    const real rh = real(1.0 / h), rh2 = real(1.0 / (h * h));
+    const real B3 = real(A.phy.Bd + 1.0 / 3.0);
+    const Side &lo = A.bnd.s[A.dir == 0 ? 0 : 2];
+    const Side &hi = A.bnd.s[A.dir == 0 ? 1 : 3];
+
+    for (int line = blockIdx.x; line < A.nlines; line += gridDim.x) {
+        const real *rhs = A.rhs + (size_t)line * A.pitch;
+        const real *dl = A.d + (size_t)line * A.pitch;
+        for (int k = tid; k < n; k += T) {
+            sR[k] = rhs[k];
+            sA[k] = dl[k];
+        }
+        __syncthreads();
+        if (!A.identity) {
+        const bool act = tid < S;
+        const int f = act ? (int)((long long)tid * n / S) : 0;
+        const int l = act ? (int)((long long)(tid + 1) * n / S) - 1 : 0;
+        real dm = real(0), dp = real(0), dcur = real(0);
+        if (act) {
+            dm = f > 0 ? sA[f - 1] : sA[0];     // mirrored depth beyond the ends
+            dp = l < n - 1 ? sA[l + 1] : sA[n - 1];
+            dcur = sA[f];
+        }
+        __syncthreads();
+        real af = 0, bf = 1, cf = 0, rf = 0;
+        if (act) {
+            // forward: rows f+1..l as alpha x_f + x_k + gamma x_{k+1} = rho
+            real dprev = dm, ap = 0, gp = 0, rp = 0;
+            for (int k = f; k <= l; k++) {
+                real dnext = k < l ? sA[k + 1] : dp;
+                real ak, bk, ck;
+                coef23(B3, rh, rh2, dcur, dprev, dnext, ak, bk, ck);
+                real rk = sR[k];
+                if (k == 0) {   // Reading A-B2: mirror, or the known ghost increment
+                    if (lo.type == kSine) {
+                        double x = A.dir == 0 ? -0.5 * G.dx : (line + 0.5) * G.dx;
+                        double y = A.dir == 0 ? (line + 0.5) * G.dy : -0.5 * G.dy;
+                        rk -= ak * real(ghost_increment(lo, A, (double)dcur, x, y));
+                    } else {
+                        bk -= ak;
+                    }
+                    ak = real(0);
+                }
+                if (k == n - 1) {
+                    if (hi.type == kSine) {
+                        double x = A.dir == 0 ? (G.nx + 0.5) * G.dx : (line + 0.5) * G.dx;
+                        double y = A.dir == 0 ? (line + 0.5) * G.dy : (G.ny + 0.5) * G.dy;
+                        rk -= ck * real(ghost_increment(hi, A, (double)dcur, x, y));
+                    } else {
+                        bk -= ck;
+                    }
+                    ck = real(0);
+                }
+                if (k == f) {
+                    af = ak;
+                    bf = bk;
+                    cf = ck;
+                    rf = rk;
+                } else {
+                    real al, ga, rho;
+                    if (k == f + 1) {
+                        real inv = real(1) / bk;
+                        al = ak * inv;
+                        ga = ck * inv;
+                        rho = rk * inv;
+                    } else {
+                        real inv = real(1) / (bk - ak * gp);
+                        al = -ak * ap * inv;
+                        ga = ck * inv;
+                        rho = (rk - ak * rp) * inv;
+                    }
+                    sA[k] = al;
+                    sC[k] = ga;
+                    sR[k] = rho;
+                    ap = al;
+                    gp = ga;
+                    rp = rho;
+                }
+                dprev = dcur;
+                dcur = dnext;
+            }
+            // backward: rows l-2..f+1 as x_k = rho^ - alpha^ x_f - gamma^ x_l
+            real ah = sA[l - 1], gh = sC[l - 1], rhh = sR[l - 1];
+            for (int k = l - 2; k >= f + 1; k--) {
+                real ga = sC[k];
+                rhh = sR[k] - ga * rhh;
+                ah = sA[k] - ga * ah;
+                gh = -ga * gh;
+                sA[k] = ah;
+                sC[k] = gh;
+                sR[k] = rhh;
+            }
+            // reduced rows: (x_{l-1 of prev}, x_f, x_l) and (x_f, x_l, x_{f of next})
+            if (l - f >= 2) {
+                ra[2 * tid] = af;
+                rb[2 * tid] = bf - cf * sA[f + 1];
+                rc[2 * tid] = -cf * sC[f + 1];
+                rr[2 * tid] = rf - cf * sR[f + 1];
+            } else {
+                ra[2 * tid] = af;
+                rb[2 * tid] = bf;
+                rc[2 * tid] = cf;
+                rr[2 * tid] = rf;
+            }
+            ra[2 * tid + 1] = sA[l];
+            rb[2 * tid + 1] = real(1);
+            rc[2 * tid + 1] = sC[l];
+            rr[2 * tid + 1] = sR[l];
+        }
+        __syncthreads();
+        // parallel cyclic reduction of the 2S interface rows
+        for (int s = 1; s < N2; s <<= 1) {
+            real na[2], nb[2], nc[2], nr[2];
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                int e = tid + u * T;
+                if (e >= N2) continue;
+                real ae = ra[e], be = rb[e], ce = rc[e], re = rr[e];
+                real k1 = real(0), k2 = real(0), am = 0, cm = 0, rm = 0, ap = 0, cp = 0, rp = 0;
+                if (e - s >= 0) {
+                    k1 = ae / rb[e - s];
+                    am = ra[e - s];
+                    cm = rc[e - s];
+                    rm = rr[e - s];
+                }
+                if (e + s < N2) {
+                    k2 = ce / rb[e + s];
+                    ap = ra[e + s];
+                    cp = rc[e + s];
+                    rp = rr[e + s];
+                }
+                na[u] = -am * k1;
+                nc[u] = -cp * k2;
+                nb[u] = be - cm * k1 - ap * k2;
+                nr[u] = re - rm * k1 - rp * k2;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                int e = tid + u * T;
+                if (e >= N2) continue;
+                ra[e] = na[u];
+                rb[e] = nb[u];
+                rc[e] = nc[u];
+                rr[e] = nr[u];
+            }
+            __syncthreads();
+        }
+        if (act) {
+            real xf = rr[2 * tid] / rb[2 * tid], xl = rr[2 * tid + 1] / rb[2 * tid + 1];
+            for (int k = f + 1; k < l; k++) sR[k] = sR[k] - sA[k] * xf - sC[k] * xl;
+            sR[f] = xf;
+            sR[l] = xl;
+        }
+        __syncthreads();
+        }
+        // epilogue: sponge (Eq. 30) on the last stage, zero discharge where dry
+        const uint32_t *mw = A.mask + (size_t)line * A.nwords;
+        const real *bs = A.base + (size_t)line * A.pitch;
+        real *out = A.sol + (size_t)line * A.pitch;
+        for (int k = tid; k < n; k += T) {
+            real v = bs[k] + sR[k];
+            if (A.final_stage) {
+                int i = A.dir == 0 ? k : line, j = A.dir == 0 ? line : k;
+                v *= sponge_gamma<real>(A.bnd, G, i, j);
+            }
+            if ((mw[k >> 5] >> (k & 31)) & 1u) v = real(0);
+            out[k] = v;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- launchers
+
+static dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+template <typename real>
+cudaError_t launch_corners(const Geo &g, const real *z, real *Bc, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_corners<real><<<grid2(g.nx + 3, g.ny + 3, b), b, 0, st>>>(g, z, Bc);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_static_cells(const Geo &g, const Phys &p, const real *Bc, real *d_r, real *d_c,
+                                cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_static_cells<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, p, Bc, d_r, d_c);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_set_state(const Geo &g, const Phys &p, const real *Bc, const real *w_in,
+                             const real *P_in, const real *Q_in, real *w, real *P, real *Qc, int rest,
+                             cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_set_state<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, p, Bc, w_in, P_in, Q_in, w, P, Qc, rest);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_clamp_state(const Geo &g, const Phys &p, const real *Bc, real *w, real *P, real *Qc,
+                               cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_clamp_state<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, p, Bc, w, P, Qc);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_get_state(const Geo &g, const real *w, const real *P, const real *Qc, real *w_out,
+                             real *P_out, real *Q_out, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_get_state<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, w, P, Qc, w_out, P_out, Q_out);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_get_field(const Geo &g, const Phys &p, int which, const real *Bc, const real *d_r,
+                             const real *U, const real *Vc, real *out, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_get_field<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, p, which, Bc, d_r, U, Vc, out);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_add_solitary(const Geo &g, const Phys &p, const real *Bc, real *w, real *P, real *Qc,
+                                double H, double ct, double st_, double x0, double y0, double ks,
+                                double cs, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_add_solitary<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, p, Bc, w, P, Qc, H, ct, st_, x0, y0, ks, cs);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_gauges(const Geo &g, const Phys &p, const real *w, const int32_t *ij, int n, real *slot,
+                          cudaStream_t st)
+{
+    k_gauges<real><<<(n + 127) / 128, 128, 0, st>>>(g, p, w, ij, n, slot);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, const real *Qc,
+                                unsigned long long *first_bad, cudaStream_t st)
+{
+    k_check_finite<real><<<304, 256, 0, st>>>(g, w, P, Qc, first_bad);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
+{
+    static bool configured = false;
+    const size_t smem = sizeof(StencilSmem<real>);
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((a.geo.nx + kTile - 1) / kTile, (a.geo.ny + kTile - 1) / kTile);
+    k_stencil<real><<<grid, kStencilThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+int line_segments(int n, int real_bytes)
+{
+    // about 16 rows per segment (32 for long FP64 lines, to fit shared memory),
+    // at least 2 rows per segment, at most 1024 segments
+    int m = (real_bytes == 8 && n > 4096) ? 32 : 16;
+    int S = (n + m - 1) / m;
+    if (S > n / 2) S = n / 2;
+    if (S > 1024) S = 1024;
+    if (S < 1) S = 1;
+    return S;
+}
+
+template <typename real>
+size_t line_smem_bytes(int n, int nseg)
+{
+    return sizeof(real) * ((size_t)3 * n + (size_t)8 * nseg);
+}
+
+template <typename real>
+cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st)
+{
+    static int configured_bytes = 0;
+    const size_t smem = line_smem_bytes<real>(a.n, a.nseg);
+    if ((int)smem > configured_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_lines<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_bytes = (int)smem;
+    }
+    int threads = round_up(a.nseg, 32);
+    if (threads < 64) threads = 64;
+    k_lines<real><<<a.nlines, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define CEL_INSTANTIATE(real)                                                                           \
+    template cudaError_t launch_corners<real>(const Geo &, const real *, real *, cudaStream_t);           \
+    template cudaError_t launch_static_cells<real>(const Geo &, const Phys &, const real *, real *,      \
+                                                   real *, cudaStream_t);                               \
+    template cudaError_t launch_set_state<real>(const Geo &, const Phys &, const real *, const real *,   \
+                                                const real *, const real *, real *, real *, real *, int, \
+                                                cudaStream_t);                                          \
+    template cudaError_t launch_clamp_state<real>(const Geo &, const Phys &, const real *, real *, real *, \
+                                                  real *, cudaStream_t);                                \
+    template cudaError_t launch_get_state<real>(const Geo &, const real *, const real *, const real *,   \
+                                                real *, real *, real *, cudaStream_t);                  \
+    template cudaError_t launch_get_field<real>(const Geo &, const Phys &, int, const real *,            \
+                                                const real *, const real *, const real *, real *,       \
+                                                cudaStream_t);                                          \
+    template cudaError_t launch_add_solitary<real>(const Geo &, const Phys &, const real *, real *,      \
+                                                   real *, real *, double, double, double, double,      \
+                                                   double, double, double, cudaStream_t);               \
+    template cudaError_t launch_gauges<real>(const Geo &, const Phys &, const real *, const int32_t *,   \
+                                             int, real *, cudaStream_t);                                \
+    template cudaError_t launch_check_finite<real>(const Geo &, const real *, const real *, const real *, \
+                                                   unsigned long long *, cudaStream_t);                 \
+    template cudaError_t launch_stencil<real>(const StencilArgs<real> &, cudaStream_t);                  \
+    template cudaError_t launch_lines<real>(const LineArgs<real> &, cudaStream_t);                       \
+    template size_t line_smem_bytes<real>(int, int);
+
+CEL_INSTANTIATE(float)
+CEL_INSTANTIATE(double)
+
+}  // namespace cel

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every entry point the header
+declares (no compute calls: no GPU here).  Host-only calls are exercised."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1611_05984_gb300 import build as cbuild
+from paper_1611_05984_gb300 import celeris
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "celeris_gb.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cel_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    try:
+        path = cbuild.build()
+    except (RuntimeError, FileNotFoundError) as e:   # no nvcc on this machine
+        pytest.skip(f"cannot build the CUDA library here: {e}")
+    return ctypes.CDLL(path)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), f"missing export {n}"
+    assert sorted(celeris.EXPORTS) == names
+
+
+def test_workspace_bytes_and_validation():
+    L = celeris.load()
+    g = celeris.CelGrid(2048, 2048, 1.0, 1.0, 4)
+    p = celeris.CelParams(0, 9.81, 1 / 15, 1.3, 5e-12, 0.01, 1, 0.0, 2, 0.015)
+    nb = ctypes.c_size_t()
+    assert L.cel_workspace_bytes(ctypes.byref(g), ctypes.byref(p), ctypes.byref(nb)) == 0
+    # 24 row-major fields (w and P twice, dU*, d, AB3 and AM4 carries), 4
+    # column-major fields (Q twice, dV*, d) and the bed corners, each 2048^2
+    # floats, plus the dry-cell masks
+    assert 29 * 2048 * 2048 * 4 <= nb.value < 30 * 2048 * 2048 * 4
+    p0 = celeris.CelParams(0, 9.81, 1 / 15, 1.3, 5e-12, 0.01, 0, 0.0, 2, 0.015)
+    nb0 = ctypes.c_size_t()
+    assert L.cel_workspace_bytes(ctypes.byref(g), ctypes.byref(p0), ctypes.byref(nb0)) == 0
+    assert nb0.value < nb.value
+    for bad in (celeris.CelGrid(1, 8, 1.0, 1.0, 4), celeris.CelGrid(8, 8, 0.0, 1.0, 4),
+                celeris.CelGrid(8, 8, 1.0, 1.0, 2), celeris.CelGrid(20000, 8, 1.0, 1.0, 4),
+                celeris.CelGrid(9000, 8, 1.0, 1.0, 8)):
+        assert L.cel_workspace_bytes(ctypes.byref(bad), ctypes.byref(p), ctypes.byref(nb)) == 1
+    for badp in (celeris.CelParams(2, 9.81, 1 / 15, 1.3, 5e-12, 0.01, 0, 0.0, 0, 0.0),
+                 celeris.CelParams(0, 9.81, 1 / 15, 1.3, 5e-12, -1.0, 0, 0.0, 0, 0.0),
+                 celeris.CelParams(0, 9.81, 1 / 15, 3.0, 5e-12, 0.01, 0, 0.0, 0, 0.0),
+                 celeris.CelParams(0, 9.81, 1 / 15, 1.3, 5e-12, 0.01, -1, 0.0, 0, 0.0)):
+        assert L.cel_workspace_bytes(ctypes.byref(g), ctypes.byref(badp), ctypes.byref(nb)) == 1
+    assert L.cel_gauge_bytes(4, 10, 4, ctypes.byref(nb)) == 0 and nb.value >= 4 * 10 * 4
+    assert L.cel_status_string(4) == b"non-finite value in the state"
+    assert L.cel_last_error(None) == b""
+
+
+def test_create_rejects_bad_arguments_without_gpu_work():
+    L = celeris.load()
+    g = celeris.CelGrid(64, 64, 1.0, 1.0, 4)
+    p = celeris.CelParams(0, 9.81, 1 / 15, 1.3, 5e-12, 0.01, 0, 0.0, 0, 0.0)
+    h = ctypes.c_void_p()
+    # NULL bed / workspace, misaligned workspace, too-small workspace: all
+    # rejected before any CUDA call is made
+    assert L.cel_create(ctypes.byref(g), ctypes.byref(p), None, 256, 1 << 30, None, ctypes.byref(h)) == 1
+    assert L.cel_create(ctypes.byref(g), ctypes.byref(p), 256, None, 1 << 30, None, ctypes.byref(h)) == 1
+    assert L.cel_create(ctypes.byref(g), ctypes.byref(p), 256, 257, 1 << 30, None, ctypes.byref(h)) == 1
+    assert L.cel_create(ctypes.byref(g), ctypes.byref(p), 256, 512, 16, None, ctypes.byref(h)) == 2
+    assert not h.value

@@ -1,0 +1,196 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: relative L2 of eta = w - w_s at every 100th step and at the end,
+FP64 <= 1e-10 and FP32 <= 1e-4; P and Q are checked with the same bars
+relative to their own norms.  Workloads are the seeded synthetic ones of
+``paper_1611_05984_gb300.scenarios``, at sizes the oracle runs in seconds,
+with ragged tile tails (sizes not multiples of 32).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_05984_gb300 import scenarios as sc
+from tests.helpers import oracle_from, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+
+
+def _solver(s, prec, **kw):
+    from paper_1611_05984_gb300 import celeris
+    dt = torch.float64 if prec == "f64" else torch.float32
+    return celeris.from_scenario(s, dtype=dt, **kw)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+def _lockstep(s, prec, nsteps, every=100, check_pq=True):
+    o = oracle_from(s)
+    g = _solver(s, prec)
+    worst = 0.0
+    done = 0
+    while done < nsteps:
+        n = min(every, nsteps - done)
+        o.step(n)
+        g.step(n)
+        done += n
+        wo, Po, Qo = o.state()
+        wg, Pg, Qg = (_np(a) for a in g.state())
+        e = rel_l2(wg - s.ws, wo - s.ws)
+        worst = max(worst, e)
+        assert e <= TOL[prec], f"eta rel-L2 {e:.3e} at step {done}"
+        if check_pq:
+            for a, b, name in ((Pg, Po, "P"), (Qg, Qo, "Q")):
+                if np.linalg.norm(b) > 1e-12:
+                    eq = rel_l2(a, b)
+                    assert eq <= 10 * TOL[prec], f"{name} rel-L2 {eq:.3e} at step {done}"
+    return worst, o, g
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_static_fields(prec):
+    s = sc.beach(nx=200, ny=150, sponge=20)
+    o = oracle_from(s)
+    g = _solver(s, prec)
+    for name in ("Bbar", "d"):
+        a, b = _np(g.field(name)), o.field(name)
+        if prec == "f64":
+            assert np.array_equal(a, b), name      # same sums in the same order
+        else:
+            assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_set_state_clamps_like_oracle(prec):
+    s = sc.beach(nx=100, ny=70, sponge=10)
+    o = oracle_from(s)
+    g = _solver(s, prec)
+    for a, b in zip(g.state(), o.state()):
+        np.testing.assert_allclose(_np(a), b, rtol=1e-6 if prec == "f32" else 0, atol=1e-30)
+
+
+@pytest.mark.parametrize("K", [0, 2])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_soliton_channel(prec, K):
+    """Solitary wave on the flat 1 m channel, 256 x 32, walls, 1000 steps."""
+    s = sc.soliton_channel(K=K)
+    worst, o, g = _lockstep(s, prec, 1000, check_pq=True)
+    w, P, Q = (_np(a) for a in g.state())
+    assert np.max(np.abs(Q)) == 0.0                 # stays y-uniform
+    assert np.max(np.abs(w - w[0:1])) == 0.0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_soliton_channel_ragged(prec):
+    s = sc.soliton_channel(nx=250, ny=30, K=0, x0=5.0)
+    _lockstep(s, prec, 600)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_beach_crop(prec):
+    """Beach and shoals (ragged 200 x 150): sine maker W, sponges N/S, wall E,
+    Manning friction, moving shoreline, one AM4 iteration, 1000 steps."""
+    s = sc.beach(nx=200, ny=150, sponge=20)
+    _lockstep(s, prec, 1000)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_directional_forcing(prec):
+    """Three oblique sine components on W: corner ghosts, P and Q forcing."""
+    s = sc.beach_directional(nx=160, ny=130, sponge=16, nshoal=3)
+    _lockstep(s, prec, 600)
+
+
+@pytest.mark.parametrize("side", [0, 1, 2, 3])
+def test_sine_on_each_side(side):
+    """A sine maker on each side in turn (others sponge/solid), flat 4 m basin."""
+    nx, ny = 70, 90
+    s = sc.flat_basin(nx, ny, 1.0, 4.0, 0.1 / math.sqrt(9.81 * 4.0), K=1, friction=1, fcoef=0.002)
+    th = {0: 0.2, 1: math.pi - 0.2, 2: math.pi / 2 + 0.3, 3: -math.pi / 2 + 0.1}[side]
+    for k in range(4):
+        s.sides[k] = sc.Side(sc.SPONGE if k != side and k % 2 == 0 else sc.SOLID, 8)
+    s.sides[side] = sc.Side(sc.SINE, 0, ((0.05, 6.0, th, 0.4), (0.02, 9.0, th + 0.3, 1.0)))
+    _lockstep(s, "f64", 400)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_nlsw_dam_break(prec):
+    """NLSW mode (no line solves), dry bed, ragged 2-D grid."""
+    nx, ny = 180, 40
+    x = (np.arange(nx) + 0.5) * 0.05
+    # the front moves at 2 sqrt(g h0): Courant 0.05 on sqrt(g h0) keeps the 2-D
+    # front inside AB3's stability interval
+    s = sc.flat_basin(nx, ny, 0.05, 0.0, 0.05 * 0.05 / math.sqrt(9.81), model=1)
+    s.z = np.zeros((ny, nx))
+    w0 = np.tile(np.where(x < 3.0, 1.0, 0.0), (ny, 1))
+    w0[: ny // 3] *= 0.7
+    s.w0 = w0
+    _lockstep(s, prec, 500)
+
+
+def test_dispersive_2d_mode_fp64():
+    """Oblique standing mode on a flat bed: exercises F*, G*, eta_xyy."""
+    n, d = 48, 1.0
+    kx = ky = 2 * math.pi / n
+    X, Y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+    s = sc.flat_basin(n, n, 1.0, d, 0.1 / math.sqrt(9.81 * d), K=1)
+    s.w0 = 1e-3 * np.cos(kx * X) * np.cos(ky * Y)
+    _lockstep(s, "f64", 500)
+
+
+def test_checkpoint_resume_bitexact():
+    s = sc.beach(nx=120, ny=100, sponge=12)
+    a = _solver(s, "f32")
+    a.step(150)
+    ck = a.checkpoint()
+    a.step(150)
+    ref = [t.clone() for t in a.state()]
+    b = _solver(s, "f32")
+    b.restore(ck)
+    assert b.time()[1] == 150
+    b.step(150)
+    for x, y in zip(b.state(), ref):
+        assert torch.equal(x, y)
+
+
+def test_gauges_match_oracle():
+    s = sc.soliton_channel(K=0)
+    o = oracle_from(s)
+    g = _solver(s, "f64")
+    ij = [(10, 3), (128, 16), (255, 31)]
+    o.set_gauges(ij, 7, 5)
+    g.set_gauges(ij, 7, 5)
+    o.step(60)
+    g.step(60)
+    ro, rg = o.read_gauges(10), g.read_gauges(10)
+    assert rg.shape == ro.shape == (5, 3)
+    np.testing.assert_allclose(rg, ro, rtol=0, atol=1e-12)
+    assert g.read_gauges(10).shape[0] == 0
+
+
+def test_check_finite_and_launch_count():
+    s = sc.soliton_channel(K=2)
+    g = _solver(s, "f32")
+    assert g.check_finite()
+    g.step(3)           # two Euler steps + one AB3 step with 2 AM4 stages
+    assert g.last_launch_count() == 3 * (1 + 1 + 3)
+    w, P, Q = g.state()
+    P[5, 7] = float("nan")          # (a NaN in w would be clamped to the bed)
+    g.set_state(w, P, Q)
+    assert not g.check_finite()
+
+
+def test_solitary_rejected_on_dry_crest():
+    from paper_1611_05984_gb300 import celeris
+    z = np.full((40, 64), -1.0)
+    z[:, 40:] = 1.0
+    g = celeris.Solver(z, 1.0, 1.0, 0.01, dtype=torch.float64)
+    with pytest.raises(celeris.CelerisError):
+        g.add_solitary(0.1, 0.0, 50.0, 20.0)
+    g.add_solitary(0.1, 0.0, 10.0, 20.0)
