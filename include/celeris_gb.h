@@ -179,6 +179,46 @@ cel_status cel_profile_enable(cel_solver *s, int32_t capacity);
 cel_status cel_profile_read(cel_solver *s, double ms[3], int64_t count[3]);
 cel_status cel_profile_disable(cel_solver *s);
 
+/* Fixed-scratch variant of the step, for callers that cannot allocate device
+ * memory.  Some callers run inside a host application that owns the GPU's
+ * memory (a rendering or visualisation engine with its own pool, where a
+ * stray cudaMalloc is forbidden or breaks the engine's accounting); some run
+ * real-time loops that must not allocate after start-up, because cudaMalloc
+ * and cudaFree can synchronise the device and stall a frame; some are thin
+ * bindings that can hand over a stream and a few existing buffers but have no
+ * way to allocate or free device memory.  They cannot provide the workspace
+ * that cel_create needs.  This call needs none: it keeps all its scratch (the
+ * AB3 and AM4 carries, the increments of U* and V*, bed corners, depths and
+ * dry-cell masks)
+ * in one fixed array of CEL_NOALLOC_SCRATCH_BYTES that the library defines in
+ * device memory; every GPU that loads the library holds that array until the
+ * process exits.  The paper has no counterpart to this entry point.
+ *
+ * It advances the state (w_in, P_in, Q_in: [ny][nx] real, device) by nsteps
+ * steps exactly as cel_create + cel_set_boundary + cel_set_state + cel_step
+ * would, starting at time first_step * dt with a fresh AB3 history (the first
+ * two steps are Euler), and writes the result to w_out, P_out, Q_out ([ny][nx]
+ * real, device; may alias the inputs).  bcs: the four sides (CEL_WEST..
+ * CEL_NORTH), or NULL for solid walls.  Asynchronous on cuda_stream.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  A grid whose
+ * scratch would exceed CEL_NOALLOC_SCRATCH_BYTES is rejected with
+ * CEL_ERR_WORKSPACE_TOO_SMALL (about 512 x 512 cells in FP32 with
+ * corrector_iters >= 1, 256 x 256 in FP64); bad arguments give
+ * CEL_ERR_INVALID_ARG.  A one-line reason is copied into msg (msg_len bytes,
+ * may be NULL).  The first call on each device looks up the array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each call clears what must
+ * start at zero, so calls that overlap on the GPU (on different streams, or
+ * from different threads) race and give wrong results: serialise them. */
+#define CEL_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params *params,
+                               const cel_bc *bcs, const void *z_dev,
+                               const void *w_in, const void *P_in,
+                               const void *Q_in, void *w_out, void *P_out,
+                               void *Q_out, int32_t nsteps, int64_t first_step,
+                               void *cuda_stream, char *msg, size_t msg_len);
+
 const char *cel_status_string(cel_status st);
 const char *cel_last_error(const cel_solver *s);  /* "" if none; never NULL */
 /* Release the handle (not the caller's memory).  Does not synchronise. */

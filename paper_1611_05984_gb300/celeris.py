@@ -32,7 +32,7 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
            "cel_load_checkpoint", "cel_last_launch_count", "cel_profile_enable",
-           "cel_profile_read", "cel_profile_disable", "cel_status_string",
+           "cel_profile_read", "cel_profile_disable", "cel_advance_noalloc", "cel_status_string",
            "cel_last_error", "cel_destroy"]
 
 
@@ -99,6 +99,9 @@ def load(build_if_missing: bool = True):
         L.cel_profile_enable.argtypes = [vp, i32]
         L.cel_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
         L.cel_profile_disable.argtypes = [vp]
+        L.cel_advance_noalloc.argtypes = [ctypes.POINTER(CelGrid), ctypes.POINTER(CelParams),
+                                          ctypes.POINTER(CelBC), vp, vp, vp, vp, vp, vp, vp, i32,
+                                          i64, vp, ctypes.c_char_p, sz]
         L.cel_status_string.restype = ctypes.c_char_p
         L.cel_status_string.argtypes = [ctypes.c_int]
         L.cel_last_error.restype = ctypes.c_char_p

@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 
 using namespace cel;
@@ -750,4 +751,121 @@ cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches)
     return CEL_OK;
 }
 
+// ------------------------------------------------- fixed-scratch variant
+
 }  // extern "C"
+
+namespace {
+
+// The scratch of cel_advance_noalloc: one array in device memory, defined
+// here so that the library never has to allocate it.  Host code must not use
+// the name as an address (it is a host-side stand-in); the device address is
+// looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CEL_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices];
+std::mutex g_noalloc_mutex;
+
+void put_msg(char *msg, size_t len, const std::string &text)
+{
+    if (!msg || len == 0) return;
+    size_t n = text.size() < len - 1 ? text.size() : len - 1;
+    memcpy(msg, text.data(), n);
+    msg[n] = 0;
+}
+
+}  // namespace
+
+extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params *params, const cel_bc *bcs,
+                                          const void *z_dev, const void *w_in, const void *P_in,
+                                          const void *Q_in, void *w_out, void *P_out, void *Q_out,
+                                          int32_t nsteps, int64_t first_step, void *cuda_stream, char *msg,
+                                          size_t msg_len)
+{
+    put_msg(msg, msg_len, "");
+    if (!grid_ok(grid) || !params_ok(params) || !z_dev || !w_in || !P_in || !Q_in || !w_out || !P_out ||
+        !Q_out || nsteps < 0 || first_step < 0) {
+        put_msg(msg, msg_len, "invalid grid, parameters, pointers or step counts");
+        return CEL_ERR_INVALID_ARG;
+    }
+    Geo G = make_geo(*grid);
+    Layout L = make_layout(G, grid->real_bytes, params->corrector_iters);
+    if (L.total > CEL_NOALLOC_SCRATCH_BYTES) {
+        char buf[200];
+        snprintf(buf, sizeof(buf), "this grid needs %zu bytes of scratch; the fixed scratch holds %zu bytes",
+                 L.total, (size_t)CEL_NOALLOC_SCRATCH_BYTES);
+        put_msg(msg, msg_len, buf);
+        return CEL_ERR_WORKSPACE_TOO_SMALL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        put_msg(msg, msg_len, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        return CEL_ERR_CUDA;
+    }
+    void *scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                put_msg(msg, msg_len, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+                return CEL_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // a handle on the stack, pointing at the fixed scratch; set up as
+    // cel_create does (the scratch is cleared, so nothing of an earlier call
+    // is read)
+    cel_solver s;
+    s.grid = *grid;
+    s.params = *params;
+    s.geo = G;
+    s.lay = L;
+    s.es = grid->real_bytes;
+    s.stream = (cudaStream_t)cuda_stream;
+    s.ws = (unsigned char *)scratch;
+    s.phy.model = params->model;
+    s.phy.friction = params->friction;
+    s.phy.K = params->corrector_iters;
+    s.phy.g = params->g;
+    s.phy.Bd = params->Bdisp;
+    s.phy.theta = params->theta;
+    s.phy.eps = params->eps;
+    s.phy.dt = params->dt;
+    s.phy.ws = params->still_water;
+    s.phy.fcoef = params->fric_coef;
+    memset(&s.bnd, 0, sizeof(s.bnd));
+    for (int k = 0; k < 4; k++) s.bnd.s[k].type = kSolid;
+    s.nseg_x = line_segments(G.nx, s.es);
+    s.nseg_y = line_segments(G.ny, s.es);
+    s.gij = nullptr;
+    s.gring = nullptr;
+    s.ng = s.log_every = s.cap = s.nrec = s.head = 0;
+    s.launches = 0;
+    s.step = first_step;
+    s.nh = 0;
+    s.cur = s.pcur = 0;
+    s.ev_beg = s.ev_end = nullptr;
+    s.ev_kind = nullptr;
+    s.ev_cap = s.ev_used = 0;
+    cel_status st = CEL_OK;
+    if (bcs)
+        for (int side = 0; side < 4 && st == CEL_OK; side++) st = cel_set_boundary(&s, side, &bcs[side]);
+    if (st == CEL_OK) {
+        e = cudaMemsetAsync(scratch, 0, L.total, s.stream);
+        if (e != cudaSuccess) st = cuda_fail(&s, e, "clear scratch");
+    }
+    if (st == CEL_OK) st = s.es == 4 ? derive_static<float>(&s, z_dev) : derive_static<double>(&s, z_dev);
+    if (st == CEL_OK)
+        st = s.es == 4 ? set_state_t<float>(&s, w_in, P_in, Q_in, 0) : set_state_t<double>(&s, w_in, P_in, Q_in, 0);
+    if (st == CEL_OK) st = s.es == 4 ? step_t<float>(&s, nsteps) : step_t<double>(&s, nsteps);
+    if (st == CEL_OK) st = cel_get_state(&s, w_out, P_out, Q_out);
+    if (st != CEL_OK) put_msg(msg, msg_len, s.err);
+    return st;
+}
+
