@@ -25,7 +25,7 @@ int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
 
 struct Layout {
     size_t w[2], P[2], U, dr, a[3], b[3][2], Y[3], q[3], e[3];
-    size_t Qc[2], Vc, dc, Bc, mr, mc, flag;
+    size_t Qc[2], Vc, dc, Bc, mr, mc, ghost, flag;
     size_t total;
     size_t row_bytes, col_bytes;
 };
@@ -81,6 +81,7 @@ Layout make_layout(const Geo &G, int es, int K)
     L.Bc = take((size_t)(G.ny + 3) * G.pc * es);
     L.mr = take((size_t)G.ny * G.nwx * 4);
     L.mc = take((size_t)G.nx * G.nwy * 4);
+    L.ghost = take(ghost_index(2, 0, 0, 0, 0, (G.nx > G.ny ? G.nx : G.ny) + 4) * es);
     L.flag = take(256);
     L.total = cur;
     return L;
@@ -214,16 +215,24 @@ cel_status step_t(cel_solver *s, int nsteps)
     const Layout &L = s->lay;
     const int K = s->params.corrector_iters;
     int64_t launches = 0;
+    const Coef<real> coef = make_coef<real>(s->geo, s->phy, s->bnd);
+    real *ghost = s->at<real>(L.ghost);
     for (int it = 0; it < nsteps; it++) {
         const int kind0 = s->nh == 0 ? kEuler0 : (s->nh == 1 ? kEuler1 : kAB3);
         const int Kn = s->nh >= 2 ? K : 0;
         const double t0 = (double)s->step * s->params.dt, t1 = (double)(s->step + 1) * s->params.dt;
         const int slot = (int)(s->nh & 1);
+        if (coef.sine) {
+            CEL_CUDA(s, launch_ghost_table<real>(s->geo, s->phy, s->bnd, s->at<real>(L.dr), t0, t1, ghost,
+                                                 coef.npos, s->stream), "ghost table");
+            launches += 1;
+        }
         for (int stage = 0; stage <= Kn; stage++) {
             StencilArgs<real> a;
             a.geo = s->geo;
             a.phy = s->phy;
-            a.bnd = s->bnd;
+            a.c = coef;
+            a.ghost = ghost;
             a.Bc = s->at<real>(L.Bc);
             a.w_in = s->at<real>(L.w[(s->cur + stage) & 1]);
             a.w_out = s->at<real>(L.w[(s->cur + stage + 1) & 1]);
@@ -243,7 +252,7 @@ cel_status step_t(cel_solver *s, int nsteps)
             a.kind = stage == 0 ? kind0 : kAM4;
             a.keepK = K > 0;
             a.final_stage = stage == Kn;
-            a.t = stage == 0 ? t0 : t1;
+            a.tsel = stage == 0 ? 0 : 1;
             int pe = prof_begin(s, 0);
             CEL_CUDA(s, launch_stencil<real>(a, s->stream), "stencil");
             prof_end(s, pe);
@@ -251,7 +260,13 @@ cel_status step_t(cel_solver *s, int nsteps)
                 LineArgs<real> l;
                 l.geo = s->geo;
                 l.phy = s->phy;
-                l.bnd = s->bnd;
+                l.c = coef;
+                l.ghost = ghost;
+                const double h = dir == 0 ? s->geo.dx : s->geo.dy;
+                l.rh = real(1.0 / h);
+                l.rh2 = real(1.0 / (h * h));
+                l.hrh = real(0.5 / h);
+                l.srh = real(1.0 / (6.0 * h));
                 l.rhs = s->at<real>(dir == 0 ? L.U : L.Vc);
                 l.d = s->at<real>(dir == 0 ? L.dr : L.dc);
                 l.mask = s->at<uint32_t>(dir == 0 ? L.mr : L.mc);
@@ -265,8 +280,6 @@ cel_status step_t(cel_solver *s, int nsteps)
                 l.nseg = dir == 0 ? s->nseg_x : s->nseg_y;
                 l.final_stage = stage == Kn;
                 l.identity = s->params.model == CEL_NLSW;
-                l.t0 = t0;
-                l.t1 = t1;
                 int pl = prof_begin(s, 1 + dir);
                 CEL_CUDA(s, launch_lines<real>(l, s->stream), dir == 0 ? "x-lines" : "y-lines");
                 prof_end(s, pl);

@@ -58,11 +58,65 @@ struct Bnd {
     Side s[4];           // west, east, south, north
 };
 
+// Real-typed constants of the step, computed once on the host so that the
+// FP32 kernels do no double-precision arithmetic (GB300's FP64 rate is a
+// small fraction of its FP32 rate).
+template <typename real>
+struct Coef {
+    real g, eps, theta, ws, dt, Bd, B3, sixth;
+    real rdx, rdy, hrdx, hrdy, rdx2, rdy2, rdxdy4, rdx3h, rdy3h, rdxdy2h, rdx2dyh;
+    real fric;           // quadratic f, or g n^2 for Manning
+    int spw[4];          // sponge width in cells per side (0: not a sponge)
+    int sine;            // bit s set: side s is a sine maker
+    int npos;            // positions per side in the ghost table
+};
+
+template <typename real>
+inline Coef<real> make_coef(const Geo &G, const Phys &p, const Bnd &b)
+{
+    Coef<real> c;
+    c.g = real(p.g);
+    c.eps = real(p.eps);
+    c.theta = real(p.theta);
+    c.ws = real(p.ws);
+    c.dt = real(p.dt);
+    c.Bd = real(p.Bd);
+    c.B3 = real(p.Bd + 1.0 / 3.0);
+    c.sixth = real(1.0 / 6.0);
+    c.rdx = real(1.0 / G.dx);
+    c.rdy = real(1.0 / G.dy);
+    c.hrdx = real(0.5 / G.dx);
+    c.hrdy = real(0.5 / G.dy);
+    c.rdx2 = real(1.0 / (G.dx * G.dx));
+    c.rdy2 = real(1.0 / (G.dy * G.dy));
+    c.rdxdy4 = real(1.0 / (4.0 * G.dx * G.dy));
+    c.rdx3h = real(1.0 / (2.0 * G.dx * G.dx * G.dx));
+    c.rdy3h = real(1.0 / (2.0 * G.dy * G.dy * G.dy));
+    c.rdxdy2h = real(1.0 / (2.0 * G.dx * G.dy * G.dy));
+    c.rdx2dyh = real(1.0 / (2.0 * G.dx * G.dx * G.dy));
+    c.fric = real(p.friction == kFricManning ? p.g * p.fcoef * p.fcoef : p.fcoef);
+    c.sine = 0;
+    for (int s = 0; s < 4; s++) {
+        c.spw[s] = b.s[s].type == kSponge ? b.s[s].width : 0;
+        if (b.s[s].type == kSine) c.sine |= 1 << s;
+    }
+    c.npos = (G.nx > G.ny ? G.nx : G.ny) + 4;
+    return c;
+}
+
+// Ghost table of the sine-wave makers, one per step: [time t0|t1][side]
+// [layer 0 (adjacent) | 1][w, P, Q][position along the side + 2].
+__host__ __device__ inline size_t ghost_index(int time, int side, int layer, int var, int pos, int npos)
+{
+    return ((((size_t)time * 4 + side) * 2 + layer) * 3 + var) * (size_t)npos + pos;
+}
+
 template <typename real>
 struct StencilArgs {
     Geo geo;
     Phys phy;
-    Bnd bnd;
+    Coef<real> c;
+    const real *ghost;                   // sine-maker ghost table of this step
     const real *Bc;
     const real *w_in, *P_in, *Qc_in;     // state (or AM4 iterate) at time t
     real *w_out, *U_out, *Vc_out;        // w^{n+1}, and the increments of U*, V*
@@ -72,14 +126,15 @@ struct StencilArgs {
     int kind;                            // kEuler0 | kEuler1 | kAB3 | kAM4
     int keepK;                           // maintain the AM4 carries
     int final_stage;                     // last stage of the step: sponge on w
-    double t;                            // time of the state read (ghosts)
+    int tsel;                            // ghost-table time: 0 = t^n, 1 = t^{n+1}
 };
 
 template <typename real>
 struct LineArgs {
     Geo geo;
     Phys phy;
-    Bnd bnd;
+    Coef<real> c;
+    const real *ghost;     // sine-maker ghost table of this step
     const real *rhs;       // increment of U* (x-lines) or V* (y-lines), line-major
     const real *d;         // still-water depth, line-major
     const uint32_t *mask;  // dry bits, line-major words
@@ -90,7 +145,7 @@ struct LineArgs {
     int nseg;              // segments per line (threads doing sweeps)
     int final_stage;       // apply the sponge
     int identity;          // NLSW model: no dispersive solve, P = U*, Q = V*
-    double t0, t1;         // times of the ghost discharge on sine sides
+    real rh, rh2, hrh, srh; // 1/h, 1/h^2, 1/(2h), 1/(6h) along the line
 };
 
 // Launchers (celeris_kernels.cu).  All return cudaGetLastError().
@@ -123,6 +178,9 @@ cudaError_t launch_gauges(const Geo &g, const Phys &p, const real *w, const int3
 template <typename real>
 cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, const real *Qc,
                                 unsigned long long *first_bad, cudaStream_t st);
+template <typename real>
+cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, double t0,
+                               double t1, real *tab, int npos, cudaStream_t st);
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st);
 template <typename real>

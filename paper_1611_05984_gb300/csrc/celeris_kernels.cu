@@ -123,23 +123,24 @@ __device__ inline void sine_ghost(const Side &s, double g, double dadj, double x
     }
 }
 
-// Eq. 30 with D the distance from the absorbing face to the cell centre;
-// the smallest gamma over the sponge sides.
+__device__ __forceinline__ float cospi_r(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_r(double x) { return cospi(x); }
+
+// Eq. 30 with D the distance from the absorbing face to the cell centre and
+// L_s = width cells: a cell idx cells from the side (idx = i for the west) is
+// inside when idx < width, with (L_s - D)/L_s = (2 (width - idx) - 1)/(2 width).
+// The smallest gamma over the sponge sides.
 template <typename real>
-__device__ __forceinline__ real sponge_gamma(const Bnd &b, const Geo &g, int i, int j)
+__device__ __forceinline__ real sponge_gamma(const Coef<real> &c, const Geo &g, int i, int j)
 {
     real gm = real(1);
+    const int idx[4] = {i, g.nx - 1 - i, j, g.ny - 1 - j};
 #pragma unroll
     for (int s = 0; s < 4; s++) {
-        if (b.s[s].type != kSponge || b.s[s].width <= 0) continue;
-        double D = s == 0   ? (i + 0.5) * g.dx
-                   : s == 1 ? (g.nx - i - 0.5) * g.dx
-                   : s == 2 ? (j + 0.5) * g.dy
-                            : (g.ny - j - 0.5) * g.dy;
-        double L = b.s[s].L;
-        if (D < L) {
-            real v = real(0.5) * (real(1) + cos(real(kPi * (L - D) / L)));
-            gm = fmin(gm, v);
+        const int w = c.spw[s];
+        if (idx[s] < w) {
+            real r = real(2 * (w - idx[s]) - 1) / real(2 * w);
+            gm = fmin(gm, real(0.5) * (real(1) + cospi_r(r)));
         }
     }
     return gm;
@@ -307,6 +308,40 @@ __global__ void k_check_finite(Geo g, const real *w, const real *P, const real *
     }
 }
 
+// Sine-maker ghosts (Eq. 25-29, Reading A-B4) for one step, in double: both
+// ghost layers of every sine side at t^n and t^{n+1}.  d is the still-water
+// depth of the adjacent interior cell (clamped along the side for the corner
+// columns of the south / north sides).
+template <typename real>
+__global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r, double t0, double t1,
+                              real *__restrict__ tab, int npos)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    int time = blockIdx.y & 1, layer = (blockIdx.y >> 1) & 1, side = blockIdx.y >> 2;
+    if (pos >= npos || b.s[side].type != kSine) return;
+    double eta = 0.0, Pg = 0.0, Qg = 0.0;
+    int along = pos - 2;
+    double x, y, dadj;
+    if (side < 2) {           // west / east: rows j
+        if (along < 0 || along >= g.ny) return;
+        int gi = side == 0 ? -1 - layer : g.nx + layer;
+        x = (gi + 0.5) * g.dx;
+        y = (along + 0.5) * g.dy;
+        dadj = (double)d_r[(size_t)along * g.px + (side == 0 ? 0 : g.nx - 1)];
+    } else {                  // south / north: columns i, corners included
+        if (along < -2 || along > g.nx + 1) return;
+        int gj = side == 2 ? -1 - layer : g.ny + layer;
+        int ia = along < 0 ? 0 : (along > g.nx - 1 ? g.nx - 1 : along);
+        x = (along + 0.5) * g.dx;
+        y = (gj + 0.5) * g.dy;
+        dadj = (double)d_r[(size_t)(side == 2 ? 0 : g.ny - 1) * g.px + ia];
+    }
+    sine_ghost(b.s[side], p.g, dadj, x, y, time ? t1 : t0, eta, Pg, Qg);
+    tab[ghost_index(time, side, layer, 0, pos, npos)] = real(p.ws + eta);
+    tab[ghost_index(time, side, layer, 1, pos, npos)] = real(Pg);
+    tab[ghost_index(time, side, layer, 2, pos, npos)] = real(Qg);
+}
+
 // ------------------------------------------------------------ the stencil
 
 template <typename real>
@@ -380,8 +415,9 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
     const int nx = G.nx, ny = G.ny;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
     const int tid = threadIdx.x;
-    const real ws = real(A.phy.ws), g = real(A.phy.g), eps = real(A.phy.eps);
-    const real th = real(A.phy.theta);
+    const Coef<real> &C = A.c;
+    const real ws = C.ws, g = C.g, eps = C.eps;
+    const real th = C.theta;
 
     // ---- 1. stage the state tile (+2 halo) and the bed corners
     for (int k = tid; k < kTileIn * kTileIn; k += kStencilThreads) {
@@ -429,16 +465,12 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
             if (tx < 0 || tx >= kTileIn) continue;
             int sx = side == 0 ? kk : nx - 1 - kk;
             int stx = sx - x0 + kHalo;
-            const Side &S = A.bnd.s[side];
             int gi = ty * kStride + tx, si = ty * kStride + stx;
-            if (S.type == kSine) {
-                int ia = side == 0 ? 0 : nx - 1;
-                double dadj = (double)cell_d(ia - x0 + 1, gy - y0 + 1);
-                double eta, Pg, Qg;
-                sine_ghost(S, A.phy.g, dadj, (gx + 0.5) * G.dx, (gy + 0.5) * G.dy, A.t, eta, Pg, Qg);
-                sm.w[gi] = real(A.phy.ws + eta);
-                sm.P[gi] = real(Pg);
-                sm.Q[gi] = real(Qg);
+            if ((C.sine >> side) & 1) {
+                const real *tb = A.ghost + ghost_index(A.tsel, side, kk, 0, gy + 2, C.npos);
+                sm.w[gi] = tb[0];
+                sm.P[gi] = tb[C.npos];
+                sm.Q[gi] = tb[2 * C.npos];
             } else {
                 sm.w[gi] = sm.w[si];
                 sm.P[gi] = -sm.P[si];
@@ -458,16 +490,12 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
             if (ty < 0 || ty >= kTileIn) continue;
             int sy = side == 2 ? kk : ny - 1 - kk;
             int sty = sy - y0 + kHalo;
-            const Side &S = A.bnd.s[side];
             int gi = ty * kStride + tx, si = sty * kStride + tx;
-            if (S.type == kSine) {
-                int ia = min(max(gx, 0), nx - 1), ja = side == 2 ? 0 : ny - 1;
-                double dadj = (double)cell_d(ia - x0 + 1, ja - y0 + 1);
-                double eta, Pg, Qg;
-                sine_ghost(S, A.phy.g, dadj, (gx + 0.5) * G.dx, (gy + 0.5) * G.dy, A.t, eta, Pg, Qg);
-                sm.w[gi] = real(A.phy.ws + eta);
-                sm.P[gi] = real(Pg);
-                sm.Q[gi] = real(Qg);
+            if ((C.sine >> side) & 1) {
+                const real *tb = A.ghost + ghost_index(A.tsel, side, kk, 0, gx + 2, C.npos);
+                sm.w[gi] = tb[0];
+                sm.P[gi] = tb[C.npos];
+                sm.Q[gi] = tb[2 * C.npos];
             } else {
                 sm.w[gi] = sm.w[si];
                 sm.P[gi] = sm.P[si];
@@ -534,14 +562,10 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
     __syncthreads();
 
     // ---- 5. per cell: Eq. 9-13, friction, U*, V*, update
-    const real dt = real(A.phy.dt);
-    const real rdx = real(1.0 / G.dx), rdy = real(1.0 / G.dy);
-    const real rdx2 = real(1.0 / (G.dx * G.dx)), rdy2 = real(1.0 / (G.dy * G.dy));
-    const real rdxdy4 = real(1.0 / (4.0 * G.dx * G.dy));
-    const real rdx3h = real(1.0 / (2.0 * G.dx * G.dx * G.dx)), rdy3h = real(1.0 / (2.0 * G.dy * G.dy * G.dy));
-    const real rdxdy2h = real(1.0 / (2.0 * G.dx * G.dy * G.dy)), rdx2dyh = real(1.0 / (2.0 * G.dx * G.dx * G.dy));
-    const real Bd = real(A.phy.Bd), B3 = real(A.phy.Bd + 1.0 / 3.0);
-    const real sixth = real(1.0 / 6.0);
+    const real dt = C.dt;
+    const real rdx = C.rdx, rdy = C.rdy, rdx2 = C.rdx2, rdy2 = C.rdy2, rdxdy4 = C.rdxdy4;
+    const real rdx3h = C.rdx3h, rdy3h = C.rdy3h, rdxdy2h = C.rdxdy2h, rdx2dyh = C.rdx2dyh;
+    const real Bd = C.Bd, B3 = C.B3, sixth = C.sixth;
     const bool bsnq = A.phy.model == kBsnq;
     const int lane = tid & 31;
     for (int rr = 0; rr < kTile / (kStencilThreads / 32); rr++) {
@@ -563,8 +587,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
                   g * hb * (ByN - ByS) * rdy;
         if (A.phy.friction != kFricNone) {   // Eq. 31-32 with the Eq. 14 device
             real hinv = desing(fmax(hb, real(0)), eps);
-            real fc = A.phy.friction == kFricManning ? real(A.phy.g * A.phy.fcoef * A.phy.fcoef) * cbrt(hinv)
-                                                     : real(A.phy.fcoef);
+            real fc = A.phy.friction == kFricManning ? C.fric * cbrt(hinv) : C.fric;
             real mag = sqrt(P0 * P0 + Q0 * Q0);
             F -= fc * P0 * mag * hinv * hinv;
             Gq -= fc * Q0 * mag * hinv * hinv;
@@ -573,8 +596,8 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
         const int od = (cy + 1) * kDStride + cx + 1;
         const real dd = sm.d[od];
         if (bsnq) {
-            const real ddx = (sm.d[od + 1] - sm.d[od - 1]) * (real(0.5) * rdx);
-            const real ddy = (sm.d[od + kDStride] - sm.d[od - kDStride]) * (real(0.5) * rdy);
+            const real ddx = (sm.d[od + 1] - sm.d[od - 1]) * C.hrdx;
+            const real ddy = (sm.d[od + kDStride] - sm.d[od - kDStride]) * C.hrdy;
             const real *W = sm.w + o;
             const int S1 = kStride, S2 = 2 * kStride;
             real e00 = W[0] - ws;
@@ -591,9 +614,9 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
             F += Bd * g * dd * dd * dd * (exxx + exyy) + Bd * g * dd * dd * (ddx * (real(2) * exx + eyy) + ddy * exy);
             Gq += Bd * g * dd * dd * dd * (eyyy + exxy) + Bd * g * dd * dd * (ddy * (real(2) * eyy + exx) + ddx * exy);
             const real *Pt = sm.P + o, *Qt = sm.Q + o;
-            real Qx = (Qt[1] - Qt[-1]) * (real(0.5) * rdx), Qy = (Qt[S1] - Qt[-S1]) * (real(0.5) * rdy);
+            real Qx = (Qt[1] - Qt[-1]) * C.hrdx, Qy = (Qt[S1] - Qt[-S1]) * C.hrdy;
             real Qxy = (Qt[S1 + 1] - Qt[-S1 + 1] - Qt[S1 - 1] + Qt[-S1 - 1]) * rdxdy4;
-            real Px = (Pt[1] - Pt[-1]) * (real(0.5) * rdx), Py = (Pt[S1] - Pt[-S1]) * (real(0.5) * rdy);
+            real Px = (Pt[1] - Pt[-1]) * C.hrdx, Py = (Pt[S1] - Pt[-S1]) * C.hrdy;
             real Pxy = (Pt[S1 + 1] - Pt[-S1 + 1] - Pt[S1 - 1] + Pt[-S1 - 1]) * rdxdy4;
             Fs = dd * ddx * Qy * sixth + dd * ddy * Qx * sixth + B3 * dd * dd * Qxy;
             Gs = dd * ddy * Px * sixth + dd * ddx * Py * sixth + B3 * dd * dd * Pxy;
@@ -607,7 +630,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
             dV = advance(A.kind, A.keepK, real(0), Gq, Gs, dt, kr, A.a[2], A.b[2], A.Y[2], A.q[2], A.e[2]);
             if (w1 < Bb) w1 = Bb;   // Reading A-D1
             if (A.final_stage) {
-                real gam = sponge_gamma<real>(A.bnd, G, i, j);
+                real gam = sponge_gamma<real>(C, G, i, j);
                 if (gam < real(1) && dd > real(0)) w1 = ws + gam * (w1 - ws);
             }
             A.w_out[kr] = w1;
@@ -630,27 +653,14 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
 
 // ------------------------------------------------------------ line solves
 
-// Change of the sine-maker ghost discharge (P for x-lines, Q for y-lines)
-// from t0 to t1: the ghost term of the boundary row of Eq. 21/22 written for
-// the increment P^{n+1} - P^n.
-template <typename real>
-__device__ inline double ghost_increment(const Side &S, const LineArgs<real> &A, double dadj, double x,
-                                         double y)
-{
-    double eta, P1, Q1, P0, Q0;
-    sine_ghost(S, A.phy.g, dadj, x, y, A.t1, eta, P1, Q1);
-    sine_ghost(S, A.phy.g, dadj, x, y, A.t0, eta, P0, Q0);
-    return A.dir == 0 ? P1 - P0 : Q1 - Q0;
-}
-
 // Eq. 23 coefficients of line element k.
 template <typename real>
-__device__ __forceinline__ void coef23(real B3, real rh, real rh2, real dd, real dm, real dp,
+__device__ __forceinline__ void coef23(real B3, real hrh, real srh, real rh2, real dd, real dm, real dp,
                                        real &a, real &b, real &c)
 {
-    real dda = (dp - dm) * (real(0.5) * rh);
+    real dda = (dp - dm) * hrh;
     real r = B3 * dd * dd * rh2;
-    real s = dd * dda * (real(1.0 / 6.0) * rh);
+    real s = dd * dda * srh;
     a = s - r;
     b = real(1) + real(2) * r;
     c = -s - r;
@@ -667,11 +677,11 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
     real *ra = sR + n, *rb = ra + N2, *rc = rb + N2, *rr = rc + N2;
     const int tid = threadIdx.x, T = blockDim.x;
     const Geo &G = A.geo;
-    const double h = A.dir == 0 ? G.dx : G.dy;
-    const real rh = real(1.0 / h), rh2 = real(1.0 / (h * h));
-    const real B3 = real(A.phy.Bd + 1.0 / 3.0);
-    const Side &lo = A.bnd.s[A.dir == 0 ? 0 : 2];
-    const Side &hi = A.bnd.s[A.dir == 0 ? 1 : 3];
+    const real rh2 = A.rh2, hrh = A.hrh, srh = A.srh;
+    const real B3 = A.c.B3;
+    const int lo_side = A.dir == 0 ? 0 : 2, hi_side = A.dir == 0 ? 1 : 3;
+    const bool lo_sine = (A.c.sine >> lo_side) & 1, hi_sine = (A.c.sine >> hi_side) & 1;
+    const int gvar = A.dir == 0 ? 1 : 2;   // ghost discharge: P on x-lines, Q on y-lines
 
     for (int line = blockIdx.x; line < A.nlines; line += gridDim.x) {
         const real *rhs = A.rhs + (size_t)line * A.pitch;
@@ -699,23 +709,23 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
             for (int k = f; k <= l; k++) {
                 real dnext = k < l ? sA[k + 1] : dp;
                 real ak, bk, ck;
-                coef23(B3, rh, rh2, dcur, dprev, dnext, ak, bk, ck);
+                coef23(B3, hrh, srh, rh2, dcur, dprev, dnext, ak, bk, ck);
                 real rk = sR[k];
                 if (k == 0) {   // Reading A-B2: mirror, or the known ghost increment
-                    if (lo.type == kSine) {
-                        double x = A.dir == 0 ? -0.5 * G.dx : (line + 0.5) * G.dx;
-                        double y = A.dir == 0 ? (line + 0.5) * G.dy : -0.5 * G.dy;
-                        rk -= ak * real(ghost_increment(lo, A, (double)dcur, x, y));
+                    if (lo_sine) {
+                        const real *tb = A.ghost + ghost_index(0, lo_side, 0, gvar, line + 2, A.c.npos);
+                        const real *t1 = A.ghost + ghost_index(1, lo_side, 0, gvar, line + 2, A.c.npos);
+                        rk -= ak * (t1[0] - tb[0]);
                     } else {
                         bk -= ak;
                     }
                     ak = real(0);
                 }
                 if (k == n - 1) {
-                    if (hi.type == kSine) {
-                        double x = A.dir == 0 ? (G.nx + 0.5) * G.dx : (line + 0.5) * G.dx;
-                        double y = A.dir == 0 ? (line + 0.5) * G.dy : (G.ny + 0.5) * G.dy;
-                        rk -= ck * real(ghost_increment(hi, A, (double)dcur, x, y));
+                    if (hi_sine) {
+                        const real *tb = A.ghost + ghost_index(0, hi_side, 0, gvar, line + 2, A.c.npos);
+                        const real *t1 = A.ghost + ghost_index(1, hi_side, 0, gvar, line + 2, A.c.npos);
+                        rk -= ck * (t1[0] - tb[0]);
                     } else {
                         bk -= ck;
                     }
@@ -832,7 +842,7 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
             real v = bs[k] + sR[k];
             if (A.final_stage) {
                 int i = A.dir == 0 ? k : line, j = A.dir == 0 ? line : k;
-                v *= sponge_gamma<real>(A.bnd, G, i, j);
+                v *= sponge_gamma<real>(A.c, G, i, j);
             }
             if ((mw[k >> 5] >> (k & 31)) & 1u) v = real(0);
             out[k] = v;
@@ -928,6 +938,14 @@ cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, cons
 }
 
 template <typename real>
+cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, double t0, double t1,
+                               real *tab, int npos, cudaStream_t st)
+{
+    k_ghost_table<real><<<dim3((npos + 127) / 128, 16), 128, 0, st>>>(g, p, b, d_r, t0, t1, tab, npos);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
 {
     static bool configured = false;
@@ -999,6 +1017,8 @@ cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st)
                                              int, real *, cudaStream_t);                                \
     template cudaError_t launch_check_finite<real>(const Geo &, const real *, const real *, const real *, \
                                                    unsigned long long *, cudaStream_t);                 \
+    template cudaError_t launch_ghost_table<real>(const Geo &, const Phys &, const Bnd &, const real *,   \
+                                                  double, double, real *, int, cudaStream_t);           \
     template cudaError_t launch_stencil<real>(const StencilArgs<real> &, cudaStream_t);                  \
     template cudaError_t launch_lines<real>(const LineArgs<real> &, cudaStream_t);                       \
     template size_t line_smem_bytes<real>(int, int);
