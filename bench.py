@@ -28,12 +28,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic values moved per cell by one launch of each kernel (see the
-# kernel notes): the stencil predictor of an AB3 step with the AM4 carries
-# reads w, P, Q, bed corners and 12 carries and writes w, U*, V* and 15
-# carries; the corrector stencil reads w, P, Q, corners, 3 bases and writes
-# w, U*, V*; a line solve reads its right side and depth and writes P or Q.
-VALUES = {"stencil_pred_k": 16 + 18, "stencil_pred_0": 10 + 9, "stencil_corr": 7 + 3, "lines": 3}
+# Algorithmic values moved per cell by one launch of each kernel: the stencil
+# predictor of an AB3 step with the AM4 carries reads w, P, Q, bed corners
+# and 12 carries and writes w, dU*, dV* and 15 carries; the corrector stencil
+# reads w, P, Q, corners, 3 bases and writes w, dU*, dV*; a line solve reads
+# its right side, depth and P^n (or Q^n) and writes P^{n+1} (or Q^{n+1}).
+VALUES = {"stencil_pred_k": 16 + 18, "stencil_pred_0": 10 + 9, "stencil_corr": 7 + 3, "lines": 4}
 
 
 def parse():

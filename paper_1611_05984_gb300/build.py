@@ -15,7 +15,10 @@ LIB = os.path.join(OUT_DIR, "libceleris_gb.so")
 SOURCES = ["celeris_kernels.cu", "celeris_api.cu"]
 HEADERS = [os.path.join(CSRC, "celeris_internal.cuh"), os.path.join(INCLUDE, "celeris_gb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# FP32 division and square root use the fast reciprocal / reciprocal-square-root
+# paths (about 2 ulp); FP64 arithmetic is unaffected by these flags.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+         "-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 _lock = threading.Lock()
 
 

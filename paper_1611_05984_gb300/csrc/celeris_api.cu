@@ -278,6 +278,8 @@ cel_status step_t(cel_solver *s, int nsteps)
                 l.pitch = dir == 0 ? s->geo.px : s->geo.py;
                 l.nwords = dir == 0 ? s->geo.nwx : s->geo.nwy;
                 l.nseg = dir == 0 ? s->nseg_x : s->nseg_y;
+                l.mshift = line_seg_shift(l.n, s->es);
+                l.sp = line_seg_stride(l.nseg);
                 l.final_stage = stage == Kn;
                 l.identity = s->params.model == CEL_NLSW;
                 int pl = prof_begin(s, 1 + dir);

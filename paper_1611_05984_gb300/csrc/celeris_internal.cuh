@@ -143,6 +143,8 @@ struct LineArgs {
     int dir;               // 0: x-lines (rows), 1: y-lines (columns)
     int n, nlines, pitch, nwords;
     int nseg;              // segments per line (threads doing sweeps)
+    int mshift;            // log2 of the rows per segment (lines padded to nseg << mshift)
+    int sp;                // odd shared-memory stride between rows of the segments
     int final_stage;       // apply the sponge
     int identity;          // NLSW model: no dispersive solve, P = U*, Q = V*
     real rh, rh2, hrh, srh; // 1/h, 1/h^2, 1/(2h), 1/(6h) along the line
@@ -188,5 +190,7 @@ cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st);
 template <typename real>
 size_t line_smem_bytes(int n, int nseg);
 int line_segments(int n, int real_bytes);
+int line_seg_shift(int n, int real_bytes);
+int line_seg_stride(int nseg);
 
 }  // namespace cel

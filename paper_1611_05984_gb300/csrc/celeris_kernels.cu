@@ -42,7 +42,7 @@ __device__ __forceinline__ real desing(real h, real eps)
 {
     real h2 = h * h;
     real h4 = h2 * h2;
-    return real(1.4142135623730951) * h / sqrt(h4 + fmax(h4, eps));
+    return real(1.4142135623730951) * h * rsqrt(h4 + fmax(h4, eps));
 }
 
 // KP07 step 1: generalized minmod of the three one-sided / central slopes.
@@ -510,53 +510,72 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
     }
     __syncthreads();
 
-    // ---- 4. fluxes through every face of the tile, each computed once
-    for (int k = tid; k < 2 * kTile * (kTile + 1); k += kStencilThreads) {
-        real H[3];
-        if (k < kTile * (kTile + 1)) {   // x-face fx (x = (x0+fx) dx) of row r
-            int r = k / (kTile + 1), fx = k % (kTile + 1);
-            int ty = r + kHalo, txL = fx + 1;   // left cell's tile column
-            const real *cb = sm.Bc + (r + 1) * kCornerStride;
-            real B0 = real(0.5) * (cb[fx] + cb[fx + kCornerStride]);
-            real B1 = real(0.5) * (cb[fx + 1] + cb[fx + 1 + kCornerStride]);
-            real B2 = real(0.5) * (cb[fx + 2] + cb[fx + 2 + kCornerStride]);
-            const int o = ty * kStride + txL;
-            real wL[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
-            real PL[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
-            real QL[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
-            real wR[3] = {sm.w[o], sm.w[o + 1], sm.w[o + 2]};
-            real PR[3] = {sm.P[o], sm.P[o + 1], sm.P[o + 2]};
-            real QR[3] = {sm.Q[o], sm.Q[o + 1], sm.Q[o + 2]};
-            real loL[3], hiL[3], loR[3], hiR[3];
-            recon(th, wL, PL, QL, B0, B1, loL, hiL);
-            recon(th, wR, PR, QR, B1, B2, loR, hiR);
-            cu_flux(g, eps, hiL[0], hiL[1], hiL[2], loR[0], loR[1], loR[2], B1, H);
-            sm.Fx[0][r][fx] = H[0];
-            sm.Fx[1][r][fx] = H[1];
-            sm.Fx[2][r][fx] = H[2];
-        } else {                          // y-face gy of column c
-            int kk = k - kTile * (kTile + 1);
-            int gy = kk / kTile, c = kk % kTile;
-            int tx = c + kHalo, tyS = gy + 1;
-            const real *cb = sm.Bc + c + 1;
-            real B0 = real(0.5) * (cb[gy * kCornerStride] + cb[gy * kCornerStride + 1]);
-            real B1 = real(0.5) * (cb[(gy + 1) * kCornerStride] + cb[(gy + 1) * kCornerStride + 1]);
-            real B2 = real(0.5) * (cb[(gy + 2) * kCornerStride] + cb[(gy + 2) * kCornerStride + 1]);
-            const int o = tyS * kStride + tx;
-            real wS[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
-            real PS[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
-            real QS[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
-            real wN[3] = {sm.w[o], sm.w[o + kStride], sm.w[o + 2 * kStride]};
-            real PN[3] = {sm.P[o], sm.P[o + kStride], sm.P[o + 2 * kStride]};
-            real QN[3] = {sm.Q[o], sm.Q[o + kStride], sm.Q[o + 2 * kStride]};
-            real loS[3], hiS[3], loN[3], hiN[3];
-            recon(th, wS, PS, QS, B0, B1, loS, hiS);
-            recon(th, wN, PN, QN, B1, B2, loN, hiN);
+    // ---- 4. fluxes through every face of the tile, each computed once.
+    //         Each thread sweeps 4 consecutive faces of one row (x-faces) or
+    //         one column (y-faces), so every cell is reconstructed once per
+    //         direction: the right cell of a face is the left cell of the next.
+    {
+        const int r = tid >> 3, sg = tid & 7;   // x: row r, faces [4 sg, 4 sg + 4) (+ face 32)
+        const int f0 = sg * 4, f1 = sg == 7 ? kTile + 1 : f0 + 4;
+        const int rowo = (r + kHalo) * kStride;
+        const real *cb = sm.Bc + (r + 1) * kCornerStride;
+        real lo[3], hiL[3], hiR[3];
+        {
+            const int o = rowo + f0 + 1;
+            const real wq[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
+            const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
+            const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
+            recon(th, wq, Pq, Qq, real(0.5) * (cb[f0] + cb[f0 + kCornerStride]),
+                  real(0.5) * (cb[f0 + 1] + cb[f0 + 1 + kCornerStride]), lo, hiL);
+        }
+        for (int f = f0; f < f1; f++) {
+            const int o = rowo + f + 2;           // right cell of face f
+            const real wq[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
+            const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
+            const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
+            const real Bf = real(0.5) * (cb[f + 1] + cb[f + 1 + kCornerStride]);
+            recon(th, wq, Pq, Qq, Bf, real(0.5) * (cb[f + 2] + cb[f + 2 + kCornerStride]), lo, hiR);
+            real H[3];
+            cu_flux(g, eps, hiL[0], hiL[1], hiL[2], lo[0], lo[1], lo[2], Bf, H);
+            sm.Fx[0][r][f] = H[0];
+            sm.Fx[1][r][f] = H[1];
+            sm.Fx[2][r][f] = H[2];
+            hiL[0] = hiR[0];
+            hiL[1] = hiR[1];
+            hiL[2] = hiR[2];
+        }
+    }
+    {
+        const int c = tid & 31, sg = tid >> 5;  // y: column c, faces [4 sg, 4 sg + 4) (+ face 32)
+        const int g0 = sg * 4, g1 = sg == 7 ? kTile + 1 : g0 + 4;
+        const int tx = c + kHalo;
+        const real *cb = sm.Bc + c + 1;
+        real lo[3], hiS[3], hiN[3];
+        {
+            const int o = (g0 + 1) * kStride + tx;
+            const real wq[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
+            const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
+            const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
+            recon(th, wq, Pq, Qq, real(0.5) * (cb[g0 * kCornerStride] + cb[g0 * kCornerStride + 1]),
+                  real(0.5) * (cb[(g0 + 1) * kCornerStride] + cb[(g0 + 1) * kCornerStride + 1]), lo, hiS);
+        }
+        for (int gq = g0; gq < g1; gq++) {
+            const int o = (gq + 2) * kStride + tx;  // north cell of face gq
+            const real wq[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
+            const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
+            const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
+            const real Bf = real(0.5) * (cb[(gq + 1) * kCornerStride] + cb[(gq + 1) * kCornerStride + 1]);
+            recon(th, wq, Pq, Qq, Bf,
+                  real(0.5) * (cb[(gq + 2) * kCornerStride] + cb[(gq + 2) * kCornerStride + 1]), lo, hiN);
+            real H[3];
             // normal discharge is Q, tangential is P
-            cu_flux(g, eps, hiS[0], hiS[2], hiS[1], loN[0], loN[2], loN[1], B1, H);
-            sm.Fy[0][gy][c] = H[0];
-            sm.Fy[1][gy][c] = H[2];
-            sm.Fy[2][gy][c] = H[1];
+            cu_flux(g, eps, hiS[0], hiS[2], hiS[1], lo[0], lo[2], lo[1], Bf, H);
+            sm.Fy[0][gq][c] = H[0];
+            sm.Fy[1][gq][c] = H[2];
+            sm.Fy[2][gq][c] = H[1];
+            hiS[0] = hiN[0];
+            hiS[1] = hiN[1];
+            hiS[2] = hiN[2];
         }
     }
     __syncthreads();
@@ -666,15 +685,25 @@ __device__ __forceinline__ void coef23(real B3, real hrh, real srh, real rh2, re
     c = -s - r;
 }
 
+// Shared-memory slot of line element k: element j of segment t sits at
+// j * sp + t (sp odd), so the threads of a warp sweeping their segments touch
+// consecutive words at every step (no bank conflicts).
+__device__ __forceinline__ int seg_slot(int k, int mshift, int sp)
+{
+    return (k & ((1 << mshift) - 1)) * sp + (k >> mshift);
+}
+
 template <typename real>
 __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n, S = A.nseg, N2 = 2 * S;
+    const int mshift = A.mshift, m = 1 << mshift, sp = A.sp;
+    const int npad = S * m;                          // lines padded with identity rows
     real *sA = reinterpret_cast<real *>(smem_raw);   // d, then alpha / alpha-hat
-    real *sC = sA + n;                               // gamma / gamma-hat
-    real *sR = sC + n;                               // rhs -> rho -> rho-hat -> x
-    real *ra = sR + n, *rb = ra + N2, *rc = rb + N2, *rr = rc + N2;
+    real *sC = sA + m * sp;                          // gamma / gamma-hat
+    real *sR = sC + m * sp;                          // rhs -> rho -> rho-hat -> x
+    real *ra = sR + m * sp, *rb = ra + N2, *rc = rb + N2, *rr = rc + N2;
     const int tid = threadIdx.x, T = blockDim.x;
     const Geo &G = A.geo;
     const real rh2 = A.rh2, hrh = A.hrh, srh = A.srh;
@@ -686,36 +715,38 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
     for (int line = blockIdx.x; line < A.nlines; line += gridDim.x) {
         const real *rhs = A.rhs + (size_t)line * A.pitch;
         const real *dl = A.d + (size_t)line * A.pitch;
-        for (int k = tid; k < n; k += T) {
-            sR[k] = rhs[k];
-            sA[k] = dl[k];
+        for (int k = tid; k < npad; k += T) {
+            const int q = seg_slot(k, mshift, sp);
+            sR[q] = k < n ? rhs[k] : real(0);
+            sA[q] = k < n ? dl[k] : real(0);     // d = 0: a = c = 0, b = 1
         }
         __syncthreads();
         if (!A.identity) {
         const bool act = tid < S;
-        const int f = act ? (int)((long long)tid * n / S) : 0;
-        const int l = act ? (int)((long long)(tid + 1) * n / S) - 1 : 0;
-        real dm = real(0), dp = real(0), dcur = real(0);
+        const int f = tid * m, l = f + m - 1;
+        real dm = real(0), dp = real(0), dcur = real(0), dlast = real(0);
         if (act) {
-            dm = f > 0 ? sA[f - 1] : sA[0];     // mirrored depth beyond the ends
-            dp = l < n - 1 ? sA[l + 1] : sA[n - 1];
-            dcur = sA[f];
+            dlast = sA[seg_slot(n - 1, mshift, sp)];
+            dm = f > 0 ? sA[seg_slot(f - 1, mshift, sp)] : sA[seg_slot(0, mshift, sp)];
+            dp = l + 1 < n ? sA[seg_slot(l + 1, mshift, sp)] : dlast;   // mirrored beyond the end
+            dcur = sA[tid];
         }
         __syncthreads();
         real af = 0, bf = 1, cf = 0, rf = 0;
         if (act) {
             // forward: rows f+1..l as alpha x_f + x_k + gamma x_{k+1} = rho
             real dprev = dm, ap = 0, gp = 0, rp = 0;
-            for (int k = f; k <= l; k++) {
-                real dnext = k < l ? sA[k + 1] : dp;
+            for (int j = 0; j < m; j++) {
+                const int k = f + j, q = j * sp + tid;
+                real dnext = j + 1 < m ? (k + 1 < n ? sA[q + sp] : dlast) : dp;
                 real ak, bk, ck;
                 coef23(B3, hrh, srh, rh2, dcur, dprev, dnext, ak, bk, ck);
-                real rk = sR[k];
+                real rk = sR[q];
                 if (k == 0) {   // Reading A-B2: mirror, or the known ghost increment
                     if (lo_sine) {
-                        const real *tb = A.ghost + ghost_index(0, lo_side, 0, gvar, line + 2, A.c.npos);
+                        const real *t0 = A.ghost + ghost_index(0, lo_side, 0, gvar, line + 2, A.c.npos);
                         const real *t1 = A.ghost + ghost_index(1, lo_side, 0, gvar, line + 2, A.c.npos);
-                        rk -= ak * (t1[0] - tb[0]);
+                        rk -= ak * (t1[0] - t0[0]);
                     } else {
                         bk -= ak;
                     }
@@ -723,22 +754,22 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
                 }
                 if (k == n - 1) {
                     if (hi_sine) {
-                        const real *tb = A.ghost + ghost_index(0, hi_side, 0, gvar, line + 2, A.c.npos);
+                        const real *t0 = A.ghost + ghost_index(0, hi_side, 0, gvar, line + 2, A.c.npos);
                         const real *t1 = A.ghost + ghost_index(1, hi_side, 0, gvar, line + 2, A.c.npos);
-                        rk -= ck * (t1[0] - tb[0]);
+                        rk -= ck * (t1[0] - t0[0]);
                     } else {
                         bk -= ck;
                     }
                     ck = real(0);
                 }
-                if (k == f) {
+                if (j == 0) {
                     af = ak;
                     bf = bk;
                     cf = ck;
                     rf = rk;
                 } else {
                     real al, ga, rho;
-                    if (k == f + 1) {
+                    if (j == 1) {
                         real inv = real(1) / bk;
                         al = ak * inv;
                         ga = ck * inv;
@@ -749,9 +780,9 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
                         ga = ck * inv;
                         rho = (rk - ak * rp) * inv;
                     }
-                    sA[k] = al;
-                    sC[k] = ga;
-                    sR[k] = rho;
+                    sA[q] = al;
+                    sC[q] = ga;
+                    sR[q] = rho;
                     ap = al;
                     gp = ga;
                     rp = rho;
@@ -760,32 +791,33 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
                 dcur = dnext;
             }
             // backward: rows l-2..f+1 as x_k = rho^ - alpha^ x_f - gamma^ x_l
-            real ah = sA[l - 1], gh = sC[l - 1], rhh = sR[l - 1];
-            for (int k = l - 2; k >= f + 1; k--) {
-                real ga = sC[k];
-                rhh = sR[k] - ga * rhh;
-                ah = sA[k] - ga * ah;
+            real ah = sA[(m - 2) * sp + tid], gh = sC[(m - 2) * sp + tid], rhh = sR[(m - 2) * sp + tid];
+            for (int j = m - 3; j >= 1; j--) {
+                const int q = j * sp + tid;
+                real ga = sC[q];
+                rhh = sR[q] - ga * rhh;
+                ah = sA[q] - ga * ah;
                 gh = -ga * gh;
-                sA[k] = ah;
-                sC[k] = gh;
-                sR[k] = rhh;
+                sA[q] = ah;
+                sC[q] = gh;
+                sR[q] = rhh;
             }
-            // reduced rows: (x_{l-1 of prev}, x_f, x_l) and (x_f, x_l, x_{f of next})
-            if (l - f >= 2) {
-                ra[2 * tid] = af;
-                rb[2 * tid] = bf - cf * sA[f + 1];
-                rc[2 * tid] = -cf * sC[f + 1];
-                rr[2 * tid] = rf - cf * sR[f + 1];
-            } else {
-                ra[2 * tid] = af;
+            // reduced rows: (x_{l of prev}, x_f, x_l) and (x_f, x_l, x_{f of next})
+            const int q1 = sp + tid, ql = (m - 1) * sp + tid;
+            ra[2 * tid] = af;
+            if (m > 2) {   // x_{f+1} = rho^ - alpha^ x_f - gamma^ x_l
+                rb[2 * tid] = bf - cf * sA[q1];
+                rc[2 * tid] = -cf * sC[q1];
+                rr[2 * tid] = rf - cf * sR[q1];
+            } else {       // two rows: x_{f+1} is x_l itself
                 rb[2 * tid] = bf;
                 rc[2 * tid] = cf;
                 rr[2 * tid] = rf;
             }
-            ra[2 * tid + 1] = sA[l];
+            ra[2 * tid + 1] = sA[ql];
             rb[2 * tid + 1] = real(1);
-            rc[2 * tid + 1] = sC[l];
-            rr[2 * tid + 1] = sR[l];
+            rc[2 * tid + 1] = sC[ql];
+            rr[2 * tid + 1] = sR[ql];
         }
         __syncthreads();
         // parallel cyclic reduction of the 2S interface rows
@@ -828,9 +860,12 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
         }
         if (act) {
             real xf = rr[2 * tid] / rb[2 * tid], xl = rr[2 * tid + 1] / rb[2 * tid + 1];
-            for (int k = f + 1; k < l; k++) sR[k] = sR[k] - sA[k] * xf - sC[k] * xl;
-            sR[f] = xf;
-            sR[l] = xl;
+            for (int j = 1; j < m - 1; j++) {
+                const int q = j * sp + tid;
+                sR[q] = sR[q] - sA[q] * xf - sC[q] * xl;
+            }
+            sR[tid] = xf;
+            sR[(m - 1) * sp + tid] = xl;
         }
         __syncthreads();
         }
@@ -839,7 +874,7 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
         const real *bs = A.base + (size_t)line * A.pitch;
         real *out = A.sol + (size_t)line * A.pitch;
         for (int k = tid; k < n; k += T) {
-            real v = bs[k] + sR[k];
+            real v = bs[k] + sR[seg_slot(k, mshift, sp)];
             if (A.final_stage) {
                 int i = A.dir == 0 ? k : line, j = A.dir == 0 ? line : k;
                 v *= sponge_gamma<real>(A.c, G, i, j);
@@ -961,22 +996,28 @@ cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+int line_seg_shift(int n, int real_bytes)
+{
+    // 16 rows per segment (32 for long FP64 lines, to fit shared memory),
+    // fewer for short lines so that there are at least 2 segments of >= 2 rows
+    int sh = (real_bytes == 8 && n > 4096) ? 5 : 4;
+    while (sh > 1 && (n >> sh) < 2) sh--;
+    return sh;
+}
+
 int line_segments(int n, int real_bytes)
 {
-    // about 16 rows per segment (32 for long FP64 lines, to fit shared memory),
-    // at least 2 rows per segment, at most 1024 segments
-    int m = (real_bytes == 8 && n > 4096) ? 32 : 16;
-    int S = (n + m - 1) / m;
-    if (S > n / 2) S = n / 2;
-    if (S > 1024) S = 1024;
-    if (S < 1) S = 1;
-    return S;
+    const int m = 1 << line_seg_shift(n, real_bytes);
+    return (n + m - 1) / m;
 }
+
+int line_seg_stride(int nseg) { return nseg | 1; }
 
 template <typename real>
 size_t line_smem_bytes(int n, int nseg)
 {
-    return sizeof(real) * ((size_t)3 * n + (size_t)8 * nseg);
+    const int m = 1 << line_seg_shift(n, (int)sizeof(real));
+    return sizeof(real) * ((size_t)3 * m * line_seg_stride(nseg) + (size_t)8 * nseg);
 }
 
 template <typename real>
@@ -992,6 +1033,7 @@ cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st)
     }
     int threads = round_up(a.nseg, 32);
     if (threads < 64) threads = 64;
+    if (a.nseg * (1 << a.mshift) < a.n || a.sp != line_seg_stride(a.nseg)) return cudaErrorInvalidValue;
     k_lines<real><<<a.nlines, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
