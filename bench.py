@@ -248,12 +248,8 @@ def main():
     launches = sol.last_launch_count()
     prof = sol.profile_read()
     sol.profile_disable()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * s.cells * args.steps / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    value = whole_job_rate(s.cells, args.steps, ms)
 
     # ---- roofline of the dominant kernel (bytes per launch / event time)
     peak, peak_src = peaks()
@@ -310,6 +306,26 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def max_over_ranks(ms: float) -> float:
+    """The slowest rank's time (ms); every rank gets it.  Single process: ms."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank: int, steps: int, ms: float) -> float:
+    """Cell-updates/s of the whole job: every replica advanced cells_per_rank
+    cells `steps` times within the slowest rank's ms."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    return world * cells_per_rank * steps / (ms / 1e3)
 
 
 def celeris_source_hash():

@@ -1,0 +1,49 @@
+"""Host logic of bench.py's multi-GPU path, on CPU with two gloo ranks: the
+timing is the max over ranks and the rate counts every replica's cells."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(10.0 + 5.0 * rank)        # rank 1 is slower
+        rate = bench.whole_job_rate(1000, 4, ms)
+        q.put((rank, ms, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_rate_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, ms, rate in got:
+        assert ms == 15.0                                    # the slower rank
+        assert rate == pytest.approx(2 * 1000 * 4 / 0.015)  # both replicas' cells
+
+
+def test_single_process_defaults():
+    import bench
+    assert bench.max_over_ranks(7.5) == 7.5
+    assert bench.whole_job_rate(100, 10, 1000.0) == pytest.approx(1000.0)
