@@ -374,11 +374,40 @@ struct StencilSmem {
 // which equals recomputing U*^n from P^n by Eq. 23 but keeps the rounding
 // relative to the increment instead of to P.
 template <typename real>
+struct Carry {
+    real a, b, q, e, Y;
+};
+
+// The carries a stage reads, loaded at the top of a cell's iteration so the
+// loads are in flight while the cell's right side is computed.
+template <typename real>
+__device__ __forceinline__ Carry<real> load_carry(int kind, int keepK, size_t k, const real *a, const real *b,
+                                                  const real *Y, const real *q, const real *e)
+{
+    Carry<real> c;
+    c.a = c.b = c.q = c.e = c.Y = real(0);
+    if (kind == kAM4) {
+        c.Y = Y[k];
+    } else if (kind == kEuler1) {
+        c.a = a[k];
+        if (keepK) c.e = e[k];
+    } else if (kind == kAB3) {
+        c.a = a[k];
+        c.b = b[k];
+        if (keepK) {
+            c.q = q[k];
+            c.e = e[k];
+        }
+    }
+    return c;
+}
+
+template <typename real>
 __device__ __forceinline__ real advance(int kind, int keepK, real X0, real R, real Phi, real dt, size_t k,
-                                        real *a, real *b, real *Y, real *q, real *e)
+                                        const Carry<real> &c, real *a, real *b, real *Y, real *q, real *e)
 {
     const real c12 = dt / real(12), c24 = dt / real(24);
-    if (kind == kAM4) return Y[k] + real(9) * c24 * R + Phi;
+    if (kind == kAM4) return c.Y + real(9) * c24 * R + Phi;
     real D;
     if (kind == kEuler0) {
         D = dt * R;
@@ -386,24 +415,63 @@ __device__ __forceinline__ real advance(int kind, int keepK, real X0, real R, re
         b[k] = real(5) * c12 * R + Phi;
         if (keepK) e[k] = c24 * R;
     } else if (kind == kEuler1) {
-        D = dt * R + (Phi - a[k]);
+        D = dt * R + (Phi - c.a);
         a[k] = real(-16) * c12 * R - real(3) * Phi;
         b[k] = real(5) * c12 * R + Phi;
         if (keepK) {
-            q[k] = real(-5) * c24 * R + e[k];
+            q[k] = real(-5) * c24 * R + c.e;
             e[k] = c24 * R;
         }
     } else {
-        D = real(23) * c12 * R + real(2) * Phi + (a[k] + b[k]);
+        D = real(23) * c12 * R + real(2) * Phi + (c.a + c.b);
         if (keepK) {
-            Y[k] = X0 + real(19) * c24 * R - Phi + q[k];
-            q[k] = real(-5) * c24 * R + e[k];
+            Y[k] = X0 + real(19) * c24 * R - Phi + c.q;
+            q[k] = real(-5) * c24 * R + c.e;
             e[k] = c24 * R;
         }
         a[k] = real(-16) * c12 * R - real(3) * Phi;
         b[k] = real(5) * c12 * R + Phi;
     }
     return D;
+}
+
+template <typename real> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Stage rows of a row-major field into a shared tile: `rows` rows of `cols`
+// elements starting at column gx0 (even) of row gy0, with pairs loaded as one
+// aligned vector where both elements are inside [0, lim_x) x [0, lim_y).
+template <typename real>
+__device__ __forceinline__ void stage_rows(const real *src, size_t pitch, int gx0, int gy0, int rows, int cols,
+                                           int lim_x, int lim_y, real *dst, int dstride, int tid, int nthreads,
+                                           bool transpose)
+{
+    using real2 = typename Vec2<real>::type;
+    const int pairs = (cols + 1) >> 1;
+    for (int k = tid; k < rows * pairs; k += nthreads) {
+        const int r = k / pairs, c = 2 * (k - r * pairs);
+        const int gy = gy0 + r, gx = gx0 + c;
+        real v0 = real(0), v1 = real(0);
+        if (gy >= 0 && gy < lim_y) {
+            const real *row = src + (size_t)gy * pitch;
+            if (gx >= 0 && gx + 1 < lim_x) {
+                real2 v = *reinterpret_cast<const real2 *>(row + gx);
+                v0 = v.x;
+                v1 = v.y;
+            } else {
+                if (gx >= 0 && gx < lim_x) v0 = row[gx];
+                if (gx + 1 >= 0 && gx + 1 < lim_x) v1 = row[gx + 1];
+            }
+        }
+        if (transpose) {
+            dst[c * dstride + r] = v0;
+            if (c + 1 < cols) dst[(c + 1) * dstride + r] = v1;
+        } else {
+            dst[r * dstride + c] = v0;
+            if (c + 1 < cols) dst[r * dstride + c + 1] = v1;
+        }
+    }
 }
 
 template <typename real>
@@ -419,26 +487,17 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
     const real ws = C.ws, g = C.g, eps = C.eps;
     const real th = C.theta;
 
-    // ---- 1. stage the state tile (+2 halo) and the bed corners
-    for (int k = tid; k < kTileIn * kTileIn; k += kStencilThreads) {
-        int ty = k / kTileIn, tx = k % kTileIn;
-        int gx = x0 - kHalo + tx, gy = y0 - kHalo + ty;
-        bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-        size_t r = (size_t)gy * G.px + gx;
-        sm.w[ty * kStride + tx] = in ? A.w_in[r] : real(0);
-        sm.P[ty * kStride + tx] = in ? A.P_in[r] : real(0);
-    }
-    for (int k = tid; k < kTileIn * kTileIn; k += kStencilThreads) {
-        int tx = k / kTileIn, ty = k % kTileIn;   // column-major: y fastest
-        int gx = x0 - kHalo + tx, gy = y0 - kHalo + ty;
-        bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-        sm.Q[ty * kStride + tx] = in ? A.Qc_in[(size_t)gx * G.py + gy] : real(0);
-    }
-    for (int k = tid; k < kCorner * kCorner; k += kStencilThreads) {
-        int cy = k / kCorner, cx = k % kCorner;
-        int ax = min(x0 + cx, nx + 2), ay = min(y0 + cy, ny + 2);   // array index = corner + 1
-        sm.Bc[cy * kCornerStride + cx] = A.Bc[(size_t)ay * G.pc + ax];
-    }
+    // ---- 1. stage the state tile (+2 halo) and the bed corners; Q is
+    //         column-major, so its tile is staged along y and transposed
+    stage_rows(A.w_in, G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.w, kStride, tid,
+               kStencilThreads, false);
+    stage_rows(A.P_in, G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.P, kStride, tid,
+               kStencilThreads, false);
+    stage_rows(A.Qc_in, G.py, y0 - kHalo, x0 - kHalo, kTileIn, kTileIn, ny, nx, sm.Q, kStride, tid,
+               kStencilThreads, true);
+    // corners: array index (corner + 1) in [0, nx + 2] x [0, ny + 2]
+    stage_rows(A.Bc, G.pc, x0, y0, kCorner, kCorner, nx + 3, ny + 3, sm.Bc, kCornerStride, tid,
+               kStencilThreads, false);
     if (tid < kTile) sm.colbits[tid] = 0u;
     __syncthreads();
 
@@ -592,6 +651,13 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
         const int i = x0 + cx, j = y0 + cy;
         const bool valid = i < nx && j < ny;
         const int o = (cy + kHalo) * kStride + cx + kHalo;
+        const size_t kr = (size_t)j * G.px + i;
+        Carry<real> cw, cu, cv;
+        if (valid) {
+            cw = load_carry(A.kind, A.keepK, kr, A.a[0], A.b[0], A.Y[0], A.q[0], A.e[0]);
+            cu = load_carry(A.kind, A.keepK, kr, A.a[1], A.b[1], A.Y[1], A.q[1], A.e[1]);
+            cv = load_carry(A.kind, A.keepK, kr, A.a[2], A.b[2], A.Y[2], A.q[2], A.e[2]);
+        }
         const real *cb = sm.Bc + (cy + 1) * kCornerStride + cx + 1;
         real c00 = cb[0], c10 = cb[1], c01 = cb[kCornerStride], c11 = cb[kCornerStride + 1];
         real Bb = cell_bbar(c00, c10, c01, c11);
@@ -642,11 +708,10 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
         }
         real w1 = w0, dU = real(0), dV = real(0);
         if (valid) {
-            const size_t kr = (size_t)j * G.px + i;
-            real dw = advance(A.kind, A.keepK, w0, E, real(0), dt, kr, A.a[0], A.b[0], A.Y[0], A.q[0], A.e[0]);
+            real dw = advance(A.kind, A.keepK, w0, E, real(0), dt, kr, cw, A.a[0], A.b[0], A.Y[0], A.q[0], A.e[0]);
             w1 = A.kind == kAM4 ? dw : w0 + dw;   // the AM4 base of w holds w^n
-            dU = advance(A.kind, A.keepK, real(0), F, Fs, dt, kr, A.a[1], A.b[1], A.Y[1], A.q[1], A.e[1]);
-            dV = advance(A.kind, A.keepK, real(0), Gq, Gs, dt, kr, A.a[2], A.b[2], A.Y[2], A.q[2], A.e[2]);
+            dU = advance(A.kind, A.keepK, real(0), F, Fs, dt, kr, cu, A.a[1], A.b[1], A.Y[1], A.q[1], A.e[1]);
+            dV = advance(A.kind, A.keepK, real(0), Gq, Gs, dt, kr, cv, A.a[2], A.b[2], A.Y[2], A.q[2], A.e[2]);
             if (w1 < Bb) w1 = Bb;   // Reading A-D1
             if (A.final_stage) {
                 real gam = sponge_gamma<real>(C, G, i, j);

@@ -194,3 +194,39 @@ def test_solitary_rejected_on_dry_crest():
     with pytest.raises(celeris.CelerisError):
         g.add_solitary(0.1, 0.0, 50.0, 20.0)
     g.add_solitary(0.1, 0.0, 10.0, 20.0)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_full_size_beach_restart_parity(prec):
+    """The 2048 x 2048 beach at full size, in the launch configuration the
+    benchmark times: the state after 300 GPU steps is given to a fresh GPU
+    solver and to the oracle, both at t = 0 (two Euler steps, then AB3 +
+    AM4), and they are compared element by element after 2 and 4 steps."""
+    s = sc.beach(nx=2048, ny=2048)
+    g0 = _solver(s, prec)
+    g0.step(300)
+    w, P, Q = g0.state()
+    assert g0.check_finite()
+    del g0
+    g = _solver(s, prec)             # both restart at t = 0 from the same state
+    g.set_state(w, P, Q)
+    o = oracle_from(s)
+    o.set_state(_np(w), _np(P), _np(Q))
+    wo0 = o.state()[0]
+    assert rel_l2(_np(g.state()[0]), wo0) <= TOL[prec]
+    for _ in range(2):
+        g.step(2)
+        o.step(2)
+        wo, Po, Qo = o.state()
+        wg, Pg, Qg = (_np(a) for a in g.state())
+        assert rel_l2(wg - s.ws, wo - s.ws) <= TOL[prec]
+        assert rel_l2(Pg, Po) <= 10 * TOL[prec]
+        assert rel_l2(Qg, Qo) <= 10 * TOL[prec]
+
+
+def test_long_run_fp32_drift():
+    """FP32 over a long run: a 256 x 256 beach crop for 4000 steps (about 40 s
+    of simulated time, 5 wave periods), eta compared every 500 steps."""
+    s = sc.beach(nx=256, ny=256, sponge=24)
+    worst, _, _ = _lockstep(s, "f32", 4000, every=500)
+    assert worst <= TOL["f32"]
