@@ -28,12 +28,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic values moved per cell by one launch of each kernel: the stencil
-# predictor of an AB3 step with the AM4 carries reads w, P, Q, bed corners
-# and 12 carries and writes w, dU*, dV* and 15 carries; the corrector stencil
-# reads w, P, Q, corners, 3 bases and writes w, dU*, dV*; a line solve reads
-# its right side, depth and P^n (or Q^n) and writes P^{n+1} (or Q^{n+1}).
-VALUES = {"stencil_pred_k": 16 + 18, "stencil_pred_0": 10 + 9, "stencil_corr": 7 + 3, "lines": 4}
+# Algorithmic values moved per cell by one launch of each kernel:
+#   stencil, AB3 predictor with K >= 1 (ring history): reads w, P, Q, bed
+#     corners, R^{n-1}, R^{n-2} of w, U*, V* and the mixed terms F*, G* at n-1,
+#     n-2 (14); writes w, dU*, dV*, R^n (3), F*^n, G*^n and 3 AM4 bases (11);
+#   stencil, AM4 corrector: reads w, P, Q, corners, 3 bases (7), writes 3;
+#   stencil, predictor with K = 0 (carries a, b): reads 10, writes 9;
+#   line solves (x-rows and y-columns in one launch): per family the right
+#     side, depth and P^n (or Q^n) read, P^{n+1} (or Q^{n+1}) written: 2 x 4.
+VALUES = {"stencil_pred_k": 14 + 11, "stencil_pred_0": 10 + 9, "stencil_corr": 7 + 3, "lines": 8}
 
 
 def parse():
@@ -238,7 +241,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sol.profile_enable(4 * (s.K + 1) * args.steps + 16)
+    sol.profile_enable(3 * (s.K + 1) * args.steps + 16)
     e0.record(stream)
     sol.step(args.steps)
     e1.record(stream)
@@ -261,12 +264,13 @@ def main():
     kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()}
     dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
     line_bytes = s.cells * es * VALUES["lines"] * (nstages_pred + nstages_corr)
-    bytes_of = {"stencil": st_bytes, "xlines": line_bytes, "ylines": line_bytes}
+    bytes_of = {"stencil": st_bytes, "lines": line_bytes, "ghosts": 0}
     dk = kernels[dominant]
     achieved = bytes_of[dominant] / (dk["ms_total"] / 1e3) / 1e9 if dk["ms_total"] > 0 else 0.0
     for k in kernels:
         kk = kernels[k]
-        kk["gbs_algorithmic"] = bytes_of[k] / (kk["ms_total"] / 1e3) / 1e9 if kk["ms_total"] > 0 else None
+        kk["gbs_algorithmic"] = (bytes_of[k] / (kk["ms_total"] / 1e3) / 1e9
+                                 if kk["ms_total"] > 0 and bytes_of[k] else None)
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -279,8 +283,8 @@ def main():
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                 "per_kernel": kernels,
-                "step_bytes_algorithmic": (st_bytes + 2 * line_bytes) / args.steps,
-                "step_gbs_algorithmic": (st_bytes + 2 * line_bytes) / (ms / 1e3) / 1e9 / world}
+                "step_bytes_algorithmic": (st_bytes + line_bytes) / args.steps,
+                "step_gbs_algorithmic": (st_bytes + line_bytes) / (ms / 1e3) / 1e9 / world}
 
     # ---- end to end through the public API with host buffers
     e2e = None

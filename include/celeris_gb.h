@@ -169,8 +169,8 @@ cel_status cel_load_checkpoint(cel_solver *s, const void *src_dev, size_t bytes)
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
- * each launch of the three step kernels (0: stencil + update, 1: x-line
- * solves, 2: y-line solves).  cel_profile_enable creates `capacity` event
+ * each launch of the step kernels (0: stencil + update, 1: line solves, x-rows
+ * and y-columns in one launch, 2: sine-maker ghost table).  cel_profile_enable creates `capacity` event
  * pairs (host-side CUDA resources; no device memory) and starts recording;
  * launches beyond capacity are not timed.  cel_profile_read synchronises and
  * returns the summed milliseconds and launch counts per kernel, then resets

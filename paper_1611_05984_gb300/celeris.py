@@ -281,7 +281,7 @@ class Solver:
         ms = (ctypes.c_double * 3)()
         cnt = (ctypes.c_int64 * 3)()
         self._check(self.L.cel_profile_read(self._h, ms, cnt), "profile_read")
-        return {name: (ms[k], cnt[k]) for k, name in enumerate(("stencil", "xlines", "ylines"))}
+        return {name: (ms[k], cnt[k]) for k, name in enumerate(("stencil", "lines", "ghosts"))}
 
     def profile_disable(self):
         self._check(self.L.cel_profile_disable(self._h), "profile_disable")

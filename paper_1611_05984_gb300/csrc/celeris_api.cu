@@ -24,8 +24,9 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
 
 struct Layout {
-    size_t w[2], P[2], U, dr, a[3], b[3][2], Y[3], q[3], e[3];
-    size_t Qc[2], Vc, dc, Bc, mr, mc, ghost, flag;
+    size_t w[2], P[2], U, dr, a[3], b[3][2];     // carries (K = 0)
+    size_t R[3][3], Ph[3][3], Y[3];              // rings and AM4 bases (K >= 1)
+    size_t Qc[2], Vc, dc, Bc, mr, mc, ghost, ktab, flag;
     size_t total;
     size_t row_bytes, col_bytes;
 };
@@ -63,17 +64,20 @@ Layout make_layout(const Geo &G, int es, int K)
     L.P[1] = take(L.row_bytes);
     L.U = take(L.row_bytes);
     L.dr = take(L.row_bytes);
-    for (int v = 0; v < 3; v++) {
-        L.a[v] = take(L.row_bytes);
-        L.b[v][0] = take(L.row_bytes);
-        L.b[v][1] = take(L.row_bytes);
-    }
-    if (K > 0)
+    if (K == 0) {
         for (int v = 0; v < 3; v++) {
-            L.Y[v] = take(L.row_bytes);
-            L.q[v] = take(L.row_bytes);
-            L.e[v] = take(L.row_bytes);
+            L.a[v] = take(L.row_bytes);
+            L.b[v][0] = take(L.row_bytes);
+            L.b[v][1] = take(L.row_bytes);
         }
+    } else {
+        for (int v = 0; v < 3; v++) {
+            for (int k = 0; k < 3; k++) L.R[v][k] = take(L.row_bytes);
+            if (v > 0)
+                for (int k = 0; k < 3; k++) L.Ph[v][k] = take(L.row_bytes);
+            L.Y[v] = take(L.row_bytes);
+        }
+    }
     L.Qc[0] = take(L.col_bytes);
     L.Qc[1] = take(L.col_bytes);
     L.Vc = take(L.col_bytes);
@@ -82,6 +86,7 @@ Layout make_layout(const Geo &G, int es, int K)
     L.mr = take((size_t)G.ny * G.nwx * 4);
     L.mc = take((size_t)G.nx * G.nwy * 4);
     L.ghost = take(ghost_index(2, 0, 0, 0, 0, (G.nx > G.ny ? G.nx : G.ny) + 4) * es);
+    L.ktab = take((size_t)4 * ((G.nx > G.ny ? G.nx : G.ny) + 4) * 8 * sizeof(double));
     L.flag = take(256);
     L.total = cur;
     return L;
@@ -130,6 +135,7 @@ struct cel_solver {
     unsigned char *gring;
     int ng, log_every, cap, nrec, head;
     int64_t launches;
+    int ktab_dirty;   // boundaries or bed changed: rebuild the Eckart table
     std::string err;
     // optional per-kernel event timing
     cudaEvent_t *ev_beg, *ev_end;
@@ -223,8 +229,16 @@ cel_status step_t(cel_solver *s, int nsteps)
         const double t0 = (double)s->step * s->params.dt, t1 = (double)(s->step + 1) * s->params.dt;
         const int slot = (int)(s->nh & 1);
         if (coef.sine) {
-            CEL_CUDA(s, launch_ghost_table<real>(s->geo, s->phy, s->bnd, s->at<real>(L.dr), t0, t1, ghost,
-                                                 coef.npos, s->stream), "ghost table");
+            int pg = prof_begin(s, 2);
+            if (s->ktab_dirty) {
+                CEL_CUDA(s, launch_eckart_table<real>(s->geo, s->phy, s->bnd, s->at<real>(L.dr),
+                                                      s->at<double>(L.ktab), coef.npos, s->stream), "Eckart table");
+                s->ktab_dirty = 0;
+                launches += 1;
+            }
+            CEL_CUDA(s, launch_ghost_table<real>(s->geo, s->phy, s->bnd, s->at<real>(L.dr), s->at<double>(L.ktab),
+                                                 t0, t1, ghost, coef.npos, s->stream), "ghost table");
+            prof_end(s, pg);
             launches += 1;
         }
         for (int stage = 0; stage <= Kn; stage++) {
@@ -240,24 +254,31 @@ cel_status step_t(cel_solver *s, int nsteps)
             a.Qc_in = s->at<real>(L.Qc[stage == 0 ? s->pcur : 1 - s->pcur]);
             a.U_out = s->at<real>(L.U);
             a.Vc_out = s->at<real>(L.Vc);
+            // ring slots: R^n goes to slot nh % 3, R^{n-1} and R^{n-2} before it
+            const int s0 = (int)(s->nh % 3), s1 = (s0 + 2) % 3, s2 = (s0 + 1) % 3;
             for (int v = 0; v < 3; v++) {
-                a.a[v] = s->at<real>(L.a[v]);
-                a.b[v] = s->at<real>(L.b[v][slot]);
+                a.a[v] = K == 0 ? s->at<real>(L.a[v]) : nullptr;
+                a.b[v] = K == 0 ? s->at<real>(L.b[v][slot]) : nullptr;
+                a.R0[v] = K > 0 ? s->at<real>(L.R[v][s0]) : nullptr;
+                a.R1[v] = K > 0 ? s->at<real>(L.R[v][s1]) : nullptr;
+                a.R2[v] = K > 0 ? s->at<real>(L.R[v][s2]) : nullptr;
+                a.F0[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s0]) : nullptr;
+                a.F1[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s1]) : nullptr;
+                a.F2[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s2]) : nullptr;
                 a.Y[v] = K > 0 ? s->at<real>(L.Y[v]) : nullptr;
-                a.q[v] = K > 0 ? s->at<real>(L.q[v]) : nullptr;
-                a.e[v] = K > 0 ? s->at<real>(L.e[v]) : nullptr;
             }
             a.mask_r = s->at<uint32_t>(L.mr);
             a.mask_c = s->at<uint32_t>(L.mc);
             a.kind = stage == 0 ? kind0 : kAM4;
-            a.keepK = K > 0;
+            a.ring = K > 0;
             a.final_stage = stage == Kn;
             a.tsel = stage == 0 ? 0 : 1;
             int pe = prof_begin(s, 0);
             CEL_CUDA(s, launch_stencil<real>(a, s->stream), "stencil");
             prof_end(s, pe);
+            LinePair<real> lp;
             for (int dir = 0; dir < 2; dir++) {
-                LineArgs<real> l;
+                LineArgs<real> &l = lp.L[dir];
                 l.geo = s->geo;
                 l.phy = s->phy;
                 l.c = coef;
@@ -282,11 +303,12 @@ cel_status step_t(cel_solver *s, int nsteps)
                 l.sp = line_seg_stride(l.nseg);
                 l.final_stage = stage == Kn;
                 l.identity = s->params.model == CEL_NLSW;
-                int pl = prof_begin(s, 1 + dir);
-                CEL_CUDA(s, launch_lines<real>(l, s->stream), dir == 0 ? "x-lines" : "y-lines");
-                prof_end(s, pl);
             }
-            launches += 3;
+            int pl = prof_begin(s, 1);
+            CEL_CUDA(s, launch_lines<real>(lp, s->stream), "line solves");
+            prof_end(s, pl);
+            if (lp.L[0].mshift != lp.L[1].mshift) launches += 1;   // two segment lengths: two launches
+            launches += 2;
         }
         s->cur = (s->cur + Kn + 1) & 1;
         s->pcur = 1 - s->pcur;
@@ -330,17 +352,19 @@ int ckpt_parts(const cel_solver *s, CkptPart *parts)
     parts[n++] = {L.w[s->cur], L.row_bytes};
     parts[n++] = {L.P[s->pcur], L.row_bytes};
     parts[n++] = {L.Qc[s->pcur], L.col_bytes};
-    for (int v = 0; v < 3; v++) {
-        parts[n++] = {L.a[v], L.row_bytes};
-        parts[n++] = {L.b[v][0], L.row_bytes};
-        parts[n++] = {L.b[v][1], L.row_bytes};
-    }
-    if (s->params.corrector_iters > 0)
+    if (s->params.corrector_iters == 0) {
         for (int v = 0; v < 3; v++) {
-            parts[n++] = {L.Y[v], L.row_bytes};
-            parts[n++] = {L.q[v], L.row_bytes};
-            parts[n++] = {L.e[v], L.row_bytes};
+            parts[n++] = {L.a[v], L.row_bytes};
+            parts[n++] = {L.b[v][0], L.row_bytes};
+            parts[n++] = {L.b[v][1], L.row_bytes};
         }
+    } else {   // the rings (the AM4 bases live within one step only)
+        for (int v = 0; v < 3; v++) {
+            for (int k = 0; k < 3; k++) parts[n++] = {L.R[v][k], L.row_bytes};
+            if (v > 0)
+                for (int k = 0; k < 3; k++) parts[n++] = {L.Ph[v][k], L.row_bytes};
+        }
+    }
     return n;
 }
 
@@ -417,6 +441,7 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->gring = nullptr;
     s->ng = s->log_every = s->cap = s->nrec = s->head = 0;
     s->launches = 0;
+    s->ktab_dirty = 1;
     s->step = 0;
     s->cur = s->pcur = 0;
     s->ev_beg = s->ev_end = nullptr;
@@ -458,6 +483,7 @@ cel_status cel_set_boundary(cel_solver *s, int32_t side, const cel_bc *bc)
                 return fail(s, CEL_ERR_INVALID_ARG, "bad sine component");
     Side &S = s->bnd.s[side];
     memset(&S, 0, sizeof(S));
+    s->ktab_dirty = 1;
     S.type = bc->type;
     S.width = bc->width_cells;
     S.L = bc->width_cells * (side < 2 ? s->grid.dx : s->grid.dy);
@@ -519,6 +545,7 @@ cel_status cel_set_bathymetry(cel_solver *s, const void *z_dev)
     if (!s || !z_dev) return fail(s, CEL_ERR_INVALID_ARG, "NULL bathymetry");
     cel_status st = s->es == 4 ? derive_static<float>(s, z_dev) : derive_static<double>(s, z_dev);
     if (st != CEL_OK) return st;
+    s->ktab_dirty = 1;
     // raise w to the new bed in place, zero the discharge where now dry
     cudaError_t e = s->es == 4
                         ? launch_clamp_state<float>(s->geo, s->phy, s->at<float>(s->lay.Bc),
@@ -862,6 +889,7 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.gring = nullptr;
     s.ng = s.log_every = s.cap = s.nrec = s.head = 0;
     s.launches = 0;
+    s.ktab_dirty = 1;
     s.step = first_step;
     s.nh = 0;
     s.cur = s.pcur = 0;

@@ -120,11 +120,14 @@ struct StencilArgs {
     const real *Bc;
     const real *w_in, *P_in, *Qc_in;     // state (or AM4 iterate) at time t
     real *w_out, *U_out, *Vc_out;        // w^{n+1}, and the increments of U*, V*
-    real *a[3], *b[3];                   // AB3 carries (w, U, V), b = this slot
-    real *Y[3], *q[3], *e[3];            // AM4 carries (K > 0)
+    // K = 0: combined AB3 carries of (w, U, V), b = this step's slot
+    real *a[3], *b[3];
+    // K >= 1: rings of the right sides R (slots of R^n written, R^{n-1},
+    // R^{n-2}), of the mixed terms F*, G* (U, V only) and the AM4 bases Y
+    real *R0[3], *R1[3], *R2[3], *F0[3], *F1[3], *F2[3], *Y[3];
     uint32_t *mask_r, *mask_c;
     int kind;                            // kEuler0 | kEuler1 | kAB3 | kAM4
-    int keepK;                           // maintain the AM4 carries
+    int ring;                            // K >= 1: ring history (else carries)
     int final_stage;                     // last stage of the step: sponge on w
     int tsel;                            // ghost-table time: 0 = t^n, 1 = t^{n+1}
 };
@@ -181,12 +184,23 @@ template <typename real>
 cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, const real *Qc,
                                 unsigned long long *first_bad, cudaStream_t st);
 template <typename real>
-cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, double t0,
-                               double t1, real *tab, int npos, cudaStream_t st);
+cudaError_t launch_eckart_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, double *ktab,
+                                int npos, cudaStream_t st);
+template <typename real>
+cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r,
+                               const double *ktab, double t0, double t1, real *tab, int npos,
+                               cudaStream_t st);
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st);
+// The x-line and the y-line solves of one stage are independent (P from
+// the increment of U*, Q from that of V*) and run in one launch.
 template <typename real>
-cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st);
+struct LinePair {
+    LineArgs<real> L[2];
+};
+
+template <typename real>
+cudaError_t launch_lines(const LinePair<real> &a, cudaStream_t st);
 template <typename real>
 size_t line_smem_bytes(int n, int nseg);
 int line_segments(int n, int real_bytes);

@@ -49,10 +49,11 @@ __device__ __forceinline__ real desing(real h, real eps)
 template <typename real>
 __device__ __forceinline__ real minmod3(real th, real qm, real q0, real qp)
 {
+    // the three slopes share a sign iff the two one-sided ones do (the
+    // central one lies between them); then the one of least magnitude
     real a = th * (q0 - qm), b = real(0.5) * (qp - qm), c = th * (qp - q0);
-    if (a > real(0) && b > real(0) && c > real(0)) return fmin(a, fmin(b, c));
-    if (a < real(0) && b < real(0) && c < real(0)) return fmax(a, fmax(b, c));
-    return real(0);
+    real lo = fmin(a, fmin(b, c)), hi = fmax(a, fmax(b, c));
+    return lo > real(0) ? lo : (hi < real(0) ? hi : real(0));
 }
 
 // KP07 steps 1-2 for one cell along one direction: face values of (w, P, Q)
@@ -105,24 +106,8 @@ __device__ __forceinline__ void cu_flux(real g, real eps, real wL, real nL, real
     H[2] = (ap * (qnL * vL) - am * (qnR * vR) + apam * (qtR - qtL)) * inv;
 }
 
-// Sine-wave maker, Eq. 25-29, summed over components; double precision.
-__device__ inline void sine_ghost(const Side &s, double g, double dadj, double x, double y,
-                                  double t, double &eta, double &Pg, double &Qg)
-{
-    eta = Pg = Qg = 0.0;
-    if (!(dadj > 0.0)) return;
-    for (int m = 0; m < s.ncomp; m++) {
-        double om = s.omega[m];
-        double k0 = om * om / g;
-        double k = k0 * sqrt(1.0 / tanh(k0 * dadj));
-        double c = om / k;
-        double em = s.amp[m] * sin(om * t - k * s.cdir[m] * x - k * s.sdir[m] * y + s.phase[m]);
-        eta += em;
-        Pg += c * s.cdir[m] * em;
-        Qg += c * s.sdir[m] * em;
-    }
-}
-
+__device__ __forceinline__ float cbrt_r(float x) { return x > 0.f ? exp2f(__log2f(x) * (1.f / 3.f)) : 0.f; }
+__device__ __forceinline__ double cbrt_r(double x) { return cbrt(x); }
 __device__ __forceinline__ float cospi_r(float x) { return cospif(x); }
 __device__ __forceinline__ double cospi_r(double x) { return cospi(x); }
 
@@ -308,35 +293,78 @@ __global__ void k_check_finite(Geo g, const real *w, const real *P, const real *
     }
 }
 
-// Sine-maker ghosts (Eq. 25-29, Reading A-B4) for one step, in double: both
-// ghost layers of every sine side at t^n and t^{n+1}.  d is the still-water
-// depth of the adjacent interior cell (clamped along the side for the corner
-// columns of the south / north sides).
+// Adjacent still-water depth d and ghost coordinates of table position pos
+// (Reading A-B4): west / east sides run along rows j = pos - 2, south /
+// north sides along columns i = pos - 2 including the corner columns, where
+// d is clamped along the side.  Returns false where the position is unused.
 template <typename real>
-__global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r, double t0, double t1,
-                              real *__restrict__ tab, int npos)
+__device__ inline bool ghost_site(const Geo &g, const real *d_r, int side, int layer, int pos, double &x,
+                                  double &y, double &dadj)
 {
-    int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    int time = blockIdx.y & 1, layer = (blockIdx.y >> 1) & 1, side = blockIdx.y >> 2;
-    if (pos >= npos || b.s[side].type != kSine) return;
-    double eta = 0.0, Pg = 0.0, Qg = 0.0;
-    int along = pos - 2;
-    double x, y, dadj;
-    if (side < 2) {           // west / east: rows j
-        if (along < 0 || along >= g.ny) return;
-        int gi = side == 0 ? -1 - layer : g.nx + layer;
+    const int along = pos - 2;
+    if (side < 2) {
+        if (along < 0 || along >= g.ny) return false;
+        const int gi = side == 0 ? -1 - layer : g.nx + layer;
         x = (gi + 0.5) * g.dx;
         y = (along + 0.5) * g.dy;
         dadj = (double)d_r[(size_t)along * g.px + (side == 0 ? 0 : g.nx - 1)];
-    } else {                  // south / north: columns i, corners included
-        if (along < -2 || along > g.nx + 1) return;
-        int gj = side == 2 ? -1 - layer : g.ny + layer;
-        int ia = along < 0 ? 0 : (along > g.nx - 1 ? g.nx - 1 : along);
+    } else {
+        if (along < -2 || along > g.nx + 1) return false;
+        const int gj = side == 2 ? -1 - layer : g.ny + layer;
+        const int ia = along < 0 ? 0 : (along > g.nx - 1 ? g.nx - 1 : along);
         x = (along + 0.5) * g.dx;
         y = (gj + 0.5) * g.dy;
         dadj = (double)d_r[(size_t)(side == 2 ? 0 : g.ny - 1) * g.px + ia];
     }
-    sine_ghost(b.s[side], p.g, dadj, x, y, time ? t1 : t0, eta, Pg, Qg);
+    return true;
+}
+
+// Eckart wave number (Eq. 29) per sine side, position and component, from
+// the static depths; 0 where the adjacent cell is dry.  Rebuilt when a
+// boundary or the bed changes.
+template <typename real>
+__global__ void k_eckart_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r, double *__restrict__ ktab,
+                               int npos)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x, side = blockIdx.y;
+    if (pos >= npos || b.s[side].type != kSine) return;
+    double x, y, dadj;
+    bool used = ghost_site(g, d_r, side, 0, pos, x, y, dadj);
+    for (int m = 0; m < 8; m++) {
+        double k = 0.0;
+        if (used && m < b.s[side].ncomp && dadj > 0.0) {
+            double om = b.s[side].omega[m];
+            double k0 = om * om / p.g;
+            k = k0 * sqrt(1.0 / tanh(k0 * dadj));
+        }
+        ktab[((size_t)side * npos + pos) * 8 + m] = k;
+    }
+}
+
+// Sine-maker ghosts (Eq. 25-28) for one step, in double: both ghost layers of
+// every sine side at t^n and t^{n+1}, summed over components.
+template <typename real>
+__global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r,
+                              const double *__restrict__ ktab, double t0, double t1, real *__restrict__ tab,
+                              int npos)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    int time = blockIdx.y & 1, layer = (blockIdx.y >> 1) & 1, side = blockIdx.y >> 2;
+    if (pos >= npos || b.s[side].type != kSine) return;
+    double x, y, dadj;
+    if (!ghost_site(g, d_r, side, layer, pos, x, y, dadj)) return;
+    const Side &S = b.s[side];
+    const double t = time ? t1 : t0;
+    double eta = 0.0, Pg = 0.0, Qg = 0.0;
+    for (int m = 0; m < S.ncomp; m++) {
+        const double k = ktab[((size_t)side * npos + pos) * 8 + m];
+        if (!(k > 0.0)) continue;
+        const double om = S.omega[m], c = om / k;
+        const double em = S.amp[m] * sin(om * t - k * S.cdir[m] * x - k * S.sdir[m] * y + S.phase[m]);
+        eta += em;
+        Pg += c * S.cdir[m] * em;
+        Qg += c * S.sdir[m] * em;
+    }
     tab[ghost_index(time, side, layer, 0, pos, npos)] = real(p.ws + eta);
     tab[ghost_index(time, side, layer, 1, pos, npos)] = real(Pg);
     tab[ghost_index(time, side, layer, 2, pos, npos)] = real(Qg);
@@ -373,65 +401,90 @@ struct StencilSmem {
 // only (X0 = 0): the line solves find P^{n+1} - P^n from the increment of U*,
 // which equals recomputing U*^n from P^n by Eq. 23 but keeps the rounding
 // relative to the increment instead of to P.
+// History of one unknown (w, U* or V*) for the update of Sec. 2.3, with R
+// its right side and Phi its mixed term (0 for w); the AB3 and AM4 stages
+// return the increment X^{n+1} - X^n (for the AM4 stage of w: w^{n+1}).
+//
+// K = 0 (predictor only): two combined carries per unknown,
+//   a = -16 (dt/12) R^{n-1} - 3 Phi^{n-1}        (in place)
+//   b = 5 (dt/12) R^{n-2} + Phi^{n-2}            (two slots, by step parity)
+// so Eq. 15-17 read X^{n+1} - X^n = 23 (dt/12) R^n + 2 Phi^n + a + b, with
+// 2 reads and 2 writes per unknown.  The first two steps are forward Euler;
+// the second adds Phi^1 - Phi^0, for which `a` holds Phi^0 after the first.
+//
+// K >= 1: rings of R and Phi (three slots each) as Eq. 15-20 write them,
+// and the corrector base
+//   Y = X0 + (dt/24)(19 R^n - 5 R^{n-1} + R^{n-2}) - Phi^n
+// (X0 = w^n for w, 0 for U*, V*), so that Eq. 18-20 read
+// X^{n+1} - X0 = Y - X0 + 9 (dt/24) R^{n+1} + Phi^{n+1}.
+//
+// U* and V* are carried as increments only: the line solves find
+// P^{n+1} - P^n from the increment of U*, which equals recomputing U*^n from
+// P^n by Eq. 23 but keeps the rounding relative to the increment.
 template <typename real>
 struct Carry {
-    real a, b, q, e, Y;
+    real a, b, r1, r2, p1, p2, Y;
 };
 
-// The carries a stage reads, loaded at the top of a cell's iteration so the
+// The history a stage reads, loaded at the top of a cell's iteration so the
 // loads are in flight while the cell's right side is computed.
 template <typename real>
-__device__ __forceinline__ Carry<real> load_carry(int kind, int keepK, size_t k, const real *a, const real *b,
-                                                  const real *Y, const real *q, const real *e)
+__device__ __forceinline__ Carry<real> load_carry(const StencilArgs<real> &A, int v, size_t k)
 {
     Carry<real> c;
-    c.a = c.b = c.q = c.e = c.Y = real(0);
-    if (kind == kAM4) {
-        c.Y = Y[k];
-    } else if (kind == kEuler1) {
-        c.a = a[k];
-        if (keepK) c.e = e[k];
-    } else if (kind == kAB3) {
-        c.a = a[k];
-        c.b = b[k];
-        if (keepK) {
-            c.q = q[k];
-            c.e = e[k];
+    c.a = c.b = c.r1 = c.r2 = c.p1 = c.p2 = c.Y = real(0);
+    if (A.kind == kAM4) {
+        c.Y = A.Y[v][k];
+    } else if (A.ring) {
+        if (A.kind == kAB3) {
+            c.r1 = A.R1[v][k];
+            c.r2 = A.R2[v][k];
         }
+        if (v > 0 && A.kind != kEuler0) {
+            c.p1 = A.F1[v][k];
+            if (A.kind == kAB3) c.p2 = A.F2[v][k];
+        }
+    } else if (A.kind == kEuler1) {
+        c.a = A.a[v][k];
+    } else if (A.kind == kAB3) {
+        c.a = A.a[v][k];
+        c.b = A.b[v][k];
     }
     return c;
 }
 
 template <typename real>
-__device__ __forceinline__ real advance(int kind, int keepK, real X0, real R, real Phi, real dt, size_t k,
-                                        const Carry<real> &c, real *a, real *b, real *Y, real *q, real *e)
+__device__ __forceinline__ real advance(const StencilArgs<real> &A, int v, real X0, real R, real Phi, size_t k,
+                                        const Carry<real> &c)
 {
-    const real c12 = dt / real(12), c24 = dt / real(24);
-    if (kind == kAM4) return c.Y + real(9) * c24 * R + Phi;
-    real D;
-    if (kind == kEuler0) {
-        D = dt * R;
-        a[k] = Phi;
-        b[k] = real(5) * c12 * R + Phi;
-        if (keepK) e[k] = c24 * R;
-    } else if (kind == kEuler1) {
-        D = dt * R + (Phi - c.a);
-        a[k] = real(-16) * c12 * R - real(3) * Phi;
-        b[k] = real(5) * c12 * R + Phi;
-        if (keepK) {
-            q[k] = real(-5) * c24 * R + c.e;
-            e[k] = c24 * R;
+    const real dt = A.c.dt, c12 = dt / real(12), c24 = dt / real(24);
+    if (A.kind == kAM4) return c.Y + real(9) * c24 * R + Phi;
+    if (A.ring) {
+        real D;
+        if (A.kind == kEuler0) {
+            D = dt * R;
+        } else if (A.kind == kEuler1) {
+            D = dt * R + (Phi - c.p1);
+        } else {
+            D = c12 * (real(23) * R - real(16) * c.r1 + real(5) * c.r2) + real(2) * Phi - real(3) * c.p1 + c.p2;
+            A.Y[v][k] = X0 + c24 * (real(19) * R - real(5) * c.r1 + c.r2) - Phi;
         }
+        A.R0[v][k] = R;
+        if (v > 0) A.F0[v][k] = Phi;
+        return D;
+    }
+    real D;
+    if (A.kind == kEuler0) {
+        D = dt * R;
+        A.a[v][k] = Phi;
+    } else if (A.kind == kEuler1) {
+        D = dt * R + (Phi - c.a);
+        A.a[v][k] = real(-16) * c12 * R - real(3) * Phi;
     } else {
         D = real(23) * c12 * R + real(2) * Phi + (c.a + c.b);
-        if (keepK) {
-            Y[k] = X0 + real(19) * c24 * R - Phi + c.q;
-            q[k] = real(-5) * c24 * R + c.e;
-            e[k] = c24 * R;
-        }
-        a[k] = real(-16) * c12 * R - real(3) * Phi;
-        b[k] = real(5) * c12 * R + Phi;
+        A.a[v][k] = real(-16) * c12 * R - real(3) * Phi;
     }
+    A.b[v][k] = real(5) * c12 * R + Phi;
     return D;
 }
 
@@ -654,9 +707,9 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
         const size_t kr = (size_t)j * G.px + i;
         Carry<real> cw, cu, cv;
         if (valid) {
-            cw = load_carry(A.kind, A.keepK, kr, A.a[0], A.b[0], A.Y[0], A.q[0], A.e[0]);
-            cu = load_carry(A.kind, A.keepK, kr, A.a[1], A.b[1], A.Y[1], A.q[1], A.e[1]);
-            cv = load_carry(A.kind, A.keepK, kr, A.a[2], A.b[2], A.Y[2], A.q[2], A.e[2]);
+            cw = load_carry(A, 0, kr);
+            cu = load_carry(A, 1, kr);
+            cv = load_carry(A, 2, kr);
         }
         const real *cb = sm.Bc + (cy + 1) * kCornerStride + cx + 1;
         real c00 = cb[0], c10 = cb[1], c01 = cb[kCornerStride], c11 = cb[kCornerStride + 1];
@@ -672,7 +725,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
                   g * hb * (ByN - ByS) * rdy;
         if (A.phy.friction != kFricNone) {   // Eq. 31-32 with the Eq. 14 device
             real hinv = desing(fmax(hb, real(0)), eps);
-            real fc = A.phy.friction == kFricManning ? C.fric * cbrt(hinv) : C.fric;
+            real fc = A.phy.friction == kFricManning ? C.fric * cbrt_r(hinv) : C.fric;
             real mag = sqrt(P0 * P0 + Q0 * Q0);
             F -= fc * P0 * mag * hinv * hinv;
             Gq -= fc * Q0 * mag * hinv * hinv;
@@ -685,10 +738,11 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
             const real ddy = (sm.d[od + kDStride] - sm.d[od - kDStride]) * C.hrdy;
             const real *W = sm.w + o;
             const int S1 = kStride, S2 = 2 * kStride;
-            real e00 = W[0] - ws;
-            real eE = W[1] - ws, eW = W[-1] - ws, eN = W[S1] - ws, eS = W[-S1] - ws;
-            real eEE = W[2] - ws, eWW = W[-2] - ws, eNN = W[S2] - ws, eSS = W[-S2] - ws;
-            real eNE = W[S1 + 1] - ws, eNW = W[S1 - 1] - ws, eSE = W[-S1 + 1] - ws, eSW = W[-S1 - 1] - ws;
+            // eta = w - w_s enters only through differences, where w_s cancels
+            real e00 = W[0];
+            real eE = W[1], eW = W[-1], eN = W[S1], eS = W[-S1];
+            real eEE = W[2], eWW = W[-2], eNN = W[S2], eSS = W[-S2];
+            real eNE = W[S1 + 1], eNW = W[S1 - 1], eSE = W[-S1 + 1], eSW = W[-S1 - 1];
             real exx = (eE - real(2) * e00 + eW) * rdx2;
             real eyy = (eN - real(2) * e00 + eS) * rdy2;
             real exy = (eNE - eSE - eNW + eSW) * rdxdy4;
@@ -708,10 +762,10 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
         }
         real w1 = w0, dU = real(0), dV = real(0);
         if (valid) {
-            real dw = advance(A.kind, A.keepK, w0, E, real(0), dt, kr, cw, A.a[0], A.b[0], A.Y[0], A.q[0], A.e[0]);
+            real dw = advance(A, 0, w0, E, real(0), kr, cw);
             w1 = A.kind == kAM4 ? dw : w0 + dw;   // the AM4 base of w holds w^n
-            dU = advance(A.kind, A.keepK, real(0), F, Fs, dt, kr, cu, A.a[1], A.b[1], A.Y[1], A.q[1], A.e[1]);
-            dV = advance(A.kind, A.keepK, real(0), Gq, Gs, dt, kr, cv, A.a[2], A.b[2], A.Y[2], A.q[2], A.e[2]);
+            dU = advance(A, 1, real(0), F, Fs, kr, cu);
+            dV = advance(A, 2, real(0), Gq, Gs, kr, cv);
             if (w1 < Bb) w1 = Bb;   // Reading A-D1
             if (A.final_stage) {
                 real gam = sponge_gamma<real>(C, G, i, j);
@@ -758,12 +812,17 @@ __device__ __forceinline__ int seg_slot(int k, int mshift, int sp)
     return (k & ((1 << mshift) - 1)) * sp + (k >> mshift);
 }
 
-template <typename real>
-__global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
+template <typename real, int M>
+__global__ void __launch_bounds__(1024) k_lines(LinePair<real> PA)
 {
+    // blocks [0, ny) solve x-rows, the rest y-columns
+    const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
+    const LineArgs<real> &A = PA.L[fam];
+    const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n, S = A.nseg, N2 = 2 * S;
-    const int mshift = A.mshift, m = 1 << mshift, sp = A.sp;
+    constexpr int m = M;                             // rows per segment
+    const int mshift = A.mshift, sp = A.sp;
     const int npad = S * m;                          // lines padded with identity rows
     real *sA = reinterpret_cast<real *>(smem_raw);   // d, then alpha / alpha-hat
     real *sC = sA + m * sp;                          // gamma / gamma-hat
@@ -777,7 +836,7 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
     const bool lo_sine = (A.c.sine >> lo_side) & 1, hi_sine = (A.c.sine >> hi_side) & 1;
     const int gvar = A.dir == 0 ? 1 : 2;   // ghost discharge: P on x-lines, Q on y-lines
 
-    for (int line = blockIdx.x; line < A.nlines; line += gridDim.x) {
+    {
         const real *rhs = A.rhs + (size_t)line * A.pitch;
         const real *dl = A.d + (size_t)line * A.pitch;
         for (int k = tid; k < npad; k += T) {
@@ -801,6 +860,7 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
         if (act) {
             // forward: rows f+1..l as alpha x_f + x_k + gamma x_{k+1} = rho
             real dprev = dm, ap = 0, gp = 0, rp = 0;
+#pragma unroll
             for (int j = 0; j < m; j++) {
                 const int k = f + j, q = j * sp + tid;
                 real dnext = j + 1 < m ? (k + 1 < n ? sA[q + sp] : dlast) : dp;
@@ -857,6 +917,7 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
             }
             // backward: rows l-2..f+1 as x_k = rho^ - alpha^ x_f - gamma^ x_l
             real ah = sA[(m - 2) * sp + tid], gh = sC[(m - 2) * sp + tid], rhh = sR[(m - 2) * sp + tid];
+#pragma unroll
             for (int j = m - 3; j >= 1; j--) {
                 const int q = j * sp + tid;
                 real ga = sC[q];
@@ -925,6 +986,7 @@ __global__ void __launch_bounds__(1024) k_lines(LineArgs<real> A)
         }
         if (act) {
             real xf = rr[2 * tid] / rb[2 * tid], xl = rr[2 * tid + 1] / rb[2 * tid + 1];
+#pragma unroll
             for (int j = 1; j < m - 1; j++) {
                 const int q = j * sp + tid;
                 sR[q] = sR[q] - sA[q] * xf - sC[q] * xl;
@@ -1038,10 +1100,18 @@ cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, cons
 }
 
 template <typename real>
-cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, double t0, double t1,
-                               real *tab, int npos, cudaStream_t st)
+cudaError_t launch_eckart_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, double *ktab, int npos,
+                                cudaStream_t st)
 {
-    k_ghost_table<real><<<dim3((npos + 127) / 128, 16), 128, 0, st>>>(g, p, b, d_r, t0, t1, tab, npos);
+    k_eckart_table<real><<<dim3((npos + 127) / 128, 4), 128, 0, st>>>(g, p, b, d_r, ktab, npos);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, const double *ktab,
+                               double t0, double t1, real *tab, int npos, cudaStream_t st)
+{
+    k_ghost_table<real><<<dim3((npos + 127) / 128, 16), 128, 0, st>>>(g, p, b, d_r, ktab, t0, t1, tab, npos);
     return cudaGetLastError();
 }
 
@@ -1086,20 +1156,39 @@ size_t line_smem_bytes(int n, int nseg)
 }
 
 template <typename real>
-cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st)
+cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
 {
-    static int configured_bytes = 0;
-    const size_t smem = line_smem_bytes<real>(a.n, a.nseg);
-    if ((int)smem > configured_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_lines<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_bytes = (int)smem;
+    size_t smem = 0;
+    int threads = 64;
+    const bool both = p.L[0].nlines > 0 && p.L[1].nlines > 0;
+    if (both && p.L[0].mshift != p.L[1].mshift) {   // one segment length per launch
+        LinePair<real> a = p, b = p;
+        a.L[1].nlines = 0;
+        b.L[0].nlines = 0;
+        cudaError_t e = launch_lines<real>(a, st);
+        return e != cudaSuccess ? e : launch_lines<real>(b, st);
     }
-    int threads = round_up(a.nseg, 32);
-    if (threads < 64) threads = 64;
-    if (a.nseg * (1 << a.mshift) < a.n || a.sp != line_seg_stride(a.nseg)) return cudaErrorInvalidValue;
-    k_lines<real><<<a.nlines, threads, smem, st>>>(a);
+    for (int f = 0; f < 2; f++) {
+        const LineArgs<real> &a = p.L[f];
+        if (a.nlines <= 0) continue;
+        if (a.nseg * (1 << a.mshift) < a.n || a.sp != line_seg_stride(a.nseg)) return cudaErrorInvalidValue;
+        size_t b = line_smem_bytes<real>(a.n, a.nseg);
+        if (b > smem) smem = b;
+        int t = round_up(a.nseg, 32);
+        if (t > threads) threads = t;
+    }
+    static int configured[6] = {0, 0, 0, 0, 0, 0};
+    const int sh = p.L[0].nlines > 0 ? p.L[0].mshift : p.L[1].mshift;
+    auto *kern = sh == 1 ? k_lines<real, 2> : sh == 2 ? k_lines<real, 4> : sh == 3 ? k_lines<real, 8>
+                                          : sh == 4 ? k_lines<real, 16> : k_lines<real, 32>;
+    if (sh < 1 || sh > 5) return cudaErrorInvalidValue;
+    if ((int)smem > configured[sh]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[sh] = (int)smem;
+    }
+    const int blocks = p.L[0].nlines + p.L[1].nlines;
+    if (blocks > 0) kern<<<blocks, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -1124,10 +1213,13 @@ cudaError_t launch_lines(const LineArgs<real> &a, cudaStream_t st)
                                              int, real *, cudaStream_t);                                \
     template cudaError_t launch_check_finite<real>(const Geo &, const real *, const real *, const real *, \
                                                    unsigned long long *, cudaStream_t);                 \
+    template cudaError_t launch_eckart_table<real>(const Geo &, const Phys &, const Bnd &, const real *,  \
+                                                   double *, int, cudaStream_t);                        \
     template cudaError_t launch_ghost_table<real>(const Geo &, const Phys &, const Bnd &, const real *,   \
-                                                  double, double, real *, int, cudaStream_t);           \
+                                                  const double *, double, double, real *, int,          \
+                                                  cudaStream_t);                                        \
     template cudaError_t launch_stencil<real>(const StencilArgs<real> &, cudaStream_t);                  \
-    template cudaError_t launch_lines<real>(const LineArgs<real> &, cudaStream_t);                       \
+    template cudaError_t launch_lines<real>(const LinePair<real> &, cudaStream_t);                       \
     template size_t line_smem_bytes<real>(int, int);
 
 CEL_INSTANTIATE(float)
