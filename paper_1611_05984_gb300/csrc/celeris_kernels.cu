@@ -492,43 +492,77 @@ template <typename real> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
-// Stage rows of a row-major field into a shared tile: `rows` rows of `cols`
-// elements starting at column gx0 (even) of row gy0, with pairs loaded as one
-// aligned vector where both elements are inside [0, lim_x) x [0, lim_y).
+// One tile to stage: `rows` rows of `cols` elements starting at column gx0
+// (even) of row gy0 of a field with row pitch `pitch`, elements outside
+// [0, lim_x) x [0, lim_y) read as 0; `transpose` stores element (r, c) at
+// dst[c * dstride + r].
 template <typename real>
-__device__ __forceinline__ void stage_rows(const real *src, size_t pitch, int gx0, int gy0, int rows, int cols,
-                                           int lim_x, int lim_y, real *dst, int dstride, int tid, int nthreads,
-                                           bool transpose)
+struct StageSpec {
+    const real *src;
+    size_t pitch;
+    int gx0, gy0, rows, cols, lim_x, lim_y;
+    real *dst;
+    int dstride;
+    bool transpose;
+};
+
+// Stage several tiles with every global load of a thread issued before any
+// of its shared-memory stores, so the loads' latencies overlap (a load-store
+// loop would pay one full latency per element pair).  Pairs are loaded as
+// one aligned vector where both elements are inside the field.
+template <typename real, int NT, int MAXP>
+__device__ __forceinline__ void stage_tiles(const StageSpec<real> *sp, int tid)
 {
     using real2 = typename Vec2<real>::type;
-    const int pairs = (cols + 1) >> 1;
-    for (int k = tid; k < rows * pairs; k += nthreads) {
-        const int r = k / pairs, c = 2 * (k - r * pairs);
-        const int gy = gy0 + r, gx = gx0 + c;
-        real v0 = real(0), v1 = real(0);
-        if (gy >= 0 && gy < lim_y) {
-            const real *row = src + (size_t)gy * pitch;
-            if (gx >= 0 && gx + 1 < lim_x) {
-                real2 v = *reinterpret_cast<const real2 *>(row + gx);
-                v0 = v.x;
-                v1 = v.y;
-            } else {
-                if (gx >= 0 && gx < lim_x) v0 = row[gx];
-                if (gx + 1 >= 0 && gx + 1 < lim_x) v1 = row[gx + 1];
+    real v0[NT][MAXP], v1[NT][MAXP];
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        const StageSpec<real> &S = sp[t];
+        const int pairs = (S.cols + 1) >> 1;
+#pragma unroll
+        for (int u = 0; u < MAXP; u++) {
+            const int k = tid + u * kStencilThreads;
+            v0[t][u] = v1[t][u] = real(0);
+            if (k < S.rows * pairs) {
+                const int r = k / pairs, c = 2 * (k - r * pairs);
+                const int gy = S.gy0 + r, gx = S.gx0 + c;
+                if (gy >= 0 && gy < S.lim_y) {
+                    const real *row = S.src + (size_t)gy * S.pitch;
+                    if (gx >= 0 && gx + 1 < S.lim_x) {
+                        real2 v = *reinterpret_cast<const real2 *>(row + gx);
+                        v0[t][u] = v.x;
+                        v1[t][u] = v.y;
+                    } else {
+                        if (gx >= 0 && gx < S.lim_x) v0[t][u] = row[gx];
+                        if (gx + 1 >= 0 && gx + 1 < S.lim_x) v1[t][u] = row[gx + 1];
+                    }
+                }
             }
         }
-        if (transpose) {
-            dst[c * dstride + r] = v0;
-            if (c + 1 < cols) dst[(c + 1) * dstride + r] = v1;
-        } else {
-            dst[r * dstride + c] = v0;
-            if (c + 1 < cols) dst[r * dstride + c + 1] = v1;
+    }
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        const StageSpec<real> &S = sp[t];
+        const int pairs = (S.cols + 1) >> 1;
+#pragma unroll
+        for (int u = 0; u < MAXP; u++) {
+            const int k = tid + u * kStencilThreads;
+            if (k < S.rows * pairs) {
+                const int r = k / pairs, c = 2 * (k - r * pairs);
+                if (S.transpose) {
+                    S.dst[c * S.dstride + r] = v0[t][u];
+                    if (c + 1 < S.cols) S.dst[(c + 1) * S.dstride + r] = v1[t][u];
+                } else {
+                    S.dst[r * S.dstride + c] = v0[t][u];
+                    if (c + 1 < S.cols) S.dst[r * S.dstride + c + 1] = v1[t][u];
+                }
+            }
         }
     }
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A)
+__global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_stencil(StencilArgs<real> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StencilSmem<real> &sm = *reinterpret_cast<StencilSmem<real> *>(smem_raw);
@@ -541,16 +575,17 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
     const real th = C.theta;
 
     // ---- 1. stage the state tile (+2 halo) and the bed corners; Q is
-    //         column-major, so its tile is staged along y and transposed
-    stage_rows(A.w_in, G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.w, kStride, tid,
-               kStencilThreads, false);
-    stage_rows(A.P_in, G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.P, kStride, tid,
-               kStencilThreads, false);
-    stage_rows(A.Qc_in, G.py, y0 - kHalo, x0 - kHalo, kTileIn, kTileIn, ny, nx, sm.Q, kStride, tid,
-               kStencilThreads, true);
-    // corners: array index (corner + 1) in [0, nx + 2] x [0, ny + 2]
-    stage_rows(A.Bc, G.pc, x0, y0, kCorner, kCorner, nx + 3, ny + 3, sm.Bc, kCornerStride, tid,
-               kStencilThreads, false);
+    //         column-major, so its tile is staged along y and transposed.
+    //         Corners: array index (corner + 1) in [0, nx + 2] x [0, ny + 2].
+    {
+        const StageSpec<real> spec[4] = {
+            {A.w_in, (size_t)G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.w, kStride, false},
+            {A.P_in, (size_t)G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.P, kStride, false},
+            {A.Qc_in, (size_t)G.py, y0 - kHalo, x0 - kHalo, kTileIn, kTileIn, ny, nx, sm.Q, kStride, true},
+            {A.Bc, (size_t)G.pc, x0, y0, kCorner, kCorner, nx + 3, ny + 3, sm.Bc, kCornerStride, false}};
+        // 36 x 18 pairs per state tile: at most 3 per thread
+        stage_tiles<real, 4, (kTileIn * (kTileIn / 2) + kStencilThreads - 1) / kStencilThreads>(spec, tid);
+    }
     if (tid < kTile) sm.colbits[tid] = 0u;
     __syncthreads();
 
@@ -699,17 +734,33 @@ __global__ void __launch_bounds__(kStencilThreads) k_stencil(StencilArgs<real> A
     const real Bd = C.Bd, B3 = C.B3, sixth = C.sixth;
     const bool bsnq = A.phy.model == kBsnq;
     const int lane = tid & 31;
-    for (int rr = 0; rr < kTile / (kStencilThreads / 32); rr++) {
+    constexpr int kRows = kTile / (kStencilThreads / 32);   // rows per thread
+    Carry<real> nw, nu, nv;                                  // next row's carries
+    {
+        const int i = x0 + lane, j = y0 + (tid >> 5);
+        if (i < nx && j < ny) {
+            const size_t kr = (size_t)j * G.px + i;
+            nw = load_carry(A, 0, kr);
+            nu = load_carry(A, 1, kr);
+            nv = load_carry(A, 2, kr);
+        }
+    }
+#pragma unroll 1
+    for (int rr = 0; rr < kRows; rr++) {
         const int cx = lane, cy = (tid >> 5) + rr * (kStencilThreads / 32);
         const int i = x0 + cx, j = y0 + cy;
         const bool valid = i < nx && j < ny;
         const int o = (cy + kHalo) * kStride + cx + kHalo;
         const size_t kr = (size_t)j * G.px + i;
-        Carry<real> cw, cu, cv;
-        if (valid) {
-            cw = load_carry(A, 0, kr);
-            cu = load_carry(A, 1, kr);
-            cv = load_carry(A, 2, kr);
+        const Carry<real> cw = nw, cu = nu, cv = nv;
+        if (rr + 1 < kRows) {   // issue the next row's loads before this row's arithmetic
+            const int jn = j + kStencilThreads / 32;
+            if (i < nx && jn < ny) {
+                const size_t kn = (size_t)jn * G.px + i;
+                nw = load_carry(A, 0, kn);
+                nu = load_carry(A, 1, kn);
+                nv = load_carry(A, 2, kn);
+            }
         }
         const real *cb = sm.Bc + (cy + 1) * kCornerStride + cx + 1;
         real c00 = cb[0], c10 = cb[1], c01 = cb[kCornerStride], c11 = cb[kCornerStride + 1];
