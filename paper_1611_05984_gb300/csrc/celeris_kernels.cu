@@ -864,7 +864,7 @@ __device__ __forceinline__ int seg_slot(int k, int mshift, int sp)
 }
 
 template <typename real, int M>
-__global__ void __launch_bounds__(1024) k_lines(LinePair<real> PA)
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(LinePair<real> PA)
 {
     // blocks [0, ny) solve x-rows, the rest y-columns
     const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
@@ -879,6 +879,7 @@ __global__ void __launch_bounds__(1024) k_lines(LinePair<real> PA)
     real *sC = sA + m * sp;                          // gamma / gamma-hat
     real *sR = sC + m * sp;                          // rhs -> rho -> rho-hat -> x
     real *ra = sR + m * sp, *rb = ra + N2, *rc = rb + N2, *rr = rc + N2;
+    uint32_t *smask = reinterpret_cast<uint32_t *>(rr + N2);   // dry bits of the line
     const int tid = threadIdx.x, T = blockDim.x;
     const Geo &G = A.geo;
     const real rh2 = A.rh2, hrh = A.hrh, srh = A.srh;
@@ -890,6 +891,21 @@ __global__ void __launch_bounds__(1024) k_lines(LinePair<real> PA)
     {
         const real *rhs = A.rhs + (size_t)line * A.pitch;
         const real *dl = A.d + (size_t)line * A.pitch;
+        // P^n (or Q^n) of the elements this thread writes in the epilogue,
+        // loaded now so the loads complete during the elimination
+        constexpr int kMaxOwn = M;   // elements per thread: ceil(n / T) <= M since T >= nseg
+        real own[kMaxOwn];
+        {
+            const real *bs = A.base + (size_t)line * A.pitch;
+#pragma unroll
+            for (int u = 0; u < kMaxOwn; u++) {
+                const int k = tid + u * T;
+                own[u] = k < n ? bs[k] : real(0);
+            }
+        }
+        const uint32_t *mw = A.mask + (size_t)line * A.nwords;
+        for (int k = tid; k < A.nwords; k += T) smask[k] = mw[k];
+#pragma unroll 4
         for (int k = tid; k < npad; k += T) {
             const int q = seg_slot(k, mshift, sp);
             sR[q] = k < n ? rhs[k] : real(0);
@@ -1047,20 +1063,21 @@ __global__ void __launch_bounds__(1024) k_lines(LinePair<real> PA)
         }
         __syncthreads();
         }
-        // epilogue: sponge (Eq. 30) on the last stage, zero discharge where dry
-        const uint32_t *mw = A.mask + (size_t)line * A.nwords;
-        const real *bs = A.base + (size_t)line * A.pitch;
+        // epilogue: P^n + increment, sponge (Eq. 30) on the last stage, zero
+        // discharge where dry
         real *out = A.sol + (size_t)line * A.pitch;
-        for (int k = tid; k < n; k += T) {
-            real v = bs[k] + sR[seg_slot(k, mshift, sp)];
+#pragma unroll
+        for (int u = 0; u < kMaxOwn; u++) {
+            const int k = tid + u * T;
+            if (k >= n) continue;
+            real v = own[u] + sR[seg_slot(k, mshift, sp)];
             if (A.final_stage) {
                 int i = A.dir == 0 ? k : line, j = A.dir == 0 ? line : k;
                 v *= sponge_gamma<real>(A.c, G, i, j);
             }
-            if ((mw[k >> 5] >> (k & 31)) & 1u) v = real(0);
+            if ((smask[k >> 5] >> (k & 31)) & 1u) v = real(0);
             out[k] = v;
         }
-        __syncthreads();
     }
 }
 
@@ -1184,9 +1201,10 @@ cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
 
 int line_seg_shift(int n, int real_bytes)
 {
-    // 16 rows per segment (32 for long FP64 lines, to fit shared memory),
-    // fewer for short lines so that there are at least 2 segments of >= 2 rows
-    int sh = (real_bytes == 8 && n > 4096) ? 5 : 4;
+    // 16 rows per segment (32 for lines above 8192 FP32 / 4096 FP64 rows, so
+    // that a line has at most 512 segments and fits shared memory), fewer for
+    // short lines so that there are at least 2 segments of >= 2 rows
+    int sh = n > (real_bytes == 8 ? 4096 : 8192) ? 5 : 4;
     while (sh > 1 && (n >> sh) < 2) sh--;
     return sh;
 }
@@ -1203,7 +1221,8 @@ template <typename real>
 size_t line_smem_bytes(int n, int nseg)
 {
     const int m = 1 << line_seg_shift(n, (int)sizeof(real));
-    return sizeof(real) * ((size_t)3 * m * line_seg_stride(nseg) + (size_t)8 * nseg);
+    return sizeof(real) * ((size_t)3 * m * line_seg_stride(nseg) + (size_t)8 * nseg) +
+           sizeof(uint32_t) * (size_t)((n + 31) / 32);
 }
 
 template <typename real>
