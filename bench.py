@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="beach2048", choices=["beach2048", "beach8192", "beach512"])
+    ap.add_argument("--workload", default="beach2048",
+                    choices=["beach2048", "beach8192", "beach512", "ensemble256"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -59,7 +60,9 @@ def workload(name):
         return sc.beach(nx=2048, ny=2048)
     if name == "beach8192":
         return sc.beach_directional(nx=8192, ny=8192)
-    return sc.beach(nx=512, ny=512, sponge=20)
+    if name == "beach512":
+        return sc.beach(nx=512, ny=512, sponge=20)
+    raise ValueError(f"{name} is not a single-grid workload")
 
 
 def peaks():
@@ -182,6 +185,10 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    if args.workload == "ensemble256":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no ensemble mode; "
+                          "its arm runs the single-grid workloads"}), flush=True)
+        return
     s = workload(args.workload)
     rows = _sample_rows(s, 120.0 / (args.steps + args.warmup + 2))
     c = _row_crop(s, rows)
@@ -205,10 +212,87 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args):
+    """The 256-scenario ensemble (uneven beaches of 128..1024 x 128..512
+    cells, about 4.8e7 cells in all, FP32 by default): cell-updates/s of the
+    ensemble step (one launch per kernel kind and stage over all members)
+    against the same members stepped one cel_step per scenario in turn, both
+    timed with CUDA events on the one stream, after the same warm-up."""
+    import torch
+
+    from paper_1611_05984_gb300 import celeris
+    from paper_1611_05984_gb300 import scenarios as sc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dtype = torch.float32 if args.precision == "f32" else torch.float64
+    es = 4 if args.precision == "f32" else 8
+    scens = sc.ensemble()
+    members = [celeris.from_scenario(s, dtype=dtype) for s in scens]
+    cells = sum(s.cells for s in scens)
+    stream = members[0].stream
+    ens = celeris.Ensemble(members, stream=stream)
+    ens.step(args.warmup)
+    for m in members:                      # the same warm-up for the one-at-a-time loop's kernels
+        m.step(1)
+    ens.step(1)                            # back in lockstep (warm-up + 1 steps each)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.4)
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        ens.step(1)
+        launches += ens.last_launch_count()
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    single_launches = 0
+    for _ in range(args.steps):
+        for m in members:
+            m.step(1)
+            single_launches += m.last_launch_count()
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_ens, ms_one = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    finite = all(m.check_finite() for m in members)
+    value = cells * args.steps / (ms_ens / 1e3)
+    one = cells * args.steps / (ms_one / 1e3)
+    peak, peak_src = peaks()
+    # algorithmic bytes of a step over all members (the per-cell values of
+    # the single-grid kernels: predictor + corrector stencil, two line stages)
+    K = scens[0].K
+    per_cell = ((VALUES["stencil_pred_k"] if K > 0 else VALUES["stencil_pred_0"]) + K * VALUES["stencil_corr"]
+                + (K + 1) * VALUES["lines"])
+    gbs = cells * es * per_cell * args.steps / (ms_ens / 1e3) / 1e9
+    line = {"metric": "ensemble cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ens / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": "ensemble256", "members": len(scens), "cells": cells,
+                       "corrector_iters": K, "parallelism": "replicas1",
+                       "l2": "inputs larger than L2 (%.1f GB of workspaces)"
+                             % (sum(m.workspace.numel() for m in members) / 1e9)},
+            "single_launch": {"value": one, "ms_per_step": ms_one / args.steps,
+                              "what": "the same members, one cel_step per member in turn",
+                              "gpu_launches": single_launches},
+            "speedup_vs_single_launch": value / one,
+            "roofline": {"bound": "hbm", "kernel": "whole ensemble step", "achieved": gbs, "peak": peak,
+                         "unit": "GB/s", "frac": gbs / peak, "traffic": None, "peak_source": peak_src},
+            "finite": finite, "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "ensemble256":
+        run_ensemble(args)
         return
     import torch
     import torch.distributed as dist

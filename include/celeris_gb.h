@@ -179,6 +179,48 @@ cel_status cel_profile_enable(cel_solver *s, int32_t capacity);
 cel_status cel_profile_read(cel_solver *s, double ms[3], int64_t count[3]);
 cel_status cel_profile_disable(cel_solver *s);
 
+/* Ensembles: many solvers stepped in lockstep, each kernel kind launched once
+ * per stage over all of them.  The paper steps one simulation at a time (the
+ * time integration of Sec. 3.3 with the solves of Eq. 21-23); an ensemble
+ * takes the same step for every member, so that a set of small grids (a few
+ * tiles each, far fewer than the GPU's SMs) fills the GPU in one launch
+ * instead of many.  Each member evolves bit for bit as it would under
+ * cel_step: the kernels, the per-member arguments and the order of every sum
+ * are the same.
+ *
+ * members: n >= 1 handles from cel_create, all of one precision and one
+ * corrector_iters, on disjoint workspaces (CEL_ERR_INVALID_ARG otherwise);
+ * they may differ in size, bed, boundaries, model, friction and dt.  The
+ * ensemble keeps the handle pointers: members must outlive it.
+ * cel_ensemble_table_bytes gives the device memory the ensemble needs for its
+ * argument tables (tens of KB per member); table_dev (256-byte aligned, owned
+ * by the caller) must stay allocated until cel_ensemble_destroy.  Every
+ * launch of the ensemble goes to cuda_stream; work the caller queued on the
+ * members' own streams must be finished (or ordered before it by the caller).
+ * cel_ensemble_create copies a few small tables (asynchronous); a one-line
+ * reason for a failure goes to msg (msg_len bytes, may be NULL).
+ *
+ * cel_ensemble_step advances every member by nsteps steps (asynchronous).
+ * The members must be in lockstep: the same number of steps since their
+ * last cel_set_state / cel_set_bathymetry / cel_add_solitary / checkpoint
+ * load (CEL_ERR_INVALID_ARG otherwise, reason in cel_ensemble_last_error).
+ * Members may be used alone between ensemble steps (cel_get_state, gauges,
+ * checkpoints, cel_set_boundary: the ensemble rebuilds its tables when a
+ * boundary or bed changed).  Gauges of members are logged as under cel_step.
+ * Two ensembles (or an ensemble and cel_step) that share a member must not
+ * overlap on the GPU. */
+typedef struct cel_ensemble cel_ensemble;     /* opaque, owned by the library (host) */
+cel_status cel_ensemble_table_bytes(cel_solver *const *members, int32_t n, size_t *bytes);
+cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *table_dev,
+                               size_t table_bytes, void *cuda_stream,
+                               cel_ensemble **out, char *msg, size_t msg_len);
+cel_status cel_ensemble_step(cel_ensemble *e, int32_t nsteps);
+/* Kernel launches issued by the most recent cel_ensemble_step call. */
+cel_status cel_ensemble_last_launch_count(const cel_ensemble *e, int64_t *launches);
+const char *cel_ensemble_last_error(const cel_ensemble *e);  /* never NULL */
+/* Release the handle (not the members, not the table).  Does not synchronise. */
+void cel_ensemble_destroy(cel_ensemble *e);
+
 /* Fixed-scratch variant of the step, for callers that cannot allocate device
  * memory.  Some callers run inside a host application that owns the GPU's
  * memory (a rendering or visualisation engine with its own pool, where a

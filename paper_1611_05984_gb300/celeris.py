@@ -32,7 +32,9 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
            "cel_load_checkpoint", "cel_last_launch_count", "cel_profile_enable",
-           "cel_profile_read", "cel_profile_disable", "cel_advance_noalloc", "cel_status_string",
+           "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
+           "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
+           "cel_ensemble_last_error", "cel_ensemble_destroy", "cel_advance_noalloc", "cel_status_string",
            "cel_last_error", "cel_destroy"]
 
 
@@ -102,6 +104,15 @@ def load(build_if_missing: bool = True):
         L.cel_advance_noalloc.argtypes = [ctypes.POINTER(CelGrid), ctypes.POINTER(CelParams),
                                           ctypes.POINTER(CelBC), vp, vp, vp, vp, vp, vp, vp, i32,
                                           i64, vp, ctypes.c_char_p, sz]
+        L.cel_ensemble_table_bytes.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(sz)]
+        L.cel_ensemble_create.argtypes = [ctypes.POINTER(vp), i32, vp, sz, vp, ctypes.POINTER(vp),
+                                          ctypes.c_char_p, sz]
+        L.cel_ensemble_step.argtypes = [vp, i32]
+        L.cel_ensemble_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+        L.cel_ensemble_last_error.restype = ctypes.c_char_p
+        L.cel_ensemble_last_error.argtypes = [vp]
+        L.cel_ensemble_destroy.argtypes = [vp]
+        L.cel_ensemble_destroy.restype = None
         L.cel_status_string.restype = ctypes.c_char_p
         L.cel_status_string.argtypes = [ctypes.c_int]
         L.cel_last_error.restype = ctypes.c_char_p
@@ -109,7 +120,8 @@ def load(build_if_missing: bool = True):
         L.cel_destroy.argtypes = [vp]
         L.cel_destroy.restype = None
         for name in EXPORTS:
-            if name not in ("cel_status_string", "cel_last_error", "cel_destroy"):
+            if name not in ("cel_status_string", "cel_last_error", "cel_destroy", "cel_ensemble_last_error",
+                            "cel_ensemble_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -290,6 +302,60 @@ class Solver:
         n = ctypes.c_int64()
         self._check(self.L.cel_last_launch_count(self._h, ctypes.byref(n)), "last_launch_count")
         return n.value
+
+
+class Ensemble:
+    """Many Solvers of one precision and one K, stepped in lockstep with one
+    launch per kernel kind and stage (cel_ensemble_*).  The members stay
+    usable alone (state, fields, gauges, checkpoints) between ensemble steps;
+    the ensemble keeps them alive.  Its launches go to ``stream`` (the current
+    stream by default)."""
+
+    def __init__(self, members: Sequence[Solver], stream=None):
+        torch = members[0].torch
+        self.torch = torch
+        self.members = list(members)
+        self.L = load()
+        n = len(self.members)
+        hs = (ctypes.c_void_p * n)(*[m._h.value for m in self.members])
+        nb = ctypes.c_size_t()
+        st = self.L.cel_ensemble_table_bytes(hs, n, ctypes.byref(nb))
+        if st != CEL_OK:
+            raise CelerisError(st, "cel_ensemble_table_bytes failed (mixed precision or K, shared workspace)")
+        dev = self.members[0].device
+        with torch.cuda.device(dev):
+            self.stream = stream or torch.cuda.current_stream(dev)
+            self.table = torch.empty(nb.value + 256, dtype=torch.uint8, device=dev)
+        ptr = (self.table.data_ptr() + 255) // 256 * 256
+        msg = ctypes.create_string_buffer(256)
+        h = ctypes.c_void_p()
+        self._h = None
+        st = self.L.cel_ensemble_create(hs, n, ptr, nb.value, self.stream.cuda_stream, ctypes.byref(h), msg,
+                                        len(msg))
+        if st != CEL_OK:
+            raise CelerisError(st, msg.value.decode())
+        self._h = h
+
+    def step(self, n: int = 1):
+        st = self.L.cel_ensemble_step(self._h, int(n))
+        if st != CEL_OK:
+            raise CelerisError(st, self.L.cel_ensemble_last_error(self._h).decode())
+
+    def last_launch_count(self) -> int:
+        v = ctypes.c_int64()
+        self.L.cel_ensemble_last_launch_count(self._h, ctypes.byref(v))
+        return v.value
+
+    def close(self):
+        if self._h is not None:
+            self.L.cel_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_scenario(s, dtype=None, K: Optional[int] = None, **kw) -> Solver:

@@ -10,8 +10,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 using namespace cel;
 
@@ -136,6 +138,7 @@ struct cel_solver {
     int ng, log_every, cap, nrec, head;
     int64_t launches;
     int ktab_dirty;   // boundaries or bed changed: rebuild the Eckart table
+    uint64_t gen;     // counts boundary and bed changes (ensembles rebuild their tables)
     std::string err;
     // optional per-kernel event timing
     cudaEvent_t *ev_beg, *ev_end;
@@ -215,19 +218,126 @@ cel_status set_state_t(cel_solver *s, const void *w, const void *P, const void *
     return CEL_OK;
 }
 
+// Arguments of the stencil launch of one stage (stage 0: the predictor or an
+// Euler step; stage >= 1: AM4 corrector iterations; Kn: last stage).
+template <typename real>
+StencilArgs<real> stencil_args(const cel_solver *s, const Coef<real> &coef, int stage, int Kn)
+{
+    const Layout &L = s->lay;
+    const int K = s->params.corrector_iters;
+    const int kind0 = s->nh == 0 ? kEuler0 : (s->nh == 1 ? kEuler1 : kAB3);
+    const int slot = (int)(s->nh & 1);
+    StencilArgs<real> a;
+    memset(&a, 0, sizeof(a));
+    a.geo = s->geo;
+    a.phy = s->phy;
+    a.c = coef;
+    a.ghost = s->at<real>(L.ghost);
+    a.Bc = s->at<real>(L.Bc);
+    a.w_in = s->at<real>(L.w[(s->cur + stage) & 1]);
+    a.w_out = s->at<real>(L.w[(s->cur + stage + 1) & 1]);
+    a.P_in = s->at<real>(L.P[stage == 0 ? s->pcur : 1 - s->pcur]);
+    a.Qc_in = s->at<real>(L.Qc[stage == 0 ? s->pcur : 1 - s->pcur]);
+    a.U_out = s->at<real>(L.U);
+    a.Vc_out = s->at<real>(L.Vc);
+    // ring slots: R^n goes to slot nh % 3, R^{n-1} and R^{n-2} before it
+    const int s0 = (int)(s->nh % 3), s1 = (s0 + 2) % 3, s2 = (s0 + 1) % 3;
+    for (int v = 0; v < 3; v++) {
+        a.a[v] = K == 0 ? s->at<real>(L.a[v]) : nullptr;
+        a.b[v] = K == 0 ? s->at<real>(L.b[v][slot]) : nullptr;
+        a.R0[v] = K > 0 ? s->at<real>(L.R[v][s0]) : nullptr;
+        a.R1[v] = K > 0 ? s->at<real>(L.R[v][s1]) : nullptr;
+        a.R2[v] = K > 0 ? s->at<real>(L.R[v][s2]) : nullptr;
+        a.F0[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s0]) : nullptr;
+        a.F1[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s1]) : nullptr;
+        a.F2[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s2]) : nullptr;
+        a.Y[v] = K > 0 ? s->at<real>(L.Y[v]) : nullptr;
+    }
+    a.mask_r = s->at<uint32_t>(L.mr);
+    a.mask_c = s->at<uint32_t>(L.mc);
+    a.kind = stage == 0 ? kind0 : kAM4;
+    a.ring = K > 0;
+    a.final_stage = stage == Kn;
+    a.tsel = stage == 0 ? 0 : 1;
+    return a;
+}
+
+// Arguments of the x-line (dir 0) or y-line (dir 1) solves of one stage.
+template <typename real>
+LineArgs<real> line_args(const cel_solver *s, const Coef<real> &coef, int dir, int stage, int Kn)
+{
+    const Layout &L = s->lay;
+    LineArgs<real> l;
+    memset(&l, 0, sizeof(l));
+    l.geo = s->geo;
+    l.phy = s->phy;
+    l.c = coef;
+    l.ghost = s->at<real>(L.ghost);
+    const double h = dir == 0 ? s->geo.dx : s->geo.dy;
+    l.rh = real(1.0 / h);
+    l.rh2 = real(1.0 / (h * h));
+    l.hrh = real(0.5 / h);
+    l.srh = real(1.0 / (6.0 * h));
+    l.rhs = s->at<real>(dir == 0 ? L.U : L.Vc);
+    l.d = s->at<real>(dir == 0 ? L.dr : L.dc);
+    l.mask = s->at<uint32_t>(dir == 0 ? L.mr : L.mc);
+    l.base = s->at<real>(dir == 0 ? L.P[s->pcur] : L.Qc[s->pcur]);
+    l.sol = s->at<real>(dir == 0 ? L.P[1 - s->pcur] : L.Qc[1 - s->pcur]);
+    l.dir = dir;
+    l.n = dir == 0 ? s->geo.nx : s->geo.ny;
+    l.nlines = dir == 0 ? s->geo.ny : s->geo.nx;
+    l.pitch = dir == 0 ? s->geo.px : s->geo.py;
+    l.nwords = dir == 0 ? s->geo.nwx : s->geo.nwy;
+    l.nseg = dir == 0 ? s->nseg_x : s->nseg_y;
+    l.mshift = line_seg_shift(l.n, s->es);
+    l.sp = line_seg_stride(l.nseg);
+    l.final_stage = stage == Kn;
+    l.identity = s->params.model == CEL_NLSW;
+    return l;
+}
+
+// Stages of the step about to be taken: AM4 iterations only once the AB3
+// history holds two earlier steps.
+int stages_of(const cel_solver *s) { return (s->nh >= 2 ? s->params.corrector_iters : 0) + 1; }
+
+// Counters after a step of Kn + 1 stages: w alternates per stage, P / Q per step.
+void finish_step(cel_solver *s, int Kn)
+{
+    s->cur = (s->cur + Kn + 1) & 1;
+    s->pcur = 1 - s->pcur;
+    s->step++;
+    s->nh++;
+}
+
+// Gauge record of the step just finished, if one is due; adds its launch.
+template <typename real>
+cel_status log_gauges(cel_solver *s, cudaStream_t st, int64_t &launches)
+{
+    if (!(s->ng > 0 && s->log_every > 0 && s->cap > 0 && s->step % s->log_every == 0)) return CEL_OK;
+    int slotg;
+    if (s->nrec < s->cap) {
+        slotg = (s->head + s->nrec) % s->cap;
+        s->nrec++;
+    } else {
+        slotg = s->head;
+        s->head = (s->head + 1) % s->cap;
+    }
+    real *dst = reinterpret_cast<real *>(s->gring) + (size_t)slotg * s->ng;
+    CEL_CUDA(s, launch_gauges<real>(s->geo, s->phy, s->at<real>(s->lay.w[s->cur]), s->gij, s->ng, dst, st), "gauges");
+    launches += 1;
+    return CEL_OK;
+}
+
 template <typename real>
 cel_status step_t(cel_solver *s, int nsteps)
 {
     const Layout &L = s->lay;
-    const int K = s->params.corrector_iters;
     int64_t launches = 0;
     const Coef<real> coef = make_coef<real>(s->geo, s->phy, s->bnd);
     real *ghost = s->at<real>(L.ghost);
     for (int it = 0; it < nsteps; it++) {
-        const int kind0 = s->nh == 0 ? kEuler0 : (s->nh == 1 ? kEuler1 : kAB3);
-        const int Kn = s->nh >= 2 ? K : 0;
+        const int Kn = stages_of(s) - 1;
         const double t0 = (double)s->step * s->params.dt, t1 = (double)(s->step + 1) * s->params.dt;
-        const int slot = (int)(s->nh & 1);
         if (coef.sine) {
             int pg = prof_begin(s, 2);
             if (s->ktab_dirty) {
@@ -242,92 +352,21 @@ cel_status step_t(cel_solver *s, int nsteps)
             launches += 1;
         }
         for (int stage = 0; stage <= Kn; stage++) {
-            StencilArgs<real> a;
-            a.geo = s->geo;
-            a.phy = s->phy;
-            a.c = coef;
-            a.ghost = ghost;
-            a.Bc = s->at<real>(L.Bc);
-            a.w_in = s->at<real>(L.w[(s->cur + stage) & 1]);
-            a.w_out = s->at<real>(L.w[(s->cur + stage + 1) & 1]);
-            a.P_in = s->at<real>(L.P[stage == 0 ? s->pcur : 1 - s->pcur]);
-            a.Qc_in = s->at<real>(L.Qc[stage == 0 ? s->pcur : 1 - s->pcur]);
-            a.U_out = s->at<real>(L.U);
-            a.Vc_out = s->at<real>(L.Vc);
-            // ring slots: R^n goes to slot nh % 3, R^{n-1} and R^{n-2} before it
-            const int s0 = (int)(s->nh % 3), s1 = (s0 + 2) % 3, s2 = (s0 + 1) % 3;
-            for (int v = 0; v < 3; v++) {
-                a.a[v] = K == 0 ? s->at<real>(L.a[v]) : nullptr;
-                a.b[v] = K == 0 ? s->at<real>(L.b[v][slot]) : nullptr;
-                a.R0[v] = K > 0 ? s->at<real>(L.R[v][s0]) : nullptr;
-                a.R1[v] = K > 0 ? s->at<real>(L.R[v][s1]) : nullptr;
-                a.R2[v] = K > 0 ? s->at<real>(L.R[v][s2]) : nullptr;
-                a.F0[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s0]) : nullptr;
-                a.F1[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s1]) : nullptr;
-                a.F2[v] = K > 0 && v > 0 ? s->at<real>(L.Ph[v][s2]) : nullptr;
-                a.Y[v] = K > 0 ? s->at<real>(L.Y[v]) : nullptr;
-            }
-            a.mask_r = s->at<uint32_t>(L.mr);
-            a.mask_c = s->at<uint32_t>(L.mc);
-            a.kind = stage == 0 ? kind0 : kAM4;
-            a.ring = K > 0;
-            a.final_stage = stage == Kn;
-            a.tsel = stage == 0 ? 0 : 1;
+            const StencilArgs<real> a = stencil_args<real>(s, coef, stage, Kn);
             int pe = prof_begin(s, 0);
             CEL_CUDA(s, launch_stencil<real>(a, s->stream), "stencil");
             prof_end(s, pe);
             LinePair<real> lp;
-            for (int dir = 0; dir < 2; dir++) {
-                LineArgs<real> &l = lp.L[dir];
-                l.geo = s->geo;
-                l.phy = s->phy;
-                l.c = coef;
-                l.ghost = ghost;
-                const double h = dir == 0 ? s->geo.dx : s->geo.dy;
-                l.rh = real(1.0 / h);
-                l.rh2 = real(1.0 / (h * h));
-                l.hrh = real(0.5 / h);
-                l.srh = real(1.0 / (6.0 * h));
-                l.rhs = s->at<real>(dir == 0 ? L.U : L.Vc);
-                l.d = s->at<real>(dir == 0 ? L.dr : L.dc);
-                l.mask = s->at<uint32_t>(dir == 0 ? L.mr : L.mc);
-                l.base = s->at<real>(dir == 0 ? L.P[s->pcur] : L.Qc[s->pcur]);
-                l.sol = s->at<real>(dir == 0 ? L.P[1 - s->pcur] : L.Qc[1 - s->pcur]);
-                l.dir = dir;
-                l.n = dir == 0 ? s->geo.nx : s->geo.ny;
-                l.nlines = dir == 0 ? s->geo.ny : s->geo.nx;
-                l.pitch = dir == 0 ? s->geo.px : s->geo.py;
-                l.nwords = dir == 0 ? s->geo.nwx : s->geo.nwy;
-                l.nseg = dir == 0 ? s->nseg_x : s->nseg_y;
-                l.mshift = line_seg_shift(l.n, s->es);
-                l.sp = line_seg_stride(l.nseg);
-                l.final_stage = stage == Kn;
-                l.identity = s->params.model == CEL_NLSW;
-            }
+            for (int dir = 0; dir < 2; dir++) lp.L[dir] = line_args<real>(s, coef, dir, stage, Kn);
             int pl = prof_begin(s, 1);
             CEL_CUDA(s, launch_lines<real>(lp, s->stream), "line solves");
             prof_end(s, pl);
             if (lp.L[0].mshift != lp.L[1].mshift) launches += 1;   // two segment lengths: two launches
             launches += 2;
         }
-        s->cur = (s->cur + Kn + 1) & 1;
-        s->pcur = 1 - s->pcur;
-        s->step++;
-        s->nh++;
-        if (s->ng > 0 && s->log_every > 0 && s->cap > 0 && s->step % s->log_every == 0) {
-            int slotg;
-            if (s->nrec < s->cap) {
-                slotg = (s->head + s->nrec) % s->cap;
-                s->nrec++;
-            } else {
-                slotg = s->head;
-                s->head = (s->head + 1) % s->cap;
-            }
-            real *dst = reinterpret_cast<real *>(s->gring) + (size_t)slotg * s->ng;
-            CEL_CUDA(s, launch_gauges<real>(s->geo, s->phy, s->at<real>(L.w[s->cur]), s->gij, s->ng, dst,
-                                            s->stream), "gauges");
-            launches += 1;
-        }
+        finish_step(s, Kn);
+        cel_status st = log_gauges<real>(s, s->stream, launches);
+        if (st != CEL_OK) return st;
     }
     s->launches = launches;
     return CEL_OK;
@@ -442,6 +481,7 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->ng = s->log_every = s->cap = s->nrec = s->head = 0;
     s->launches = 0;
     s->ktab_dirty = 1;
+    s->gen = 0;
     s->step = 0;
     s->cur = s->pcur = 0;
     s->ev_beg = s->ev_end = nullptr;
@@ -484,6 +524,7 @@ cel_status cel_set_boundary(cel_solver *s, int32_t side, const cel_bc *bc)
     Side &S = s->bnd.s[side];
     memset(&S, 0, sizeof(S));
     s->ktab_dirty = 1;
+    s->gen++;
     S.type = bc->type;
     S.width = bc->width_cells;
     S.L = bc->width_cells * (side < 2 ? s->grid.dx : s->grid.dy);
@@ -546,6 +587,7 @@ cel_status cel_set_bathymetry(cel_solver *s, const void *z_dev)
     cel_status st = s->es == 4 ? derive_static<float>(s, z_dev) : derive_static<double>(s, z_dev);
     if (st != CEL_OK) return st;
     s->ktab_dirty = 1;
+    s->gen++;
     // raise w to the new bed in place, zero the discharge where now dry
     cudaError_t e = s->es == 4
                         ? launch_clamp_state<float>(s->geo, s->phy, s->at<float>(s->lay.Bc),
@@ -890,6 +932,7 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.ng = s.log_every = s.cap = s.nrec = s.head = 0;
     s.launches = 0;
     s.ktab_dirty = 1;
+    s.gen = 0;
     s.step = first_step;
     s.nh = 0;
     s.cur = s.pcur = 0;
@@ -912,3 +955,412 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     return st;
 }
 
+
+// ------------------------------------------------------------- ensembles
+//
+// An ensemble steps many solvers (members) in lockstep with one launch per
+// kernel kind and stage: the stencil launch covers every member's tiles, the
+// line launch every member's x- and y-lines of one segment length, the ghost
+// launch every member's sine-maker table.  Each member keeps its own
+// workspace; the ensemble only adds argument tables in the caller's device
+// memory.  The argument blocks of a stage are the ones the member's own step
+// would pass (same builders), so every member evolves bit for bit as if it
+// were stepped alone.
+
+struct cel_ensemble {
+    struct Group {            // line families of one segment length
+        int mshift, first, nfam, blocks, threads;
+        size_t smem, off_start;
+    };
+    std::vector<cel_solver *> m;
+    int es, K;
+    cudaStream_t stream;
+    unsigned char *tab;
+    size_t tab_bytes;
+    int tiles;                           // stencil blocks over all members
+    size_t off_tile_start;               // int[N + 1]
+    std::vector<std::pair<int, int>> fam;   // (member, dir) in table order
+    std::vector<Group> groups;
+    std::vector<int> gmem;               // members with a sine maker
+    int gblocks;
+    size_t off_gargs, off_gstart;
+    std::vector<int64_t> gstep0;         // member steps the ghost arguments were built at
+    bool gvalid;
+    size_t sarg_bytes, entry_bytes, off_entries;
+    int cap;
+    std::vector<uint64_t> keys;          // key of each filled entry
+    uint64_t gen_sum;
+    int64_t launches;
+    std::string err;
+};
+
+namespace {
+
+struct EnsPlan {
+    int tiles = 0, gblocks = 0;
+    std::vector<std::pair<int, int>> fam;
+    std::vector<cel_ensemble::Group> groups;
+    std::vector<int> gmem;
+    size_t off_tile_start = 0, off_gargs = 0, off_gstart = 0, sarg_bytes = 0, entry_bytes = 0, off_entries = 0;
+    int cap = 0;
+    size_t total = 0;
+};
+
+template <typename real>
+void plan_t(cel_solver *const *ms, int n, EnsPlan &P)
+{
+    size_t cur = 0;
+    auto take = [&](size_t b) {
+        size_t o = cur;
+        cur += align256(b);
+        return o;
+    };
+    P.tiles = 0;
+    for (int e = 0; e < n; e++)
+        P.tiles += ((ms[e]->geo.nx + kTile - 1) / kTile) * ((ms[e]->geo.ny + kTile - 1) / kTile);
+    P.off_tile_start = take(sizeof(int) * (size_t)(n + 1));
+    // line families grouped by segment length, longest lines first in a group
+    P.fam.clear();
+    P.groups.clear();
+    for (int sh = 1; sh <= 5; sh++) {
+        std::vector<std::pair<int, int>> g;
+        for (int e = 0; e < n; e++)
+            for (int dir = 0; dir < 2; dir++) {
+                const int len = dir == 0 ? ms[e]->geo.nx : ms[e]->geo.ny;
+                if (line_seg_shift(len, ms[e]->es) == sh) g.push_back({e, dir});
+            }
+        if (g.empty()) continue;
+        std::stable_sort(g.begin(), g.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+            const int la = a.second == 0 ? ms[a.first]->geo.nx : ms[a.first]->geo.ny;
+            const int lb = b.second == 0 ? ms[b.first]->geo.nx : ms[b.first]->geo.ny;
+            return la > lb;
+        });
+        cel_ensemble::Group G;
+        G.mshift = sh;
+        G.first = (int)P.fam.size();
+        G.nfam = (int)g.size();
+        G.blocks = 0;
+        G.threads = 64;
+        G.smem = 0;
+        for (auto &f : g) {
+            const cel_solver *s = ms[f.first];
+            const int len = f.second == 0 ? s->geo.nx : s->geo.ny;
+            const int nseg = f.second == 0 ? s->nseg_x : s->nseg_y;
+            G.blocks += f.second == 0 ? s->geo.ny : s->geo.nx;
+            G.threads = std::max(G.threads, round_up_i(nseg, 32));
+            G.smem = std::max(G.smem, line_smem_bytes<real>(len, nseg));
+            P.fam.push_back(f);
+        }
+        G.off_start = take(sizeof(int) * (size_t)(G.nfam + 1));
+        P.groups.push_back(G);
+    }
+    P.gmem.clear();
+    P.gblocks = 0;
+    for (int e = 0; e < n; e++) {
+        bool sine = false;
+        for (int k = 0; k < 4; k++) sine |= ms[e]->bnd.s[k].type == kSine;
+        if (!sine) continue;
+        P.gmem.push_back(e);
+        const int npos = (ms[e]->geo.nx > ms[e]->geo.ny ? ms[e]->geo.nx : ms[e]->geo.ny) + 4;
+        P.gblocks += ((npos + 127) / 128) * 16;
+    }
+    P.off_gargs = take(sizeof(GhostArgs<real>) * (size_t)n);
+    P.off_gstart = take(sizeof(int) * (size_t)(n + 1));
+    P.sarg_bytes = align256(sizeof(StencilArgs<real>) * (size_t)n);
+    P.entry_bytes = P.sarg_bytes + align256(sizeof(LineArgs<real>) * P.fam.size());
+    // the argument blocks repeat every 6 steps once the AB3 history is full
+    // (ring slot nh % 3, carry slot nh % 2, P / Q buffers alternate), plus
+    // the two Euler steps: 8 (K + 1) entries hold a run from set_state on
+    P.cap = 8 * (ms[0]->params.corrector_iters + 1);
+    P.off_entries = cur;
+    P.total = cur + P.entry_bytes * (size_t)P.cap;
+}
+
+cel_status plan(cel_solver *const *ms, int n, EnsPlan &P, std::string &why)
+{
+    if (!ms || n < 1) {
+        why = "an ensemble needs at least one member";
+        return CEL_ERR_INVALID_ARG;
+    }
+    for (int e = 0; e < n; e++) {
+        if (!ms[e]) {
+            why = "NULL member";
+            return CEL_ERR_INVALID_ARG;
+        }
+        if (ms[e]->es != ms[0]->es || ms[e]->params.corrector_iters != ms[0]->params.corrector_iters) {
+            why = "members differ in precision or in the number of corrector iterations";
+            return CEL_ERR_INVALID_ARG;
+        }
+    }
+    // members must not share workspace memory: one launch writes all of them
+    std::vector<std::pair<uintptr_t, uintptr_t>> r;
+    for (int e = 0; e < n; e++) r.push_back({(uintptr_t)ms[e]->ws, (uintptr_t)ms[e]->ws + ms[e]->lay.total});
+    std::sort(r.begin(), r.end());
+    for (size_t k = 1; k < r.size(); k++)
+        if (r[k].first < r[k - 1].second) {
+            why = "two members share workspace memory (or a member is listed twice)";
+            return CEL_ERR_INVALID_ARG;
+        }
+    if (ms[0]->es == 4) plan_t<float>(ms, n, P);
+    else plan_t<double>(ms, n, P);
+    return CEL_OK;
+}
+
+cel_status ens_fail(cel_ensemble *e, cel_status st, const std::string &msg)
+{
+    e->err = msg;
+    return st;
+}
+
+#define ENS_CUDA(e, expr, where)                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess) return ens_fail(e, CEL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+uint64_t ens_key(const cel_solver *s, int stage)
+{
+    const uint64_t nhk = s->nh < 2 ? (uint64_t)s->nh : 2 + (uint64_t)((s->nh - 2) % 6);
+    return (nhk << 16) | ((uint64_t)s->cur << 9) | ((uint64_t)s->pcur << 8) | (uint64_t)stage;
+}
+
+// Index of the table entry holding the arguments of this stage for the
+// members' present state; built and uploaded if missing (stream-ordered, so
+// launches queued earlier still read the old contents).
+template <typename real>
+cel_status ens_entry(cel_ensemble *e, int stage, int Kn, int *idx)
+{
+    const uint64_t key = ens_key(e->m[0], stage);
+    for (size_t k = 0; k < e->keys.size(); k++)
+        if (e->keys[k] == key) {
+            *idx = (int)k;
+            return CEL_OK;
+        }
+    if ((int)e->keys.size() >= e->cap) e->keys.clear();
+    const int k = (int)e->keys.size();
+    const int n = (int)e->m.size();
+    std::vector<unsigned char> host(e->entry_bytes, 0);
+    StencilArgs<real> *sa = reinterpret_cast<StencilArgs<real> *>(host.data());
+    LineArgs<real> *la = reinterpret_cast<LineArgs<real> *>(host.data() + e->sarg_bytes);
+    std::vector<Coef<real>> coef(n);
+    for (int j = 0; j < n; j++) {
+        const cel_solver *s = e->m[j];
+        coef[j] = make_coef<real>(s->geo, s->phy, s->bnd);
+        sa[j] = stencil_args<real>(s, coef[j], stage, Kn);
+    }
+    for (size_t f = 0; f < e->fam.size(); f++)
+        la[f] = line_args<real>(e->m[e->fam[f].first], coef[e->fam[f].first], e->fam[f].second, stage, Kn);
+    ENS_CUDA(e, cudaMemcpyAsync(e->tab + e->off_entries + (size_t)k * e->entry_bytes, host.data(), e->entry_bytes,
+                                cudaMemcpyHostToDevice, e->stream), "ensemble arguments");
+    e->keys.push_back(key);
+    *idx = k;
+    return CEL_OK;
+}
+
+template <typename real>
+cel_status ens_step_t(cel_ensemble *e, int nsteps)
+{
+    const int n = (int)e->m.size();
+    int64_t launches = 0;
+    for (int it = 0; it < nsteps; it++) {
+        const cel_solver *m0 = e->m[0];
+        uint64_t gsum = 0;
+        for (int j = 0; j < n; j++) {
+            const cel_solver *s = e->m[j];
+            if (s->nh != m0->nh || s->cur != m0->cur || s->pcur != m0->pcur)
+                return ens_fail(e, CEL_ERR_INVALID_ARG,
+                                "members are not in lockstep (set their states together, then step the ensemble)");
+            gsum += s->gen;
+        }
+        if (gsum != e->gen_sum) {      // a boundary or bed changed: rebuild every table
+            e->keys.clear();
+            e->gvalid = false;
+            e->gen_sum = gsum;
+        }
+        const int Kn = stages_of(m0) - 1;
+        if (e->gvalid && !e->gmem.empty()) {        // members moved on outside the ensemble?
+            const int64_t k0 = e->m[e->gmem[0]]->step - e->gstep0[0];
+            for (size_t g = 0; g < e->gmem.size(); g++)
+                if (e->m[e->gmem[g]]->step - e->gstep0[g] != k0) e->gvalid = false;
+        }
+        if (!e->gvalid) {                           // members with a sine maker, their ghost arguments
+            e->gmem.clear();
+            for (int j = 0; j < n; j++)
+                if (make_coef<real>(e->m[j]->geo, e->m[j]->phy, e->m[j]->bnd).sine) e->gmem.push_back(j);
+            e->gstep0.assign(e->gmem.size(), 0);
+            std::vector<GhostArgs<real>> ga(e->gmem.size());
+            std::vector<int> start(e->gmem.size() + 1, 0);
+            for (size_t g = 0; g < e->gmem.size(); g++) {
+                const cel_solver *s = e->m[e->gmem[g]];
+                GhostArgs<real> &a = ga[g];
+                memset(&a, 0, sizeof(a));
+                a.g = s->geo;
+                a.p = s->phy;
+                a.b = s->bnd;
+                a.d_r = s->at<real>(s->lay.dr);
+                a.ktab = s->at<double>(s->lay.ktab);
+                a.tab = s->at<real>(s->lay.ghost);
+                a.npos = make_coef<real>(s->geo, s->phy, s->bnd).npos;
+                a.step0 = s->step;
+                a.dt = s->params.dt;
+                e->gstep0[g] = s->step;
+                start[g + 1] = start[g] + ((a.npos + 127) / 128) * 16;
+            }
+            e->gblocks = start.back();
+            if (!ga.empty()) {
+                ENS_CUDA(e, cudaMemcpyAsync(e->tab + e->off_gargs, ga.data(), sizeof(GhostArgs<real>) * ga.size(),
+                                            cudaMemcpyHostToDevice, e->stream), "ensemble ghost arguments");
+                ENS_CUDA(e, cudaMemcpyAsync(e->tab + e->off_gstart, start.data(), sizeof(int) * start.size(),
+                                            cudaMemcpyHostToDevice, e->stream), "ensemble ghost arguments");
+            }
+            e->gvalid = true;
+        }
+        if (!e->gmem.empty()) {
+            for (int j : e->gmem) {
+                cel_solver *s = e->m[j];
+                if (!s->ktab_dirty) continue;
+                const Coef<real> c = make_coef<real>(s->geo, s->phy, s->bnd);
+                ENS_CUDA(e, launch_eckart_table<real>(s->geo, s->phy, s->bnd, s->at<real>(s->lay.dr),
+                                                      s->at<double>(s->lay.ktab), c.npos, e->stream), "Eckart table");
+                s->ktab_dirty = 0;
+                launches += 1;
+            }
+            const int64_t k = e->m[e->gmem[0]]->step - e->gstep0[0];
+            ENS_CUDA(e, launch_ghost_batch<real>(reinterpret_cast<const GhostArgs<real> *>(e->tab + e->off_gargs),
+                                                 reinterpret_cast<const int *>(e->tab + e->off_gstart),
+                                                 (int)e->gmem.size(), e->gblocks, k, e->stream), "ensemble ghost tables");
+            launches += 1;
+        }
+        for (int stage = 0; stage <= Kn; stage++) {
+            int idx = 0;
+            cel_status st = ens_entry<real>(e, stage, Kn, &idx);
+            if (st != CEL_OK) return st;
+            const unsigned char *ent = e->tab + e->off_entries + (size_t)idx * e->entry_bytes;
+            ENS_CUDA(e, launch_stencil_batch<real>(reinterpret_cast<const StencilArgs<real> *>(ent),
+                                                   reinterpret_cast<const int *>(e->tab + e->off_tile_start), n,
+                                                   e->tiles, e->stream), "ensemble stencil");
+            launches += 1;
+            const LineArgs<real> *la = reinterpret_cast<const LineArgs<real> *>(ent + e->sarg_bytes);
+            for (const cel_ensemble::Group &G : e->groups) {
+                ENS_CUDA(e, launch_lines_batch<real>(la + G.first, reinterpret_cast<const int *>(e->tab + G.off_start),
+                                                     G.nfam, G.blocks, G.mshift, G.threads, G.smem, e->stream),
+                         "ensemble line solves");
+                launches += 1;
+            }
+        }
+        for (int j = 0; j < n; j++) {
+            cel_solver *s = e->m[j];
+            finish_step(s, Kn);
+            int64_t lg = 0;
+            cel_status st = log_gauges<real>(s, e->stream, lg);
+            if (st != CEL_OK) return ens_fail(e, st, s->err);
+            launches += lg;
+        }
+    }
+    e->launches = launches;
+    return CEL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cel_status cel_ensemble_table_bytes(cel_solver *const *members, int32_t n, size_t *bytes)
+{
+    if (!bytes) return CEL_ERR_INVALID_ARG;
+    EnsPlan P;
+    std::string why;
+    cel_status st = plan(members, n, P, why);
+    if (st != CEL_OK) return st;
+    *bytes = P.total;
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *table_dev, size_t table_bytes,
+                               void *cuda_stream, cel_ensemble **out, char *msg, size_t msg_len)
+{
+    put_msg(msg, msg_len, "");
+    if (!out) return CEL_ERR_INVALID_ARG;
+    *out = nullptr;
+    EnsPlan P;
+    std::string why;
+    cel_status st = plan(members, n, P, why);
+    if (st != CEL_OK) {
+        put_msg(msg, msg_len, why);
+        return st;
+    }
+    if (!table_dev || ((uintptr_t)table_dev & 255) != 0) {
+        put_msg(msg, msg_len, "the table must be device memory aligned to 256 bytes");
+        return CEL_ERR_INVALID_ARG;
+    }
+    if (table_bytes < P.total) {
+        put_msg(msg, msg_len, "table smaller than cel_ensemble_table_bytes");
+        return CEL_ERR_WORKSPACE_TOO_SMALL;
+    }
+    cel_ensemble *e = new cel_ensemble();
+    e->m.assign(members, members + n);
+    e->es = members[0]->es;
+    e->K = members[0]->params.corrector_iters;
+    e->stream = (cudaStream_t)cuda_stream;
+    e->tab = (unsigned char *)table_dev;
+    e->tab_bytes = table_bytes;
+    e->tiles = P.tiles;
+    e->off_tile_start = P.off_tile_start;
+    e->fam = P.fam;
+    e->groups = P.groups;
+    e->gmem = P.gmem;
+    e->gblocks = P.gblocks;
+    e->off_gargs = P.off_gargs;
+    e->off_gstart = P.off_gstart;
+    e->gstep0.assign(P.gmem.size(), 0);
+    e->gvalid = false;
+    e->sarg_bytes = P.sarg_bytes;
+    e->entry_bytes = P.entry_bytes;
+    e->off_entries = P.off_entries;
+    e->cap = P.cap;
+    e->gen_sum = 0;
+    for (int j = 0; j < n; j++) e->gen_sum += members[j]->gen;
+    e->launches = 0;
+    // block ranges of the members' tiles and of each group's line families
+    std::vector<int> ts(n + 1, 0);
+    for (int j = 0; j < n; j++)
+        ts[j + 1] = ts[j] + ((members[j]->geo.nx + kTile - 1) / kTile) * ((members[j]->geo.ny + kTile - 1) / kTile);
+    cudaError_t ce = cudaMemcpyAsync(e->tab + e->off_tile_start, ts.data(), sizeof(int) * ts.size(),
+                                     cudaMemcpyHostToDevice, e->stream);
+    for (const cel_ensemble::Group &G : e->groups) {
+        if (ce != cudaSuccess) break;
+        std::vector<int> fs(G.nfam + 1, 0);
+        for (int f = 0; f < G.nfam; f++) {
+            const std::pair<int, int> &fm = e->fam[G.first + f];
+            fs[f + 1] = fs[f] + (fm.second == 0 ? members[fm.first]->geo.ny : members[fm.first]->geo.nx);
+        }
+        ce = cudaMemcpyAsync(e->tab + G.off_start, fs.data(), sizeof(int) * fs.size(), cudaMemcpyHostToDevice,
+                             e->stream);
+    }
+    if (ce != cudaSuccess) {
+        put_msg(msg, msg_len, std::string("ensemble tables: ") + cudaGetErrorString(ce));
+        delete e;
+        return CEL_ERR_CUDA;
+    }
+    *out = e;
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_step(cel_ensemble *e, int32_t nsteps)
+{
+    if (!e || nsteps < 0) return CEL_ERR_INVALID_ARG;
+    return e->es == 4 ? ens_step_t<float>(e, nsteps) : ens_step_t<double>(e, nsteps);
+}
+
+cel_status cel_ensemble_last_launch_count(const cel_ensemble *e, int64_t *launches)
+{
+    if (!e || !launches) return CEL_ERR_INVALID_ARG;
+    *launches = e->launches;
+    return CEL_OK;
+}
+
+const char *cel_ensemble_last_error(const cel_ensemble *e) { return e ? e->err.c_str() : ""; }
+
+void cel_ensemble_destroy(cel_ensemble *e) { delete e; }
+
+}  // extern "C"

@@ -297,6 +297,18 @@ __global__ void k_check_finite(Geo g, const real *w, const real *P, const real *
 // (Reading A-B4): west / east sides run along rows j = pos - 2, south /
 // north sides along columns i = pos - 2 including the corner columns, where
 // d is clamped along the side.  Returns false where the position is unused.
+// Last entry of a sorted prefix array not above b: the ensemble member (or line family) that block b belongs to.
+__device__ __forceinline__ int find_owner(const int *__restrict__ start, int n, int b)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <typename real>
 __device__ inline bool ghost_site(const Geo &g, const real *d_r, int side, int layer, int pos, double &x,
                                   double &y, double &dadj)
@@ -344,12 +356,11 @@ __global__ void k_eckart_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_
 // Sine-maker ghosts (Eq. 25-28) for one step, in double: both ghost layers of
 // every sine side at t^n and t^{n+1}, summed over components.
 template <typename real>
-__global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r,
-                              const double *__restrict__ ktab, double t0, double t1, real *__restrict__ tab,
-                              int npos)
+__device__ __forceinline__ void ghost_entry(const Geo &g, const Phys &p, const Bnd &b, const real *__restrict__ d_r,
+                                            const double *__restrict__ ktab, double t0, double t1,
+                                            real *__restrict__ tab, int npos, int pos, int yb)
 {
-    int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    int time = blockIdx.y & 1, layer = (blockIdx.y >> 1) & 1, side = blockIdx.y >> 2;
+    int time = yb & 1, layer = (yb >> 1) & 1, side = yb >> 2;
     if (pos >= npos || b.s[side].type != kSine) return;
     double x, y, dadj;
     if (!ghost_site(g, d_r, side, layer, pos, x, y, dadj)) return;
@@ -368,6 +379,30 @@ __global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r
     tab[ghost_index(time, side, layer, 0, pos, npos)] = real(p.ws + eta);
     tab[ghost_index(time, side, layer, 1, pos, npos)] = real(Pg);
     tab[ghost_index(time, side, layer, 2, pos, npos)] = real(Qg);
+}
+
+template <typename real>
+__global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r,
+                              const double *__restrict__ ktab, double t0, double t1, real *__restrict__ tab,
+                              int npos)
+{
+    ghost_entry(g, p, b, d_r, ktab, t0, t1, tab, npos, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+}
+
+// Ensemble: the ghost tables of every member with a sine maker; member e
+// owns blocks [start[e], start[e+1]), 16 per 128 positions, and is at step
+// step0 + k.
+template <typename real>
+__global__ void k_ghost_batch(const GhostArgs<real> *__restrict__ args, const int *__restrict__ start, int n,
+                              int64_t k)
+{
+    const int e = find_owner(start, n, blockIdx.x);
+    const GhostArgs<real> &A = args[e];
+    const int b = blockIdx.x - start[e];
+    const int nbx = (A.npos + 127) / 128;
+    const int64_t step = A.step0 + k;
+    ghost_entry(A.g, A.p, A.b, A.d_r, A.ktab, (double)step * A.dt, (double)(step + 1) * A.dt, A.tab, A.npos,
+                (b % nbx) * 128 + threadIdx.x, b / nbx);
 }
 
 // ------------------------------------------------------------ the stencil
@@ -561,14 +596,34 @@ __device__ __forceinline__ void stage_tiles(const StageSpec<real> *sp, int tid)
     }
 }
 
-template <typename real>
-__global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_stencil(StencilArgs<real> A)
+// Tile origin of a single-grid launch: the block index, which the compiler
+// re-reads where it needs it instead of keeping it in a register.
+struct GridOrigin {
+    __device__ __forceinline__ int x0() const { return blockIdx.x * kTile; }
+    __device__ __forceinline__ int y0() const { return blockIdx.y * kTile; }
+};
+
+// Tile origin of an ensemble launch: two ints in shared memory, loaded at
+// each use for the same reason.
+struct SharedOrigin {
+    const int *o;
+    __device__ __forceinline__ int ld(int k) const
+    {
+        int v;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(o + k)));
+        return v;
+    }
+    __device__ __forceinline__ int x0() const { return ld(0); }
+    __device__ __forceinline__ int y0() const { return ld(1); }
+};
+
+// One 32 x 32 tile of one grid, at the origin O gives: the whole stencil stage.
+template <typename real, typename Origin>
+__device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const Origin &O, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     StencilSmem<real> &sm = *reinterpret_cast<StencilSmem<real> *>(smem_raw);
     const Geo &G = A.geo;
     const int nx = G.nx, ny = G.ny;
-    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
     const int tid = threadIdx.x;
     const Coef<real> &C = A.c;
     const real ws = C.ws, g = C.g, eps = C.eps;
@@ -579,10 +634,10 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_
     //         Corners: array index (corner + 1) in [0, nx + 2] x [0, ny + 2].
     {
         const StageSpec<real> spec[4] = {
-            {A.w_in, (size_t)G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.w, kStride, false},
-            {A.P_in, (size_t)G.px, x0 - kHalo, y0 - kHalo, kTileIn, kTileIn, nx, ny, sm.P, kStride, false},
-            {A.Qc_in, (size_t)G.py, y0 - kHalo, x0 - kHalo, kTileIn, kTileIn, ny, nx, sm.Q, kStride, true},
-            {A.Bc, (size_t)G.pc, x0, y0, kCorner, kCorner, nx + 3, ny + 3, sm.Bc, kCornerStride, false}};
+            {A.w_in, (size_t)G.px, O.x0() - kHalo, O.y0() - kHalo, kTileIn, kTileIn, nx, ny, sm.w, kStride, false},
+            {A.P_in, (size_t)G.px, O.x0() - kHalo, O.y0() - kHalo, kTileIn, kTileIn, nx, ny, sm.P, kStride, false},
+            {A.Qc_in, (size_t)G.py, O.y0() - kHalo, O.x0() - kHalo, kTileIn, kTileIn, ny, nx, sm.Q, kStride, true},
+            {A.Bc, (size_t)G.pc, O.x0(), O.y0(), kCorner, kCorner, nx + 3, ny + 3, sm.Bc, kCornerStride, false}};
         // 36 x 18 pairs per state tile: at most 3 per thread
         stage_tiles<real, 4, (kTileIn * (kTileIn / 2) + kStencilThreads - 1) / kStencilThreads>(spec, tid);
     }
@@ -598,20 +653,20 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_
 
     // ---- 2. ghost layers (Sec. 2.4): x-sides over interior rows, then
     //         y-sides over every column, so corners come by composition.
-    const bool westT = x0 == 0, eastT = x0 + kTile + kHalo > nx;
-    const bool southT = y0 == 0, northT = y0 + kTile + kHalo > ny;
+    const bool westT = O.x0() == 0, eastT = O.x0() + kTile + kHalo > nx;
+    const bool southT = O.y0() == 0, northT = O.y0() + kTile + kHalo > ny;
     if (westT || eastT) {
         for (int k = tid; k < 4 * (kTileIn - 2); k += kStencilThreads) {
             int ty = 1 + k % (kTileIn - 2), which = k / (kTileIn - 2);   // ty in [1, 35)
-            int gy = y0 - kHalo + ty;
+            int gy = O.y0() - kHalo + ty;
             if (gy < 0 || gy >= ny) continue;
             int side = which < 2 ? 0 : 1, kk = which & 1;
             if ((side == 0 && !westT) || (side == 1 && !eastT)) continue;
             int gx = side == 0 ? -1 - kk : nx + kk;
-            int tx = gx - x0 + kHalo;
+            int tx = gx - O.x0() + kHalo;
             if (tx < 0 || tx >= kTileIn) continue;
             int sx = side == 0 ? kk : nx - 1 - kk;
-            int stx = sx - x0 + kHalo;
+            int stx = sx - O.x0() + kHalo;
             int gi = ty * kStride + tx, si = ty * kStride + stx;
             if ((C.sine >> side) & 1) {
                 const real *tb = A.ghost + ghost_index(A.tsel, side, kk, 0, gy + 2, C.npos);
@@ -629,14 +684,14 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_
     if (southT || northT) {
         for (int k = tid; k < 4 * (kTileIn - 2); k += kStencilThreads) {
             int tx = 1 + k % (kTileIn - 2), which = k / (kTileIn - 2);
-            int gx = x0 - kHalo + tx;
+            int gx = O.x0() - kHalo + tx;
             int side = which < 2 ? 2 : 3, kk = which & 1;
             if ((side == 2 && !southT) || (side == 3 && !northT)) continue;
             int gy = side == 2 ? -1 - kk : ny + kk;
-            int ty = gy - y0 + kHalo;
+            int ty = gy - O.y0() + kHalo;
             if (ty < 0 || ty >= kTileIn) continue;
             int sy = side == 2 ? kk : ny - 1 - kk;
-            int sty = sy - y0 + kHalo;
+            int sty = sy - O.y0() + kHalo;
             int gi = ty * kStride + tx, si = sty * kStride + tx;
             if ((C.sine >> side) & 1) {
                 const real *tb = A.ghost + ghost_index(A.tsel, side, kk, 0, gx + 2, C.npos);
@@ -737,7 +792,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_
     constexpr int kRows = kTile / (kStencilThreads / 32);   // rows per thread
     Carry<real> nw, nu, nv;                                  // next row's carries
     {
-        const int i = x0 + lane, j = y0 + (tid >> 5);
+        const int i = O.x0() + lane, j = O.y0() + (tid >> 5);
         if (i < nx && j < ny) {
             const size_t kr = (size_t)j * G.px + i;
             nw = load_carry(A, 0, kr);
@@ -748,7 +803,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_
 #pragma unroll 1
     for (int rr = 0; rr < kRows; rr++) {
         const int cx = lane, cy = (tid >> 5) + rr * (kStencilThreads / 32);
-        const int i = x0 + cx, j = y0 + cy;
+        const int i = O.x0() + cx, j = O.y0() + cy;
         const bool valid = i < nx && j < ny;
         const int o = (cy + kHalo) * kStride + cx + kHalo;
         const size_t kr = (size_t)j * G.px + i;
@@ -827,17 +882,54 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_
         }
         const bool dry = valid && (w1 - Bb <= real(0));
         unsigned bits = __ballot_sync(0xffffffffu, dry);
-        if (lane == 0 && j < ny) A.mask_r[(size_t)j * G.nwx + (x0 >> 5)] = bits;
+        if (lane == 0 && j < ny) A.mask_r[(size_t)j * G.nwx + (O.x0() >> 5)] = bits;
         if (dry) atomicOr(&sm.colbits[cx], 1u << cy);
         sm.Vout[cy][cx] = dV;
     }
     __syncthreads();
     for (int k = tid; k < kTile * kTile; k += kStencilThreads) {
         int c = k / kTile, r = k % kTile;
-        int i = x0 + c, j = y0 + r;
+        int i = O.x0() + c, j = O.y0() + r;
         if (i < nx && j < ny) A.Vc_out[(size_t)i * G.py + j] = sm.Vout[r][c];
     }
-    if (tid < kTile && x0 + tid < nx) A.mask_c[(size_t)(x0 + tid) * G.nwy + (y0 >> 5)] = sm.colbits[tid];
+    if (tid < kTile && O.x0() + tid < nx) A.mask_c[(size_t)(O.x0() + tid) * G.nwy + (O.y0() >> 5)] = sm.colbits[tid];
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_stencil(const __grid_constant__ StencilArgs<real> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stencil_tile(A, GridOrigin(), smem_raw);
+}
+
+// Copy a scenario's argument block (device memory) into shared memory.
+template <typename T>
+__device__ __forceinline__ void load_args(T &dst, const T *src)
+{
+    const int nw = (int)(sizeof(T) / sizeof(int));
+    int *d = reinterpret_cast<int *>(&dst);
+    const int *s = reinterpret_cast<const int *>(src);
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) d[k] = s[k];
+}
+
+// Ensemble: the tiles of every member in one launch; block b belongs to the
+// member whose tile range [start[s], start[s+1]) holds it.
+template <typename real>
+__global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 3 : 2)
+    k_stencil_batch(const StencilArgs<real> *__restrict__ args, const int *__restrict__ start, int nmem)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int origin[2];
+    const int s = find_owner(start, nmem, blockIdx.x);
+    const StencilArgs<real> &A = args[s];
+    if (threadIdx.x == 0) {
+        const int t = blockIdx.x - start[s];
+        const int tiles_x = (args[s].geo.nx + kTile - 1) / kTile;
+        origin[0] = (t % tiles_x) * kTile;
+        origin[1] = (t / tiles_x) * kTile;
+    }
+    __syncthreads();
+    stencil_tile(A, SharedOrigin{origin}, smem_raw);
 }
 
 // ------------------------------------------------------------ line solves
@@ -863,14 +955,10 @@ __device__ __forceinline__ int seg_slot(int k, int mshift, int sp)
     return (k & ((1 << mshift) - 1)) * sp + (k >> mshift);
 }
 
+// One line of one family (x-row or y-column): the whole solve and epilogue.
 template <typename real, int M>
-__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(LinePair<real> PA)
+__device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, unsigned char *smem_raw)
 {
-    // blocks [0, ny) solve x-rows, the rest y-columns
-    const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
-    const LineArgs<real> &A = PA.L[fam];
-    const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n, S = A.nseg, N2 = 2 * S;
     constexpr int m = M;                             // rows per segment
     const int mshift = A.mshift, sp = A.sp;
@@ -1081,6 +1169,30 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(LinePa
     }
 }
 
+template <typename real, int M>
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(const __grid_constant__ LinePair<real> PA)
+{
+    // blocks [0, ny) solve x-rows, the rest y-columns
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
+    const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
+    line_solve<real, M>(PA.L[fam], line, smem_raw);
+}
+
+// Ensemble: the lines of every member and family (all of one segment length
+// M) in one launch; block b belongs to family f with b in [start[f], start[f+1]).
+template <typename real, int M>
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512)
+    k_lines_batch(const LineArgs<real> *__restrict__ args, const int *__restrict__ start, int nfam)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) LineArgs<real> A;
+    const int f = find_owner(start, nfam, blockIdx.x);
+    load_args(A, args + f);
+    __syncthreads();
+    line_solve<real, M>(A, blockIdx.x - start[f], smem_raw);
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
@@ -1199,6 +1311,30 @@ cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_ghost_batch(const GhostArgs<real> *args, const int *start, int n, int nblocks, int64_t k,
+                               cudaStream_t st)
+{
+    if (nblocks > 0) k_ghost_batch<real><<<nblocks, 128, 0, st>>>(args, start, n, k);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int *start, int n, int nblocks,
+                                 cudaStream_t st)
+{
+    static bool configured = false;
+    const size_t smem = sizeof(StencilSmem<real>);
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_batch<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (nblocks > 0) k_stencil_batch<real><<<nblocks, kStencilThreads, smem, st>>>(args, start, n);
+    return cudaGetLastError();
+}
+
 int line_seg_shift(int n, int real_bytes)
 {
     // 16 rows per segment (32 for lines above 8192 FP32 / 4096 FP64 rows, so
@@ -1262,6 +1398,25 @@ cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_lines_batch(const LineArgs<real> *args, const int *start, int nfam, int nblocks, int mshift,
+                               int threads, size_t smem, cudaStream_t st)
+{
+    static int configured[6] = {0, 0, 0, 0, 0, 0};
+    if (mshift < 1 || mshift > 5 || threads < 32 || threads > (sizeof(real) == 4 ? 1024 : 512))
+        return cudaErrorInvalidValue;
+    auto *kern = mshift == 1 ? k_lines_batch<real, 2> : mshift == 2 ? k_lines_batch<real, 4>
+               : mshift == 3 ? k_lines_batch<real, 8> : mshift == 4 ? k_lines_batch<real, 16>
+                             : k_lines_batch<real, 32>;
+    if ((int)smem > configured[mshift]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[mshift] = (int)smem;
+    }
+    if (nblocks > 0) kern<<<nblocks, threads, smem, st>>>(args, start, nfam);
+    return cudaGetLastError();
+}
+
 #define CEL_INSTANTIATE(real)                                                                           \
     template cudaError_t launch_corners<real>(const Geo &, const real *, real *, cudaStream_t);           \
     template cudaError_t launch_static_cells<real>(const Geo &, const Phys &, const real *, real *,      \
@@ -1290,7 +1445,13 @@ cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
                                                   cudaStream_t);                                        \
     template cudaError_t launch_stencil<real>(const StencilArgs<real> &, cudaStream_t);                  \
     template cudaError_t launch_lines<real>(const LinePair<real> &, cudaStream_t);                       \
-    template size_t line_smem_bytes<real>(int, int);
+    template size_t line_smem_bytes<real>(int, int);                                                    \
+    template cudaError_t launch_ghost_batch<real>(const GhostArgs<real> *, const int *, int, int, int64_t, \
+                                                  cudaStream_t);                                        \
+    template cudaError_t launch_stencil_batch<real>(const StencilArgs<real> *, const int *, int, int,     \
+                                                    cudaStream_t);                                      \
+    template cudaError_t launch_lines_batch<real>(const LineArgs<real> *, const int *, int, int, int, int, \
+                                                  size_t, cudaStream_t);
 
 CEL_INSTANTIATE(float)
 CEL_INSTANTIATE(double)

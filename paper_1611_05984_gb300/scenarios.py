@@ -180,3 +180,31 @@ def random_bed(nx: int, ny: int, seed: int, lo: float, hi: float,
         zp = np.pad(z, 1, mode="edge")
         z = (zp[:-2, 1:-1] + zp[2:, 1:-1] + zp[1:-1, :-2] + zp[1:-1, 2:] + zp[1:-1, 1:-1]) / 5.0
     return np.ascontiguousarray(z)
+
+
+def ensemble(n: int = 256, seed: int = 4, steps: int = 5000, K: int = 1, cr: float = 0.1,
+             d0: float = 10.0, nx_range=(128, 1024), ny_range=(128, 512)) -> list:
+    """n beach scenarios of uneven size and forcing, for ensemble runs.
+
+    Per scenario: n_x ~ U{128..1024}, n_y ~ U{128..512}, sine amplitude
+    a ~ U(0.05, 1) m, period T ~ U(5, 15) s, beach slope ~ U(1/50, 1/10),
+    shoal count ~ U{0..12}, bed seed seed * 1000 + k.  The grid spacing is
+    the larger of 1 m and the spacing that puts the toe of the beach (depth
+    d0) at 15 % of the domain length, so that every maker stands in water d0
+    deep; dt follows from Courant cr on d0; sponges of n_y / 8 cells (at most
+    50) on the north and south sides."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nx = int(rng.integers(nx_range[0], nx_range[1] + 1))
+        ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
+        a = float(rng.uniform(0.05, 1.0))
+        T = float(rng.uniform(5.0, 15.0))
+        slope = float(rng.uniform(1.0 / 50.0, 1.0 / 10.0))
+        nshoal = int(rng.integers(0, 13))
+        dx = max(1.0, math.ceil(d0 / slope / (0.7 * nx) * 4.0) / 4.0)
+        sc = beach(nx, ny, dx, seed=seed * 1000 + k, nshoal=nshoal, amp=a, period=T,
+                   sponge=min(50, ny // 8), steps=steps, K=K, cr=cr, slope=slope, d0=d0)
+        sc.name = f"ensemble{k}_{nx}x{ny}"
+        out.append(sc)
+    return out

@@ -76,3 +76,20 @@ def test_create_rejects_bad_arguments_without_gpu_work():
     assert L.cel_create(ctypes.byref(g), ctypes.byref(p), 256, 257, 1 << 30, None, ctypes.byref(h)) == 1
     assert L.cel_create(ctypes.byref(g), ctypes.byref(p), 256, 512, 16, None, ctypes.byref(h)) == 2
     assert not h.value
+
+
+def test_ensemble_rejects_empty_member_lists_without_gpu_work():
+    lib = celeris.load()
+    nb = ctypes.c_size_t(123)
+    assert lib.cel_ensemble_table_bytes(None, 0, ctypes.byref(nb)) == 1
+    assert nb.value == 123
+    out = ctypes.c_void_p()
+    msg = ctypes.create_string_buffer(128)
+    assert lib.cel_ensemble_create(None, 0, None, 0, None, ctypes.byref(out), msg, len(msg)) == 1
+    assert out.value is None
+    assert b"at least one member" in msg.value
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert lib.cel_ensemble_table_bytes(arr, 2, ctypes.byref(nb)) == 1
+    assert lib.cel_ensemble_step(None, 1) == 1
+    assert lib.cel_ensemble_last_error(None) == b""
+    lib.cel_ensemble_destroy(None)

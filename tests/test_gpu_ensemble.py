@@ -1,0 +1,168 @@
+"""Ensembles (cel_ensemble_*): many grids stepped with one launch per kernel
+kind and stage, against the same grids stepped one cel_step at a time.
+
+The bar is bitwise equality of w, P and Q for every member: the ensemble
+launches the same per-tile and per-line code with the same arguments, so
+nothing may differ, in FP32 or in FP64.  The member mix covers uneven and
+ragged sizes, lines of different segment lengths (several line launches per
+stage), sine makers with one and three components, sponges, walls, the NLSW
+model, friction laws and per-member dt.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_05984_gb300 import scenarios as sc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dtype(prec):
+    return torch.float64 if prec == "f64" else torch.float32
+
+
+def _members(K):
+    out = [sc.beach(nx=200, ny=150, sponge=20, K=K),
+           sc.beach_directional(nx=160, ny=130, sponge=16, nshoal=3, K=K),
+           sc.soliton_channel(nx=250, ny=30, K=K, x0=5.0)]
+    # NLSW dam break on a dry bed
+    nx, ny = 180, 40
+    x = (np.arange(nx) + 0.5) * 0.05
+    d = sc.flat_basin(nx, ny, 0.05, 0.0, 0.05 * 0.05 / math.sqrt(9.81), model=1, K=K)
+    d.z = np.zeros((ny, nx))
+    d.w0 = np.tile(np.where(x < 3.0, 1.0, 0.0), (ny, 1))
+    out.append(d)
+    # a long thin and a short wide grid: other segment lengths of the lines
+    out.append(sc.flat_basin(1100, 36, 1.0, 4.0, 0.1 / math.sqrt(9.81 * 4.0), K=K, friction=1, fcoef=0.002))
+    out[-1].sides[sc.W] = sc.Side(sc.SINE, 0, ((0.05, 6.0, 0.2, 0.4),))
+    out.append(sc.flat_basin(20, 300, 1.0, 4.0, 0.1 / math.sqrt(9.81 * 4.0), K=K))
+    out[-1].sides[sc.S] = sc.Side(sc.SINE, 0, ((0.03, 7.0, math.pi / 2, 0.0),))
+    out[-1].sides[sc.N] = sc.Side(sc.SPONGE, 30)
+    out += sc.ensemble(n=4, seed=9, K=K, nx_range=(40, 300), ny_range=(33, 200))
+    return out
+
+
+def _seg_shift(n, es):
+    # segment length of the line solver (rows per segment = 2**shift)
+    sh = 5 if n > (4096 if es == 8 else 8192) else 4
+    while sh > 1 and (n >> sh) < 2:
+        sh -= 1
+    return sh
+
+
+def _pairs(scens, prec):
+    from paper_1611_05984_gb300 import celeris
+    a = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    b = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    return a, b
+
+
+def _assert_equal(a, b):
+    for k, (x, y) in enumerate(zip(a, b)):
+        assert x.check_finite() and y.check_finite(), f"member {k} blew up"
+        for u, v, name in zip(x.state(), y.state(), "wPQ"):
+            assert torch.equal(u, v), f"member {k}: {name} differs"
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_ensemble_bitwise_equals_single_runs(prec):
+    """The whole mix with one AM4 iteration (K = 1)."""
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)
+    alone, together = _pairs(scens, prec)
+    ens = celeris.Ensemble(together)
+    for n in (1, 2, 9, 40):            # the Euler steps, then more than one cycle of the tables
+        for s in alone:
+            s.step(n)
+        ens.step(n)
+        _assert_equal(alone, together)
+
+
+@pytest.mark.parametrize("K,prec", [(0, "f32"), (0, "f64"), (2, "f32")])
+def test_ensemble_other_corrector_counts(K, prec):
+    """K = 0 (predictor only, AB3 carries) and K = 2 (three stages per step)
+    on the members that are stable without an odd K: the walled channel, the
+    dam break and the flat basins."""
+    from paper_1611_05984_gb300 import celeris
+    scens = [m for m in _members(K) if m.name.startswith(("soliton", "flat"))]
+    alone, together = _pairs(scens, prec)
+    ens = celeris.Ensemble(together)
+    for n in (3, 30):
+        for s in alone:
+            s.step(n)
+        ens.step(n)
+        _assert_equal(alone, together)
+
+
+def test_ensemble_gauges_boundary_change_and_restore():
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)[:4]
+    alone, together = _pairs(scens, "f32")
+    for s in alone + together:
+        s.set_gauges([(5, 5), (20, 10)], 3, 50)
+    ens = celeris.Ensemble(together)
+    for s in alone:
+        s.step(30)
+    ens.step(30)
+    _assert_equal(alone, together)
+    for x, y in zip(alone, together):
+        np.testing.assert_array_equal(x.read_gauges(50), y.read_gauges(50))
+    # a new boundary on one member: the ensemble rebuilds its argument tables
+    for s in (alone[0], together[0]):
+        s.set_boundary(sc.S, sc.SOLID)
+    # a checkpoint restored into every member (same step count for all)
+    cks = [s.checkpoint() for s in together]
+    for s in alone:
+        s.step(25)
+    ens.step(25)
+    _assert_equal(alone, together)
+    for s, ck in zip(together, cks):
+        s.restore(ck)
+    for s, ck in zip(alone, cks):
+        s.restore(ck)
+    for s in alone:
+        s.step(12)
+    ens.step(12)
+    _assert_equal(alone, together)
+
+
+def test_ensemble_launch_count():
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)
+    together = [celeris.from_scenario(s, dtype=torch.float32) for s in scens]
+    ens = celeris.Ensemble(together)
+    ens.step(3)
+    first = ens.last_launch_count()
+    ens.step(1)
+    groups = len({_seg_shift(n, 4) for s in scens for n in (s.nx, s.ny)})
+    assert groups >= 2
+    assert ens.last_launch_count() == 1 + 2 * (1 + groups)     # ghost tables + 2 stages
+    assert first > 3 * (1 + groups)                            # Eckart tables, Euler steps
+
+
+def test_ensemble_lockstep_and_argument_errors():
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)[:3]
+    together = [celeris.from_scenario(s, dtype=torch.float32) for s in scens]
+    ens = celeris.Ensemble(together)
+    ens.step(2)
+    together[1].step(1)
+    with pytest.raises(celeris.CelerisError, match="lockstep"):
+        ens.step(1)
+    with pytest.raises(celeris.CelerisError):
+        celeris.Ensemble([together[0], together[0]])
+    f64 = celeris.from_scenario(scens[0], dtype=torch.float64)
+    with pytest.raises(celeris.CelerisError):
+        celeris.Ensemble([together[0], f64])
+
+
+def test_ensemble_256_uneven_scenarios_stay_finite():
+    """The 256-scenario mix (about 4.8e7 cells, FP32), 300 steps."""
+    from paper_1611_05984_gb300 import celeris
+    members = [celeris.from_scenario(s, dtype=torch.float32) for s in sc.ensemble()]
+    ens = celeris.Ensemble(members)
+    ens.step(300)
+    for m in members:
+        assert m.check_finite()
