@@ -217,6 +217,12 @@ cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *tabl
 cel_status cel_ensemble_step(cel_ensemble *e, int32_t nsteps);
 /* Kernel launches issued by the most recent cel_ensemble_step call. */
 cel_status cel_ensemble_last_launch_count(const cel_ensemble *e, int64_t *launches);
+/* Per-kernel event timing of the ensemble's launches, as cel_profile_* for a
+ * solver (0: stencil, 1: line solves, one entry per line launch, 2: ghost
+ * tables). */
+cel_status cel_ensemble_profile_enable(cel_ensemble *e, int32_t capacity);
+cel_status cel_ensemble_profile_read(cel_ensemble *e, double ms[3], int64_t count[3]);
+cel_status cel_ensemble_profile_disable(cel_ensemble *e);
 const char *cel_ensemble_last_error(const cel_ensemble *e);  /* never NULL */
 /* Release the handle (not the members, not the table).  Does not synchronise. */
 void cel_ensemble_destroy(cel_ensemble *e);

@@ -34,6 +34,7 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_load_checkpoint", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
+           "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
            "cel_ensemble_last_error", "cel_ensemble_destroy", "cel_advance_noalloc", "cel_status_string",
            "cel_last_error", "cel_destroy"]
 
@@ -109,6 +110,9 @@ def load(build_if_missing: bool = True):
                                           ctypes.c_char_p, sz]
         L.cel_ensemble_step.argtypes = [vp, i32]
         L.cel_ensemble_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+        L.cel_ensemble_profile_enable.argtypes = [vp, i32]
+        L.cel_ensemble_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
+        L.cel_ensemble_profile_disable.argtypes = [vp]
         L.cel_ensemble_last_error.restype = ctypes.c_char_p
         L.cel_ensemble_last_error.argtypes = [vp]
         L.cel_ensemble_destroy.argtypes = [vp]
@@ -345,6 +349,23 @@ class Ensemble:
         v = ctypes.c_int64()
         self.L.cel_ensemble_last_launch_count(self._h, ctypes.byref(v))
         return v.value
+
+    def profile_enable(self, capacity: int):
+        st = self.L.cel_ensemble_profile_enable(self._h, int(capacity))
+        if st != CEL_OK:
+            raise CelerisError(st, self.L.cel_ensemble_last_error(self._h).decode())
+
+    def profile_read(self):
+        """{kernel: (ms summed, launches)} for 'stencil', 'lines', 'ghosts'."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        st = self.L.cel_ensemble_profile_read(self._h, ms, n)
+        if st != CEL_OK:
+            raise CelerisError(st, self.L.cel_ensemble_last_error(self._h).decode())
+        return {k: (ms[i], n[i]) for i, k in enumerate(("stencil", "lines", "ghosts"))}
+
+    def profile_disable(self):
+        self.L.cel_ensemble_profile_disable(self._h)
 
     def close(self):
         if self._h is not None:

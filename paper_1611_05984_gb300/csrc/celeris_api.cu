@@ -116,6 +116,78 @@ bool params_ok(const cel_params *p)
     return true;
 }
 
+// Optional per-kernel timing: CUDA event pairs recorded around launches.
+struct EventProf {
+    cudaEvent_t *beg = nullptr, *end = nullptr;
+    int *kind = nullptr;
+    int cap = 0, used = 0;
+
+    void release()
+    {
+        for (int k = 0; k < cap; k++) {
+            cudaEventDestroy(beg[k]);
+            cudaEventDestroy(end[k]);
+        }
+        delete[] beg;
+        delete[] end;
+        delete[] kind;
+        beg = end = nullptr;
+        kind = nullptr;
+        cap = used = 0;
+    }
+    cudaError_t create(int capacity)
+    {
+        release();
+        beg = new cudaEvent_t[capacity];
+        end = new cudaEvent_t[capacity];
+        kind = new int[capacity];
+        for (int k = 0; k < capacity; k++) {
+            cudaError_t e1 = cudaEventCreate(&beg[k]);
+            cudaError_t e2 = e1 == cudaSuccess ? cudaEventCreate(&end[k]) : e1;
+            if (e2 != cudaSuccess) {
+                if (e1 == cudaSuccess) cudaEventDestroy(beg[k]);
+                cap = k;
+                release();
+                return e2;
+            }
+        }
+        cap = capacity;
+        used = 0;
+        return cudaSuccess;
+    }
+    int begin(int kd, cudaStream_t st)
+    {
+        if (!cap || used >= cap) return -1;
+        int k = used++;
+        kind[k] = kd;
+        cudaEventRecord(beg[k], st);
+        return k;
+    }
+    void finish(int k, cudaStream_t st)
+    {
+        if (k >= 0) cudaEventRecord(end[k], st);
+    }
+    // summed milliseconds and counts per kind (0..2); synchronises the stream
+    cudaError_t read(cudaStream_t st, double ms[3], int64_t count[3])
+    {
+        for (int k = 0; k < 3; k++) {
+            ms[k] = 0.0;
+            count[k] = 0;
+        }
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        for (int k = 0; k < used; k++) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, beg[k], end[k]);
+            if (e != cudaSuccess) return e;
+            ms[kind[k]] += t;
+            count[kind[k]] += 1;
+        }
+        used = 0;
+        return cudaSuccess;
+    }
+};
+
 }  // namespace
 
 struct cel_solver {
@@ -140,10 +212,7 @@ struct cel_solver {
     int ktab_dirty;   // boundaries or bed changed: rebuild the Eckart table
     uint64_t gen;     // counts boundary and bed changes (ensembles rebuild their tables)
     std::string err;
-    // optional per-kernel event timing
-    cudaEvent_t *ev_beg, *ev_end;
-    int *ev_kind;
-    int ev_cap, ev_used;
+    EventProf prof;   // optional per-kernel event timing
 
     template <typename T>
     T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
@@ -168,33 +237,11 @@ cel_status cuda_fail(cel_solver *s, cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(s, e_, where); \
     } while (0)
 
-int prof_begin(cel_solver *s, int kind)
-{
-    if (!s->ev_cap || s->ev_used >= s->ev_cap) return -1;
-    int k = s->ev_used++;
-    s->ev_kind[k] = kind;
-    cudaEventRecord(s->ev_beg[k], s->stream);
-    return k;
-}
+int prof_begin(cel_solver *s, int kind) { return s->prof.begin(kind, s->stream); }
 
-void prof_end(cel_solver *s, int k)
-{
-    if (k >= 0) cudaEventRecord(s->ev_end[k], s->stream);
-}
+void prof_end(cel_solver *s, int k) { s->prof.finish(k, s->stream); }
 
-void prof_free(cel_solver *s)
-{
-    for (int k = 0; k < s->ev_cap; k++) {
-        cudaEventDestroy(s->ev_beg[k]);
-        cudaEventDestroy(s->ev_end[k]);
-    }
-    delete[] s->ev_beg;
-    delete[] s->ev_end;
-    delete[] s->ev_kind;
-    s->ev_beg = s->ev_end = nullptr;
-    s->ev_kind = nullptr;
-    s->ev_cap = s->ev_used = 0;
-}
+void prof_free(cel_solver *s) { s->prof.release(); }
 
 template <typename real>
 cel_status derive_static(cel_solver *s, const void *z)
@@ -484,9 +531,6 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->gen = 0;
     s->step = 0;
     s->cur = s->pcur = 0;
-    s->ev_beg = s->ev_end = nullptr;
-    s->ev_kind = nullptr;
-    s->ev_cap = s->ev_used = 0;
     cudaError_t e = cudaMemsetAsync(workspace_dev, 0, L.total, s->stream);
     if (e != cudaSuccess) {
         delete s;
@@ -785,39 +829,14 @@ cel_status cel_load_checkpoint(cel_solver *s, const void *src_dev, size_t bytes)
 cel_status cel_profile_enable(cel_solver *s, int32_t capacity)
 {
     if (!s || capacity < 1 || capacity > (1 << 20)) return fail(s, CEL_ERR_INVALID_ARG, "bad profile capacity");
-    prof_free(s);
-    s->ev_beg = new cudaEvent_t[capacity];
-    s->ev_end = new cudaEvent_t[capacity];
-    s->ev_kind = new int[capacity];
-    for (int k = 0; k < capacity; k++) {
-        cudaError_t e1 = cudaEventCreate(&s->ev_beg[k]);
-        cudaError_t e2 = cudaEventCreate(&s->ev_end[k]);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
-            s->ev_cap = k + (e1 == cudaSuccess && e2 == cudaSuccess);
-            prof_free(s);
-            return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "profile events");
-        }
-    }
-    s->ev_cap = capacity;
-    s->ev_used = 0;
+    CEL_CUDA(s, s->prof.create(capacity), "profile events");
     return CEL_OK;
 }
 
 cel_status cel_profile_read(cel_solver *s, double ms[3], int64_t count[3])
 {
     if (!s || !ms || !count) return CEL_ERR_INVALID_ARG;
-    for (int k = 0; k < 3; k++) {
-        ms[k] = 0.0;
-        count[k] = 0;
-    }
-    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "profile read");
-    for (int k = 0; k < s->ev_used; k++) {
-        float t = 0.f;
-        CEL_CUDA(s, cudaEventElapsedTime(&t, s->ev_beg[k], s->ev_end[k]), "profile elapsed");
-        ms[s->ev_kind[k]] += t;
-        count[s->ev_kind[k]] += 1;
-    }
-    s->ev_used = 0;
+    CEL_CUDA(s, s->prof.read(s->stream, ms, count), "profile read");
     return CEL_OK;
 }
 
@@ -936,9 +955,6 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.step = first_step;
     s.nh = 0;
     s.cur = s.pcur = 0;
-    s.ev_beg = s.ev_end = nullptr;
-    s.ev_kind = nullptr;
-    s.ev_cap = s.ev_used = 0;
     cel_status st = CEL_OK;
     if (bcs)
         for (int side = 0; side < 4 && st == CEL_OK; side++) st = cel_set_boundary(&s, side, &bcs[side]);
@@ -968,9 +984,9 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
 // were stepped alone.
 
 struct cel_ensemble {
-    struct Group {            // line families of one segment length
+    struct Group {            // line families of one segment length and block size
         int mshift, first, nfam, blocks, threads;
-        size_t smem, off_start;
+        size_t smem, off_desc;
     };
     std::vector<cel_solver *> m;
     int es, K;
@@ -978,7 +994,7 @@ struct cel_ensemble {
     unsigned char *tab;
     size_t tab_bytes;
     int tiles;                           // stencil blocks over all members
-    size_t off_tile_start;               // int[N + 1]
+    size_t off_tile_desc;                // int2 per stencil block
     std::vector<std::pair<int, int>> fam;   // (member, dir) in table order
     std::vector<Group> groups;
     std::vector<int> gmem;               // members with a sine maker
@@ -991,6 +1007,7 @@ struct cel_ensemble {
     std::vector<uint64_t> keys;          // key of each filled entry
     uint64_t gen_sum;
     int64_t launches;
+    EventProf prof;
     std::string err;
 };
 
@@ -1001,7 +1018,7 @@ struct EnsPlan {
     std::vector<std::pair<int, int>> fam;
     std::vector<cel_ensemble::Group> groups;
     std::vector<int> gmem;
-    size_t off_tile_start = 0, off_gargs = 0, off_gstart = 0, sarg_bytes = 0, entry_bytes = 0, off_entries = 0;
+    size_t off_tile_desc = 0, off_gargs = 0, off_gstart = 0, sarg_bytes = 0, entry_bytes = 0, off_entries = 0;
     int cap = 0;
     size_t total = 0;
 };
@@ -1018,42 +1035,41 @@ void plan_t(cel_solver *const *ms, int n, EnsPlan &P)
     P.tiles = 0;
     for (int e = 0; e < n; e++)
         P.tiles += ((ms[e]->geo.nx + kTile - 1) / kTile) * ((ms[e]->geo.ny + kTile - 1) / kTile);
-    P.off_tile_start = take(sizeof(int) * (size_t)(n + 1));
-    // line families grouped by segment length, longest lines first in a group
+    P.off_tile_desc = take(sizeof(int2) * (size_t)P.tiles);
+    // line families grouped by segment length and block size (one launch
+    // each), longest lines first within a group
     P.fam.clear();
     P.groups.clear();
-    for (int sh = 1; sh <= 5; sh++) {
-        std::vector<std::pair<int, int>> g;
-        for (int e = 0; e < n; e++)
-            for (int dir = 0; dir < 2; dir++) {
-                const int len = dir == 0 ? ms[e]->geo.nx : ms[e]->geo.ny;
-                if (line_seg_shift(len, ms[e]->es) == sh) g.push_back({e, dir});
+    auto len_of = [&](const std::pair<int, int> &f) { return f.second == 0 ? ms[f.first]->geo.nx : ms[f.first]->geo.ny; };
+    auto seg_of = [&](const std::pair<int, int> &f) { return f.second == 0 ? ms[f.first]->nseg_x : ms[f.first]->nseg_y; };
+    for (int sh = 1; sh <= 5; sh++)
+        for (int th = 32; th <= 1024; th += 32) {
+            std::vector<std::pair<int, int>> g;
+            for (int e = 0; e < n; e++)
+                for (int dir = 0; dir < 2; dir++) {
+                    const std::pair<int, int> f(e, dir);
+                    if (line_seg_shift(len_of(f), ms[e]->es) == sh && round_up_i(seg_of(f), 32) == th)
+                        g.push_back(f);
+                }
+            if (g.empty()) continue;
+            std::stable_sort(g.begin(), g.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+                return len_of(a) > len_of(b);
+            });
+            cel_ensemble::Group G;
+            G.mshift = sh;
+            G.threads = th;
+            G.first = (int)P.fam.size();
+            G.nfam = (int)g.size();
+            G.blocks = 0;
+            G.smem = 0;
+            for (auto &f : g) {
+                G.blocks += f.second == 0 ? ms[f.first]->geo.ny : ms[f.first]->geo.nx;
+                G.smem = std::max(G.smem, line_smem_bytes<real>(len_of(f), seg_of(f)));
+                P.fam.push_back(f);
             }
-        if (g.empty()) continue;
-        std::stable_sort(g.begin(), g.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
-            const int la = a.second == 0 ? ms[a.first]->geo.nx : ms[a.first]->geo.ny;
-            const int lb = b.second == 0 ? ms[b.first]->geo.nx : ms[b.first]->geo.ny;
-            return la > lb;
-        });
-        cel_ensemble::Group G;
-        G.mshift = sh;
-        G.first = (int)P.fam.size();
-        G.nfam = (int)g.size();
-        G.blocks = 0;
-        G.threads = 64;
-        G.smem = 0;
-        for (auto &f : g) {
-            const cel_solver *s = ms[f.first];
-            const int len = f.second == 0 ? s->geo.nx : s->geo.ny;
-            const int nseg = f.second == 0 ? s->nseg_x : s->nseg_y;
-            G.blocks += f.second == 0 ? s->geo.ny : s->geo.nx;
-            G.threads = std::max(G.threads, round_up_i(nseg, 32));
-            G.smem = std::max(G.smem, line_smem_bytes<real>(len, nseg));
-            P.fam.push_back(f);
+            G.off_desc = take(sizeof(int2) * (size_t)G.blocks);
+            P.groups.push_back(G);
         }
-        G.off_start = take(sizeof(int) * (size_t)(G.nfam + 1));
-        P.groups.push_back(G);
-    }
     P.gmem.clear();
     P.gblocks = 0;
     for (int e = 0; e < n; e++) {
@@ -1226,9 +1242,11 @@ cel_status ens_step_t(cel_ensemble *e, int nsteps)
                 launches += 1;
             }
             const int64_t k = e->m[e->gmem[0]]->step - e->gstep0[0];
+            const int pg = e->prof.begin(2, e->stream);
             ENS_CUDA(e, launch_ghost_batch<real>(reinterpret_cast<const GhostArgs<real> *>(e->tab + e->off_gargs),
                                                  reinterpret_cast<const int *>(e->tab + e->off_gstart),
                                                  (int)e->gmem.size(), e->gblocks, k, e->stream), "ensemble ghost tables");
+            e->prof.finish(pg, e->stream);
             launches += 1;
         }
         for (int stage = 0; stage <= Kn; stage++) {
@@ -1236,15 +1254,19 @@ cel_status ens_step_t(cel_ensemble *e, int nsteps)
             cel_status st = ens_entry<real>(e, stage, Kn, &idx);
             if (st != CEL_OK) return st;
             const unsigned char *ent = e->tab + e->off_entries + (size_t)idx * e->entry_bytes;
+            const int pe = e->prof.begin(0, e->stream);
             ENS_CUDA(e, launch_stencil_batch<real>(reinterpret_cast<const StencilArgs<real> *>(ent),
-                                                   reinterpret_cast<const int *>(e->tab + e->off_tile_start), n,
+                                                   reinterpret_cast<const int2 *>(e->tab + e->off_tile_desc),
                                                    e->tiles, e->stream), "ensemble stencil");
+            e->prof.finish(pe, e->stream);
             launches += 1;
             const LineArgs<real> *la = reinterpret_cast<const LineArgs<real> *>(ent + e->sarg_bytes);
             for (const cel_ensemble::Group &G : e->groups) {
-                ENS_CUDA(e, launch_lines_batch<real>(la + G.first, reinterpret_cast<const int *>(e->tab + G.off_start),
-                                                     G.nfam, G.blocks, G.mshift, G.threads, G.smem, e->stream),
+                const int pl = e->prof.begin(1, e->stream);
+                ENS_CUDA(e, launch_lines_batch<real>(la + G.first, reinterpret_cast<const int2 *>(e->tab + G.off_desc),
+                                                     G.blocks, G.mshift, G.threads, G.smem, e->stream),
                          "ensemble line solves");
+                e->prof.finish(pl, e->stream);
                 launches += 1;
             }
         }
@@ -1305,7 +1327,7 @@ cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *tabl
     e->tab = (unsigned char *)table_dev;
     e->tab_bytes = table_bytes;
     e->tiles = P.tiles;
-    e->off_tile_start = P.off_tile_start;
+    e->off_tile_desc = P.off_tile_desc;
     e->fam = P.fam;
     e->groups = P.groups;
     e->gmem = P.gmem;
@@ -1321,20 +1343,26 @@ cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *tabl
     e->gen_sum = 0;
     for (int j = 0; j < n; j++) e->gen_sum += members[j]->gen;
     e->launches = 0;
-    // block ranges of the members' tiles and of each group's line families
-    std::vector<int> ts(n + 1, 0);
-    for (int j = 0; j < n; j++)
-        ts[j + 1] = ts[j] + ((members[j]->geo.nx + kTile - 1) / kTile) * ((members[j]->geo.ny + kTile - 1) / kTile);
-    cudaError_t ce = cudaMemcpyAsync(e->tab + e->off_tile_start, ts.data(), sizeof(int) * ts.size(),
+    // block descriptors: (member, tile) of every stencil block, (family,
+    // line) of every line block
+    std::vector<int2> td;
+    td.reserve(P.tiles);
+    for (int j = 0; j < n; j++) {
+        const int tx = (members[j]->geo.nx + kTile - 1) / kTile, ty = (members[j]->geo.ny + kTile - 1) / kTile;
+        for (int b = 0; b < tx * ty; b++) td.push_back(make_int2(j, ((b / tx) << 16) | (b % tx)));
+    }
+    cudaError_t ce = cudaMemcpyAsync(e->tab + e->off_tile_desc, td.data(), sizeof(int2) * td.size(),
                                      cudaMemcpyHostToDevice, e->stream);
     for (const cel_ensemble::Group &G : e->groups) {
         if (ce != cudaSuccess) break;
-        std::vector<int> fs(G.nfam + 1, 0);
+        std::vector<int2> ld;
+        ld.reserve(G.blocks);
         for (int f = 0; f < G.nfam; f++) {
             const std::pair<int, int> &fm = e->fam[G.first + f];
-            fs[f + 1] = fs[f] + (fm.second == 0 ? members[fm.first]->geo.ny : members[fm.first]->geo.nx);
+            const int nl = fm.second == 0 ? members[fm.first]->geo.ny : members[fm.first]->geo.nx;
+            for (int l = 0; l < nl; l++) ld.push_back(make_int2(f, l));
         }
-        ce = cudaMemcpyAsync(e->tab + G.off_start, fs.data(), sizeof(int) * fs.size(), cudaMemcpyHostToDevice,
+        ce = cudaMemcpyAsync(e->tab + G.off_desc, ld.data(), sizeof(int2) * ld.size(), cudaMemcpyHostToDevice,
                              e->stream);
     }
     if (ce != cudaSuccess) {
@@ -1359,8 +1387,36 @@ cel_status cel_ensemble_last_launch_count(const cel_ensemble *e, int64_t *launch
     return CEL_OK;
 }
 
+cel_status cel_ensemble_profile_enable(cel_ensemble *e, int32_t capacity)
+{
+    if (!e || capacity < 1 || capacity > (1 << 20)) return CEL_ERR_INVALID_ARG;
+    cudaError_t ce = e->prof.create(capacity);
+    if (ce != cudaSuccess) return ens_fail(e, CEL_ERR_CUDA, std::string("profile events: ") + cudaGetErrorString(ce));
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_profile_read(cel_ensemble *e, double ms[3], int64_t count[3])
+{
+    if (!e || !ms || !count) return CEL_ERR_INVALID_ARG;
+    cudaError_t ce = e->prof.read(e->stream, ms, count);
+    if (ce != cudaSuccess) return ens_fail(e, CEL_ERR_CUDA, std::string("profile read: ") + cudaGetErrorString(ce));
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_profile_disable(cel_ensemble *e)
+{
+    if (!e) return CEL_ERR_INVALID_ARG;
+    e->prof.release();
+    return CEL_OK;
+}
+
 const char *cel_ensemble_last_error(const cel_ensemble *e) { return e ? e->err.c_str() : ""; }
 
-void cel_ensemble_destroy(cel_ensemble *e) { delete e; }
+void cel_ensemble_destroy(cel_ensemble *e)
+{
+    if (!e) return;
+    e->prof.release();
+    delete e;
+}
 
 }  // extern "C"

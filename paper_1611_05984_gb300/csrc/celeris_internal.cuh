@@ -203,8 +203,10 @@ template <typename real>
 cudaError_t launch_lines(const LinePair<real> &a, cudaStream_t st);
 
 // Ensembles: one launch covers every member.  The argument blocks live in
-// device memory, one per member (stencil, ghost table) or per line family;
-// start[e] is the first block of entry e (ascending, start[0] = 0).
+// device memory, one per member (stencil, ghost table) or per line family.
+// Ghost tables: start[e] is the first block of entry e (ascending, start[0]
+// = 0).  Stencil and lines: desc[b] = (argument block, tile or line) of
+// block b, the tile as row << 16 | column.
 template <typename real>
 struct GhostArgs {
     Geo g;
@@ -222,12 +224,12 @@ template <typename real>
 cudaError_t launch_ghost_batch(const GhostArgs<real> *args, const int *start, int n, int nblocks, int64_t k,
                                cudaStream_t st);
 template <typename real>
-cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int *start, int n, int nblocks,
-                                 cudaStream_t st);
-// All families of one launch share the segment length 1 << mshift.
+cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, cudaStream_t st);
+// All families of one launch share the segment length 1 << mshift; threads
+// (a multiple of 32) is at least the segment count of every family.
 template <typename real>
-cudaError_t launch_lines_batch(const LineArgs<real> *args, const int *start, int nfam, int nblocks, int mshift,
-                               int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int nblocks, int mshift, int threads,
+                               size_t smem, cudaStream_t st);
 template <typename real>
 size_t line_smem_bytes(int n, int nseg);
 int line_segments(int n, int real_bytes);

@@ -912,22 +912,22 @@ __device__ __forceinline__ void load_args(T &dst, const T *src)
     for (int k = threadIdx.x; k < nw; k += blockDim.x) d[k] = s[k];
 }
 
-// Ensemble: the tiles of every member in one launch; block b belongs to the
-// member whose tile range [start[s], start[s+1]) holds it.
+// Ensemble: the tiles of every member in one launch.  desc[b] names block
+// b's member (x) and tile (y: row << 16 | column); the member's arguments
+// are copied to shared memory.
 template <typename real>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 3 : 2)
-    k_stencil_batch(const StencilArgs<real> *__restrict__ args, const int *__restrict__ start, int nmem)
+    k_stencil_batch(const StencilArgs<real> *__restrict__ args, const int2 *__restrict__ desc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) StencilArgs<real> A;
     __shared__ int origin[2];
-    const int s = find_owner(start, nmem, blockIdx.x);
-    const StencilArgs<real> &A = args[s];
+    const int2 d = desc[blockIdx.x];
     if (threadIdx.x == 0) {
-        const int t = blockIdx.x - start[s];
-        const int tiles_x = (args[s].geo.nx + kTile - 1) / kTile;
-        origin[0] = (t % tiles_x) * kTile;
-        origin[1] = (t / tiles_x) * kTile;
+        origin[0] = (d.y & 0xffff) * kTile;
+        origin[1] = (d.y >> 16) * kTile;
     }
+    load_args(A, args + d.x);
     __syncthreads();
     stencil_tile(A, SharedOrigin{origin}, smem_raw);
 }
@@ -1179,18 +1179,18 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(const 
     line_solve<real, M>(PA.L[fam], line, smem_raw);
 }
 
-// Ensemble: the lines of every member and family (all of one segment length
-// M) in one launch; block b belongs to family f with b in [start[f], start[f+1]).
+// Ensemble: lines of many members and both families in one launch, all of
+// one segment length M.  desc[b] names block b's family (x) and line (y).
 template <typename real, int M>
 __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512)
-    k_lines_batch(const LineArgs<real> *__restrict__ args, const int *__restrict__ start, int nfam)
+    k_lines_batch(const LineArgs<real> *__restrict__ args, const int2 *__restrict__ desc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) LineArgs<real> A;
-    const int f = find_owner(start, nfam, blockIdx.x);
-    load_args(A, args + f);
+    const int2 d = desc[blockIdx.x];
+    load_args(A, args + d.x);
     __syncthreads();
-    line_solve<real, M>(A, blockIdx.x - start[f], smem_raw);
+    line_solve<real, M>(A, d.y, smem_raw);
 }
 
 }  // namespace
@@ -1320,8 +1320,7 @@ cudaError_t launch_ghost_batch(const GhostArgs<real> *args, const int *start, in
 }
 
 template <typename real>
-cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int *start, int n, int nblocks,
-                                 cudaStream_t st)
+cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, cudaStream_t st)
 {
     static bool configured = false;
     const size_t smem = sizeof(StencilSmem<real>);
@@ -1331,16 +1330,17 @@ cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int *start
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    if (nblocks > 0) k_stencil_batch<real><<<nblocks, kStencilThreads, smem, st>>>(args, start, n);
+    if (nblocks > 0) k_stencil_batch<real><<<nblocks, kStencilThreads, smem, st>>>(args, desc);
     return cudaGetLastError();
 }
 
 int line_seg_shift(int n, int real_bytes)
 {
-    // 16 rows per segment (32 for lines above 8192 FP32 / 4096 FP64 rows, so
-    // that a line has at most 512 segments and fits shared memory), fewer for
-    // short lines so that there are at least 2 segments of >= 2 rows
-    int sh = n > (real_bytes == 8 ? 4096 : 8192) ? 5 : 4;
+    // 8 rows per segment up to 1024 rows, 16 above (32 above 8192 FP32 /
+    // 4096 FP64 rows, so that a line has at most 512 segments and fits
+    // shared memory); fewer for short lines so that there are at least 2
+    // segments of >= 2 rows
+    int sh = n > (real_bytes == 8 ? 4096 : 8192) ? 5 : (n > 1024 ? 4 : 3);
     while (sh > 1 && (n >> sh) < 2) sh--;
     return sh;
 }
@@ -1365,7 +1365,7 @@ template <typename real>
 cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
 {
     size_t smem = 0;
-    int threads = 64;
+    int threads = 32;
     const bool both = p.L[0].nlines > 0 && p.L[1].nlines > 0;
     if (both && p.L[0].mshift != p.L[1].mshift) {   // one segment length per launch
         LinePair<real> a = p, b = p;
@@ -1399,11 +1399,11 @@ cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
 }
 
 template <typename real>
-cudaError_t launch_lines_batch(const LineArgs<real> *args, const int *start, int nfam, int nblocks, int mshift,
-                               int threads, size_t smem, cudaStream_t st)
+cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int nblocks, int mshift, int threads,
+                               size_t smem, cudaStream_t st)
 {
     static int configured[6] = {0, 0, 0, 0, 0, 0};
-    if (mshift < 1 || mshift > 5 || threads < 32 || threads > (sizeof(real) == 4 ? 1024 : 512))
+    if (mshift < 1 || mshift > 5 || threads < 32 || threads % 32 || threads > (sizeof(real) == 4 ? 1024 : 512))
         return cudaErrorInvalidValue;
     auto *kern = mshift == 1 ? k_lines_batch<real, 2> : mshift == 2 ? k_lines_batch<real, 4>
                : mshift == 3 ? k_lines_batch<real, 8> : mshift == 4 ? k_lines_batch<real, 16>
@@ -1413,7 +1413,7 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int *start, int
         if (e != cudaSuccess) return e;
         configured[mshift] = (int)smem;
     }
-    if (nblocks > 0) kern<<<nblocks, threads, smem, st>>>(args, start, nfam);
+    if (nblocks > 0) kern<<<nblocks, threads, smem, st>>>(args, desc);
     return cudaGetLastError();
 }
 
@@ -1448,10 +1448,9 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int *start, int
     template size_t line_smem_bytes<real>(int, int);                                                    \
     template cudaError_t launch_ghost_batch<real>(const GhostArgs<real> *, const int *, int, int, int64_t, \
                                                   cudaStream_t);                                        \
-    template cudaError_t launch_stencil_batch<real>(const StencilArgs<real> *, const int *, int, int,     \
-                                                    cudaStream_t);                                      \
-    template cudaError_t launch_lines_batch<real>(const LineArgs<real> *, const int *, int, int, int, int, \
-                                                  size_t, cudaStream_t);
+    template cudaError_t launch_stencil_batch<real>(const StencilArgs<real> *, const int2 *, int, cudaStream_t); \
+    template cudaError_t launch_lines_batch<real>(const LineArgs<real> *, const int2 *, int, int, int, size_t, \
+                                                  cudaStream_t);
 
 CEL_INSTANTIATE(float)
 CEL_INSTANTIATE(double)

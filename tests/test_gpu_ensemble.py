@@ -44,12 +44,15 @@ def _members(K):
     return out
 
 
-def _seg_shift(n, es):
-    # segment length of the line solver (rows per segment = 2**shift)
-    sh = 5 if n > (4096 if es == 8 else 8192) else 4
+def _line_launch_class(n, es):
+    # segment length and block size of the line solver: 2**shift rows per
+    # segment (8 up to 1024 rows, 16 above, 32 above 8192 FP32 / 4096 FP64,
+    # fewer for short lines), one thread per segment rounded up to a warp
+    sh = 5 if n > (4096 if es == 8 else 8192) else (4 if n > 1024 else 3)
     while sh > 1 and (n >> sh) < 2:
         sh -= 1
-    return sh
+    nseg = -(-n // (1 << sh))
+    return sh, -(-nseg // 32) * 32
 
 
 def _pairs(scens, prec):
@@ -136,7 +139,7 @@ def test_ensemble_launch_count():
     ens.step(3)
     first = ens.last_launch_count()
     ens.step(1)
-    groups = len({_seg_shift(n, 4) for s in scens for n in (s.nx, s.ny)})
+    groups = len({_line_launch_class(n, 4) for s in scens for n in (s.nx, s.ny)})
     assert groups >= 2
     assert ens.last_launch_count() == 1 + 2 * (1 + groups)     # ghost tables + 2 stages
     assert first > 3 * (1 + groups)                            # Eckart tables, Euler steps
