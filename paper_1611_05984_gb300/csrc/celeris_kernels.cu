@@ -790,16 +790,6 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
     const bool bsnq = A.phy.model == kBsnq;
     const int lane = tid & 31;
     constexpr int kRows = kTile / (kStencilThreads / 32);   // rows per thread
-    Carry<real> nw, nu, nv;                                  // next row's carries
-    {
-        const int i = O.x0() + lane, j = O.y0() + (tid >> 5);
-        if (i < nx && j < ny) {
-            const size_t kr = (size_t)j * G.px + i;
-            nw = load_carry(A, 0, kr);
-            nu = load_carry(A, 1, kr);
-            nv = load_carry(A, 2, kr);
-        }
-    }
 #pragma unroll 1
     for (int rr = 0; rr < kRows; rr++) {
         const int cx = lane, cy = (tid >> 5) + rr * (kStencilThreads / 32);
@@ -807,15 +797,14 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
         const bool valid = i < nx && j < ny;
         const int o = (cy + kHalo) * kStride + cx + kHalo;
         const size_t kr = (size_t)j * G.px + i;
-        const Carry<real> cw = nw, cu = nu, cv = nv;
-        if (rr + 1 < kRows) {   // issue the next row's loads before this row's arithmetic
-            const int jn = j + kStencilThreads / 32;
-            if (i < nx && jn < ny) {
-                const size_t kn = (size_t)jn * G.px + i;
-                nw = load_carry(A, 0, kn);
-                nu = load_carry(A, 1, kn);
-                nv = load_carry(A, 2, kn);
-            }
+        // the history this stage reads, issued before the cell's arithmetic
+        // (holding the next row's history in registers as well costs more
+        // occupancy than it saves latency)
+        Carry<real> cw, cu, cv;
+        if (valid) {
+            cw = load_carry(A, 0, kr);
+            cu = load_carry(A, 1, kr);
+            cv = load_carry(A, 2, kr);
         }
         const real *cb = sm.Bc + (cy + 1) * kCornerStride + cx + 1;
         real c00 = cb[0], c10 = cb[1], c01 = cb[kCornerStride], c11 = cb[kCornerStride + 1];
@@ -916,7 +905,7 @@ __device__ __forceinline__ void load_args(T &dst, const T *src)
 // b's member (x) and tile (y: row << 16 | column); the member's arguments
 // are copied to shared memory.
 template <typename real>
-__global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
     k_stencil_batch(const StencilArgs<real> *__restrict__ args, const int2 *__restrict__ desc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
