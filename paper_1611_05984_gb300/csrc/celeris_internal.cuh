@@ -23,7 +23,7 @@ constexpr int kHalo = 2;           // ghost layers (Sec. 2.4)
 constexpr int kTileIn = kTile + 2 * kHalo;   // 36
 constexpr int kStride = kTileIn + 1;         // padded smem row of the state tile
 constexpr int kCorner = kTile + 3;           // 35 corners per tile edge
-constexpr int kCornerStride = kCorner + 1;
+constexpr int kCornerStride = kCorner + 2;    // odd: a warp reading one corner per row hits 32 banks
 constexpr int kDcell = kTile + 2;            // 34 cells of d per tile edge
 constexpr int kDStride = kDcell + 1;
 constexpr int kStencilThreads = 256;

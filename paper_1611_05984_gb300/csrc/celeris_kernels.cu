@@ -713,71 +713,73 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
     __syncthreads();
 
     // ---- 4. fluxes through every face of the tile, each computed once.
-    //         Each thread sweeps 4 consecutive faces of one row (x-faces) or
-    //         one column (y-faces), so every cell is reconstructed once per
-    //         direction: the right cell of a face is the left cell of the next.
+    //         Warps 0-3 sweep x-faces, warps 4-7 y-faces; a lane owns one
+    //         row (x) or column (y) and 8 consecutive faces of it (the last
+    //         warp of each half also face 32), so every cell is reconstructed
+    //         once per direction: the right cell of a face is the left cell
+    //         of the next.
     {
-        const int r = tid >> 3, sg = tid & 7;   // x: row r, faces [4 sg, 4 sg + 4) (+ face 32)
-        const int f0 = sg * 4, f1 = sg == 7 ? kTile + 1 : f0 + 4;
-        const int rowo = (r + kHalo) * kStride;
-        const real *cb = sm.Bc + (r + 1) * kCornerStride;
+        const int lane = tid & 31, wq = (tid >> 5) & 3;
+        const int f0 = wq * 8, f1 = wq == 3 ? kTile + 1 : f0 + 8;
         real lo[3], hiL[3], hiR[3];
-        {
-            const int o = rowo + f0 + 1;
-            const real wq[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
-            const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
-            const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
-            recon(th, wq, Pq, Qq, real(0.5) * (cb[f0] + cb[f0 + kCornerStride]),
-                  real(0.5) * (cb[f0 + 1] + cb[f0 + 1 + kCornerStride]), lo, hiL);
-        }
-        for (int f = f0; f < f1; f++) {
-            const int o = rowo + f + 2;           // right cell of face f
-            const real wq[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
-            const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
-            const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
-            const real Bf = real(0.5) * (cb[f + 1] + cb[f + 1 + kCornerStride]);
-            recon(th, wq, Pq, Qq, Bf, real(0.5) * (cb[f + 2] + cb[f + 2 + kCornerStride]), lo, hiR);
-            real H[3];
-            cu_flux(g, eps, hiL[0], hiL[1], hiL[2], lo[0], lo[1], lo[2], Bf, H);
-            sm.Fx[0][r][f] = H[0];
-            sm.Fx[1][r][f] = H[1];
-            sm.Fx[2][r][f] = H[2];
-            hiL[0] = hiR[0];
-            hiL[1] = hiR[1];
-            hiL[2] = hiR[2];
-        }
-    }
-    {
-        const int c = tid & 31, sg = tid >> 5;  // y: column c, faces [4 sg, 4 sg + 4) (+ face 32)
-        const int g0 = sg * 4, g1 = sg == 7 ? kTile + 1 : g0 + 4;
-        const int tx = c + kHalo;
-        const real *cb = sm.Bc + c + 1;
-        real lo[3], hiS[3], hiN[3];
-        {
-            const int o = (g0 + 1) * kStride + tx;
-            const real wq[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
-            const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
-            const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
-            recon(th, wq, Pq, Qq, real(0.5) * (cb[g0 * kCornerStride] + cb[g0 * kCornerStride + 1]),
-                  real(0.5) * (cb[(g0 + 1) * kCornerStride] + cb[(g0 + 1) * kCornerStride + 1]), lo, hiS);
-        }
-        for (int gq = g0; gq < g1; gq++) {
-            const int o = (gq + 2) * kStride + tx;  // north cell of face gq
-            const real wq[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
-            const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
-            const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
-            const real Bf = real(0.5) * (cb[(gq + 1) * kCornerStride] + cb[(gq + 1) * kCornerStride + 1]);
-            recon(th, wq, Pq, Qq, Bf,
-                  real(0.5) * (cb[(gq + 2) * kCornerStride] + cb[(gq + 2) * kCornerStride + 1]), lo, hiN);
-            real H[3];
-            // normal discharge is Q, tangential is P
-            cu_flux(g, eps, hiS[0], hiS[2], hiS[1], lo[0], lo[2], lo[1], Bf, H);
-            sm.Fy[0][gq][c] = H[0];
-            sm.Fy[1][gq][c] = H[2];
-            sm.Fy[2][gq][c] = H[1];
-            hiS[0] = hiN[0];
-            hiS[1] = hiN[1];
-            hiS[2] = hiN[2];
+        if (tid < 4 * 32) {
+            const int r = lane;
+            const int rowo = (r + kHalo) * kStride;
+            const real *cb = sm.Bc + (r + 1) * kCornerStride;
+            {
+                const int o = rowo + f0 + 1;
+                const real wq3[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
+                const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
+                const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
+                recon(th, wq3, Pq, Qq, real(0.5) * (cb[f0] + cb[f0 + kCornerStride]),
+                      real(0.5) * (cb[f0 + 1] + cb[f0 + 1 + kCornerStride]), lo, hiL);
+            }
+            for (int f = f0; f < f1; f++) {
+                const int o = rowo + f + 2;           // right cell of face f
+                const real wq3[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
+                const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
+                const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
+                const real Bf = real(0.5) * (cb[f + 1] + cb[f + 1 + kCornerStride]);
+                recon(th, wq3, Pq, Qq, Bf, real(0.5) * (cb[f + 2] + cb[f + 2 + kCornerStride]), lo, hiR);
+                real H[3];
+                cu_flux(g, eps, hiL[0], hiL[1], hiL[2], lo[0], lo[1], lo[2], Bf, H);
+                sm.Fx[0][r][f] = H[0];
+                sm.Fx[1][r][f] = H[1];
+                sm.Fx[2][r][f] = H[2];
+                hiL[0] = hiR[0];
+                hiL[1] = hiR[1];
+                hiL[2] = hiR[2];
+            }
+        } else {
+            const int c = lane;
+            const int tx = c + kHalo;
+            const real *cb = sm.Bc + c + 1;
+            {
+                const int o = (f0 + 1) * kStride + tx;
+                const real wq3[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
+                const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
+                const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
+                recon(th, wq3, Pq, Qq, real(0.5) * (cb[f0 * kCornerStride] + cb[f0 * kCornerStride + 1]),
+                      real(0.5) * (cb[(f0 + 1) * kCornerStride] + cb[(f0 + 1) * kCornerStride + 1]), lo, hiL);
+            }
+            for (int gq = f0; gq < f1; gq++) {
+                const int o = (gq + 2) * kStride + tx;  // north cell of face gq
+                const real wq3[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
+                const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
+                const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
+                const real Bf = real(0.5) * (cb[(gq + 1) * kCornerStride] + cb[(gq + 1) * kCornerStride + 1]);
+                recon(th, wq3, Pq, Qq, Bf,
+                      real(0.5) * (cb[(gq + 2) * kCornerStride] + cb[(gq + 2) * kCornerStride + 1]), lo, hiR);
+                real H[3];
+                // normal discharge is Q, tangential is P
+                cu_flux(g, eps, hiL[0], hiL[2], hiL[1], lo[0], lo[2], lo[1], Bf, H);
+                sm.Fy[0][gq][c] = H[0];
+                sm.Fy[1][gq][c] = H[2];
+                sm.Fy[2][gq][c] = H[1];
+                hiL[0] = hiR[0];
+                hiL[1] = hiR[1];
+                hiL[2] = hiR[2];
+            }
         }
     }
     __syncthreads();
