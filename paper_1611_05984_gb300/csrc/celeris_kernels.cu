@@ -938,6 +938,23 @@ __device__ __forceinline__ void coef23(real B3, real hrh, real srh, real rh2, re
     c = -s - r;
 }
 
+// Asynchronous copy of one element from global to shared memory (zero-filled
+// when !valid, reading nothing); all of a thread's copies are in flight at
+// once and cost no registers.  cp_async_wait_all waits for this thread's.
+template <typename real>
+__device__ __forceinline__ void cp_async_elem(real *smem, const real *gmem, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(real) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0)
+                     : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Shared-memory slot of line element k: element j of segment t sits at
 // j * sp + t (sp odd), so the threads of a warp sweeping their segments touch
 // consecutive words at every step (no bank conflicts).
@@ -984,12 +1001,19 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
         }
         const uint32_t *mw = A.mask + (size_t)line * A.nwords;
         for (int k = tid; k < A.nwords; k += T) smask[k] = mw[k];
-#pragma unroll 4
-        for (int k = tid; k < npad; k += T) {
-            const int q = seg_slot(k, mshift, sp);
-            sR[q] = k < n ? rhs[k] : real(0);
-            sA[q] = k < n ? dl[k] : real(0);     // d = 0: a = c = 0, b = 1
+        // right side and depth straight into their segment-major slots
+        // (d = 0 on the padding rows: a = c = 0, b = 1)
+#pragma unroll
+        for (int u = 0; u < M; u++) {
+            const int k = tid + u * T;
+            if (k < npad) {
+                const int q = seg_slot(k, mshift, sp);
+                const bool in = k < n;
+                cp_async_elem(sR + q, rhs + (in ? k : 0), in);
+                cp_async_elem(sA + q, dl + (in ? k : 0), in);
+            }
         }
+        cp_async_wait_all();
         __syncthreads();
         if (!A.identity) {
         const bool act = tid < S;
