@@ -1048,7 +1048,7 @@ void plan_t(cel_solver *const *ms, int n, EnsPlan &P)
             for (int e = 0; e < n; e++)
                 for (int dir = 0; dir < 2; dir++) {
                     const std::pair<int, int> f(e, dir);
-                    if (line_seg_shift(len_of(f), ms[e]->es) == sh && round_up_i(seg_of(f), 32) == th)
+                    if (line_seg_shift(len_of(f), ms[e]->es) == sh && line_threads(len_of(f), ms[e]->es) == th)
                         g.push_back(f);
                 }
             if (g.empty()) continue;

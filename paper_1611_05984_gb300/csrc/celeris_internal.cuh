@@ -235,5 +235,6 @@ size_t line_smem_bytes(int n, int nseg);
 int line_segments(int n, int real_bytes);
 int line_seg_shift(int n, int real_bytes);
 int line_seg_stride(int nseg);
+int line_threads(int n, int real_bytes);
 
 }  // namespace cel

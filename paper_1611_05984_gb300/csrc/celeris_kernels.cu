@@ -989,7 +989,7 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
         const real *dl = A.d + (size_t)line * A.pitch;
         // P^n (or Q^n) of the elements this thread writes in the epilogue,
         // loaded now so the loads complete during the elimination
-        constexpr int kMaxOwn = M;   // elements per thread: ceil(n / T) <= M since T >= nseg
+        constexpr int kMaxOwn = M < 16 ? M : 16;   // ceil(n / T) <= kMaxOwn (line_threads)
         real own[kMaxOwn];
         {
             const real *bs = A.base + (size_t)line * A.pitch;
@@ -1351,11 +1351,12 @@ cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc
 
 int line_seg_shift(int n, int real_bytes)
 {
-    // 8 rows per segment up to 1024 rows, 16 above (32 above 8192 FP32 /
-    // 4096 FP64 rows, so that a line has at most 512 segments and fits
-    // shared memory); fewer for short lines so that there are at least 2
-    // segments of >= 2 rows
-    int sh = n > (real_bytes == 8 ? 4096 : 8192) ? 5 : (n > 1024 ? 4 : 3);
+    // 8 rows per segment up to 1024 rows, 16 up to 4096, 32 above (at most
+    // 512 segments, and two 8192-row FP32 lines fit one SM's shared memory);
+    // fewer for short lines so that there are at least 2 segments of >= 2
+    // rows
+    (void)real_bytes;
+    int sh = n > 4096 ? 5 : (n > 1024 ? 4 : 3);
     while (sh > 1 && (n >> sh) < 2) sh--;
     return sh;
 }
@@ -1367,6 +1368,19 @@ int line_segments(int n, int real_bytes)
 }
 
 int line_seg_stride(int nseg) { return nseg | 1; }
+
+// Block size of a line solve: a thread per segment, and at most 16 elements
+// of P^n per thread held through the solve (32-row segments get two
+// threads per segment).
+int line_threads(int n, int real_bytes)
+{
+    const int m = 1 << line_seg_shift(n, real_bytes);
+    const int own = m < 16 ? m : 16;
+    int t = line_segments(n, real_bytes);
+    if ((n + own - 1) / own > t) t = (n + own - 1) / own;
+    t = round_up(t, 32);
+    return t < 32 ? 32 : t;
+}
 
 template <typename real>
 size_t line_smem_bytes(int n, int nseg)
@@ -1395,7 +1409,7 @@ cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
         if (a.nseg * (1 << a.mshift) < a.n || a.sp != line_seg_stride(a.nseg)) return cudaErrorInvalidValue;
         size_t b = line_smem_bytes<real>(a.n, a.nseg);
         if (b > smem) smem = b;
-        int t = round_up(a.nseg, 32);
+        int t = line_threads(a.n, (int)sizeof(real));
         if (t > threads) threads = t;
     }
     static int configured[6] = {0, 0, 0, 0, 0, 0};

@@ -46,13 +46,16 @@ def _members(K):
 
 def _line_launch_class(n, es):
     # segment length and block size of the line solver: 2**shift rows per
-    # segment (8 up to 1024 rows, 16 above, 32 above 8192 FP32 / 4096 FP64,
-    # fewer for short lines), one thread per segment rounded up to a warp
-    sh = 5 if n > (4096 if es == 8 else 8192) else (4 if n > 1024 else 3)
+    # segment (8 up to 1024 rows, 16 up to 4096, 32 above, fewer for short
+    # lines), a thread per segment and at most 16 elements per thread,
+    # rounded up to a warp
+    sh = 5 if n > 4096 else (4 if n > 1024 else 3)
     while sh > 1 and (n >> sh) < 2:
         sh -= 1
-    nseg = -(-n // (1 << sh))
-    return sh, -(-nseg // 32) * 32
+    m = 1 << sh
+    nseg = -(-n // m)
+    t = max(nseg, -(-n // min(m, 16)))
+    return sh, max(32, -(-t // 32) * 32)
 
 
 def _pairs(scens, prec):
