@@ -989,7 +989,7 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
         const real *dl = A.d + (size_t)line * A.pitch;
         // P^n (or Q^n) of the elements this thread writes in the epilogue,
         // loaded now so the loads complete during the elimination
-        constexpr int kMaxOwn = M < 16 ? M : 16;   // ceil(n / T) <= kMaxOwn (line_threads)
+        constexpr int kMaxOwn = M == 32 ? 16 : (M < 8 ? M : 8);   // ceil(n / T) <= kMaxOwn (line_threads)
         real own[kMaxOwn];
         {
             const real *bs = A.base + (size_t)line * A.pitch;
@@ -1369,13 +1369,14 @@ int line_segments(int n, int real_bytes)
 
 int line_seg_stride(int nseg) { return nseg | 1; }
 
-// Block size of a line solve: a thread per segment, and at most 16 elements
-// of P^n per thread held through the solve (32-row segments get two
-// threads per segment).
+// Block size of a line solve: a thread per segment, and at most 8 elements
+// of P^n per thread held through the solve (16 with 32-row segments, so that
+// the longest lines stay within 1024 threads): segments of 16 or 32 rows get
+// two threads each, which hides more of the loads' latency.
 int line_threads(int n, int real_bytes)
 {
     const int m = 1 << line_seg_shift(n, real_bytes);
-    const int own = m < 16 ? m : 16;
+    const int own = m == 32 ? 16 : (m < 8 ? m : 8);
     int t = line_segments(n, real_bytes);
     if ((n + own - 1) / own > t) t = (n + own - 1) / own;
     t = round_up(t, 32);

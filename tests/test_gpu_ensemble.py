@@ -47,14 +47,14 @@ def _members(K):
 def _line_launch_class(n, es):
     # segment length and block size of the line solver: 2**shift rows per
     # segment (8 up to 1024 rows, 16 up to 4096, 32 above, fewer for short
-    # lines), a thread per segment and at most 16 elements per thread,
-    # rounded up to a warp
+    # lines), a thread per segment and at most 8 elements per thread (16 with
+    # 32-row segments), rounded up to a warp
     sh = 5 if n > 4096 else (4 if n > 1024 else 3)
     while sh > 1 and (n >> sh) < 2:
         sh -= 1
     m = 1 << sh
     nseg = -(-n // m)
-    t = max(nseg, -(-n // min(m, 16)))
+    t = max(nseg, -(-n // (16 if m == 32 else min(m, 8))))
     return sh, max(32, -(-t // 32) * 32)
 
 
