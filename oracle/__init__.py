@@ -96,6 +96,8 @@ def lib():
             L.orc_clamp_mass.argtypes = [p]
             L.orc_set_gauges.argtypes = [p, ctypes.POINTER(ctypes.c_int), i, i, i]
             L.orc_read_gauges.argtypes = [p, dp, i, ctypes.POINTER(ctypes.c_int)]
+            L.orc_runup_enable.argtypes = [p, d]
+            L.orc_runup_read.argtypes = [p, dp]
             L.orc_num_threads.restype = i
             L.orc_minmod.restype = d
             L.orc_minmod.argtypes = [d, d, d, d]
@@ -205,6 +207,21 @@ class Oracle:
         n = ctypes.c_int()
         self._L.orc_read_gauges(self._h, _dp(out), max_rec, ctypes.byref(n))
         return out[: n.value]
+
+
+    def runup_enable(self, delta):
+        """Track the highest w seen where the depth exceeds delta (Sec. 4.1,
+        4.3), starting from the present state."""
+        if self._L.orc_runup_enable(self._h, float(delta)) != 0:
+            raise ValueError("bad run-up threshold")
+
+    def runup(self):
+        """(ny, nx) highest w seen while wetter than the threshold; -inf where
+        never."""
+        out = np.empty((self.ny, self.nx))
+        if self._L.orc_runup_read(self._h, _dp(out)) != 0:
+            raise ValueError("run-up tracking is not enabled")
+        return out
 
 
 def minmod(theta, qm, q0, qp):

@@ -45,6 +45,7 @@ struct orc {
     int ng, log_every, cap, nrec, head;
     int *gij;
     double *grec;
+    double *maxw, delta;                        /* run-up tracking         */
 };
 
 static size_t IX(const orc *o, int i, int j)
@@ -561,6 +562,21 @@ static void record_gauges(orc *o)
     }
 }
 
+/* Run-up tracking (Sec. 4.1, 4.3): the highest w seen at each cell while its
+ * depth w - Bbar exceeded the threshold delta; -inf where it never did.
+ * start = 1 sets the field from the present state. */
+static void track_runup(orc *o, int start)
+{
+    if (!o->maxw) return;
+    for (int j = 0; j < o->ny; j++)
+        for (int i = 0; i < o->nx; i++) {
+            size_t c = IX(o, i, j), k = (size_t)j * o->nx + i;
+            int wet = o->w[c] - o->Bbar[c] > o->delta;
+            if (start) o->maxw[k] = wet ? o->w[c] : -INFINITY;
+            else if (wet && o->w[c] > o->maxw[k]) o->maxw[k] = o->w[c];
+        }
+}
+
 /* -------------------------------------------------------------- the step */
 
 static void swap3(double **h)
@@ -658,6 +674,7 @@ int orc_step(orc *o, int nsteps)
         o->step++;
         o->nh++;
         record_gauges(o);
+        track_runup(o, 0);
     }
     return 0;
 }
@@ -714,6 +731,7 @@ void orc_destroy(orc *o)
     }
     free(o->gij);
     free(o->grec);
+    free(o->maxw);
     free(o);
 }
 
@@ -841,5 +859,21 @@ int orc_read_gauges(orc *o, double *eta, int max_rec, int *n_rec)
     o->head = o->cap ? (o->head + n) % o->cap : 0;
     o->nrec -= n;
     *n_rec = n;
+    return 0;
+}
+
+int orc_runup_enable(orc *o, double delta)
+{
+    if (!o || !(delta >= 0.0)) return -1;
+    if (!o->maxw) o->maxw = (double *)malloc(sizeof(double) * (size_t)o->nx * o->ny);
+    o->delta = delta;
+    track_runup(o, 1);
+    return 0;
+}
+
+int orc_runup_read(const orc *o, double *maxw)
+{
+    if (!o || !o->maxw || !maxw) return -1;
+    memcpy(maxw, o->maxw, sizeof(double) * (size_t)o->nx * o->ny);
     return 0;
 }

@@ -66,6 +66,11 @@ double orc_clamp_mass(const orc *o);  /* mass added by the w >= Bbar clamp */
 int orc_set_gauges(orc *o, const int *ij, int n, int log_every, int capacity);
 int orc_read_gauges(orc *o, double *eta, int max_rec, int *n_rec);
 int orc_num_threads(void);
+/* Run-up tracking (Sec. 4.1, 4.3): after every step, maxw[j][i] = the highest
+ * w seen while the cell's depth w - Bbar exceeded delta (-inf if never);
+ * enable starts it from the present state, read copies it out ([ny][nx]). */
+int orc_runup_enable(orc *o, double delta);
+int orc_runup_read(const orc *o, double *maxw);
 
 /* Building blocks exported so tests can pin them one by one. */
 double orc_minmod(double theta, double qm, double q0, double qp);

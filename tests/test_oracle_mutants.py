@@ -42,6 +42,10 @@ MUTANTS = [
      "test_eckart_vs_exact_dispersion"),
     ("transpose_y_solve", "coef23(o->p.Bd, o->p.dy, o->d[c], o->ddy[c], &a, &b, &cc);",
      "coef23(o->p.Bd, o->p.dy, o->d[c], o->ddx[c], &a, &b, &cc);", "test_lake_at_rest_submerged"),
+    ("runup_keeps_last", "else if (wet && o->w[c] > o->maxw[k]) o->maxw[k] = o->w[c];",
+     "else if (wet) o->maxw[k] = o->w[c];", "test_runup_tracking_standing_mode"),
+    ("runup_no_threshold", "int wet = o->w[c] - o->Bbar[c] > o->delta;", "int wet = 1;",
+     "test_runup_tracking_threshold_and_dry_land"),
 ]
 
 

@@ -402,3 +402,48 @@ def test_gauge_ring(oracle_mod):
             etas.append([w[5, 10], w[16, 200]])
     np.testing.assert_array_equal(rec, np.array(etas[-4:]))
     assert o.read_gauges(10).shape == (0, 2)
+
+
+def test_runup_tracking_standing_mode(oracle_mod):
+    """Run-up tracking (Sec. 4.1, 4.3) keeps the highest w seen: over half a
+    period of the 1-D standing mode eta = a cos(kx) cos(wt) it must be
+    |a cos(kx)| everywhere (the initial and the final state each give only
+    half of the cells), within the scheme's amplitude error."""
+    d, kd, cpl = 1.0, 1.0, 64
+    k = kd / d
+    dx = 2 * math.pi / k / cpl
+    x = (np.arange(cpl) + 0.5) * dx
+    a = 1e-4 * d
+    eta = np.tile(a * np.cos(k * x), (2, 1))
+    z = np.full((2, cpl), -d)
+    dt = 0.2 * dx / math.sqrt(G * d)
+    o = oracle_mod.Oracle(z, dx, dx, dt)
+    o.set_state(eta, 0 * z, 0 * z)
+    o.runup_enable(0.5 * d)
+    first = o.runup()[0].copy()
+    np.testing.assert_array_equal(first, eta[0])           # starts from the state
+    T = 2 * math.pi / _omega(k, d)
+    o.step(int(round(0.5 * T / dt)))
+    m = o.runup()[0]
+    last = o.state()[0][0]
+    assert np.max(np.abs(m - np.abs(a * np.cos(k * x)))) <= 0.03 * a
+    assert np.all(m >= np.maximum(first, last))            # never below what it saw
+    assert np.max(np.abs(m - last)) > 0.5 * a              # not the last state
+
+
+def test_runup_tracking_threshold_and_dry_land(oracle_mod):
+    """Cells never deeper than the threshold keep -inf: dry land behind a
+    lake, and the whole lake once the threshold exceeds its depth."""
+    z = np.full((4, 12), -0.05)
+    z[:, 8:] = 0.4
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.01)
+    o.runup_enable(0.01)
+    o.step(5)
+    m = o.runup()
+    # column 7's cell bed (the mean of its corners, which average in the
+    # land) is above w_s, so it is dry too
+    assert np.all(np.isneginf(m[:, 7:]))
+    np.testing.assert_allclose(m[:, :7], 0.0, atol=1e-14)   # lake at rest: w = w_s
+    o.runup_enable(0.06)
+    o.step(2)
+    assert np.all(np.isneginf(o.runup()))
