@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="beach2048",
-                    choices=["beach2048", "beach8192", "beach512", "ensemble256"])
+                    choices=["beach2048", "beach8192", "beach512", "whalin2000", "conical601", "ensemble256"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,6 +62,10 @@ def workload(name):
         return sc.beach_directional(nx=8192, ny=8192)
     if name == "beach512":
         return sc.beach(nx=512, ny=512, sponge=20)
+    if name == "whalin2000":
+        return sc.whalin()
+    if name == "conical601":
+        return sc.conical_island(0.18)
     raise ValueError(f"{name} is not a single-grid workload")
 
 

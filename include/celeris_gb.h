@@ -165,6 +165,15 @@ cel_status cel_checkpoint_bytes(const cel_solver *s, size_t *bytes);
 cel_status cel_save_checkpoint(cel_solver *s, void *dst_dev, size_t bytes);
 cel_status cel_load_checkpoint(cel_solver *s, const void *src_dev, size_t bytes);
 
+/* Run-up tracking (Sec. 4.1 and 4.3 read the run-up off the wet extent,
+ * with a depth threshold delta = s dx / 3).  maxw_dev: [ny][nx] real,
+ * device, owned by the caller; after every step maxw[j][i] becomes the
+ * highest w seen so far while the cell's depth w - Bbar exceeded delta, and
+ * stays -inf where it never did.  Enabling sets the field from the present
+ * state (asynchronous); maxw_dev = NULL disables.  The field must stay
+ * allocated while enabled.  CEL_ERR_INVALID_ARG for delta < 0. */
+cel_status cel_runup_enable(cel_solver *s, void *maxw_dev, double delta);
+
 /* Kernel launches issued by the most recent cel_step call. */
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);
 

@@ -31,7 +31,7 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_add_solitary", "cel_set_bathymetry", "cel_step", "cel_get_state", "cel_get_field",
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
-           "cel_load_checkpoint", "cel_last_launch_count", "cel_profile_enable",
+           "cel_load_checkpoint", "cel_runup_enable", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         L.cel_checkpoint_bytes.argtypes = [vp, ctypes.POINTER(sz)]
         L.cel_save_checkpoint.argtypes = [vp, vp, sz]
         L.cel_load_checkpoint.argtypes = [vp, vp, sz]
+        L.cel_runup_enable.argtypes = [vp, vp, d]
         L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_profile_enable.argtypes = [vp, i32]
         L.cel_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
@@ -306,6 +307,26 @@ class Solver:
         n = ctypes.c_int64()
         self._check(self.L.cel_last_launch_count(self._h, ctypes.byref(n)), "last_launch_count")
         return n.value
+
+    def runup_enable(self, delta: float):
+        """Track the highest w seen where the depth exceeds delta (Sec. 4.1,
+        4.3), from the present state on; the field lives in a tensor this
+        object keeps."""
+        with self.torch.cuda.device(self.device):
+            self._runup = self.torch.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
+        self._check(self.L.cel_runup_enable(self._h, self._runup.data_ptr(), float(delta)), "runup_enable")
+
+    def runup_disable(self):
+        self._check(self.L.cel_runup_enable(self._h, None, 0.0), "runup_disable")
+        self._runup = None
+
+    def runup(self):
+        """(ny, nx) highest w seen while wetter than the threshold, -inf where
+        never (a copy, after the stream's work so far)."""
+        if getattr(self, "_runup", None) is None:
+            raise CelerisError(1, "run-up tracking is not enabled")
+        self.stream.synchronize()
+        return self._runup.clone()
 
 
 class Ensemble:

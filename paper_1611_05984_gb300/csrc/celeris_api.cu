@@ -209,6 +209,8 @@ struct cel_solver {
     unsigned char *gring;
     int ng, log_every, cap, nrec, head;
     int64_t launches;
+    void *runup;      // caller's [ny][nx] run-up field, or NULL
+    double runup_delta;
     int ktab_dirty;   // boundaries or bed changed: rebuild the Eckart table
     uint64_t gen;     // counts boundary and bed changes (ensembles rebuild their tables)
     std::string err;
@@ -356,10 +358,16 @@ void finish_step(cel_solver *s, int Kn)
     s->nh++;
 }
 
-// Gauge record of the step just finished, if one is due; adds its launch.
+// Gauge record and run-up update of the step just finished, where enabled;
+// adds their launches.
 template <typename real>
 cel_status log_gauges(cel_solver *s, cudaStream_t st, int64_t &launches)
 {
+    if (s->runup) {
+        CEL_CUDA(s, launch_runup<real>(s->geo, s->at<real>(s->lay.Bc), s->at<real>(s->lay.w[s->cur]),
+                                       (real *)s->runup, s->runup_delta, 0, st), "run-up");
+        launches += 1;
+    }
     if (!(s->ng > 0 && s->log_every > 0 && s->cap > 0 && s->step % s->log_every == 0)) return CEL_OK;
     int slotg;
     if (s->nrec < s->cap) {
@@ -527,6 +535,8 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->gring = nullptr;
     s->ng = s->log_every = s->cap = s->nrec = s->head = 0;
     s->launches = 0;
+    s->runup = nullptr;
+    s->runup_delta = 0.0;
     s->ktab_dirty = 1;
     s->gen = 0;
     s->step = 0;
@@ -847,6 +857,25 @@ cel_status cel_profile_disable(cel_solver *s)
     return CEL_OK;
 }
 
+cel_status cel_runup_enable(cel_solver *s, void *maxw_dev, double delta)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    if (!maxw_dev) {
+        s->runup = nullptr;
+        return CEL_OK;
+    }
+    if (!(delta >= 0.0) || !isfinite(delta)) return fail(s, CEL_ERR_INVALID_ARG, "bad run-up threshold");
+    s->runup = maxw_dev;
+    s->runup_delta = delta;
+    cudaError_t e = s->es == 4 ? launch_runup<float>(s->geo, s->at<float>(s->lay.Bc), s->at<float>(s->lay.w[s->cur]),
+                                                     (float *)maxw_dev, delta, 1, s->stream)
+                               : launch_runup<double>(s->geo, s->at<double>(s->lay.Bc),
+                                                      s->at<double>(s->lay.w[s->cur]), (double *)maxw_dev, delta, 1,
+                                                      s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "run-up");
+    return CEL_OK;
+}
+
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches)
 {
     if (!s || !launches) return CEL_ERR_INVALID_ARG;
@@ -950,6 +979,8 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.gring = nullptr;
     s.ng = s.log_every = s.cap = s.nrec = s.head = 0;
     s.launches = 0;
+    s.runup = nullptr;
+    s.runup_delta = 0.0;
     s.ktab_dirty = 1;
     s.gen = 0;
     s.step = first_step;

@@ -178,6 +178,9 @@ cudaError_t launch_add_solitary(const Geo &g, const Phys &p, const real *Bc, rea
                                 real *Qc, double H, double ct, double st_, double x0,
                                 double y0, double ks, double cs, cudaStream_t st);
 template <typename real>
+cudaError_t launch_runup(const Geo &g, const real *Bc, const real *w, real *maxw, double delta, int start,
+                         cudaStream_t st);
+template <typename real>
 cudaError_t launch_gauges(const Geo &g, const Phys &p, const real *w, const int32_t *ij,
                           int n, real *slot, cudaStream_t st);
 template <typename real>

@@ -242,6 +242,21 @@ __global__ void k_get_field(Geo g, Phys p, int which, const real *Bc, const real
     out[(size_t)j * g.nx + i] = v;
 }
 
+// Run-up tracking (Sec. 4.1, 4.3): maxw ([ny][nx]) keeps the highest w seen
+// while the cell's depth w - Bbar exceeds delta, -inf where it never did;
+// start sets it from the present state.
+template <typename real>
+__global__ void k_runup(Geo g, const real *Bc, const real *w, real *maxw, real delta, int start)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const real wv = w[(size_t)j * g.px + i];
+    const bool wet = wv - bbar_at(Bc, g, i, j) > delta;
+    real *m = maxw + (size_t)j * g.nx + i;
+    if (start) *m = wet ? wv : real(-INFINITY);
+    else if (wet && wv > *m) *m = wv;
+}
+
 // Eq. 33-36 (Reading A-S1), evaluated in double, added where d > 0.
 template <typename real>
 __global__ void k_add_solitary(Geo g, Phys p, const real *Bc, real *w, real *P, real *Qc,
@@ -1269,6 +1284,15 @@ cudaError_t launch_get_field(const Geo &g, const Phys &p, int which, const real 
 }
 
 template <typename real>
+cudaError_t launch_runup(const Geo &g, const real *Bc, const real *w, real *maxw, double delta, int start,
+                         cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_runup<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, Bc, w, maxw, real(delta), start);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_add_solitary(const Geo &g, const Phys &p, const real *Bc, real *w, real *P, real *Qc,
                                 double H, double ct, double st_, double x0, double y0, double ks,
                                 double cs, cudaStream_t st)
@@ -1464,6 +1488,8 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
     template cudaError_t launch_add_solitary<real>(const Geo &, const Phys &, const real *, real *,      \
                                                    real *, real *, double, double, double, double,      \
                                                    double, double, double, cudaStream_t);               \
+    template cudaError_t launch_runup<real>(const Geo &, const real *, const real *, real *, double, int,   \
+                                            cudaStream_t);                                              \
     template cudaError_t launch_gauges<real>(const Geo &, const Phys &, const real *, const int32_t *,   \
                                              int, real *, cudaStream_t);                                \
     template cudaError_t launch_check_finite<real>(const Geo &, const real *, const real *, const real *, \

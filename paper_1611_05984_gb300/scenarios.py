@@ -208,3 +208,92 @@ def ensemble(n: int = 256, seed: int = 4, steps: int = 5000, K: int = 1, cr: flo
         sc.name = f"ensemble{k}_{nx}x{ny}"
         out.append(sc)
     return out
+
+
+# ----------------------------------------------------------------------
+# The paper's validation geometries (Sec. 4), as synthetic workloads: the
+# laboratory records are not available, so only the set-ups are rebuilt.
+
+def whalin(nx: int = 2000, ny: int = 65, a: float = 0.0075, period: float = 2.0,
+           dt: float = 0.001, K: int = 1, steps: int = 20000, sponge_m: float = 5.0) -> Scenario:
+    """Whalin's semicircular shoal (Sec. 4.2, Eq. 37): a 35 m x 6.096 m
+    tank, still water 0.4572 m deep over the flat part, the bed rising by
+    1/25 between x = 10.67 - G(y) and 18.29 - G(y) to 0.3048 m
+    (G(y) = sqrt(y (6.096 - y))), so the shallow end is 0.1524 m deep.  Sine
+    maker on the west (a = 0.0075 m, T = 2 s), a 5 m sponge on the east, walls
+    north and south, dt = 0.001 s on 2000 x 65 cells.  Eq. 37 prints the
+    ramp as (10.67 - G - x)/25, which is negative on its own interval; the
+    ramp that reaches 0.3048 m at x = 18.29 - G is (x - 10.67 + G)/25.  K = 1
+    (an odd corrector count keeps the explicit mixed terms stable at
+    depth/dx = 26)."""
+    Lx, Ly, h0 = 35.0, 6.096, 0.4572
+    dx, dy = Lx / nx, Ly / ny
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dy)
+    Gy = np.sqrt(Y * (Ly - Y))
+    rise = np.clip((X - 10.67 + Gy) / 25.0, 0.0, 0.3048)
+    z = -h0 + rise
+    sides = {W: Side(SINE, 0, ((a, period, 0.0, 0.0),)), E: Side(SPONGE, int(round(sponge_m / dx))),
+             S: Side(SOLID), N: Side(SOLID)}
+    return Scenario(name=f"whalin_{nx}x{ny}", nx=nx, ny=ny, dx=dx, dy=dy, dt=dt, z=z, steps=steps, K=K,
+                    sides=sides)
+
+
+def planar_beach_soliton(H_over_d: float = 0.28, d: float = 1.0, slope: float = 1.0 / 19.85,
+                         f: float = 0.0, K: int = 1, eps: float = 1e-8) -> Scenario:
+    """Solitary-wave run-up on a planar beach (Sec. 4.1): slope 1:19.85,
+    still-water depth d, dx / d = 0.25 and dt sqrt(g/d) = 0.03 (dx / d =
+    0.0625 and dt sqrt(g/d) = 0.0075 for H/d < 0.01), a tank one depth wide,
+    sponge on the west, walls elsewhere, quadratic friction f.  The beach sits
+    near the east end; the tank holds a 20 d sponge, the soliton (centred one
+    half-length, arccosh(sqrt(20)) / gamma with gamma = sqrt(3H/(4d^3)), off the
+    toe) and land up to 1.5 d above the still water."""
+    fine = H_over_d < 0.01
+    dx = (0.0625 if fine else 0.25) * d
+    dt = (0.0075 if fine else 0.03) * math.sqrt(d / G)
+    H = H_over_d * d
+    half = math.acosh(math.sqrt(20.0)) / math.sqrt(3.0 * H / (4.0 * d ** 3))
+    sponge = 20.0 * d
+    x_toe = sponge + 2.0 * half + 2.0 * d
+    x_top = x_toe + 2.5 * d / slope           # land rises to 1.5 d above the still water
+    nx = int(math.ceil(x_top / dx))
+    ny = max(4, int(round(d / dx)))
+    x = (np.arange(nx) + 0.5) * dx
+    z = np.tile(np.maximum(-d, -d + (x - x_toe) * slope), (ny, 1))
+    sides = {W: Side(SPONGE, int(round(sponge / dx))), E: Side(SOLID), S: Side(SOLID), N: Side(SOLID)}
+    sc = Scenario(name=f"planar_beach_H{H_over_d:g}", nx=nx, ny=ny, dx=dx, dy=dx, dt=dt, z=z,
+                  steps=int(round(((x_toe + d / slope - (x_toe - half)) / math.sqrt(G * d)
+                                   + 40.0 * math.sqrt(d / G)) / dt)), K=K, friction=1 if f > 0 else 0, fcoef=f,
+                  sides=sides, eps=eps, solitons=[(H, 0.0, x_toe - half, 0.5 * ny * dx)])
+    sc.runup_delta = slope * dx / 3.0
+    return sc
+
+
+def conical_island(H_over_d: float = 0.09, n: int = 601, dt: float = 0.005, K: int = 1,
+                   eps: float = 1e-10) -> Scenario:
+    """Solitary wave on a conical island (Sec. 4.3): a 30 m x 30 m domain on
+    n x n cells, still water 0.32 m deep, an island of 7.2 m base diameter
+    and 1/4 side slope at the centre (shoreline radius 2.32 m), a soliton of
+    height H near the west side, sponges west and east (parallel to the
+    crest), walls north and south, no friction, dt = 0.005 s.  The text gives
+    no island top; the cone is cut flat at 0.625 m above the tank floor (a top
+    diameter of 2.2 m), above any run-up of these cases."""
+    L, d = 30.0, 0.32
+    dx = L / n
+    X, Y = np.meshgrid((np.arange(n) + 0.5) * dx, (np.arange(n) + 0.5) * dx)
+    r = np.hypot(X - 0.5 * L, Y - 0.5 * L)
+    z = -d + np.clip((3.6 - r) / 4.0, 0.0, 0.625)
+    H = H_over_d * d
+    half = math.acosh(math.sqrt(20.0)) / math.sqrt(3.0 * H / (4.0 * d ** 3))
+    sponge = 1.5
+    x0 = sponge + half
+    sides = {W: Side(SPONGE, int(round(sponge / dx))), E: Side(SPONGE, int(round(sponge / dx))),
+             S: Side(SOLID), N: Side(SOLID)}
+    sc = Scenario(name=f"conical_island_H{H_over_d:g}_{n}", nx=n, ny=n, dx=dx, dy=dx, dt=dt, z=z,
+                  steps=int(round(20.0 / dt)), K=K, sides=sides, eps=eps, solitons=[(H, 0.0, x0, 0.5 * L)])
+    sc.runup_delta = 0.25 * dx / 3.0
+    sc.center = (0.5 * L, 0.5 * L)
+    # gauges by role: the toe in front, the shoreline in front, on the north
+    # side and behind (the paper's gauge numbers refer to its Fig. 10)
+    sc.gauges_xy = [(0.5 * L - 3.6 - 0.5, 0.5 * L), (0.5 * L - 2.32 - 0.1, 0.5 * L),
+                    (0.5 * L, 0.5 * L + 2.32 + 0.1), (0.5 * L + 2.32 + 0.1, 0.5 * L)]
+    return sc
