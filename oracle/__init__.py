@@ -17,6 +17,11 @@ each one are named in the test module docstrings):
   * friction + AB3 order: uniform-flow ODE -- pinned
   * Euler start-up, AM4 corrector, sine-ghost timing, corner ghosts:
     parity unpinned (internal consistency only).
+  * run-up tracking: standing-mode maximum, dry threshold -- pinned
+  * render oracle (render_oracle.c, the headless renderer): Fresnel closed
+    forms, colormap control points, flat lake / tilted plane / flat land by
+    formula, grid lines, speed, mirror symmetry -- pinned
+    (tests/test_render_oracle_pins.py).
 """
 from __future__ import annotations
 
@@ -251,3 +256,77 @@ def central_upwind(g, eps, wL, nL, tL, wR, nR, tR, Bf):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+# ------------------------------------------------------------------ render
+# CPU restatement of the headless renderer (render_oracle.c): a separate
+# library, single precision, one rounded operation at a time.
+
+_RSRC = os.path.join(_HERE, "render_oracle.c")
+_RHDR = os.path.join(_HERE, "render_oracle.h")
+_RLIB = os.path.join(_HERE, "_build", "librender_oracle.so")
+_rlib = None
+
+RENDER_MODES = {"eta": 0, "u": 1, "v": 2, "speed": 3, "fresnel": 4}
+
+
+class RoParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("vmin", ctypes.c_float), ("vmax", ctypes.c_float),
+                ("dry_h", ctypes.c_float), ("h_min", ctypes.c_float), ("zmin", ctypes.c_float),
+                ("zmax", ctypes.c_float), ("grid", ctypes.c_float), ("exaggeration", ctypes.c_float),
+                ("view", ctypes.c_float * 3), ("sun", ctypes.c_float * 3), ("absorb", ctypes.c_float)]
+
+
+def build_render(force: bool = False) -> str:
+    """Compile the render oracle (plain C99, single precision, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_RLIB), exist_ok=True)
+    newest = max(os.path.getmtime(_RSRC), os.path.getmtime(_RHDR))
+    if not force and os.path.exists(_RLIB) and os.path.getmtime(_RLIB) >= newest:
+        return _RLIB
+    tmp = _RLIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _RSRC, "-lm"],
+                   check=True)
+    os.replace(tmp, _RLIB)
+    return _RLIB
+
+
+def render_lib():
+    global _rlib
+    with _lock:
+        if _rlib is None:
+            L = ctypes.CDLL(os.environ.get("RENDER_ORACLE_LIB") or build_render())
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.ro_render.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    dp, dp, dp, dp, ctypes.POINTER(RoParams), ctypes.c_void_p]
+            L.ro_fresnel.restype = ctypes.c_float
+            L.ro_fresnel.argtypes = [ctypes.c_float]
+            L.ro_colormap.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
+            _rlib = L
+        return _rlib
+
+
+def render_params(mode="eta", vmin=-1.0, vmax=1.0, dry_h=1e-3, h_min=1e-2, zmin=-1.0, zmax=1.0, grid=0.0,
+                  exaggeration=1.0, view=(0.0, 0.0, -1.0), sun=(0.3, 0.4, 1.0), absorb=0.5) -> RoParams:
+    return RoParams(RENDER_MODES[mode] if isinstance(mode, str) else int(mode), vmin, vmax, dry_h, h_min, zmin,
+                    zmax, grid, exaggeration, (ctypes.c_float * 3)(*view), (ctypes.c_float * 3)(*sun), absorb)
+
+
+def render(w, P, Q, Bbar, dx, dy, ws=0.0, params: RoParams = None) -> np.ndarray:
+    """RGBA image (ny, nx, 4) uint8 of the state (row j = grid row j)."""
+    w, P, Q, Bbar = (_f64(a) for a in (w, P, Q, Bbar))
+    ny, nx = w.shape
+    out = np.zeros((ny, nx, 4), np.uint8)
+    p = params or render_params()
+    render_lib().ro_render(nx, ny, dx, dy, ws, _dp(w), _dp(P), _dp(Q), _dp(Bbar), ctypes.byref(p),
+                           out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def fresnel(cos_i):
+    return render_lib().ro_fresnel(cos_i)
+
+
+def colormap(which, t):
+    out = (ctypes.c_float * 3)()
+    render_lib().ro_colormap(which, t, out)
+    return np.array(out[:], np.float32)

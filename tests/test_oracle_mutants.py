@@ -66,3 +66,36 @@ def test_pin_catches_mutant(tmp_path, name, orig, mut, pin):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", pin],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, f"pin {pin} did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
+RENDER_SRC = os.path.join(ROOT, "oracle", "render_oracle.c")
+RENDER_MUTANTS = [
+    ("fresnel_index_side", "float rs = (cos_i - kN2 * cos_t) / (cos_i + kN2 * cos_t);",
+     "float rs = (kN2 * cos_i - cos_t) / (kN2 * cos_i + cos_t);", "test_fresnel_closed_forms"),
+    ("grid_off_by_one", "floorf((float)(i + 1) * dx / p->grid) != floorf((float)i * dx / p->grid)",
+     "floorf((float)(i + 2) * dx / p->grid) != floorf((float)(i + 1) * dx / p->grid)", "test_grid_lines"),
+    ("normal_gradient_sign", "float n[3] = {-(p->exaggeration * gx), -(p->exaggeration * gy), 1.0f};",
+     "float n[3] = {(p->exaggeration * gx), -(p->exaggeration * gy), 1.0f};", "test_tilted_plane_oblique_view"),
+    ("refraction_weight", "float a = 1.0f / (1.0f + p->absorb * h);", "float a = 1.0f / (1.0f + p->absorb);",
+     "test_flat_lake_from_above"),
+    ("speed_uses_P_twice", "v = sqrtf(u * u + vv * vv);", "v = sqrtf(u * u + u * u);",
+     "test_speed_and_velocity_components"),
+]
+
+
+@pytest.mark.parametrize("name,orig,mut,pin", RENDER_MUTANTS, ids=[m[0] for m in RENDER_MUTANTS])
+def test_render_pin_catches_mutant(tmp_path, name, orig, mut, pin):
+    src = open(RENDER_SRC).read()
+    assert src.count(orig) == 1, f"mutation site for {name} not found"
+    mdir = tmp_path / "render_mutant"
+    mdir.mkdir()
+    (mdir / "render_oracle.c").write_text(src.replace(orig, mut, 1))
+    (mdir / "render_oracle.h").write_text(open(os.path.join(ROOT, "oracle", "render_oracle.h")).read())
+    so = mdir / "librender_mutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                    str(mdir / "render_oracle.c"), "-lm"], check=True)
+    env = dict(os.environ, RENDER_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_render_oracle_pins.py"), "-k", pin],
+                       cwd=ROOT, env=env, capture_output=True, text=True)
+    assert r.returncode != 0, f"pin {pin} did not catch mutant {name}:\n{r.stdout[-2000:]}"

@@ -1,0 +1,149 @@
+"""Pins of the render oracle (the CPU restatement of the headless renderer)
+against closed forms and invariants, computed here in FP64:
+
+* Fresnel reflectance: the unpolarised Fresnel equations for air -> water
+  (R = ((n - 1)/(n + 1))^2 at normal incidence, 1 at grazing incidence);
+* colormaps: their control points and linearity between them;
+* a flat lake seen from straight above: reflection of the zenith colour with
+  the normal-incidence R, refraction of the bed colour weighted by
+  1 / (1 + absorb h), by formula;
+* flat land under a sun straight above is the bare terrain colour, and
+  under a sun 60 degrees off the vertical the terrain colour times 0.675;
+* grid lines where x / spacing crosses an integer;
+* speed = |(P, Q)| / h;
+* mirror symmetry: a state mirrored in x, seen and lit from the mirrored
+  directions, renders as the mirrored image, byte for byte.
+"""
+import math
+
+import numpy as np
+import pytest
+
+N2 = 1.333
+SKY_ZENITH = np.array([0.250, 0.450, 0.800])
+WATER = np.array([0.020, 0.150, 0.200])
+TERRAIN0 = np.array([0.780, 0.700, 0.500])     # the terrain map at t = 0
+
+
+def _fresnel64(cos_i):
+    sin_t = math.sqrt(1 - cos_i ** 2) / N2
+    cos_t = math.sqrt(1 - sin_t ** 2)
+    rs = (cos_i - N2 * cos_t) / (cos_i + N2 * cos_t)
+    rp = (N2 * cos_i - cos_t) / (N2 * cos_i + cos_t)
+    return 0.5 * (rs * rs + rp * rp)
+
+
+def _bytes(rgb):
+    return np.array([int(min(max(c, 0.0), 1.0) * 255 + 0.5) for c in rgb])
+
+
+def test_fresnel_closed_forms(oracle_mod):
+    assert abs(oracle_mod.fresnel(1.0) - ((N2 - 1) / (N2 + 1)) ** 2) <= 1e-7
+    assert abs(oracle_mod.fresnel(0.0) - 1.0) <= 1e-7
+    prev = 2.0
+    for c in np.linspace(0.0, 1.0, 41):
+        r = oracle_mod.fresnel(float(c))
+        assert abs(r - _fresnel64(c)) <= 2e-6
+        assert r <= prev + 1e-7            # reflectance falls as the incidence steepens
+        prev = r
+
+
+def test_colormap_control_points_and_linearity(oracle_mod):
+    for which in range(3):
+        pts = [oracle_mod.colormap(which, k / 4) for k in range(5)]
+        for k in range(4):
+            mid = oracle_mod.colormap(which, (k + 0.5) / 4)
+            np.testing.assert_allclose(mid, 0.5 * (pts[k] + pts[k + 1]), atol=1e-6)
+        np.testing.assert_array_equal(oracle_mod.colormap(which, -3.0), pts[0])
+        np.testing.assert_array_equal(oracle_mod.colormap(which, 7.0), pts[4])
+    np.testing.assert_allclose(oracle_mod.colormap(2, 0.0), TERRAIN0, atol=1e-7)
+
+
+def test_flat_lake_from_above(oracle_mod):
+    h, absorb = 2.0, 0.5
+    w = np.zeros((6, 7))
+    B = np.full((6, 7), -h)
+    p = oracle_mod.render_params("fresnel", zmin=-h, zmax=1.0, absorb=absorb, view=(0.0, 0.0, -1.0))
+    img = oracle_mod.render(w, w, w, B, 1.0, 1.0, 0.0, p)
+    R = ((N2 - 1) / (N2 + 1)) ** 2
+    refr = WATER + (TERRAIN0 - WATER) / (1 + absorb * h)   # the bed sits at zmin
+    want = _bytes(R * SKY_ZENITH + (1 - R) * refr)
+    assert np.all(np.abs(img[..., :3].astype(int) - want) <= 1)
+    assert np.all(img[..., 3] == 255)
+    assert np.all(img == img[0, 0])                          # uniform
+
+
+def test_flat_land_hillshade(oracle_mod):
+    z = np.full((5, 5), 0.5)
+    w = z.copy()                                             # dry: w = bed
+    p = oracle_mod.render_params("eta", zmin=0.5, zmax=1.5, sun=(0.0, 0.0, 1.0))
+    img = oracle_mod.render(w, 0 * w, 0 * w, z, 1.0, 1.0, 0.0, p)
+    assert np.all(np.abs(img[..., :3].astype(int) - _bytes(TERRAIN0)) <= 1)
+    p = oracle_mod.render_params("eta", zmin=0.5, zmax=1.5, sun=(math.sin(math.pi / 3), 0.0, 0.5))
+    img = oracle_mod.render(w, 0 * w, 0 * w, z, 1.0, 1.0, 0.0, p)
+    assert np.all(np.abs(img[..., :3].astype(int) - _bytes(TERRAIN0 * (0.35 + 0.65 * 0.5))) <= 1)
+
+
+def test_grid_lines(oracle_mod):
+    nx, ny, dx = 40, 3, 0.5
+    w = np.zeros((ny, nx))
+    B = np.full((ny, nx), -1.0)
+    base = oracle_mod.render(w, w, w, B, dx, 0.3, 0.0, oracle_mod.render_params("eta"))
+    img = oracle_mod.render(w, w, w, B, dx, 0.3, 0.0, oracle_mod.render_params("eta", grid=2.0))
+    darker = np.where(np.any(img[1, :, :3] != base[1, :, :3], axis=-1))[0]
+    # x = (i + 1) dx crosses a multiple of 2 m for i = 3, 7, 11, ...
+    np.testing.assert_array_equal(darker, np.arange(3, nx, 4))
+
+
+def test_speed_and_velocity_components(oracle_mod):
+    h = 2.0
+    B = np.full((3, 3), -h)
+    w = np.zeros((3, 3))
+    P = np.full((3, 3), 3.0 * h)
+    Q = np.full((3, 3), 4.0 * h)
+    for mode, val, m in (("speed", 5.0, 1), ("u", 3.0, 0), ("v", 4.0, 0)):
+        p = oracle_mod.render_params(mode, vmin=0.0, vmax=10.0)
+        img = oracle_mod.render(w, P, Q, B, 1.0, 1.0, 0.0, p)
+        want = _bytes(oracle_mod.colormap(m, val / 10.0))
+        np.testing.assert_array_equal(img[1, 1, :3], want)
+
+
+@pytest.mark.parametrize("mode", ["fresnel", "eta", "v", "speed"])
+def test_mirror_symmetry(oracle_mod, mode):
+    rng = np.random.default_rng(3)
+    ny, nx = 9, 12
+    B = -1.0 + 1.2 * rng.random((ny, nx))
+    w = np.maximum(B, 0.05 * rng.standard_normal((ny, nx)))
+    P = 0.3 * rng.standard_normal((ny, nx))
+    Q = 0.3 * rng.standard_normal((ny, nx))
+    args = dict(vmin=-0.5, vmax=0.5, zmin=-1.0, zmax=0.5, grid=0.0, exaggeration=4.0)
+    a = oracle_mod.render(w, P, Q, B, 1.0, 1.0, 0.0,
+                          oracle_mod.render_params(mode, view=(0.4, 0.2, -1.0), sun=(0.5, 0.3, 1.0), **args))
+    b = oracle_mod.render(w[:, ::-1], -P[:, ::-1], Q[:, ::-1], B[:, ::-1], 1.0, 1.0, 0.0,
+                          oracle_mod.render_params(mode, view=(-0.4, 0.2, -1.0), sun=(-0.5, 0.3, 1.0), **args))
+    np.testing.assert_array_equal(a, b[:, ::-1])
+
+
+def test_tilted_plane_oblique_view(oracle_mod):
+    """A plane water surface eta = s x seen along (0.6, 0, -0.8): the
+    surface normal (-s, 0, 1)/sqrt(1 + s^2) gives cos i = (0.6 s + 0.8) /
+    sqrt(1 + s^2) and the reflected ray's height -0.8 + 2 cos_i / sqrt(1 +
+    s^2); the interior pixels follow by formula (the edges use one-sided
+    differences of the same plane)."""
+    nx, ny, dx, s, d = 12, 5, 0.1, 0.5, 3.0
+    x = (np.arange(nx) + 0.5) * dx
+    w = np.tile(s * x, (ny, 1))
+    B = np.full((ny, nx), -d)
+    p = oracle_mod.render_params("fresnel", zmin=-d, zmax=1.0, absorb=0.5, view=(0.6, 0.0, -0.8))
+    img = oracle_mod.render(w, 0 * w, 0 * w, B, dx, dx, 0.0, p)
+    nz = 1 / math.sqrt(1 + s * s)
+    cos_i = (0.6 * s + 0.8) * nz
+    R = _fresnel64(cos_i)
+    rz = -0.8 + 2 * cos_i * nz
+    horizon = np.array([0.780, 0.850, 0.920])
+    sky = horizon + (SKY_ZENITH - horizon) * min(max(rz, 0.0), 1.0)
+    for i in range(1, nx - 1):
+        h = w[2, i] + d
+        refr = WATER + (TERRAIN0 - WATER) / (1 + 0.5 * h)
+        want = _bytes(R * sky + (1 - R) * refr)
+        assert np.all(np.abs(img[2, i, :3].astype(int) - want) <= 1), i
