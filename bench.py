@@ -397,6 +397,21 @@ def main():
                 "step_bytes_algorithmic": (st_bytes + line_bytes) / args.steps,
                 "step_gbs_algorithmic": (st_bytes + line_bytes) / (ms / 1e3) / 1e9 / world}
 
+    # ---- headless rendering of the final state (Fresnel water, hillshaded land)
+    rp = celeris.render_params("fresnel", zmin=-10.0, zmax=3.0, exaggeration=10.0, view=(0.5, 0.3, -0.8))
+    img = sol.render(rp)
+    for _ in range(3):
+        sol.render(rp, out=img)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(20):
+        sol.render(rp, out=img)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rms = r0.elapsed_time(r1) / 20
+    render = {"mode": "fresnel", "ms_per_frame": rms, "pixels_per_s": s.cells / (rms / 1e3),
+              "what": "cel_render of the final state into a device RGBA8 image, one pixel per cell"}
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -416,7 +431,7 @@ def main():
                            "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (workspace %.0f MB > 129 MB)"
                                  % (sol.workspace.numel() / 1e6)},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "render": render,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

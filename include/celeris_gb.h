@@ -174,6 +174,38 @@ cel_status cel_load_checkpoint(cel_solver *s, const void *src_dev, size_t bytes)
  * allocated while enabled.  CEL_ERR_INVALID_ARG for delta < 0. */
 cel_status cel_runup_enable(cel_solver *s, void *maxw_dev, double delta);
 
+/* Headless rendering of the present state into an RGBA image, for the
+ * visualisation options of Sec. 3: a colormap of eta, u, v or the velocity
+ * magnitude, or the water surface shaded photorealistically (reflection of a
+ * sky gradient and refraction of the bed, weighted by the Fresnel equations
+ * for air -> water); land (depth <= dry_h) is the terrain colormap of the bed
+ * elevation with a hillshade; optional grid lines every `grid` metres.  No
+ * graphics API is involved: the image is written to device memory.
+ *
+ * rgba_dev: [ny][nx][4] bytes (R, G, B, 255), device, owned by the caller;
+ * row j of the image is grid row j (south first), one pixel per cell.
+ * Velocities are u = P / max(h, h_min), v = Q / max(h, h_min).  The shading
+ * is single precision, each operation rounded on its own (no fused
+ * multiply-add, no transcendental functions), so the bytes are reproducible.
+ * Asynchronous on the handle's stream.  CEL_ERR_INVALID_ARG for a bad mode,
+ * vmax <= vmin, zmax <= zmin, grid < 0, dry_h < 0, h_min <= 0, absorb < 0,
+ * a zero view or sun vector or non-finite values. */
+enum { CEL_RENDER_ETA = 0, CEL_RENDER_U = 1, CEL_RENDER_V = 2, CEL_RENDER_SPEED = 3,
+       CEL_RENDER_FRESNEL = 4 };
+typedef struct {
+    int32_t mode;          /* CEL_RENDER_*                                         */
+    float vmin, vmax;      /* colormap range of the shown value (modes 0-3)        */
+    float dry_h;           /* land where w - Bbar <= dry_h                         */
+    float h_min;           /* floor of the depth in the velocities                 */
+    float zmin, zmax;      /* terrain colormap range of the bed elevation          */
+    float grid;            /* grid line spacing [m], 0 for none                    */
+    float exaggeration;    /* vertical scale of the surface and bed normals        */
+    float view[3];         /* direction of view, towards the surface               */
+    float sun[3];          /* direction towards the light (terrain hillshade)      */
+    float absorb;          /* refraction: the bed colour weighs 1 / (1 + absorb h) */
+} cel_render_params;
+cel_status cel_render(cel_solver *s, const cel_render_params *params, void *rgba_dev);
+
 /* Kernel launches issued by the most recent cel_step call. */
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);
 

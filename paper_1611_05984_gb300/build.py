@@ -12,7 +12,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libceleris_gb.so")
-SOURCES = ["celeris_kernels.cu", "celeris_api.cu"]
+SOURCES = ["celeris_kernels.cu", "celeris_api.cu", "celeris_render.cu"]
+# the renderer's bytes must not depend on fast-math choices: IEEE division and
+# square root, no contraction into FMA, denormals kept (its arithmetic also
+# spells out each rounding)
+SOURCE_FLAGS = {"celeris_render.cu": ["-ftz=false", "-prec-div=true", "-prec-sqrt=true", "-fmad=false"]}
 HEADERS = [os.path.join(CSRC, "celeris_internal.cuh"), os.path.join(INCLUDE, "celeris_gb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 division and square root use the fast reciprocal / reciprocal-square-root
@@ -48,7 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for src in SOURCES:
             obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
             objs.append(obj)
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+            flags = [f for f in FLAGS if not any(f.split("=")[0] == o.split("=")[0] for o in SOURCE_FLAGS.get(src, []))]
+            cmd = [nvcc, *ARCH, *flags, *SOURCE_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -31,7 +31,7 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_add_solitary", "cel_set_bathymetry", "cel_step", "cel_get_state", "cel_get_field",
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
-           "cel_load_checkpoint", "cel_runup_enable", "cel_last_launch_count", "cel_profile_enable",
+           "cel_load_checkpoint", "cel_runup_enable", "cel_render", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
         L.cel_save_checkpoint.argtypes = [vp, vp, sz]
         L.cel_load_checkpoint.argtypes = [vp, vp, sz]
         L.cel_runup_enable.argtypes = [vp, vp, d]
+        L.cel_render.argtypes = [vp, ctypes.POINTER(CelRenderParams), vp]
         L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_profile_enable.argtypes = [vp, i32]
         L.cel_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
@@ -130,6 +131,23 @@ def load(build_if_missing: bool = True):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
+
+
+RENDER_MODES = {"eta": 0, "u": 1, "v": 2, "speed": 3, "fresnel": 4}
+
+
+class CelRenderParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("vmin", ctypes.c_float), ("vmax", ctypes.c_float),
+                ("dry_h", ctypes.c_float), ("h_min", ctypes.c_float), ("zmin", ctypes.c_float),
+                ("zmax", ctypes.c_float), ("grid", ctypes.c_float), ("exaggeration", ctypes.c_float),
+                ("view", ctypes.c_float * 3), ("sun", ctypes.c_float * 3), ("absorb", ctypes.c_float)]
+
+
+def render_params(mode="eta", vmin=-1.0, vmax=1.0, dry_h=1e-3, h_min=1e-2, zmin=-1.0, zmax=1.0, grid=0.0,
+                  exaggeration=1.0, view=(0.0, 0.0, -1.0), sun=(0.3, 0.4, 1.0), absorb=0.5) -> CelRenderParams:
+    return CelRenderParams(RENDER_MODES[mode] if isinstance(mode, str) else int(mode), vmin, vmax, dry_h, h_min,
+                           zmin, zmax, grid, exaggeration, (ctypes.c_float * 3)(*view),
+                           (ctypes.c_float * 3)(*sun), absorb)
 
 
 class CelerisError(RuntimeError):
@@ -307,6 +325,16 @@ class Solver:
         n = ctypes.c_int64()
         self._check(self.L.cel_last_launch_count(self._h, ctypes.byref(n)), "last_launch_count")
         return n.value
+
+    def render(self, params: Optional[CelRenderParams] = None, out=None, **kw):
+        """RGBA image (ny, nx, 4) uint8 on the device of the present state
+        (row j = grid row j); params from render_params(...) or keywords."""
+        p = params if params is not None else render_params(**kw)
+        if out is None:
+            with self.torch.cuda.device(self.device):
+                out = self.torch.empty((self.ny, self.nx, 4), dtype=self.torch.uint8, device=self.device)
+        self._check(self.L.cel_render(self._h, ctypes.byref(p), out.data_ptr()), "render")
+        return out
 
     def runup_enable(self, delta: float):
         """Track the highest w seen where the depth exceeds delta (Sec. 4.1,

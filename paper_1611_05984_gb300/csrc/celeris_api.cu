@@ -876,6 +876,52 @@ cel_status cel_runup_enable(cel_solver *s, void *maxw_dev, double delta)
     return CEL_OK;
 }
 
+cel_status cel_render(cel_solver *s, const cel_render_params *p, void *rgba_dev)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    if (!p || !rgba_dev) return fail(s, CEL_ERR_INVALID_ARG, "NULL render parameters or image");
+    const float vals[] = {p->vmin, p->vmax, p->dry_h, p->h_min, p->zmin, p->zmax, p->grid, p->exaggeration,
+                          p->view[0], p->view[1], p->view[2], p->sun[0], p->sun[1], p->sun[2], p->absorb};
+    for (float v : vals)
+        if (!isfinite(v)) return fail(s, CEL_ERR_INVALID_ARG, "non-finite render parameter");
+    const bool view0 = p->view[0] == 0.f && p->view[1] == 0.f && p->view[2] == 0.f;
+    const bool sun0 = p->sun[0] == 0.f && p->sun[1] == 0.f && p->sun[2] == 0.f;
+    if (p->mode < CEL_RENDER_ETA || p->mode > CEL_RENDER_FRESNEL || !(p->vmax > p->vmin) ||
+        !(p->zmax > p->zmin) || p->grid < 0.f || p->dry_h < 0.f || !(p->h_min > 0.f) || p->absorb < 0.f || view0 ||
+        sun0)
+        return fail(s, CEL_ERR_INVALID_ARG, "bad render parameters");
+    cudaError_t e;
+    if (s->es == 4) {
+        RenderArgs<float> a;
+        a.geo = s->geo;
+        a.dx = (float)s->grid.dx;
+        a.dy = (float)s->grid.dy;
+        a.ws = (float)s->params.still_water;
+        a.p = *p;
+        a.w = s->at<float>(s->lay.w[s->cur]);
+        a.P = s->at<float>(s->lay.P[s->pcur]);
+        a.Qc = s->at<float>(s->lay.Qc[s->pcur]);
+        a.Bc = s->at<float>(s->lay.Bc);
+        a.rgba = (uchar4 *)rgba_dev;
+        e = launch_render<float>(a, s->stream);
+    } else {
+        RenderArgs<double> a;
+        a.geo = s->geo;
+        a.dx = (float)s->grid.dx;
+        a.dy = (float)s->grid.dy;
+        a.ws = (float)s->params.still_water;
+        a.p = *p;
+        a.w = s->at<double>(s->lay.w[s->cur]);
+        a.P = s->at<double>(s->lay.P[s->pcur]);
+        a.Qc = s->at<double>(s->lay.Qc[s->pcur]);
+        a.Bc = s->at<double>(s->lay.Bc);
+        a.rgba = (uchar4 *)rgba_dev;
+        e = launch_render<double>(a, s->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "render");
+    return CEL_OK;
+}
+
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches)
 {
     if (!s || !launches) return CEL_ERR_INVALID_ARG;

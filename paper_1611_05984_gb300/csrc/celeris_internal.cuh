@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "celeris_gb.h"
+
 namespace cel {
 
 constexpr int kTile = 32;          // stencil tile edge (cells)
@@ -111,6 +113,27 @@ __host__ __device__ inline size_t ghost_index(int time, int side, int layer, int
     return ((((size_t)time * 4 + side) * 2 + layer) * 3 + var) * (size_t)npos + pos;
 }
 
+// Reading A-W1: the cell bed Bbar is the mean of the cell's 4 corners; the
+// corner array is (nx + 3) x (ny + 3) with corner (ci, cj) at [cj + 1][ci + 1].
+template <typename real>
+__device__ __forceinline__ real cell_bbar(real c00, real c10, real c01, real c11)
+{
+    return real(0.25) * (((c00 + c10) + c01) + c11);
+}
+
+template <typename real>
+__device__ __forceinline__ real corner(const real *Bc, const Geo &g, int ci, int cj)
+{
+    return Bc[(size_t)(cj + 1) * g.pc + (ci + 1)];
+}
+
+template <typename real>
+__device__ __forceinline__ real bbar_at(const real *Bc, const Geo &g, int i, int j)
+{
+    return cell_bbar(corner(Bc, g, i, j), corner(Bc, g, i + 1, j), corner(Bc, g, i, j + 1),
+                     corner(Bc, g, i + 1, j + 1));
+}
+
 template <typename real>
 struct StencilArgs {
     Geo geo;
@@ -152,6 +175,19 @@ struct LineArgs {
     int identity;          // NLSW model: no dispersive solve, P = U*, Q = V*
     real rh, rh2, hrh, srh; // 1/h, 1/h^2, 1/(2h), 1/(6h) along the line
 };
+
+// Headless rendering of the state (celeris_render.cu).
+template <typename real>
+struct RenderArgs {
+    Geo geo;
+    float dx, dy, ws;
+    cel_render_params p;
+    const real *w, *P, *Qc, *Bc;
+    uchar4 *rgba;          // [ny][nx]
+};
+
+template <typename real>
+cudaError_t launch_render(const RenderArgs<real> &a, cudaStream_t st);
 
 // Launchers (celeris_kernels.cu).  All return cudaGetLastError().
 template <typename real>

@@ -131,12 +131,6 @@ __device__ __forceinline__ real sponge_gamma(const Coef<real> &c, const Geo &g, 
     return gm;
 }
 
-template <typename real>
-__device__ __forceinline__ real cell_bbar(real c00, real c10, real c01, real c11)
-{
-    return real(0.25) * (((c00 + c10) + c01) + c11);
-}
-
 // ------------------------------------------------------------ static fields
 
 // a0 (Reading A-W1): corner bed = mean of the 4 cells around it, with the
@@ -152,19 +146,6 @@ __global__ void k_corners(Geo g, const real *__restrict__ z, real *__restrict__ 
     real z00 = z[(size_t)j0 * g.nx + i0], z10 = z[(size_t)j0 * g.nx + i1];
     real z01 = z[(size_t)j1 * g.nx + i0], z11 = z[(size_t)j1 * g.nx + i1];
     Bc[(size_t)(cj + 1) * g.pc + (ci + 1)] = real(0.25) * (((z00 + z10) + z01) + z11);
-}
-
-template <typename real>
-__device__ __forceinline__ real corner(const real *Bc, const Geo &g, int ci, int cj)
-{
-    return Bc[(size_t)(cj + 1) * g.pc + (ci + 1)];
-}
-
-template <typename real>
-__device__ __forceinline__ real bbar_at(const real *Bc, const Geo &g, int i, int j)
-{
-    return cell_bbar(corner(Bc, g, i, j), corner(Bc, g, i + 1, j), corner(Bc, g, i, j + 1),
-                     corner(Bc, g, i + 1, j + 1));
 }
 
 template <typename real>
