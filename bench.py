@@ -227,12 +227,26 @@ def run_ensemble(args):
     from paper_1611_05984_gb300 import celeris
     from paper_1611_05984_gb300 import scenarios as sc
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:   # scenarios are independent: each rank steps its share, no data-path collective
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
     dtype = torch.float32 if args.precision == "f32" else torch.float64
     es = 4 if args.precision == "f32" else 8
-    scens = sc.ensemble()
+    every = sc.ensemble()
+    share = sc.partition([s.cells for s in every], world)[rank]
+    scens = [every[k] for k in share]
     members = [celeris.from_scenario(s, dtype=dtype) for s in scens]
     cells = sum(s.cells for s in scens)
+    total_cells = sum(s.cells for s in every)
     stream = members[0].stream
     ens = celeris.Ensemble(members, stream=stream)
     ens.step(args.warmup)
@@ -246,6 +260,8 @@ def run_ensemble(args):
     time.sleep(0.4)
     torch.cuda.synchronize()
     ens.profile_enable(8 * (scens[0].K + 1) * args.steps + 16)
+    barrier()
+    torch.cuda.synchronize()
     e[0].record(stream)
     launches = 0
     for _ in range(args.steps):
@@ -253,11 +269,14 @@ def run_ensemble(args):
         launches += ens.last_launch_count()
     e[1].record(stream)
     torch.cuda.synchronize()
+    barrier()
     prof = ens.profile_read()
     ens.profile_disable()
     # the same members one at a time: one cel_step of all K steps per member
     # (launch-bound on small grids, with the least host work per launch), and
     # interleaved (every member one step, K times)
+    barrier()
+    torch.cuda.synchronize()
     e[2].record(stream)
     single_launches = 0
     for m in members:
@@ -265,6 +284,7 @@ def run_ensemble(args):
         single_launches += m.last_launch_count()
     e[3].record(stream)
     torch.cuda.synchronize()
+    barrier()
     e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e4.record(stream)
     for _ in range(args.steps):
@@ -272,12 +292,15 @@ def run_ensemble(args):
             m.step(1)
     e5.record(stream)
     torch.cuda.synchronize()
+    barrier()
     clk = clocks.stop()
-    ms_ens, ms_one, ms_inter = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]), e4.elapsed_time(e5)
-    ms_one = min(ms_one, ms_inter)
+    ms_ens = max_over_ranks(e[0].elapsed_time(e[1]))
+    ms_runs = max_over_ranks(e[2].elapsed_time(e[3]))
+    ms_inter = max_over_ranks(e4.elapsed_time(e5))
+    ms_one = min(ms_runs, ms_inter)
     finite = all(m.check_finite() for m in members)
-    value = cells * args.steps / (ms_ens / 1e3)
-    one = cells * args.steps / (ms_one / 1e3)
+    value = total_cells * args.steps / (ms_ens / 1e3)
+    one = total_cells * args.steps / (ms_one / 1e3)
     peak, peak_src = peaks()
     # algorithmic bytes over all members: the per-cell values of the
     # single-grid kernels (predictor + K corrector stencils, K + 1 line stages)
@@ -291,18 +314,23 @@ def run_ensemble(args):
     dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
     achieved = kernels[dominant]["gbs_algorithmic"]
     gbs = (bytes_of["stencil"] + bytes_of["lines"]) / (ms_ens / 1e3) / 1e9
-    line = {"metric": "ensemble cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": 1,
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {"metric": "ensemble cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ens / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic",
-            "config": {"workload": "ensemble256", "members": len(scens), "cells": cells,
-                       "corrector_iters": K, "parallelism": "replicas1",
+            "config": {"workload": "ensemble256", "members": len(every), "cells": total_cells,
+                       "members_rank0": len(scens), "corrector_iters": K,
+                       "parallelism": f"scenarios partitioned over {world} ranks by cell count",
                        "l2": "inputs larger than L2 (%.1f GB of workspaces)"
                              % (sum(m.workspace.numel() for m in members) / 1e9)},
             "single_launch": {"value": one, "ms_per_step": ms_one / args.steps,
                               "what": "the same members one at a time, the faster of: one cel_step(K steps) "
                                       "per member in turn, and every member one cel_step(1) per step",
-                              "ms_per_step_per_member_runs": e[2].elapsed_time(e[3]) / args.steps,
+                              "ms_per_step_per_member_runs": ms_runs / args.steps,
                               "ms_per_step_interleaved": ms_inter / args.steps,
                               "gpu_launches": single_launches},
             "speedup_vs_single_launch": value / one,
@@ -311,6 +339,8 @@ def run_ensemble(args):
                          "per_kernel": kernels, "step_gbs_algorithmic": gbs},
             "finite": finite, "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():

@@ -297,3 +297,16 @@ def conical_island(H_over_d: float = 0.09, n: int = 601, dt: float = 0.005, K: i
     sc.gauges_xy = [(0.5 * L - 3.6 - 0.5, 0.5 * L), (0.5 * L - 2.32 - 0.1, 0.5 * L),
                     (0.5 * L, 0.5 * L + 2.32 + 0.1), (0.5 * L + 2.32 + 0.1, 0.5 * L)]
     return sc
+
+
+def partition(cells, parts: int) -> list:
+    """Indices of the items split into `parts` groups of nearly equal total
+    cells: largest first, each to the group with the fewest cells so far
+    (ties to the lowest group).  Every index appears exactly once."""
+    groups = [[] for _ in range(parts)]
+    load = [0] * parts
+    for k in sorted(range(len(cells)), key=lambda k: (-cells[k], k)):
+        g = min(range(parts), key=lambda r: (load[r], r))
+        groups[g].append(k)
+        load[g] += cells[k]
+    return [sorted(g) for g in groups]

@@ -47,3 +47,17 @@ def test_single_process_defaults():
     import bench
     assert bench.max_over_ranks(7.5) == 7.5
     assert bench.whole_job_rate(100, 10, 1000.0) == pytest.approx(1000.0)
+
+
+def test_ensemble_partition_covers_and_balances():
+    """The multi-rank ensemble bench gives each rank a share of the
+    scenarios: every scenario exactly once, totals within one scenario."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    cells = [s.cells for s in sc.ensemble()]
+    for world in (1, 2, 3, 8):
+        parts = sc.partition(cells, world)
+        flat = sorted(k for p in parts for k in p)
+        assert flat == list(range(len(cells)))
+        loads = [sum(cells[k] for k in p) for p in parts]
+        assert max(loads) - min(loads) <= max(cells)
+    assert sc.partition([5, 4, 3, 3, 2, 1], 2) == [[0, 3, 5], [1, 2, 4]]   # loads 9 and 9
