@@ -491,7 +491,7 @@ def whole_job_rate(cells_per_rank: int, steps: int, ms: float) -> float:
 def celeris_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("celeris_kernels.cu", "celeris_internal.cuh"):
+    for f in ("celeris_kernels.cu", "celeris_internal.cuh", "celeris_physics.cuh"):
         with open(os.path.join(ROOT, "paper_1611_05984_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

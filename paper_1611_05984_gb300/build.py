@@ -12,12 +12,13 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libceleris_gb.so")
-SOURCES = ["celeris_kernels.cu", "celeris_api.cu", "celeris_render.cu"]
+SOURCES = ["celeris_kernels.cu", "celeris_api.cu", "celeris_render.cu", "celeris_adjoint.cu"]
 # the renderer's bytes must not depend on fast-math choices: IEEE division and
 # square root, no contraction into FMA, denormals kept (its arithmetic also
 # spells out each rounding)
 SOURCE_FLAGS = {"celeris_render.cu": ["-ftz=false", "-prec-div=true", "-prec-sqrt=true", "-fmad=false"]}
-HEADERS = [os.path.join(CSRC, "celeris_internal.cuh"), os.path.join(INCLUDE, "celeris_gb.h")]
+HEADERS = [os.path.join(CSRC, "celeris_internal.cuh"), os.path.join(CSRC, "celeris_physics.cuh"),
+           os.path.join(INCLUDE, "celeris_gb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 division and square root use the fast reciprocal / reciprocal-square-root
 # paths (about 2 ulp); FP64 arithmetic is unaffected by these flags.

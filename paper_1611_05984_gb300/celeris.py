@@ -31,7 +31,8 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_add_solitary", "cel_set_bathymetry", "cel_step", "cel_get_state", "cel_get_field",
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
-           "cel_load_checkpoint", "cel_runup_enable", "cel_render", "cel_last_launch_count", "cel_profile_enable",
+           "cel_load_checkpoint", "cel_runup_enable", "cel_render", "cel_adjoint_bytes",
+           "cel_adjoint_gauge_misfit", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
@@ -100,6 +101,9 @@ def load(build_if_missing: bool = True):
         L.cel_load_checkpoint.argtypes = [vp, vp, sz]
         L.cel_runup_enable.argtypes = [vp, vp, d]
         L.cel_render.argtypes = [vp, ctypes.POINTER(CelRenderParams), vp]
+        L.cel_adjoint_bytes.argtypes = [vp, i32, i32, i32, ctypes.POINTER(sz)]
+        L.cel_adjoint_gauge_misfit.argtypes = [vp, i32, i32, ctypes.POINTER(i32), i32, vp, vp, sz, vp, vp,
+                                               ctypes.POINTER(d)]
         L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_profile_enable.argtypes = [vp, i32]
         L.cel_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
@@ -426,6 +430,64 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every: int = 100):
+    """Run nsteps from the solver's present (freshly set) state and return
+    (L, eta, dL/dw0): the gauge misfit L = 1/2 sum (eta - obs)^2 over steps
+    1..nsteps, the recorded eta ([nsteps, ngauges] tensor) and its gradient
+    with respect to w at the start ([ny, nx] tensor), by the discrete
+    adjoint (cel_adjoint_gauge_misfit).  obs: [nsteps, ngauges]."""
+    torch = solver.torch
+    ij = np.ascontiguousarray(np.asarray(gauges, dtype=np.int32).reshape(-1, 2))
+    ng = len(ij)
+    obs_t = torch.as_tensor(obs).to(device=solver.device, dtype=solver.dtype).contiguous()
+    if tuple(obs_t.shape) != (nsteps, ng):
+        raise ValueError("obs must be [nsteps, ngauges]")
+    nb = ctypes.c_size_t()
+    solver._check(solver.L.cel_adjoint_bytes(solver._h, nsteps, ckpt_every, ng, ctypes.byref(nb)), "adjoint_bytes")
+    with torch.cuda.device(solver.device):
+        scratch = torch.empty(nb.value + 256, dtype=torch.uint8, device=solver.device)
+        eta = torch.empty((nsteps, ng), dtype=solver.dtype, device=solver.device)
+        grad = torch.empty((solver.ny, solver.nx), dtype=solver.dtype, device=solver.device)
+    ptr = (scratch.data_ptr() + 255) // 256 * 256
+    loss = ctypes.c_double()
+    st = solver.L.cel_adjoint_gauge_misfit(solver._h, nsteps, ckpt_every,
+                                           ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ng,
+                                           obs_t.data_ptr(), ptr, nb.value, eta.data_ptr(), grad.data_ptr(),
+                                           ctypes.byref(loss))
+    solver._check(st, "adjoint_gauge_misfit")
+    return loss.value, eta, grad
+
+
+def _gauge_misfit_function():
+    import torch
+
+    class GaugeMisfit(torch.autograd.Function):
+        """L(w0) = 1/2 sum (eta - obs)^2 over nsteps steps from w0 (with P0, Q0
+        fixed); backward gives dL/dw0 from the discrete adjoint.  Where w0 lies
+        below the bed the state is clamped to it, and the gradient there is 0."""
+
+        @staticmethod
+        def forward(ctx, w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every=100):
+            solver.set_state(w0, P0, Q0)
+            loss, _, grad = gauge_misfit_gradient(solver, nsteps, gauges, obs, ckpt_every)
+            bed = solver.field("Bbar").to(grad.dtype)
+            grad = torch.where(w0.to(device=grad.device, dtype=grad.dtype) > bed, grad, torch.zeros_like(grad))
+            ctx.save_for_backward(grad)
+            return torch.tensor(loss, dtype=w0.dtype, device=w0.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return (grad * gout).to(gout.dtype), None, None, None, None, None, None, None
+
+    return GaugeMisfit
+
+
+def gauge_misfit(w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every=100):
+    """Differentiable gauge misfit (torch.autograd) of a run from w0."""
+    return _gauge_misfit_function().apply(w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every)
 
 
 def from_scenario(s, dtype=None, K: Optional[int] = None, **kw) -> Solver:

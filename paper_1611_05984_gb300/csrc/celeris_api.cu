@@ -1497,3 +1497,201 @@ void cel_ensemble_destroy(cel_ensemble *e)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------- discrete adjoint
+//
+// Gradient of the gauge misfit L = 1/2 sum_{n=1..N} sum_g (eta_g^n - obs_g^n)^2
+// with respect to w at the start, by the reverse of every step in
+// celeris_adjoint.cu.  The forward run keeps a checkpoint every C steps;
+// the reverse sweep goes through the segments from the last, recomputing
+// each segment's states from its checkpoint (the resume is bit-exact) and
+// then reversing its steps.
+
+namespace {
+
+struct AdjLayout {
+    size_t ckpt_bytes, cells_bytes;
+    size_t ckpt, seg, lam, G, rec, gij, total;
+    int nseg;
+};
+
+AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng)
+{
+    AdjLayout L;
+    L.ckpt_bytes = align256(ckpt_total(s));
+    L.cells_bytes = align256((size_t)s->grid.nx * s->grid.ny * s->es);
+    L.nseg = (N + C - 1) / C;
+    size_t cur = 0;
+    auto take = [&](size_t b) {
+        size_t o = cur;
+        cur += align256(b);
+        return o;
+    };
+    L.ckpt = take(L.ckpt_bytes * (size_t)(L.nseg + 1));   // + the final state
+    L.seg = take(L.cells_bytes * 3 * (size_t)(C + 1));
+    L.lam = take(L.cells_bytes * 3);
+    L.G = take(L.cells_bytes * 9);
+    L.rec = take((size_t)N * ng * s->es);
+    L.gij = take((size_t)ng * 2 * sizeof(int32_t));
+    L.total = cur;
+    return L;
+}
+
+// Coefficients of R^n, R^{n-1}, R^{n-2} in the update of step n of a fresh
+// history, predictor only (Eq. 15; Euler for the first two steps).
+void adj_coefs(int64_t n, double dt, double c[3])
+{
+    if (n < 2) {
+        c[0] = dt;
+        c[1] = c[2] = 0.0;
+    } else {
+        c[0] = 23.0 * dt / 12.0;
+        c[1] = -16.0 * dt / 12.0;
+        c[2] = 5.0 * dt / 12.0;
+    }
+}
+
+template <typename real>
+cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int ng, const real *obs, unsigned char *scr,
+                     const AdjLayout &L, real *eta_out, real *grad, double *loss)
+{
+    cudaStream_t st = s->stream;
+    const size_t cells = (size_t)s->grid.nx * s->grid.ny;
+    int32_t *gij = reinterpret_cast<int32_t *>(scr + L.gij);
+    real *rec = reinterpret_cast<real *>(scr + L.rec);
+    CEL_CUDA(s, cudaMemcpyAsync(gij, gij_host, sizeof(int32_t) * 2 * ng, cudaMemcpyHostToDevice, st), "adjoint gauges");
+    auto ckpt = [&](int k) { return scr + L.ckpt + L.ckpt_bytes * (size_t)k; };
+    auto segf = [&](int k, int v) { return reinterpret_cast<real *>(scr + L.seg + L.cells_bytes * (3 * (size_t)k + v)); };
+    auto lam = [&](int v) { return reinterpret_cast<real *>(scr + L.lam + L.cells_bytes * v); };
+    auto Gb = [&](int slot, int v) { return reinterpret_cast<real *>(scr + L.G + L.cells_bytes * (3 * slot + v)); };
+    const int64_t step0 = s->step;
+    cel_status stt;
+    // forward, with checkpoints and the gauge records
+    for (int n = 0; n < N; n++) {
+        if (n % C == 0 && (stt = cel_save_checkpoint(s, ckpt(n / C), L.ckpt_bytes)) != CEL_OK) return stt;
+        if ((stt = step_t<real>(s, 1)) != CEL_OK) return stt;
+        CEL_CUDA(s, launch_gauges<real>(s->geo, s->phy, s->at<real>(s->lay.w[s->cur]), gij, ng, rec + (size_t)n * ng, st),
+                 "adjoint gauges");
+    }
+    if ((stt = cel_save_checkpoint(s, ckpt(L.nseg), L.ckpt_bytes)) != CEL_OK) return stt;
+    {
+        std::vector<real> r((size_t)N * ng), o((size_t)N * ng);
+        CEL_CUDA(s, cudaMemcpyAsync(r.data(), rec, sizeof(real) * r.size(), cudaMemcpyDeviceToHost, st), "adjoint loss");
+        CEL_CUDA(s, cudaMemcpyAsync(o.data(), obs, sizeof(real) * o.size(), cudaMemcpyDeviceToHost, st), "adjoint loss");
+        CEL_CUDA(s, cudaStreamSynchronize(st), "adjoint loss");
+        double acc = 0.0;
+        for (size_t k = 0; k < r.size(); k++) acc += 0.5 * ((double)r[k] - (double)o[k]) * ((double)r[k] - (double)o[k]);
+        if (loss) *loss = acc;
+    }
+    // reverse
+    CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 3, st), "adjoint");
+    CEL_CUDA(s, cudaMemsetAsync(scr + L.G, 0, L.cells_bytes * 9, st), "adjoint");
+    AdjArgs<real> a;
+    memset(&a, 0, sizeof(a));
+    a.geo = s->geo;
+    a.phy = s->phy;
+    a.c = make_coef<real>(s->geo, s->phy, s->bnd);
+    a.Bc = s->at<real>(s->lay.Bc);
+    a.ghost = s->at<real>(s->lay.ghost);
+    a.lw = lam(0);
+    a.lP = lam(1);
+    a.lQ = lam(2);
+    CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(N - 1) * ng, obs + (size_t)(N - 1) * ng, st),
+             "adjoint misfit");
+    for (int sg = L.nseg - 1; sg >= 0; sg--) {
+        const int n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
+        if ((stt = cel_load_checkpoint(s, ckpt(sg), L.ckpt_bytes)) != CEL_OK) return stt;
+        for (int k = 0; k <= n1 - n0; k++) {
+            CEL_CUDA(s, launch_get_state<real>(s->geo, s->at<real>(s->lay.w[s->cur]), s->at<real>(s->lay.P[s->pcur]),
+                                               s->at<real>(s->lay.Qc[s->pcur]), segf(k, 0), segf(k, 1), segf(k, 2), st),
+                     "adjoint states");
+            if (k < n1 - n0 && (stt = step_t<real>(s, 1)) != CEL_OK) return stt;
+        }
+        for (int n = n1 - 1; n >= n0; n--) {
+            const int k = n - n0;
+            if (a.c.sine)
+                CEL_CUDA(s, launch_ghost_table<real>(s->geo, s->phy, s->bnd, s->at<real>(s->lay.dr),
+                                                     s->at<double>(s->lay.ktab), (double)(step0 + n) * s->params.dt,
+                                                     (double)(step0 + n + 1) * s->params.dt,
+                                                     s->at<real>(s->lay.ghost), a.c.npos, st),
+                         "adjoint ghosts");
+            double c[3];
+            adj_coefs(n, s->params.dt, c);
+            a.c0 = real(c[0]);
+            a.c1 = real(c[1]);
+            a.c2 = real(c[2]);
+            a.w = segf(k, 0);
+            a.P = segf(k, 1);
+            a.Q = segf(k, 2);
+            a.w_next = segf(k + 1, 0);
+            for (int v = 0; v < 3; v++) {
+                a.G0[v] = Gb(n % 3, v);
+                a.G1[v] = Gb((n + 2) % 3, v);
+                a.G2[v] = Gb((n + 1) % 3, v);
+            }
+            CEL_CUDA(s, launch_adjoint_step<real>(a, st), "adjoint step");
+            if (n >= 1)
+                CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(n - 1) * ng,
+                                                        obs + (size_t)(n - 1) * ng, st),
+                         "adjoint misfit");
+            CEL_CUDA(s, cudaMemsetAsync(Gb(n % 3, 0), 0, L.cells_bytes * 3, st), "adjoint");
+        }
+    }
+    CEL_CUDA(s, cudaMemcpyAsync(grad, lam(0), sizeof(real) * cells, cudaMemcpyDeviceToDevice, st), "adjoint gradient");
+    if (eta_out)
+        CEL_CUDA(s, cudaMemcpyAsync(eta_out, rec, sizeof(real) * (size_t)N * ng, cudaMemcpyDeviceToDevice, st),
+                 "adjoint records");
+    return cel_load_checkpoint(s, ckpt(L.nseg), L.ckpt_bytes);   // leave the solver after step N
+}
+
+cel_status adjoint_check(const cel_solver *s, int N, int C, int ng, std::string &why)
+{
+    if (s->params.model != CEL_NLSW || s->params.corrector_iters != 0) {
+        why = "the adjoint covers the NLSW model with the predictor only (corrector_iters = 0)";
+        return CEL_ERR_NOT_IMPLEMENTED;
+    }
+    if (N < 1 || C < 1 || ng < 1) {
+        why = "nsteps, ckpt_every and the gauge count must be positive";
+        return CEL_ERR_INVALID_ARG;
+    }
+    return CEL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cel_status cel_adjoint_bytes(const cel_solver *s, int32_t nsteps, int32_t ckpt_every, int32_t ngauges, size_t *bytes)
+{
+    if (!s || !bytes) return CEL_ERR_INVALID_ARG;
+    std::string why;
+    cel_status st = adjoint_check(s, nsteps, ckpt_every, ngauges, why);
+    if (st != CEL_OK) return st;
+    *bytes = adj_layout(s, nsteps, ckpt_every, ngauges).total;
+    return CEL_OK;
+}
+
+cel_status cel_adjoint_gauge_misfit(cel_solver *s, int32_t nsteps, int32_t ckpt_every, const int32_t *gij_host,
+                                    int32_t ngauges, const void *obs_dev, void *scratch_dev, size_t scratch_bytes,
+                                    void *eta_dev, void *grad_w_dev, double *loss)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    std::string why;
+    cel_status st = adjoint_check(s, nsteps, ckpt_every, ngauges, why);
+    if (st != CEL_OK) return fail(s, st, why);
+    if (s->nh != 0) return fail(s, CEL_ERR_INVALID_ARG, "set the initial state first (the history must be fresh)");
+    if (!gij_host || !obs_dev || !scratch_dev || !grad_w_dev || ((uintptr_t)scratch_dev & 255) != 0)
+        return fail(s, CEL_ERR_INVALID_ARG, "NULL argument or unaligned scratch");
+    for (int k = 0; k < ngauges; k++)
+        if (gij_host[2 * k] < 0 || gij_host[2 * k] >= s->grid.nx || gij_host[2 * k + 1] < 0 ||
+            gij_host[2 * k + 1] >= s->grid.ny)
+            return fail(s, CEL_ERR_INVALID_ARG, "gauge outside the grid");
+    AdjLayout L = adj_layout(s, nsteps, ckpt_every, ngauges);
+    if (scratch_bytes < L.total) return fail(s, CEL_ERR_WORKSPACE_TOO_SMALL, "adjoint scratch too small");
+    return s->es == 4 ? adjoint_t<float>(s, nsteps, ckpt_every, gij_host, ngauges, (const float *)obs_dev,
+                                         (unsigned char *)scratch_dev, L, (float *)eta_dev, (float *)grad_w_dev, loss)
+                      : adjoint_t<double>(s, nsteps, ckpt_every, gij_host, ngauges, (const double *)obs_dev,
+                                          (unsigned char *)scratch_dev, L, (double *)eta_dev, (double *)grad_w_dev, loss);
+}
+
+}  // extern "C"

@@ -189,6 +189,29 @@ struct RenderArgs {
 template <typename real>
 cudaError_t launch_render(const RenderArgs<real> &a, cudaStream_t st);
 
+// Discrete adjoint of one step (celeris_adjoint.cu): NLSW model, predictor
+// only.  State arrays are dense [ny][nx]: w, P, Q the state before the step,
+// w_next w after it; lw, lP, lQ the adjoint (in: of the state after the step,
+// out: of the state before it); G0, G1, G2 the adjoint of the right sides
+// (E, F, G) of this step and the two before it.
+template <typename real>
+struct AdjArgs {
+    Geo geo;
+    Phys phy;
+    Coef<real> c;
+    const real *Bc, *ghost;
+    const real *w, *P, *Q, *w_next;
+    real *lw, *lP, *lQ;
+    real *G0[3], *G1[3], *G2[3];
+    real c0, c1, c2;       // coefficients of R^n, R^{n-1}, R^{n-2} in this step's update
+};
+
+template <typename real>
+cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st);
+template <typename real>
+cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, int ng, const real *rec,
+                                  const real *obs, cudaStream_t st);
+
 // Launchers (celeris_kernels.cu).  All return cudaGetLastError().
 template <typename real>
 cudaError_t launch_corners(const Geo &g, const real *z, real *Bc, cudaStream_t st);

@@ -20,6 +20,7 @@
 //              2-per-segment interface system is solved by parallel cyclic
 //              reduction), then P^n + increment, sponge and dry-cell epilogue.
 #include "celeris_internal.cuh"
+#include "celeris_physics.cuh"
 
 #include <math.h>
 
@@ -30,106 +31,6 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
-
-__device__ __forceinline__ int mirror_index(int i, int n)
-{
-    return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i);
-}
-
-// Eq. 14: u = k(h) P with k(h) = sqrt(2) h / sqrt(h^4 + max(h^4, eps)).
-template <typename real>
-__device__ __forceinline__ real desing(real h, real eps)
-{
-    real h2 = h * h;
-    real h4 = h2 * h2;
-    return real(1.4142135623730951) * h * rsqrt(h4 + fmax(h4, eps));
-}
-
-// KP07 step 1: generalized minmod of the three one-sided / central slopes.
-template <typename real>
-__device__ __forceinline__ real minmod3(real th, real qm, real q0, real qp)
-{
-    // the three slopes share a sign iff the two one-sided ones do (the
-    // central one lies between them); then the one of least magnitude
-    real a = th * (q0 - qm), b = real(0.5) * (qp - qm), c = th * (qp - q0);
-    real lo = fmin(a, fmin(b, c)), hi = fmax(a, fmax(b, c));
-    return lo > real(0) ? lo : (hi < real(0) ? hi : real(0));
-}
-
-// KP07 steps 1-2 for one cell along one direction: face values of (w, P, Q)
-// at the low and high faces, then the positivity fix of w.
-template <typename real>
-__device__ __forceinline__ void recon(real th, const real wq[3], const real Pq[3],
-                                      const real Qq[3], real Blo, real Bhi, real lo[3],
-                                      real hi[3])
-{
-    real sw = minmod3(th, wq[0], wq[1], wq[2]);
-    real sP = minmod3(th, Pq[0], Pq[1], Pq[2]);
-    real sQ = minmod3(th, Qq[0], Qq[1], Qq[2]);
-    lo[0] = wq[1] - real(0.5) * sw;
-    hi[0] = wq[1] + real(0.5) * sw;
-    lo[1] = Pq[1] - real(0.5) * sP;
-    hi[1] = Pq[1] + real(0.5) * sP;
-    lo[2] = Qq[1] - real(0.5) * sQ;
-    hi[2] = Qq[1] + real(0.5) * sQ;
-    if (hi[0] < Bhi) {
-        hi[0] = Bhi;
-        lo[0] = real(2) * wq[1] - Bhi;
-    } else if (lo[0] < Blo) {
-        lo[0] = Blo;
-        hi[0] = real(2) * wq[1] - Blo;
-    }
-}
-
-// KP07 step 3: central-upwind flux.  States are (w, normal, tangential
-// discharge); H = (mass, normal momentum, tangential momentum).
-template <typename real>
-__device__ __forceinline__ void cu_flux(real g, real eps, real wL, real nL, real tL, real wR,
-                                        real nR, real tR, real Bf, real H[3])
-{
-    real hL = fmax(wL - Bf, real(0)), hR = fmax(wR - Bf, real(0));
-    real kL = desing(hL, eps), kR = desing(hR, eps);
-    real uL = kL * nL, vL = kL * tL, uR = kR * nR, vR = kR * tR;
-    real qnL = hL * uL, qtL = hL * vL, qnR = hR * uR, qtR = hR * vR;
-    real sL = sqrt(g * hL), sR = sqrt(g * hR);
-    real ap = fmax(fmax(uL + sL, uR + sR), real(0));
-    real am = fmin(fmin(uL - sL, uR - sR), real(0));
-    real den = ap - am;
-    if (!(den > real(0))) {
-        H[0] = H[1] = H[2] = real(0);
-        return;
-    }
-    real inv = real(1) / den, apam = ap * am;
-    real FL1 = qnL * uL + real(0.5) * g * hL * hL, FR1 = qnR * uR + real(0.5) * g * hR * hR;
-    H[0] = (ap * qnL - am * qnR + apam * (wR - wL)) * inv;
-    H[1] = (ap * FL1 - am * FR1 + apam * (qnR - qnL)) * inv;
-    H[2] = (ap * (qnL * vL) - am * (qnR * vR) + apam * (qtR - qtL)) * inv;
-}
-
-__device__ __forceinline__ float cbrt_r(float x) { return x > 0.f ? exp2f(__log2f(x) * (1.f / 3.f)) : 0.f; }
-__device__ __forceinline__ double cbrt_r(double x) { return cbrt(x); }
-__device__ __forceinline__ float cospi_r(float x) { return cospif(x); }
-__device__ __forceinline__ double cospi_r(double x) { return cospi(x); }
-
-// Eq. 30 with D the distance from the absorbing face to the cell centre and
-// L_s = width cells: a cell idx cells from the side (idx = i for the west) is
-// inside when idx < width, with (L_s - D)/L_s = (2 (width - idx) - 1)/(2 width).
-// The smallest gamma over the sponge sides.
-template <typename real>
-__device__ __forceinline__ real sponge_gamma(const Coef<real> &c, const Geo &g, int i, int j)
-{
-    real gm = real(1);
-    const int idx[4] = {i, g.nx - 1 - i, j, g.ny - 1 - j};
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        const int w = c.spw[s];
-        if (idx[s] < w) {
-            real r = real(2 * (w - idx[s]) - 1) / real(2 * w);
-            gm = fmin(gm, real(0.5) * (real(1) + cospi_r(r)));
-        }
-    }
-    return gm;
-}
 
 // ------------------------------------------------------------ static fields
 
