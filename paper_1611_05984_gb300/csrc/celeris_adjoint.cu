@@ -1,16 +1,22 @@
-// Discrete adjoint of the time step, for the nonlinear shallow-water model
-// (Sec. 3.2: the dispersive terms and the line solves off) with the AB3
-// predictor and the Euler start-up (Eq. 15, Sec. 2.3), and the gradient of a
-// gauge misfit.  The reverse of one step, given the adjoint lambda of the
-// state after it:
+// Discrete adjoint of the time step with the AB3 predictor and the Euler
+// start-up (Eq. 15-17, Sec. 2.3), for the Boussinesq model and the
+// nonlinear shallow-water model (Sec. 3.2), and the gradient of a gauge
+// misfit.  The reverse of one step, given the adjoint lambda of the state
+// after it:
 //   1. the masks of the update: the dry clamp w >= Bbar (Reading A-D1), the
 //      sponge (Eq. 30), the zero discharge of dry cells;
-//   2. the AB3 history: the right side R^n = (E, F, G) collects the
-//      adjoint weighted by its coefficient in steps n, n+1 and n+2;
-//   3. R^n's Jacobian transposed, applied to that adjoint: every face flux
-//      (KP07 reconstruction with the limiter and positivity branches of the
-//      forward state, then the central-upwind flux) and the per-cell bed
-//      slope and friction terms.
+//   2. the line solves (Eq. 21-23) transposed: the adjoint of the U* and V*
+//      increments solves the transposed tridiagonal system of every line
+//      (sub- and super-diagonals exchanged, boundary rows included);
+//   3. the AB3 history: the right sides R^n = (E, F, G) and the mixed terms
+//      F*^n, G*^n collect the adjoint weighted by their coefficients in steps
+//      n, n+1 and n+2;
+//   4. R^n's and F*^n's Jacobians transposed: every face flux (KP07
+//      reconstruction with the limiter and positivity branches of the
+//      forward state, then the central-upwind flux), the bed slope and
+//      friction, the dispersive eta terms of Eq. 10-11 and F*, G* of
+//      Eq. 12-13 (linear in the neighbours, ghosts mapped back to the cells
+//      they mirror).
 // The face and cell Jacobians are exact: the forward device functions are
 // evaluated on dual numbers, one input direction at a time, so every branch
 // follows the forward state.  Adjoints reach a cell through the faces around
@@ -110,6 +116,33 @@ __device__ __forceinline__ Src<real> source(const AdjArgs<real> &A, int i, int j
     return s;
 }
 
+// Any cell of the one-cell ring around the grid, or two cells out along an
+// axis, as the stencil fills it: x-side ghosts over interior rows, then
+// y-side ghosts over every column, so a corner ghost is the y-mirror of an
+// x-ghost (Reading A-B5).
+template <typename real>
+__device__ __forceinline__ Src<real> source2d(const AdjArgs<real> &A, int i, int j)
+{
+    const Geo &G = A.geo;
+    if (j >= 0 && j < G.ny) return source(A, i, j, 0);
+    const int side = j < 0 ? 2 : 3, layer = j < 0 ? -1 - j : j - G.ny;
+    const int sj = j < 0 ? -1 - j : 2 * G.ny - 1 - j;
+    Src<real> s;
+    if ((A.c.sine >> side) & 1) {
+        const real *tb = A.ghost + ghost_index(0, side, layer, 0, i + 2, A.c.npos);
+        s.v[0] = tb[0];
+        s.v[1] = tb[A.c.npos];
+        s.v[2] = tb[2 * A.c.npos];
+        s.idx = -1;
+        s.sgn[0] = s.sgn[1] = s.sgn[2] = real(1);
+        return s;
+    }
+    s = source(A, i, sj, 0);   // the cell of the mirrored row (an x-ghost if i is outside)
+    s.v[2] = -s.v[2];
+    s.sgn[2] = -s.sgn[2];
+    return s;
+}
+
 // Flux through x-face f (dir 0: between cells f-1 and f of row `line`) or
 // y-face f (dir 1: between rows f-1 and f of column `line`) from the 4 cells
 // around it, in the forward's order of operations.
@@ -128,9 +161,10 @@ __device__ __forceinline__ void face_flux(const Dual<T> w[4], const Dual<T> P[4]
         cu_flux(Dual<T>(g), Dual<T>(eps), hiL[0], hiL[2], hiL[1], loR[0], loR[2], loR[1], Dual<T>(Bf), H);
 }
 
-// Step 1 and 2 of the reverse for one cell: the masks, then the history.
+// Step 1 of the reverse for one cell: the masks; the state's own path
+// (w^{n+1} = w^n + ...) passes the masked adjoint on unchanged.
 template <typename real>
-__global__ void k_adj_update(AdjArgs<real> A)
+__global__ void k_adj_mask(AdjArgs<real> A)
 {
     const Geo &G = A.geo;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -146,19 +180,108 @@ __global__ void k_adj_update(AdjArgs<real> A)
     const real w1 = spw ? ws + (wn - ws) / gam : wn;   // before the sponge
     const real tol = (sizeof(real) == 8 ? real(1e-12) : real(1e-6)) * fmax(real(1), fabs(Bb));
     const bool clamped = w1 - Bb <= tol;
-    const real mw = clamped ? real(0) : A.lw[k] * (spw ? gam : real(1));
-    const real mP = dry ? real(0) : A.lP[k] * gam;
-    const real mQ = dry ? real(0) : A.lQ[k] * gam;
-    A.lw[k] = mw;
-    A.lP[k] = mP;
-    A.lQ[k] = mQ;
-    const real m[3] = {mw, mP, mQ};
+    A.lw[k] = clamped ? real(0) : A.lw[k] * (spw ? gam : real(1));
+    A.lP[k] = dry ? real(0) : A.lP[k] * gam;
+    A.lQ[k] = dry ? real(0) : A.lQ[k] * gam;
+}
+
+// Step 3: the history.  The increments of w, U* and V* weigh R^n, R^{n-1},
+// R^{n-2} by c0, c1, c2 and (U*, V*) the mixed terms F*, G* by e0, e1, e2.
+template <typename real>
+__global__ void k_adj_hist(AdjArgs<real> A)
+{
+    const Geo &G = A.geo;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const int k = j * G.nx + i;
+    const real m[5] = {A.lw[k], A.ldU[k], A.ldV[k], A.ldU[k], A.ldV[k]};
 #pragma unroll
     for (int v = 0; v < 3; v++) {
         A.G0[v][k] += A.c0 * m[v];
         A.G1[v][k] += A.c1 * m[v];
         A.G2[v][k] += A.c2 * m[v];
     }
+    if (A.bsnq) {
+#pragma unroll
+        for (int v = 3; v < 5; v++) {
+            A.G0[v][k] += A.e0 * m[v];
+            A.G1[v][k] += A.e1 * m[v];
+            A.G2[v][k] += A.e2 * m[v];
+        }
+    }
+}
+
+// Step 2: the transposed line solves, one thread per line (Thomas, in the
+// scratch array).  The forward solves T x = r with the Eq. 23 rows
+// a_k x_{k-1} + b_k x_k + c_k x_{k+1} and their boundary rows (Reading
+// A-B2); here T^T y = mu, whose row k is c_{k-1} y_{k-1} + b_k y_k +
+// a_{k+1} y_{k+1}.
+template <typename real>
+__global__ void k_adj_lines_t(AdjArgs<real> A, int dir)
+{
+    const Geo &G = A.geo;
+    const int n = dir == 0 ? G.nx : G.ny, nl = dir == 0 ? G.ny : G.nx;
+    const int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nl) return;
+    auto at = [&](int k) { return dir == 0 ? line * G.nx + k : k * G.nx + line; };
+    auto dcell = [&](int k) {
+        const int i = dir == 0 ? k : line, j = dir == 0 ? line : k;
+        return fmax(A.c.ws - bbar_at(A.Bc, G, i, j), real(0));
+    };
+    const double h = dir == 0 ? G.dx : G.dy;   // the forward's constants, rounded once
+    const real rh2 = real(1.0 / (h * h)), hrh = real(0.5 / h), srh = real(1.0 / (6.0 * h));
+    const int lo_side = dir == 0 ? 0 : 2, hi_side = dir == 0 ? 1 : 3;
+    const bool lo_sine = (A.c.sine >> lo_side) & 1, hi_sine = (A.c.sine >> hi_side) & 1;
+    const real *mu = dir == 0 ? A.lP : A.lQ;
+    real *y = dir == 0 ? A.ldU : A.ldV;
+    real *cp = A.tri;   // c' of the forward sweep, then y
+    // coefficients of row k of T (Eq. 23) with the ends mirrored
+    auto row = [&](int k, real &a, real &b, real &c) {
+        const real dk = dcell(k), dm = dcell(k > 0 ? k - 1 : 0), dp = dcell(k + 1 < n ? k + 1 : n - 1);
+        const real dda = (dp - dm) * hrh, r = A.c.B3 * dk * dk * rh2, s = dk * dda * srh;
+        a = s - r;
+        b = real(1) + real(2) * r;
+        c = -s - r;
+        if (k == 0) {
+            if (!lo_sine) b -= a;
+            a = real(0);
+        }
+        if (k == n - 1) {
+            if (!hi_sine) b -= c;
+            c = real(0);
+        }
+    };
+    // T^T: sub_k = c_{k-1}, diag_k = b_k, sup_k = a_{k+1}
+    real a0, b0, c0v, an, bn, cn;
+    row(0, a0, b0, c0v);
+    real sub = real(0), diag = b0, sup = real(0);
+    if (n > 1) {
+        row(1, an, bn, cn);
+        sup = an;
+    }
+    real cprev = sup / diag, dprev = mu[at(0)] / diag;
+    cp[at(0)] = cprev;
+    y[at(0)] = dprev;
+    real ck_prev = c0v;   // c_{k-1} of T
+    for (int k = 1; k < n; k++) {
+        real ak, bk, ck;
+        row(k, ak, bk, ck);
+        sub = ck_prev;
+        diag = bk;
+        sup = real(0);
+        if (k + 1 < n) {
+            real a1, b1, c1;
+            row(k + 1, a1, b1, c1);
+            sup = a1;
+        }
+        const real den = diag - sub * cprev;
+        cprev = sup / den;
+        dprev = (mu[at(k)] - sub * dprev) / den;
+        cp[at(k)] = cprev;
+        y[at(k)] = dprev;
+        ck_prev = ck;
+    }
+    for (int k = n - 2; k >= 0; k--) y[at(k)] = y[at(k)] - cp[at(k)] * y[at(k + 1)];
 }
 
 // Bed slope and friction (Eq. 9-10, 31-32): per cell, no neighbours.
@@ -249,6 +372,70 @@ __global__ void k_adj_faces(AdjArgs<real> A, int dir)
     }
 }
 
+// Eq. 10-13 transposed: the dispersive eta terms of F and G and the mixed
+// terms F*(Q), G*(P) are linear in the neighbouring eta, Q and P, with
+// coefficients from the still-water depth; each cell adds its adjoints to
+// the cells (or the cells their ghosts mirror) its stencil reads.
+template <typename real>
+__global__ void k_adj_disp(AdjArgs<real> A)
+{
+    const Geo &G = A.geo;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const int k = j * G.nx + i;
+    const real lF = A.G0[1][k], lG = A.G0[2][k], lFs = A.G0[3][k], lGs = A.G0[4][k];
+    if (lF == real(0) && lG == real(0) && lFs == real(0) && lGs == real(0)) return;
+    const Coef<real> &C = A.c;
+    auto dcell = [&](int ii, int jj) { return fmax(C.ws - bbar_at(A.Bc, G, ii, jj), real(0)); };
+    const real dd = dcell(i, j);
+    const real ddx = (dcell(i + 1, j) - dcell(i - 1, j)) * C.hrdx, ddy = (dcell(i, j + 1) - dcell(i, j - 1)) * C.hrdy;
+    const real K3 = C.Bd * C.g * dd * dd * dd, K2 = C.Bd * C.g * dd * dd;
+    // d F / d eta_p and d G / d eta_p over the 13 points, through exx, eyy,
+    // exy, exxx, eyyy, exyy, exxy
+    const real fxx = K2 * ddx * real(2) * lF + K2 * ddy * lG;          // weight of exx
+    const real fyy = K2 * ddx * lF + K2 * ddy * real(2) * lG;          // eyy
+    const real fxy = K2 * ddy * lF + K2 * ddx * lG;                    // exy
+    const real fxxx = K3 * lF, fyyy = K3 * lG, fxyy = K3 * lF, fxxy = K3 * lG;
+    const real ax = fxx * C.rdx2, ay = fyy * C.rdy2, axy = fxy * C.rdxdy4;
+    const real a3x = fxxx * C.rdx3h, a3y = fyyy * C.rdy3h, bxyy = fxyy * C.rdxdy2h, bxxy = fxxy * C.rdx2dyh;
+    struct Pt { int di, dj; real wgt; };
+    const Pt pts[13] = {
+        {0, 0, -real(2) * ax - real(2) * ay},
+        {1, 0, ax - real(2) * a3x - real(2) * bxyy},
+        {-1, 0, ax + real(2) * a3x + real(2) * bxyy},
+        {0, 1, ay - real(2) * a3y - real(2) * bxxy},
+        {0, -1, ay + real(2) * a3y + real(2) * bxxy},
+        {2, 0, a3x},
+        {-2, 0, -a3x},
+        {0, 2, a3y},
+        {0, -2, -a3y},
+        {1, 1, axy + bxyy + bxxy},
+        {-1, 1, -axy - bxyy + bxxy},
+        {1, -1, -axy + bxyy - bxxy},
+        {-1, -1, axy - bxyy - bxxy}};
+#pragma unroll
+    for (int q = 0; q < 13; q++) {
+        if (pts[q].wgt == real(0)) continue;
+        const Src<real> s = source2d(A, i + pts[q].di, j + pts[q].dj);
+        if (s.idx >= 0) atomicAdd(A.lw + s.idx, pts[q].wgt);
+    }
+    // F* = d ddx Qy / 6 + d ddy Qx / 6 + B3 d^2 Qxy; G* the same in P with x, y exchanged
+    const real qx = dd * ddy * C.sixth * C.hrdx, qy = dd * ddx * C.sixth * C.hrdy, qxy = C.B3 * dd * dd * C.rdxdy4;
+    const real px = dd * ddy * C.sixth * C.hrdx, py = dd * ddx * C.sixth * C.hrdy;
+    // Gs = dd ddy Px / 6 + dd ddx Py / 6 + B3 dd^2 Pxy, Fs = dd ddx Qy / 6 + dd ddy Qx / 6 + B3 dd^2 Qxy
+    const Pt mq[8] = {{1, 0, qx * lFs}, {-1, 0, -qx * lFs}, {0, 1, qy * lFs}, {0, -1, -qy * lFs},
+                      {1, 1, qxy * lFs}, {1, -1, -qxy * lFs}, {-1, 1, -qxy * lFs}, {-1, -1, qxy * lFs}};
+    const Pt mp[8] = {{1, 0, px * lGs}, {-1, 0, -px * lGs}, {0, 1, py * lGs}, {0, -1, -py * lGs},
+                      {1, 1, qxy * lGs}, {1, -1, -qxy * lGs}, {-1, 1, -qxy * lGs}, {-1, -1, qxy * lGs}};
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const Src<real> s = source2d(A, i + mq[q].di, j + mq[q].dj);
+        if (s.idx >= 0 && mq[q].wgt != real(0)) atomicAdd(A.lQ + s.idx, s.sgn[2] * mq[q].wgt);
+        const Src<real> t = source2d(A, i + mp[q].di, j + mp[q].dj);
+        if (t.idx >= 0 && mp[q].wgt != real(0)) atomicAdd(A.lP + t.idx, t.sgn[1] * mp[q].wgt);
+    }
+}
+
 // The misfit at the gauges after step n enters the adjoint of w^n.
 template <typename real>
 __global__ void k_adj_misfit(AdjArgs<real> A, const int32_t *gij, int ng, const real *rec, const real *obs)
@@ -264,8 +451,17 @@ template <typename real>
 cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st)
 {
     dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
-    k_adj_update<real><<<g, b, 0, st>>>(a);
+    k_adj_mask<real><<<g, b, 0, st>>>(a);
+    if (a.bsnq) {
+        k_adj_lines_t<real><<<(a.geo.ny + 127) / 128, 128, 0, st>>>(a, 0);
+        k_adj_lines_t<real><<<(a.geo.nx + 127) / 128, 128, 0, st>>>(a, 1);
+    } else {
+        cudaMemcpyAsync(a.ldU, a.lP, sizeof(real) * (size_t)a.geo.nx * a.geo.ny, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(a.ldV, a.lQ, sizeof(real) * (size_t)a.geo.nx * a.geo.ny, cudaMemcpyDeviceToDevice, st);
+    }
+    k_adj_hist<real><<<g, b, 0, st>>>(a);
     k_adj_cells<real><<<g, b, 0, st>>>(a);
+    if (a.bsnq) k_adj_disp<real><<<g, b, 0, st>>>(a);
     dim3 bf(64, 4);
     k_adj_faces<real><<<dim3((a.geo.nx + 1 + 63) / 64, (a.geo.ny + 3) / 4), bf, 0, st>>>(a, 0);
     k_adj_faces<real><<<dim3((a.geo.ny + 1 + 63) / 64, (a.geo.nx + 3) / 4), bf, 0, st>>>(a, 1);

@@ -1529,25 +1529,32 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng)
     };
     L.ckpt = take(L.ckpt_bytes * (size_t)(L.nseg + 1));   // + the final state
     L.seg = take(L.cells_bytes * 3 * (size_t)(C + 1));
-    L.lam = take(L.cells_bytes * 3);
-    L.G = take(L.cells_bytes * 9);
+    L.lam = take(L.cells_bytes * 6);   // lambda of w, P, Q; of the U*, V* increments; solve scratch
+    L.G = take(L.cells_bytes * 15);    // 3 steps x (E, F, G, F*, G*)
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
     L.total = cur;
     return L;
 }
 
-// Coefficients of R^n, R^{n-1}, R^{n-2} in the update of step n of a fresh
-// history, predictor only (Eq. 15; Euler for the first two steps).
-void adj_coefs(int64_t n, double dt, double c[3])
+// Weights of R^n, R^{n-1}, R^{n-2} (c) and of F*^n, F*^{n-1}, F*^{n-2} (e)
+// in the update of step n of a fresh history, predictor only (Eq. 15-17;
+// Euler for the first two steps, the second adding F*^1 - F*^0).
+void adj_coefs(int64_t n, double dt, double c[3], double e[3])
 {
     if (n < 2) {
         c[0] = dt;
         c[1] = c[2] = 0.0;
+        e[0] = n == 1 ? 1.0 : 0.0;
+        e[1] = n == 1 ? -1.0 : 0.0;
+        e[2] = 0.0;
     } else {
         c[0] = 23.0 * dt / 12.0;
         c[1] = -16.0 * dt / 12.0;
         c[2] = 5.0 * dt / 12.0;
+        e[0] = 2.0;
+        e[1] = -3.0;
+        e[2] = 1.0;
     }
 }
 
@@ -1563,7 +1570,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     auto ckpt = [&](int k) { return scr + L.ckpt + L.ckpt_bytes * (size_t)k; };
     auto segf = [&](int k, int v) { return reinterpret_cast<real *>(scr + L.seg + L.cells_bytes * (3 * (size_t)k + v)); };
     auto lam = [&](int v) { return reinterpret_cast<real *>(scr + L.lam + L.cells_bytes * v); };
-    auto Gb = [&](int slot, int v) { return reinterpret_cast<real *>(scr + L.G + L.cells_bytes * (3 * slot + v)); };
+    auto Gb = [&](int slot, int v) { return reinterpret_cast<real *>(scr + L.G + L.cells_bytes * (5 * slot + v)); };
     const int64_t step0 = s->step;
     cel_status stt;
     // forward, with checkpoints and the gauge records
@@ -1584,8 +1591,8 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         if (loss) *loss = acc;
     }
     // reverse
-    CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 3, st), "adjoint");
-    CEL_CUDA(s, cudaMemsetAsync(scr + L.G, 0, L.cells_bytes * 9, st), "adjoint");
+    CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 6, st), "adjoint");
+    CEL_CUDA(s, cudaMemsetAsync(scr + L.G, 0, L.cells_bytes * 15, st), "adjoint");
     AdjArgs<real> a;
     memset(&a, 0, sizeof(a));
     a.geo = s->geo;
@@ -1596,6 +1603,10 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     a.lw = lam(0);
     a.lP = lam(1);
     a.lQ = lam(2);
+    a.ldU = lam(3);
+    a.ldV = lam(4);
+    a.tri = lam(5);
+    a.bsnq = s->params.model == CEL_BSNQ;
     CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(N - 1) * ng, obs + (size_t)(N - 1) * ng, st),
              "adjoint misfit");
     for (int sg = L.nseg - 1; sg >= 0; sg--) {
@@ -1615,16 +1626,19 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                                                      (double)(step0 + n + 1) * s->params.dt,
                                                      s->at<real>(s->lay.ghost), a.c.npos, st),
                          "adjoint ghosts");
-            double c[3];
-            adj_coefs(n, s->params.dt, c);
+            double c[3], e[3];
+            adj_coefs(n, s->params.dt, c, e);
             a.c0 = real(c[0]);
             a.c1 = real(c[1]);
             a.c2 = real(c[2]);
+            a.e0 = real(e[0]);
+            a.e1 = real(e[1]);
+            a.e2 = real(e[2]);
             a.w = segf(k, 0);
             a.P = segf(k, 1);
             a.Q = segf(k, 2);
             a.w_next = segf(k + 1, 0);
-            for (int v = 0; v < 3; v++) {
+            for (int v = 0; v < 5; v++) {
                 a.G0[v] = Gb(n % 3, v);
                 a.G1[v] = Gb((n + 2) % 3, v);
                 a.G2[v] = Gb((n + 1) % 3, v);
@@ -1634,7 +1648,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(n - 1) * ng,
                                                         obs + (size_t)(n - 1) * ng, st),
                          "adjoint misfit");
-            CEL_CUDA(s, cudaMemsetAsync(Gb(n % 3, 0), 0, L.cells_bytes * 3, st), "adjoint");
+            CEL_CUDA(s, cudaMemsetAsync(Gb(n % 3, 0), 0, L.cells_bytes * 5, st), "adjoint");
         }
     }
     CEL_CUDA(s, cudaMemcpyAsync(grad, lam(0), sizeof(real) * cells, cudaMemcpyDeviceToDevice, st), "adjoint gradient");
@@ -1646,8 +1660,8 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
 
 cel_status adjoint_check(const cel_solver *s, int N, int C, int ng, std::string &why)
 {
-    if (s->params.model != CEL_NLSW || s->params.corrector_iters != 0) {
-        why = "the adjoint covers the NLSW model with the predictor only (corrector_iters = 0)";
+    if (s->params.corrector_iters != 0) {
+        why = "the adjoint covers the predictor only (corrector_iters = 0)";
         return CEL_ERR_NOT_IMPLEMENTED;
     }
     if (N < 1 || C < 1 || ng < 1) {

@@ -189,11 +189,13 @@ struct RenderArgs {
 template <typename real>
 cudaError_t launch_render(const RenderArgs<real> &a, cudaStream_t st);
 
-// Discrete adjoint of one step (celeris_adjoint.cu): NLSW model, predictor
-// only.  State arrays are dense [ny][nx]: w, P, Q the state before the step,
-// w_next w after it; lw, lP, lQ the adjoint (in: of the state after the step,
-// out: of the state before it); G0, G1, G2 the adjoint of the right sides
-// (E, F, G) of this step and the two before it.
+// Discrete adjoint of one step (celeris_adjoint.cu), predictor only.  State
+// arrays are dense [ny][nx]: w, P, Q the state before the step, w_next w
+// after it; lw, lP, lQ the adjoint (in: of the state after the step, out: of
+// the state before it); G0, G1, G2 the adjoint of this step's right sides
+// and of the two before it, per component E, F, G, F*, G*; ldU, ldV the
+// adjoint of the U* and V* increments (the line solves' right sides); tri a
+// [ny][nx] scratch for the transposed solves.
 template <typename real>
 struct AdjArgs {
     Geo geo;
@@ -202,8 +204,11 @@ struct AdjArgs {
     const real *Bc, *ghost;
     const real *w, *P, *Q, *w_next;
     real *lw, *lP, *lQ;
-    real *G0[3], *G1[3], *G2[3];
-    real c0, c1, c2;       // coefficients of R^n, R^{n-1}, R^{n-2} in this step's update
+    real *G0[5], *G1[5], *G2[5];
+    real *ldU, *ldV, *tri;
+    real c0, c1, c2;       // weights of R^n, R^{n-1}, R^{n-2} in this step's update
+    real e0, e1, e2;       // weights of F*^n, F*^{n-1}, F*^{n-2} (Boussinesq)
+    int bsnq;
 };
 
 template <typename real>
