@@ -209,11 +209,13 @@ cel_status cel_render(cel_solver *s, const cel_render_params *params, void *rgba
 /* Discrete adjoint: the gradient of the gauge misfit
  *   L = 1/2 sum_{n=1..N} sum_g (eta_g^n - obs_g^n)^2,
  * eta_g^n = w - w_s at gauge g after step n, with respect to w at the start,
- * by the exact reverse of every step (the KP07 flux with the limiter and
+ * by the exact reverse of every step: the KP07 flux with the limiter and
  * positivity branches taken in the forward run, the dry clamp and dry
- * masks, the sponge, friction, the AB3 history and the Euler start-up).
- * Covered: the NLSW model (Sec. 3.2) with corrector_iters = 0; other
- * settings give CEL_ERR_NOT_IMPLEMENTED.  The solver must hold a fresh
+ * masks, the sponge, friction, the dispersive and mixed terms (Eq. 10-13),
+ * the line solves transposed (Eq. 21-23), the AB3 predictor with its
+ * history and Euler start-up, and the AM4 corrector iterations (Eq. 15-20),
+ * for both models (Sec. 3.2).  The gradient is the derivative along the
+ * branches the forward run took (the step is piecewise smooth).  The solver must hold a fresh
  * history (cel_set_state just before); it runs N steps forward keeping a
  * checkpoint every ckpt_every steps, then the reverse sweep, recomputing one
  * segment of states at a time from its checkpoint; it ends holding the state

@@ -101,7 +101,7 @@ __device__ __forceinline__ Src<real> source(const AdjArgs<real> &A, int i, int j
     if (dir == 1 && j >= G.ny) { side = 3; layer = j - G.ny; sj = 2 * G.ny - 1 - j; }
     if (side >= 0 && ((A.c.sine >> side) & 1)) {
         const int pos = (dir == 0 ? j : i) + 2;
-        const real *tb = A.ghost + ghost_index(0, side, layer, 0, pos, A.c.npos);
+        const real *tb = A.ghost + ghost_index(A.tsel, side, layer, 0, pos, A.c.npos);
         s.v[0] = tb[0];
         s.v[1] = tb[A.c.npos];
         s.v[2] = tb[2 * A.c.npos];
@@ -129,7 +129,7 @@ __device__ __forceinline__ Src<real> source2d(const AdjArgs<real> &A, int i, int
     const int sj = j < 0 ? -1 - j : 2 * G.ny - 1 - j;
     Src<real> s;
     if ((A.c.sine >> side) & 1) {
-        const real *tb = A.ghost + ghost_index(0, side, layer, 0, i + 2, A.c.npos);
+        const real *tb = A.ghost + ghost_index(A.tsel, side, layer, 0, i + 2, A.c.npos);
         s.v[0] = tb[0];
         s.v[1] = tb[A.c.npos];
         s.v[2] = tb[2 * A.c.npos];
@@ -173,7 +173,7 @@ __global__ void k_adj_mask(AdjArgs<real> A)
     const real Bb = bbar_at(A.Bc, G, i, j);
     const real ws = A.c.ws;
     const real d = fmax(ws - Bb, real(0));
-    const real gam = sponge_gamma<real>(A.c, G, i, j);
+    const real gam = A.final_stage ? sponge_gamma<real>(A.c, G, i, j) : real(1);
     const real wn = A.w_next[k];
     const bool dry = wn - Bb <= real(0);
     const bool spw = gam < real(1) && d > real(0);
@@ -196,19 +196,25 @@ __global__ void k_adj_hist(AdjArgs<real> A)
     const int k = j * G.nx + i;
     const real m[5] = {A.lw[k], A.ldU[k], A.ldV[k], A.ldU[k], A.ldV[k]};
 #pragma unroll
-    for (int v = 0; v < 3; v++) {
-        A.G0[v][k] += A.c0 * m[v];
-        A.G1[v][k] += A.c1 * m[v];
-        A.G2[v][k] += A.c2 * m[v];
+    for (int v = 0; v < 5; v++) {
+        if (v >= 3 && !A.bsnq) break;
+        const real c0 = v < 3 ? A.c0 : A.e0, c1 = v < 3 ? A.c1 : A.e1, c2 = v < 3 ? A.c2 : A.e2;
+        A.G0[v][k] += c0 * m[v];
+        if (A.G1[v]) A.G1[v][k] += c1 * m[v];
+        if (A.G2[v]) A.G2[v][k] += c2 * m[v];
     }
-    if (A.bsnq) {
-#pragma unroll
-        for (int v = 3; v < 5; v++) {
-            A.G0[v][k] += A.e0 * m[v];
-            A.G1[v][k] += A.e1 * m[v];
-            A.G2[v][k] += A.e2 * m[v];
-        }
-    }
+}
+
+template <typename real>
+__global__ void k_adj_add(AdjArgs<real> A, const real *xw, const real *xP, const real *xQ)
+{
+    const Geo &G = A.geo;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const int k = j * G.nx + i;
+    A.lw[k] += xw[k];
+    A.lP[k] += xP[k];
+    A.lQ[k] += xQ[k];
 }
 
 // Step 2: the transposed line solves, one thread per line (Thomas, in the
@@ -448,24 +454,63 @@ __global__ void k_adj_misfit(AdjArgs<real> A, const int32_t *gij, int ng, const 
 }  // namespace
 
 template <typename real>
-cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st)
+cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st)
 {
     dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
     k_adj_mask<real><<<g, b, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_adjoint_solves(const AdjArgs<real> &a, cudaStream_t st)
+{
     if (a.bsnq) {
         k_adj_lines_t<real><<<(a.geo.ny + 127) / 128, 128, 0, st>>>(a, 0);
         k_adj_lines_t<real><<<(a.geo.nx + 127) / 128, 128, 0, st>>>(a, 1);
-    } else {
-        cudaMemcpyAsync(a.ldU, a.lP, sizeof(real) * (size_t)a.geo.nx * a.geo.ny, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(a.ldV, a.lQ, sizeof(real) * (size_t)a.geo.nx * a.geo.ny, cudaMemcpyDeviceToDevice, st);
+        return cudaGetLastError();
     }
+    const size_t bytes = sizeof(real) * (size_t)a.geo.nx * a.geo.ny;   // NLSW: P = U*, Q = V*
+    cudaError_t e = cudaMemcpyAsync(a.ldU, a.lP, bytes, cudaMemcpyDeviceToDevice, st);
+    return e != cudaSuccess ? e : cudaMemcpyAsync(a.ldV, a.lQ, bytes, cudaMemcpyDeviceToDevice, st);
+}
+
+template <typename real>
+cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st)
+{
+    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
     k_adj_hist<real><<<g, b, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st)
+{
+    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
     k_adj_cells<real><<<g, b, 0, st>>>(a);
     if (a.bsnq) k_adj_disp<real><<<g, b, 0, st>>>(a);
     dim3 bf(64, 4);
     k_adj_faces<real><<<dim3((a.geo.nx + 1 + 63) / 64, (a.geo.ny + 3) / 4), bf, 0, st>>>(a, 0);
     k_adj_faces<real><<<dim3((a.geo.ny + 1 + 63) / 64, (a.geo.nx + 3) / 4), bf, 0, st>>>(a, 1);
     return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
+                               cudaStream_t st)
+{
+    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
+    k_adj_add<real><<<g, b, 0, st>>>(a, xw, xP, xQ);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st)
+{
+    cudaError_t e = launch_adjoint_mask(a, st);
+    if (e == cudaSuccess) e = launch_adjoint_solves(a, st);
+    if (e == cudaSuccess) e = launch_adjoint_hist(a, st);
+    if (e == cudaSuccess) e = launch_adjoint_vjp(a, st);
+    return e;
 }
 
 template <typename real>
@@ -478,6 +523,12 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
 
 #define CEL_ADJ_INSTANTIATE(real)                                                                        \
     template cudaError_t launch_adjoint_step<real>(const AdjArgs<real> &, cudaStream_t);                 \
+    template cudaError_t launch_adjoint_mask<real>(const AdjArgs<real> &, cudaStream_t);                 \
+    template cudaError_t launch_adjoint_solves<real>(const AdjArgs<real> &, cudaStream_t);               \
+    template cudaError_t launch_adjoint_hist<real>(const AdjArgs<real> &, cudaStream_t);                 \
+    template cudaError_t launch_adjoint_vjp<real>(const AdjArgs<real> &, cudaStream_t);                  \
+    template cudaError_t launch_adjoint_add<real>(const AdjArgs<real> &, const real *, const real *,      \
+                                                  const real *, cudaStream_t);                          \
     template cudaError_t launch_adjoint_misfit<real>(const AdjArgs<real> &, const int32_t *, int,         \
                                                      const real *, const real *, cudaStream_t);
 

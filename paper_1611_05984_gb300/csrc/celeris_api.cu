@@ -211,6 +211,10 @@ struct cel_solver {
     int64_t launches;
     void *runup;      // caller's [ny][nx] run-up field, or NULL
     double runup_delta;
+    // adjoint recomputation: where to copy the iterate after every stage but
+    // the last ([stage][w, P, Q][ny][nx] dense), or NULL
+    unsigned char *capture;
+    size_t capture_field;
     int ktab_dirty;   // boundaries or bed changed: rebuild the Eckart table
     uint64_t gen;     // counts boundary and bed changes (ensembles rebuild their tables)
     std::string err;
@@ -418,6 +422,14 @@ cel_status step_t(cel_solver *s, int nsteps)
             prof_end(s, pl);
             if (lp.L[0].mshift != lp.L[1].mshift) launches += 1;   // two segment lengths: two launches
             launches += 2;
+            if (s->capture && stage < Kn) {
+                real *dst = reinterpret_cast<real *>(s->capture + s->capture_field * 3 * stage);
+                const size_t f = s->capture_field / sizeof(real);
+                CEL_CUDA(s, launch_get_state<real>(s->geo, s->at<real>(L.w[(s->cur + stage + 1) & 1]),
+                                                   s->at<real>(L.P[1 - s->pcur]), s->at<real>(L.Qc[1 - s->pcur]), dst,
+                                                   dst + f, dst + 2 * f, s->stream),
+                         "iterate capture");
+            }
         }
         finish_step(s, Kn);
         cel_status st = log_gauges<real>(s, s->stream, launches);
@@ -537,6 +549,8 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->launches = 0;
     s->runup = nullptr;
     s->runup_delta = 0.0;
+    s->capture = nullptr;
+    s->capture_field = 0;
     s->ktab_dirty = 1;
     s->gen = 0;
     s->step = 0;
@@ -1027,6 +1041,8 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.launches = 0;
     s.runup = nullptr;
     s.runup_delta = 0.0;
+    s.capture = nullptr;
+    s.capture_field = 0;
     s.ktab_dirty = 1;
     s.gen = 0;
     s.step = first_step;
@@ -1511,7 +1527,7 @@ namespace {
 
 struct AdjLayout {
     size_t ckpt_bytes, cells_bytes;
-    size_t ckpt, seg, lam, G, rec, gij, total;
+    size_t ckpt, seg, iter, lam, G, rec, gij, total;
     int nseg;
 };
 
@@ -1528,9 +1544,11 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng)
         return o;
     };
     L.ckpt = take(L.ckpt_bytes * (size_t)(L.nseg + 1));   // + the final state
+    const int K = s->params.corrector_iters;
     L.seg = take(L.cells_bytes * 3 * (size_t)(C + 1));
-    L.lam = take(L.cells_bytes * 6);   // lambda of w, P, Q; of the U*, V* increments; solve scratch
-    L.G = take(L.cells_bytes * 15);    // 3 steps x (E, F, G, F*, G*)
+    L.iter = take(L.cells_bytes * 3 * (size_t)K * (size_t)(C + 1));   // the iterates of every step
+    L.lam = take(L.cells_bytes * 12);  // 3 sets of (w, P, Q); the U*, V* increments; solve scratch
+    L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
     L.total = cur;
@@ -1571,6 +1589,10 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     auto segf = [&](int k, int v) { return reinterpret_cast<real *>(scr + L.seg + L.cells_bytes * (3 * (size_t)k + v)); };
     auto lam = [&](int v) { return reinterpret_cast<real *>(scr + L.lam + L.cells_bytes * v); };
     auto Gb = [&](int slot, int v) { return reinterpret_cast<real *>(scr + L.G + L.cells_bytes * (5 * slot + v)); };
+    const int K = s->params.corrector_iters;
+    auto iterf = [&](int k, int stage, int v) {   // iterate after `stage` of step k of the segment
+        return reinterpret_cast<real *>(scr + L.iter + L.cells_bytes * (3 * ((size_t)k * K + stage) + v));
+    };
     const int64_t step0 = s->step;
     cel_status stt;
     // forward, with checkpoints and the gauge records
@@ -1590,9 +1612,11 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         for (size_t k = 0; k < r.size(); k++) acc += 0.5 * ((double)r[k] - (double)o[k]) * ((double)r[k] - (double)o[k]);
         if (loss) *loss = acc;
     }
-    // reverse
-    CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 6, st), "adjoint");
-    CEL_CUDA(s, cudaMemsetAsync(scr + L.G, 0, L.cells_bytes * 15, st), "adjoint");
+    // reverse.  lam sets 0-2: the adjoint of the state after the step (then
+    // before it), of the present iterate, and the accumulator of the state
+    // before the step; 9, 10: the U*, V* increments; 11: solve scratch.
+    CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 12, st), "adjoint");
+    CEL_CUDA(s, cudaMemsetAsync(scr + L.G, 0, L.cells_bytes * 20, st), "adjoint");
     AdjArgs<real> a;
     memset(&a, 0, sizeof(a));
     a.geo = s->geo;
@@ -1600,15 +1624,35 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     a.c = make_coef<real>(s->geo, s->phy, s->bnd);
     a.Bc = s->at<real>(s->lay.Bc);
     a.ghost = s->at<real>(s->lay.ghost);
-    a.lw = lam(0);
-    a.lP = lam(1);
-    a.lQ = lam(2);
-    a.ldU = lam(3);
-    a.ldV = lam(4);
-    a.tri = lam(5);
+    a.ldU = lam(9);
+    a.ldV = lam(10);
+    a.tri = lam(11);
     a.bsnq = s->params.model == CEL_BSNQ;
+    int lset = 0;   // which lam set holds the adjoint of the state after the step
+    auto setl = [&](AdjArgs<real> &x, int set) {
+        x.lw = lam(3 * set);
+        x.lP = lam(3 * set + 1);
+        x.lQ = lam(3 * set + 2);
+    };
+    auto setG = [&](AdjArgs<real> &x, int slot0, int slot1, int slot2) {
+        for (int v = 0; v < 5; v++) {
+            x.G0[v] = Gb(slot0, v);
+            x.G1[v] = slot1 >= 0 ? Gb(slot1, v) : nullptr;
+            x.G2[v] = slot2 >= 0 ? Gb(slot2, v) : nullptr;
+        }
+    };
+    auto coefs = [&](AdjArgs<real> &x, double c0, double c1, double c2, double e0, double e1, double e2) {
+        x.c0 = real(c0);
+        x.c1 = real(c1);
+        x.c2 = real(c2);
+        x.e0 = real(e0);
+        x.e1 = real(e1);
+        x.e2 = real(e2);
+    };
+    setl(a, lset);
     CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(N - 1) * ng, obs + (size_t)(N - 1) * ng, st),
              "adjoint misfit");
+    const double dt = s->params.dt, c12 = dt / 12.0, c24 = dt / 24.0;
     for (int sg = L.nseg - 1; sg >= 0; sg--) {
         const int n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
         if ((stt = cel_load_checkpoint(s, ckpt(sg), L.ckpt_bytes)) != CEL_OK) return stt;
@@ -1616,54 +1660,110 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
             CEL_CUDA(s, launch_get_state<real>(s->geo, s->at<real>(s->lay.w[s->cur]), s->at<real>(s->lay.P[s->pcur]),
                                                s->at<real>(s->lay.Qc[s->pcur]), segf(k, 0), segf(k, 1), segf(k, 2), st),
                      "adjoint states");
-            if (k < n1 - n0 && (stt = step_t<real>(s, 1)) != CEL_OK) return stt;
+            if (k < n1 - n0) {
+                s->capture = K > 0 ? reinterpret_cast<unsigned char *>(iterf(k, 0, 0)) : nullptr;
+                s->capture_field = L.cells_bytes;
+                stt = step_t<real>(s, 1);
+                s->capture = nullptr;
+                if (stt != CEL_OK) return stt;
+            }
         }
         for (int n = n1 - 1; n >= n0; n--) {
             const int k = n - n0;
             if (a.c.sine)
                 CEL_CUDA(s, launch_ghost_table<real>(s->geo, s->phy, s->bnd, s->at<real>(s->lay.dr),
-                                                     s->at<double>(s->lay.ktab), (double)(step0 + n) * s->params.dt,
-                                                     (double)(step0 + n + 1) * s->params.dt,
-                                                     s->at<real>(s->lay.ghost), a.c.npos, st),
+                                                     s->at<double>(s->lay.ktab), (double)(step0 + n) * dt,
+                                                     (double)(step0 + n + 1) * dt, s->at<real>(s->lay.ghost),
+                                                     a.c.npos, st),
                          "adjoint ghosts");
-            double c[3], e[3];
-            adj_coefs(n, s->params.dt, c, e);
-            a.c0 = real(c[0]);
-            a.c1 = real(c[1]);
-            a.c2 = real(c[2]);
-            a.e0 = real(e[0]);
-            a.e1 = real(e[1]);
-            a.e2 = real(e[2]);
-            a.w = segf(k, 0);
-            a.P = segf(k, 1);
-            a.Q = segf(k, 2);
-            a.w_next = segf(k + 1, 0);
-            for (int v = 0; v < 5; v++) {
-                a.G0[v] = Gb(n % 3, v);
-                a.G1[v] = Gb((n + 2) % 3, v);
-                a.G2[v] = Gb((n + 1) % 3, v);
+            const int Kn = n >= 2 ? K : 0;
+            const int sn = n % 3, sm1 = (n + 2) % 3, sm2 = (n + 1) % 3;
+            if (Kn == 0) {
+                double c[3], e[3];
+                adj_coefs(n, dt, c, e);
+                coefs(a, c[0], c[1], c[2], e[0], e[1], e[2]);
+                setl(a, lset);
+                setG(a, sn, sm1, sm2);
+                a.w = segf(k, 0);
+                a.P = segf(k, 1);
+                a.Q = segf(k, 2);
+                a.w_next = segf(k + 1, 0);
+                a.final_stage = 1;
+                CEL_CUDA(s, launch_adjoint_step<real>(a, st), "adjoint step");
+            } else {
+                // corrector stages Kn..1, then the predictor; acc collects the
+                // adjoint of the state before the step
+                const int acc = (lset + 2) % 3;
+                int cur = lset, nxt = (lset + 1) % 3;
+                CEL_CUDA(s, cudaMemsetAsync(lam(3 * acc), 0, L.cells_bytes * 3, st), "adjoint");
+                for (int stg = Kn; stg >= 1; stg--) {
+                    AdjArgs<real> b = a;
+                    setl(b, cur);
+                    b.w_next = stg == Kn ? segf(k + 1, 0) : iterf(k, stg, 0);
+                    b.final_stage = stg == Kn;
+                    CEL_CUDA(s, launch_adjoint_mask<real>(b, st), "adjoint mask");
+                    CEL_CUDA(s, launch_adjoint_solves<real>(b, st), "adjoint solves");
+                    // the AM4 base (Eq. 18-20): w^n + dt/24 (19 R^n - 5 R^{n-1} + R^{n-2}) - F*^n
+                    coefs(b, 19.0 * c24, -5.0 * c24, c24, -1.0, 0.0, 0.0);
+                    setG(b, sn, sm1, sm2);
+                    CEL_CUDA(s, launch_adjoint_hist<real>(b, st), "adjoint history");
+                    AdjArgs<real> x = a;
+                    setl(x, acc);
+                    CEL_CUDA(s, launch_adjoint_add<real>(x, b.lw, b.lP, b.lQ, st), "adjoint");
+                    // the right side at the iterate before this stage: 9 dt/24 R + F*
+                    CEL_CUDA(s, cudaMemsetAsync(Gb(3, 0), 0, L.cells_bytes * 5, st), "adjoint");
+                    coefs(b, 9.0 * c24, 0.0, 0.0, 1.0, 0.0, 0.0);
+                    setG(b, 3, -1, -1);
+                    CEL_CUDA(s, launch_adjoint_hist<real>(b, st), "adjoint history");
+                    AdjArgs<real> v = b;
+                    v.tsel = 1;   // the corrector stages read the ghosts at t^{n+1}
+                    setl(v, nxt);
+                    CEL_CUDA(s, cudaMemsetAsync(lam(3 * nxt), 0, L.cells_bytes * 3, st), "adjoint");
+                    v.w = iterf(k, stg - 1, 0);
+                    v.P = iterf(k, stg - 1, 1);
+                    v.Q = iterf(k, stg - 1, 2);
+                    CEL_CUDA(s, launch_adjoint_vjp<real>(v, st), "adjoint iterate");
+                    std::swap(cur, nxt);
+                }
+                // the predictor (Eq. 15-17): masks without the sponge, solves, AB3 history
+                AdjArgs<real> p = a;
+                setl(p, cur);
+                p.w_next = iterf(k, 0, 0);
+                p.final_stage = 0;
+                CEL_CUDA(s, launch_adjoint_mask<real>(p, st), "adjoint mask");
+                CEL_CUDA(s, launch_adjoint_solves<real>(p, st), "adjoint solves");
+                coefs(p, 23.0 * c12, -16.0 * c12, 5.0 * c12, 2.0, -3.0, 1.0);
+                setG(p, sn, sm1, sm2);
+                CEL_CUDA(s, launch_adjoint_hist<real>(p, st), "adjoint history");
+                AdjArgs<real> x = a;
+                setl(x, acc);
+                CEL_CUDA(s, launch_adjoint_add<real>(x, p.lw, p.lP, p.lQ, st), "adjoint");
+                // R^n and F*^n at the state before the step
+                x.w = segf(k, 0);
+                x.P = segf(k, 1);
+                x.Q = segf(k, 2);
+                setG(x, sn, -1, -1);
+                CEL_CUDA(s, launch_adjoint_vjp<real>(x, st), "adjoint state");
+                lset = acc;
             }
-            CEL_CUDA(s, launch_adjoint_step<real>(a, st), "adjoint step");
+            setl(a, lset);
             if (n >= 1)
                 CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(n - 1) * ng,
                                                         obs + (size_t)(n - 1) * ng, st),
                          "adjoint misfit");
-            CEL_CUDA(s, cudaMemsetAsync(Gb(n % 3, 0), 0, L.cells_bytes * 5, st), "adjoint");
+            CEL_CUDA(s, cudaMemsetAsync(Gb(sn, 0), 0, L.cells_bytes * 5, st), "adjoint");
         }
     }
-    CEL_CUDA(s, cudaMemcpyAsync(grad, lam(0), sizeof(real) * cells, cudaMemcpyDeviceToDevice, st), "adjoint gradient");
+    CEL_CUDA(s, cudaMemcpyAsync(grad, lam(3 * lset), sizeof(real) * cells, cudaMemcpyDeviceToDevice, st),
+             "adjoint gradient");
     if (eta_out)
         CEL_CUDA(s, cudaMemcpyAsync(eta_out, rec, sizeof(real) * (size_t)N * ng, cudaMemcpyDeviceToDevice, st),
                  "adjoint records");
     return cel_load_checkpoint(s, ckpt(L.nseg), L.ckpt_bytes);   // leave the solver after step N
 }
 
-cel_status adjoint_check(const cel_solver *s, int N, int C, int ng, std::string &why)
+cel_status adjoint_check(const cel_solver *, int N, int C, int ng, std::string &why)
 {
-    if (s->params.corrector_iters != 0) {
-        why = "the adjoint covers the predictor only (corrector_iters = 0)";
-        return CEL_ERR_NOT_IMPLEMENTED;
-    }
     if (N < 1 || C < 1 || ng < 1) {
         why = "nsteps, ckpt_every and the gauge count must be positive";
         return CEL_ERR_INVALID_ARG;

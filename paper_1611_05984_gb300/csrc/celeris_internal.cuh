@@ -189,7 +189,7 @@ struct RenderArgs {
 template <typename real>
 cudaError_t launch_render(const RenderArgs<real> &a, cudaStream_t st);
 
-// Discrete adjoint of one step (celeris_adjoint.cu), predictor only.  State
+// Discrete adjoint of one stage (celeris_adjoint.cu).  State
 // arrays are dense [ny][nx]: w, P, Q the state before the step, w_next w
 // after it; lw, lP, lQ the adjoint (in: of the state after the step, out: of
 // the state before it); G0, G1, G2 the adjoint of this step's right sides
@@ -209,10 +209,28 @@ struct AdjArgs {
     real c0, c1, c2;       // weights of R^n, R^{n-1}, R^{n-2} in this step's update
     real e0, e1, e2;       // weights of F*^n, F*^{n-1}, F*^{n-2} (Boussinesq)
     int bsnq;
+    int final_stage;       // the masks include the sponge
+    int tsel;              // sine-maker ghosts at t^n (0, predictor) or t^{n+1} (1, corrector)
 };
 
+// One predictor-only step reversed: masks, transposed solves, history, the
+// right sides' Jacobians transposed.
 template <typename real>
 cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st);
+// The same phases one at a time (a corrector step composes them); G1 and G2
+// may be NULL in the history phase.
+template <typename real>
+cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st);
+template <typename real>
+cudaError_t launch_adjoint_solves(const AdjArgs<real> &a, cudaStream_t st);
+template <typename real>
+cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st);
+template <typename real>
+cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st);
+// lw += xw, lP += xP, lQ += xQ
+template <typename real>
+cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
+                               cudaStream_t st);
 template <typename real>
 cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, int ng, const real *rec,
                                   const real *obs, cudaStream_t st);

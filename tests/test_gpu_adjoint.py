@@ -165,12 +165,15 @@ def test_autograd_function_and_rejections():
     bed = g.field("Bbar").double().cpu().numpy()
     want = np.where(s.w0 > bed, ref, 0.0)
     np.testing.assert_allclose(w0.grad.cpu().numpy(), want, rtol=1e-9, atol=1e-14)
-    b = celeris.from_scenario(sc.beach(nx=64, ny=48, sponge=8), dtype=torch.float64)   # Boussinesq, K = 1
-    with pytest.raises(celeris.CelerisError):
-        celeris.gauge_misfit_gradient(b, 5, gauges[:1], torch.zeros((5, 1), dtype=torch.float64))
+    b = celeris.from_scenario(sc.beach(nx=64, ny=48, sponge=8), dtype=torch.float64)
+    with pytest.raises(celeris.CelerisError):                       # a gauge off the grid
+        celeris.gauge_misfit_gradient(b, 5, [(64, 3)], torch.zeros((5, 1), dtype=torch.float64))
+    b.step(1)
+    with pytest.raises(celeris.CelerisError):                       # the history is not fresh
+        celeris.gauge_misfit_gradient(b, 5, [(6, 3)], torch.zeros((5, 1), dtype=torch.float64))
 
 
-def _tilted_bsnq(model, nsteps=12):
+def _tilted_bsnq(model, nsteps=12, K=0):
     """Boussinesq-ready kink-free state: a tilted surface and discharge with
     cubic terms and a short ripple (wavelength 8 cells, depth/dx = 1, so the
     dispersive and mixed terms matter and K = 0 is stable), every slope of
@@ -178,7 +181,7 @@ def _tilted_bsnq(model, nsteps=12):
     from paper_1611_05984_gb300 import scenarios as sc
     nx, ny, dx, d0 = 48, 36, 0.5, 0.5
     dt = 0.1 * dx / math.sqrt(9.81 * d0)
-    s = sc.flat_basin(nx, ny, dx, d0, dt, model=model, K=0, friction=1, fcoef=0.01, eps=1e-8)
+    s = sc.flat_basin(nx, ny, dx, d0, dt, model=model, K=K, friction=1, fcoef=0.01, eps=1e-8)
     X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
     xs, ys = X / (nx * dx), Y / (ny * dx)
     s.w0 = 0.04 * xs + 0.03 * xs ** 3 + 0.02 * ys + 0.015 * ys ** 3 + 0.004 * xs * ys \
@@ -218,3 +221,56 @@ def test_adjoint_boussinesq_matches_oracle_away_from_kinks():
         adb, adn = float(np.sum(gb * v)), float(np.sum(gn * v))
         assert abs(adb - fdb) <= 1e-3 * abs(fdb)
         assert abs((adb - adn) - (fdb - fdn)) <= 1e-2 * abs(fdb - fdn) + 1e-6 * abs(fdb)
+
+
+@pytest.mark.parametrize("model", [0, 1], ids=["bsnq", "nlsw"])
+def test_adjoint_corrector_matches_oracle_away_from_kinks(model):
+    """One AM4 corrector iteration (K = 1): the reverse runs the corrector
+    stage (its base Y, its right side at the predicted state, the sine
+    ghosts at t^{n+1}) and then the predictor; a sine maker on the west."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    s, gauges, X, Y = _tilted_bsnq(model, nsteps=10, K=1)
+    s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.002, 4.0, 0.2, 0.3),))
+    rng = np.random.default_rng(8)
+    obs = 0.01 * rng.standard_normal((s.steps, len(gauges)))
+    loss, _, grad, _ = _gpu_gradient(s, gauges, obs, ckpt=3)
+    assert abs(loss - _oracle_loss_state(s, s.w0, gauges, obs)) <= 1e-9 * loss
+    eps = 1e-5
+    for _ in range(5):
+        v = np.zeros_like(X)
+        for _ in range(3):
+            cx, cy = rng.uniform(2.0, 22.0), rng.uniform(2.0, 16.0)
+            v += rng.standard_normal() * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / rng.uniform(2.0, 8.0))
+        v *= 1e-4
+        fd = (_oracle_loss_state(s, s.w0 + eps * v, gauges, obs)
+              - _oracle_loss_state(s, s.w0 - eps * v, gauges, obs)) / (2 * eps)
+        ad = float(np.sum(grad * v))
+        assert abs(ad - fd) <= 1e-3 * abs(fd), (ad, fd)
+
+
+def test_adjoint_corrector_beach_with_dry_land():
+    """K = 1 Boussinesq on a beach with dry land (dx = 0.5 m, depth/dx <=
+    1): loss and records equal the oracle's, checkpoint spacing changes
+    nothing, land far from the water gets zero gradient."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    nx, ny, dx = 48, 32, 0.5
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
+    z = np.maximum(-0.5, (X - 17.0) * 0.1)
+    dt = 0.1 * dx / math.sqrt(9.81 * 0.5)
+    s = sc.flat_basin(nx, ny, dx, 0.5, dt, model=0, K=1, friction=2, fcoef=0.02, eps=1e-8)
+    s.z = z
+    s.sides[sc.S] = sc.Side(sc.SPONGE, 5)
+    s.w0 = np.maximum(z, 0.05 * np.exp(-((X - 9.0) ** 2 + (Y - 8.0) ** 2) / 6.0))
+    s.steps = 30
+    rng = np.random.default_rng(12)
+    gauges = [(int(rng.integers(4, 30)), int(rng.integers(3, ny - 3))) for _ in range(5)]
+    obs = 0.005 * rng.standard_normal((s.steps, len(gauges)))
+    loss, eta, g4, g = _gpu_gradient(s, gauges, obs, ckpt=4)
+    lo, eta_o = _oracle_loss(s, s.w0, gauges, obs)
+    assert abs(loss - lo) <= 1e-9 * abs(lo)
+    np.testing.assert_allclose(eta, eta_o, rtol=0, atol=1e-11)
+    _, _, g30, _ = _gpu_gradient(s, gauges, obs, ckpt=30)
+    assert np.linalg.norm(g4 - g30) <= 1e-10 * np.linalg.norm(g30)
+    land = z > 0.5
+    assert np.any(land) and np.all(g4[land] == 0.0)
+    assert np.linalg.norm(g4) > 0
