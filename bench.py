@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="beach2048",
-                    choices=["beach2048", "beach8192", "beach512", "whalin2000", "conical601", "ensemble256"])
+                    choices=["beach2048", "beach8192", "beach512", "whalin2000", "conical601", "ensemble256",
+                             "adjoint512"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -189,8 +190,8 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    if args.workload == "ensemble256":
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no ensemble mode; "
+    if args.workload in ("ensemble256", "adjoint512"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no ensemble or adjoint mode; "
                           "its arm runs the single-grid workloads"}), flush=True)
         return
     s = workload(args.workload)
@@ -343,6 +344,50 @@ def run_ensemble(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Cost of the discrete adjoint on the hump-on-beach workload (512^2,
+    Boussinesq, K = 1, 16 gauges, checkpoints every 100 steps): the time of
+    the gauge-misfit gradient (forward with checkpoints, recomputation,
+    reverse) against the time of the forward steps alone, both with CUDA
+    events on the solver's stream; --steps is the run length."""
+    import torch
+
+    from paper_1611_05984_gb300 import celeris
+    from paper_1611_05984_gb300 import scenarios as sc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dtype = torch.float32 if args.precision == "f32" else torch.float64
+    s, gauges = sc.hump_beach(steps=args.steps)
+    g = celeris.from_scenario(s, dtype=dtype)
+    stream = g.stream
+    g.step(args.warmup)
+    obs = torch.zeros((args.steps, len(gauges)), dtype=dtype, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    g.set_state(*s.initial_state())
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    g.step(args.steps)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    g.set_state(*s.initial_state())
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    loss, eta, grad = celeris.gauge_misfit_gradient(g, args.steps, gauges, obs, ckpt_every=100)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    fwd, adj = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    line = {"metric": "adjoint cost / forward cost", "value": adj / fwd, "unit": "ratio", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": adj / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": s.name, "nx": s.nx, "ny": s.ny, "corrector_iters": s.K, "gauges": len(gauges),
+                       "ckpt_every": 100},
+            "forward_ms_per_step": fwd / args.steps, "loss": loss,
+            "grad_finite": bool(torch.isfinite(grad).all().item()),
+            "grad_norm": float(torch.linalg.norm(grad.double()).item())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -350,6 +395,9 @@ def main():
         return
     if args.workload == "ensemble256":
         run_ensemble(args)
+        return
+    if args.workload == "adjoint512":
+        run_adjoint(args)
         return
     import torch
     import torch.distributed as dist

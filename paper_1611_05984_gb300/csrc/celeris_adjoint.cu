@@ -442,6 +442,28 @@ __global__ void k_adj_disp(AdjArgs<real> A)
     }
 }
 
+// The adjoint of P and Q into the line solver's layouts (x-rows [ny][px],
+// y-columns [nx][py]) and the transposed solves' solutions back.
+template <typename real>
+__global__ void k_adj_pack(Geo g, const real *lP, const real *lQ, real *X, real *Yc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t k = (size_t)j * g.nx + i;
+    X[(size_t)j * g.px + i] = lP[k];
+    Yc[(size_t)i * g.py + j] = lQ[k];
+}
+
+template <typename real>
+__global__ void k_adj_unpack(Geo g, const real *X, const real *Yc, real *ldU, real *ldV)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t k = (size_t)j * g.nx + i;
+    ldU[k] = X[(size_t)j * g.px + i];
+    ldV[k] = Yc[(size_t)i * g.py + j];
+}
+
 // The misfit at the gauges after step n enters the adjoint of w^n.
 template <typename real>
 __global__ void k_adj_misfit(AdjArgs<real> A, const int32_t *gij, int ng, const real *rec, const real *obs)
@@ -504,6 +526,15 @@ cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const rea
 }
 
 template <typename real>
+cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int back, cudaStream_t st)
+{
+    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
+    if (back) k_adj_unpack<real><<<g, b, 0, st>>>(a.geo, X, Yc, a.ldU, a.ldV);
+    else k_adj_pack<real><<<g, b, 0, st>>>(a.geo, a.lP, a.lQ, X, Yc);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st)
 {
     cudaError_t e = launch_adjoint_mask(a, st);
@@ -529,6 +560,7 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
     template cudaError_t launch_adjoint_vjp<real>(const AdjArgs<real> &, cudaStream_t);                  \
     template cudaError_t launch_adjoint_add<real>(const AdjArgs<real> &, const real *, const real *,      \
                                                   const real *, cudaStream_t);                          \
+    template cudaError_t launch_adjoint_pack<real>(const AdjArgs<real> &, real *, real *, int, cudaStream_t); \
     template cudaError_t launch_adjoint_misfit<real>(const AdjArgs<real> &, const int32_t *, int,         \
                                                      const real *, const real *, cudaStream_t);
 

@@ -1649,6 +1649,32 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         x.e1 = real(e1);
         x.e2 = real(e2);
     };
+    // the transposed line solves (Boussinesq) through the forward's line
+    // solver, in the solver's U* and V* increment buffers (idle here)
+    auto solves = [&](const AdjArgs<real> &x) -> cudaError_t {
+        if (!x.bsnq) return launch_adjoint_solves<real>(x, st);
+        real *X = s->at<real>(s->lay.U), *Yc = s->at<real>(s->lay.Vc);
+        cudaError_t e = launch_adjoint_pack<real>(x, X, Yc, 0, st);
+        if (e != cudaSuccess) return e;
+        LinePair<real> lp;
+        for (int dir = 0; dir < 2; dir++) {
+            lp.L[dir] = line_args<real>(s, x.c, dir, 0, 0);
+            real *buf = dir == 0 ? X : Yc;
+            lp.L[dir].rhs = buf;
+            lp.L[dir].base = buf;
+            lp.L[dir].sol = buf;
+            lp.L[dir].identity = 0;
+        }
+        e = launch_lines_transposed<real>(lp, st);
+        return e != cudaSuccess ? e : launch_adjoint_pack<real>(x, X, Yc, 1, st);
+    };
+    auto full_step = [&](const AdjArgs<real> &x) -> cudaError_t {
+        cudaError_t e = launch_adjoint_mask<real>(x, st);
+        if (e == cudaSuccess) e = solves(x);
+        if (e == cudaSuccess) e = launch_adjoint_hist<real>(x, st);
+        if (e == cudaSuccess) e = launch_adjoint_vjp<real>(x, st);
+        return e;
+    };
     setl(a, lset);
     CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(N - 1) * ng, obs + (size_t)(N - 1) * ng, st),
              "adjoint misfit");
@@ -1689,7 +1715,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 a.Q = segf(k, 2);
                 a.w_next = segf(k + 1, 0);
                 a.final_stage = 1;
-                CEL_CUDA(s, launch_adjoint_step<real>(a, st), "adjoint step");
+                CEL_CUDA(s, full_step(a), "adjoint step");
             } else {
                 // corrector stages Kn..1, then the predictor; acc collects the
                 // adjoint of the state before the step
@@ -1702,7 +1728,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                     b.w_next = stg == Kn ? segf(k + 1, 0) : iterf(k, stg, 0);
                     b.final_stage = stg == Kn;
                     CEL_CUDA(s, launch_adjoint_mask<real>(b, st), "adjoint mask");
-                    CEL_CUDA(s, launch_adjoint_solves<real>(b, st), "adjoint solves");
+                    CEL_CUDA(s, solves(b), "adjoint solves");
                     // the AM4 base (Eq. 18-20): w^n + dt/24 (19 R^n - 5 R^{n-1} + R^{n-2}) - F*^n
                     coefs(b, 19.0 * c24, -5.0 * c24, c24, -1.0, 0.0, 0.0);
                     setG(b, sn, sm1, sm2);
@@ -1731,7 +1757,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 p.w_next = iterf(k, 0, 0);
                 p.final_stage = 0;
                 CEL_CUDA(s, launch_adjoint_mask<real>(p, st), "adjoint mask");
-                CEL_CUDA(s, launch_adjoint_solves<real>(p, st), "adjoint solves");
+                CEL_CUDA(s, solves(p), "adjoint solves");
                 coefs(p, 23.0 * c12, -16.0 * c12, 5.0 * c12, 2.0, -3.0, 1.0);
                 setG(p, sn, sm1, sm2);
                 CEL_CUDA(s, launch_adjoint_hist<real>(p, st), "adjoint history");

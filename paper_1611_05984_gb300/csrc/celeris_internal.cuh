@@ -227,6 +227,9 @@ template <typename real>
 cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st);
 template <typename real>
 cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st);
+// back = 0: lP, lQ into X ([ny][px]) and Yc ([nx][py]); back = 1: X, Yc into ldU, ldV
+template <typename real>
+cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int back, cudaStream_t st);
 // lw += xw, lP += xP, lQ += xQ
 template <typename real>
 cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
@@ -286,6 +289,10 @@ struct LinePair {
 
 template <typename real>
 cudaError_t launch_lines(const LinePair<real> &a, cudaStream_t st);
+// The transposed systems T^T y = rhs of the same lines (the adjoint): y goes
+// to sol; base, mask and the sponge are not used.
+template <typename real>
+cudaError_t launch_lines_transposed(const LinePair<real> &a, cudaStream_t st);
 
 // Ensembles: one launch covers every member.  The argument blocks live in
 // device memory, one per member (stencil, ghost table) or per line family.

@@ -861,7 +861,10 @@ __device__ __forceinline__ int seg_slot(int k, int mshift, int sp)
 }
 
 // One line of one family (x-row or y-column): the whole solve and epilogue.
-template <typename real, int M>
+// kT: solve the transposed system T^T y = r instead (the adjoint), whose
+// row k is (c_{k-1}, b_k, a_{k+1}) of T's rows with T's boundary rows, and
+// write y alone (no P^n, sponge or dry mask).
+template <typename real, int M, bool kT = false>
 __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, unsigned char *smem_raw)
 {
     const int n = A.n, S = A.nseg, N2 = 2 * S;
@@ -915,18 +918,22 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
         if (!A.identity) {
         const bool act = tid < S;
         const int f = tid * m, l = f + m - 1;
-        real dm = real(0), dp = real(0), dcur = real(0), dlast = real(0);
+        real dm = real(0), dp = real(0), dcur = real(0), dlast = real(0), dm2 = real(0), dp2 = real(0);
         if (act) {
             dlast = sA[seg_slot(n - 1, mshift, sp)];
             dm = f > 0 ? sA[seg_slot(f - 1, mshift, sp)] : sA[seg_slot(0, mshift, sp)];
             dp = l + 1 < n ? sA[seg_slot(l + 1, mshift, sp)] : dlast;   // mirrored beyond the end
             dcur = sA[tid];
+            if (kT) {   // one more on each side for the neighbouring rows' coefficients
+                dm2 = f > 1 ? sA[seg_slot(f - 2, mshift, sp)] : sA[seg_slot(0, mshift, sp)];
+                dp2 = l + 2 < n ? sA[seg_slot(l + 2, mshift, sp)] : dlast;
+            }
         }
         __syncthreads();
         real af = 0, bf = 1, cf = 0, rf = 0;
         if (act) {
             // forward: rows f+1..l as alpha x_f + x_k + gamma x_{k+1} = rho
-            real dprev = dm, ap = 0, gp = 0, rp = 0;
+            real dprev = dm, dprev2 = dm2, ap = 0, gp = 0, rp = 0;
 #pragma unroll
             for (int j = 0; j < m; j++) {
                 const int k = f + j, q = j * sp + tid;
@@ -934,7 +941,21 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
                 real ak, bk, ck;
                 coef23(B3, hrh, srh, rh2, dcur, dprev, dnext, ak, bk, ck);
                 real rk = sR[q];
-                if (k == 0) {   // Reading A-B2: mirror, or the known ghost increment
+                if (kT) {
+                    const real dnext2 = j + 2 < m ? (k + 2 < n ? sA[q + 2 * sp] : dlast) : (j + 2 == m ? dp : dp2);
+                    if (k == 0 && !lo_sine) bk -= ak;
+                    if (k == n - 1 && !hi_sine) bk -= ck;
+                    real am, bm, cm, a1, b1, c1;
+                    coef23(B3, hrh, srh, rh2, dprev, dprev2, dcur, am, bm, cm);    // row k - 1
+                    coef23(B3, hrh, srh, rh2, dnext, dcur, dnext2, a1, b1, c1);    // row k + 1
+                    ak = k >= 1 && k - 1 < n - 1 ? cm : real(0);   // c_{n-1} is 0 (boundary row)
+                    ck = k + 1 <= n - 1 ? a1 : real(0);
+                    if (k >= n) {   // padding: identity rows
+                        ak = ck = real(0);
+                        bk = real(1);
+                    }
+                    dprev2 = dprev;
+                } else if (k == 0) {   // Reading A-B2: mirror, or the known ghost increment
                     if (lo_sine) {
                         const real *t0 = A.ghost + ghost_index(0, lo_side, 0, gvar, line + 2, A.c.npos);
                         const real *t1 = A.ghost + ghost_index(1, lo_side, 0, gvar, line + 2, A.c.npos);
@@ -944,7 +965,7 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
                     }
                     ak = real(0);
                 }
-                if (k == n - 1) {
+                if (!kT && k == n - 1) {
                     if (hi_sine) {
                         const real *t0 = A.ghost + ghost_index(0, hi_side, 0, gvar, line + 2, A.c.npos);
                         const real *t1 = A.ghost + ghost_index(1, hi_side, 0, gvar, line + 2, A.c.npos);
@@ -1066,6 +1087,10 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
         // epilogue: P^n + increment, sponge (Eq. 30) on the last stage, zero
         // discharge where dry
         real *out = A.sol + (size_t)line * A.pitch;
+        if (kT) {   // the transposed solve's solution alone
+            for (int k = tid; k < n; k += T) out[k] = sR[seg_slot(k, mshift, sp)];
+            return;
+        }
 #pragma unroll
         for (int u = 0; u < kMaxOwn; u++) {
             const int k = tid + u * T;
@@ -1089,6 +1114,16 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(const 
     const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
     const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
     line_solve<real, M>(PA.L[fam], line, smem_raw);
+}
+
+// The transposed solves of the adjoint: x-rows and y-columns in one launch.
+template <typename real, int M>
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines_t(const __grid_constant__ LinePair<real> PA)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
+    const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
+    line_solve<real, M, true>(PA.L[fam], line, smem_raw);
 }
 
 // Ensemble: lines of many members and both families in one launch, all of
@@ -1298,7 +1333,22 @@ size_t line_smem_bytes(int n, int nseg)
 }
 
 template <typename real>
+cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, bool transposed);
+
+template <typename real>
 cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
+{
+    return launch_lines_impl(p, st, false);
+}
+
+template <typename real>
+cudaError_t launch_lines_transposed(const LinePair<real> &p, cudaStream_t st)
+{
+    return launch_lines_impl(p, st, true);
+}
+
+template <typename real>
+cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, bool transposed)
 {
     size_t smem = 0;
     int threads = 32;
@@ -1307,8 +1357,8 @@ cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
         LinePair<real> a = p, b = p;
         a.L[1].nlines = 0;
         b.L[0].nlines = 0;
-        cudaError_t e = launch_lines<real>(a, st);
-        return e != cudaSuccess ? e : launch_lines<real>(b, st);
+        cudaError_t e = launch_lines_impl<real>(a, st, transposed);
+        return e != cudaSuccess ? e : launch_lines_impl<real>(b, st, transposed);
     }
     for (int f = 0; f < 2; f++) {
         const LineArgs<real> &a = p.L[f];
@@ -1319,15 +1369,17 @@ cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
         int t = line_threads(a.n, (int)sizeof(real));
         if (t > threads) threads = t;
     }
-    static int configured[6] = {0, 0, 0, 0, 0, 0};
+    static int configured[2][6] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
     const int sh = p.L[0].nlines > 0 ? p.L[0].mshift : p.L[1].mshift;
-    auto *kern = sh == 1 ? k_lines<real, 2> : sh == 2 ? k_lines<real, 4> : sh == 3 ? k_lines<real, 8>
-                                          : sh == 4 ? k_lines<real, 16> : k_lines<real, 32>;
     if (sh < 1 || sh > 5) return cudaErrorInvalidValue;
-    if ((int)smem > configured[sh]) {
+    auto *kern = transposed ? (sh == 1 ? k_lines_t<real, 2> : sh == 2 ? k_lines_t<real, 4> : sh == 3 ? k_lines_t<real, 8>
+                                                          : sh == 4 ? k_lines_t<real, 16> : k_lines_t<real, 32>)
+                            : (sh == 1 ? k_lines<real, 2> : sh == 2 ? k_lines<real, 4> : sh == 3 ? k_lines<real, 8>
+                                                          : sh == 4 ? k_lines<real, 16> : k_lines<real, 32>);
+    if ((int)smem > configured[transposed][sh]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[sh] = (int)smem;
+        configured[transposed][sh] = (int)smem;
     }
     const int blocks = p.L[0].nlines + p.L[1].nlines;
     if (blocks > 0) kern<<<blocks, threads, smem, st>>>(p);
@@ -1383,6 +1435,7 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
                                                   cudaStream_t);                                        \
     template cudaError_t launch_stencil<real>(const StencilArgs<real> &, cudaStream_t);                  \
     template cudaError_t launch_lines<real>(const LinePair<real> &, cudaStream_t);                       \
+    template cudaError_t launch_lines_transposed<real>(const LinePair<real> &, cudaStream_t);            \
     template size_t line_smem_bytes<real>(int, int);                                                    \
     template cudaError_t launch_ghost_batch<real>(const GhostArgs<real> *, const int *, int, int, int64_t, \
                                                   cudaStream_t);                                        \

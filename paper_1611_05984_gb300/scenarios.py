@@ -310,3 +310,23 @@ def partition(cells, parts: int) -> list:
         groups[g].append(k)
         load[g] += cells[k]
     return [sorted(g) for g in groups]
+
+
+def hump_beach(n: int = 512, seed: int = 5, steps: int = 2000, H: float = 0.5, width: float = 30.0,
+               ngauges: int = 16, K: int = 1, cr: float = 0.1):
+    """Gauge-misfit workload for the adjoint: the beach-and-shoal bed
+    (make_beach, seed 5) on n x n cells of 1 m, a Gaussian hump of water
+    H exp(-r^2 / width^2) offshore as the initial state, sponges on the west,
+    north and south, a wall behind the dry east, Manning 0.015, K = 1,
+    Courant 0.1, and ngauges seeded gauges in water deeper than 2 m.
+    Returns (scenario, gauges)."""
+    sc = beach(n, n, 1.0, seed=seed, steps=steps, K=K, cr=cr, sponge=min(50, n // 10))
+    sc.sides[W] = Side(SPONGE, min(50, n // 10))
+    X, Y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+    sc.w0 = np.maximum(sc.z, H * np.exp(-((X - 0.4 * n) ** 2 + (Y - 0.5 * n) ** 2) / width ** 2))
+    sc.name = f"hump_beach_{n}"
+    rng = np.random.default_rng(seed + 2000)
+    deep = np.argwhere(sc.z < -2.0)
+    pick = rng.choice(len(deep), size=ngauges, replace=False)
+    gauges = [(int(deep[k][1]), int(deep[k][0])) for k in pick]
+    return sc, gauges
