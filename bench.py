@@ -347,9 +347,11 @@ def run_ensemble(args):
 def run_adjoint(args):
     """Cost of the discrete adjoint on the hump-on-beach workload (512^2,
     Boussinesq, K = 1, 16 gauges, checkpoints every 100 steps): the time of
-    the gauge-misfit gradient (forward with checkpoints, recomputation,
-    reverse) against the time of the forward steps alone, both with CUDA
-    events on the solver's stream; --steps is the run length."""
+    the gauge-misfit gradients with respect to the initial w and the bed
+    (forward with checkpoints, recomputation, reverse) against the time of
+    the forward steps alone, both with CUDA events on the solver's stream;
+    --steps is the run length.  The observations are the gauges of a target
+    run from a perturbed hump over a perturbed bed."""
     import torch
 
     from paper_1611_05984_gb300 import celeris
@@ -360,8 +362,12 @@ def run_adjoint(args):
     s, gauges = sc.hump_beach(steps=args.steps)
     g = celeris.from_scenario(s, dtype=dtype)
     stream = g.stream
+    t = celeris.from_scenario(sc.hump_beach_target(s), dtype=dtype)
+    t.set_gauges(gauges, 1, args.steps)
+    t.step(args.steps)
+    obs = torch.as_tensor(t.read_gauges(args.steps)).to(device="cuda", dtype=dtype)
+    t.close()
     g.step(args.warmup)
-    obs = torch.zeros((args.steps, len(gauges)), dtype=dtype, device="cuda")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     g.set_state(*s.initial_state())
     torch.cuda.synchronize()
@@ -372,7 +378,7 @@ def run_adjoint(args):
     g.set_state(*s.initial_state())
     torch.cuda.synchronize()
     ev[2].record(stream)
-    loss, eta, grad = celeris.gauge_misfit_gradient(g, args.steps, gauges, obs, ckpt_every=100)
+    loss, eta, grad, grad_z = celeris.gauge_misfit_gradient(g, args.steps, gauges, obs, ckpt_every=100, bed=True)
     ev[3].record(stream)
     torch.cuda.synchronize()
     fwd, adj = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
@@ -383,8 +389,9 @@ def run_adjoint(args):
             "config": {"workload": s.name, "nx": s.nx, "ny": s.ny, "corrector_iters": s.K, "gauges": len(gauges),
                        "ckpt_every": 100},
             "forward_ms_per_step": fwd / args.steps, "loss": loss,
-            "grad_finite": bool(torch.isfinite(grad).all().item()),
-            "grad_norm": float(torch.linalg.norm(grad.double()).item())}
+            "grad_finite": bool(torch.isfinite(grad).all().item() and torch.isfinite(grad_z).all().item()),
+            "grad_w_norm": float(torch.linalg.norm(grad.double()).item()),
+            "grad_z_norm": float(torch.linalg.norm(grad_z.double()).item())}
     print(json.dumps(line), flush=True)
 
 

@@ -208,31 +208,39 @@ cel_status cel_render(cel_solver *s, const cel_render_params *params, void *rgba
 
 /* Discrete adjoint: the gradient of the gauge misfit
  *   L = 1/2 sum_{n=1..N} sum_g (eta_g^n - obs_g^n)^2,
- * eta_g^n = w - w_s at gauge g after step n, with respect to w at the start,
- * by the exact reverse of every step: the KP07 flux with the limiter and
- * positivity branches taken in the forward run, the dry clamp and dry
- * masks, the sponge, friction, the dispersive and mixed terms (Eq. 10-13),
- * the line solves transposed (Eq. 21-23), the AB3 predictor with its
- * history and Euler start-up, and the AM4 corrector iterations (Eq. 15-20),
- * for both models (Sec. 3.2).  The gradient is the derivative along the
- * branches the forward run took (the step is piecewise smooth).  The solver must hold a fresh
- * history (cel_set_state just before); it runs N steps forward keeping a
- * checkpoint every ckpt_every steps, then the reverse sweep, recomputing one
- * segment of states at a time from its checkpoint; it ends holding the state
- * after step N.
+ * eta_g^n = w - w_s at gauge g after step n, with respect to w at the start
+ * and (optionally) to the cell-centre bed z, by the exact reverse of every
+ * step: the KP07 flux with the limiter and positivity branches taken in the
+ * forward run, the dry clamp and dry masks, the sponge, friction, the
+ * dispersive and mixed terms (Eq. 10-13), the line solves transposed
+ * (Eq. 21-23), the AB3 predictor with its history and Euler start-up, and
+ * the AM4 corrector iterations (Eq. 15-20), for both models (Sec. 3.2).
+ * The gradient is the derivative along the branches the forward run took
+ * (the step is piecewise smooth).  The solver must hold a fresh history
+ * (cel_set_state just before); it runs N steps forward keeping a checkpoint
+ * every ckpt_every steps, then the reverse sweep, recomputing one segment of
+ * states at a time from its checkpoint; it ends holding the state after
+ * step N.
  *
  * gij_host: ngauges (i, j) pairs; obs_dev: [N][ngauges] real, device;
- * scratch_dev: cel_adjoint_bytes bytes of device memory (256-byte aligned),
- * owned by the caller; eta_dev (may be NULL): [N][ngauges] real, the
- * recorded eta; grad_w_dev: [ny][nx] real, dL/dw(t = 0) (w after
- * cel_set_state's clamp to the bed); *loss (may be NULL): L in double.
- * Synchronises.  The adjoint sums reach a cell from several faces in no
- * fixed order, so repeated runs agree to rounding, not bit for bit. */
+ * scratch_dev: cel_adjoint_bytes(..., with_bed = grad_z_dev != NULL) bytes
+ * of device memory (256-byte aligned), owned by the caller; eta_dev (may be
+ * NULL): [N][ngauges] real, the recorded eta; grad_w_dev: [ny][nx] real,
+ * dL/dw(t = 0) (w after cel_set_state's clamp to the bed); grad_z_dev (may
+ * be NULL): [ny][nx] real, dL/dz for the bed z of cel_create or
+ * cel_set_bathymetry, with the initial w held where the cell is wet and
+ * equal to the cell bed where it is dry (the clamp), as when cel_set_state
+ * is called again after a change of bed.  The bed enters the sine maker's
+ * ghost values through the depth at the boundary; that path is not
+ * differentiated.  *loss (may be NULL): L in double.  Synchronises.  The
+ * adjoint sums reach a cell from several faces in no fixed order, so
+ * repeated runs agree to rounding, not bit for bit. */
 cel_status cel_adjoint_bytes(const cel_solver *s, int32_t nsteps, int32_t ckpt_every, int32_t ngauges,
-                             size_t *bytes);
+                             int32_t with_bed, size_t *bytes);
 cel_status cel_adjoint_gauge_misfit(cel_solver *s, int32_t nsteps, int32_t ckpt_every, const int32_t *gij_host,
                                     int32_t ngauges, const void *obs_dev, void *scratch_dev,
-                                    size_t scratch_bytes, void *eta_dev, void *grad_w_dev, double *loss);
+                                    size_t scratch_bytes, void *eta_dev, void *grad_w_dev, void *grad_z_dev,
+                                    double *loss);
 
 /* Kernel launches issued by the most recent cel_step call. */
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);

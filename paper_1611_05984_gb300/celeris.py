@@ -101,8 +101,8 @@ def load(build_if_missing: bool = True):
         L.cel_load_checkpoint.argtypes = [vp, vp, sz]
         L.cel_runup_enable.argtypes = [vp, vp, d]
         L.cel_render.argtypes = [vp, ctypes.POINTER(CelRenderParams), vp]
-        L.cel_adjoint_bytes.argtypes = [vp, i32, i32, i32, ctypes.POINTER(sz)]
-        L.cel_adjoint_gauge_misfit.argtypes = [vp, i32, i32, ctypes.POINTER(i32), i32, vp, vp, sz, vp, vp,
+        L.cel_adjoint_bytes.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(sz)]
+        L.cel_adjoint_gauge_misfit.argtypes = [vp, i32, i32, ctypes.POINTER(i32), i32, vp, vp, sz, vp, vp, vp,
                                                ctypes.POINTER(d)]
         L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_profile_enable.argtypes = [vp, i32]
@@ -432,11 +432,12 @@ class Ensemble:
             pass
 
 
-def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every: int = 100):
+def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every: int = 100, bed: bool = False):
     """Run nsteps from the solver's present (freshly set) state and return
-    (L, eta, dL/dw0): the gauge misfit L = 1/2 sum (eta - obs)^2 over steps
-    1..nsteps, the recorded eta ([nsteps, ngauges] tensor) and its gradient
-    with respect to w at the start ([ny, nx] tensor), by the discrete
+    (L, eta, dL/dw0), plus dL/dz when bed is set: the gauge misfit
+    L = 1/2 sum (eta - obs)^2 over steps 1..nsteps, the recorded eta
+    ([nsteps, ngauges] tensor) and its gradients with respect to w at the
+    start and to the cell-centre bed ([ny, nx] tensors), by the discrete
     adjoint (cel_adjoint_gauge_misfit).  obs: [nsteps, ngauges]."""
     torch = solver.torch
     ij = np.ascontiguousarray(np.asarray(gauges, dtype=np.int32).reshape(-1, 2))
@@ -445,49 +446,60 @@ def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every
     if tuple(obs_t.shape) != (nsteps, ng):
         raise ValueError("obs must be [nsteps, ngauges]")
     nb = ctypes.c_size_t()
-    solver._check(solver.L.cel_adjoint_bytes(solver._h, nsteps, ckpt_every, ng, ctypes.byref(nb)), "adjoint_bytes")
+    solver._check(solver.L.cel_adjoint_bytes(solver._h, nsteps, ckpt_every, ng, int(bed), ctypes.byref(nb)),
+                  "adjoint_bytes")
     with torch.cuda.device(solver.device):
         scratch = torch.empty(nb.value + 256, dtype=torch.uint8, device=solver.device)
         eta = torch.empty((nsteps, ng), dtype=solver.dtype, device=solver.device)
         grad = torch.empty((solver.ny, solver.nx), dtype=solver.dtype, device=solver.device)
+        grad_z = torch.empty((solver.ny, solver.nx), dtype=solver.dtype, device=solver.device) if bed else None
     ptr = (scratch.data_ptr() + 255) // 256 * 256
     loss = ctypes.c_double()
     st = solver.L.cel_adjoint_gauge_misfit(solver._h, nsteps, ckpt_every,
                                            ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ng,
                                            obs_t.data_ptr(), ptr, nb.value, eta.data_ptr(), grad.data_ptr(),
-                                           ctypes.byref(loss))
+                                           grad_z.data_ptr() if bed else None, ctypes.byref(loss))
     solver._check(st, "adjoint_gauge_misfit")
-    return loss.value, eta, grad
+    return (loss.value, eta, grad, grad_z) if bed else (loss.value, eta, grad)
 
 
 def _gauge_misfit_function():
     import torch
 
     class GaugeMisfit(torch.autograd.Function):
-        """L(w0) = 1/2 sum (eta - obs)^2 over nsteps steps from w0 (with P0, Q0
-        fixed); backward gives dL/dw0 from the discrete adjoint.  Where w0 lies
-        below the bed the state is clamped to it, and the gradient there is 0."""
+        """L(w0, z) = 1/2 sum (eta - obs)^2 over nsteps steps from w0 (with P0,
+        Q0 fixed) over the bed z (None: the solver's bed, not differentiated);
+        backward gives dL/dw0 and dL/dz from the discrete adjoint.  Where w0
+        lies below the bed the state is clamped to it: the gradient in w0 is
+        0 there, and w follows the bed."""
 
         @staticmethod
-        def forward(ctx, w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every=100):
+        def forward(ctx, w0, z, solver, P0, Q0, nsteps, gauges, obs, ckpt_every=100):
+            if z is not None:
+                solver.set_bathymetry(z)
             solver.set_state(w0, P0, Q0)
-            loss, _, grad = gauge_misfit_gradient(solver, nsteps, gauges, obs, ckpt_every)
+            out = gauge_misfit_gradient(solver, nsteps, gauges, obs, ckpt_every, bed=z is not None)
+            loss, grad = out[0], out[2]
             bed = solver.field("Bbar").to(grad.dtype)
             grad = torch.where(w0.to(device=grad.device, dtype=grad.dtype) > bed, grad, torch.zeros_like(grad))
-            ctx.save_for_backward(grad)
+            grad_z = out[3] if z is not None else torch.zeros_like(grad)
+            ctx.has_z = z is not None
+            ctx.save_for_backward(grad, grad_z)
             return torch.tensor(loss, dtype=w0.dtype, device=w0.device)
 
         @staticmethod
         def backward(ctx, gout):
-            (grad,) = ctx.saved_tensors
-            return (grad * gout).to(gout.dtype), None, None, None, None, None, None, None
+            grad, grad_z = ctx.saved_tensors
+            gz = (grad_z * gout).to(gout.dtype) if ctx.has_z else None
+            return (grad * gout).to(gout.dtype), gz, None, None, None, None, None, None, None
 
     return GaugeMisfit
 
 
-def gauge_misfit(w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every=100):
-    """Differentiable gauge misfit (torch.autograd) of a run from w0."""
-    return _gauge_misfit_function().apply(w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every)
+def gauge_misfit(w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every=100, z=None):
+    """Differentiable gauge misfit (torch.autograd) of a run from w0, and
+    over the bed z when one is given."""
+    return _gauge_misfit_function().apply(w0, z, solver, P0, Q0, nsteps, gauges, obs, ckpt_every)
 
 
 def from_scenario(s, dtype=None, K: Optional[int] = None, **kw) -> Solver:

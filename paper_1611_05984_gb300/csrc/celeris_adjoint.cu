@@ -17,6 +17,13 @@
 //      friction, the dispersive eta terms of Eq. 10-11 and F*, G* of
 //      Eq. 12-13 (linear in the neighbours, ghosts mapped back to the cells
 //      they mirror).
+// With the bed's gradient requested, the same Jacobians are taken with
+// respect to the bed as well: the face beds of the reconstruction and the
+// flux, the cell bed of the bed slope, friction and the dry clamp, the
+// still-water depth d of the dispersive terms and of the line systems' rows
+// (dT/dd with the transposed solves' solution and the forward's), summed
+// over the run and mapped through d = max(w_s - Bbar, 0), Bbar = mean of 4
+// corners and corner = mean of 4 cell-centre beds (Reading A-W1) to dL/dz.
 // The face and cell Jacobians are exact: the forward device functions are
 // evaluated on dual numbers, one input direction at a time, so every branch
 // follows the forward state.  Adjoints reach a cell through the faces around
@@ -147,18 +154,30 @@ __device__ __forceinline__ Src<real> source2d(const AdjArgs<real> &A, int i, int
 // y-face f (dir 1: between rows f-1 and f of column `line`) from the 4 cells
 // around it, in the forward's order of operations.
 template <typename T>
-__device__ __forceinline__ void face_flux(const Dual<T> w[4], const Dual<T> P[4], const Dual<T> Q[4], T Bm, T Bf,
-                                          T Bp, T th, T g, T eps, int dir, Dual<T> H[3])
+__device__ __forceinline__ void face_flux(const Dual<T> w[4], const Dual<T> P[4], const Dual<T> Q[4], Dual<T> Bm,
+                                          Dual<T> Bf, Dual<T> Bp, T th, T g, T eps, int dir, Dual<T> H[3])
 {
     Dual<T> lo[3], hiL[3], loR[3], hiR[3];
     const Dual<T> w0[3] = {w[0], w[1], w[2]}, P0[3] = {P[0], P[1], P[2]}, Q0[3] = {Q[0], Q[1], Q[2]};
     const Dual<T> w1[3] = {w[1], w[2], w[3]}, P1[3] = {P[1], P[2], P[3]}, Q1[3] = {Q[1], Q[2], Q[3]};
-    recon(Dual<T>(th), w0, P0, Q0, Dual<T>(Bm), Dual<T>(Bf), lo, hiL);
-    recon(Dual<T>(th), w1, P1, Q1, Dual<T>(Bf), Dual<T>(Bp), loR, hiR);
+    recon(Dual<T>(th), w0, P0, Q0, Bm, Bf, lo, hiL);
+    recon(Dual<T>(th), w1, P1, Q1, Bf, Bp, loR, hiR);
     if (dir == 0)
-        cu_flux(Dual<T>(g), Dual<T>(eps), hiL[0], hiL[1], hiL[2], loR[0], loR[1], loR[2], Dual<T>(Bf), H);
+        cu_flux(Dual<T>(g), Dual<T>(eps), hiL[0], hiL[1], hiL[2], loR[0], loR[1], loR[2], Bf, H);
     else
-        cu_flux(Dual<T>(g), Dual<T>(eps), hiL[0], hiL[2], hiL[1], loR[0], loR[2], loR[1], Dual<T>(Bf), H);
+        cu_flux(Dual<T>(g), Dual<T>(eps), hiL[0], hiL[2], hiL[1], loR[0], loR[2], loR[1], Bf, H);
+}
+
+// Index of cell (i, j), i in [-1, nx], j in [-1, ny], in the ring arrays.
+__device__ __forceinline__ size_t ring_index(const Geo &G, int i, int j)
+{
+    return (size_t)(j + 1) * (G.nx + 2) + (i + 1);
+}
+
+// Index of corner (ci, cj) in the corner arrays.
+__device__ __forceinline__ size_t corner_index(const Geo &G, int ci, int cj)
+{
+    return (size_t)(cj + 1) * G.pc + (ci + 1);
 }
 
 // Step 1 of the reverse for one cell: the masks; the state's own path
@@ -180,6 +199,7 @@ __global__ void k_adj_mask(AdjArgs<real> A)
     const real w1 = spw ? ws + (wn - ws) / gam : wn;   // before the sponge
     const real tol = (sizeof(real) == 8 ? real(1e-12) : real(1e-6)) * fmax(real(1), fabs(Bb));
     const bool clamped = w1 - Bb <= tol;
+    if (clamped && A.lBb) A.lBb[ring_index(G, i, j)] += A.lw[k] * (spw ? gam : real(1));   // w = Bbar there
     A.lw[k] = clamped ? real(0) : A.lw[k] * (spw ? gam : real(1));
     A.lP[k] = dry ? real(0) : A.lP[k] * gam;
     A.lQ[k] = dry ? real(0) : A.lQ[k] * gam;
@@ -306,7 +326,7 @@ __global__ void k_adj_cells(AdjArgs<real> A)
     const real ByS = real(0.5) * (c00 + c10), ByN = real(0.5) * (c01 + c11);
     const real g = A.c.g;
     real dw = -(g * (BxE - BxW) * A.c.rdx) * lF - (g * (ByN - ByS) * A.c.rdy) * lG;
-    real dP = real(0), dQ = real(0);
+    real dP = real(0), dQ = real(0), dfw = real(0);   // dfw: friction's part of dw
     if (A.phy.friction != kFricNone) {
         const real x[3] = {A.w[k], A.P[k], A.Q[k]};
         real grad[3];
@@ -321,9 +341,20 @@ __global__ void k_adj_cells(AdjArgs<real> A)
             Dual<real> fF = -(fc * P0 * mag * hinv * hinv), fG = -(fc * Q0 * mag * hinv * hinv);
             grad[v] = lF * fF.d + lG * fG.d;
         }
-        dw += grad[0];
+        dfw = grad[0];
+        dw += dfw;
         dP = grad[1];
         dQ = grad[2];
+    }
+    if (A.lBc) {   // the bed: Bbar through h = w - Bbar, the face beds through the slope
+        const real hb = A.w[k] - Bb;
+        A.lBb[ring_index(G, i, j)] += g * (BxE - BxW) * A.c.rdx * lF + g * (ByN - ByS) * A.c.rdy * lG - dfw;
+        const real lBxE = -(g * hb * A.c.rdx) * lF, lByN = -(g * hb * A.c.rdy) * lG;
+        // BxW = (c00 + c01) / 2, BxE = (c10 + c11) / 2, ByS = (c00 + c10) / 2, ByN = (c01 + c11) / 2
+        atomicAdd(A.lBc + corner_index(G, i, j), real(0.5) * (-lBxE - lByN));
+        atomicAdd(A.lBc + corner_index(G, i + 1, j), real(0.5) * (lBxE - lByN));
+        atomicAdd(A.lBc + corner_index(G, i, j + 1), real(0.5) * (-lBxE + lByN));
+        atomicAdd(A.lBc + corner_index(G, i + 1, j + 1), real(0.5) * (lBxE + lByN));
     }
     A.lw[k] += dw;
     A.lP[k] += dP;
@@ -357,6 +388,26 @@ __global__ void k_adj_faces(AdjArgs<real> A, int dir)
                         : real(0.5) * (corner(A.Bc, G, line, q) + corner(A.Bc, G, line + 1, q));
     };
     const real Bm = face_bed(f - 1), Bf = face_bed(f), Bp = face_bed(f + 1);
+    if (A.lBc) {   // the three face beds, each the mean of its two corners
+        for (int b = 0; b < 3; b++) {
+            Dual<real> w[4], P[4], Q[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                w[q] = Dual<real>(s[q].v[0]);
+                P[q] = Dual<real>(s[q].v[1]);
+                Q[q] = Dual<real>(s[q].v[2]);
+            }
+            Dual<real> H[3];
+            face_flux(w, P, Q, Dual<real>(Bm, b == 0 ? real(1) : real(0)), Dual<real>(Bf, b == 1 ? real(1) : real(0)),
+                      Dual<real>(Bp, b == 2 ? real(1) : real(0)), A.c.theta, A.c.g, A.c.eps, dir, H);
+            const real gsum = real(0.5) * (lH[0] * H[0].d + lH[1] * H[1].d + lH[2] * H[2].d);
+            if (gsum != real(0)) {
+                const int q = f - 1 + b;
+                atomicAdd(A.lBc + (dir == 0 ? corner_index(G, q, line) : corner_index(G, line, q)), gsum);
+                atomicAdd(A.lBc + (dir == 0 ? corner_index(G, q, line + 1) : corner_index(G, line + 1, q)), gsum);
+            }
+        }
+    }
     for (int c = 0; c < 4; c++) {
         if (s[c].idx < 0) continue;
         for (int v = 0; v < 3; v++) {
@@ -368,7 +419,7 @@ __global__ void k_adj_faces(AdjArgs<real> A, int dir)
                 Q[q] = Dual<real>(s[q].v[2], q == c && v == 2 ? real(1) : real(0));
             }
             Dual<real> H[3];
-            face_flux(w, P, Q, Bm, Bf, Bp, A.c.theta, A.c.g, A.c.eps, dir, H);
+            face_flux(w, P, Q, Dual<real>(Bm), Dual<real>(Bf), Dual<real>(Bp), A.c.theta, A.c.g, A.c.eps, dir, H);
             const real gsum = lH[0] * H[0].d + lH[1] * H[1].d + lH[2] * H[2].d;
             if (gsum != real(0)) {
                 real *dst = v == 0 ? A.lw : (v == 1 ? A.lP : A.lQ);
@@ -440,6 +491,124 @@ __global__ void k_adj_disp(AdjArgs<real> A)
         const Src<real> t = source2d(A, i + mp[q].di, j + mp[q].dj);
         if (t.idx >= 0 && mp[q].wgt != real(0)) atomicAdd(A.lP + t.idx, t.sgn[1] * mp[q].wgt);
     }
+    if (!A.ld) return;
+    // the same terms with respect to d at the cell (dd) and its 4 neighbours
+    // (through ddx, ddy), at the forward's eta, P and Q (ghosts included)
+    auto val = [&](int di, int dj, int v) { return source2d(A, i + di, j + dj).v[v]; };
+    const real e00 = val(0, 0, 0), eE = val(1, 0, 0), eW = val(-1, 0, 0), eN = val(0, 1, 0), eS = val(0, -1, 0);
+    const real eNE = val(1, 1, 0), eNW = val(-1, 1, 0), eSE = val(1, -1, 0), eSW = val(-1, -1, 0);
+    const real exx = (eE - real(2) * e00 + eW) * C.rdx2;
+    const real eyy = (eN - real(2) * e00 + eS) * C.rdy2;
+    const real exy = (eNE - eSE - eNW + eSW) * C.rdxdy4;
+    const real exxx = (val(2, 0, 0) - real(2) * eE + real(2) * eW - val(-2, 0, 0)) * C.rdx3h;
+    const real eyyy = (val(0, 2, 0) - real(2) * eN + real(2) * eS - val(0, -2, 0)) * C.rdy3h;
+    const real exyy = ((eNE - real(2) * eE + eSE) - (eNW - real(2) * eW + eSW)) * C.rdxdy2h;
+    const real exxy = ((eNE - real(2) * eN + eNW) - (eSE - real(2) * eS + eSW)) * C.rdx2dyh;
+    const real Qx = (val(1, 0, 2) - val(-1, 0, 2)) * C.hrdx, Qy = (val(0, 1, 2) - val(0, -1, 2)) * C.hrdy;
+    const real Qxy = (val(1, 1, 2) - val(1, -1, 2) - val(-1, 1, 2) + val(-1, -1, 2)) * C.rdxdy4;
+    const real Px = (val(1, 0, 1) - val(-1, 0, 1)) * C.hrdx, Py = (val(0, 1, 1) - val(0, -1, 1)) * C.hrdy;
+    const real Pxy = (val(1, 1, 1) - val(1, -1, 1) - val(-1, 1, 1) + val(-1, -1, 1)) * C.rdxdy4;
+    const real Bg = C.Bd * C.g;
+    // F = Bg d^3 (exxx + exyy) + Bg d^2 (ddx (2 exx + eyy) + ddy exy), G likewise,
+    // Fs = d ddx Qy / 6 + d ddy Qx / 6 + B3 d^2 Qxy, Gs = d ddy Px / 6 + d ddx Py / 6 + B3 d^2 Pxy
+    const real Ld = lF * (real(3) * Bg * dd * dd * (exxx + exyy) + real(2) * Bg * dd * (ddx * (real(2) * exx + eyy) + ddy * exy)) +
+                    lG * (real(3) * Bg * dd * dd * (eyyy + exxy) + real(2) * Bg * dd * (ddy * (real(2) * eyy + exx) + ddx * exy)) +
+                    lFs * (ddx * Qy * C.sixth + ddy * Qx * C.sixth + real(2) * C.B3 * dd * Qxy) +
+                    lGs * (ddy * Px * C.sixth + ddx * Py * C.sixth + real(2) * C.B3 * dd * Pxy);
+    const real Ldx = (lF * Bg * dd * dd * (real(2) * exx + eyy) + lG * Bg * dd * dd * exy + lFs * dd * Qy * C.sixth +
+                      lGs * dd * Py * C.sixth) * C.hrdx;
+    const real Ldy = (lF * Bg * dd * dd * exy + lG * Bg * dd * dd * (real(2) * eyy + exx) + lFs * dd * Qx * C.sixth +
+                      lGs * dd * Px * C.sixth) * C.hrdy;
+    atomicAdd(A.ld + ring_index(G, i, j), Ld);
+    atomicAdd(A.ld + ring_index(G, i + 1, j), Ldx);
+    atomicAdd(A.ld + ring_index(G, i - 1, j), -Ldx);
+    atomicAdd(A.ld + ring_index(G, i, j + 1), Ldy);
+    atomicAdd(A.ld + ring_index(G, i, j - 1), -Ldy);
+}
+
+// Eq. 23's rows depend on d: a_k = s_k - r_k, b_k = 1 + 2 r_k, c_k = -s_k - r_k
+// with r_k = B3 d_k^2 / h^2, s_k = d_k (d_{k+1} - d_{k-1}) / (12 h^2) (the
+// ends mirrored, d_{-1} = d_0, d_n = d_{n-1}).  T x = r gives dL/dT_kl =
+// -mu_k x_l with mu = T^-T (adjoint of x); a wall's boundary row folds a_0
+// into b_0 (x_{-1} = -x_0), a sine maker's moves a_0 times the ghost
+// increment to the right side (x_{-1} = that increment).  One thread per
+// line element.
+template <typename real>
+__global__ void k_adj_tri_bed(AdjArgs<real> A, const real *X, int dir)
+{
+    const Geo &G = A.geo;
+    const int n = dir == 0 ? G.nx : G.ny, nl = dir == 0 ? G.ny : G.nx;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, line = blockIdx.y * blockDim.y + threadIdx.y;
+    if (k >= n || line >= nl) return;
+    auto cell = [&](int e) { return dir == 0 ? (size_t)line * G.nx + e : (size_t)e * G.nx + line; };
+    auto ring = [&](int e) { return dir == 0 ? ring_index(G, e, line) : ring_index(G, line, e); };
+    auto dcell = [&](int e) {
+        const int i = dir == 0 ? e : line, j = dir == 0 ? line : e;
+        return fmax(A.c.ws - bbar_at(A.Bc, G, i, j), real(0));
+    };
+    const real mu = (dir == 0 ? A.ldU : A.ldV)[cell(k)];
+    if (mu == real(0)) return;
+    const real *x = X + (size_t)line * (dir == 0 ? G.px : G.py);
+    const int lo_side = dir == 0 ? 0 : 2, hi_side = dir == 0 ? 1 : 3, gvar = dir == 0 ? 1 : 2;
+    auto ghost_inc = [&](int side) {
+        return A.ghost[ghost_index(1, side, 0, gvar, line + 2, A.c.npos)] -
+               A.ghost[ghost_index(0, side, 0, gvar, line + 2, A.c.npos)];
+    };
+    const real xk = x[k];
+    const real xm = k > 0 ? x[k - 1] : (((A.c.sine >> lo_side) & 1) ? ghost_inc(lo_side) : -xk);
+    const real xp = k < n - 1 ? x[k + 1] : (((A.c.sine >> hi_side) & 1) ? ghost_inc(hi_side) : -xk);
+    const real gA = -mu * xm, gB = -mu * xk, gC = -mu * xp;
+    const real Lr = -gA + real(2) * gB - gC, Ls = gA - gC;
+    const double h = dir == 0 ? G.dx : G.dy;   // the forward's constants, rounded once
+    const real rh2 = real(1.0 / (h * h)), hrh = real(0.5 / h), srh = real(1.0 / (6.0 * h));
+    const int km = k > 0 ? k - 1 : 0, kp = k < n - 1 ? k + 1 : n - 1;
+    const real dd = dcell(k), dm = dcell(km), dp = dcell(kp);
+    const real Ldp = Ls * dd * srh * hrh;
+    atomicAdd(A.ld + ring(k), Lr * real(2) * A.c.B3 * dd * rh2 + Ls * (dp - dm) * hrh * srh);
+    atomicAdd(A.ld + ring(kp), Ldp);
+    atomicAdd(A.ld + ring(km), -Ldp);
+}
+
+// ld into lBb (d = max(w_s - Bbar, 0)), the initial clamp, and lBb into the
+// 4 corners of each cell (ring included).
+template <typename real>
+__global__ void k_adj_bed_cells(AdjArgs<real> A, const real *w0, const real *lw0)
+{
+    const Geo &G = A.geo;
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1, j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+    if (i > G.nx || j > G.ny) return;
+    const size_t r = ring_index(G, i, j);
+    const real Bb = bbar_at(A.Bc, G, i, j);
+    real lb = A.lBb[r];
+    if (A.c.ws - Bb > real(0)) lb -= A.ld[r];
+    if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) {
+        const size_t k = (size_t)j * G.nx + i;
+        if (w0[k] - Bb <= real(0)) lb += lw0[k];   // w0 = max(w_in, Bbar) follows the bed on dry cells
+    }
+    if (lb == real(0)) return;
+    lb *= real(0.25);
+    atomicAdd(A.lBc + corner_index(G, i, j), lb);
+    atomicAdd(A.lBc + corner_index(G, i + 1, j), lb);
+    atomicAdd(A.lBc + corner_index(G, i, j + 1), lb);
+    atomicAdd(A.lBc + corner_index(G, i + 1, j + 1), lb);
+}
+
+// Corner (ci, cj) = mean of the cell-centre beds around it, mirrored evenly
+// beyond the grid: its adjoint goes to those 4 cells.
+template <typename real>
+__global__ void k_adj_bed_z(AdjArgs<real> A, real *grad_z)
+{
+    const Geo &G = A.geo;
+    const int ci = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1, cj = (int)(blockIdx.y * blockDim.y + threadIdx.y) - 1;
+    if (ci > G.nx + 1 || cj > G.ny + 1) return;
+    const real v = real(0.25) * A.lBc[corner_index(G, ci, cj)];
+    if (v == real(0)) return;
+    const int i0 = mirror_index(ci - 1, G.nx), i1 = mirror_index(ci, G.nx);
+    const int j0 = mirror_index(cj - 1, G.ny), j1 = mirror_index(cj, G.ny);
+    atomicAdd(grad_z + (size_t)j0 * G.nx + i0, v);
+    atomicAdd(grad_z + (size_t)j0 * G.nx + i1, v);
+    atomicAdd(grad_z + (size_t)j1 * G.nx + i0, v);
+    atomicAdd(grad_z + (size_t)j1 * G.nx + i1, v);
 }
 
 // The adjoint of P and Q into the line solver's layouts (x-rows [ny][px],
@@ -517,6 +686,27 @@ cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st)
 }
 
 template <typename real>
+cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_adj_tri_bed<real><<<dim3((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8), b, 0, st>>>(a, X, 0);
+    k_adj_tri_bed<real><<<dim3((a.geo.ny + 31) / 32, (a.geo.nx + 7) / 8), b, 0, st>>>(a, Yc, 1);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_adjoint_bed_final(const AdjArgs<real> &a, const real *w0, const real *lw0, real *grad_z,
+                                     cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_adj_bed_cells<real><<<dim3((a.geo.nx + 2 + 31) / 32, (a.geo.ny + 2 + 7) / 8), b, 0, st>>>(a, w0, lw0);
+    cudaError_t e = cudaMemsetAsync(grad_z, 0, sizeof(real) * (size_t)a.geo.nx * a.geo.ny, st);
+    if (e != cudaSuccess) return e;
+    k_adj_bed_z<real><<<dim3((a.geo.nx + 3 + 31) / 32, (a.geo.ny + 3 + 7) / 8), b, 0, st>>>(a, grad_z);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
                                cudaStream_t st)
 {
@@ -561,6 +751,10 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
     template cudaError_t launch_adjoint_add<real>(const AdjArgs<real> &, const real *, const real *,      \
                                                   const real *, cudaStream_t);                          \
     template cudaError_t launch_adjoint_pack<real>(const AdjArgs<real> &, real *, real *, int, cudaStream_t); \
+    template cudaError_t launch_adjoint_tri_bed<real>(const AdjArgs<real> &, const real *, const real *,   \
+                                                      cudaStream_t);                                   \
+    template cudaError_t launch_adjoint_bed_final<real>(const AdjArgs<real> &, const real *, const real *, \
+                                                        real *, cudaStream_t);                         \
     template cudaError_t launch_adjoint_misfit<real>(const AdjArgs<real> &, const int32_t *, int,         \
                                                      const real *, const real *, cudaStream_t);
 

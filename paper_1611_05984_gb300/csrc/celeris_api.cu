@@ -215,6 +215,10 @@ struct cel_solver {
     // the last ([stage][w, P, Q][ny][nx] dense), or NULL
     unsigned char *capture;
     size_t capture_field;
+    // and where to copy the line solves' right sides of every stage
+    // ([stage][U*, V* increments][line layout], capture_line bytes each), or NULL
+    unsigned char *capture_rhs;
+    size_t capture_line;
     int ktab_dirty;   // boundaries or bed changed: rebuild the Eckart table
     uint64_t gen;     // counts boundary and bed changes (ensembles rebuild their tables)
     std::string err;
@@ -430,6 +434,14 @@ cel_status step_t(cel_solver *s, int nsteps)
                                                    dst + f, dst + 2 * f, s->stream),
                          "iterate capture");
             }
+            if (s->capture_rhs) {
+                unsigned char *dst = s->capture_rhs + s->capture_line * 2 * stage;
+                CEL_CUDA(s, cudaMemcpyAsync(dst, s->at<real>(L.U), sizeof(real) * (size_t)s->geo.ny * s->geo.px,
+                                            cudaMemcpyDeviceToDevice, s->stream), "right-side capture");
+                CEL_CUDA(s, cudaMemcpyAsync(dst + s->capture_line, s->at<real>(L.Vc),
+                                            sizeof(real) * (size_t)s->geo.nx * s->geo.py, cudaMemcpyDeviceToDevice,
+                                            s->stream), "right-side capture");
+            }
         }
         finish_step(s, Kn);
         cel_status st = log_gauges<real>(s, s->stream, launches);
@@ -551,6 +563,8 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->runup_delta = 0.0;
     s->capture = nullptr;
     s->capture_field = 0;
+    s->capture_rhs = nullptr;
+    s->capture_line = 0;
     s->ktab_dirty = 1;
     s->gen = 0;
     s->step = 0;
@@ -1043,6 +1057,8 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.runup_delta = 0.0;
     s.capture = nullptr;
     s.capture_field = 0;
+    s.capture_rhs = nullptr;
+    s.capture_line = 0;
     s.ktab_dirty = 1;
     s.gen = 0;
     s.step = first_step;
@@ -1526,16 +1542,19 @@ void cel_ensemble_destroy(cel_ensemble *e)
 namespace {
 
 struct AdjLayout {
-    size_t ckpt_bytes, cells_bytes;
+    size_t ckpt_bytes, cells_bytes, line_bytes;
     size_t ckpt, seg, iter, lam, G, rec, gij, total;
-    int nseg;
+    size_t rhs, xs, lBc, lBb, ld;   // the bed's gradient (bed != 0)
+    int nseg, bed;
 };
 
-AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng)
+AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
 {
     AdjLayout L;
+    L.bed = bed;
     L.ckpt_bytes = align256(ckpt_total(s));
     L.cells_bytes = align256((size_t)s->grid.nx * s->grid.ny * s->es);
+    L.line_bytes = align256(std::max((size_t)s->geo.ny * s->geo.px, (size_t)s->geo.nx * s->geo.py) * s->es);
     L.nseg = (N + C - 1) / C;
     size_t cur = 0;
     auto take = [&](size_t b) {
@@ -1551,6 +1570,15 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng)
     L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
+    L.rhs = L.xs = L.lBc = L.lBb = L.ld = 0;
+    if (bed) {
+        const bool lines = s->params.model == CEL_BSNQ;
+        L.rhs = take(lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0);   // every stage's right sides
+        L.xs = take(lines ? L.line_bytes * 2 : 0);                                  // and their solutions
+        L.lBc = take((size_t)s->geo.pc * (s->grid.ny + 3) * s->es);
+        L.lBb = take((size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * s->es);
+        L.ld = take((size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * s->es);
+    }
     L.total = cur;
     return L;
 }
@@ -1578,7 +1606,7 @@ void adj_coefs(int64_t n, double dt, double c[3], double e[3])
 
 template <typename real>
 cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int ng, const real *obs, unsigned char *scr,
-                     const AdjLayout &L, real *eta_out, real *grad, double *loss)
+                     const AdjLayout &L, real *eta_out, real *grad, real *grad_z, double *loss)
 {
     cudaStream_t st = s->stream;
     const size_t cells = (size_t)s->grid.nx * s->grid.ny;
@@ -1592,6 +1620,10 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     const int K = s->params.corrector_iters;
     auto iterf = [&](int k, int stage, int v) {   // iterate after `stage` of step k of the segment
         return reinterpret_cast<real *>(scr + L.iter + L.cells_bytes * (3 * ((size_t)k * K + stage) + v));
+    };
+    const bool bed = grad_z != nullptr, bed_lines = bed && s->params.model == CEL_BSNQ;
+    auto rhsf = [&](int k, int stage) {   // right sides of `stage` of step k of the segment
+        return scr + L.rhs + L.line_bytes * 2 * ((size_t)k * (K + 1) + stage);
     };
     const int64_t step0 = s->step;
     cel_status stt;
@@ -1628,6 +1660,14 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     a.ldV = lam(10);
     a.tri = lam(11);
     a.bsnq = s->params.model == CEL_BSNQ;
+    if (bed) {
+        a.lBc = reinterpret_cast<real *>(scr + L.lBc);
+        a.lBb = reinterpret_cast<real *>(scr + L.lBb);
+        a.ld = reinterpret_cast<real *>(scr + L.ld);
+        CEL_CUDA(s, cudaMemsetAsync(a.lBc, 0, (size_t)s->geo.pc * (s->grid.ny + 3) * sizeof(real), st), "adjoint");
+        CEL_CUDA(s, cudaMemsetAsync(a.lBb, 0, (size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * sizeof(real), st), "adjoint");
+        CEL_CUDA(s, cudaMemsetAsync(a.ld, 0, (size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * sizeof(real), st), "adjoint");
+    }
     int lset = 0;   // which lam set holds the adjoint of the state after the step
     auto setl = [&](AdjArgs<real> &x, int set) {
         x.lw = lam(3 * set);
@@ -1668,9 +1708,27 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         e = launch_lines_transposed<real>(lp, st);
         return e != cudaSuccess ? e : launch_adjoint_pack<real>(x, X, Yc, 1, st);
     };
-    auto full_step = [&](const AdjArgs<real> &x) -> cudaError_t {
+    // the line systems' dependence on d: the stage's solutions again from
+    // its captured right sides, with the transposed solves' in ldU, ldV
+    auto tri_bed = [&](const AdjArgs<real> &x, int k, int stage) -> cudaError_t {
+        if (!bed_lines) return cudaSuccess;
+        real *Rx = reinterpret_cast<real *>(rhsf(k, stage)), *Ry = reinterpret_cast<real *>(rhsf(k, stage) + L.line_bytes);
+        real *Xs = reinterpret_cast<real *>(scr + L.xs), *Ys = reinterpret_cast<real *>(scr + L.xs + L.line_bytes);
+        LinePair<real> lp;
+        for (int dir = 0; dir < 2; dir++) {
+            lp.L[dir] = line_args<real>(s, x.c, dir, 0, 0);
+            lp.L[dir].rhs = dir == 0 ? Rx : Ry;
+            lp.L[dir].base = dir == 0 ? Rx : Ry;
+            lp.L[dir].sol = dir == 0 ? Xs : Ys;
+            lp.L[dir].identity = 0;
+        }
+        cudaError_t e = launch_lines_solution<real>(lp, st);
+        return e != cudaSuccess ? e : launch_adjoint_tri_bed<real>(x, Xs, Ys, st);
+    };
+    auto full_step = [&](const AdjArgs<real> &x, int k) -> cudaError_t {
         cudaError_t e = launch_adjoint_mask<real>(x, st);
         if (e == cudaSuccess) e = solves(x);
+        if (e == cudaSuccess) e = tri_bed(x, k, 0);
         if (e == cudaSuccess) e = launch_adjoint_hist<real>(x, st);
         if (e == cudaSuccess) e = launch_adjoint_vjp<real>(x, st);
         return e;
@@ -1689,8 +1747,11 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
             if (k < n1 - n0) {
                 s->capture = K > 0 ? reinterpret_cast<unsigned char *>(iterf(k, 0, 0)) : nullptr;
                 s->capture_field = L.cells_bytes;
+                s->capture_rhs = bed_lines ? rhsf(k, 0) : nullptr;
+                s->capture_line = L.line_bytes;
                 stt = step_t<real>(s, 1);
                 s->capture = nullptr;
+                s->capture_rhs = nullptr;
                 if (stt != CEL_OK) return stt;
             }
         }
@@ -1715,7 +1776,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 a.Q = segf(k, 2);
                 a.w_next = segf(k + 1, 0);
                 a.final_stage = 1;
-                CEL_CUDA(s, full_step(a), "adjoint step");
+                CEL_CUDA(s, full_step(a, k), "adjoint step");
             } else {
                 // corrector stages Kn..1, then the predictor; acc collects the
                 // adjoint of the state before the step
@@ -1729,6 +1790,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                     b.final_stage = stg == Kn;
                     CEL_CUDA(s, launch_adjoint_mask<real>(b, st), "adjoint mask");
                     CEL_CUDA(s, solves(b), "adjoint solves");
+                    CEL_CUDA(s, tri_bed(b, k, stg), "adjoint solves");
                     // the AM4 base (Eq. 18-20): w^n + dt/24 (19 R^n - 5 R^{n-1} + R^{n-2}) - F*^n
                     coefs(b, 19.0 * c24, -5.0 * c24, c24, -1.0, 0.0, 0.0);
                     setG(b, sn, sm1, sm2);
@@ -1758,6 +1820,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 p.final_stage = 0;
                 CEL_CUDA(s, launch_adjoint_mask<real>(p, st), "adjoint mask");
                 CEL_CUDA(s, solves(p), "adjoint solves");
+                CEL_CUDA(s, tri_bed(p, k, 0), "adjoint solves");
                 coefs(p, 23.0 * c12, -16.0 * c12, 5.0 * c12, 2.0, -3.0, 1.0);
                 setG(p, sn, sm1, sm2);
                 CEL_CUDA(s, launch_adjoint_hist<real>(p, st), "adjoint history");
@@ -1782,6 +1845,8 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     }
     CEL_CUDA(s, cudaMemcpyAsync(grad, lam(3 * lset), sizeof(real) * cells, cudaMemcpyDeviceToDevice, st),
              "adjoint gradient");
+    if (bed)   // segment 0's first state is the initial one
+        CEL_CUDA(s, launch_adjoint_bed_final<real>(a, segf(0, 0), lam(3 * lset), grad_z, st), "adjoint bed");
     if (eta_out)
         CEL_CUDA(s, cudaMemcpyAsync(eta_out, rec, sizeof(real) * (size_t)N * ng, cudaMemcpyDeviceToDevice, st),
                  "adjoint records");
@@ -1801,19 +1866,20 @@ cel_status adjoint_check(const cel_solver *, int N, int C, int ng, std::string &
 
 extern "C" {
 
-cel_status cel_adjoint_bytes(const cel_solver *s, int32_t nsteps, int32_t ckpt_every, int32_t ngauges, size_t *bytes)
+cel_status cel_adjoint_bytes(const cel_solver *s, int32_t nsteps, int32_t ckpt_every, int32_t ngauges,
+                             int32_t with_bed, size_t *bytes)
 {
     if (!s || !bytes) return CEL_ERR_INVALID_ARG;
     std::string why;
     cel_status st = adjoint_check(s, nsteps, ckpt_every, ngauges, why);
     if (st != CEL_OK) return st;
-    *bytes = adj_layout(s, nsteps, ckpt_every, ngauges).total;
+    *bytes = adj_layout(s, nsteps, ckpt_every, ngauges, with_bed != 0).total;
     return CEL_OK;
 }
 
 cel_status cel_adjoint_gauge_misfit(cel_solver *s, int32_t nsteps, int32_t ckpt_every, const int32_t *gij_host,
                                     int32_t ngauges, const void *obs_dev, void *scratch_dev, size_t scratch_bytes,
-                                    void *eta_dev, void *grad_w_dev, double *loss)
+                                    void *eta_dev, void *grad_w_dev, void *grad_z_dev, double *loss)
 {
     if (!s) return CEL_ERR_INVALID_ARG;
     std::string why;
@@ -1826,12 +1892,14 @@ cel_status cel_adjoint_gauge_misfit(cel_solver *s, int32_t nsteps, int32_t ckpt_
         if (gij_host[2 * k] < 0 || gij_host[2 * k] >= s->grid.nx || gij_host[2 * k + 1] < 0 ||
             gij_host[2 * k + 1] >= s->grid.ny)
             return fail(s, CEL_ERR_INVALID_ARG, "gauge outside the grid");
-    AdjLayout L = adj_layout(s, nsteps, ckpt_every, ngauges);
+    AdjLayout L = adj_layout(s, nsteps, ckpt_every, ngauges, grad_z_dev != nullptr);
     if (scratch_bytes < L.total) return fail(s, CEL_ERR_WORKSPACE_TOO_SMALL, "adjoint scratch too small");
     return s->es == 4 ? adjoint_t<float>(s, nsteps, ckpt_every, gij_host, ngauges, (const float *)obs_dev,
-                                         (unsigned char *)scratch_dev, L, (float *)eta_dev, (float *)grad_w_dev, loss)
+                                         (unsigned char *)scratch_dev, L, (float *)eta_dev, (float *)grad_w_dev,
+                                         (float *)grad_z_dev, loss)
                       : adjoint_t<double>(s, nsteps, ckpt_every, gij_host, ngauges, (const double *)obs_dev,
-                                          (unsigned char *)scratch_dev, L, (double *)eta_dev, (double *)grad_w_dev, loss);
+                                          (unsigned char *)scratch_dev, L, (double *)eta_dev, (double *)grad_w_dev,
+                                          (double *)grad_z_dev, loss);
 }
 
 }  // extern "C"

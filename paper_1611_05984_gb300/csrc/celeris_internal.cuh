@@ -206,6 +206,10 @@ struct AdjArgs {
     real *lw, *lP, *lQ;
     real *G0[5], *G1[5], *G2[5];
     real *ldU, *ldV, *tri;
+    // the bed's adjoints, or NULL: lBc at the corners (Bc's layout), lBb of
+    // the cell bed Bbar and ld of the still-water depth d on the cells with
+    // a one-cell ring ([ny + 2][nx + 2], cell (i, j) at [j + 1][i + 1])
+    real *lBc, *lBb, *ld;
     real c0, c1, c2;       // weights of R^n, R^{n-1}, R^{n-2} in this step's update
     real e0, e1, e2;       // weights of F*^n, F*^{n-1}, F*^{n-2} (Boussinesq)
     int bsnq;
@@ -230,6 +234,17 @@ cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st);
 // back = 0: lP, lQ into X ([ny][px]) and Yc ([nx][py]); back = 1: X, Yc into ldU, ldV
 template <typename real>
 cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int back, cudaStream_t st);
+// The line systems' dependence on d (Eq. 23): with x the stage's solutions
+// (line layouts, X [ny][px] and Yc [nx][py]) and ldU, ldV the transposed
+// solves' solutions, dL/dT_kl = -ldU_k x_l is added to ld.
+template <typename real>
+cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, cudaStream_t st);
+// The end of the reverse: ld and the clamp of the initial state (cells with
+// w0 <= Bbar follow the bed, weight lw0) into lBb, lBb into lBc, and lBc
+// into the cell-centre bed z as dL/dz (grad_z zeroed here).
+template <typename real>
+cudaError_t launch_adjoint_bed_final(const AdjArgs<real> &a, const real *w0, const real *lw0, real *grad_z,
+                                     cudaStream_t st);
 // lw += xw, lP += xP, lQ += xQ
 template <typename real>
 cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
@@ -293,6 +308,9 @@ cudaError_t launch_lines(const LinePair<real> &a, cudaStream_t st);
 // to sol; base, mask and the sponge are not used.
 template <typename real>
 cudaError_t launch_lines_transposed(const LinePair<real> &a, cudaStream_t st);
+// The step's systems T x = rhs, x alone to sol (no base, sponge or mask).
+template <typename real>
+cudaError_t launch_lines_solution(const LinePair<real> &a, cudaStream_t st);
 
 // Ensembles: one launch covers every member.  The argument blocks live in
 // device memory, one per member (stencil, ghost table) or per line family.

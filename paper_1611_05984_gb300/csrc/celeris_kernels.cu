@@ -861,10 +861,11 @@ __device__ __forceinline__ int seg_slot(int k, int mshift, int sp)
 }
 
 // One line of one family (x-row or y-column): the whole solve and epilogue.
-// kT: solve the transposed system T^T y = r instead (the adjoint), whose
-// row k is (c_{k-1}, b_k, a_{k+1}) of T's rows with T's boundary rows, and
-// write y alone (no P^n, sponge or dry mask).
-template <typename real, int M, bool kT = false>
+// kMode 0: the step's solve, P^n + x with the sponge and the dry mask;
+// 1: the transposed system T^T y = r (the adjoint), whose row k is
+// (c_{k-1}, b_k, a_{k+1}) of T's rows with T's boundary rows, y alone;
+// 2: the step's system T x = r, x alone.
+template <typename real, int M, int kMode = 0>
 __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, unsigned char *smem_raw)
 {
     const int n = A.n, S = A.nseg, N2 = 2 * S;
@@ -883,6 +884,7 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
     const int lo_side = A.dir == 0 ? 0 : 2, hi_side = A.dir == 0 ? 1 : 3;
     const bool lo_sine = (A.c.sine >> lo_side) & 1, hi_sine = (A.c.sine >> hi_side) & 1;
     const int gvar = A.dir == 0 ? 1 : 2;   // ghost discharge: P on x-lines, Q on y-lines
+    constexpr bool kT = kMode == 1;
 
     {
         const real *rhs = A.rhs + (size_t)line * A.pitch;
@@ -1087,7 +1089,7 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
         // epilogue: P^n + increment, sponge (Eq. 30) on the last stage, zero
         // discharge where dry
         real *out = A.sol + (size_t)line * A.pitch;
-        if (kT) {   // the transposed solve's solution alone
+        if (kMode != 0) {   // the solution alone
             for (int k = tid; k < n; k += T) out[k] = sR[seg_slot(k, mshift, sp)];
             return;
         }
@@ -1116,14 +1118,15 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(const 
     line_solve<real, M>(PA.L[fam], line, smem_raw);
 }
 
-// The transposed solves of the adjoint: x-rows and y-columns in one launch.
-template <typename real, int M>
+// The adjoint's solves (kMode 1: transposed, 2: plain), solutions alone:
+// x-rows and y-columns in one launch.
+template <typename real, int M, int kMode>
 __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines_t(const __grid_constant__ LinePair<real> PA)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
     const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
-    line_solve<real, M, true>(PA.L[fam], line, smem_raw);
+    line_solve<real, M, kMode>(PA.L[fam], line, smem_raw);
 }
 
 // Ensemble: lines of many members and both families in one launch, all of
@@ -1333,22 +1336,35 @@ size_t line_smem_bytes(int n, int nseg)
 }
 
 template <typename real>
-cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, bool transposed);
+cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, int mode);
 
 template <typename real>
 cudaError_t launch_lines(const LinePair<real> &p, cudaStream_t st)
 {
-    return launch_lines_impl(p, st, false);
+    return launch_lines_impl(p, st, 0);
 }
 
 template <typename real>
 cudaError_t launch_lines_transposed(const LinePair<real> &p, cudaStream_t st)
 {
-    return launch_lines_impl(p, st, true);
+    return launch_lines_impl(p, st, 1);
 }
 
 template <typename real>
-cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, bool transposed)
+cudaError_t launch_lines_solution(const LinePair<real> &p, cudaStream_t st)
+{
+    return launch_lines_impl(p, st, 2);
+}
+
+template <typename real, int kMode>
+auto lines_kernel(int sh)
+{
+    return sh == 1 ? k_lines_t<real, 2, kMode> : sh == 2 ? k_lines_t<real, 4, kMode> : sh == 3 ? k_lines_t<real, 8, kMode>
+         : sh == 4 ? k_lines_t<real, 16, kMode> : k_lines_t<real, 32, kMode>;
+}
+
+template <typename real>
+cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, int mode)
 {
     size_t smem = 0;
     int threads = 32;
@@ -1357,8 +1373,8 @@ cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, bool tra
         LinePair<real> a = p, b = p;
         a.L[1].nlines = 0;
         b.L[0].nlines = 0;
-        cudaError_t e = launch_lines_impl<real>(a, st, transposed);
-        return e != cudaSuccess ? e : launch_lines_impl<real>(b, st, transposed);
+        cudaError_t e = launch_lines_impl<real>(a, st, mode);
+        return e != cudaSuccess ? e : launch_lines_impl<real>(b, st, mode);
     }
     for (int f = 0; f < 2; f++) {
         const LineArgs<real> &a = p.L[f];
@@ -1369,17 +1385,17 @@ cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, bool tra
         int t = line_threads(a.n, (int)sizeof(real));
         if (t > threads) threads = t;
     }
-    static int configured[2][6] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
+    static int configured[3][6] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
     const int sh = p.L[0].nlines > 0 ? p.L[0].mshift : p.L[1].mshift;
-    if (sh < 1 || sh > 5) return cudaErrorInvalidValue;
-    auto *kern = transposed ? (sh == 1 ? k_lines_t<real, 2> : sh == 2 ? k_lines_t<real, 4> : sh == 3 ? k_lines_t<real, 8>
-                                                          : sh == 4 ? k_lines_t<real, 16> : k_lines_t<real, 32>)
-                            : (sh == 1 ? k_lines<real, 2> : sh == 2 ? k_lines<real, 4> : sh == 3 ? k_lines<real, 8>
-                                                          : sh == 4 ? k_lines<real, 16> : k_lines<real, 32>);
-    if ((int)smem > configured[transposed][sh]) {
+    if (sh < 1 || sh > 5 || mode < 0 || mode > 2) return cudaErrorInvalidValue;
+    auto *kern = mode == 1 ? lines_kernel<real, 1>(sh)
+               : mode == 2 ? lines_kernel<real, 2>(sh)
+                           : (sh == 1 ? k_lines<real, 2> : sh == 2 ? k_lines<real, 4> : sh == 3 ? k_lines<real, 8>
+                                                       : sh == 4 ? k_lines<real, 16> : k_lines<real, 32>);
+    if ((int)smem > configured[mode][sh]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[transposed][sh] = (int)smem;
+        configured[mode][sh] = (int)smem;
     }
     const int blocks = p.L[0].nlines + p.L[1].nlines;
     if (blocks > 0) kern<<<blocks, threads, smem, st>>>(p);
@@ -1436,6 +1452,7 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
     template cudaError_t launch_stencil<real>(const StencilArgs<real> &, cudaStream_t);                  \
     template cudaError_t launch_lines<real>(const LinePair<real> &, cudaStream_t);                       \
     template cudaError_t launch_lines_transposed<real>(const LinePair<real> &, cudaStream_t);            \
+    template cudaError_t launch_lines_solution<real>(const LinePair<real> &, cudaStream_t);              \
     template size_t line_smem_bytes<real>(int, int);                                                    \
     template cudaError_t launch_ghost_batch<real>(const GhostArgs<real> *, const int *, int, int, int64_t, \
                                                   cudaStream_t);                                        \

@@ -330,3 +330,24 @@ def hump_beach(n: int = 512, seed: int = 5, steps: int = 2000, H: float = 0.5, w
     pick = rng.choice(len(deep), size=ngauges, replace=False)
     gauges = [(int(deep[k][1]), int(deep[k][0])) for k in pick]
     return sc, gauges
+
+
+def hump_beach_target(sc: Scenario, seed: int = 5) -> Scenario:
+    """The run the misfit compares against: the hump_beach scenario with its
+    hump 10 % higher and wider and moved by (8, -6) m, and its bed raised by
+    4 seeded Gaussian bumps offshore (0.1-0.3 m, widths 20-40 m)."""
+    import copy
+    t = copy.deepcopy(sc)
+    n = sc.nx
+    X, Y = np.meshgrid((np.arange(n) + 0.5) * sc.dx, (np.arange(sc.ny) + 0.5) * sc.dy)
+    rng = np.random.default_rng(seed + 3000)
+    for _ in range(4):
+        cx, cy = rng.uniform(0.15, 0.6) * n * sc.dx, rng.uniform(0.2, 0.8) * sc.ny * sc.dy
+        t.z = t.z + rng.uniform(0.1, 0.3) * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / rng.uniform(20, 40) ** 2)
+    hump = np.asarray(sc.w0) - np.maximum(sc.z, sc.ws)
+    amp = float(hump.max())
+    wid = float(np.sqrt(np.sum(hump > amp / np.e) / math.pi))   # radius where the hump falls to 1/e
+    t.w0 = np.maximum(t.z, 1.1 * amp * np.exp(-((X - 0.4 * n * sc.dx - 8.0) ** 2 + (Y - 0.5 * sc.ny * sc.dy + 6.0) ** 2)
+                                              / (1.1 * wid) ** 2))
+    t.name = sc.name + "_target"
+    return t

@@ -1,5 +1,5 @@
 """Discrete adjoint (cel_adjoint_gauge_misfit) vs FP64 finite differences of
-the oracle.
+the oracle, for the gradients with respect to the initial w and the bed z.
 
 The loss is the gauge misfit L = 1/2 sum over steps and gauges of
 (eta - obs)^2.  The step is piecewise smooth: the generalized minmod, the
@@ -11,7 +11,11 @@ state is away from kinks: a tilted free surface with a steady discharge
 quadratic friction, a sponge, a sine maker, walls, the Euler start-up and
 the AB3 history.  There <dL/dw0, v> from the GPU adjoint must match the
 oracle's central difference (L(w0 + e v) - L(w0 - e v)) / 2e within 1e-3
-relative for seeded smooth directions v.  A beach with dry land and a moving
+relative for seeded smooth directions v, and <dL/dz, v> the difference of
+L(z + e v) and L(z - e v) at fixed w0.  Shallow water without a sponge or a
+wave maker is unchanged when w and z move up together, so there
+sum(dL/dw0 + dL/dz) equals the summed misfit exactly, dry land included.
+A beach with dry land and a moving
 shoreline checks the rest: checkpoint spacing changes nothing, the loss and
 the gauge records equal the oracle's, land far from the water gets a zero
 gradient; FP32 agrees with FP64 on the kink-free state.
@@ -57,12 +61,14 @@ def _oracle_loss(s, w0, gauges, obs):
     return 0.5 * float(np.sum((eta - obs) ** 2)), eta
 
 
-def _gpu_gradient(s, gauges, obs, prec="f64", ckpt=7):
+def _gpu_gradient(s, gauges, obs, prec="f64", ckpt=7, bed=False):
     from paper_1611_05984_gb300 import celeris
     dtype = torch.float64 if prec == "f64" else torch.float32
     g = celeris.from_scenario(s, dtype=dtype)
-    loss, eta, grad = celeris.gauge_misfit_gradient(g, s.steps, gauges, torch.as_tensor(obs, dtype=dtype), ckpt)
-    return loss, eta.double().cpu().numpy(), grad.double().cpu().numpy(), g
+    out = celeris.gauge_misfit_gradient(g, s.steps, gauges, torch.as_tensor(obs, dtype=dtype), ckpt, bed=bed)
+    loss, eta, grad = out[:3]
+    res = (loss, eta.double().cpu().numpy(), grad.double().cpu().numpy(), g)
+    return res + (out[3].double().cpu().numpy(),) if bed else res
 
 
 def _tilted(nsteps=15):
@@ -149,6 +155,11 @@ def test_adjoint_checkpoint_spacing_and_fp32():
     # measured 2.4e-3: FP32 reciprocals and square roots are the fast ~2 ulp
     # ones, and the gradient is more sensitive to rounding than the state
     assert np.linalg.norm(h32 - h64) <= 5e-3 * np.linalg.norm(h64)
+    b, bg, _, _ = _tilted_bed(0, 1, 2)
+    obs_b = np.zeros((b.steps, len(bg)))
+    _, _, _, _, z64 = _gpu_gradient(b, bg, obs_b, ckpt=4, bed=True)
+    _, _, _, _, z32 = _gpu_gradient(b, bg, obs_b, prec="f32", ckpt=4, bed=True)
+    assert np.linalg.norm(z32 - z64) <= 1e-2 * np.linalg.norm(z64)
 
 
 def test_autograd_function_and_rejections():
@@ -165,6 +176,14 @@ def test_autograd_function_and_rejections():
     bed = g.field("Bbar").double().cpu().numpy()
     want = np.where(s.w0 > bed, ref, 0.0)
     np.testing.assert_allclose(w0.grad.cpu().numpy(), want, rtol=1e-9, atol=1e-14)
+    # with the bed as a second input
+    w1 = torch.tensor(s.w0, dtype=torch.float64, device="cuda", requires_grad=True)
+    zt = torch.tensor(s.z, dtype=torch.float64, device="cuda", requires_grad=True)
+    L2 = celeris.gauge_misfit(w1, g, zero, zero, s.steps, gauges, torch.as_tensor(obs), 5, z=zt)
+    (3.0 * L2).backward()
+    _, _, _, _, refz = _gpu_gradient(s, gauges, obs, ckpt=5, bed=True)
+    np.testing.assert_allclose(zt.grad.cpu().numpy(), 3.0 * refz, rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(w1.grad.cpu().numpy(), 3.0 * want, rtol=1e-9, atol=1e-14)
     b = celeris.from_scenario(sc.beach(nx=64, ny=48, sponge=8), dtype=torch.float64)
     with pytest.raises(celeris.CelerisError):                       # a gauge off the grid
         celeris.gauge_misfit_gradient(b, 5, [(64, 3)], torch.zeros((5, 1), dtype=torch.float64))
@@ -248,6 +267,83 @@ def test_adjoint_corrector_matches_oracle_away_from_kinks(model):
         assert abs(ad - fd) <= 1e-3 * abs(fd), (ad, fd)
 
 
+def _oracle_loss_bed(s, z, gauges, obs):
+    import dataclasses
+    o = oracle_from(dataclasses.replace(s, z=z))
+    _, P, Q = s.initial_state()
+    o.set_state(s.w0, P, Q)
+    o.set_gauges(gauges, 1, s.steps)
+    o.step(s.steps)
+    return 0.5 * float(np.sum((o.read_gauges(s.steps) - obs) ** 2))
+
+
+def _tilted_bed(model, K, friction, nsteps=10):
+    """The kink-free tilted state over a sloping, undulating bed (depth 0.35
+    to 0.6 m, wet everywhere), sponge on the east, walls elsewhere."""
+    s, gauges, X, Y = _tilted_bsnq(model, nsteps=nsteps, K=K)
+    s.friction = friction
+    xs, ys = X / (s.nx * s.dx), Y / (s.ny * s.dy)
+    s.z = -0.5 + 0.08 * xs + 0.04 * ys ** 2 + 0.01 * np.sin(2 * math.pi * X / 6.0) * np.cos(2 * math.pi * Y / 9.0)
+    return s, gauges, X, Y
+
+
+@pytest.mark.parametrize("model,K,friction", [(0, 0, 2), (0, 1, 1), (1, 1, 2)],
+                         ids=["bsnq-K0-manning", "bsnq-K1-quadratic", "nlsw-K1-manning"])
+def test_bed_gradient_matches_oracle_away_from_kinks(model, K, friction):
+    """dL/dz: the face beds of the reconstruction and the flux, the bed slope,
+    friction, the dispersive and mixed terms' depth and the line systems'
+    rows (Eq. 23), through the corners to the cell-centre bed."""
+    s, gauges, X, Y = _tilted_bed(model, K, friction)
+    rng = np.random.default_rng(21 + model + 2 * K)
+    obs = 0.01 * rng.standard_normal((s.steps, len(gauges)))
+    loss, _, _, _, gz = _gpu_gradient(s, gauges, obs, ckpt=3, bed=True)
+    assert abs(loss - _oracle_loss_bed(s, s.z, gauges, obs)) <= 1e-9 * loss
+    # bed perturbations of 1e-7 m: the loss's rounding over the run (about
+    # 1e-15 L) stays 4 orders below the difference
+    eps = 1e-5
+    errs = []
+    for _ in range(5):
+        v = np.zeros_like(X)
+        for _ in range(3):
+            cx, cy = rng.uniform(2.0, 22.0), rng.uniform(2.0, 16.0)
+            v += rng.standard_normal() * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / rng.uniform(2.0, 8.0))
+        v *= 1e-2
+        fd = (_oracle_loss_bed(s, s.z + eps * v, gauges, obs) - _oracle_loss_bed(s, s.z - eps * v, gauges, obs)) / (2 * eps)
+        ad = float(np.sum(gz * v))
+        errs.append(abs(ad - fd) / abs(fd))
+    assert max(errs) <= 1e-3, errs
+
+
+def test_bed_gradient_vertical_shift_identity_with_dry_land():
+    """Shallow water (K = 1, Manning friction, walls, a beach with dry land):
+    moving the given w0 and z up by c moves eta by c at every gauge and
+    changes nothing else.  On dry cells w0 is the cell bed (the clamp), a
+    path dL/dz already holds, so sum(dL/dw0 over wet cells) + sum(dL/dz) =
+    sum over steps and gauges of (eta - obs)."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    nx, ny, dx = 48, 32, 0.5
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
+    z = np.maximum(-0.5, (X - 17.0) * 0.1)
+    dt = 0.1 * dx / math.sqrt(9.81 * 0.5)
+    s = sc.flat_basin(nx, ny, dx, 0.5, dt, model=1, K=1, friction=2, fcoef=0.02, eps=1e-8)
+    s.z = z
+    s.w0 = np.maximum(z, 0.05 * np.exp(-((X - 9.0) ** 2 + (Y - 8.0) ** 2) / 6.0))
+    s.steps = 30
+    rng = np.random.default_rng(13)
+    gauges = [(int(rng.integers(4, 30)), int(rng.integers(3, ny - 3))) for _ in range(5)]
+    obs = 0.005 * rng.standard_normal((s.steps, len(gauges)))
+    loss, eta, gw, g, gz = _gpu_gradient(s, gauges, obs, ckpt=4, bed=True)
+    bed = g.field("Bbar").double().cpu().numpy()
+    wet = s.w0 > bed
+    assert np.any(~wet) and np.any(gw[~wet] != 0.0)   # the shoreline's dry cells do matter
+    want = float(np.sum(eta - obs))
+    assert abs(float(np.sum(gw[wet]) + np.sum(gz)) - want) <= 1e-9 * np.sum(np.abs(eta - obs))
+    # and the bed's gradient is not the trivial one: dry land follows the bed
+    # (the clamp), the wet bed carries the rest
+    land = z > 0.5
+    assert np.all(gz[land] == 0.0) and np.linalg.norm(gz) > 0
+
+
 def test_adjoint_corrector_beach_with_dry_land():
     """K = 1 Boussinesq on a beach with dry land (dx = 0.5 m, depth/dx <=
     1): loss and records equal the oracle's, checkpoint spacing changes
@@ -265,12 +361,13 @@ def test_adjoint_corrector_beach_with_dry_land():
     rng = np.random.default_rng(12)
     gauges = [(int(rng.integers(4, 30)), int(rng.integers(3, ny - 3))) for _ in range(5)]
     obs = 0.005 * rng.standard_normal((s.steps, len(gauges)))
-    loss, eta, g4, g = _gpu_gradient(s, gauges, obs, ckpt=4)
+    loss, eta, g4, g, z4 = _gpu_gradient(s, gauges, obs, ckpt=4, bed=True)
     lo, eta_o = _oracle_loss(s, s.w0, gauges, obs)
     assert abs(loss - lo) <= 1e-9 * abs(lo)
     np.testing.assert_allclose(eta, eta_o, rtol=0, atol=1e-11)
-    _, _, g30, _ = _gpu_gradient(s, gauges, obs, ckpt=30)
+    _, _, g30, _, z30 = _gpu_gradient(s, gauges, obs, ckpt=30, bed=True)
     assert np.linalg.norm(g4 - g30) <= 1e-10 * np.linalg.norm(g30)
+    assert np.linalg.norm(z4 - z30) <= 1e-10 * np.linalg.norm(z30)
     land = z > 0.5
-    assert np.any(land) and np.all(g4[land] == 0.0)
-    assert np.linalg.norm(g4) > 0
+    assert np.any(land) and np.all(g4[land] == 0.0) and np.all(z4[land] == 0.0)
+    assert np.linalg.norm(g4) > 0 and np.all(np.isfinite(z4)) and np.linalg.norm(z4) > 0
