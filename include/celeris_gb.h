@@ -242,6 +242,20 @@ cel_status cel_adjoint_gauge_misfit(cel_solver *s, int32_t nsteps, int32_t ckpt_
                                     size_t scratch_bytes, void *eta_dev, void *grad_w_dev, void *grad_z_dev,
                                     double *loss);
 
+/* Self-check of the adjoint's face-flux derivative (Sec. 2.2, Eq. 14): the
+ * reverse sweep uses a hand-written vector-Jacobian product of the KP07
+ * reconstruction and central-upwind flux; this evaluates it beside the
+ * dual-number product of the forward's own flux code on caller-chosen
+ * faces.  in_dev: [n][22] real, device (real_bytes 4 or 8), per face, in
+ * order: the 4 cells' w[4], P[4], Q[4] (cells f-2..f+1), the face beds Bm,
+ * Bf, Bp, the flux adjoints lH[3] (mass, normal, tangential momentum),
+ * theta, g, eps and dir (0: x-face, P normal; 1: y-face, Q normal).  out_dev:
+ * [n][30] real, device: the adjoints of (w[4], P[4], Q[4], Bm, Bf, Bp) by
+ * dual numbers, then by hand.  cuda_stream as in cel_create.  Synchronises;
+ * CEL_ERR_CUDA on a CUDA error, CEL_ERR_INVALID_ARG on bad arguments. */
+cel_status cel_adjoint_face_selfcheck(int32_t real_bytes, const void *in_dev, int32_t n, void *out_dev,
+                                      void *cuda_stream);
+
 /* Kernel launches issued by the most recent cel_step call. */
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);
 

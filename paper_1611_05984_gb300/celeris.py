@@ -32,7 +32,7 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
            "cel_load_checkpoint", "cel_runup_enable", "cel_render", "cel_adjoint_bytes",
-           "cel_adjoint_gauge_misfit", "cel_last_launch_count", "cel_profile_enable",
+           "cel_adjoint_gauge_misfit", "cel_adjoint_face_selfcheck", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
         L.cel_adjoint_bytes.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(sz)]
         L.cel_adjoint_gauge_misfit.argtypes = [vp, i32, i32, ctypes.POINTER(i32), i32, vp, vp, sz, vp, vp, vp,
                                                ctypes.POINTER(d)]
+        L.cel_adjoint_face_selfcheck.argtypes = [i32, vp, i32, vp, vp]
         L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_profile_enable.argtypes = [vp, i32]
         L.cel_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
@@ -461,6 +462,23 @@ def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every
                                            grad_z.data_ptr() if bed else None, ctypes.byref(loss))
     solver._check(st, "adjoint_gauge_misfit")
     return (loss.value, eta, grad, grad_z) if bed else (loss.value, eta, grad)
+
+
+def face_vjp_selfcheck(inputs):
+    """The adjoint's face-flux VJP by dual numbers and by hand on the faces
+    in `inputs` ([n, 22] device tensor, float32 or float64; the column order
+    of cel_adjoint_face_selfcheck).  Returns ([n, 15], [n, 15])."""
+    import torch
+    x = inputs.contiguous()
+    if x.dim() != 2 or x.shape[1] != 22 or x.dtype not in (torch.float32, torch.float64) or not x.is_cuda:
+        raise ValueError("inputs must be an [n, 22] float32/float64 CUDA tensor")
+    out = torch.empty((x.shape[0], 30), dtype=x.dtype, device=x.device)
+    lib = load()
+    st = lib.cel_adjoint_face_selfcheck(x.element_size(), x.data_ptr(), x.shape[0], out.data_ptr(),
+                                        torch.cuda.current_stream(x.device).cuda_stream)
+    if st != 0:
+        raise CelerisError(f"face_vjp_selfcheck failed ({st})")
+    return out[:, :15], out[:, 15:]
 
 
 def _gauge_misfit_function():

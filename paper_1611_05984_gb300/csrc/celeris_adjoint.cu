@@ -168,6 +168,179 @@ __device__ __forceinline__ void face_flux(const Dual<T> w[4], const Dual<T> P[4]
         cu_flux(Dual<T>(g), Dual<T>(eps), hiL[0], hiL[2], hiL[1], loR[0], loR[2], loR[1], Bf, H);
 }
 
+// The same flux's vector-Jacobian product by hand (reverse mode): one pass
+// forward keeping the branch each max, min, minmod and positivity test took
+// (ties resolved as the dual numbers resolve them: fmax keeps its first
+// argument when equal, fmin too, sqrt has derivative 0 at 0), then the
+// adjoints back through every operation.  Outputs: the adjoints of the 4
+// cells' (w, P, Q) and of the three face beds (Bm, Bf, Bp), added to.
+template <typename T>
+__device__ __forceinline__ int minmod3_sel(T th, T qm, T q0, T qp)
+{
+    const T a = th * (q0 - qm), b = T(0.5) * (qp - qm), c = th * (qp - q0);
+    const int ilo_bc = b <= c ? 2 : 3, ihi_bc = b >= c ? 2 : 3;
+    const T lo_bc = b <= c ? b : c, hi_bc = b >= c ? b : c;
+    const int ilo = a <= lo_bc ? 1 : ilo_bc, ihi = a >= hi_bc ? 1 : ihi_bc;
+    const T lo = a <= lo_bc ? a : lo_bc, hi = a >= hi_bc ? a : hi_bc;
+    return lo > T(0) ? ilo : (hi < T(0) ? ihi : 0);
+}
+
+template <typename T>
+__device__ __forceinline__ T slope_of(int sel, T th, T qm, T q0, T qp)
+{
+    return sel == 1 ? th * (q0 - qm) : sel == 2 ? T(0.5) * (qp - qm) : sel == 3 ? th * (qp - q0) : T(0);
+}
+
+// adjoint ls of the selected slope into its three cells
+template <typename T>
+__device__ __forceinline__ void slope_vjp(int sel, T th, T ls, T &lqm, T &lq0, T &lqp)
+{
+    if (sel == 1) { lqm -= th * ls; lq0 += th * ls; }
+    else if (sel == 2) { lqm -= T(0.5) * ls; lqp += T(0.5) * ls; }
+    else if (sel == 3) { lq0 -= th * ls; lqp += th * ls; }
+}
+
+// dk/dh of desing (Eq. 14) with its branch of max(h^4, eps)
+template <typename T>
+__device__ __forceinline__ T desing_dh(T h, T eps)
+{
+    const T h2 = h * h, h4 = h2 * h2;
+    const bool sel = h4 >= eps;
+    const T r = rsqrt(h4 + (sel ? h4 : eps));
+    return T(1.4142135623730951) * r * (T(1) - T(2) * h4 * r * r * (sel ? T(2) : T(1)));
+}
+
+template <typename T>
+__device__ __forceinline__ void face_flux_vjp(const T w[4], const T P[4], const T Q[4], T Bm, T Bf, T Bp, T th, T g,
+                                              T eps, int dir, const T lH[3], T lw[4], T lP[4], T lQ[4], T lB[3])
+{
+    // reconstruction: left cell 1 (its high face), right cell 2 (its low face)
+    int sw[2], sP[2], sQ[2], fix[2];   // fix: 0 none, 1 high face clamped, 2 low face clamped
+    T f[2][3];                          // hiL and loR in (w, P, Q)
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const T Blo = c == 0 ? Bm : Bf, Bhi = c == 0 ? Bf : Bp;
+        sw[c] = minmod3_sel(th, w[c], w[c + 1], w[c + 2]);
+        sP[c] = minmod3_sel(th, P[c], P[c + 1], P[c + 2]);
+        sQ[c] = minmod3_sel(th, Q[c], Q[c + 1], Q[c + 2]);
+        const T s0 = slope_of(sw[c], th, w[c], w[c + 1], w[c + 2]);
+        const T lo0 = w[c + 1] - T(0.5) * s0, hi0 = w[c + 1] + T(0.5) * s0;
+        fix[c] = hi0 < Bhi ? 1 : (lo0 < Blo ? 2 : 0);
+        const T v0 = c == 0 ? (fix[c] == 1 ? Bhi : fix[c] == 2 ? T(2) * w[1] - Blo : hi0)
+                            : (fix[c] == 1 ? T(2) * w[2] - Bhi : fix[c] == 2 ? Blo : lo0);
+        const T sgn = c == 0 ? T(0.5) : T(-0.5);
+        f[c][0] = v0;
+        f[c][1] = P[c + 1] + sgn * slope_of(sP[c], th, P[c], P[c + 1], P[c + 2]);
+        f[c][2] = Q[c + 1] + sgn * slope_of(sQ[c], th, Q[c], Q[c + 1], Q[c + 2]);
+    }
+    // central-upwind flux on (w, normal, tangential)
+    const int nv = dir == 0 ? 1 : 2, tv = dir == 0 ? 2 : 1;
+    const T wL = f[0][0], nL = f[0][nv], tL = f[0][tv], wR = f[1][0], nR = f[1][nv], tR = f[1][tv];
+    const T aL = wL - Bf, aR = wR - Bf;
+    const bool pL = aL >= T(0), pR = aR >= T(0);
+    const T hL = pL ? aL : T(0), hR = pR ? aR : T(0);
+    const T kL = desing(hL, eps), kR = desing(hR, eps);
+    const T uL = kL * nL, vL = kL * tL, uR = kR * nR, vR = kR * tR;
+    const T qnL = hL * uL, qtL = hL * vL, qnR = hR * uR, qtR = hR * vR;
+    const T sL = sqrt(g * hL), sR = sqrt(g * hR);
+    const T ap1c = uL + sL, ap2c = uR + sR, am1c = uL - sL, am2c = uR - sR;
+    const bool apL = ap1c >= ap2c, amL = am1c <= am2c;
+    const T ap1 = apL ? ap1c : ap2c, am1 = amL ? am1c : am2c;
+    const bool apK = ap1 >= T(0), amK = am1 <= T(0);
+    const T ap = apK ? ap1 : T(0), am = amK ? am1 : T(0);
+    const T den = ap - am;
+    if (!(den > T(0))) return;
+    const T inv = T(1) / den, apam = ap * am;
+    const T FL1 = qnL * uL + T(0.5) * g * hL * hL, FR1 = qnR * uR + T(0.5) * g * hR * hR;
+    const T N0 = ap * qnL - am * qnR + apam * (wR - wL);
+    const T N1 = ap * FL1 - am * FR1 + apam * (qnR - qnL);
+    const T N2 = ap * (qnL * vL) - am * (qnR * vR) + apam * (qtR - qtL);
+    // reverse
+    const T lN0 = lH[0] * inv, lN1 = lH[1] * inv, lN2 = lH[2] * inv;
+    const T lden = -(lH[0] * N0 + lH[1] * N1 + lH[2] * N2) * inv * inv;
+    const T lapam = lN0 * (wR - wL) + lN1 * (qnR - qnL) + lN2 * (qtR - qtL);
+    const T lap = lN0 * qnL + lN1 * FL1 + lN2 * (qnL * vL) + lapam * am + lden;
+    const T lam = -(lN0 * qnR) - lN1 * FR1 - lN2 * (qnR * vR) + lapam * ap - lden;
+    const T lFL1 = lN1 * ap, lFR1 = -(lN1 * am);
+    T lqnL = lN0 * ap - lN1 * apam + lN2 * ap * vL + lFL1 * uL;
+    T lqnR = -(lN0 * am) + lN1 * apam - lN2 * am * vR + lFR1 * uR;
+    T lvL = lN2 * ap * qnL, lvR = -(lN2 * am * qnR);
+    const T lqtL = -(lN2 * apam), lqtR = lN2 * apam;
+    T lwL = -(lN0 * apam), lwR = lN0 * apam;
+    T luL = lFL1 * qnL, luR = lFR1 * qnR;
+    T lhL = lFL1 * g * hL, lhR = lFR1 * g * hR;
+    T lsL = T(0), lsR = T(0);
+    if (apK) {
+        if (apL) { luL += lap; lsL += lap; }
+        else { luR += lap; lsR += lap; }
+    }
+    if (amK) {
+        if (amL) { luL += lam; lsL -= lam; }
+        else { luR += lam; lsR -= lam; }
+    }
+    if (sL > T(0)) lhL += lsL * g / (T(2) * sL);
+    if (sR > T(0)) lhR += lsR * g / (T(2) * sR);
+    lhL += lqnL * uL + lqtL * vL;
+    luL += lqnL * hL;
+    lvL += lqtL * hL;
+    lhR += lqnR * uR + lqtR * vR;
+    luR += lqnR * hR;
+    lvR += lqtR * hR;
+    const T lkL = luL * nL + lvL * tL, lkR = luR * nR + lvR * tR;
+    T lf[2][3];
+    lf[0][nv] = luL * kL;
+    lf[0][tv] = lvL * kL;
+    lf[1][nv] = luR * kR;
+    lf[1][tv] = lvR * kR;
+    lhL += lkL * desing_dh(hL, eps);
+    lhR += lkR * desing_dh(hR, eps);
+    const T laL = pL ? lhL : T(0), laR = pR ? lhR : T(0);
+    lf[0][0] = lwL + laL;
+    lf[1][0] = lwR + laR;
+    lB[1] -= laL + laR;
+    // reconstruction reversed
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const T sgn = c == 0 ? T(0.5) : T(-0.5);
+        const T lv = lf[c][0];
+        const int bl = c == 0 ? 0 : 1, bh = c == 0 ? 1 : 2;   // indices of Blo, Bhi in lB
+        if (c == 0) {
+            if (fix[c] == 1) lB[bh] += lv;
+            else if (fix[c] == 2) { lw[1] += T(2) * lv; lB[bl] -= lv; }
+            else { lw[1] += lv; slope_vjp(sw[c], th, sgn * lv, lw[0], lw[1], lw[2]); }
+        } else {
+            if (fix[c] == 1) { lw[2] += T(2) * lv; lB[bh] -= lv; }
+            else if (fix[c] == 2) lB[bl] += lv;
+            else { lw[2] += lv; slope_vjp(sw[c], th, sgn * lv, lw[1], lw[2], lw[3]); }
+        }
+        lP[c + 1] += lf[c][1];
+        slope_vjp(sP[c], th, sgn * lf[c][1], lP[c], lP[c + 1], lP[c + 2]);
+        lQ[c + 1] += lf[c][2];
+        slope_vjp(sQ[c], th, sgn * lf[c][2], lQ[c], lQ[c + 1], lQ[c + 2]);
+    }
+}
+
+// The dual-number VJP of the same flux, one input direction at a time: the
+// reference the hand-written reverse is checked against.
+template <typename T>
+__device__ __forceinline__ void face_flux_vjp_dual(const T w[4], const T P[4], const T Q[4], T Bm, T Bf, T Bp, T th,
+                                                   T g, T eps, int dir, const T lH[3], T out[15])
+{
+    for (int k = 0; k < 15; k++) {
+        Dual<T> dw[4], dP[4], dQ[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            dw[q] = Dual<T>(w[q], k == q ? T(1) : T(0));
+            dP[q] = Dual<T>(P[q], k == 4 + q ? T(1) : T(0));
+            dQ[q] = Dual<T>(Q[q], k == 8 + q ? T(1) : T(0));
+        }
+        Dual<T> H[3];
+        face_flux(dw, dP, dQ, Dual<T>(Bm, k == 12 ? T(1) : T(0)), Dual<T>(Bf, k == 13 ? T(1) : T(0)),
+                  Dual<T>(Bp, k == 14 ? T(1) : T(0)), th, g, eps, dir, H);
+        out[k] = lH[0] * H[0].d + lH[1] * H[1].d + lH[2] * H[2].d;
+    }
+}
+
 // Index of cell (i, j), i in [-1, nx], j in [-1, ny], in the ring arrays.
 __device__ __forceinline__ size_t ring_index(const Geo &G, int i, int j)
 {
@@ -388,19 +561,25 @@ __global__ void k_adj_faces(AdjArgs<real> A, int dir)
                         : real(0.5) * (corner(A.Bc, G, line, q) + corner(A.Bc, G, line + 1, q));
     };
     const real Bm = face_bed(f - 1), Bf = face_bed(f), Bp = face_bed(f + 1);
-    if (A.lBc) {   // the three face beds, each the mean of its two corners
-        for (int b = 0; b < 3; b++) {
-            Dual<real> w[4], P[4], Q[4];
+    real w[4], P[4], Q[4], lw[4] = {0, 0, 0, 0}, lP[4] = {0, 0, 0, 0}, lQ[4] = {0, 0, 0, 0}, lB[3] = {0, 0, 0};
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                w[q] = Dual<real>(s[q].v[0]);
-                P[q] = Dual<real>(s[q].v[1]);
-                Q[q] = Dual<real>(s[q].v[2]);
-            }
-            Dual<real> H[3];
-            face_flux(w, P, Q, Dual<real>(Bm, b == 0 ? real(1) : real(0)), Dual<real>(Bf, b == 1 ? real(1) : real(0)),
-                      Dual<real>(Bp, b == 2 ? real(1) : real(0)), A.c.theta, A.c.g, A.c.eps, dir, H);
-            const real gsum = real(0.5) * (lH[0] * H[0].d + lH[1] * H[1].d + lH[2] * H[2].d);
+    for (int q = 0; q < 4; q++) {
+        w[q] = s[q].v[0];
+        P[q] = s[q].v[1];
+        Q[q] = s[q].v[2];
+    }
+    face_flux_vjp(w, P, Q, Bm, Bf, Bp, A.c.theta, A.c.g, A.c.eps, dir, lH, lw, lP, lQ, lB);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        if (s[c].idx < 0) continue;
+        if (lw[c] != real(0)) atomicAdd(A.lw + s[c].idx, lw[c]);
+        if (lP[c] != real(0)) atomicAdd(A.lP + s[c].idx, s[c].sgn[1] * lP[c]);
+        if (lQ[c] != real(0)) atomicAdd(A.lQ + s[c].idx, s[c].sgn[2] * lQ[c]);
+    }
+    if (A.lBc) {   // the three face beds, each the mean of its two corners
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const real gsum = real(0.5) * lB[b];
             if (gsum != real(0)) {
                 const int q = f - 1 + b;
                 atomicAdd(A.lBc + (dir == 0 ? corner_index(G, q, line) : corner_index(G, line, q)), gsum);
@@ -408,25 +587,28 @@ __global__ void k_adj_faces(AdjArgs<real> A, int dir)
             }
         }
     }
-    for (int c = 0; c < 4; c++) {
-        if (s[c].idx < 0) continue;
-        for (int v = 0; v < 3; v++) {
-            Dual<real> w[4], P[4], Q[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                w[q] = Dual<real>(s[q].v[0], q == c && v == 0 ? real(1) : real(0));
-                P[q] = Dual<real>(s[q].v[1], q == c && v == 1 ? real(1) : real(0));
-                Q[q] = Dual<real>(s[q].v[2], q == c && v == 2 ? real(1) : real(0));
-            }
-            Dual<real> H[3];
-            face_flux(w, P, Q, Dual<real>(Bm), Dual<real>(Bf), Dual<real>(Bp), A.c.theta, A.c.g, A.c.eps, dir, H);
-            const real gsum = lH[0] * H[0].d + lH[1] * H[1].d + lH[2] * H[2].d;
-            if (gsum != real(0)) {
-                real *dst = v == 0 ? A.lw : (v == 1 ? A.lP : A.lQ);
-                atomicAdd(dst + s[c].idx, s[c].sgn[v] * gsum);
-            }
-        }
+}
+
+// Self-check of the hand-written flux VJP against the dual numbers: per
+// face 22 inputs (w[4], P[4], Q[4], Bm, Bf, Bp, lH[3], theta, g, eps, dir)
+// and 30 outputs (the 15 adjoints by dual numbers, then by hand).
+template <typename real>
+__global__ void k_face_vjp_check(const real *in, int n, real *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const real *x = in + (size_t)k * 22;
+    real *o = out + (size_t)k * 30;
+    const int dir = x[21] != real(0) ? 1 : 0;
+    face_flux_vjp_dual(x, x + 4, x + 8, x[12], x[13], x[14], x[18], x[19], x[20], dir, x + 15, o);
+    real lw[4] = {0, 0, 0, 0}, lP[4] = {0, 0, 0, 0}, lQ[4] = {0, 0, 0, 0}, lB[3] = {0, 0, 0};
+    face_flux_vjp(x, x + 4, x + 8, x[12], x[13], x[14], x[18], x[19], x[20], dir, x + 15, lw, lP, lQ, lB);
+    for (int q = 0; q < 4; q++) {
+        o[15 + q] = lw[q];
+        o[19 + q] = lP[q];
+        o[23 + q] = lQ[q];
     }
+    for (int b = 0; b < 3; b++) o[27 + b] = lB[b];
 }
 
 // Eq. 10-13 transposed: the dispersive eta terms of F and G and the mixed
@@ -686,6 +868,13 @@ cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st)
 }
 
 template <typename real>
+cudaError_t launch_face_vjp_check(const real *in, int n, real *out, cudaStream_t st)
+{
+    k_face_vjp_check<real><<<(n + 127) / 128, 128, 0, st>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, cudaStream_t st)
 {
     dim3 b(32, 8);
@@ -751,6 +940,7 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
     template cudaError_t launch_adjoint_add<real>(const AdjArgs<real> &, const real *, const real *,      \
                                                   const real *, cudaStream_t);                          \
     template cudaError_t launch_adjoint_pack<real>(const AdjArgs<real> &, real *, real *, int, cudaStream_t); \
+    template cudaError_t launch_face_vjp_check<real>(const real *, int, real *, cudaStream_t);            \
     template cudaError_t launch_adjoint_tri_bed<real>(const AdjArgs<real> &, const real *, const real *,   \
                                                       cudaStream_t);                                   \
     template cudaError_t launch_adjoint_bed_final<real>(const AdjArgs<real> &, const real *, const real *, \

@@ -1866,6 +1866,18 @@ cel_status adjoint_check(const cel_solver *, int N, int C, int ng, std::string &
 
 extern "C" {
 
+cel_status cel_adjoint_face_selfcheck(int32_t real_bytes, const void *in_dev, int32_t n, void *out_dev,
+                                      void *cuda_stream)
+{
+    if ((real_bytes != 4 && real_bytes != 8) || n < 0 || (n > 0 && (!in_dev || !out_dev))) return CEL_ERR_INVALID_ARG;
+    if (n == 0) return CEL_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = real_bytes == 4 ? launch_face_vjp_check<float>((const float *)in_dev, n, (float *)out_dev, st)
+                                    : launch_face_vjp_check<double>((const double *)in_dev, n, (double *)out_dev, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? CEL_OK : CEL_ERR_CUDA;
+}
+
 cel_status cel_adjoint_bytes(const cel_solver *s, int32_t nsteps, int32_t ckpt_every, int32_t ngauges,
                              int32_t with_bed, size_t *bytes)
 {

@@ -245,6 +245,10 @@ cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const 
 template <typename real>
 cudaError_t launch_adjoint_bed_final(const AdjArgs<real> &a, const real *w0, const real *lw0, real *grad_z,
                                      cudaStream_t st);
+// Self-check of the face flux's hand-written VJP against dual numbers
+// (inputs [n][22], outputs [n][30]; see cel_adjoint_face_selfcheck).
+template <typename real>
+cudaError_t launch_face_vjp_check(const real *in, int n, real *out, cudaStream_t st);
 // lw += xw, lP += xP, lQ += xQ
 template <typename real>
 cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
