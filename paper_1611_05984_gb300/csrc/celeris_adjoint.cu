@@ -90,6 +90,7 @@ template <typename real>
 struct Src {
     real v[3];
     int idx;          // interior cell, -1 for a constant ghost
+    int ci, cj;       // its coordinates
     real sgn[3];
 };
 
@@ -117,6 +118,8 @@ __device__ __forceinline__ Src<real> source(const AdjArgs<real> &A, int i, int j
     }
     if (side >= 0) s.sgn[dir == 0 ? 1 : 2] = real(-1);   // the normal discharge is negated
     s.idx = sj * G.nx + si;
+    s.ci = si;
+    s.cj = sj;
     s.v[0] = A.w[s.idx];
     s.v[1] = s.sgn[1] * A.P[s.idx];
     s.v[2] = s.sgn[2] * A.Q[s.idx];
@@ -148,6 +151,30 @@ __device__ __forceinline__ Src<real> source2d(const AdjArgs<real> &A, int i, int
     s.v[2] = -s.v[2];
     s.sgn[2] = -s.sgn[2];
     return s;
+}
+
+// Where a cell of the ring source2d reads comes from, without its values:
+// the interior cell it mirrors and the signs, or idx = -1 for a sine-maker
+// ghost (the same cases as source and source2d).
+template <typename real>
+__device__ __forceinline__ void mirror2d(const Geo &G, int sine, int i, int j, Src<real> &s)
+{
+    s.sgn[0] = s.sgn[1] = s.sgn[2] = real(1);
+    s.idx = -1;
+    int si = i, sj = j;
+    if (j < 0 || j >= G.ny) {   // a y-ghost: the mirrored row's cell, Q negated
+        if ((sine >> (j < 0 ? 2 : 3)) & 1) return;
+        sj = j < 0 ? -1 - j : 2 * G.ny - 1 - j;
+        s.sgn[2] = real(-1);
+    }
+    if (i < 0 || i >= G.nx) {   // an x-ghost: P negated
+        if ((sine >> (i < 0 ? 0 : 1)) & 1) return;
+        si = i < 0 ? -1 - i : 2 * G.nx - 1 - i;
+        s.sgn[1] = real(-1);
+    }
+    s.ci = si;
+    s.cj = sj;
+    s.idx = sj * G.nx + si;
 }
 
 // Flux through x-face f (dir 0: between cells f-1 and f of row `line`) or
@@ -410,90 +437,15 @@ __global__ void k_adj_add(AdjArgs<real> A, const real *xw, const real *xP, const
     A.lQ[k] += xQ[k];
 }
 
-// Step 2: the transposed line solves, one thread per line (Thomas, in the
-// scratch array).  The forward solves T x = r with the Eq. 23 rows
-// a_k x_{k-1} + b_k x_k + c_k x_{k+1} and their boundary rows (Reading
-// A-B2); here T^T y = mu, whose row k is c_{k-1} y_{k-1} + b_k y_k +
-// a_{k+1} y_{k+1}.
-template <typename real>
-__global__ void k_adj_lines_t(AdjArgs<real> A, int dir)
+// Bed slope and friction (Eq. 9-10, 31-32) at cell (i, j): no neighbours.
+template <typename real, typename Acc>
+__device__ __forceinline__ void cell_vjp(const AdjArgs<real> &A, int i, int j, const Acc &acc)
 {
     const Geo &G = A.geo;
-    const int n = dir == 0 ? G.nx : G.ny, nl = dir == 0 ? G.ny : G.nx;
-    const int line = blockIdx.x * blockDim.x + threadIdx.x;
-    if (line >= nl) return;
-    auto at = [&](int k) { return dir == 0 ? line * G.nx + k : k * G.nx + line; };
-    auto dcell = [&](int k) {
-        const int i = dir == 0 ? k : line, j = dir == 0 ? line : k;
-        return fmax(A.c.ws - bbar_at(A.Bc, G, i, j), real(0));
-    };
-    const double h = dir == 0 ? G.dx : G.dy;   // the forward's constants, rounded once
-    const real rh2 = real(1.0 / (h * h)), hrh = real(0.5 / h), srh = real(1.0 / (6.0 * h));
-    const int lo_side = dir == 0 ? 0 : 2, hi_side = dir == 0 ? 1 : 3;
-    const bool lo_sine = (A.c.sine >> lo_side) & 1, hi_sine = (A.c.sine >> hi_side) & 1;
-    const real *mu = dir == 0 ? A.lP : A.lQ;
-    real *y = dir == 0 ? A.ldU : A.ldV;
-    real *cp = A.tri;   // c' of the forward sweep, then y
-    // coefficients of row k of T (Eq. 23) with the ends mirrored
-    auto row = [&](int k, real &a, real &b, real &c) {
-        const real dk = dcell(k), dm = dcell(k > 0 ? k - 1 : 0), dp = dcell(k + 1 < n ? k + 1 : n - 1);
-        const real dda = (dp - dm) * hrh, r = A.c.B3 * dk * dk * rh2, s = dk * dda * srh;
-        a = s - r;
-        b = real(1) + real(2) * r;
-        c = -s - r;
-        if (k == 0) {
-            if (!lo_sine) b -= a;
-            a = real(0);
-        }
-        if (k == n - 1) {
-            if (!hi_sine) b -= c;
-            c = real(0);
-        }
-    };
-    // T^T: sub_k = c_{k-1}, diag_k = b_k, sup_k = a_{k+1}
-    real a0, b0, c0v, an, bn, cn;
-    row(0, a0, b0, c0v);
-    real sub = real(0), diag = b0, sup = real(0);
-    if (n > 1) {
-        row(1, an, bn, cn);
-        sup = an;
-    }
-    real cprev = sup / diag, dprev = mu[at(0)] / diag;
-    cp[at(0)] = cprev;
-    y[at(0)] = dprev;
-    real ck_prev = c0v;   // c_{k-1} of T
-    for (int k = 1; k < n; k++) {
-        real ak, bk, ck;
-        row(k, ak, bk, ck);
-        sub = ck_prev;
-        diag = bk;
-        sup = real(0);
-        if (k + 1 < n) {
-            real a1, b1, c1;
-            row(k + 1, a1, b1, c1);
-            sup = a1;
-        }
-        const real den = diag - sub * cprev;
-        cprev = sup / den;
-        dprev = (mu[at(k)] - sub * dprev) / den;
-        cp[at(k)] = cprev;
-        y[at(k)] = dprev;
-        ck_prev = ck;
-    }
-    for (int k = n - 2; k >= 0; k--) y[at(k)] = y[at(k)] - cp[at(k)] * y[at(k + 1)];
-}
-
-// Bed slope and friction (Eq. 9-10, 31-32): per cell, no neighbours.
-template <typename real>
-__global__ void k_adj_cells(AdjArgs<real> A)
-{
-    const Geo &G = A.geo;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
     const int k = j * G.nx + i;
     const real lF = A.G0[1][k], lG = A.G0[2][k];
-    const real c00 = corner(A.Bc, G, i, j), c10 = corner(A.Bc, G, i + 1, j);
-    const real c01 = corner(A.Bc, G, i, j + 1), c11 = corner(A.Bc, G, i + 1, j + 1);
+    const real c00 = acc.bed(i, j), c10 = acc.bed(i + 1, j);
+    const real c01 = acc.bed(i, j + 1), c11 = acc.bed(i + 1, j + 1);
     const real Bb = cell_bbar(c00, c10, c01, c11);
     const real BxW = real(0.5) * (c00 + c01), BxE = real(0.5) * (c10 + c11);
     const real ByS = real(0.5) * (c00 + c10), ByN = real(0.5) * (c01 + c11);
@@ -501,7 +453,7 @@ __global__ void k_adj_cells(AdjArgs<real> A)
     real dw = -(g * (BxE - BxW) * A.c.rdx) * lF - (g * (ByN - ByS) * A.c.rdy) * lG;
     real dP = real(0), dQ = real(0), dfw = real(0);   // dfw: friction's part of dw
     if (A.phy.friction != kFricNone) {
-        const real x[3] = {A.w[k], A.P[k], A.Q[k]};
+        const real x[3] = {acc.val(i, j, 0), acc.val(i, j, 1), acc.val(i, j, 2)};
         real grad[3];
 #pragma unroll
         for (int v = 0; v < 3; v++) {
@@ -520,29 +472,27 @@ __global__ void k_adj_cells(AdjArgs<real> A)
         dQ = grad[2];
     }
     if (A.lBc) {   // the bed: Bbar through h = w - Bbar, the face beds through the slope
-        const real hb = A.w[k] - Bb;
+        const real hb = acc.val(i, j, 0) - Bb;
         A.lBb[ring_index(G, i, j)] += g * (BxE - BxW) * A.c.rdx * lF + g * (ByN - ByS) * A.c.rdy * lG - dfw;
         const real lBxE = -(g * hb * A.c.rdx) * lF, lByN = -(g * hb * A.c.rdy) * lG;
         // BxW = (c00 + c01) / 2, BxE = (c10 + c11) / 2, ByS = (c00 + c10) / 2, ByN = (c01 + c11) / 2
-        atomicAdd(A.lBc + corner_index(G, i, j), real(0.5) * (-lBxE - lByN));
-        atomicAdd(A.lBc + corner_index(G, i + 1, j), real(0.5) * (lBxE - lByN));
-        atomicAdd(A.lBc + corner_index(G, i, j + 1), real(0.5) * (-lBxE + lByN));
-        atomicAdd(A.lBc + corner_index(G, i + 1, j + 1), real(0.5) * (lBxE + lByN));
+        acc.corner(i, j, real(0.5) * (-lBxE - lByN));
+        acc.corner(i + 1, j, real(0.5) * (lBxE - lByN));
+        acc.corner(i, j + 1, real(0.5) * (-lBxE + lByN));
+        acc.corner(i + 1, j + 1, real(0.5) * (lBxE + lByN));
     }
-    A.lw[k] += dw;
-    A.lP[k] += dP;
-    A.lQ[k] += dQ;
+    acc.cell(0, i, j, dw);
+    acc.cell(1, i, j, dP);
+    acc.cell(2, i, j, dQ);
 }
 
 // The face fluxes' Jacobians transposed.  dir 0: x-face f of row `line`;
 // dir 1: y-face f of column `line`.
-template <typename real>
-__global__ void k_adj_faces(AdjArgs<real> A, int dir)
+template <typename real, typename Acc>
+__device__ __forceinline__ void face_vjp(const AdjArgs<real> &A, int dir, int f, int line, const Acc &acc)
 {
     const Geo &G = A.geo;
-    const int n = dir == 0 ? G.nx : G.ny, nl = dir == 0 ? G.ny : G.nx;
-    const int f = blockIdx.x * blockDim.x + threadIdx.x, line = blockIdx.y * blockDim.y + threadIdx.y;
-    if (f > n || line >= nl) return;
+    const int n = dir == 0 ? G.nx : G.ny;
     auto cell = [&](int c) { return dir == 0 ? line * G.nx + c : c * G.nx + line; };
     // H enters R of the cell after the face with +1/h and the cell before with -1/h
     const real rh = dir == 0 ? A.c.rdx : A.c.rdy;
@@ -555,10 +505,10 @@ __global__ void k_adj_faces(AdjArgs<real> A, int dir)
     if (lH[0] == real(0) && lH[1] == real(0) && lH[2] == real(0)) return;
     Src<real> s[4];
 #pragma unroll
-    for (int c = 0; c < 4; c++) s[c] = dir == 0 ? source(A, f - 2 + c, line, 0) : source(A, line, f - 2 + c, 1);
+    for (int c = 0; c < 4; c++) s[c] = dir == 0 ? acc.src(f - 2 + c, line) : acc.src(line, f - 2 + c);
     auto face_bed = [&](int q) {   // bed of face q (dir 0: x-face q of row line)
-        return dir == 0 ? real(0.5) * (corner(A.Bc, G, q, line) + corner(A.Bc, G, q, line + 1))
-                        : real(0.5) * (corner(A.Bc, G, line, q) + corner(A.Bc, G, line + 1, q));
+        return dir == 0 ? real(0.5) * (acc.bed(q, line) + acc.bed(q, line + 1))
+                        : real(0.5) * (acc.bed(line, q) + acc.bed(line + 1, q));
     };
     const real Bm = face_bed(f - 1), Bf = face_bed(f), Bp = face_bed(f + 1);
     real w[4], P[4], Q[4], lw[4] = {0, 0, 0, 0}, lP[4] = {0, 0, 0, 0}, lQ[4] = {0, 0, 0, 0}, lB[3] = {0, 0, 0};
@@ -572,18 +522,21 @@ __global__ void k_adj_faces(AdjArgs<real> A, int dir)
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         if (s[c].idx < 0) continue;
-        if (lw[c] != real(0)) atomicAdd(A.lw + s[c].idx, lw[c]);
-        if (lP[c] != real(0)) atomicAdd(A.lP + s[c].idx, s[c].sgn[1] * lP[c]);
-        if (lQ[c] != real(0)) atomicAdd(A.lQ + s[c].idx, s[c].sgn[2] * lQ[c]);
+        acc.cell(0, s[c].ci, s[c].cj, lw[c]);
+        acc.cell(1, s[c].ci, s[c].cj, s[c].sgn[1] * lP[c]);
+        acc.cell(2, s[c].ci, s[c].cj, s[c].sgn[2] * lQ[c]);
     }
     if (A.lBc) {   // the three face beds, each the mean of its two corners
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             const real gsum = real(0.5) * lB[b];
-            if (gsum != real(0)) {
-                const int q = f - 1 + b;
-                atomicAdd(A.lBc + (dir == 0 ? corner_index(G, q, line) : corner_index(G, line, q)), gsum);
-                atomicAdd(A.lBc + (dir == 0 ? corner_index(G, q, line + 1) : corner_index(G, line + 1, q)), gsum);
+            const int q = f - 1 + b;
+            if (dir == 0) {
+                acc.corner(q, line, gsum);
+                acc.corner(q, line + 1, gsum);
+            } else {
+                acc.corner(line, q, gsum);
+                acc.corner(line + 1, q, gsum);
             }
         }
     }
@@ -615,17 +568,15 @@ __global__ void k_face_vjp_check(const real *in, int n, real *out)
 // terms F*(Q), G*(P) are linear in the neighbouring eta, Q and P, with
 // coefficients from the still-water depth; each cell adds its adjoints to
 // the cells (or the cells their ghosts mirror) its stencil reads.
-template <typename real>
-__global__ void k_adj_disp(AdjArgs<real> A)
+template <typename real, typename Acc>
+__device__ __forceinline__ void disp_vjp(const AdjArgs<real> &A, int i, int j, const Acc &acc)
 {
     const Geo &G = A.geo;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
     const int k = j * G.nx + i;
     const real lF = A.G0[1][k], lG = A.G0[2][k], lFs = A.G0[3][k], lGs = A.G0[4][k];
     if (lF == real(0) && lG == real(0) && lFs == real(0) && lGs == real(0)) return;
     const Coef<real> &C = A.c;
-    auto dcell = [&](int ii, int jj) { return fmax(C.ws - bbar_at(A.Bc, G, ii, jj), real(0)); };
+    auto dcell = [&](int ii, int jj) { return fmax(C.ws - acc.bbar(ii, jj), real(0)); };
     const real dd = dcell(i, j);
     const real ddx = (dcell(i + 1, j) - dcell(i - 1, j)) * C.hrdx, ddy = (dcell(i, j + 1) - dcell(i, j - 1)) * C.hrdy;
     const real K3 = C.Bd * C.g * dd * dd * dd, K2 = C.Bd * C.g * dd * dd;
@@ -655,8 +606,8 @@ __global__ void k_adj_disp(AdjArgs<real> A)
 #pragma unroll
     for (int q = 0; q < 13; q++) {
         if (pts[q].wgt == real(0)) continue;
-        const Src<real> s = source2d(A, i + pts[q].di, j + pts[q].dj);
-        if (s.idx >= 0) atomicAdd(A.lw + s.idx, pts[q].wgt);
+        const Src<real> s = acc.src(i + pts[q].di, j + pts[q].dj);
+        if (s.idx >= 0) acc.cell(0, s.ci, s.cj, pts[q].wgt);
     }
     // F* = d ddx Qy / 6 + d ddy Qx / 6 + B3 d^2 Qxy; G* the same in P with x, y exchanged
     const real qx = dd * ddy * C.sixth * C.hrdx, qy = dd * ddx * C.sixth * C.hrdy, qxy = C.B3 * dd * dd * C.rdxdy4;
@@ -668,15 +619,15 @@ __global__ void k_adj_disp(AdjArgs<real> A)
                       {1, 1, qxy * lGs}, {1, -1, -qxy * lGs}, {-1, 1, -qxy * lGs}, {-1, -1, qxy * lGs}};
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-        const Src<real> s = source2d(A, i + mq[q].di, j + mq[q].dj);
-        if (s.idx >= 0 && mq[q].wgt != real(0)) atomicAdd(A.lQ + s.idx, s.sgn[2] * mq[q].wgt);
-        const Src<real> t = source2d(A, i + mp[q].di, j + mp[q].dj);
-        if (t.idx >= 0 && mp[q].wgt != real(0)) atomicAdd(A.lP + t.idx, t.sgn[1] * mp[q].wgt);
+        const Src<real> s = acc.src(i + mq[q].di, j + mq[q].dj);
+        if (s.idx >= 0) acc.cell(2, s.ci, s.cj, s.sgn[2] * mq[q].wgt);
+        const Src<real> t = acc.src(i + mp[q].di, j + mp[q].dj);
+        if (t.idx >= 0) acc.cell(1, t.ci, t.cj, t.sgn[1] * mp[q].wgt);
     }
     if (!A.ld) return;
     // the same terms with respect to d at the cell (dd) and its 4 neighbours
     // (through ddx, ddy), at the forward's eta, P and Q (ghosts included)
-    auto val = [&](int di, int dj, int v) { return source2d(A, i + di, j + dj).v[v]; };
+    auto val = [&](int di, int dj, int v) { return acc.src(i + di, j + dj).v[v]; };
     const real e00 = val(0, 0, 0), eE = val(1, 0, 0), eW = val(-1, 0, 0), eN = val(0, 1, 0), eS = val(0, -1, 0);
     const real eNE = val(1, 1, 0), eNW = val(-1, 1, 0), eSE = val(1, -1, 0), eSW = val(-1, -1, 0);
     const real exx = (eE - real(2) * e00 + eW) * C.rdx2;
@@ -701,11 +652,160 @@ __global__ void k_adj_disp(AdjArgs<real> A)
                       lGs * dd * Py * C.sixth) * C.hrdx;
     const real Ldy = (lF * Bg * dd * dd * exy + lG * Bg * dd * dd * (real(2) * eyy + exx) + lFs * dd * Qx * C.sixth +
                       lGs * dd * Px * C.sixth) * C.hrdy;
-    atomicAdd(A.ld + ring_index(G, i, j), Ld);
-    atomicAdd(A.ld + ring_index(G, i + 1, j), Ldx);
-    atomicAdd(A.ld + ring_index(G, i - 1, j), -Ldx);
-    atomicAdd(A.ld + ring_index(G, i, j + 1), Ldy);
-    atomicAdd(A.ld + ring_index(G, i, j - 1), -Ldy);
+    acc.ring(i, j, Ld);
+    acc.ring(i + 1, j, Ldx);
+    acc.ring(i - 1, j, -Ldx);
+    acc.ring(i, j + 1, Ldy);
+    acc.ring(i, j - 1, -Ldy);
+}
+
+// The right sides' Jacobians transposed over one 32 x 32 tile: the cells'
+// bed slope, friction and dispersive terms, the x-faces of the tile's rows
+// and the y-faces of its columns (the east and north boundary faces with the
+// last tiles).  Their adjoints reach cells up to 2 beyond the tile (ghosts
+// mapped to the cells they mirror), depths 1 beyond and corners 2 beyond; they
+// are summed in shared memory over that window and added to global memory
+// once per window element.
+constexpr int kVT = 32;              // tile edge
+constexpr int kVW = kVT + 4;         // cell window: x0 - 2 .. x0 + 33
+constexpr int kVWS = kVW + 1;
+constexpr int kVC = kVT + 5;         // corner window: x0 - 2 .. x0 + 34
+constexpr int kVCS = kVC + 1;
+constexpr int kVjpThreads = 256;
+
+template <typename real>
+struct TileAcc {
+    real *sv[3], *sd, *sc;   // shared windows: lw, lP, lQ, ld, lBc
+    real *gv[3], *gd, *gc;   // global arrays
+    const real *xv[3], *xb;  // shared windows: the state as source2d gives it, the bed corners
+    const Geo *G;
+    int sine;
+    int x0, y0, nx, pc;
+    __device__ __forceinline__ real val(int i, int j, int v) const
+    {
+        return xv[v][(j - y0 + 2) * kVWS + (i - x0 + 2)];
+    }
+    __device__ __forceinline__ Src<real> src(int i, int j) const
+    {
+        Src<real> s;
+        mirror2d(*G, sine, i, j, s);
+        const int o = (j - y0 + 2) * kVWS + (i - x0 + 2);
+        s.v[0] = xv[0][o];
+        s.v[1] = xv[1][o];
+        s.v[2] = xv[2][o];
+        return s;
+    }
+    __device__ __forceinline__ real bed(int ci, int cj) const { return xb[(cj - y0 + 2) * kVCS + (ci - x0 + 2)]; }
+    __device__ __forceinline__ real bbar(int i, int j) const
+    {
+        return cell_bbar(bed(i, j), bed(i + 1, j), bed(i, j + 1), bed(i + 1, j + 1));
+    }
+    __device__ __forceinline__ void cell(int var, int i, int j, real v) const
+    {
+        if (v == real(0)) return;
+        const int li = i - x0 + 2, lj = j - y0 + 2;
+        if (li >= 0 && li < kVW && lj >= 0 && lj < kVW) atomicAdd(sv[var] + lj * kVWS + li, v);
+        else atomicAdd(gv[var] + (size_t)j * nx + i, v);
+    }
+    __device__ __forceinline__ void ring(int i, int j, real v) const
+    {
+        if (v == real(0)) return;
+        const int li = i - x0 + 2, lj = j - y0 + 2;
+        if (li >= 0 && li < kVW && lj >= 0 && lj < kVW) atomicAdd(sd + lj * kVWS + li, v);
+        else atomicAdd(gd + (size_t)(j + 1) * (nx + 2) + (i + 1), v);
+    }
+    __device__ __forceinline__ void corner(int ci, int cj, real v) const
+    {
+        if (v == real(0)) return;
+        const int li = ci - x0 + 2, lj = cj - y0 + 2;
+        if (li >= 0 && li < kVC && lj >= 0 && lj < kVC) atomicAdd(sc + lj * kVCS + li, v);
+        else atomicAdd(gc + (size_t)(cj + 1) * pc + (ci + 1), v);
+    }
+};
+
+template <typename real>
+constexpr size_t vjp_smem_bytes()
+{
+    return sizeof(real) * (size_t)(7 * kVW * kVWS + 2 * kVC * kVCS);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__ AdjArgs<real> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sm = reinterpret_cast<real *>(smem_raw);
+    const Geo &G = A.geo;
+    const int x0 = blockIdx.x * kVT, y0 = blockIdx.y * kVT;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    constexpr int ntot = 4 * kVW * kVWS + kVC * kVCS;
+    for (int k = tid; k < ntot; k += kVjpThreads) sm[k] = real(0);
+    TileAcc<real> acc;
+    for (int v = 0; v < 3; v++) acc.sv[v] = sm + v * kVW * kVWS;
+    acc.sd = sm + 3 * kVW * kVWS;
+    acc.sc = sm + 4 * kVW * kVWS;
+    real *xs = sm + ntot;
+    for (int v = 0; v < 3; v++) acc.xv[v] = xs + v * kVW * kVWS;
+    real *xb = xs + 3 * kVW * kVWS;
+    acc.xb = xb;
+    acc.G = &G;
+    acc.sine = A.c.sine;
+    // the state with its ghosts (source2d) on cells within 2 of the grid,
+    // and the bed corners, over the windows
+    for (int k = tid; k < kVW * kVW; k += kVjpThreads) {
+        const int li = k % kVW, lj = k / kVW, i = x0 - 2 + li, j = y0 - 2 + lj, o = lj * kVWS + li;
+        if (i >= -2 && i <= G.nx + 1 && j >= -2 && j <= G.ny + 1) {
+            const Src<real> q = source2d(A, i, j);
+            for (int v = 0; v < 3; v++) xs[v * kVW * kVWS + o] = q.v[v];
+        }
+    }
+    for (int k = tid; k < kVC * kVC; k += kVjpThreads) {
+        const int li = k % kVC, lj = k / kVC, ci = x0 - 2 + li, cj = y0 - 2 + lj;
+        if (ci >= -1 && ci <= G.nx + 1 && cj >= -1 && cj <= G.ny + 1) xb[lj * kVCS + li] = corner(A.Bc, G, ci, cj);
+    }
+    acc.gv[0] = A.lw;
+    acc.gv[1] = A.lP;
+    acc.gv[2] = A.lQ;
+    acc.gd = A.ld;
+    acc.gc = A.lBc;
+    acc.x0 = x0;
+    acc.y0 = y0;
+    acc.nx = G.nx;
+    acc.pc = G.pc;
+    __syncthreads();
+    const int xe = min(x0 + kVT, G.nx), ye = min(y0 + kVT, G.ny);
+    for (int j = y0 + ty; j < ye; j += kVjpThreads / 32) {
+        const int i = x0 + tx;
+        if (i < xe) {
+            cell_vjp(A, i, j, acc);
+            if (A.bsnq) disp_vjp(A, i, j, acc);
+        }
+    }
+    const int fe = xe + (xe == G.nx ? 1 : 0);
+    for (int j = y0 + ty; j < ye; j += kVjpThreads / 32)
+        for (int f = x0 + tx; f < fe; f += 32) face_vjp(A, 0, f, j, acc);
+    const int ge = ye + (ye == G.ny ? 1 : 0);
+    for (int gq = y0 + ty; gq < ge; gq += kVjpThreads / 32) {
+        const int i = x0 + tx;
+        if (i < xe) face_vjp(A, 1, gq, i, acc);
+    }
+    __syncthreads();
+    for (int k = tid; k < kVW * kVW; k += kVjpThreads) {
+        const int li = k % kVW, lj = k / kVW, i = x0 - 2 + li, j = y0 - 2 + lj, o = lj * kVWS + li;
+        if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) {
+            const size_t c = (size_t)j * G.nx + i;
+            for (int v = 0; v < 3; v++)
+                if (acc.sv[v][o] != real(0)) atomicAdd(acc.gv[v] + c, acc.sv[v][o]);
+        }
+        if (A.ld && i >= -1 && i <= G.nx && j >= -1 && j <= G.ny && acc.sd[o] != real(0))
+            atomicAdd(A.ld + ring_index(G, i, j), acc.sd[o]);
+    }
+    if (A.lBc)
+        for (int k = tid; k < kVC * kVC; k += kVjpThreads) {
+            const int li = k % kVC, lj = k / kVC, ci = x0 - 2 + li, cj = y0 - 2 + lj;
+            const real v = acc.sc[lj * kVCS + li];
+            if (v != real(0) && ci >= -1 && ci <= G.nx + 1 && cj >= -1 && cj <= G.ny + 1)
+                atomicAdd(A.lBc + corner_index(G, ci, cj), v);
+        }
 }
 
 // Eq. 23's rows depend on d: a_k = s_k - r_k, b_k = 1 + 2 r_k, c_k = -s_k - r_k
@@ -714,41 +814,60 @@ __global__ void k_adj_disp(AdjArgs<real> A)
 // -mu_k x_l with mu = T^-T (adjoint of x); a wall's boundary row folds a_0
 // into b_0 (x_{-1} = -x_0), a sine maker's moves a_0 times the ghost
 // increment to the right side (x_{-1} = that increment).  One thread per
-// line element.
+// line element gathers the terms of rows k-1, k, k+1 that hold its d; all
+// arrays in the line layout (x-rows [ny][px], y-columns [nx][py]), so both
+// families read along their lines.  blockIdx.z: the family.
+// Eq. 23's constants 1/h^2, 1/(2h), 1/(6h) of one family, rounded once on
+// the host from the double spacing, as the forward's line solver gets them.
 template <typename real>
-__global__ void k_adj_tri_bed(AdjArgs<real> A, const real *X, int dir)
+struct LineConst {
+    real rh2[2], hrh[2], srh[2];
+};
+
+template <typename real>
+__global__ void k_adj_tri_bed(AdjArgs<real> A, const real *X, const real *Yc, const real *MUx, const real *MUy,
+                              const real *dr, const real *dc, LineConst<real> K)
 {
     const Geo &G = A.geo;
+    const int dir = blockIdx.z;
     const int n = dir == 0 ? G.nx : G.ny, nl = dir == 0 ? G.ny : G.nx;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x, line = blockIdx.y * blockDim.y + threadIdx.y;
-    if (k >= n || line >= nl) return;
-    auto cell = [&](int e) { return dir == 0 ? (size_t)line * G.nx + e : (size_t)e * G.nx + line; };
-    auto ring = [&](int e) { return dir == 0 ? ring_index(G, e, line) : ring_index(G, line, e); };
-    auto dcell = [&](int e) {
-        const int i = dir == 0 ? e : line, j = dir == 0 ? line : e;
-        return fmax(A.c.ws - bbar_at(A.Bc, G, i, j), real(0));
-    };
-    const real mu = (dir == 0 ? A.ldU : A.ldV)[cell(k)];
-    if (mu == real(0)) return;
-    const real *x = X + (size_t)line * (dir == 0 ? G.px : G.py);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, line = blockIdx.y;
+    if (e >= n || line >= nl) return;
+    const size_t base = (size_t)line * (dir == 0 ? G.px : G.py);
+    const real *x = (dir == 0 ? X : Yc) + base, *mu = (dir == 0 ? MUx : MUy) + base, *d = (dir == 0 ? dr : dc) + base;
     const int lo_side = dir == 0 ? 0 : 2, hi_side = dir == 0 ? 1 : 3, gvar = dir == 0 ? 1 : 2;
     auto ghost_inc = [&](int side) {
         return A.ghost[ghost_index(1, side, 0, gvar, line + 2, A.c.npos)] -
                A.ghost[ghost_index(0, side, 0, gvar, line + 2, A.c.npos)];
     };
-    const real xk = x[k];
-    const real xm = k > 0 ? x[k - 1] : (((A.c.sine >> lo_side) & 1) ? ghost_inc(lo_side) : -xk);
-    const real xp = k < n - 1 ? x[k + 1] : (((A.c.sine >> hi_side) & 1) ? ghost_inc(hi_side) : -xk);
-    const real gA = -mu * xm, gB = -mu * xk, gC = -mu * xp;
-    const real Lr = -gA + real(2) * gB - gC, Ls = gA - gC;
-    const double h = dir == 0 ? G.dx : G.dy;   // the forward's constants, rounded once
-    const real rh2 = real(1.0 / (h * h)), hrh = real(0.5 / h), srh = real(1.0 / (6.0 * h));
-    const int km = k > 0 ? k - 1 : 0, kp = k < n - 1 ? k + 1 : n - 1;
-    const real dd = dcell(k), dm = dcell(km), dp = dcell(kp);
-    const real Ldp = Ls * dd * srh * hrh;
-    atomicAdd(A.ld + ring(k), Lr * real(2) * A.c.B3 * dd * rh2 + Ls * (dp - dm) * hrh * srh);
-    atomicAdd(A.ld + ring(kp), Ldp);
-    atomicAdd(A.ld + ring(km), -Ldp);
+    const real xlo = ((A.c.sine >> lo_side) & 1) ? ghost_inc(lo_side) : -x[0];
+    const real xhi = ((A.c.sine >> hi_side) & 1) ? ghost_inc(hi_side) : -x[n - 1];
+    // row k's adjoints of r_k and s_k
+    auto row = [&](int k, real &Lr, real &Ls) {
+        const real m = mu[k], xk = x[k];
+        const real xm = k > 0 ? x[k - 1] : xlo, xp = k < n - 1 ? x[k + 1] : xhi;
+        const real gA = -m * xm, gB = -m * xk, gC = -m * xp;
+        Lr = -gA + real(2) * gB - gC;
+        Ls = gA - gC;
+    };
+    const real rh2 = K.rh2[dir], hrh = K.hrh[dir], srh = K.srh[dir];
+    const real sh = srh * hrh;
+    real Lr, Ls;
+    row(e, Lr, Ls);
+    const real de = d[e], dm = d[e > 0 ? e - 1 : 0], dp = d[e < n - 1 ? e + 1 : n - 1];
+    real ld = Lr * real(2) * A.c.B3 * de * rh2 + Ls * (dp - dm) * hrh * srh;
+    if (e == n - 1) ld += Ls * de * sh;   // d_n = d_{n-1}
+    if (e == 0) ld -= Ls * de * sh;       // d_{-1} = d_0
+    real L2r, L2s;
+    if (e >= 1) {   // row e-1 reads d_e as its d_{k+1}
+        row(e - 1, L2r, L2s);
+        ld += L2s * d[e - 1] * sh;
+    }
+    if (e <= n - 2) {   // row e+1 reads d_e as its d_{k-1}
+        row(e + 1, L2r, L2s);
+        ld -= L2s * d[e + 1] * sh;
+    }
+    (dir == 0 ? A.ldx : A.ldy)[base + e] += ld;
 }
 
 // ld into lBb (d = max(w_s - Bbar, 0)), the initial clamp, and lBb into the
@@ -762,8 +881,13 @@ __global__ void k_adj_bed_cells(AdjArgs<real> A, const real *w0, const real *lw0
     const size_t r = ring_index(G, i, j);
     const real Bb = bbar_at(A.Bc, G, i, j);
     real lb = A.lBb[r];
-    if (A.c.ws - Bb > real(0)) lb -= A.ld[r];
-    if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) {
+    const bool inside = i >= 0 && i < G.nx && j >= 0 && j < G.ny;
+    if (A.c.ws - Bb > real(0)) {
+        real ld = A.ld[r];
+        if (inside && A.ldx) ld += A.ldx[(size_t)j * G.px + i] + A.ldy[(size_t)i * G.py + j];
+        lb -= ld;
+    }
+    if (inside) {
         const size_t k = (size_t)j * G.nx + i;
         if (w0[k] - Bb <= real(0)) lb += lw0[k];   // w0 = max(w_in, Bbar) follows the bed on dry cells
     }
@@ -837,11 +961,7 @@ cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st)
 template <typename real>
 cudaError_t launch_adjoint_solves(const AdjArgs<real> &a, cudaStream_t st)
 {
-    if (a.bsnq) {
-        k_adj_lines_t<real><<<(a.geo.ny + 127) / 128, 128, 0, st>>>(a, 0);
-        k_adj_lines_t<real><<<(a.geo.nx + 127) / 128, 128, 0, st>>>(a, 1);
-        return cudaGetLastError();
-    }
+    if (a.bsnq) return cudaErrorInvalidValue;   // the Boussinesq solves go through launch_lines_transposed
     const size_t bytes = sizeof(real) * (size_t)a.geo.nx * a.geo.ny;   // NLSW: P = U*, Q = V*
     cudaError_t e = cudaMemcpyAsync(a.ldU, a.lP, bytes, cudaMemcpyDeviceToDevice, st);
     return e != cudaSuccess ? e : cudaMemcpyAsync(a.ldV, a.lQ, bytes, cudaMemcpyDeviceToDevice, st);
@@ -858,12 +978,15 @@ cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st)
 template <typename real>
 cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st)
 {
-    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
-    k_adj_cells<real><<<g, b, 0, st>>>(a);
-    if (a.bsnq) k_adj_disp<real><<<g, b, 0, st>>>(a);
-    dim3 bf(64, 4);
-    k_adj_faces<real><<<dim3((a.geo.nx + 1 + 63) / 64, (a.geo.ny + 3) / 4), bf, 0, st>>>(a, 0);
-    k_adj_faces<real><<<dim3((a.geo.ny + 1 + 63) / 64, (a.geo.nx + 3) / 4), bf, 0, st>>>(a, 1);
+    constexpr size_t smem = vjp_smem_bytes<real>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_adj_vjp<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 g((a.geo.nx + kVT - 1) / kVT, (a.geo.ny + kVT - 1) / kVT);
+    k_adj_vjp<real><<<g, kVjpThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -875,11 +998,18 @@ cudaError_t launch_face_vjp_check(const real *in, int n, real *out, cudaStream_t
 }
 
 template <typename real>
-cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, cudaStream_t st)
+cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, const real *MUx,
+                                   const real *MUy, const real *dr, const real *dc, cudaStream_t st)
 {
-    dim3 b(32, 8);
-    k_adj_tri_bed<real><<<dim3((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8), b, 0, st>>>(a, X, 0);
-    k_adj_tri_bed<real><<<dim3((a.geo.ny + 31) / 32, (a.geo.nx + 7) / 8), b, 0, st>>>(a, Yc, 1);
+    const int n = a.geo.nx > a.geo.ny ? a.geo.nx : a.geo.ny, nl = a.geo.nx > a.geo.ny ? a.geo.nx : a.geo.ny;
+    LineConst<real> K;
+    for (int d = 0; d < 2; d++) {
+        const double h = d == 0 ? a.geo.dx : a.geo.dy;
+        K.rh2[d] = real(1.0 / (h * h));
+        K.hrh[d] = real(0.5 / h);
+        K.srh[d] = real(1.0 / (6.0 * h));
+    }
+    k_adj_tri_bed<real><<<dim3((n + 127) / 128, nl, 2), 128, 0, st>>>(a, X, Yc, MUx, MUy, dr, dc, K);
     return cudaGetLastError();
 }
 
@@ -914,16 +1044,6 @@ cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int b
 }
 
 template <typename real>
-cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st)
-{
-    cudaError_t e = launch_adjoint_mask(a, st);
-    if (e == cudaSuccess) e = launch_adjoint_solves(a, st);
-    if (e == cudaSuccess) e = launch_adjoint_hist(a, st);
-    if (e == cudaSuccess) e = launch_adjoint_vjp(a, st);
-    return e;
-}
-
-template <typename real>
 cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, int ng, const real *rec, const real *obs,
                                   cudaStream_t st)
 {
@@ -932,7 +1052,6 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
 }
 
 #define CEL_ADJ_INSTANTIATE(real)                                                                        \
-    template cudaError_t launch_adjoint_step<real>(const AdjArgs<real> &, cudaStream_t);                 \
     template cudaError_t launch_adjoint_mask<real>(const AdjArgs<real> &, cudaStream_t);                 \
     template cudaError_t launch_adjoint_solves<real>(const AdjArgs<real> &, cudaStream_t);               \
     template cudaError_t launch_adjoint_hist<real>(const AdjArgs<real> &, cudaStream_t);                 \
@@ -942,7 +1061,8 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
     template cudaError_t launch_adjoint_pack<real>(const AdjArgs<real> &, real *, real *, int, cudaStream_t); \
     template cudaError_t launch_face_vjp_check<real>(const real *, int, real *, cudaStream_t);            \
     template cudaError_t launch_adjoint_tri_bed<real>(const AdjArgs<real> &, const real *, const real *,   \
-                                                      cudaStream_t);                                   \
+                                                      const real *, const real *, const real *,         \
+                                                      const real *, cudaStream_t);                      \
     template cudaError_t launch_adjoint_bed_final<real>(const AdjArgs<real> &, const real *, const real *, \
                                                         real *, cudaStream_t);                         \
     template cudaError_t launch_adjoint_misfit<real>(const AdjArgs<real> &, const int32_t *, int,         \

@@ -1544,7 +1544,7 @@ namespace {
 struct AdjLayout {
     size_t ckpt_bytes, cells_bytes, line_bytes;
     size_t ckpt, seg, iter, lam, G, rec, gij, total;
-    size_t rhs, xs, lBc, lBb, ld;   // the bed's gradient (bed != 0)
+    size_t rhs, xs, lBc, lBb, ld, ldl;   // the bed's gradient (bed != 0)
     int nseg, bed;
 };
 
@@ -1570,11 +1570,12 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
     L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
-    L.rhs = L.xs = L.lBc = L.lBb = L.ld = 0;
+    L.rhs = L.xs = L.lBc = L.lBb = L.ld = L.ldl = 0;
     if (bed) {
         const bool lines = s->params.model == CEL_BSNQ;
         L.rhs = take(lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0);   // every stage's right sides
         L.xs = take(lines ? L.line_bytes * 2 : 0);                                  // and their solutions
+        L.ldl = take(lines ? L.line_bytes * 2 : 0);                                 // ld of the line systems
         L.lBc = take((size_t)s->geo.pc * (s->grid.ny + 3) * s->es);
         L.lBb = take((size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * s->es);
         L.ld = take((size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * s->es);
@@ -1667,6 +1668,11 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         CEL_CUDA(s, cudaMemsetAsync(a.lBc, 0, (size_t)s->geo.pc * (s->grid.ny + 3) * sizeof(real), st), "adjoint");
         CEL_CUDA(s, cudaMemsetAsync(a.lBb, 0, (size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * sizeof(real), st), "adjoint");
         CEL_CUDA(s, cudaMemsetAsync(a.ld, 0, (size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * sizeof(real), st), "adjoint");
+        if (bed_lines) {
+            a.ldx = reinterpret_cast<real *>(scr + L.ldl);
+            a.ldy = reinterpret_cast<real *>(scr + L.ldl + L.line_bytes);
+            CEL_CUDA(s, cudaMemsetAsync(scr + L.ldl, 0, L.line_bytes * 2, st), "adjoint");
+        }
     }
     int lset = 0;   // which lam set holds the adjoint of the state after the step
     auto setl = [&](AdjArgs<real> &x, int set) {
@@ -1723,7 +1729,10 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
             lp.L[dir].identity = 0;
         }
         cudaError_t e = launch_lines_solution<real>(lp, st);
-        return e != cudaSuccess ? e : launch_adjoint_tri_bed<real>(x, Xs, Ys, st);
+        // mu: the transposed solves' solutions, still in the solver's U*, V* buffers
+        return e != cudaSuccess ? e
+                                : launch_adjoint_tri_bed<real>(x, Xs, Ys, s->at<real>(s->lay.U), s->at<real>(s->lay.Vc),
+                                                               s->at<real>(s->lay.dr), s->at<real>(s->lay.dc), st);
     };
     auto full_step = [&](const AdjArgs<real> &x, int k) -> cudaError_t {
         cudaError_t e = launch_adjoint_mask<real>(x, st);

@@ -210,6 +210,7 @@ struct AdjArgs {
     // the cell bed Bbar and ld of the still-water depth d on the cells with
     // a one-cell ring ([ny + 2][nx + 2], cell (i, j) at [j + 1][i + 1])
     real *lBc, *lBb, *ld;
+    real *ldx, *ldy;       // the line systems' part of ld, in the line layouts (Boussinesq)
     real c0, c1, c2;       // weights of R^n, R^{n-1}, R^{n-2} in this step's update
     real e0, e1, e2;       // weights of F*^n, F*^{n-1}, F*^{n-2} (Boussinesq)
     int bsnq;
@@ -217,12 +218,10 @@ struct AdjArgs {
     int tsel;              // sine-maker ghosts at t^n (0, predictor) or t^{n+1} (1, corrector)
 };
 
-// One predictor-only step reversed: masks, transposed solves, history, the
-// right sides' Jacobians transposed.
-template <typename real>
-cudaError_t launch_adjoint_step(const AdjArgs<real> &a, cudaStream_t st);
-// The same phases one at a time (a corrector step composes them); G1 and G2
-// may be NULL in the history phase.
+// The phases of one stage's reverse: masks, transposed solves (NLSW only:
+// a copy; the Boussinesq solves go through launch_lines_transposed),
+// history, the right sides' Jacobians transposed.  G1 and G2 may be NULL in
+// the history phase.
 template <typename real>
 cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st);
 template <typename real>
@@ -235,10 +234,12 @@ cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st);
 template <typename real>
 cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int back, cudaStream_t st);
 // The line systems' dependence on d (Eq. 23): with x the stage's solutions
-// (line layouts, X [ny][px] and Yc [nx][py]) and ldU, ldV the transposed
-// solves' solutions, dL/dT_kl = -ldU_k x_l is added to ld.
+// and mu the transposed solves' solutions (line layouts: x-rows [ny][px],
+// y-columns [nx][py]) and dr, dc the depths in the same layouts,
+// dL/dT_kl = -mu_k x_l is added to ldx, ldy.
 template <typename real>
-cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, cudaStream_t st);
+cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, const real *MUx,
+                                   const real *MUy, const real *dr, const real *dc, cudaStream_t st);
 // The end of the reverse: ld and the clamp of the initial state (cells with
 // w0 <= Bbar follow the bed, weight lw0) into lBb, lBb into lBc, and lBc
 // into the cell-centre bed z as dL/dz (grad_z zeroed here).
