@@ -627,7 +627,7 @@ __device__ __forceinline__ void disp_vjp(const AdjArgs<real> &A, int i, int j, c
     if (!A.ld) return;
     // the same terms with respect to d at the cell (dd) and its 4 neighbours
     // (through ddx, ddy), at the forward's eta, P and Q (ghosts included)
-    auto val = [&](int di, int dj, int v) { return acc.src(i + di, j + dj).v[v]; };
+    auto val = [&](int di, int dj, int v) { return acc.val(i + di, j + dj, v); };
     const real e00 = val(0, 0, 0), eE = val(1, 0, 0), eW = val(-1, 0, 0), eN = val(0, 1, 0), eS = val(0, -1, 0);
     const real eNE = val(1, 1, 0), eNW = val(-1, 1, 0), eSE = val(1, -1, 0), eSW = val(-1, -1, 0);
     const real exx = (eE - real(2) * e00 + eW) * C.rdx2;
@@ -680,6 +680,7 @@ struct TileAcc {
     const real *xv[3], *xb;  // shared windows: the state as source2d gives it, the bed corners
     const Geo *G;
     int sine;
+    int interior;            // the whole cell window lies inside the grid: no ghosts
     int x0, y0, nx, pc;
     __device__ __forceinline__ real val(int i, int j, int v) const
     {
@@ -688,7 +689,14 @@ struct TileAcc {
     __device__ __forceinline__ Src<real> src(int i, int j) const
     {
         Src<real> s;
-        mirror2d(*G, sine, i, j, s);
+        if (interior) {
+            s.sgn[0] = s.sgn[1] = s.sgn[2] = real(1);
+            s.ci = i;
+            s.cj = j;
+            s.idx = j * nx + i;
+        } else {
+            mirror2d(*G, sine, i, j, s);
+        }
         const int o = (j - y0 + 2) * kVWS + (i - x0 + 2);
         s.v[0] = xv[0][o];
         s.v[1] = xv[1][o];
@@ -749,6 +757,7 @@ __global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__
     acc.xb = xb;
     acc.G = &G;
     acc.sine = A.c.sine;
+    acc.interior = x0 >= 2 && y0 >= 2 && x0 + kVW - 2 <= G.nx && y0 + kVW - 2 <= G.ny;
     // the state with its ghosts (source2d) on cells within 2 of the grid,
     // and the bed corners, over the windows
     for (int k = tid; k < kVW * kVW; k += kVjpThreads) {
