@@ -435,3 +435,33 @@ def test_face_flux_vjp_by_hand_matches_dual_numbers(prec):
         assert np.max(err) <= 1e-10
     else:   # FP32: the two roundings may pick different sides of a near-tie in a few faces
         assert np.quantile(err, 0.999) <= 1e-3 and np.median(err) <= 1e-5
+
+
+def test_gradients_on_32_random_directions():
+    """Both gradients against FP64 central differences of the oracle along
+    32 seeded random directions (16 in w0, 16 in z), each a random field
+    smoothed over a few cells, on the kink-free Boussinesq state over the
+    undulating bed with one AM4 corrector iteration: every one within 1e-3
+    relative."""
+    from scipy.ndimage import uniform_filter
+    s, gauges, X, Y = _tilted_bed(0, 1, 2)
+    rng = np.random.default_rng(32)
+    obs = 0.01 * rng.standard_normal((s.steps, len(gauges)))
+    loss, _, gw, _, gz = _gpu_gradient(s, gauges, obs, ckpt=4, bed=True)
+    assert abs(loss - _oracle_loss_bed(s, s.z, gauges, obs)) <= 1e-9 * loss
+    eps = 1e-5
+    errs = []
+    for k in range(32):
+        v = uniform_filter(rng.standard_normal(X.shape), size=5, mode="nearest")
+        if k < 16:
+            v *= 1e-4 / np.max(np.abs(v))
+            fd = (_oracle_loss_state(s, s.w0 + eps * v, gauges, obs)
+                  - _oracle_loss_state(s, s.w0 - eps * v, gauges, obs)) / (2 * eps)
+            ad = float(np.sum(gw * v))
+        else:
+            v *= 1e-2 / np.max(np.abs(v))
+            fd = (_oracle_loss_bed(s, s.z + eps * v, gauges, obs)
+                  - _oracle_loss_bed(s, s.z - eps * v, gauges, obs)) / (2 * eps)
+            ad = float(np.sum(gz * v))
+        errs.append(abs(ad - fd) / abs(fd))
+    assert max(errs) <= 1e-3, errs
