@@ -18,6 +18,7 @@ SOURCES = ["celeris_kernels.cu", "celeris_api.cu", "celeris_render.cu", "celeris
 # spells out each rounding)
 SOURCE_FLAGS = {"celeris_render.cu": ["-ftz=false", "-prec-div=true", "-prec-sqrt=true", "-fmad=false"]}
 HEADERS = [os.path.join(CSRC, "celeris_internal.cuh"), os.path.join(CSRC, "celeris_physics.cuh"),
+           os.path.join(CSRC, "celeris_adjoint.cuh"),
            os.path.join(INCLUDE, "celeris_gb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 division and square root use the fast reciprocal / reciprocal-square-root

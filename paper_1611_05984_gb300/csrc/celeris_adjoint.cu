@@ -28,7 +28,7 @@
 // evaluated on dual numbers, one input direction at a time, so every branch
 // follows the forward state.  Adjoints reach a cell through the faces around
 // it, so they are added with atomics (the sums' order is not fixed).
-#include "celeris_internal.cuh"
+#include "celeris_adjoint.cuh"
 #include "celeris_physics.cuh"
 
 #include <math.h>

@@ -5,6 +5,7 @@
 // records the text of the last error in the handle.
 #include "celeris_gb.h"
 #include "celeris_internal.cuh"
+#include "celeris_adjoint.cuh"
 
 #include <math.h>
 #include <stdio.h>
