@@ -230,9 +230,9 @@ cel_status cel_render(cel_solver *s, const cel_render_params *params, void *rgba
  * be NULL): [ny][nx] real, dL/dz for the bed z of cel_create or
  * cel_set_bathymetry, with the initial w held where the cell is wet and
  * equal to the cell bed where it is dry (the clamp), as when cel_set_state
- * is called again after a change of bed.  The bed enters the sine maker's
- * ghost values through the depth at the boundary; that path is not
- * differentiated.  *loss (may be NULL): L in double.  Synchronises.  The
+ * is called again after a change of bed; the sine makers' ghost values
+ * follow the depth beside them (Eckart wave number, celerity) and are
+ * differentiated too.  *loss (may be NULL): L in double.  Synchronises.  The
  * adjoint sums reach a cell from several faces in no fixed order, so
  * repeated runs agree to rounding, not bit for bit. */
 cel_status cel_adjoint_bytes(const cel_solver *s, int32_t nsteps, int32_t ckpt_every, int32_t ngauges,

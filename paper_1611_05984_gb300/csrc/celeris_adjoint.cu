@@ -89,8 +89,9 @@ using ::rsqrt;
 template <typename real>
 struct Src {
     real v[3];
-    int idx;          // interior cell, -1 for a constant ghost
+    int idx;          // interior cell, -1 for a sine-maker ghost
     int ci, cj;       // its coordinates
+    int gs, gl, gp;   // the ghost's side, layer and table position (idx = -1)
     real sgn[3];
 };
 
@@ -114,6 +115,9 @@ __device__ __forceinline__ Src<real> source(const AdjArgs<real> &A, int i, int j
         s.v[1] = tb[A.c.npos];
         s.v[2] = tb[2 * A.c.npos];
         s.idx = -1;
+        s.gs = side;
+        s.gl = layer;
+        s.gp = pos;
         return s;
     }
     if (side >= 0) s.sgn[dir == 0 ? 1 : 2] = real(-1);   // the normal discharge is negated
@@ -144,6 +148,9 @@ __device__ __forceinline__ Src<real> source2d(const AdjArgs<real> &A, int i, int
         s.v[1] = tb[A.c.npos];
         s.v[2] = tb[2 * A.c.npos];
         s.idx = -1;
+        s.gs = side;
+        s.gl = layer;
+        s.gp = i + 2;
         s.sgn[0] = s.sgn[1] = s.sgn[2] = real(1);
         return s;
     }
@@ -163,12 +170,24 @@ __device__ __forceinline__ void mirror2d(const Geo &G, int sine, int i, int j, S
     s.idx = -1;
     int si = i, sj = j;
     if (j < 0 || j >= G.ny) {   // a y-ghost: the mirrored row's cell, Q negated
-        if ((sine >> (j < 0 ? 2 : 3)) & 1) return;
+        if ((sine >> (j < 0 ? 2 : 3)) & 1) {
+            s.gs = j < 0 ? 2 : 3;
+            s.gl = j < 0 ? -1 - j : j - G.ny;
+            s.gp = i + 2;
+            s.sgn[2] = real(1);
+            return;
+        }
         sj = j < 0 ? -1 - j : 2 * G.ny - 1 - j;
         s.sgn[2] = real(-1);
     }
     if (i < 0 || i >= G.nx) {   // an x-ghost: P negated
-        if ((sine >> (i < 0 ? 0 : 1)) & 1) return;
+        if ((sine >> (i < 0 ? 0 : 1)) & 1) {
+            s.gs = i < 0 ? 0 : 1;
+            s.gl = i < 0 ? -1 - i : i - G.nx;
+            s.gp = sj + 2;
+            s.sgn[0] = s.sgn[1] = s.sgn[2] = real(1);
+            return;
+        }
         si = i < 0 ? -1 - i : 2 * G.nx - 1 - i;
         s.sgn[1] = real(-1);
     }
@@ -521,7 +540,12 @@ __device__ __forceinline__ void face_vjp(const AdjArgs<real> &A, int dir, int f,
     face_flux_vjp(w, P, Q, Bm, Bf, Bp, A.c.theta, A.c.g, A.c.eps, dir, lH, lw, lP, lQ, lB);
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        if (s[c].idx < 0) continue;
+        if (s[c].idx < 0) {   // a sine-maker ghost: its values' adjoints, for the depth they follow
+            acc.ghost(s[c], 0, lw[c]);
+            acc.ghost(s[c], 1, lP[c]);
+            acc.ghost(s[c], 2, lQ[c]);
+            continue;
+        }
         acc.cell(0, s[c].ci, s[c].cj, lw[c]);
         acc.cell(1, s[c].ci, s[c].cj, s[c].sgn[1] * lP[c]);
         acc.cell(2, s[c].ci, s[c].cj, s[c].sgn[2] * lQ[c]);
@@ -608,6 +632,7 @@ __device__ __forceinline__ void disp_vjp(const AdjArgs<real> &A, int i, int j, c
         if (pts[q].wgt == real(0)) continue;
         const Src<real> s = acc.src(i + pts[q].di, j + pts[q].dj);
         if (s.idx >= 0) acc.cell(0, s.ci, s.cj, pts[q].wgt);
+        else acc.ghost(s, 0, pts[q].wgt);
     }
     // F* = d ddx Qy / 6 + d ddy Qx / 6 + B3 d^2 Qxy; G* the same in P with x, y exchanged
     const real qx = dd * ddy * C.sixth * C.hrdx, qy = dd * ddx * C.sixth * C.hrdy, qxy = C.B3 * dd * dd * C.rdxdy4;
@@ -621,8 +646,10 @@ __device__ __forceinline__ void disp_vjp(const AdjArgs<real> &A, int i, int j, c
     for (int q = 0; q < 8; q++) {
         const Src<real> s = acc.src(i + mq[q].di, j + mq[q].dj);
         if (s.idx >= 0) acc.cell(2, s.ci, s.cj, s.sgn[2] * mq[q].wgt);
+        else acc.ghost(s, 2, mq[q].wgt);
         const Src<real> t = acc.src(i + mp[q].di, j + mp[q].dj);
         if (t.idx >= 0) acc.cell(1, t.ci, t.cj, t.sgn[1] * mp[q].wgt);
+        else acc.ghost(t, 1, mp[q].wgt);
     }
     if (!A.ld) return;
     // the same terms with respect to d at the cell (dd) and its 4 neighbours
@@ -681,6 +708,12 @@ struct TileAcc {
     const Geo *G;
     int sine;
     int interior;            // the whole cell window lies inside the grid: no ghosts
+    real *lg;                // ghost adjoints (NULL: not wanted)
+    int tsel, npos;
+    __device__ __forceinline__ void ghost(const Src<real> &s, int var, real v) const
+    {
+        if (lg && v != real(0)) atomicAdd(lg + ghost_index(tsel, s.gs, s.gl, var, s.gp, npos), v);
+    }
     int x0, y0, nx, pc;
     __device__ __forceinline__ real val(int i, int j, int v) const
     {
@@ -758,6 +791,9 @@ __global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__
     acc.G = &G;
     acc.sine = A.c.sine;
     acc.interior = x0 >= 2 && y0 >= 2 && x0 + kVW - 2 <= G.nx && y0 + kVW - 2 <= G.ny;
+    acc.lg = A.lg;
+    acc.tsel = A.tsel;
+    acc.npos = A.c.npos;
     // the state with its ghosts (source2d) on cells within 2 of the grid,
     // and the bed corners, over the windows
     for (int k = tid; k < kVW * kVW; k += kVjpThreads) {
@@ -849,8 +885,9 @@ __global__ void k_adj_tri_bed(AdjArgs<real> A, const real *X, const real *Yc, co
         return A.ghost[ghost_index(1, side, 0, gvar, line + 2, A.c.npos)] -
                A.ghost[ghost_index(0, side, 0, gvar, line + 2, A.c.npos)];
     };
-    const real xlo = ((A.c.sine >> lo_side) & 1) ? ghost_inc(lo_side) : -x[0];
-    const real xhi = ((A.c.sine >> hi_side) & 1) ? ghost_inc(hi_side) : -x[n - 1];
+    const bool lo_sine = (A.c.sine >> lo_side) & 1, hi_sine = (A.c.sine >> hi_side) & 1;
+    const real xlo = lo_sine ? ghost_inc(lo_side) : -x[0];
+    const real xhi = hi_sine ? ghost_inc(hi_side) : -x[n - 1];
     // row k's adjoints of r_k and s_k
     auto row = [&](int k, real &Lr, real &Ls) {
         const real m = mu[k], xk = x[k];
@@ -877,6 +914,61 @@ __global__ void k_adj_tri_bed(AdjArgs<real> A, const real *X, const real *Yc, co
         ld -= L2s * d[e + 1] * sh;
     }
     (dir == 0 ? A.ldx : A.ldy)[base + e] += ld;
+    // a maker's row: r_0 - a_0 (g^{n+1} - g^n) (and the last row with c), so
+    // the ghost increments' adjoints are -+ mu a_0
+    if (A.lg && ((e == 0 && lo_sine) || (e == n - 1 && hi_sine))) {
+        const bool lo = e == 0 && lo_sine;
+        const int side = lo ? lo_side : hi_side;
+        const real r = A.c.B3 * de * de * rh2, sk = de * (dp - dm) * hrh * srh;
+        const real coef = lo ? sk - r : -sk - r;
+        const real gi = -mu[e] * coef;
+        atomicAdd(A.lg + ghost_index(1, side, 0, gvar, line + 2, A.c.npos), gi);
+        atomicAdd(A.lg + ghost_index(0, side, 0, gvar, line + 2, A.c.npos), -gi);
+        if (n == 1 && lo_sine && hi_sine) {   // one row carries both ends
+            const real gh = -mu[e] * (-sk - r);
+            atomicAdd(A.lg + ghost_index(1, hi_side, 0, gvar, line + 2, A.c.npos), gh);
+            atomicAdd(A.lg + ghost_index(0, hi_side, 0, gvar, line + 2, A.c.npos), -gh);
+        }
+    }
+}
+
+// The ghost values of one table entry (Eq. 25-28: eta, P, Q summed over the
+// components, Eckart wave number k = k0 / sqrt(tanh(k0 d)), celerity w / k)
+// differentiated with respect to the adjacent depth d, in double:
+// dk/dd = -k0^2 / (2 sqrt(coth(k0 d)) sinh^2(k0 d)), d(a sin th)/dk =
+// -a cos th (x cos + y sin), dc/dk = -c / k.  Their adjoints (lg) go to ld
+// of the cell whose depth the entry reads; lg is zeroed.
+template <typename real>
+__global__ void k_adj_ghost_bed(AdjArgs<real> A, Bnd b, const double *ktab, const real *d_r, double t0, double t1)
+{
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x, yb = blockIdx.y;
+    const int time = yb & 1, layer = (yb >> 1) & 1, side = yb >> 2;
+    const int npos = A.c.npos;
+    if (pos >= npos || !((A.c.sine >> side) & 1)) return;
+    real *l0 = A.lg + ghost_index(time, side, layer, 0, pos, npos);
+    const double le = (double)l0[0], lP = (double)l0[npos], lQ = (double)l0[2 * npos];
+    l0[0] = l0[npos] = l0[2 * npos] = real(0);
+    double x, y, dadj;
+    if (!ghost_site(A.geo, d_r, side, layer, pos, x, y, dadj)) return;
+    if ((le == 0.0 && lP == 0.0 && lQ == 0.0) || !(dadj > 0.0)) return;
+    const Side &S = b.s[side];
+    const double t = time ? t1 : t0, g = (double)A.phy.g;
+    double dd = 0.0;
+    for (int m = 0; m < S.ncomp; m++) {
+        const double k = ktab[((size_t)side * npos + pos) * 8 + m];
+        if (!(k > 0.0)) continue;
+        const double om = S.omega[m], k0 = om * om / g, kd = k0 * dadj;
+        const double sh = sinh(kd);
+        const double dkdd = -k0 * k0 / (2.0 * sqrt(1.0 / tanh(kd)) * sh * sh);
+        const double arg = om * t - k * S.cdir[m] * x - k * S.sdir[m] * y + S.phase[m];
+        const double em = S.amp[m] * sin(arg), demdk = -S.amp[m] * cos(arg) * (S.cdir[m] * x + S.sdir[m] * y);
+        const double c = om / k, dcdk = -c / k;
+        const double dPdk = S.cdir[m] * (dcdk * em + c * demdk), dQdk = S.sdir[m] * (dcdk * em + c * demdk);
+        dd += (le * demdk + lP * dPdk + lQ * dQdk) * dkdd;
+    }
+    int i, j;
+    ghost_adjacent(A.geo, side, pos, i, j);
+    atomicAdd(A.ld + ring_index(A.geo, i, j), real(dd));
 }
 
 // ld into lBb (d = max(w_s - Bbar, 0)), the initial clamp, and lBb into the
@@ -1023,6 +1115,15 @@ cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const 
 }
 
 template <typename real>
+cudaError_t launch_adjoint_ghost_bed(const AdjArgs<real> &a, const Bnd &b, const double *ktab, const real *d_r,
+                                     double t0, double t1, cudaStream_t st)
+{
+    if (!a.lg || !a.c.sine) return cudaSuccess;
+    k_adj_ghost_bed<real><<<dim3((a.c.npos + 127) / 128, 16), 128, 0, st>>>(a, b, ktab, d_r, t0, t1);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_adjoint_bed_final(const AdjArgs<real> &a, const real *w0, const real *lw0, real *grad_z,
                                      cudaStream_t st)
 {
@@ -1072,6 +1173,8 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
     template cudaError_t launch_adjoint_tri_bed<real>(const AdjArgs<real> &, const real *, const real *,   \
                                                       const real *, const real *, const real *,         \
                                                       const real *, cudaStream_t);                      \
+    template cudaError_t launch_adjoint_ghost_bed<real>(const AdjArgs<real> &, const Bnd &, const double *, \
+                                                        const real *, double, double, cudaStream_t);    \
     template cudaError_t launch_adjoint_bed_final<real>(const AdjArgs<real> &, const real *, const real *, \
                                                         real *, cudaStream_t);                         \
     template cudaError_t launch_adjoint_misfit<real>(const AdjArgs<real> &, const int32_t *, int,         \

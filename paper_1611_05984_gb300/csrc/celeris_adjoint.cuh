@@ -27,6 +27,7 @@ struct AdjArgs {
     // a one-cell ring ([ny + 2][nx + 2], cell (i, j) at [j + 1][i + 1])
     real *lBc, *lBb, *ld;
     real *ldx, *ldy;       // the line systems' part of ld, in the line layouts (Boussinesq)
+    real *lg;              // adjoint of the sine makers' ghost values (the ghost table's layout), or NULL
     real c0, c1, c2;       // weights of R^n, R^{n-1}, R^{n-2} in this step's update
     real e0, e1, e2;       // weights of F*^n, F*^{n-1}, F*^{n-2} (Boussinesq)
     int bsnq;
@@ -56,6 +57,12 @@ cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int b
 template <typename real>
 cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const real *Yc, const real *MUx,
                                    const real *MUy, const real *dr, const real *dc, cudaStream_t st);
+// The sine makers' ghost values depend on the adjacent depth through the
+// Eckart wave number (Eq. 25-29): lg (this step's ghost adjoints, t0 = t^n,
+// t1 = t^{n+1}) into ld, then lg zeroed.
+template <typename real>
+cudaError_t launch_adjoint_ghost_bed(const AdjArgs<real> &a, const Bnd &b, const double *ktab, const real *d_r,
+                                     double t0, double t1, cudaStream_t st);
 // The end of the reverse: ld and the clamp of the initial state (cells with
 // w0 <= Bbar follow the bed, weight lw0) into lBb, lBb into lBc, and lBc
 // into the cell-centre bed z as dL/dz (grad_z zeroed here).

@@ -1545,7 +1545,8 @@ namespace {
 struct AdjLayout {
     size_t ckpt_bytes, cells_bytes, line_bytes;
     size_t ckpt, seg, iter, lam, G, rec, gij, total;
-    size_t rhs, xs, lBc, lBb, ld, ldl;   // the bed's gradient (bed != 0)
+    size_t rhs, xs, lBc, lBb, ld, ldl, lg;   // the bed's gradient (bed != 0)
+    size_t ghost_bytes;
     int nseg, bed;
 };
 
@@ -1571,7 +1572,8 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
     L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
-    L.rhs = L.xs = L.lBc = L.lBb = L.ld = L.ldl = 0;
+    L.rhs = L.xs = L.lBc = L.lBb = L.ld = L.ldl = L.lg = 0;
+    L.ghost_bytes = ghost_index(2, 0, 0, 0, 0, (s->geo.nx > s->geo.ny ? s->geo.nx : s->geo.ny) + 4) * s->es;
     if (bed) {
         const bool lines = s->params.model == CEL_BSNQ;
         L.rhs = take(lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0);   // every stage's right sides
@@ -1580,6 +1582,7 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
         L.lBc = take((size_t)s->geo.pc * (s->grid.ny + 3) * s->es);
         L.lBb = take((size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * s->es);
         L.ld = take((size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * s->es);
+        L.lg = take(L.ghost_bytes);   // the sine makers' ghost values
     }
     L.total = cur;
     return L;
@@ -1669,6 +1672,10 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         CEL_CUDA(s, cudaMemsetAsync(a.lBc, 0, (size_t)s->geo.pc * (s->grid.ny + 3) * sizeof(real), st), "adjoint");
         CEL_CUDA(s, cudaMemsetAsync(a.lBb, 0, (size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * sizeof(real), st), "adjoint");
         CEL_CUDA(s, cudaMemsetAsync(a.ld, 0, (size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * sizeof(real), st), "adjoint");
+        if (a.c.sine) {
+            a.lg = reinterpret_cast<real *>(scr + L.lg);
+            CEL_CUDA(s, cudaMemsetAsync(a.lg, 0, L.ghost_bytes, st), "adjoint");
+        }
         if (bed_lines) {
             a.ldx = reinterpret_cast<real *>(scr + L.ldl);
             a.ldy = reinterpret_cast<real *>(scr + L.ldl + L.line_bytes);
@@ -1845,6 +1852,11 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 CEL_CUDA(s, launch_adjoint_vjp<real>(x, st), "adjoint state");
                 lset = acc;
             }
+            if (a.lg)   // the step's ghost values (t^n, t^{n+1}) follow the adjacent depth
+                CEL_CUDA(s, launch_adjoint_ghost_bed<real>(a, s->bnd, s->at<double>(s->lay.ktab),
+                                                           s->at<real>(s->lay.dr), (double)(step0 + n) * dt,
+                                                           (double)(step0 + n + 1) * dt, st),
+                         "adjoint ghosts");
             setl(a, lset);
             if (n >= 1)
                 CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(n - 1) * ng,

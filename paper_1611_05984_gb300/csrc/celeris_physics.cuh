@@ -108,4 +108,43 @@ __device__ __forceinline__ real sponge_gamma(const Coef<real> &c, const Geo &g, 
     return gm;
 }
 
+// Adjacent still-water depth d and ghost coordinates of table position pos
+// (Reading A-B4): west / east sides run along rows j = pos - 2, south /
+// north sides along columns i = pos - 2 including the corner columns, where
+// d is clamped along the side.  Returns false where the position is unused.
+template <typename real>
+__device__ inline bool ghost_site(const Geo &g, const real *d_r, int side, int layer, int pos, double &x,
+                                  double &y, double &dadj)
+{
+    const int along = pos - 2;
+    if (side < 2) {
+        if (along < 0 || along >= g.ny) return false;
+        const int gi = side == 0 ? -1 - layer : g.nx + layer;
+        x = (gi + 0.5) * g.dx;
+        y = (along + 0.5) * g.dy;
+        dadj = (double)d_r[(size_t)along * g.px + (side == 0 ? 0 : g.nx - 1)];
+    } else {
+        if (along < -2 || along > g.nx + 1) return false;
+        const int gj = side == 2 ? -1 - layer : g.ny + layer;
+        const int ia = along < 0 ? 0 : (along > g.nx - 1 ? g.nx - 1 : along);
+        x = (along + 0.5) * g.dx;
+        y = (gj + 0.5) * g.dy;
+        dadj = (double)d_r[(size_t)(side == 2 ? 0 : g.ny - 1) * g.px + ia];
+    }
+    return true;
+}
+
+// The interior cell whose depth ghost_site reads for table position pos.
+__device__ __forceinline__ void ghost_adjacent(const Geo &g, int side, int pos, int &i, int &j)
+{
+    const int along = pos - 2;
+    if (side < 2) {
+        i = side == 0 ? 0 : g.nx - 1;
+        j = along;
+    } else {
+        i = along < 0 ? 0 : (along > g.nx - 1 ? g.nx - 1 : along);
+        j = side == 2 ? 0 : g.ny - 1;
+    }
+}
+
 }  // namespace cel

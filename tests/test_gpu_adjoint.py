@@ -287,13 +287,21 @@ def _tilted_bed(model, K, friction, nsteps=10):
     return s, gauges, X, Y
 
 
-@pytest.mark.parametrize("model,K,friction", [(0, 0, 2), (0, 1, 1), (1, 1, 2)],
-                         ids=["bsnq-K0-manning", "bsnq-K1-quadratic", "nlsw-K1-manning"])
-def test_bed_gradient_matches_oracle_away_from_kinks(model, K, friction):
+@pytest.mark.parametrize("model,K,friction,sine", [(0, 0, 2, False), (0, 1, 1, False), (1, 1, 2, False),
+                                                   (0, 1, 1, True), (1, 0, 2, True)],
+                         ids=["bsnq-K0-manning", "bsnq-K1-quadratic", "nlsw-K1-manning",
+                              "bsnq-K1-sine", "nlsw-K0-sine"])
+def test_bed_gradient_matches_oracle_away_from_kinks(model, K, friction, sine):
     """dL/dz: the face beds of the reconstruction and the flux, the bed slope,
     friction, the dispersive and mixed terms' depth and the line systems'
-    rows (Eq. 23), through the corners to the cell-centre bed."""
+    rows (Eq. 23), through the corners to the cell-centre bed; with a sine
+    maker on the west also its ghost values, which follow the adjacent depth
+    through the Eckart wave number (Eq. 25-29), in the fluxes, the dispersive
+    terms and the line solves' boundary rows."""
+    from paper_1611_05984_gb300 import scenarios as sc
     s, gauges, X, Y = _tilted_bed(model, K, friction)
+    if sine:
+        s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.002, 4.0, 0.2, 0.3), (0.001, 2.5, -0.3, 1.1)))
     rng = np.random.default_rng(21 + model + 2 * K)
     obs = 0.01 * rng.standard_normal((s.steps, len(gauges)))
     loss, _, _, _, gz = _gpu_gradient(s, gauges, obs, ckpt=3, bed=True)
@@ -463,5 +471,33 @@ def test_gradients_on_32_random_directions():
             fd = (_oracle_loss_bed(s, s.z + eps * v, gauges, obs)
                   - _oracle_loss_bed(s, s.z - eps * v, gauges, obs)) / (2 * eps)
             ad = float(np.sum(gz * v))
+        errs.append(abs(ad - fd) / abs(fd))
+    assert max(errs) <= 1e-3, errs
+
+
+@pytest.mark.parametrize("model", [0, 1], ids=["bsnq", "nlsw"])
+def test_bed_gradient_through_the_sine_makers_ghosts(model):
+    """The sine maker's ghost values (Eq. 25-28) follow the depth of the
+    cell beside them: the wave number by Eckart (Eq. 29) and the celerity
+    w / k.  A 3 cm + 2 cm maker, gauges in the first four columns and bed
+    directions concentrated on the west columns make that path about 2 % of
+    <dL/dz, v> (the celerity's depth derivative times the ghost discharge
+    against the flux's own bed terms), so leaving it out would fail the 1e-3
+    bound; a short run keeps the state off the limiter's kinks."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    s, _, X, Y = _tilted_bed(model, 1, 1, nsteps=6)
+    s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.03, 4.0, 0.2, 0.3), (0.02, 2.5, -0.3, 1.1)))
+    gauges = [(i, j) for i in range(4) for j in (6, 13, 20, 27)]
+    rng = np.random.default_rng(61 + model)
+    obs = 0.01 * rng.standard_normal((s.steps, len(gauges)))
+    loss, _, _, _, gz = _gpu_gradient(s, gauges, obs, ckpt=2, bed=True)
+    assert abs(loss - _oracle_loss_bed(s, s.z, gauges, obs)) <= 1e-9 * loss
+    eps = 1e-5
+    errs = []
+    for _ in range(6):
+        v = np.exp(-(X ** 2) / 1.0) * (1.0 + 0.5 * np.sin(2 * math.pi * Y / rng.uniform(4.0, 12.0) + rng.uniform(0, 6)))
+        v *= 1e-2 * rng.choice([-1.0, 1.0])
+        fd = (_oracle_loss_bed(s, s.z + eps * v, gauges, obs) - _oracle_loss_bed(s, s.z - eps * v, gauges, obs)) / (2 * eps)
+        ad = float(np.sum(gz * v))
         errs.append(abs(ad - fd) / abs(fd))
     assert max(errs) <= 1e-3, errs
