@@ -433,7 +433,9 @@ __global__ void k_adj_hist(AdjArgs<real> A)
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
     const int k = j * G.nx + i;
-    const real m[5] = {A.lw[k], A.ldU[k], A.ldV[k], A.ldU[k], A.ldV[k]};
+    const real mu = A.muX ? A.muX[(size_t)j * G.px + i] : A.ldU[k];
+    const real mv = A.muY ? A.muY[(size_t)i * G.py + j] : A.ldV[k];
+    const real m[5] = {A.lw[k], mu, mv, mu, mv};
 #pragma unroll
     for (int v = 0; v < 5; v++) {
         if (v >= 3 && !A.bsnq) break;
@@ -441,19 +443,13 @@ __global__ void k_adj_hist(AdjArgs<real> A)
         A.G0[v][k] += c0 * m[v];
         if (A.G1[v]) A.G1[v][k] += c1 * m[v];
         if (A.G2[v]) A.G2[v][k] += c2 * m[v];
+        if (A.H0[v]) A.H0[v][k] = (v < 3 ? A.hc : A.he) * m[v];
     }
-}
-
-template <typename real>
-__global__ void k_adj_add(AdjArgs<real> A, const real *xw, const real *xP, const real *xQ)
-{
-    const Geo &G = A.geo;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    const int k = j * G.nx + i;
-    A.lw[k] += xw[k];
-    A.lP[k] += xP[k];
-    A.lQ[k] += xQ[k];
+    if (A.accw) {
+        A.accw[k] += m[0];
+        A.accP[k] += A.lP[k];
+        A.accQ[k] += A.lQ[k];
+    }
 }
 
 // Bed slope and friction (Eq. 9-10, 31-32) at cell (i, j): no neighbours.
@@ -1019,7 +1015,7 @@ __global__ void k_adj_bed_z(AdjArgs<real> A, real *grad_z)
 }
 
 // The adjoint of P and Q into the line solver's layouts (x-rows [ny][px],
-// y-columns [nx][py]) and the transposed solves' solutions back.
+// y-columns [nx][py]), the transposed solves' right sides.
 template <typename real>
 __global__ void k_adj_pack(Geo g, const real *lP, const real *lQ, real *X, real *Yc)
 {
@@ -1028,16 +1024,6 @@ __global__ void k_adj_pack(Geo g, const real *lP, const real *lQ, real *X, real 
     const size_t k = (size_t)j * g.nx + i;
     X[(size_t)j * g.px + i] = lP[k];
     Yc[(size_t)i * g.py + j] = lQ[k];
-}
-
-template <typename real>
-__global__ void k_adj_unpack(Geo g, const real *X, const real *Yc, real *ldU, real *ldV)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    const size_t k = (size_t)j * g.nx + i;
-    ldU[k] = X[(size_t)j * g.px + i];
-    ldV[k] = Yc[(size_t)i * g.py + j];
 }
 
 // The misfit at the gauges after step n enters the adjoint of w^n.
@@ -1057,15 +1043,6 @@ cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st)
     dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
     k_adj_mask<real><<<g, b, 0, st>>>(a);
     return cudaGetLastError();
-}
-
-template <typename real>
-cudaError_t launch_adjoint_solves(const AdjArgs<real> &a, cudaStream_t st)
-{
-    if (a.bsnq) return cudaErrorInvalidValue;   // the Boussinesq solves go through launch_lines_transposed
-    const size_t bytes = sizeof(real) * (size_t)a.geo.nx * a.geo.ny;   // NLSW: P = U*, Q = V*
-    cudaError_t e = cudaMemcpyAsync(a.ldU, a.lP, bytes, cudaMemcpyDeviceToDevice, st);
-    return e != cudaSuccess ? e : cudaMemcpyAsync(a.ldV, a.lQ, bytes, cudaMemcpyDeviceToDevice, st);
 }
 
 template <typename real>
@@ -1136,20 +1113,10 @@ cudaError_t launch_adjoint_bed_final(const AdjArgs<real> &a, const real *w0, con
 }
 
 template <typename real>
-cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
-                               cudaStream_t st)
+cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, cudaStream_t st)
 {
     dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
-    k_adj_add<real><<<g, b, 0, st>>>(a, xw, xP, xQ);
-    return cudaGetLastError();
-}
-
-template <typename real>
-cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int back, cudaStream_t st)
-{
-    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
-    if (back) k_adj_unpack<real><<<g, b, 0, st>>>(a.geo, X, Yc, a.ldU, a.ldV);
-    else k_adj_pack<real><<<g, b, 0, st>>>(a.geo, a.lP, a.lQ, X, Yc);
+    k_adj_pack<real><<<g, b, 0, st>>>(a.geo, a.lP, a.lQ, X, Yc);
     return cudaGetLastError();
 }
 
@@ -1163,12 +1130,9 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
 
 #define CEL_ADJ_INSTANTIATE(real)                                                                        \
     template cudaError_t launch_adjoint_mask<real>(const AdjArgs<real> &, cudaStream_t);                 \
-    template cudaError_t launch_adjoint_solves<real>(const AdjArgs<real> &, cudaStream_t);               \
     template cudaError_t launch_adjoint_hist<real>(const AdjArgs<real> &, cudaStream_t);                 \
     template cudaError_t launch_adjoint_vjp<real>(const AdjArgs<real> &, cudaStream_t);                  \
-    template cudaError_t launch_adjoint_add<real>(const AdjArgs<real> &, const real *, const real *,      \
-                                                  const real *, cudaStream_t);                          \
-    template cudaError_t launch_adjoint_pack<real>(const AdjArgs<real> &, real *, real *, int, cudaStream_t); \
+    template cudaError_t launch_adjoint_pack<real>(const AdjArgs<real> &, real *, real *, cudaStream_t);  \
     template cudaError_t launch_face_vjp_check<real>(const real *, int, real *, cudaStream_t);            \
     template cudaError_t launch_adjoint_tri_bed<real>(const AdjArgs<real> &, const real *, const real *,   \
                                                       const real *, const real *, const real *,         \

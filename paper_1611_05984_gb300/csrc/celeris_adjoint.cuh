@@ -10,8 +10,8 @@ namespace cel {
 // after it; lw, lP, lQ the adjoint (in: of the state after the step, out: of
 // the state before it); G0, G1, G2 the adjoint of this step's right sides
 // and of the two before it, per component E, F, G, F*, G*; ldU, ldV the
-// adjoint of the U* and V* increments (the line solves' right sides); tri a
-// [ny][nx] scratch for the transposed solves.
+// adjoint of the U* and V* increments (the line solves' right sides) in the
+// dense layout, where the history phase reads them (see muX, muY).
 template <typename real>
 struct AdjArgs {
     Geo geo;
@@ -21,7 +21,7 @@ struct AdjArgs {
     const real *w, *P, *Q, *w_next;
     real *lw, *lP, *lQ;
     real *G0[5], *G1[5], *G2[5];
-    real *ldU, *ldV, *tri;
+    const real *ldU, *ldV;
     // the bed's adjoints, or NULL: lBc at the corners (Bc's layout), lBb of
     // the cell bed Bbar and ld of the still-water depth d on the cells with
     // a one-cell ring ([ny + 2][nx + 2], cell (i, j) at [j + 1][i + 1])
@@ -30,26 +30,31 @@ struct AdjArgs {
     real *lg;              // adjoint of the sine makers' ghost values (the ghost table's layout), or NULL
     real c0, c1, c2;       // weights of R^n, R^{n-1}, R^{n-2} in this step's update
     real e0, e1, e2;       // weights of F*^n, F*^{n-1}, F*^{n-2} (Boussinesq)
+    // optional parts of the history phase: the U*, V* adjoints read from
+    // the transposed solves' line layouts (muX [ny][px], muY [nx][py])
+    // instead of ldU, ldV; a second right side H = (hc E, F, G; he F*, G*)
+    // weights written (not added) to H0; the masked adjoint added to acc
+    const real *muX, *muY;
+    real *H0[5];
+    real hc, he;
+    real *accw, *accP, *accQ;
     int bsnq;
     int final_stage;       // the masks include the sponge
     int tsel;              // sine-maker ghosts at t^n (0, predictor) or t^{n+1} (1, corrector)
 };
 
-// The phases of one stage's reverse: masks, transposed solves (NLSW only:
-// a copy; the Boussinesq solves go through launch_lines_transposed),
-// history, the right sides' Jacobians transposed.  G1 and G2 may be NULL in
-// the history phase.
+// The phases of one stage's reverse: masks, the transposed solves (through
+// launch_lines_transposed), history, the right sides' Jacobians transposed.
+// G1 and G2 may be NULL in the history phase.
 template <typename real>
 cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st);
-template <typename real>
-cudaError_t launch_adjoint_solves(const AdjArgs<real> &a, cudaStream_t st);
 template <typename real>
 cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st);
 template <typename real>
 cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st);
-// back = 0: lP, lQ into X ([ny][px]) and Yc ([nx][py]); back = 1: X, Yc into ldU, ldV
+// lP, lQ into X ([ny][px]) and Yc ([nx][py])
 template <typename real>
-cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, int back, cudaStream_t st);
+cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, cudaStream_t st);
 // The line systems' dependence on d (Eq. 23): with x the stage's solutions
 // and mu the transposed solves' solutions (line layouts: x-rows [ny][px],
 // y-columns [nx][py]) and dr, dc the depths in the same layouts,
@@ -73,10 +78,6 @@ cudaError_t launch_adjoint_bed_final(const AdjArgs<real> &a, const real *w0, con
 // (inputs [n][22], outputs [n][30]; see cel_adjoint_face_selfcheck).
 template <typename real>
 cudaError_t launch_face_vjp_check(const real *in, int n, real *out, cudaStream_t st);
-// lw += xw, lP += xP, lQ += xQ
-template <typename real>
-cudaError_t launch_adjoint_add(const AdjArgs<real> &a, const real *xw, const real *xP, const real *xQ,
-                               cudaStream_t st);
 template <typename real>
 cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, int ng, const real *rec,
                                   const real *obs, cudaStream_t st);

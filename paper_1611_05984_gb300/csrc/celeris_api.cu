@@ -1568,7 +1568,7 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
     const int K = s->params.corrector_iters;
     L.seg = take(L.cells_bytes * 3 * (size_t)(C + 1));
     L.iter = take(L.cells_bytes * 3 * (size_t)K * (size_t)(C + 1));   // the iterates of every step
-    L.lam = take(L.cells_bytes * 12);  // 3 sets of (w, P, Q); the U*, V* increments; solve scratch
+    L.lam = take(L.cells_bytes * 9);   // 3 sets of (w, P, Q)
     L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
@@ -1651,8 +1651,8 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     }
     // reverse.  lam sets 0-2: the adjoint of the state after the step (then
     // before it), of the present iterate, and the accumulator of the state
-    // before the step; 9, 10: the U*, V* increments; 11: solve scratch.
-    CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 12, st), "adjoint");
+    // before the step.
+    CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 9, st), "adjoint");
     CEL_CUDA(s, cudaMemsetAsync(scr + L.G, 0, L.cells_bytes * 20, st), "adjoint");
     AdjArgs<real> a;
     memset(&a, 0, sizeof(a));
@@ -1661,9 +1661,6 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     a.c = make_coef<real>(s->geo, s->phy, s->bnd);
     a.Bc = s->at<real>(s->lay.Bc);
     a.ghost = s->at<real>(s->lay.ghost);
-    a.ldU = lam(9);
-    a.ldV = lam(10);
-    a.tri = lam(11);
     a.bsnq = s->params.model == CEL_BSNQ;
     if (bed) {
         a.lBc = reinterpret_cast<real *>(scr + L.lBc);
@@ -1705,10 +1702,20 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     };
     // the transposed line solves (Boussinesq) through the forward's line
     // solver, in the solver's U* and V* increment buffers (idle here)
-    auto solves = [&](const AdjArgs<real> &x) -> cudaError_t {
-        if (!x.bsnq) return launch_adjoint_solves<real>(x, st);
+    // after it the history phase reads the U*, V* adjoints from x.muX, x.muY
+    // (Boussinesq: the solutions in the line layouts) or x.ldU, x.ldV (the
+    // shallow-water model, where U* = P: the masked lP, lQ themselves)
+    auto solves = [&](AdjArgs<real> &x) -> cudaError_t {
+        if (!x.bsnq) {
+            x.ldU = x.lP;
+            x.ldV = x.lQ;
+            x.muX = x.muY = nullptr;
+            return cudaSuccess;
+        }
         real *X = s->at<real>(s->lay.U), *Yc = s->at<real>(s->lay.Vc);
-        cudaError_t e = launch_adjoint_pack<real>(x, X, Yc, 0, st);
+        x.muX = X;
+        x.muY = Yc;
+        cudaError_t e = launch_adjoint_pack<real>(x, X, Yc, st);
         if (e != cudaSuccess) return e;
         LinePair<real> lp;
         for (int dir = 0; dir < 2; dir++) {
@@ -1719,11 +1726,11 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
             lp.L[dir].sol = buf;
             lp.L[dir].identity = 0;
         }
-        e = launch_lines_transposed<real>(lp, st);
-        return e != cudaSuccess ? e : launch_adjoint_pack<real>(x, X, Yc, 1, st);
+        return launch_lines_transposed<real>(lp, st);
     };
     // the line systems' dependence on d: the stage's solutions again from
-    // its captured right sides, with the transposed solves' in ldU, ldV
+    // its captured right sides, with the transposed solves' still in the
+    // solver's U*, V* buffers
     auto tri_bed = [&](const AdjArgs<real> &x, int k, int stage) -> cudaError_t {
         if (!bed_lines) return cudaSuccess;
         real *Rx = reinterpret_cast<real *>(rhsf(k, stage)), *Ry = reinterpret_cast<real *>(rhsf(k, stage) + L.line_bytes);
@@ -1742,7 +1749,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                                 : launch_adjoint_tri_bed<real>(x, Xs, Ys, s->at<real>(s->lay.U), s->at<real>(s->lay.Vc),
                                                                s->at<real>(s->lay.dr), s->at<real>(s->lay.dc), st);
     };
-    auto full_step = [&](const AdjArgs<real> &x, int k) -> cudaError_t {
+    auto full_step = [&](AdjArgs<real> &x, int k) -> cudaError_t {
         cudaError_t e = launch_adjoint_mask<real>(x, st);
         if (e == cudaSuccess) e = solves(x);
         if (e == cudaSuccess) e = tri_bed(x, k, 0);
@@ -1808,18 +1815,23 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                     CEL_CUDA(s, launch_adjoint_mask<real>(b, st), "adjoint mask");
                     CEL_CUDA(s, solves(b), "adjoint solves");
                     CEL_CUDA(s, tri_bed(b, k, stg), "adjoint solves");
-                    // the AM4 base (Eq. 18-20): w^n + dt/24 (19 R^n - 5 R^{n-1} + R^{n-2}) - F*^n
+                    // one pass: the AM4 base (Eq. 18-20), w^n + dt/24 (19 R^n - 5 R^{n-1}
+                    // + R^{n-2}) - F*^n, into the history slots; the right side at the
+                    // iterate before this stage, 9 dt/24 R + F*, written to slot 3; the
+                    // masked adjoint (the state's own path) added to acc
                     coefs(b, 19.0 * c24, -5.0 * c24, c24, -1.0, 0.0, 0.0);
                     setG(b, sn, sm1, sm2);
+                    for (int v = 0; v < 5; v++) b.H0[v] = Gb(3, v);
+                    b.hc = real(9.0 * c24);
+                    b.he = real(1.0);
+                    b.accw = lam(3 * acc);
+                    b.accP = lam(3 * acc + 1);
+                    b.accQ = lam(3 * acc + 2);
                     CEL_CUDA(s, launch_adjoint_hist<real>(b, st), "adjoint history");
-                    AdjArgs<real> x = a;
-                    setl(x, acc);
-                    CEL_CUDA(s, launch_adjoint_add<real>(x, b.lw, b.lP, b.lQ, st), "adjoint");
-                    // the right side at the iterate before this stage: 9 dt/24 R + F*
-                    CEL_CUDA(s, cudaMemsetAsync(Gb(3, 0), 0, L.cells_bytes * 5, st), "adjoint");
+                    for (int v = 0; v < 5; v++) b.H0[v] = nullptr;
+                    b.accw = b.accP = b.accQ = nullptr;
                     coefs(b, 9.0 * c24, 0.0, 0.0, 1.0, 0.0, 0.0);
                     setG(b, 3, -1, -1);
-                    CEL_CUDA(s, launch_adjoint_hist<real>(b, st), "adjoint history");
                     AdjArgs<real> v = b;
                     v.tsel = 1;   // the corrector stages read the ghosts at t^{n+1}
                     setl(v, nxt);
@@ -1840,10 +1852,12 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 CEL_CUDA(s, tri_bed(p, k, 0), "adjoint solves");
                 coefs(p, 23.0 * c12, -16.0 * c12, 5.0 * c12, 2.0, -3.0, 1.0);
                 setG(p, sn, sm1, sm2);
+                p.accw = lam(3 * acc);
+                p.accP = lam(3 * acc + 1);
+                p.accQ = lam(3 * acc + 2);
                 CEL_CUDA(s, launch_adjoint_hist<real>(p, st), "adjoint history");
                 AdjArgs<real> x = a;
                 setl(x, acc);
-                CEL_CUDA(s, launch_adjoint_add<real>(x, p.lw, p.lP, p.lQ, st), "adjoint");
                 // R^n and F*^n at the state before the step
                 x.w = segf(k, 0);
                 x.P = segf(k, 1);
