@@ -1545,6 +1545,8 @@ namespace {
 struct AdjLayout {
     size_t ckpt_bytes, cells_bytes, line_bytes;
     size_t ckpt, seg, iter, lam, G, rec, gij, total;
+    size_t seg_slot, iter_slot, rhs_slot;   // two slots each: one segment recomputed while the next is reversed
+    size_t gtab, xy;                        // the reverse's own ghost table and line-layout scratch
     size_t rhs, xs, lBc, lBb, ld, ldl, lg;   // the bed's gradient (bed != 0)
     size_t ghost_bytes;
     int nseg, bed;
@@ -1566,17 +1568,23 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
     };
     L.ckpt = take(L.ckpt_bytes * (size_t)(L.nseg + 1));   // + the final state
     const int K = s->params.corrector_iters;
-    L.seg = take(L.cells_bytes * 3 * (size_t)(C + 1));
-    L.iter = take(L.cells_bytes * 3 * (size_t)K * (size_t)(C + 1));   // the iterates of every step
+    L.seg_slot = L.cells_bytes * 3 * (size_t)(C + 1);
+    L.seg = take(L.seg_slot * 2);
+    L.iter_slot = L.cells_bytes * 3 * (size_t)K * (size_t)(C + 1);   // the iterates of every step
+    L.iter = take(L.iter_slot * 2);
     L.lam = take(L.cells_bytes * 9);   // 3 sets of (w, P, Q)
     L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
     L.rhs = L.xs = L.lBc = L.lBb = L.ld = L.ldl = L.lg = 0;
+    L.rhs_slot = 0;
     L.ghost_bytes = ghost_index(2, 0, 0, 0, 0, (s->geo.nx > s->geo.ny ? s->geo.nx : s->geo.ny) + 4) * s->es;
+    L.gtab = take(L.ghost_bytes);
+    L.xy = take(L.line_bytes * 2);
     if (bed) {
         const bool lines = s->params.model == CEL_BSNQ;
-        L.rhs = take(lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0);   // every stage's right sides
+        L.rhs_slot = lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0;   // every stage's right sides
+        L.rhs = take(L.rhs_slot * 2);
         L.xs = take(lines ? L.line_bytes * 2 : 0);                                  // and their solutions
         L.ldl = take(lines ? L.line_bytes * 2 : 0);                                 // ld of the line systems
         L.lBc = take((size_t)s->geo.pc * (s->grid.ny + 3) * s->es);
@@ -1619,17 +1627,25 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     real *rec = reinterpret_cast<real *>(scr + L.rec);
     CEL_CUDA(s, cudaMemcpyAsync(gij, gij_host, sizeof(int32_t) * 2 * ng, cudaMemcpyHostToDevice, st), "adjoint gauges");
     auto ckpt = [&](int k) { return scr + L.ckpt + L.ckpt_bytes * (size_t)k; };
-    auto segf = [&](int k, int v) { return reinterpret_cast<real *>(scr + L.seg + L.cells_bytes * (3 * (size_t)k + v)); };
+    // segment sg's recomputed data live in slot sg & 1
+    int slot = 0;   // the slot the reverse is reading
+    auto segf_in = [&](int sl, int k, int v) {
+        return reinterpret_cast<real *>(scr + L.seg + L.seg_slot * sl + L.cells_bytes * (3 * (size_t)k + v));
+    };
+    auto segf = [&](int k, int v) { return segf_in(slot, k, v); };
     auto lam = [&](int v) { return reinterpret_cast<real *>(scr + L.lam + L.cells_bytes * v); };
-    auto Gb = [&](int slot, int v) { return reinterpret_cast<real *>(scr + L.G + L.cells_bytes * (5 * slot + v)); };
+    auto Gb = [&](int sl, int v) { return reinterpret_cast<real *>(scr + L.G + L.cells_bytes * (5 * sl + v)); };
     const int K = s->params.corrector_iters;
-    auto iterf = [&](int k, int stage, int v) {   // iterate after `stage` of step k of the segment
-        return reinterpret_cast<real *>(scr + L.iter + L.cells_bytes * (3 * ((size_t)k * K + stage) + v));
+    auto iterf_in = [&](int sl, int k, int stage, int v) {   // iterate after `stage` of step k of the segment
+        return reinterpret_cast<real *>(scr + L.iter + L.iter_slot * sl +
+                                        L.cells_bytes * (3 * ((size_t)k * K + stage) + v));
     };
+    auto iterf = [&](int k, int stage, int v) { return iterf_in(slot, k, stage, v); };
     const bool bed = grad_z != nullptr, bed_lines = bed && s->params.model == CEL_BSNQ;
-    auto rhsf = [&](int k, int stage) {   // right sides of `stage` of step k of the segment
-        return scr + L.rhs + L.line_bytes * 2 * ((size_t)k * (K + 1) + stage);
+    auto rhsf_in = [&](int sl, int k, int stage) {   // right sides of `stage` of step k of the segment
+        return scr + L.rhs + L.rhs_slot * sl + L.line_bytes * 2 * ((size_t)k * (K + 1) + stage);
     };
+    auto rhsf = [&](int k, int stage) { return rhsf_in(slot, k, stage); };
     const int64_t step0 = s->step;
     cel_status stt;
     // forward, with checkpoints and the gauge records
@@ -1649,9 +1665,40 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         for (size_t k = 0; k < r.size(); k++) acc += 0.5 * ((double)r[k] - (double)o[k]) * ((double)r[k] - (double)o[k]);
         if (loss) *loss = acc;
     }
-    // reverse.  lam sets 0-2: the adjoint of the state after the step (then
-    // before it), of the present iterate, and the accumulator of the state
-    // before the step.
+    // reverse, on a stream of its own: segment sg is reversed while segment
+    // sg - 1 is recomputed on the solver's stream (the solver's workspace
+    // belongs to the recomputation; the reverse has its own ghost table and
+    // line scratch).  Events order the two: rec[slot] when a slot's segment
+    // is recomputed, rev[slot] when its reverse is done with it.
+    struct Streams {
+        cudaStream_t rs = nullptr;
+        cudaEvent_t rec[2] = {nullptr, nullptr}, rev[2] = {nullptr, nullptr}, fin = nullptr;
+        ~Streams()
+        {
+            if (rs) {
+                cudaStreamSynchronize(rs);
+                cudaStreamDestroy(rs);
+            }
+            for (int k = 0; k < 2; k++) {
+                if (rec[k]) cudaEventDestroy(rec[k]);
+                if (rev[k]) cudaEventDestroy(rev[k]);
+            }
+            if (fin) cudaEventDestroy(fin);
+        }
+    } ss;
+    CEL_CUDA(s, cudaStreamCreateWithFlags(&ss.rs, cudaStreamNonBlocking), "adjoint stream");
+    for (int k = 0; k < 2; k++) {
+        CEL_CUDA(s, cudaEventCreateWithFlags(&ss.rec[k], cudaEventDisableTiming), "adjoint events");
+        CEL_CUDA(s, cudaEventCreateWithFlags(&ss.rev[k], cudaEventDisableTiming), "adjoint events");
+    }
+    CEL_CUDA(s, cudaEventCreateWithFlags(&ss.fin, cudaEventDisableTiming), "adjoint events");
+    const cudaStream_t fst = st;   // forward and recomputation
+    st = ss.rs;                    // the reverse
+    real *gtab = reinterpret_cast<real *>(scr + L.gtab);
+    real *Xr = reinterpret_cast<real *>(scr + L.xy), *Yr = reinterpret_cast<real *>(scr + L.xy + L.line_bytes);
+    // lam sets 0-2: the adjoint of the state after the step (then before
+    // it), of the present iterate, and the accumulator of the state before
+    // the step.
     CEL_CUDA(s, cudaMemsetAsync(scr + L.lam, 0, L.cells_bytes * 9, st), "adjoint");
     CEL_CUDA(s, cudaMemsetAsync(scr + L.G, 0, L.cells_bytes * 20, st), "adjoint");
     AdjArgs<real> a;
@@ -1660,7 +1707,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     a.phy = s->phy;
     a.c = make_coef<real>(s->geo, s->phy, s->bnd);
     a.Bc = s->at<real>(s->lay.Bc);
-    a.ghost = s->at<real>(s->lay.ghost);
+    a.ghost = gtab;
     a.bsnq = s->params.model == CEL_BSNQ;
     if (bed) {
         a.lBc = reinterpret_cast<real *>(scr + L.lBc);
@@ -1700,8 +1747,15 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         x.e1 = real(e1);
         x.e2 = real(e2);
     };
+    // the line solves' arguments for the reverse: its own ghost table
+    auto rline = [&](const AdjArgs<real> &x, int dir) {
+        LineArgs<real> l = line_args<real>(s, x.c, dir, 0, 0);
+        l.ghost = gtab;
+        l.identity = 0;
+        return l;
+    };
     // the transposed line solves (Boussinesq) through the forward's line
-    // solver, in the solver's U* and V* increment buffers (idle here)
+    // solver, in the reverse's line-layout scratch;
     // after it the history phase reads the U*, V* adjoints from x.muX, x.muY
     // (Boussinesq: the solutions in the line layouts) or x.ldU, x.ldV (the
     // shallow-water model, where U* = P: the masked lP, lQ themselves)
@@ -1712,42 +1766,37 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
             x.muX = x.muY = nullptr;
             return cudaSuccess;
         }
-        real *X = s->at<real>(s->lay.U), *Yc = s->at<real>(s->lay.Vc);
-        x.muX = X;
-        x.muY = Yc;
-        cudaError_t e = launch_adjoint_pack<real>(x, X, Yc, st);
+        x.muX = Xr;
+        x.muY = Yr;
+        cudaError_t e = launch_adjoint_pack<real>(x, Xr, Yr, st);
         if (e != cudaSuccess) return e;
         LinePair<real> lp;
         for (int dir = 0; dir < 2; dir++) {
-            lp.L[dir] = line_args<real>(s, x.c, dir, 0, 0);
-            real *buf = dir == 0 ? X : Yc;
+            lp.L[dir] = rline(x, dir);
+            real *buf = dir == 0 ? Xr : Yr;
             lp.L[dir].rhs = buf;
             lp.L[dir].base = buf;
             lp.L[dir].sol = buf;
-            lp.L[dir].identity = 0;
         }
         return launch_lines_transposed<real>(lp, st);
     };
     // the line systems' dependence on d: the stage's solutions again from
-    // its captured right sides, with the transposed solves' still in the
-    // solver's U*, V* buffers
+    // its captured right sides, with the transposed solves' still in Xr, Yr
     auto tri_bed = [&](const AdjArgs<real> &x, int k, int stage) -> cudaError_t {
         if (!bed_lines) return cudaSuccess;
         real *Rx = reinterpret_cast<real *>(rhsf(k, stage)), *Ry = reinterpret_cast<real *>(rhsf(k, stage) + L.line_bytes);
         real *Xs = reinterpret_cast<real *>(scr + L.xs), *Ys = reinterpret_cast<real *>(scr + L.xs + L.line_bytes);
         LinePair<real> lp;
         for (int dir = 0; dir < 2; dir++) {
-            lp.L[dir] = line_args<real>(s, x.c, dir, 0, 0);
+            lp.L[dir] = rline(x, dir);
             lp.L[dir].rhs = dir == 0 ? Rx : Ry;
             lp.L[dir].base = dir == 0 ? Rx : Ry;
             lp.L[dir].sol = dir == 0 ? Xs : Ys;
-            lp.L[dir].identity = 0;
         }
         cudaError_t e = launch_lines_solution<real>(lp, st);
-        // mu: the transposed solves' solutions, still in the solver's U*, V* buffers
         return e != cudaSuccess ? e
-                                : launch_adjoint_tri_bed<real>(x, Xs, Ys, s->at<real>(s->lay.U), s->at<real>(s->lay.Vc),
-                                                               s->at<real>(s->lay.dr), s->at<real>(s->lay.dc), st);
+                                : launch_adjoint_tri_bed<real>(x, Xs, Ys, Xr, Yr, s->at<real>(s->lay.dr),
+                                                               s->at<real>(s->lay.dc), st);
     };
     auto full_step = [&](AdjArgs<real> &x, int k) -> cudaError_t {
         cudaError_t e = launch_adjoint_mask<real>(x, st);
@@ -1761,31 +1810,45 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(N - 1) * ng, obs + (size_t)(N - 1) * ng, st),
              "adjoint misfit");
     const double dt = s->params.dt, c12 = dt / 12.0, c24 = dt / 24.0;
-    for (int sg = L.nseg - 1; sg >= 0; sg--) {
-        const int n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
-        if ((stt = cel_load_checkpoint(s, ckpt(sg), L.ckpt_bytes)) != CEL_OK) return stt;
+    bool used[2] = {false, false};
+    // recompute segment sg into slot sg & 1 on the solver's stream, once the
+    // reverse of the segment that held the slot is done
+    auto recompute = [&](int sg) -> cel_status {
+        const int sl = sg & 1, n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
+        if (used[sl]) CEL_CUDA(s, cudaStreamWaitEvent(fst, ss.rev[sl], 0), "adjoint order");
+        cel_status r = cel_load_checkpoint(s, ckpt(sg), L.ckpt_bytes);
+        if (r != CEL_OK) return r;
         for (int k = 0; k <= n1 - n0; k++) {
             CEL_CUDA(s, launch_get_state<real>(s->geo, s->at<real>(s->lay.w[s->cur]), s->at<real>(s->lay.P[s->pcur]),
-                                               s->at<real>(s->lay.Qc[s->pcur]), segf(k, 0), segf(k, 1), segf(k, 2), st),
+                                               s->at<real>(s->lay.Qc[s->pcur]), segf_in(sl, k, 0), segf_in(sl, k, 1),
+                                               segf_in(sl, k, 2), fst),
                      "adjoint states");
             if (k < n1 - n0) {
-                s->capture = K > 0 ? reinterpret_cast<unsigned char *>(iterf(k, 0, 0)) : nullptr;
+                s->capture = K > 0 ? reinterpret_cast<unsigned char *>(iterf_in(sl, k, 0, 0)) : nullptr;
                 s->capture_field = L.cells_bytes;
-                s->capture_rhs = bed_lines ? rhsf(k, 0) : nullptr;
+                s->capture_rhs = bed_lines ? rhsf_in(sl, k, 0) : nullptr;
                 s->capture_line = L.line_bytes;
-                stt = step_t<real>(s, 1);
+                r = step_t<real>(s, 1);
                 s->capture = nullptr;
                 s->capture_rhs = nullptr;
-                if (stt != CEL_OK) return stt;
+                if (r != CEL_OK) return r;
             }
         }
+        CEL_CUDA(s, cudaEventRecord(ss.rec[sl], fst), "adjoint order");
+        used[sl] = true;
+        return CEL_OK;
+    };
+    if ((stt = recompute(L.nseg - 1)) != CEL_OK) return stt;
+    for (int sg = L.nseg - 1; sg >= 0; sg--) {
+        const int n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
+        slot = sg & 1;
+        CEL_CUDA(s, cudaStreamWaitEvent(st, ss.rec[slot], 0), "adjoint order");
         for (int n = n1 - 1; n >= n0; n--) {
             const int k = n - n0;
             if (a.c.sine)
                 CEL_CUDA(s, launch_ghost_table<real>(s->geo, s->phy, s->bnd, s->at<real>(s->lay.dr),
                                                      s->at<double>(s->lay.ktab), (double)(step0 + n) * dt,
-                                                     (double)(step0 + n + 1) * dt, s->at<real>(s->lay.ghost),
-                                                     a.c.npos, st),
+                                                     (double)(step0 + n + 1) * dt, gtab, a.c.npos, st),
                          "adjoint ghosts");
             const int Kn = n >= 2 ? K : 0;
             const int sn = n % 3, sm1 = (n + 2) % 3, sm2 = (n + 1) % 3;
@@ -1878,6 +1941,8 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                          "adjoint misfit");
             CEL_CUDA(s, cudaMemsetAsync(Gb(sn, 0), 0, L.cells_bytes * 5, st), "adjoint");
         }
+        CEL_CUDA(s, cudaEventRecord(ss.rev[slot], st), "adjoint order");
+        if (sg > 0 && (stt = recompute(sg - 1)) != CEL_OK) return stt;   // overlaps this segment's reverse
     }
     CEL_CUDA(s, cudaMemcpyAsync(grad, lam(3 * lset), sizeof(real) * cells, cudaMemcpyDeviceToDevice, st),
              "adjoint gradient");
@@ -1886,7 +1951,11 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     if (eta_out)
         CEL_CUDA(s, cudaMemcpyAsync(eta_out, rec, sizeof(real) * (size_t)N * ng, cudaMemcpyDeviceToDevice, st),
                  "adjoint records");
-    return cel_load_checkpoint(s, ckpt(L.nseg), L.ckpt_bytes);   // leave the solver after step N
+    CEL_CUDA(s, cudaEventRecord(ss.fin, st), "adjoint order");
+    CEL_CUDA(s, cudaStreamWaitEvent(fst, ss.fin, 0), "adjoint order");
+    stt = cel_load_checkpoint(s, ckpt(L.nseg), L.ckpt_bytes);   // leave the solver after step N
+    if (stt == CEL_OK) CEL_CUDA(s, cudaStreamSynchronize(fst), "adjoint");
+    return stt;
 }
 
 cel_status adjoint_check(const cel_solver *, int N, int C, int ng, std::string &why)

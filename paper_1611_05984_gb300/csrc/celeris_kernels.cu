@@ -876,8 +876,10 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
                 own[u] = k < n ? bs[k] : real(0);
             }
         }
-        const uint32_t *mw = A.mask + (size_t)line * A.nwords;
-        for (int k = tid; k < A.nwords; k += T) smask[k] = mw[k];
+        if (kMode == 0) {   // the dry bits serve the epilogue alone
+            const uint32_t *mw = A.mask + (size_t)line * A.nwords;
+            for (int k = tid; k < A.nwords; k += T) smask[k] = mw[k];
+        }
         // right side and depth straight into their segment-major slots
         // (d = 0 on the padding rows: a = c = 0, b = 1)
 #pragma unroll
