@@ -420,8 +420,14 @@ __global__ void k_adj_mask(AdjArgs<real> A)
     const bool clamped = w1 - Bb <= tol;
     if (clamped && A.lBb) A.lBb[ring_index(G, i, j)] += A.lw[k] * (spw ? gam : real(1));   // w = Bbar there
     A.lw[k] = clamped ? real(0) : A.lw[k] * (spw ? gam : real(1));
-    A.lP[k] = dry ? real(0) : A.lP[k] * gam;
-    A.lQ[k] = dry ? real(0) : A.lQ[k] * gam;
+    const real lp = dry ? real(0) : A.lP[k] * gam, lq = dry ? real(0) : A.lQ[k] * gam;
+    A.lP[k] = lp;
+    A.lQ[k] = lq;
+    if (A.packX) {
+        A.packX[(size_t)j * G.px + i] = lp;
+        A.packY[(size_t)i * G.py + j] = lq;
+    }
+    if (A.zero[0]) A.zero[0][k] = A.zero[1][k] = A.zero[2][k] = real(0);
 }
 
 // Step 3: the history.  The increments of w, U* and V* weigh R^n, R^{n-1},
@@ -1014,18 +1020,6 @@ __global__ void k_adj_bed_z(AdjArgs<real> A, real *grad_z)
     atomicAdd(grad_z + (size_t)j1 * G.nx + i1, v);
 }
 
-// The adjoint of P and Q into the line solver's layouts (x-rows [ny][px],
-// y-columns [nx][py]), the transposed solves' right sides.
-template <typename real>
-__global__ void k_adj_pack(Geo g, const real *lP, const real *lQ, real *X, real *Yc)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    const size_t k = (size_t)j * g.nx + i;
-    X[(size_t)j * g.px + i] = lP[k];
-    Yc[(size_t)i * g.py + j] = lQ[k];
-}
-
 // The misfit at the gauges after step n enters the adjoint of w^n.
 template <typename real>
 __global__ void k_adj_misfit(AdjArgs<real> A, const int32_t *gij, int ng, const real *rec, const real *obs)
@@ -1113,14 +1107,6 @@ cudaError_t launch_adjoint_bed_final(const AdjArgs<real> &a, const real *w0, con
 }
 
 template <typename real>
-cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, cudaStream_t st)
-{
-    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
-    k_adj_pack<real><<<g, b, 0, st>>>(a.geo, a.lP, a.lQ, X, Yc);
-    return cudaGetLastError();
-}
-
-template <typename real>
 cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, int ng, const real *rec, const real *obs,
                                   cudaStream_t st)
 {
@@ -1132,7 +1118,6 @@ cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, in
     template cudaError_t launch_adjoint_mask<real>(const AdjArgs<real> &, cudaStream_t);                 \
     template cudaError_t launch_adjoint_hist<real>(const AdjArgs<real> &, cudaStream_t);                 \
     template cudaError_t launch_adjoint_vjp<real>(const AdjArgs<real> &, cudaStream_t);                  \
-    template cudaError_t launch_adjoint_pack<real>(const AdjArgs<real> &, real *, real *, cudaStream_t);  \
     template cudaError_t launch_face_vjp_check<real>(const real *, int, real *, cudaStream_t);            \
     template cudaError_t launch_adjoint_tri_bed<real>(const AdjArgs<real> &, const real *, const real *,   \
                                                       const real *, const real *, const real *,         \

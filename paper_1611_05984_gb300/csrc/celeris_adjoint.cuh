@@ -35,6 +35,10 @@ struct AdjArgs {
     // instead of ldU, ldV; a second right side H = (hc E, F, G; he F*, G*)
     // weights written (not added) to H0; the masked adjoint added to acc
     const real *muX, *muY;
+    // optional parts of the mask phase: the masked lP, lQ also written to
+    // the line layouts packX [ny][px], packY [nx][py] (the transposed solves'
+    // right sides); three dense fields zero[0..2] cleared
+    real *packX, *packY, *zero[3];
     real *H0[5];
     real hc, he;
     real *accw, *accP, *accQ;
@@ -52,9 +56,6 @@ template <typename real>
 cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st);
 template <typename real>
 cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st);
-// lP, lQ into X ([ny][px]) and Yc ([nx][py])
-template <typename real>
-cudaError_t launch_adjoint_pack(const AdjArgs<real> &a, real *X, real *Yc, cudaStream_t st);
 // The line systems' dependence on d (Eq. 23): with x the stage's solutions
 // and mu the transposed solves' solutions (line layouts: x-rows [ny][px],
 // y-columns [nx][py]) and dr, dc the depths in the same layouts,

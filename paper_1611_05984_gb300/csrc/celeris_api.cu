@@ -1768,9 +1768,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         }
         x.muX = Xr;
         x.muY = Yr;
-        cudaError_t e = launch_adjoint_pack<real>(x, Xr, Yr, st);
-        if (e != cudaSuccess) return e;
-        LinePair<real> lp;
+        LinePair<real> lp;   // the right sides: the mask phase wrote them to Xr, Yr
         for (int dir = 0; dir < 2; dir++) {
             lp.L[dir] = rline(x, dir);
             real *buf = dir == 0 ? Xr : Yr;
@@ -1798,8 +1796,18 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                                 : launch_adjoint_tri_bed<real>(x, Xs, Ys, Xr, Yr, s->at<real>(s->lay.dr),
                                                                s->at<real>(s->lay.dc), st);
     };
-    auto full_step = [&](AdjArgs<real> &x, int k) -> cudaError_t {
+    // the mask phase, writing the Boussinesq solves' right sides as well
+    auto mask = [&](AdjArgs<real> &x, int zero_set) -> cudaError_t {
+        x.packX = x.bsnq ? Xr : nullptr;
+        x.packY = x.bsnq ? Yr : nullptr;
+        for (int v = 0; v < 3; v++) x.zero[v] = zero_set >= 0 ? lam(3 * zero_set + v) : nullptr;
         cudaError_t e = launch_adjoint_mask<real>(x, st);
+        x.packX = x.packY = nullptr;
+        for (int v = 0; v < 3; v++) x.zero[v] = nullptr;
+        return e;
+    };
+    auto full_step = [&](AdjArgs<real> &x, int k) -> cudaError_t {
+        cudaError_t e = mask(x, -1);
         if (e == cudaSuccess) e = solves(x);
         if (e == cudaSuccess) e = tri_bed(x, k, 0);
         if (e == cudaSuccess) e = launch_adjoint_hist<real>(x, st);
@@ -1875,7 +1883,8 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                     setl(b, cur);
                     b.w_next = stg == Kn ? segf(k + 1, 0) : iterf(k, stg, 0);
                     b.final_stage = stg == Kn;
-                    CEL_CUDA(s, launch_adjoint_mask<real>(b, st), "adjoint mask");
+                    // the mask also clears the set the iterate's adjoint collects in
+                    CEL_CUDA(s, mask(b, nxt), "adjoint mask");
                     CEL_CUDA(s, solves(b), "adjoint solves");
                     CEL_CUDA(s, tri_bed(b, k, stg), "adjoint solves");
                     // one pass: the AM4 base (Eq. 18-20), w^n + dt/24 (19 R^n - 5 R^{n-1}
@@ -1898,7 +1907,6 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                     AdjArgs<real> v = b;
                     v.tsel = 1;   // the corrector stages read the ghosts at t^{n+1}
                     setl(v, nxt);
-                    CEL_CUDA(s, cudaMemsetAsync(lam(3 * nxt), 0, L.cells_bytes * 3, st), "adjoint");
                     v.w = iterf(k, stg - 1, 0);
                     v.P = iterf(k, stg - 1, 1);
                     v.Q = iterf(k, stg - 1, 2);
@@ -1910,7 +1918,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 setl(p, cur);
                 p.w_next = iterf(k, 0, 0);
                 p.final_stage = 0;
-                CEL_CUDA(s, launch_adjoint_mask<real>(p, st), "adjoint mask");
+                CEL_CUDA(s, mask(p, -1), "adjoint mask");
                 CEL_CUDA(s, solves(p), "adjoint solves");
                 CEL_CUDA(s, tri_bed(p, k, 0), "adjoint solves");
                 coefs(p, 23.0 * c12, -16.0 * c12, 5.0 * c12, 2.0, -3.0, 1.0);
