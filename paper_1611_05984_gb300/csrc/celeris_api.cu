@@ -1670,28 +1670,46 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     // belongs to the recomputation; the reverse has its own ghost table and
     // line scratch).  Events order the two: rec[slot] when a slot's segment
     // is recomputed, rev[slot] when its reverse is done with it.
+    // The line systems' depth term (a re-solve and a gather per stage, read
+    // by nothing until the end) runs on a third stream beside the stage's
+    // history and Jacobian passes: it starts when the transposed solves are
+    // done (event mu) and the reverse waits for it (event tri) before the
+    // next mask pass rewrites their solutions, before the ghost table is
+    // rewritten or its adjoints mapped, and before a segment's slot is freed.
     struct Streams {
-        cudaStream_t rs = nullptr;
-        cudaEvent_t rec[2] = {nullptr, nullptr}, rev[2] = {nullptr, nullptr}, fin = nullptr;
+        cudaStream_t rs = nullptr, ts = nullptr;
+        cudaEvent_t rec[2] = {nullptr, nullptr}, rev[2] = {nullptr, nullptr}, fin = nullptr, mu = nullptr,
+                    tri = nullptr;
         ~Streams()
         {
-            if (rs) {
-                cudaStreamSynchronize(rs);
-                cudaStreamDestroy(rs);
-            }
+            for (cudaStream_t q : {rs, ts})
+                if (q) {
+                    cudaStreamSynchronize(q);
+                    cudaStreamDestroy(q);
+                }
             for (int k = 0; k < 2; k++) {
                 if (rec[k]) cudaEventDestroy(rec[k]);
                 if (rev[k]) cudaEventDestroy(rev[k]);
             }
-            if (fin) cudaEventDestroy(fin);
+            for (cudaEvent_t e : {fin, mu, tri})
+                if (e) cudaEventDestroy(e);
         }
     } ss;
     CEL_CUDA(s, cudaStreamCreateWithFlags(&ss.rs, cudaStreamNonBlocking), "adjoint stream");
+    CEL_CUDA(s, cudaStreamCreateWithFlags(&ss.ts, cudaStreamNonBlocking), "adjoint stream");
     for (int k = 0; k < 2; k++) {
         CEL_CUDA(s, cudaEventCreateWithFlags(&ss.rec[k], cudaEventDisableTiming), "adjoint events");
         CEL_CUDA(s, cudaEventCreateWithFlags(&ss.rev[k], cudaEventDisableTiming), "adjoint events");
     }
     CEL_CUDA(s, cudaEventCreateWithFlags(&ss.fin, cudaEventDisableTiming), "adjoint events");
+    CEL_CUDA(s, cudaEventCreateWithFlags(&ss.mu, cudaEventDisableTiming), "adjoint events");
+    CEL_CUDA(s, cudaEventCreateWithFlags(&ss.tri, cudaEventDisableTiming), "adjoint events");
+    bool tri_pending = false;   // the depth term's stream has work the reverse must wait for
+    auto wait_tri = [&]() -> cudaError_t {
+        if (!tri_pending) return cudaSuccess;
+        tri_pending = false;
+        return cudaStreamWaitEvent(ss.rs, ss.tri, 0);
+    };
     const cudaStream_t fst = st;   // forward and recomputation
     st = ss.rs;                    // the reverse
     real *gtab = reinterpret_cast<real *>(scr + L.gtab);
@@ -1782,6 +1800,9 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     // its captured right sides, with the transposed solves' still in Xr, Yr
     auto tri_bed = [&](const AdjArgs<real> &x, int k, int stage) -> cudaError_t {
         if (!bed_lines) return cudaSuccess;
+        cudaError_t e = cudaEventRecord(ss.mu, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.ts, ss.mu, 0);
+        if (e != cudaSuccess) return e;
         real *Rx = reinterpret_cast<real *>(rhsf(k, stage)), *Ry = reinterpret_cast<real *>(rhsf(k, stage) + L.line_bytes);
         real *Xs = reinterpret_cast<real *>(scr + L.xs), *Ys = reinterpret_cast<real *>(scr + L.xs + L.line_bytes);
         LinePair<real> lp;
@@ -1791,13 +1812,17 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
             lp.L[dir].base = dir == 0 ? Rx : Ry;
             lp.L[dir].sol = dir == 0 ? Xs : Ys;
         }
-        cudaError_t e = launch_lines_solution<real>(lp, st);
-        return e != cudaSuccess ? e
-                                : launch_adjoint_tri_bed<real>(x, Xs, Ys, Xr, Yr, s->at<real>(s->lay.dr),
-                                                               s->at<real>(s->lay.dc), st);
+        e = launch_lines_solution<real>(lp, ss.ts);
+        if (e == cudaSuccess)
+            e = launch_adjoint_tri_bed<real>(x, Xs, Ys, Xr, Yr, s->at<real>(s->lay.dr), s->at<real>(s->lay.dc), ss.ts);
+        if (e == cudaSuccess) e = cudaEventRecord(ss.tri, ss.ts);
+        tri_pending = e == cudaSuccess;
+        return e;
     };
     // the mask phase, writing the Boussinesq solves' right sides as well
     auto mask = [&](AdjArgs<real> &x, int zero_set) -> cudaError_t {
+        cudaError_t w = wait_tri();   // it rewrites Xr, Yr
+        if (w != cudaSuccess) return w;
         x.packX = x.bsnq ? Xr : nullptr;
         x.packY = x.bsnq ? Yr : nullptr;
         for (int v = 0; v < 3; v++) x.zero[v] = zero_set >= 0 ? lam(3 * zero_set + v) : nullptr;
@@ -1853,6 +1878,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         CEL_CUDA(s, cudaStreamWaitEvent(st, ss.rec[slot], 0), "adjoint order");
         for (int n = n1 - 1; n >= n0; n--) {
             const int k = n - n0;
+            CEL_CUDA(s, wait_tri(), "adjoint order");
             if (a.c.sine)
                 CEL_CUDA(s, launch_ghost_table<real>(s->geo, s->phy, s->bnd, s->at<real>(s->lay.dr),
                                                      s->at<double>(s->lay.ktab), (double)(step0 + n) * dt,
@@ -1937,11 +1963,13 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                 CEL_CUDA(s, launch_adjoint_vjp<real>(x, st), "adjoint state");
                 lset = acc;
             }
-            if (a.lg)   // the step's ghost values (t^n, t^{n+1}) follow the adjacent depth
+            if (a.lg) {   // the step's ghost values (t^n, t^{n+1}) follow the adjacent depth
+                CEL_CUDA(s, wait_tri(), "adjoint order");
                 CEL_CUDA(s, launch_adjoint_ghost_bed<real>(a, s->bnd, s->at<double>(s->lay.ktab),
                                                            s->at<real>(s->lay.dr), (double)(step0 + n) * dt,
                                                            (double)(step0 + n + 1) * dt, st),
                          "adjoint ghosts");
+            }
             setl(a, lset);
             if (n >= 1)
                 CEL_CUDA(s, launch_adjoint_misfit<real>(a, gij, ng, rec + (size_t)(n - 1) * ng,
@@ -1949,11 +1977,13 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                          "adjoint misfit");
             CEL_CUDA(s, cudaMemsetAsync(Gb(sn, 0), 0, L.cells_bytes * 5, st), "adjoint");
         }
+        CEL_CUDA(s, wait_tri(), "adjoint order");   // the captured right sides of this slot
         CEL_CUDA(s, cudaEventRecord(ss.rev[slot], st), "adjoint order");
         if (sg > 0 && (stt = recompute(sg - 1)) != CEL_OK) return stt;   // overlaps this segment's reverse
     }
     CEL_CUDA(s, cudaMemcpyAsync(grad, lam(3 * lset), sizeof(real) * cells, cudaMemcpyDeviceToDevice, st),
              "adjoint gradient");
+    CEL_CUDA(s, wait_tri(), "adjoint order");
     if (bed)   // segment 0's first state is the initial one
         CEL_CUDA(s, launch_adjoint_bed_final<real>(a, segf(0, 0), lam(3 * lset), grad_z, st), "adjoint bed");
     if (eta_out)
