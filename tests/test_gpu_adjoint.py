@@ -501,3 +501,36 @@ def test_bed_gradient_through_the_sine_makers_ghosts(model):
         ad = float(np.sum(gz * v))
         errs.append(abs(ad - fd) / abs(fd))
     assert max(errs) <= 1e-3, errs
+
+
+@pytest.mark.parametrize("model", [0, 1], ids=["bsnq", "nlsw"])
+def test_gradients_with_two_corrector_iterations(model):
+    """K = 2: every step reverses two AM4 stages (each with its own masks,
+    solves, base and right side at the iterate before it) before the
+    predictor; both gradients against oracle central differences."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    s, gauges, X, Y = _tilted_bed(model, 2, 1, nsteps=8)
+    s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.002, 4.0, 0.2, 0.3),))
+    rng = np.random.default_rng(71 + model)
+    obs = 0.01 * rng.standard_normal((s.steps, len(gauges)))
+    loss, _, gw, _, gz = _gpu_gradient(s, gauges, obs, ckpt=3, bed=True)
+    assert abs(loss - _oracle_loss_bed(s, s.z, gauges, obs)) <= 1e-9 * loss
+    eps = 1e-5
+    errs = []
+    for k in range(6):
+        v = np.zeros_like(X)
+        for _ in range(3):
+            cx, cy = rng.uniform(2.0, 22.0), rng.uniform(2.0, 16.0)
+            v += rng.standard_normal() * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / rng.uniform(2.0, 8.0))
+        if k < 3:
+            v *= 1e-4
+            fd = (_oracle_loss_state(s, s.w0 + eps * v, gauges, obs)
+                  - _oracle_loss_state(s, s.w0 - eps * v, gauges, obs)) / (2 * eps)
+            ad = float(np.sum(gw * v))
+        else:
+            v *= 1e-2
+            fd = (_oracle_loss_bed(s, s.z + eps * v, gauges, obs)
+                  - _oracle_loss_bed(s, s.z - eps * v, gauges, obs)) / (2 * eps)
+            ad = float(np.sum(gz * v))
+        errs.append(abs(ad - fd) / abs(fd))
+    assert max(errs) <= 1e-3, errs
