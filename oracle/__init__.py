@@ -18,6 +18,9 @@ each one are named in the test module docstrings):
   * Euler start-up, AM4 corrector, sine-ghost timing, corner ghosts:
     parity unpinned (internal consistency only).
   * run-up tracking: standing-mode maximum, dry threshold -- pinned
+  * tangent-linear oracle (celeris_tlm.cpp: this source on dual numbers):
+    values bit for bit the oracle's, tangents vs central differences,
+    linearity -- pinned (tests/test_tlm_oracle.py).
   * render oracle (render_oracle.c, the headless renderer): Fresnel closed
     forms, colormap control points, flat lake / tilted plane / flat land by
     formula, grid lines, speed, mirror symmetry -- pinned
@@ -330,3 +333,100 @@ def colormap(which, t):
     out = (ctypes.c_float * 3)()
     render_lib().ro_colormap(which, t, out)
     return np.array(out[:], np.float32)
+
+
+# ------------------------------------------------- tangent-linear oracle
+#
+# celeris_tlm.cpp compiles celeris_oracle.c again with a forward-mode dual
+# number as its arithmetic type: the tangent of every output along one
+# direction (dz, dw, dP, dQ) of the inputs, the exact directional derivative
+# of the oracle's own arithmetic and branches.  The discrete adjoint's
+# gradients are checked against it: <dL/dx, v> must equal dL(x; v).
+
+_TLM_SRC = os.path.join(_HERE, "celeris_tlm.cpp")
+_TLM_LIB = os.path.join(_HERE, "_build", "libceleris_tlm.so")
+_tlm = None
+
+
+def build_tlm(force: bool = False) -> str:
+    """Compile the tangent-linear oracle (g++, FP64, no FMA contraction, one thread)."""
+    os.makedirs(os.path.dirname(_TLM_LIB), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR), os.path.getmtime(_TLM_SRC))
+    if not force and os.path.exists(_TLM_LIB) and os.path.getmtime(_TLM_LIB) >= newest:
+        return _TLM_LIB
+    tmp = _TLM_LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _TLM_SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _TLM_LIB)
+    return _TLM_LIB
+
+
+def tlm_lib():
+    global _tlm
+    with _lock:
+        if _tlm is None:
+            L = ctypes.CDLL(build_tlm())
+            i, p = ctypes.c_int, ctypes.c_void_p
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.tlm_create.restype = p
+            L.tlm_create.argtypes = [ctypes.POINTER(OrcParams), dp, dp]
+            L.tlm_destroy.argtypes = [p]
+            L.tlm_set_boundary.argtypes = [p, i, ctypes.POINTER(OrcBC)]
+            L.tlm_set_state.argtypes = [p, i, dp, dp, dp, dp, dp, dp]
+            L.tlm_set_gauges.argtypes = [p, ctypes.POINTER(ctypes.c_int), i, i, i]
+            L.tlm_step.argtypes = [p, i]
+            L.tlm_read_gauges.argtypes = [p, dp, dp, i, i, ctypes.POINTER(ctypes.c_int)]
+            _tlm = L
+        return _tlm
+
+
+class TangentOracle:
+    """The oracle with a tangent: the bed z with its direction dz; then
+    set_state(w, P, Q, dw, dP, dQ); gauges read as (eta, d eta)."""
+
+    def __init__(self, z, dz, dx, dy, dt, *, model=BSNQ, g=9.81, Bd=1.0 / 15.0,
+                 theta=1.3, eps=5e-12, K=0, ws=0.0, friction=FRIC_NONE, fcoef=0.0):
+        z = _f64(z)
+        ny, nx = z.shape
+        dz = _f64(dz, (ny, nx))
+        self.nx, self.ny, self.ng = nx, ny, 0
+        self.p = OrcParams(nx, ny, dx, dy, model, g, Bd, theta, eps, dt, K, ws, friction, fcoef)
+        self._L = tlm_lib()
+        self._h = self._L.tlm_create(ctypes.byref(self.p), _dp(z), _dp(dz))
+        if not self._h:
+            raise ValueError("tlm_create rejected the parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.tlm_destroy(h)
+            self._h = None
+
+    def set_boundary(self, side, type=SOLID, width=0, comps=()):
+        bc = make_bc(type, width, comps)
+        if self._L.tlm_set_boundary(self._h, side, ctypes.byref(bc)) != 0:
+            raise ValueError("bad boundary")
+
+    def set_state(self, w, P, Q, dw, dP, dQ):
+        sh = (self.ny, self.nx)
+        a = [_f64(x, sh) for x in (w, dw, P, dP, Q, dQ)]
+        if self._L.tlm_set_state(self._h, self.nx * self.ny, *[_dp(x) for x in a]) != 0:
+            raise ValueError("bad state")
+
+    def set_gauges(self, ij, log_every, capacity):
+        ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int32).reshape(-1, 2))
+        self.ng = len(ij)
+        if self._L.tlm_set_gauges(self._h, ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(ij),
+                                  int(log_every), int(capacity)) != 0:
+            raise ValueError("bad gauges")
+
+    def step(self, n=1):
+        if self._L.tlm_step(self._h, int(n)) != 0:
+            raise RuntimeError("tlm_step failed")
+
+    def read_gauges(self, max_rec):
+        eta, deta = np.zeros((max_rec, self.ng)), np.zeros((max_rec, self.ng))
+        n = ctypes.c_int()
+        if self._L.tlm_read_gauges(self._h, _dp(eta), _dp(deta), int(max_rec), self.ng, ctypes.byref(n)) != 0:
+            raise RuntimeError("tlm_read_gauges failed")
+        return eta[: n.value], deta[: n.value]

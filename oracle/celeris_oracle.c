@@ -35,17 +35,17 @@ struct orc {
     int nx, ny, ex, ey;
     long long step;   /* steps since create: t = step * dt                  */
     long long nh;     /* steps since the last restart of the AB3 history    */
-    double clamp_mass;
-    double *z, *Bc, *Bbar, *d, *ddx, *ddy;      /* static fields           */
-    double *w, *P, *Q, *w1, *P1, *Q1;           /* state n and iterate n+1 */
-    double *U, *V, *U1, *V1;                    /* U*, V* (Eq. 7-8)        */
-    double *E[3], *F[3], *G[3], *Fs[3], *Gs[3]; /* [0]=n, [1]=n-1, [2]=n-2 */
-    double *Ec, *Fc, *Gc, *Fsc, *Gsc;           /* rhs at the AM4 iterate  */
-    double *Hx[3], *Hy[3];                      /* face fluxes             */
+    orc_real clamp_mass;
+    orc_real *z, *Bc, *Bbar, *d, *ddx, *ddy;      /* static fields           */
+    orc_real *w, *P, *Q, *w1, *P1, *Q1;           /* state n and iterate n+1 */
+    orc_real *U, *V, *U1, *V1;                    /* U*, V* (Eq. 7-8)        */
+    orc_real *E[3], *F[3], *G[3], *Fs[3], *Gs[3]; /* [0]=n, [1]=n-1, [2]=n-2 */
+    orc_real *Ec, *Fc, *Gc, *Fsc, *Gsc;           /* rhs at the AM4 iterate  */
+    orc_real *Hx[3], *Hy[3];                      /* face fluxes             */
     int ng, log_every, cap, nrec, head;
     int *gij;
-    double *grec;
-    double *maxw, delta;                        /* run-up tracking         */
+    orc_real *grec;
+    orc_real *maxw, delta;                        /* run-up tracking         */
 };
 
 static size_t IX(const orc *o, int i, int j)
@@ -58,11 +58,11 @@ static size_t CX(const orc *o, int ci, int cj)
 }
 /* Bed on the x-face f (x = f dx) of row j, and on the y-face g of column i:
  * mean of the face's two end corners (Reading A-W1). */
-static double Bx(const orc *o, int f, int j)
+static orc_real Bx(const orc *o, int f, int j)
 {
     return 0.5 * (o->Bc[CX(o, f, j)] + o->Bc[CX(o, f, j + 1)]);
 }
-static double By(const orc *o, int i, int g)
+static orc_real By(const orc *o, int i, int g)
 {
     return 0.5 * (o->Bc[CX(o, i, g)] + o->Bc[CX(o, i + 1, g)]);
 }
@@ -81,36 +81,36 @@ int orc_num_threads(void)
 /* Generalized minmod of KP07 step 1 (Sec. 2.2): the slope is
  * minmod(theta*(q0-qm), (qp-qm)/2, theta*(qp-q0)); zero unless all three
  * share a sign, else the one of least magnitude (Reading A-L1). */
-double orc_minmod(double theta, double qm, double q0, double qp)
+orc_real orc_minmod(orc_real theta, orc_real qm, orc_real q0, orc_real qp)
 {
-    double a = theta * (q0 - qm), b = 0.5 * (qp - qm), c = theta * (qp - q0);
+    orc_real a = theta * (q0 - qm), b = 0.5 * (qp - qm), c = theta * (qp - q0);
     if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
     if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
     return 0.0;
 }
 
 /* Eq. 29: Eckart's approximation k = omega^2/g * sqrt(coth(omega^2 d / g)). */
-double orc_eckart_k(double omega, double d, double g)
+orc_real orc_eckart_k(orc_real omega, orc_real d, orc_real g)
 {
-    double k0 = omega * omega / g;
+    orc_real k0 = omega * omega / g;
     return k0 * sqrt(1.0 / tanh(k0 * d));
 }
 
 /* Eq. 30: gamma = (1 + cos(pi (Ls - D)/Ls))/2 inside the layer, 1 outside. */
-double orc_sponge_gamma(double D, double Ls)
+orc_real orc_sponge_gamma(orc_real D, orc_real Ls)
 {
     if (!(D < Ls)) return 1.0;
     return 0.5 * (1.0 + cos(ORC_PI * (Ls - D) / Ls));
 }
 
 /* Textbook Thomas algorithm: a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = r[i]. */
-static void thomas_ws(int n, const double *a, const double *b, const double *c,
-                      const double *r, double *x, double *cp, double *dp)
+static void thomas_ws(int n, const orc_real *a, const orc_real *b, const orc_real *c,
+                      const orc_real *r, orc_real *x, orc_real *cp, orc_real *dp)
 {
     cp[0] = c[0] / b[0];
     dp[0] = r[0] / b[0];
     for (int i = 1; i < n; i++) {
-        double m = b[i] - a[i] * cp[i - 1];
+        orc_real m = b[i] - a[i] * cp[i - 1];
         cp[i] = c[i] / m;
         dp[i] = (r[i] - a[i] * dp[i - 1]) / m;
     }
@@ -118,12 +118,12 @@ static void thomas_ws(int n, const double *a, const double *b, const double *c,
     for (int i = n - 2; i >= 0; i--) x[i] = dp[i] - cp[i] * x[i + 1];
 }
 
-void orc_thomas(int n, const double *a, const double *b, const double *c,
-                const double *r, double *x)
+void orc_thomas(int n, const orc_real *a, const orc_real *b, const orc_real *c,
+                const orc_real *r, orc_real *x)
 {
     if (n <= 0) return;
-    double *cp = (double *)malloc(sizeof(double) * (size_t)n);
-    double *dp = (double *)malloc(sizeof(double) * (size_t)n);
+    orc_real *cp = (orc_real *)malloc(sizeof(orc_real) * (size_t)n);
+    orc_real *dp = (orc_real *)malloc(sizeof(orc_real) * (size_t)n);
     thomas_ws(n, a, b, c, r, x, cp, dp);
     free(cp);
     free(dp);
@@ -131,49 +131,49 @@ void orc_thomas(int n, const double *a, const double *b, const double *c,
 
 /* Eq. 14 factor: u = k(h) * P with k(h) = sqrt(2) h / sqrt(h^4 + max(h^4, eps))
  * (Reading A-G3); also the desingularised 1/h of the friction term (Sec. 2.6). */
-static double desing(double h, double eps)
+static orc_real desing(orc_real h, orc_real eps)
 {
-    double h4 = (h * h) * (h * h);
+    orc_real h4 = (h * h) * (h * h);
     return sqrt(2.0) * h / sqrt(h4 + fmax(h4, eps));
 }
 
 /* KP07 step 3 (Sec. 2.2): central-upwind flux through one face.  L/R states
  * are (w, normal discharge, tangential discharge) at the face; Bf is the bed
  * on the face.  H = (mass, normal momentum, tangential momentum). */
-void orc_central_upwind(double g, double eps, double wL, double nL, double tL,
-                        double wR, double nR, double tR, double Bf, double H[3])
+void orc_central_upwind(orc_real g, orc_real eps, orc_real wL, orc_real nL, orc_real tL,
+                        orc_real wR, orc_real nR, orc_real tR, orc_real Bf, orc_real H[3])
 {
-    double hL = fmax(wL - Bf, 0.0), hR = fmax(wR - Bf, 0.0);
-    double kL = desing(hL, eps), kR = desing(hR, eps);
-    double uL = kL * nL, vL = kL * tL, uR = kR * nR, vR = kR * tR;
-    double qnL = hL * uL, qtL = hL * vL, qnR = hR * uR, qtR = hR * vR;
-    double sL = sqrt(g * hL), sR = sqrt(g * hR);
-    double ap = fmax(fmax(uL + sL, uR + sR), 0.0);
-    double am = fmin(fmin(uL - sL, uR - sR), 0.0);
-    double den = ap - am;
+    orc_real hL = fmax(wL - Bf, 0.0), hR = fmax(wR - Bf, 0.0);
+    orc_real kL = desing(hL, eps), kR = desing(hR, eps);
+    orc_real uL = kL * nL, vL = kL * tL, uR = kR * nR, vR = kR * tR;
+    orc_real qnL = hL * uL, qtL = hL * vL, qnR = hR * uR, qtR = hR * vR;
+    orc_real sL = sqrt(g * hL), sR = sqrt(g * hR);
+    orc_real ap = fmax(fmax(uL + sL, uR + sR), 0.0);
+    orc_real am = fmin(fmin(uL - sL, uR - sR), 0.0);
+    orc_real den = ap - am;
     if (!(den > 0.0)) { /* both sides dry (Reading A-F1) */
         H[0] = H[1] = H[2] = 0.0;
         return;
     }
-    double FL0 = qnL, FL1 = qnL * uL + 0.5 * g * hL * hL, FL2 = qnL * vL;
-    double FR0 = qnR, FR1 = qnR * uR + 0.5 * g * hR * hR, FR2 = qnR * vR;
+    orc_real FL0 = qnL, FL1 = qnL * uL + 0.5 * g * hL * hL, FL2 = qnL * vL;
+    orc_real FR0 = qnR, FR1 = qnR * uR + 0.5 * g * hR * hR, FR2 = qnR * vR;
     H[0] = (ap * FL0 - am * FR0 + ap * am * (wR - wL)) / den;
     H[1] = (ap * FL1 - am * FR1 + ap * am * (qnR - qnL)) / den;
     H[2] = (ap * FL2 - am * FR2 + ap * am * (qtR - qtL)) / den;
 }
 
 /* Sine-wave maker, Eq. 25-28 summed over components (Reading A-B4). */
-static void sine_eval(const orc *o, const orc_bc *bc, double dadj, double x,
-                      double y, double t, double *eta, double *Pg, double *Qg)
+static void sine_eval(const orc *o, const orc_bc *bc, orc_real dadj, orc_real x,
+                      orc_real y, orc_real t, orc_real *eta, orc_real *Pg, orc_real *Qg)
 {
     *eta = *Pg = *Qg = 0.0;
     if (!(dadj > 0.0)) return;
     for (int m = 0; m < bc->ncomp; m++) {
-        double om = 2.0 * ORC_PI / bc->period[m];
-        double k = orc_eckart_k(om, dadj, o->p.g);
-        double c = om / k;
-        double cs = cos(bc->dir[m]), sn = sin(bc->dir[m]);
-        double em = bc->amp[m] * sin(om * t - k * cs * x - k * sn * y + bc->phase[m]);
+        orc_real om = 2.0 * ORC_PI / bc->period[m];
+        orc_real k = orc_eckart_k(om, dadj, o->p.g);
+        orc_real c = om / k;
+        orc_real cs = cos(bc->dir[m]), sn = sin(bc->dir[m]);
+        orc_real em = bc->amp[m] * sin(om * t - k * cs * x - k * sn * y + bc->phase[m]);
         *eta += em;
         *Pg += c * cs * em;
         *Qg += c * sn * em;
@@ -186,10 +186,10 @@ static void sine_eval(const orc *o, const orc_bc *bc, double dadj, double x,
  * y-sides over every column, so corner ghosts come by composition.
  * Solid (and the outer ghosts behind a sponge): face-centred mirror, ghost
  * -1-k <- interior k, normal discharge negated (Eq. 24, Reading A-B1). */
-static void fill_ghosts(orc *o, double *w, double *P, double *Q, double t)
+static void fill_ghosts(orc *o, orc_real *w, orc_real *P, orc_real *Q, orc_real t)
 {
     const int nx = o->nx, ny = o->ny;
-    const double ws = o->p.ws;
+    const orc_real ws = o->p.ws;
     for (int side = ORC_W; side <= ORC_E; side++) {
         const orc_bc *bc = &o->bc[side];
         for (int j = 0; j < ny; j++)
@@ -198,8 +198,8 @@ static void fill_ghosts(orc *o, double *w, double *P, double *Q, double t)
                 int si = side == ORC_W ? k : nx - 1 - k;
                 size_t gc = IX(o, gi, j), sc = IX(o, si, j);
                 if (bc->type == ORC_SINE) {
-                    double eta, Pg, Qg;
-                    double dadj = o->d[IX(o, side == ORC_W ? 0 : nx - 1, j)];
+                    orc_real eta, Pg, Qg;
+                    orc_real dadj = o->d[IX(o, side == ORC_W ? 0 : nx - 1, j)];
                     sine_eval(o, bc, dadj, (gi + 0.5) * o->p.dx,
                               (j + 0.5) * o->p.dy, t, &eta, &Pg, &Qg);
                     w[gc] = ws + eta;
@@ -220,9 +220,9 @@ static void fill_ghosts(orc *o, double *w, double *P, double *Q, double t)
                 int sj = side == ORC_S ? k : ny - 1 - k;
                 size_t gc = IX(o, i, gj), sc = IX(o, i, sj);
                 if (bc->type == ORC_SINE) {
-                    double eta, Pg, Qg;
+                    orc_real eta, Pg, Qg;
                     int ic = i < 0 ? 0 : (i > nx - 1 ? nx - 1 : i);
-                    double dadj = o->d[IX(o, ic, side == ORC_S ? 0 : ny - 1)];
+                    orc_real dadj = o->d[IX(o, ic, side == ORC_S ? 0 : ny - 1)];
                     sine_eval(o, bc, dadj, (i + 0.5) * o->p.dx,
                               (gj + 0.5) * o->p.dy, t, &eta, &Pg, &Qg);
                     w[gc] = ws + eta;
@@ -240,13 +240,13 @@ static void fill_ghosts(orc *o, double *w, double *P, double *Q, double t)
 /* Sponge coefficient of cell (i,j): Eq. 30 with D the distance from the
  * absorbing boundary face to the cell centre; the smallest gamma over all
  * sponge sides (Reading A-B3). */
-static double sponge_at(const orc *o, int i, int j)
+static orc_real sponge_at(const orc *o, int i, int j)
 {
-    double gmin = 1.0;
+    orc_real gmin = 1.0;
     for (int s = 0; s < 4; s++) {
         const orc_bc *bc = &o->bc[s];
         if (bc->type != ORC_SPONGE || bc->width <= 0) continue;
-        double D, L;
+        orc_real D, L;
         if (s == ORC_W) { D = (i + 0.5) * o->p.dx; L = bc->width * o->p.dx; }
         else if (s == ORC_E) { D = (o->nx - i - 0.5) * o->p.dx; L = bc->width * o->p.dx; }
         else if (s == ORC_S) { D = (j + 0.5) * o->p.dy; L = bc->width * o->p.dy; }
@@ -261,7 +261,7 @@ static double sponge_at(const orc *o, int i, int j)
 /* a0: bed corners from cell-centre z (Reading A-W1): ghost z mirrored evenly,
  * corner = mean of its 4 cells, cell Bbar = mean of its 4 corners,
  * d = max(w_s - Bbar, 0) (Sec. 2.1), d_x, d_y by central differences. */
-static void derive_static(orc *o, const double *zin)
+static void derive_static(orc *o, const orc_real *zin)
 {
     const int nx = o->nx, ny = o->ny;
     for (int j = 0; j < ny; j++)
@@ -283,7 +283,7 @@ static void derive_static(orc *o, const double *zin)
                         o->z[IX(o, ci - 1, cj)] + o->z[IX(o, ci, cj)]);
     for (int j = -1; j <= ny; j++)
         for (int i = -1; i <= nx; i++) {
-            double b = 0.25 * (o->Bc[CX(o, i, j)] + o->Bc[CX(o, i + 1, j)] +
+            orc_real b = 0.25 * (o->Bc[CX(o, i, j)] + o->Bc[CX(o, i + 1, j)] +
                                o->Bc[CX(o, i, j + 1)] + o->Bc[CX(o, i + 1, j + 1)]);
             o->Bbar[IX(o, i, j)] = b;
             o->d[IX(o, i, j)] = fmax(o->p.ws - b, 0.0);
@@ -302,13 +302,13 @@ static void derive_static(orc *o, const double *zin)
 /* KP07 steps 1-2 for one cell along one direction (stride s): minmod slopes
  * of w, P, Q give the low- and high-face values; then the conservative
  * positivity fix of w against the face beds Blo, Bhi (Reading A-L2). */
-static void recon_cell(double theta, const double *w, const double *P,
-                       const double *Q, size_t c, size_t s, double Blo,
-                       double Bhi, double lo[3], double hi[3])
+static void recon_cell(orc_real theta, const orc_real *w, const orc_real *P,
+                       const orc_real *Q, size_t c, size_t s, orc_real Blo,
+                       orc_real Bhi, orc_real lo[3], orc_real hi[3])
 {
-    const double *q[3] = {w, P, Q};
+    const orc_real *q[3] = {w, P, Q};
     for (int v = 0; v < 3; v++) {
-        double sig = orc_minmod(theta, q[v][c - s], q[v][c], q[v][c + s]);
+        orc_real sig = orc_minmod(theta, q[v][c - s], q[v][c], q[v][c + s]);
         lo[v] = q[v][c] - 0.5 * sig;
         hi[v] = q[v][c] + 0.5 * sig;
     }
@@ -325,19 +325,19 @@ static void recon_cell(double theta, const double *w, const double *P,
  * E, F, G: flux divergence of KP07 (steps 3-4) + bed slope + friction
  * (Eq. 31-32) + the dispersive eta terms of Eq. 10-11 by central FD;
  * Fs = F*(Q) (Eq. 12), Gs = G*(P) (Eq. 13, Reading A-G2). */
-static void compute_rhs(orc *o, const double *w, const double *P,
-                        const double *Q, double *E, double *F, double *G,
-                        double *Fs, double *Gs)
+static void compute_rhs(orc *o, const orc_real *w, const orc_real *P,
+                        const orc_real *Q, orc_real *E, orc_real *F, orc_real *G,
+                        orc_real *Fs, orc_real *Gs)
 {
     const int nx = o->nx, ny = o->ny;
-    const double dx = o->p.dx, dy = o->p.dy, g = o->p.g, eps = o->p.eps;
-    const double th = o->p.theta;
+    const orc_real dx = o->p.dx, dy = o->p.dy, g = o->p.g, eps = o->p.eps;
+    const orc_real th = o->p.theta;
     const size_t ex = (size_t)o->ex;
 
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int f = 0; f <= nx; f++) {
-            double loL[3], hiL[3], loR[3], hiR[3], H[3];
+            orc_real loL[3], hiL[3], loR[3], hiR[3], H[3];
             recon_cell(th, w, P, Q, IX(o, f - 1, j), 1, Bx(o, f - 1, j), Bx(o, f, j), loL, hiL);
             recon_cell(th, w, P, Q, IX(o, f, j), 1, Bx(o, f, j), Bx(o, f + 1, j), loR, hiR);
             orc_central_upwind(g, eps, hiL[0], hiL[1], hiL[2], loR[0], loR[1],
@@ -350,7 +350,7 @@ static void compute_rhs(orc *o, const double *w, const double *P,
 #pragma omp parallel for schedule(static)
     for (int gq = 0; gq <= ny; gq++)
         for (int i = 0; i < nx; i++) {
-            double loS[3], hiS[3], loN[3], hiN[3], H[3];
+            orc_real loS[3], hiS[3], loN[3], hiN[3], H[3];
             recon_cell(th, w, P, Q, IX(o, i, gq - 1), ex, By(o, i, gq - 1), By(o, i, gq), loS, hiS);
             recon_cell(th, w, P, Q, IX(o, i, gq), ex, By(o, i, gq), By(o, i, gq + 1), loN, hiN);
             /* normal discharge is Q, tangential is P */
@@ -363,7 +363,7 @@ static void compute_rhs(orc *o, const double *w, const double *P,
         }
 
     const int bsnq = o->p.model == ORC_BSNQ;
-    const double Bd = o->p.Bd, ws = o->p.ws, B3 = o->p.Bd + 1.0 / 3.0;
+    const orc_real Bd = o->p.Bd, ws = o->p.ws, B3 = o->p.Bd + 1.0 / 3.0;
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -371,39 +371,39 @@ static void compute_rhs(orc *o, const double *w, const double *P,
             size_t kx = (size_t)j * (size_t)(nx + 1) + (size_t)i;
             size_t ky = (size_t)j * (size_t)nx + (size_t)i;
             size_t kyn = (size_t)(j + 1) * (size_t)nx + (size_t)i;
-            double hb = w[c] - o->Bbar[c];
-            double e = -(o->Hx[0][kx + 1] - o->Hx[0][kx]) / dx -
+            orc_real hb = w[c] - o->Bbar[c];
+            orc_real e = -(o->Hx[0][kx + 1] - o->Hx[0][kx]) / dx -
                        (o->Hy[0][kyn] - o->Hy[0][ky]) / dy;
-            double f = -(o->Hx[1][kx + 1] - o->Hx[1][kx]) / dx -
+            orc_real f = -(o->Hx[1][kx + 1] - o->Hx[1][kx]) / dx -
                        (o->Hy[1][kyn] - o->Hy[1][ky]) / dy -
                        g * hb * (Bx(o, i + 1, j) - Bx(o, i, j)) / dx;
-            double gg = -(o->Hx[2][kx + 1] - o->Hx[2][kx]) / dx -
+            orc_real gg = -(o->Hx[2][kx + 1] - o->Hx[2][kx]) / dx -
                         (o->Hy[2][kyn] - o->Hy[2][ky]) / dy -
                         g * hb * (By(o, i, j + 1) - By(o, i, j)) / dy;
             if (o->p.friction != ORC_FRIC_NONE) {
-                double hinv = desing(fmax(hb, 0.0), eps);
-                double fc = o->p.friction == ORC_FRIC_MANNING
+                orc_real hinv = desing(fmax(hb, 0.0), eps);
+                orc_real fc = o->p.friction == ORC_FRIC_MANNING
                                 ? g * o->p.fcoef * o->p.fcoef * cbrt(hinv)
                                 : o->p.fcoef;
-                double mag = sqrt(P[c] * P[c] + Q[c] * Q[c]);
+                orc_real mag = sqrt(P[c] * P[c] + Q[c] * Q[c]);
                 f -= fc * P[c] * mag * hinv * hinv;
                 gg -= fc * Q[c] * mag * hinv * hinv;
             }
-            double fs = 0.0, gs = 0.0;
+            orc_real fs = 0.0, gs = 0.0;
             if (bsnq) {
-                double dd = o->d[c], dxd = o->ddx[c], dyd = o->ddy[c];
+                orc_real dd = o->d[c], dxd = o->ddx[c], dyd = o->ddy[c];
 #define ETA(a, b) (w[IX(o, i + (a), j + (b))] - ws)
-                double exx = (ETA(1, 0) - 2.0 * ETA(0, 0) + ETA(-1, 0)) / (dx * dx);
-                double eyy = (ETA(0, 1) - 2.0 * ETA(0, 0) + ETA(0, -1)) / (dy * dy);
-                double exy = (ETA(1, 1) - ETA(1, -1) - ETA(-1, 1) + ETA(-1, -1)) / (4.0 * dx * dy);
-                double exxx = (ETA(2, 0) - 2.0 * ETA(1, 0) + 2.0 * ETA(-1, 0) - ETA(-2, 0)) /
+                orc_real exx = (ETA(1, 0) - 2.0 * ETA(0, 0) + ETA(-1, 0)) / (dx * dx);
+                orc_real eyy = (ETA(0, 1) - 2.0 * ETA(0, 0) + ETA(0, -1)) / (dy * dy);
+                orc_real exy = (ETA(1, 1) - ETA(1, -1) - ETA(-1, 1) + ETA(-1, -1)) / (4.0 * dx * dy);
+                orc_real exxx = (ETA(2, 0) - 2.0 * ETA(1, 0) + 2.0 * ETA(-1, 0) - ETA(-2, 0)) /
                               (2.0 * dx * dx * dx);
-                double eyyy = (ETA(0, 2) - 2.0 * ETA(0, 1) + 2.0 * ETA(0, -1) - ETA(0, -2)) /
+                orc_real eyyy = (ETA(0, 2) - 2.0 * ETA(0, 1) + 2.0 * ETA(0, -1) - ETA(0, -2)) /
                               (2.0 * dy * dy * dy);
-                double exyy = ((ETA(1, 1) - 2.0 * ETA(1, 0) + ETA(1, -1)) -
+                orc_real exyy = ((ETA(1, 1) - 2.0 * ETA(1, 0) + ETA(1, -1)) -
                                (ETA(-1, 1) - 2.0 * ETA(-1, 0) + ETA(-1, -1))) /
                               (2.0 * dx * dy * dy);
-                double exxy = ((ETA(1, 1) - 2.0 * ETA(0, 1) + ETA(-1, 1)) -
+                orc_real exxy = ((ETA(1, 1) - 2.0 * ETA(0, 1) + ETA(-1, 1)) -
                                (ETA(1, -1) - 2.0 * ETA(0, -1) + ETA(-1, -1))) /
                               (2.0 * dx * dx * dy);
 #undef ETA
@@ -413,12 +413,12 @@ static void compute_rhs(orc *o, const double *w, const double *P,
                       Bd * g * dd * dd * (dyd * (2.0 * eyy + exx) + dxd * exy);
 #define QQ(a, b) Q[IX(o, i + (a), j + (b))]
 #define PP(a, b) P[IX(o, i + (a), j + (b))]
-                double Qx = (QQ(1, 0) - QQ(-1, 0)) / (2.0 * dx);
-                double Qy = (QQ(0, 1) - QQ(0, -1)) / (2.0 * dy);
-                double Qxy = (QQ(1, 1) - QQ(1, -1) - QQ(-1, 1) + QQ(-1, -1)) / (4.0 * dx * dy);
-                double Px = (PP(1, 0) - PP(-1, 0)) / (2.0 * dx);
-                double Py = (PP(0, 1) - PP(0, -1)) / (2.0 * dy);
-                double Pxy = (PP(1, 1) - PP(1, -1) - PP(-1, 1) + PP(-1, -1)) / (4.0 * dx * dy);
+                orc_real Qx = (QQ(1, 0) - QQ(-1, 0)) / (2.0 * dx);
+                orc_real Qy = (QQ(0, 1) - QQ(0, -1)) / (2.0 * dy);
+                orc_real Qxy = (QQ(1, 1) - QQ(1, -1) - QQ(-1, 1) + QQ(-1, -1)) / (4.0 * dx * dy);
+                orc_real Px = (PP(1, 0) - PP(-1, 0)) / (2.0 * dx);
+                orc_real Py = (PP(0, 1) - PP(0, -1)) / (2.0 * dy);
+                orc_real Pxy = (PP(1, 1) - PP(1, -1) - PP(-1, 1) + PP(-1, -1)) / (4.0 * dx * dy);
 #undef QQ
 #undef PP
                 fs = dd * dxd * Qy / 6.0 + dd * dyd * Qx / 6.0 + B3 * dd * dd * Qxy;
@@ -433,11 +433,11 @@ static void compute_rhs(orc *o, const double *w, const double *P,
 }
 
 /* Eq. 23 coefficients of the line through cell c (spacing h, d, d_alpha). */
-static void coef23(double Bd, double h, double dd, double dda, double *a,
-                   double *b, double *c)
+static void coef23(orc_real Bd, orc_real h, orc_real dd, orc_real dda, orc_real *a,
+                   orc_real *b, orc_real *c)
 {
-    double r = (Bd + 1.0 / 3.0) * dd * dd / (h * h);
-    double s = dd * dda / (6.0 * h);
+    orc_real r = (Bd + 1.0 / 3.0) * dd * dd / (h * h);
+    orc_real s = dd * dda / (6.0 * h);
     *a = s - r;
     *b = 1.0 + 2.0 * r;
     *c = -s - r;
@@ -445,8 +445,8 @@ static void coef23(double Bd, double h, double dd, double dda, double *a,
 
 /* U*, V* of Eq. 7-8 discretised exactly as the rows of Eq. 21-23, from P, Q
  * with their ghosts (Reading A-T3).  NLSW: U* = P, V* = Q. */
-static void compute_ustar(orc *o, const double *P, const double *Q, double *U,
-                          double *V)
+static void compute_ustar(orc *o, const orc_real *P, const orc_real *Q, orc_real *U,
+                          orc_real *V)
 {
     const int nx = o->nx, ny = o->ny;
     const size_t ex = (size_t)o->ex;
@@ -459,7 +459,7 @@ static void compute_ustar(orc *o, const double *P, const double *Q, double *U,
                 V[c] = Q[c];
                 continue;
             }
-            double a, b, cc;
+            orc_real a, b, cc;
             coef23(o->p.Bd, o->p.dx, o->d[c], o->ddx[c], &a, &b, &cc);
             U[c] = a * P[c - 1] + b * P[c] + cc * P[c + 1];
             coef23(o->p.Bd, o->p.dy, o->d[c], o->ddy[c], &a, &b, &cc);
@@ -470,17 +470,17 @@ static void compute_ustar(orc *o, const double *P, const double *Q, double *U,
 /* Eq. 21 per x-row (dir 0) or Eq. 22 per y-column (dir 1), Thomas.  Boundary
  * rows (Reading A-B2): a solid or sponge end uses the mirror P_{-1} = -P_0;
  * a sine end moves the known ghost discharge at t1 to the right side. */
-static void solve_lines(orc *o, int dir, const double *R, double *X, double t1)
+static void solve_lines(orc *o, int dir, const orc_real *R, orc_real *X, orc_real t1)
 {
     const int nx = o->nx, ny = o->ny;
     const int n = dir == 0 ? nx : ny, nl = dir == 0 ? ny : nx;
-    const double h = dir == 0 ? o->p.dx : o->p.dy;
+    const orc_real h = dir == 0 ? o->p.dx : o->p.dy;
     const orc_bc *lo = &o->bc[dir == 0 ? ORC_W : ORC_S];
     const orc_bc *hi = &o->bc[dir == 0 ? ORC_E : ORC_N];
 #pragma omp parallel
     {
-        double *a = (double *)malloc(sizeof(double) * (size_t)n * 7);
-        double *b = a + n, *c = b + n, *r = c + n, *x = r + n, *cp = x + n, *dp = cp + n;
+        orc_real *a = (orc_real *)malloc(sizeof(orc_real) * (size_t)n * 7);
+        orc_real *b = a + n, *c = b + n, *r = c + n, *x = r + n, *cp = x + n, *dp = cp + n;
 #pragma omp for schedule(static)
         for (int l = 0; l < nl; l++) {
             for (int k = 0; k < n; k++) {
@@ -493,12 +493,12 @@ static void solve_lines(orc *o, int dir, const double *R, double *X, double t1)
             for (int end = 0; end < 2; end++) {
                 const orc_bc *bc = end == 0 ? lo : hi;
                 int k = end == 0 ? 0 : n - 1;
-                double *off = end == 0 ? &a[0] : &c[n - 1];
+                orc_real *off = end == 0 ? &a[0] : &c[n - 1];
                 if (bc->type == ORC_SINE) {
                     int gk = end == 0 ? -1 : n;
                     int gi = dir == 0 ? gk : l, gj = dir == 0 ? l : gk;
                     int ai = dir == 0 ? k : l, aj = dir == 0 ? l : k;
-                    double eta, Pg, Qg;
+                    orc_real eta, Pg, Qg;
                     sine_eval(o, bc, o->d[IX(o, ai, aj)], (gi + 0.5) * o->p.dx,
                               (gj + 0.5) * o->p.dy, t1, &eta, &Pg, &Qg);
                     r[k] -= *off * (dir == 0 ? Pg : Qg);
@@ -519,9 +519,9 @@ static void solve_lines(orc *o, int dir, const double *R, double *X, double t1)
 
 /* Reading A-D1: AB3 is not positivity preserving, so w is clamped to the
  * bed after each update and P, Q are zeroed where the depth is zero. */
-static void clamp_w(orc *o, double *w)
+static void clamp_w(orc *o, orc_real *w)
 {
-    double added = 0.0;
+    orc_real added = 0.0;
     for (int j = 0; j < o->ny; j++)
         for (int i = 0; i < o->nx; i++) {
             size_t c = IX(o, i, j);
@@ -533,7 +533,7 @@ static void clamp_w(orc *o, double *w)
     o->clamp_mass += added * o->p.dx * o->p.dy;
 }
 
-static void dry_zero(orc *o, const double *w, double *P, double *Q)
+static void dry_zero(orc *o, const orc_real *w, orc_real *P, orc_real *Q)
 {
     for (int j = 0; j < o->ny; j++)
         for (int i = 0; i < o->nx; i++) {
@@ -579,9 +579,9 @@ static void track_runup(orc *o, int start)
 
 /* -------------------------------------------------------------- the step */
 
-static void swap3(double **h)
+static void swap3(orc_real **h)
 {
-    double *t = h[2];
+    orc_real *t = h[2];
     h[2] = h[1];
     h[1] = h[0];
     h[0] = t;
@@ -591,10 +591,10 @@ int orc_step(orc *o, int nsteps)
 {
     if (!o || nsteps < 0) return -1;
     const int nx = o->nx, ny = o->ny;
-    const double dt = o->p.dt;
+    const orc_real dt = o->p.dt;
     const int bsnq = o->p.model == ORC_BSNQ;
     for (int s = 0; s < nsteps; s++) {
-        double t0 = (double)o->step * dt, t1 = (double)(o->step + 1) * dt;
+        orc_real t0 = (orc_real)o->step * dt, t1 = (orc_real)(o->step + 1) * dt;
         fill_ghosts(o, o->w, o->P, o->Q, t0);
         compute_rhs(o, o->w, o->P, o->Q, o->E[0], o->F[0], o->G[0], o->Fs[0], o->Gs[0]);
         compute_ustar(o, o->P, o->Q, o->U, o->V);
@@ -656,7 +656,7 @@ int orc_step(orc *o, int nsteps)
             if (stage == Kn) { /* Eq. 30 once per step (Reading A-B3) */
                 for (int j = 0; j < ny; j++)
                     for (int i = 0; i < nx; i++) {
-                        double gam = sponge_at(o, i, j);
+                        orc_real gam = sponge_at(o, i, j);
                         if (gam >= 1.0) continue;
                         size_t c = IX(o, i, j);
                         if (o->d[c] > 0.0) o->w1[c] = o->p.ws + gam * (o->w1[c] - o->p.ws);
@@ -667,7 +667,7 @@ int orc_step(orc *o, int nsteps)
             dry_zero(o, o->w1, o->P1, o->Q1);
         }
         swap3(o->E); swap3(o->F); swap3(o->G); swap3(o->Fs); swap3(o->Gs);
-        double *t;
+        orc_real *t;
         t = o->w; o->w = o->w1; o->w1 = t;
         t = o->P; o->P = o->P1; o->P1 = t;
         t = o->Q; o->Q = o->Q1; o->Q1 = t;
@@ -681,7 +681,7 @@ int orc_step(orc *o, int nsteps)
 
 /* ------------------------------------------------------------------ API */
 
-orc *orc_create(const orc_params *p, const double *z)
+orc *orc_create(const orc_params *p, const orc_real *z)
 {
     if (!p || !z || p->nx < 2 || p->ny < 2 || !(p->dx > 0) || !(p->dy > 0) ||
         !(p->dt > 0) || p->K < 0 || !(p->eps > 0))
@@ -693,21 +693,21 @@ orc *orc_create(const orc_params *p, const double *z)
     o->ex = p->nx + 4;
     o->ey = p->ny + 4;
     size_t ne = (size_t)o->ex * (size_t)o->ey;
-    double **cell[] = {&o->z, &o->Bbar, &o->d, &o->ddx, &o->ddy, &o->w, &o->P,
+    orc_real **cell[] = {&o->z, &o->Bbar, &o->d, &o->ddx, &o->ddy, &o->w, &o->P,
                        &o->Q, &o->w1, &o->P1, &o->Q1, &o->U, &o->V, &o->U1,
                        &o->V1, &o->Ec, &o->Fc, &o->Gc, &o->Fsc, &o->Gsc};
     for (size_t k = 0; k < sizeof(cell) / sizeof(cell[0]); k++)
-        *cell[k] = (double *)calloc(ne, sizeof(double));
+        *cell[k] = (orc_real *)calloc(ne, sizeof(orc_real));
     for (int k = 0; k < 3; k++) {
-        o->E[k] = (double *)calloc(ne, sizeof(double));
-        o->F[k] = (double *)calloc(ne, sizeof(double));
-        o->G[k] = (double *)calloc(ne, sizeof(double));
-        o->Fs[k] = (double *)calloc(ne, sizeof(double));
-        o->Gs[k] = (double *)calloc(ne, sizeof(double));
-        o->Hx[k] = (double *)calloc((size_t)(p->nx + 1) * p->ny, sizeof(double));
-        o->Hy[k] = (double *)calloc((size_t)p->nx * (p->ny + 1), sizeof(double));
+        o->E[k] = (orc_real *)calloc(ne, sizeof(orc_real));
+        o->F[k] = (orc_real *)calloc(ne, sizeof(orc_real));
+        o->G[k] = (orc_real *)calloc(ne, sizeof(orc_real));
+        o->Fs[k] = (orc_real *)calloc(ne, sizeof(orc_real));
+        o->Gs[k] = (orc_real *)calloc(ne, sizeof(orc_real));
+        o->Hx[k] = (orc_real *)calloc((size_t)(p->nx + 1) * p->ny, sizeof(orc_real));
+        o->Hy[k] = (orc_real *)calloc((size_t)p->nx * (p->ny + 1), sizeof(orc_real));
     }
-    o->Bc = (double *)calloc((size_t)(p->nx + 3) * (p->ny + 3), sizeof(double));
+    o->Bc = (orc_real *)calloc((size_t)(p->nx + 3) * (p->ny + 3), sizeof(orc_real));
     for (int s = 0; s < 4; s++) o->bc[s].type = ORC_SOLID;
     derive_static(o, z);
     for (int j = 0; j < o->ny; j++)
@@ -721,7 +721,7 @@ orc *orc_create(const orc_params *p, const double *z)
 void orc_destroy(orc *o)
 {
     if (!o) return;
-    double *cell[] = {o->z, o->Bbar, o->d, o->ddx, o->ddy, o->w, o->P, o->Q,
+    orc_real *cell[] = {o->z, o->Bbar, o->d, o->ddx, o->ddy, o->w, o->P, o->Q,
                       o->w1, o->P1, o->Q1, o->U, o->V, o->U1, o->V1, o->Ec,
                       o->Fc, o->Gc, o->Fsc, o->Gsc, o->Bc};
     for (size_t k = 0; k < sizeof(cell) / sizeof(cell[0]); k++) free(cell[k]);
@@ -744,7 +744,7 @@ int orc_set_boundary(orc *o, int side, const orc_bc *bc)
     return 0;
 }
 
-int orc_set_state(orc *o, const double *w, const double *P, const double *Q)
+int orc_set_state(orc *o, const orc_real *w, const orc_real *P, const orc_real *Q)
 {
     if (!o || !w || !P || !Q) return -1;
     for (int j = 0; j < o->ny; j++)
@@ -761,24 +761,24 @@ int orc_set_state(orc *o, const double *w, const double *P, const double *Q)
 
 /* Eq. 33-36 (Reading A-S1): d is the still-water depth of the cell holding
  * the crest; the wave is added where d > 0. */
-int orc_add_solitary(orc *o, double H, double theta, double x0, double y0)
+int orc_add_solitary(orc *o, orc_real H, orc_real theta, orc_real x0, orc_real y0)
 {
     if (!o) return -1;
     int ic = (int)floor(x0 / o->p.dx), jc = (int)floor(y0 / o->p.dy);
     ic = ic < 0 ? 0 : (ic > o->nx - 1 ? o->nx - 1 : ic);
     jc = jc < 0 ? 0 : (jc > o->ny - 1 ? o->ny - 1 : jc);
-    double ds = o->d[IX(o, ic, jc)];
+    orc_real ds = o->d[IX(o, ic, jc)];
     if (!(ds > 0.0) || !(H + ds > 0.0)) return -1;
-    double ks = sqrt(3.0 * fabs(H) / (4.0 * ds * ds * ds));
-    double cs = sqrt(o->p.g * (H + ds));
-    double ct = cos(theta), st = sin(theta);
+    orc_real ks = sqrt(3.0 * fabs(H) / (4.0 * ds * ds * ds));
+    orc_real cs = sqrt(o->p.g * (H + ds));
+    orc_real ct = cos(theta), st = sin(theta);
     for (int j = 0; j < o->ny; j++)
         for (int i = 0; i < o->nx; i++) {
             size_t c = IX(o, i, j);
             if (!(o->d[c] > 0.0)) continue;
-            double xi = ((i + 0.5) * o->p.dx - x0) * ct + ((j + 0.5) * o->p.dy - y0) * st;
-            double sh = 1.0 / cosh(ks * xi);
-            double es = H * sh * sh;
+            orc_real xi = ((i + 0.5) * o->p.dx - x0) * ct + ((j + 0.5) * o->p.dy - y0) * st;
+            orc_real sh = 1.0 / cosh(ks * xi);
+            orc_real es = H * sh * sh;
             o->w[c] = fmax(o->w[c] + es, o->Bbar[c]);
             o->P[c] += cs * es * ct;
             o->Q[c] += cs * es * st;
@@ -788,7 +788,7 @@ int orc_add_solitary(orc *o, double H, double theta, double x0, double y0)
     return 0;
 }
 
-void orc_get_state(const orc *o, double *w, double *P, double *Q)
+void orc_get_state(const orc *o, orc_real *w, orc_real *P, orc_real *Q)
 {
     for (int j = 0; j < o->ny; j++)
         for (int i = 0; i < o->nx; i++) {
@@ -799,9 +799,9 @@ void orc_get_state(const orc *o, double *w, double *P, double *Q)
         }
 }
 
-int orc_get_field(const orc *o, int which, double *out)
+int orc_get_field(const orc *o, int which, orc_real *out)
 {
-    const double *src = which == 0 ? o->Bbar : which == 1 ? o->d
+    const orc_real *src = which == 0 ? o->Bbar : which == 1 ? o->d
                         : which == 2 ? o->U : which == 3 ? o->V : NULL;
     if (!src || !out) return -1;
     for (int j = 0; j < o->ny; j++)
@@ -809,15 +809,15 @@ int orc_get_field(const orc *o, int which, double *out)
     return 0;
 }
 
-void orc_get_time(const orc *o, double *t, long long *step)
+void orc_get_time(const orc *o, orc_real *t, long long *step)
 {
-    if (t) *t = (double)o->step * o->p.dt;
+    if (t) *t = (orc_real)o->step * o->p.dt;
     if (step) *step = o->step;
 }
 
-double orc_mass(const orc *o)
+orc_real orc_mass(const orc *o)
 {
-    double m = 0.0;
+    orc_real m = 0.0;
     for (int j = 0; j < o->ny; j++)
         for (int i = 0; i < o->nx; i++) {
             size_t c = IX(o, i, j);
@@ -826,7 +826,7 @@ double orc_mass(const orc *o)
     return m * o->p.dx * o->p.dy;
 }
 
-double orc_clamp_mass(const orc *o) { return o->clamp_mass; }
+orc_real orc_clamp_mass(const orc *o) { return o->clamp_mass; }
 
 int orc_set_gauges(orc *o, const int *ij, int n, int log_every, int capacity)
 {
@@ -838,7 +838,7 @@ int orc_set_gauges(orc *o, const int *ij, int n, int log_every, int capacity)
     free(o->grec);
     o->gij = n ? (int *)malloc(sizeof(int) * 2 * (size_t)n) : NULL;
     if (n) memcpy(o->gij, ij, sizeof(int) * 2 * (size_t)n);
-    o->grec = (n && capacity) ? (double *)calloc((size_t)n * capacity, sizeof(double)) : NULL;
+    o->grec = (n && capacity) ? (orc_real *)calloc((size_t)n * capacity, sizeof(orc_real)) : NULL;
     o->ng = n;
     o->log_every = log_every;
     o->cap = capacity;
@@ -847,7 +847,7 @@ int orc_set_gauges(orc *o, const int *ij, int n, int log_every, int capacity)
     return 0;
 }
 
-int orc_read_gauges(orc *o, double *eta, int max_rec, int *n_rec)
+int orc_read_gauges(orc *o, orc_real *eta, int max_rec, int *n_rec)
 {
     if (!o || !n_rec || max_rec < 0) return -1;
     int n = o->nrec < max_rec ? o->nrec : max_rec;
@@ -862,18 +862,18 @@ int orc_read_gauges(orc *o, double *eta, int max_rec, int *n_rec)
     return 0;
 }
 
-int orc_runup_enable(orc *o, double delta)
+int orc_runup_enable(orc *o, orc_real delta)
 {
     if (!o || !(delta >= 0.0)) return -1;
-    if (!o->maxw) o->maxw = (double *)malloc(sizeof(double) * (size_t)o->nx * o->ny);
+    if (!o->maxw) o->maxw = (orc_real *)malloc(sizeof(orc_real) * (size_t)o->nx * o->ny);
     o->delta = delta;
     track_runup(o, 1);
     return 0;
 }
 
-int orc_runup_read(const orc *o, double *maxw)
+int orc_runup_read(const orc *o, orc_real *maxw)
 {
     if (!o || !o->maxw || !maxw) return -1;
-    memcpy(maxw, o->maxw, sizeof(double) * (size_t)o->nx * o->ny);
+    memcpy(maxw, o->maxw, sizeof(orc_real) * (size_t)o->nx * o->ny);
     return 0;
 }
