@@ -1,33 +1,34 @@
-// Discrete adjoint of the time step with the AB3 predictor and the Euler
-// start-up (Eq. 15-17, Sec. 2.3), for the Boussinesq model and the
-// nonlinear shallow-water model (Sec. 3.2), and the gradient of a gauge
-// misfit.  The reverse of one step, given the adjoint lambda of the state
-// after it:
+// Discrete adjoint of the time step -- the AB3 predictor with its Euler
+// start-up and the AM4 corrector stages (Eq. 15-20, Sec. 2.3) -- for the
+// Boussinesq model and the nonlinear shallow-water model (Sec. 3.2), and the
+// gradient of a gauge misfit.  The reverse of one stage, given the adjoint
+// lambda of the state after it (the driver in celeris_api.cu orders the
+// stages, the checkpoints and the recomputation):
 //   1. the masks of the update: the dry clamp w >= Bbar (Reading A-D1), the
 //      sponge (Eq. 30), the zero discharge of dry cells;
 //   2. the line solves (Eq. 21-23) transposed: the adjoint of the U* and V*
 //      increments solves the transposed tridiagonal system of every line
-//      (sub- and super-diagonals exchanged, boundary rows included);
-//   3. the AB3 history: the right sides R^n = (E, F, G) and the mixed terms
-//      F*^n, G*^n collect the adjoint weighted by their coefficients in steps
-//      n, n+1 and n+2;
-//   4. R^n's and F*^n's Jacobians transposed: every face flux (KP07
-//      reconstruction with the limiter and positivity branches of the
-//      forward state, then the central-upwind flux), the bed slope and
-//      friction, the dispersive eta terms of Eq. 10-11 and F*, G* of
-//      Eq. 12-13 (linear in the neighbours, ghosts mapped back to the cells
-//      they mirror).
+//      (the forward's line solver in its transposed mode);
+//   3. the history: the right sides R = (E, F, G) and the mixed terms F*, G*
+//      collect the adjoint weighted by their AB3 / AM4 coefficients;
+//   4. R's and F*'s Jacobians transposed at the stage's input state: every
+//      face flux (KP07 reconstruction with the limiter and positivity
+//      branches the forward took, then the central-upwind flux: a reverse
+//      written by hand, checked against dual numbers), the bed slope and
+//      friction (dual numbers), the dispersive eta terms of Eq. 10-11 and
+//      F*, G* of Eq. 12-13 (linear in the neighbours, transposed in closed
+//      form, ghosts mapped back to the cells they mirror).
 // With the bed's gradient requested, the same Jacobians are taken with
 // respect to the bed as well: the face beds of the reconstruction and the
 // flux, the cell bed of the bed slope, friction and the dry clamp, the
 // still-water depth d of the dispersive terms and of the line systems' rows
-// (dT/dd with the transposed solves' solution and the forward's), summed
-// over the run and mapped through d = max(w_s - Bbar, 0), Bbar = mean of 4
-// corners and corner = mean of 4 cell-centre beds (Reading A-W1) to dL/dz.
-// The face and cell Jacobians are exact: the forward device functions are
-// evaluated on dual numbers, one input direction at a time, so every branch
-// follows the forward state.  Adjoints reach a cell through the faces around
-// it, so they are added with atomics (the sums' order is not fixed).
+// (dT/dd with the transposed solves' solution and the forward's), the sine
+// makers' ghost values (Eq. 25-29), summed over the run and mapped through
+// d = max(w_s - Bbar, 0), Bbar = mean of 4 corners and corner = mean of 4
+// cell-centre beds (Reading A-W1) to dL/dz.  Every branch is the forward's.
+// Adjoints reach a cell from several faces and cells; they are summed in
+// shared memory per tile and added to global memory with atomics, so the
+// sums' order is not fixed.
 #include "celeris_adjoint.cuh"
 #include "celeris_physics.cuh"
 
@@ -83,9 +84,9 @@ using ::fmin;
 using ::sqrt;
 using ::rsqrt;
 
-// A cell a face stencil reads: its (w, P, Q) and, unless it is a sine-maker
-// ghost (a constant), the interior cell it mirrors and the sign of each
-// variable there (Sec. 2.4, Reading A-B1).
+// A cell a face stencil reads: its (w, P, Q) and either the interior cell it
+// mirrors with the sign of each variable there (Sec. 2.4, Reading A-B1), or,
+// for a sine-maker ghost, its place in the ghost table.
 template <typename real>
 struct Src {
     real v[3];

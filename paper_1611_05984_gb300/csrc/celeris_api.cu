@@ -1534,11 +1534,12 @@ void cel_ensemble_destroy(cel_ensemble *e)
 // ------------------------------------------------------- discrete adjoint
 //
 // Gradient of the gauge misfit L = 1/2 sum_{n=1..N} sum_g (eta_g^n - obs_g^n)^2
-// with respect to w at the start, by the reverse of every step in
-// celeris_adjoint.cu.  The forward run keeps a checkpoint every C steps;
-// the reverse sweep goes through the segments from the last, recomputing
-// each segment's states from its checkpoint (the resume is bit-exact) and
-// then reversing its steps.
+// with respect to w at the start and the bed, by the reverse of every stage
+// of every step (kernels in celeris_adjoint.cu).  The forward run keeps a
+// checkpoint every C steps; the reverse sweep goes through the segments
+// from the last, each recomputed from its checkpoint (the resume is
+// bit-exact) on the solver's stream while the segment after it is reversed
+// on a stream of its own.
 
 namespace {
 
