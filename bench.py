@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="beach2048",
                     choices=["beach2048", "beach8192", "beach512", "whalin2000", "conical601", "ensemble256",
-                             "adjoint512"])
+                             "adjoint512", "adjoint2048"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -190,8 +190,9 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    if args.workload in ("ensemble256", "adjoint512"):
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no ensemble or adjoint mode; "
+    if args.workload in ("ensemble256", "adjoint512", "adjoint2048"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no ensemble mode and no adjoint (its "
+                          "tangent-linear build gives one directional derivative per run, not the gradient); "
                           "its arm runs the single-grid workloads"}), flush=True)
         return
     s = workload(args.workload)
@@ -345,8 +346,9 @@ def run_ensemble(args):
 
 
 def run_adjoint(args):
-    """Cost of the discrete adjoint on the hump-on-beach workload (512^2,
-    Boussinesq, K = 1, 16 gauges, checkpoints every 100 steps): the time of
+    """Cost of the discrete adjoint on the hump-on-beach workload (512^2, or
+    2048^2 for adjoint2048; Boussinesq, K = 1, 16 gauges, checkpoints every
+    100 steps): the time of
     the gauge-misfit gradients with respect to the initial w and the bed
     (forward with checkpoints, recomputation, reverse) against the time of
     the forward steps alone, both with CUDA events on the solver's stream;
@@ -359,7 +361,7 @@ def run_adjoint(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dtype = torch.float32 if args.precision == "f32" else torch.float64
-    s, gauges = sc.hump_beach(steps=args.steps)
+    s, gauges = sc.hump_beach(n=2048 if args.workload == "adjoint2048" else 512, steps=args.steps)
     g = celeris.from_scenario(s, dtype=dtype)
     stream = g.stream
     t = celeris.from_scenario(sc.hump_beach_target(s), dtype=dtype)
@@ -403,7 +405,7 @@ def main():
     if args.workload == "ensemble256":
         run_ensemble(args)
         return
-    if args.workload == "adjoint512":
+    if args.workload in ("adjoint512", "adjoint2048"):
         run_adjoint(args)
         return
     import torch
