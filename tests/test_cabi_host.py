@@ -93,3 +93,19 @@ def test_ensemble_rejects_empty_member_lists_without_gpu_work():
     assert lib.cel_ensemble_step(None, 1) == 1
     assert lib.cel_ensemble_last_error(None) == b""
     lib.cel_ensemble_destroy(None)
+
+
+def test_adjoint_entry_points_reject_bad_arguments_without_gpu_work():
+    """The adjoint's calls validate on the host before any device work: a
+    NULL solver, non-positive step, checkpoint or gauge counts, and the
+    face self-check's element size and counts."""
+    L = celeris.load()
+    nb = ctypes.c_size_t()
+    assert L.cel_adjoint_bytes(None, 10, 5, 4, 1, ctypes.byref(nb)) == 1
+    loss = ctypes.c_double()
+    assert L.cel_adjoint_gauge_misfit(None, 10, 5, None, 4, None, None, 0, None, None, None,
+                                      ctypes.byref(loss)) == 1
+    assert L.cel_adjoint_face_selfcheck(3, None, 4, None, None) == 1     # element size 4 or 8
+    assert L.cel_adjoint_face_selfcheck(4, None, -1, None, None) == 1    # a negative count
+    assert L.cel_adjoint_face_selfcheck(8, None, 5, None, None) == 1     # NULL buffers
+    assert L.cel_adjoint_face_selfcheck(4, None, 0, None, None) == 0     # nothing to do
