@@ -15,7 +15,7 @@
 //      face flux (KP07 reconstruction with the limiter and positivity
 //      branches the forward took, then the central-upwind flux: a reverse
 //      written by hand, checked against dual numbers), the bed slope and
-//      friction (dual numbers), the dispersive eta terms of Eq. 10-11 and
+//      friction (by hand), the dispersive eta terms of Eq. 10-11 and
 //      F*, G* of Eq. 12-13 (linear in the neighbours, transposed in closed
 //      form, ghosts mapped back to the cells they mirror).
 // With the bed's gradient requested, the same Jacobians are taken with
@@ -475,23 +475,28 @@ __device__ __forceinline__ void cell_vjp(const AdjArgs<real> &A, int i, int j, c
     real dw = -(g * (BxE - BxW) * A.c.rdx) * lF - (g * (ByN - ByS) * A.c.rdy) * lG;
     real dP = real(0), dQ = real(0), dfw = real(0);   // dfw: friction's part of dw
     if (A.phy.friction != kFricNone) {
-        const real x[3] = {acc.val(i, j, 0), acc.val(i, j, 1), acc.val(i, j, 2)};
-        real grad[3];
-#pragma unroll
-        for (int v = 0; v < 3; v++) {
-            Dual<real> w0(x[0], v == 0 ? real(1) : real(0)), P0(x[1], v == 1 ? real(1) : real(0)),
-                Q0(x[2], v == 2 ? real(1) : real(0));
-            Dual<real> hb = w0 - Dual<real>(Bb);
-            Dual<real> hinv = desing(fmax(hb, Dual<real>(real(0))), Dual<real>(A.c.eps));
-            Dual<real> fc = A.phy.friction == kFricManning ? Dual<real>(A.c.fric) * cbrt_r(hinv) : Dual<real>(A.c.fric);
-            Dual<real> mag = sqrt(P0 * P0 + Q0 * Q0);
-            Dual<real> fF = -(fc * P0 * mag * hinv * hinv), fG = -(fc * Q0 * mag * hinv * hinv);
-            grad[v] = lF * fF.d + lG * fG.d;
-        }
-        dfw = grad[0];
+        // -fc |u| u / h with u = k(h) P (Eq. 31-32, Eq. 14): lF fF + lG fG =
+        // -fc mag k^2 (lF P + lG Q), mag = |(P, Q)|, k = desing(max(h, 0)),
+        // fc = f or g n^2 k^(1/3); its derivatives by hand, along the
+        // forward's branches (max keeps h at h = 0; sqrt and cbrt have
+        // derivative 0 at 0)
+        const real P0 = acc.val(i, j, 1), Q0 = acc.val(i, j, 2);
+        const real hb = acc.val(i, j, 0) - Bb;
+        const bool hpos = hb >= real(0);
+        const real hp = hpos ? hb : real(0);
+        const real hinv = desing(hp, A.c.eps);
+        const bool man = A.phy.friction == kFricManning;
+        const real cr = man ? cel::cbrt_r(hinv) : real(1);
+        const real fc = man ? A.c.fric * cr : A.c.fric;
+        const real dfc = man && hinv > real(0) ? A.c.fric / (real(3) * cr * cr) : real(0);
+        const real mag = sqrt(P0 * P0 + Q0 * Q0);
+        const real Aq = lF * P0 + lG * Q0;
+        const real k2 = hinv * hinv;
+        dfw = hpos ? -mag * Aq * (dfc * k2 + real(2) * fc * hinv) * desing_dh(hp, A.c.eps) : real(0);
+        const real um = mag > real(0) ? Aq / mag : real(0);
         dw += dfw;
-        dP = grad[1];
-        dQ = grad[2];
+        dP = -fc * k2 * (P0 * um + mag * lF);
+        dQ = -fc * k2 * (Q0 * um + mag * lG);
     }
     if (A.lBc) {   // the bed: Bbar through h = w - Bbar, the face beds through the slope
         const real hb = acc.val(i, j, 0) - Bb;
