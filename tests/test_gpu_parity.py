@@ -230,3 +230,26 @@ def test_long_run_fp32_drift():
     s = sc.beach(nx=256, ny=256, sponge=24)
     worst, _, _ = _lockstep(s, "f32", 4000, every=500)
     assert worst <= TOL["f32"]
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 4), (4, 16), (2, 40), (40, 2), (33, 5), (5, 33), (3, 3)])
+def test_tiny_and_degenerate_grids(nx, ny):
+    """Grids smaller than one tile, lines of 2 to 5 cells (the line solver's
+    shortest segments), one-tile-plus-one widths: every ghost, boundary-row
+    and tile-edge path on few cells, Boussinesq with one corrector
+    iteration, Manning friction, a sine maker on the west and sponges where
+    the side is long enough, against the oracle in FP64."""
+    rng = np.random.default_rng(100 * nx + ny)
+    dx = 0.5
+    dt = 0.1 * dx / math.sqrt(9.81 * 0.6)
+    s = sc.flat_basin(nx, ny, dx, 0.5, dt, model=0, K=1, friction=2, fcoef=0.02, eps=1e-8)
+    s.z = -0.5 + 0.1 * rng.random((ny, nx))
+    s.w0 = 0.01 * rng.standard_normal((ny, nx))
+    s.P0 = 0.005 * rng.standard_normal((ny, nx))
+    s.Q0 = 0.005 * rng.standard_normal((ny, nx))
+    s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.01, 3.0, 0.1, 0.2),))
+    if nx >= 8:
+        s.sides[sc.E] = sc.Side(sc.SPONGE, nx // 4)
+    if ny >= 8:
+        s.sides[sc.N] = sc.Side(sc.SPONGE, ny // 4)
+    _lockstep(s, "f64", 60, every=20)
