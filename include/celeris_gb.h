@@ -158,6 +158,18 @@ cel_status cel_get_time(cel_solver *s, double *t, int64_t *step);
  * (the first offending cell index goes into cel_last_error).  Synchronises. */
 cel_status cel_check_finite(cel_solver *s);
 
+/* Diagnostics of the present state (device reduction over the interior):
+ * mass = sum of (w - Bbar) dx dy [m^3]; max_speed = the largest |(P, Q)|
+ * k(h) [m/s] with k the velocity factor of Eq. 14 (h = max(w - Bbar, 0));
+ * wet_cells = the cells with w > Bbar.  The mass is summed in double, in no
+ * fixed order.  Synchronises. */
+typedef struct {
+    double mass;
+    double max_speed;
+    int64_t wet_cells;
+} cel_stats;
+cel_status cel_get_stats(cel_solver *s, cel_stats *out);
+
 /* Checkpoint: state, AB3/AM4 history, step count and time, enough for a
  * bit-exact resume.  Device buffer of cel_checkpoint_bytes.  Asynchronous
  * (save) / synchronises (load reads the header). */

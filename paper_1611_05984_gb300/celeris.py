@@ -32,7 +32,7 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
            "cel_load_checkpoint", "cel_runup_enable", "cel_render", "cel_adjoint_bytes",
-           "cel_adjoint_gauge_misfit", "cel_adjoint_face_selfcheck", "cel_last_launch_count", "cel_profile_enable",
+           "cel_adjoint_gauge_misfit", "cel_adjoint_face_selfcheck", "cel_get_stats", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
         L.cel_adjoint_gauge_misfit.argtypes = [vp, i32, i32, ctypes.POINTER(i32), i32, vp, vp, sz, vp, vp, vp,
                                                ctypes.POINTER(d)]
         L.cel_adjoint_face_selfcheck.argtypes = [i32, vp, i32, vp, vp]
+        L.cel_get_stats.argtypes = [vp, ctypes.POINTER(CelStats)]
         L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_profile_enable.argtypes = [vp, i32]
         L.cel_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
@@ -139,6 +140,10 @@ def load(build_if_missing: bool = True):
 
 
 RENDER_MODES = {"eta": 0, "u": 1, "v": 2, "speed": 3, "fresnel": 4}
+
+
+class CelStats(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("max_speed", ctypes.c_double), ("wet_cells", ctypes.c_int64)]
 
 
 class CelRenderParams(ctypes.Structure):
@@ -264,6 +269,13 @@ class Solver:
         self._check(self.L.cel_get_state(self._h, w.data_ptr(), P.data_ptr(), Q.data_ptr()), "get_state")
         self.stream.synchronize()
         return w, P, Q
+
+    def stats(self) -> dict:
+        """Mass [m^3], largest speed [m/s] and wet-cell count of the present
+        state (cel_get_stats)."""
+        st = CelStats()
+        self._check(self.L.cel_get_stats(self._h, ctypes.byref(st)), "get_stats")
+        return {"mass": st.mass, "max_speed": st.max_speed, "wet_cells": st.wet_cells}
 
     def field(self, name: str):
         out = self.torch.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)

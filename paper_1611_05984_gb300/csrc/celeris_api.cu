@@ -7,6 +7,8 @@
 #include "celeris_internal.cuh"
 #include "celeris_adjoint.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -248,9 +250,22 @@ cel_status cuda_fail(cel_solver *s, cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(s, e_, where); \
     } while (0)
 
-int prof_begin(cel_solver *s, int kind) { return s->prof.begin(kind, s->stream); }
+// Each kernel kind of the step is also an NVTX range (stencil, line
+// solves, ghost table), for profilers that filter by range; without a tool
+// attached a range costs a few host nanoseconds.
+const char *const kRangeName[3] = {"cel stencil", "cel line solves", "cel ghost table"};
 
-void prof_end(cel_solver *s, int k) { s->prof.finish(k, s->stream); }
+int prof_begin(cel_solver *s, int kind)
+{
+    nvtxRangePushA(kRangeName[kind]);
+    return s->prof.begin(kind, s->stream);
+}
+
+void prof_end(cel_solver *s, int k)
+{
+    s->prof.finish(k, s->stream);
+    nvtxRangePop();
+}
 
 void prof_free(cel_solver *s) { s->prof.release(); }
 
@@ -797,6 +812,33 @@ cel_status cel_check_finite(cel_solver *s)
                  v / (unsigned long long)s->grid.nx);
         return fail(s, CEL_ERR_NONFINITE, buf);
     }
+    return CEL_OK;
+}
+
+cel_status cel_get_stats(cel_solver *s, cel_stats *out)
+{
+    if (!s || !out) return CEL_ERR_INVALID_ARG;
+    unsigned long long *acc = s->at<unsigned long long>(s->lay.flag) + 8;   // 64 bytes in, beside the finite flag
+    CEL_CUDA(s, cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), s->stream), "stats");
+    const Coef<float> cf = make_coef<float>(s->geo, s->phy, s->bnd);
+    const Coef<double> cd = make_coef<double>(s->geo, s->phy, s->bnd);
+    cudaError_t e = s->es == 4
+                        ? launch_stats<float>(s->geo, s->phy, s->at<float>(s->lay.Bc), s->at<float>(s->lay.w[s->cur]),
+                                              s->at<float>(s->lay.P[s->pcur]), s->at<float>(s->lay.Qc[s->pcur]), cf.eps,
+                                              acc, s->stream)
+                        : launch_stats<double>(s->geo, s->phy, s->at<double>(s->lay.Bc),
+                                               s->at<double>(s->lay.w[s->cur]), s->at<double>(s->lay.P[s->pcur]),
+                                               s->at<double>(s->lay.Qc[s->pcur]), cd.eps, acc, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stats");
+    unsigned long long v[3];
+    CEL_CUDA(s, cudaMemcpyAsync(v, acc, sizeof(v), cudaMemcpyDeviceToHost, s->stream), "stats");
+    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "stats");
+    double mass, vmax;
+    memcpy(&mass, &v[0], sizeof(double));
+    memcpy(&vmax, &v[1], sizeof(double));
+    out->mass = mass * s->geo.dx * s->geo.dy;
+    out->max_speed = vmax;
+    out->wet_cells = (int64_t)v[2];
     return CEL_OK;
 }
 
@@ -1650,6 +1692,11 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     const int64_t step0 = s->step;
     cel_status stt;
     // forward, with checkpoints and the gauge records
+    struct Range {   // an NVTX range over a scope
+        explicit Range(const char *name) { nvtxRangePushA(name); }
+        ~Range() { nvtxRangePop(); }
+    };
+    Range whole("cel adjoint");
     for (int n = 0; n < N; n++) {
         if (n % C == 0 && (stt = cel_save_checkpoint(s, ckpt(n / C), L.ckpt_bytes)) != CEL_OK) return stt;
         if ((stt = step_t<real>(s, 1)) != CEL_OK) return stt;
@@ -1848,6 +1895,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     // recompute segment sg into slot sg & 1 on the solver's stream, once the
     // reverse of the segment that held the slot is done
     auto recompute = [&](int sg) -> cel_status {
+        Range r_("cel adjoint recompute");
         const int sl = sg & 1, n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
         if (used[sl]) CEL_CUDA(s, cudaStreamWaitEvent(fst, ss.rev[sl], 0), "adjoint order");
         cel_status r = cel_load_checkpoint(s, ckpt(sg), L.ckpt_bytes);
@@ -1877,6 +1925,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         const int n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
         slot = sg & 1;
         CEL_CUDA(s, cudaStreamWaitEvent(st, ss.rec[slot], 0), "adjoint order");
+        nvtxRangePushA("cel adjoint reverse");
         for (int n = n1 - 1; n >= n0; n--) {
             const int k = n - n0;
             CEL_CUDA(s, wait_tri(), "adjoint order");
@@ -1978,6 +2027,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                          "adjoint misfit");
             CEL_CUDA(s, cudaMemsetAsync(Gb(sn, 0), 0, L.cells_bytes * 5, st), "adjoint");
         }
+        nvtxRangePop();
         CEL_CUDA(s, wait_tri(), "adjoint order");   // the captured right sides of this slot
         CEL_CUDA(s, cudaEventRecord(ss.rev[slot], st), "adjoint order");
         if (sg > 0 && (stt = recompute(sg - 1)) != CEL_OK) return stt;   // overlaps this segment's reverse

@@ -219,6 +219,11 @@ cudaError_t launch_runup(const Geo &g, const real *Bc, const real *w, real *maxw
 template <typename real>
 cudaError_t launch_gauges(const Geo &g, const Phys &p, const real *w, const int32_t *ij,
                           int n, real *slot, cudaStream_t st);
+// Sum of depths, largest speed (as bits), wet-cell count into out[0..2]
+// (zeroed by the caller).
+template <typename real>
+cudaError_t launch_stats(const Geo &g, const Phys &p, const real *Bc, const real *w, const real *P, const real *Qc,
+                         real eps, unsigned long long *out, cudaStream_t st);
 template <typename real>
 cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, const real *Qc,
                                 unsigned long long *first_bad, cudaStream_t st);

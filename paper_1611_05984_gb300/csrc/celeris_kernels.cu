@@ -177,6 +177,53 @@ __global__ void k_gauges(Geo g, Phys p, const real *w, const int32_t *ij, int n,
     slot[k] = w[(size_t)j * g.px + i] - real(p.ws);
 }
 
+// Diagnostics over the interior cells: sum of the depths w - Bbar (the
+// mass over dx dy), the largest speed |(P, Q)| k(h) with the Eq. 14
+// velocity factor, the count of wet cells (w > Bbar).  Block sums, one
+// atomic per block and quantity: out[0] double sum, out[1] the bits of the
+// largest speed (non-negative doubles order as their bits), out[2] count.
+template <typename real>
+__global__ void k_stats(Geo g, Phys p, const real *Bc, const real *w, const real *P, const real *Qc, real eps,
+                        unsigned long long *out)
+{
+    double mass = 0.0, vmax = 0.0;
+    unsigned long long wet = 0;
+    const size_t n = (size_t)g.nx * g.ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % g.nx), j = (int)(k / g.nx);
+        const real h = w[(size_t)j * g.px + i] - bbar_at(Bc, g, i, j);
+        const real Pv = P[(size_t)j * g.px + i], Qv = Qc[(size_t)i * g.py + j];
+        mass += (double)h;
+        const real sp = desing(fmax(h, real(0)), eps) * sqrt(Pv * Pv + Qv * Qv);
+        vmax = fmax(vmax, (double)sp);
+        wet += h > real(0) ? 1ull : 0ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mass += __shfl_down_sync(0xffffffffu, mass, o);
+        vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+        wet += __shfl_down_sync(0xffffffffu, wet, o);
+    }
+    __shared__ double sm[32], sv[32];
+    __shared__ unsigned long long sw[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        sm[wid] = mass;
+        sv[wid] = vmax;
+        sw[wid] = wet;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; k++) {
+            mass += sm[k];
+            vmax = fmax(vmax, sv[k]);
+            wet += sw[k];
+        }
+        atomicAdd(reinterpret_cast<double *>(out), mass);
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(vmax));
+        atomicAdd(out + 2, wet);
+    }
+}
+
 template <typename real>
 __global__ void k_check_finite(Geo g, const real *w, const real *P, const real *Qc,
                                unsigned long long *first_bad)
@@ -1208,6 +1255,14 @@ cudaError_t launch_gauges(const Geo &g, const Phys &p, const real *w, const int3
 }
 
 template <typename real>
+cudaError_t launch_stats(const Geo &g, const Phys &p, const real *Bc, const real *w, const real *P, const real *Qc,
+                         real eps, unsigned long long *out, cudaStream_t st)
+{
+    k_stats<real><<<304, 256, 0, st>>>(g, p, Bc, w, P, Qc, eps, out);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, const real *Qc,
                                 unsigned long long *first_bad, cudaStream_t st)
 {
@@ -1419,6 +1474,8 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
                                             cudaStream_t);                                              \
     template cudaError_t launch_gauges<real>(const Geo &, const Phys &, const real *, const int32_t *,   \
                                              int, real *, cudaStream_t);                                \
+    template cudaError_t launch_stats<real>(const Geo &, const Phys &, const real *, const real *, const real *, \
+                                            const real *, real, unsigned long long *, cudaStream_t);       \
     template cudaError_t launch_check_finite<real>(const Geo &, const real *, const real *, const real *, \
                                                    unsigned long long *, cudaStream_t);                 \
     template cudaError_t launch_eckart_table<real>(const Geo &, const Phys &, const Bnd &, const real *,  \

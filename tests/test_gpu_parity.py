@@ -253,3 +253,23 @@ def test_tiny_and_degenerate_grids(nx, ny):
     if ny >= 8:
         s.sides[sc.N] = sc.Side(sc.SPONGE, ny // 4)
     _lockstep(s, "f64", 60, every=20)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_stats_match_the_oracle_state(prec):
+    """cel_get_stats: the mass against the oracle's own (sum of w - Bbar over
+    dx dy), the wet-cell count and the largest speed (Eq. 14 velocities)
+    against the oracle's state read back, on a beach with a moving shoreline."""
+    s = sc.beach(nx=200, ny=150, sponge=20)
+    worst, o, g = _lockstep(s, prec, 100)
+    st = g.stats()
+    w, P, Q = o.state()
+    h = w - o.field("Bbar")
+    hp = np.maximum(h, 0.0)
+    k = math.sqrt(2.0) * hp / np.sqrt(hp ** 4 + np.maximum(hp ** 4, s.eps))
+    tol = 1e-12 if prec == "f64" else 1e-5
+    assert abs(st["mass"] - o.mass()) <= tol * abs(o.mass())
+    assert st["wet_cells"] == int(np.sum(h > 0.0)) or prec == "f32"
+    assert abs(st["wet_cells"] - int(np.sum(h > 0.0))) <= 0.001 * h.size
+    vmax = float(np.max(k * np.hypot(P, Q)))
+    assert abs(st["max_speed"] - vmax) <= (1e-9 if prec == "f64" else 1e-3) * vmax
