@@ -15,8 +15,10 @@ each one are named in the test module docstrings):
   * mirror / transpose symmetry -- pinned
   * Thomas solver: dense solve -- pinned; Eckart, sponge, soliton -- pinned
   * friction + AB3 order: uniform-flow ODE -- pinned
-  * Euler start-up, AM4 corrector, sine-ghost timing, corner ghosts:
-    parity unpinned (internal consistency only).
+  * Euler start-up, AB3 predictor and AM4 corrector iterations: each step's
+    formula on the friction ODE, to rounding -- pinned
+  * sine-ghost timing, corner ghosts: parity unpinned (internal consistency
+    only).
   * run-up tracking: standing-mode maximum, dry threshold -- pinned
   * tangent-linear oracle (celeris_tlm.cpp: this source on dual numbers):
     values bit for bit the oracle's, tangents vs central differences,

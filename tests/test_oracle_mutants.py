@@ -28,6 +28,9 @@ MUTANTS = [
      "(23.0 * o->E[0][c] - 15.0 * o->E[1][c] + 5.0 * o->E[2][c])", "test_dispersion_relation_1d"),
     ("ab3_U_coef", "(23.0 * o->F[0][c] - 16.0 * o->F[1][c] + 5.0 * o->F[2][c])",
      "(23.0 * o->F[0][c] - 16.0 * o->F[1][c] + 4.0 * o->F[2][c])", "test_friction_quadratic_order"),
+    ("am4_U_coef", "(9.0 * o->Fc[c] + 19.0 * o->F[0][c] - 5.0 * o->F[1][c] + o->F[2][c])",
+     "(9.0 * o->Fc[c] + 18.0 * o->F[0][c] - 5.0 * o->F[1][c] + o->F[2][c])",
+     "test_time_stepping_formulas_step_by_step"),
     ("wall_no_negate", "P[gc] = -P[sc];", "P[gc] = P[sc];", "test_mass_soliton_channel"),
     ("eq23_sign_s", "*a = s - r;", "*a = -s - r;", "test_symmetry_mirror_x"),
     ("tridiag_B", "*b = 1.0 + 2.0 * r;", "*b = 1.0 + r;", "test_dispersion_relation_1d"),

@@ -447,3 +447,40 @@ def test_runup_tracking_threshold_and_dry_land(oracle_mod):
     o.runup_enable(0.06)
     o.step(2)
     assert np.all(np.isneginf(o.runup()))
+
+
+def _uniform_flow_states(oracle_mod, K, nsteps, dt=0.01, f=0.5, P0=0.5):
+    """P after 0..nsteps steps in the middle of a uniform 1 m deep flow under
+    quadratic friction: away from the walls the step is the ODE update of
+    P' = F(P) = -f P |P| (h = 1, so Eq. 14's k(h) = 1)."""
+    nx, ny, dx = 400, 2, 0.1
+    z = np.full((ny, nx), -1.0)
+    out = []
+    for n in range(nsteps + 1):
+        o = oracle_mod.Oracle(z, dx, dx, dt, model=oracle_mod.NLSW, friction=1, fcoef=f, K=K)
+        o.set_state(0 * z, P0 + 0 * z, 0 * z)
+        o.step(n)
+        out.append(o.state()[1][0, nx // 2])
+    return out
+
+
+@pytest.mark.parametrize("K", [0, 1, 3])
+def test_time_stepping_formulas_step_by_step(oracle_mod, K):
+    """Sec. 2.3, one step at a time on the friction ODE: steps 1 and 2 are
+    forward Euler; step 3 is the AB3 predictor (Eq. 15-17, weights 23, -16,
+    5 over 12) and, with K corrector iterations, K applications of the AM4
+    corrector (Eq. 18-20, weights 9, 19, -5, 1 over 24) starting from the
+    predicted value.  Each checked against the formula with the oracle's
+    own previous states, to rounding."""
+    dt, f = 0.01, 0.5
+    F = lambda P: -f * P * abs(P)
+    P = _uniform_flow_states(oracle_mod, K, 3, dt=dt, f=f)
+    assert P[1] == pytest.approx(P[0] + dt * F(P[0]), rel=1e-14, abs=0)
+    assert P[2] == pytest.approx(P[1] + dt * F(P[1]), rel=1e-14, abs=0)
+    y = P[2] + dt / 12 * (23 * F(P[2]) - 16 * F(P[1]) + 5 * F(P[0]))
+    for _ in range(K):
+        y = P[2] + dt / 24 * (9 * F(y) + 19 * F(P[2]) - 5 * F(P[1]) + F(P[0]))
+    assert P[3] == pytest.approx(y, rel=1e-14, abs=0)
+    if K >= 1:   # and not the predictor alone: the corrector moved the value
+        ab3 = P[2] + dt / 12 * (23 * F(P[2]) - 16 * F(P[1]) + 5 * F(P[0]))
+        assert abs(P[3] - ab3) > 1e-9
