@@ -351,13 +351,14 @@ _tlm = None
 
 
 def build_tlm(force: bool = False) -> str:
-    """Compile the tangent-linear oracle (g++, FP64, no FMA contraction, one thread)."""
+    """Compile the tangent-linear oracle (g++, FP64, no FMA contraction, OpenMP over rows and lines as
+    the oracle)."""
     os.makedirs(os.path.dirname(_TLM_LIB), exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR), os.path.getmtime(_TLM_SRC))
     if not force and os.path.exists(_TLM_LIB) and os.path.getmtime(_TLM_LIB) >= newest:
         return _TLM_LIB
     tmp = _TLM_LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _TLM_SRC]
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _TLM_SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _TLM_LIB)
     return _TLM_LIB

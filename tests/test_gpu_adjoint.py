@@ -601,3 +601,39 @@ def test_adjoint_against_tangent_linear_oracle_on_a_beach():
         ad = float(np.sum(gw * vw) + np.sum(gz * vz))
         errs.append(abs(ad - ref) / abs(ref))
     assert max(errs) <= 1e-3, errs
+
+
+@pytest.mark.parametrize("steps,ckpt,bound", [(40, 10, 1e-12), (2000, 100, 1e-3)], ids=["40-steps", "2000-steps"])
+def test_adjoint_against_tangent_linear_oracle_on_the_hump_beach(steps, ckpt, bound):
+    """The adjoint's own configuration (the 512 x 512 hump beach, Boussinesq,
+    K = 1, 16 gauges, observations from the perturbed-hump, perturbed-bed
+    target run), over its first 40 steps (checkpoints every 10) and its full
+    2000 (every 100): both gradients against the tangent-linear oracle along
+    smooth random directions in the initial state and the bed."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    from tests.helpers import tangent_run
+    s, gauges = sc.hump_beach(n=512, steps=steps)
+    t = oracle_from(sc.hump_beach_target(s))
+    t.set_gauges(gauges, 1, s.steps)
+    t.step(s.steps)
+    obs = t.read_gauges(s.steps)
+    loss, eta, gw, g, gz = _gpu_gradient(s, gauges, obs, ckpt=ckpt, bed=True)
+    bed = g.field("Bbar").double().cpu().numpy()
+    wet = s.w0 > bed
+    X, Y = np.meshgrid(np.arange(s.nx) + 0.5, np.arange(s.ny) + 0.5)
+    rng = np.random.default_rng(512)
+    errs = []
+    for _ in range(3):
+        vw = np.zeros_like(X)
+        vz = np.zeros_like(X)
+        for _ in range(4):
+            cx, cy, r = rng.uniform(100, 380), rng.uniform(60, 450), rng.uniform(15, 50)
+            vw += rng.standard_normal() * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / r ** 2)
+            vz += rng.standard_normal() * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / r ** 2)
+        vw *= wet
+        e, de = tangent_run(s, gauges, vz, vw)
+        ref = float(np.sum((e - obs) * de))
+        ad = float(np.sum(gw * vw) + np.sum(gz * vz))
+        errs.append(abs(ad - ref) / abs(ref))
+    print("tlm hump", steps, errs)
+    assert max(errs) <= bound, errs
