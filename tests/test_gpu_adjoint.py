@@ -637,3 +637,53 @@ def test_adjoint_against_tangent_linear_oracle_on_the_hump_beach(steps, ckpt, bo
         errs.append(abs(ad - ref) / abs(ref))
     print("tlm hump", steps, errs)
     assert max(errs) <= bound, errs
+
+
+@pytest.mark.parametrize("steps", [500, 2000])
+def test_fp32_gradients_on_the_hump_beach(steps):
+    """The benchmark's precision: on the 512 x 512 hump beach (checkpoints
+    every 100) the FP32 adjoint's gradients against the FP64 adjoint's
+    (which equals the tangent-linear reference within 5e-5 at 2000 steps).
+    Before the wave reaches the beach (500 steps) both gradients agree
+    within 5e-3.  After it runs up the beach (2000 steps) the moving
+    shoreline's wet-dry and limiter branches differ between the two
+    precisions' states, and dL/dw0 -- the adjoint after all 2000 reversed
+    steps -- carries those differences (6 % measured); dL/dz, summed over the
+    run, stays within 1e-3.  Directional errors are scaled by the directions'
+    rms derivative (a single direction can nearly cancel).  The hump is
+    clipped at 4 widths so that both precisions see the same exact rest far
+    away (an unclipped Gaussian's 1e-44 tail exists in FP64 only)."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    s, gauges = sc.hump_beach(n=512, steps=steps)
+    X, Y = np.meshgrid(np.arange(s.nx) + 0.5, np.arange(s.ny) + 0.5)
+    r2 = (X - 0.4 * s.nx) ** 2 + (Y - 0.5 * s.ny) ** 2
+    s.w0 = np.where(r2 < (4 * 30.0) ** 2, s.w0, np.maximum(s.z, 0.0))
+    t = oracle_from(sc.hump_beach_target(s))
+    t.set_gauges(gauges, 1, s.steps)
+    t.step(s.steps)
+    obs = t.read_gauges(s.steps)
+    _, _, w64, g, z64 = _gpu_gradient(s, gauges, obs, ckpt=100, bed=True)
+    _, _, w32, _, z32 = _gpu_gradient(s, gauges, obs, prec="f32", ckpt=100, bed=True)
+    bed = g.field("Bbar").double().cpu().numpy()
+    wet = s.w0 > bed
+    rng = np.random.default_rng(32)
+    d32, d64 = [], []
+    for _ in range(8):
+        vw = np.zeros_like(X)
+        vz = np.zeros_like(X)
+        for _ in range(4):
+            cx, cy, r = rng.uniform(100, 380), rng.uniform(60, 450), rng.uniform(15, 50)
+            vw += rng.standard_normal() * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / r ** 2)
+            vz += rng.standard_normal() * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / r ** 2)
+        vw *= wet
+        d64.append(float(np.sum(w64 * vw) + np.sum(z64 * vz)))
+        d32.append(float(np.sum(w32 * vw) + np.sum(z32 * vz)))
+    d32, d64 = np.array(d32), np.array(d64)
+    dirs = np.max(np.abs(d32 - d64)) / np.sqrt(np.mean(d64 ** 2))
+    fw = np.linalg.norm((w32 - w64)[wet]) / np.linalg.norm(w64[wet])
+    fz = np.linalg.norm(z32 - z64) / np.linalg.norm(z64)
+    assert fz <= 1e-3, fz
+    if steps == 500:
+        assert fw <= 5e-3 and dirs <= 5e-3, (fw, dirs)
+    else:
+        assert fw <= 0.1 and dirs <= 0.05, (fw, dirs)
