@@ -181,7 +181,10 @@ class Solver:
     def __init__(self, z, dx: float, dy: float, dt: float, *, dtype=None, model: int = BSNQ,
                  g: float = 9.81, Bd: float = 1.0 / 15.0, theta: float = 1.3, eps: float = 5e-12,
                  K: int = 0, ws: float = 0.0, friction: int = FRIC_NONE, fcoef: float = 0.0,
-                 device=None, stream=None):
+                 device=None, stream=None, poison: bool = False):
+        """poison: fill the workspace with 0xFF bytes (NaN in every real
+        field) before cel_create, so that a read of memory the library never
+        wrote shows up as a non-finite state (a test aid)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the Celeris GB300 solver needs a CUDA device")
@@ -202,6 +205,8 @@ class Solver:
         with torch.cuda.device(self.device):
             self.stream = stream or torch.cuda.current_stream(self.device)
             self.workspace = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+            if poison:
+                self.workspace.fill_(255)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         h = ctypes.c_void_p()
@@ -445,13 +450,15 @@ class Ensemble:
             pass
 
 
-def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every: int = 100, bed: bool = False):
+def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every: int = 100, bed: bool = False,
+                          poison: bool = False):
     """Run nsteps from the solver's present (freshly set) state and return
     (L, eta, dL/dw0), plus dL/dz when bed is set: the gauge misfit
     L = 1/2 sum (eta - obs)^2 over steps 1..nsteps, the recorded eta
     ([nsteps, ngauges] tensor) and its gradients with respect to w at the
     start and to the cell-centre bed ([ny, nx] tensors), by the discrete
-    adjoint (cel_adjoint_gauge_misfit).  obs: [nsteps, ngauges]."""
+    adjoint (cel_adjoint_gauge_misfit).  obs: [nsteps, ngauges].  poison:
+    fill the scratch with 0xFF bytes first (a test aid, as for Solver)."""
     torch = solver.torch
     ij = np.ascontiguousarray(np.asarray(gauges, dtype=np.int32).reshape(-1, 2))
     ng = len(ij)
@@ -463,6 +470,8 @@ def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every
                   "adjoint_bytes")
     with torch.cuda.device(solver.device):
         scratch = torch.empty(nb.value + 256, dtype=torch.uint8, device=solver.device)
+        if poison:
+            scratch.fill_(255)
         eta = torch.empty((nsteps, ng), dtype=solver.dtype, device=solver.device)
         grad = torch.empty((solver.ny, solver.nx), dtype=solver.dtype, device=solver.device)
         grad_z = torch.empty((solver.ny, solver.nx), dtype=solver.dtype, device=solver.device) if bed else None

@@ -687,3 +687,29 @@ def test_fp32_gradients_on_the_hump_beach(steps):
         assert fw <= 5e-3 and dirs <= 5e-3, (fw, dirs)
     else:
         assert fw <= 0.1 and dirs <= 0.05, (fw, dirs)
+
+
+@pytest.mark.parametrize("model,K", [(0, 1), (1, 2)], ids=["bsnq-K1", "nlsw-K2"])
+def test_adjoint_reads_nothing_unwritten(model, K):
+    """The solver's workspace and the adjoint's scratch filled with 0xFF
+    bytes (NaN in every real field) beforehand: the loss, the records and
+    both gradients equal those of fresh allocations (to the atomics'
+    summation order), with a sine maker, so the reverse's own ghost table,
+    the ghost adjoints, both segment slots and the captured right sides are
+    all exercised."""
+    from paper_1611_05984_gb300 import celeris
+    from paper_1611_05984_gb300 import scenarios as sc
+    from tests.helpers import tilted_bed_scenario
+    s, gauges, _, _ = tilted_bed_scenario(model=model, K=K, friction=2, nsteps=12, sine=True)
+    rng = np.random.default_rng(3)
+    obs = torch.as_tensor(0.01 * rng.standard_normal((s.steps, len(gauges))), dtype=torch.float64)
+    out = []
+    for poison in (False, True):
+        g = celeris.from_scenario(s, dtype=torch.float64, poison=poison)
+        out.append(celeris.gauge_misfit_gradient(g, s.steps, gauges, obs, 3, bed=True, poison=poison))
+    (l0, e0, w0, z0), (l1, e1, w1, z1) = out
+    assert l1 == pytest.approx(l0, rel=1e-14)
+    assert torch.equal(e0, e1)
+    for a, b in ((w0, w1), (z0, z1)):
+        assert torch.isfinite(b).all()
+        assert float(torch.linalg.norm(b - a)) <= 1e-12 * float(torch.linalg.norm(a))

@@ -273,3 +273,38 @@ def test_stats_match_the_oracle_state(prec):
     assert abs(st["wet_cells"] - int(np.sum(h > 0.0))) <= 0.001 * h.size
     vmax = float(np.max(k * np.hypot(P, Q)))
     assert abs(st["max_speed"] - vmax) <= (1e-9 if prec == "f64" else 1e-3) * vmax
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("case", ["beach_crop", "tiny_sine", "channel_K2"])
+def test_poisoned_workspace_reads_nothing_unwritten(prec, case):
+    """The workspace filled with 0xFF bytes (NaN in every real field, all
+    dry bits set) before cel_create: a kernel that reads memory the library
+    never wrote -- padding columns, history slots before the start-up steps
+    fill them, mask words, ghost tables -- would turn the state non-finite or
+    off the oracle.  Parity must hold as with a fresh allocation."""
+    if case == "beach_crop":
+        s = sc.beach(nx=200, ny=150, sponge=20)
+        n = 200
+    elif case == "tiny_sine":
+        rng = np.random.default_rng(7)
+        s = sc.flat_basin(5, 33, 0.5, 0.5, 0.1 * 0.5 / math.sqrt(9.81 * 0.6), model=0, K=1, friction=2,
+                          fcoef=0.02, eps=1e-8)
+        s.z = -0.5 + 0.1 * rng.random((33, 5))
+        s.w0 = 0.01 * rng.standard_normal((33, 5))
+        s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.01, 3.0, 0.1, 0.2),))
+        s.sides[sc.N] = sc.Side(sc.SPONGE, 8)
+        n = 60
+    else:
+        s = sc.soliton_channel(nx=250, ny=30, K=2, x0=5.0)
+        n = 200
+    o = oracle_from(s)
+    from paper_1611_05984_gb300 import celeris
+    dt = torch.float64 if prec == "f64" else torch.float32
+    g = celeris.from_scenario(s, dtype=dt, poison=True)
+    o.step(n)
+    g.step(n)
+    assert g.check_finite()
+    wo, _, _ = o.state()
+    wg = _np(g.state()[0])
+    assert rel_l2(wg - s.ws, wo - s.ws) <= TOL[prec]
