@@ -384,9 +384,10 @@ class Ensemble:
     launch per kernel kind and stage (cel_ensemble_*).  The members stay
     usable alone (state, fields, gauges, checkpoints) between ensemble steps;
     the ensemble keeps them alive.  Its launches go to ``stream`` (the current
-    stream by default)."""
+    stream by default).  poison: fill the argument tables with 0xFF bytes
+    before cel_ensemble_create (a test aid, as for Solver)."""
 
-    def __init__(self, members: Sequence[Solver], stream=None):
+    def __init__(self, members: Sequence[Solver], stream=None, poison: bool = False):
         torch = members[0].torch
         self.torch = torch
         self.members = list(members)
@@ -401,6 +402,8 @@ class Ensemble:
         with torch.cuda.device(dev):
             self.stream = stream or torch.cuda.current_stream(dev)
             self.table = torch.empty(nb.value + 256, dtype=torch.uint8, device=dev)
+            if poison:
+                self.table.fill_(255)
         ptr = (self.table.data_ptr() + 255) // 256 * 256
         msg = ctypes.create_string_buffer(256)
         h = ctypes.c_void_p()

@@ -86,6 +86,23 @@ def test_ensemble_bitwise_equals_single_runs(prec):
         _assert_equal(alone, together)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_poisoned_ensemble_equals_single_runs(prec):
+    """Members built on workspaces of NaN bytes, stepped with argument tables
+    of NaN bytes, still equal fresh members stepped alone bit for bit: neither
+    the ensemble's launches nor its tables read memory nothing wrote."""
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)
+    alone = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    together = [celeris.from_scenario(s, dtype=_dtype(prec), poison=True) for s in scens]
+    ens = celeris.Ensemble(together, poison=True)
+    for n in (1, 2, 9):
+        for s in alone:
+            s.step(n)
+        ens.step(n)
+        _assert_equal(alone, together)
+
+
 @pytest.mark.parametrize("K,prec", [(0, "f32"), (0, "f64"), (2, "f32")])
 def test_ensemble_other_corrector_counts(K, prec):
     """K = 0 (predictor only, AB3 carries) and K = 2 (three stages per step)
