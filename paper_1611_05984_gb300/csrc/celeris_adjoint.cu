@@ -530,9 +530,11 @@ __device__ __forceinline__ void face_vjp(const AdjArgs<real> &A, int dir, int f,
     // flux components: mass, normal and tangential momentum
     const real lH[3] = {lR[0], dir == 0 ? lR[1] : lR[2], dir == 0 ? lR[2] : lR[1]};
     if (lH[0] == real(0) && lH[1] == real(0) && lH[2] == real(0)) return;
-    Src<real> s[4];
-#pragma unroll
-    for (int c = 0; c < 4; c++) s[c] = dir == 0 ? acc.src(f - 2 + c, line) : acc.src(line, f - 2 + c);
+    // the values now, the mappings after the reverse (fewer live registers)
+    auto at = [&](int c, int &i, int &j) {
+        i = dir == 0 ? f - 2 + c : line;
+        j = dir == 0 ? line : f - 2 + c;
+    };
     auto face_bed = [&](int q) {   // bed of face q (dir 0: x-face q of row line)
         return dir == 0 ? real(0.5) * (acc.bed(q, line) + acc.bed(q, line + 1))
                         : real(0.5) * (acc.bed(line, q) + acc.bed(line + 1, q));
@@ -541,22 +543,27 @@ __device__ __forceinline__ void face_vjp(const AdjArgs<real> &A, int dir, int f,
     real w[4], P[4], Q[4], lw[4] = {0, 0, 0, 0}, lP[4] = {0, 0, 0, 0}, lQ[4] = {0, 0, 0, 0}, lB[3] = {0, 0, 0};
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        w[q] = s[q].v[0];
-        P[q] = s[q].v[1];
-        Q[q] = s[q].v[2];
+        int i, j;
+        at(q, i, j);
+        w[q] = acc.val(i, j, 0);
+        P[q] = acc.val(i, j, 1);
+        Q[q] = acc.val(i, j, 2);
     }
     face_flux_vjp(w, P, Q, Bm, Bf, Bp, A.c.theta, A.c.g, A.c.eps, dir, lH, lw, lP, lQ, lB);
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        if (s[c].idx < 0) {   // a sine-maker ghost: its values' adjoints, for the depth they follow
-            acc.ghost(s[c], 0, lw[c]);
-            acc.ghost(s[c], 1, lP[c]);
-            acc.ghost(s[c], 2, lQ[c]);
+        int i, j;
+        at(c, i, j);
+        const Src<real> s = acc.map(i, j);
+        if (s.idx < 0) {   // a sine-maker ghost: its values' adjoints, for the depth they follow
+            acc.ghost(s, 0, lw[c]);
+            acc.ghost(s, 1, lP[c]);
+            acc.ghost(s, 2, lQ[c]);
             continue;
         }
-        acc.cell(0, s[c].ci, s[c].cj, lw[c]);
-        acc.cell(1, s[c].ci, s[c].cj, s[c].sgn[1] * lP[c]);
-        acc.cell(2, s[c].ci, s[c].cj, s[c].sgn[2] * lQ[c]);
+        acc.cell(0, s.ci, s.cj, lw[c]);
+        acc.cell(1, s.ci, s.cj, s.sgn[1] * lP[c]);
+        acc.cell(2, s.ci, s.cj, s.sgn[2] * lQ[c]);
     }
     if (A.lBc) {   // the three face beds, each the mean of its two corners
 #pragma unroll
@@ -638,7 +645,7 @@ __device__ __forceinline__ void disp_vjp(const AdjArgs<real> &A, int i, int j, c
 #pragma unroll
     for (int q = 0; q < 13; q++) {
         if (pts[q].wgt == real(0)) continue;
-        const Src<real> s = acc.src(i + pts[q].di, j + pts[q].dj);
+        const Src<real> s = acc.map(i + pts[q].di, j + pts[q].dj);
         if (s.idx >= 0) acc.cell(0, s.ci, s.cj, pts[q].wgt);
         else acc.ghost(s, 0, pts[q].wgt);
     }
@@ -652,10 +659,10 @@ __device__ __forceinline__ void disp_vjp(const AdjArgs<real> &A, int i, int j, c
                       {1, 1, qxy * lGs}, {1, -1, -qxy * lGs}, {-1, 1, -qxy * lGs}, {-1, -1, qxy * lGs}};
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-        const Src<real> s = acc.src(i + mq[q].di, j + mq[q].dj);
+        const Src<real> s = acc.map(i + mq[q].di, j + mq[q].dj);
         if (s.idx >= 0) acc.cell(2, s.ci, s.cj, s.sgn[2] * mq[q].wgt);
         else acc.ghost(s, 2, mq[q].wgt);
-        const Src<real> t = acc.src(i + mp[q].di, j + mp[q].dj);
+        const Src<real> t = acc.map(i + mp[q].di, j + mp[q].dj);
         if (t.idx >= 0) acc.cell(1, t.ci, t.cj, t.sgn[1] * mp[q].wgt);
         else acc.ghost(t, 1, mp[q].wgt);
     }
@@ -694,22 +701,24 @@ __device__ __forceinline__ void disp_vjp(const AdjArgs<real> &A, int i, int j, c
     acc.ring(i, j - 1, -Ldy);
 }
 
-// The right sides' Jacobians transposed over one 32 x 32 tile: the cells'
-// bed slope, friction and dispersive terms, the x-faces of the tile's rows
-// and the y-faces of its columns (the east and north boundary faces with the
-// last tiles).  Their adjoints reach cells up to 2 beyond the tile (ghosts
-// mapped to the cells they mirror), depths 1 beyond and corners 2 beyond; they
-// are summed in shared memory over that window and added to global memory
-// once per window element.
-constexpr int kVT = 32;              // tile edge
+// The right sides' Jacobians transposed over one tile of 32 columns and TY
+// rows: the cells' bed slope, friction and dispersive terms, the x-faces of
+// the tile's rows and the y-faces of its columns (the east and north boundary
+// faces with the last tiles).  Their adjoints reach cells up to 2 beyond the
+// tile (ghosts mapped to the cells they mirror), depths 1 beyond and corners
+// 2 beyond; they are summed in shared memory over that window and added to
+// global memory once per window element.
+constexpr int kVT = 32;              // tile width
 constexpr int kVW = kVT + 4;         // cell window: x0 - 2 .. x0 + 33
 constexpr int kVWS = kVW + 1;
 constexpr int kVC = kVT + 5;         // corner window: x0 - 2 .. x0 + 34
 constexpr int kVCS = kVC + 1;
 constexpr int kVjpThreads = 256;
 
-template <typename real>
+template <typename real, int TY>
 struct TileAcc {
+    static constexpr int kWH = TY + 4;   // cell window rows: y0 - 2 .. y0 + TY + 1
+    static constexpr int kCH = TY + 5;   // corner window rows
     real *sv[3], *sd, *sc;   // shared windows: lw, lP, lQ, ld, lBc
     real *gv[3], *gd, *gc;   // global arrays
     const real *xv[3], *xb;  // shared windows: the state as source2d gives it, the bed corners
@@ -727,7 +736,9 @@ struct TileAcc {
     {
         return xv[v][(j - y0 + 2) * kVWS + (i - x0 + 2)];
     }
-    __device__ __forceinline__ Src<real> src(int i, int j) const
+    // where the adjoint of window cell (i, j) goes: the cell it is or
+    // mirrors, with the signs, or a sine-maker ghost (no values)
+    __device__ __forceinline__ Src<real> map(int i, int j) const
     {
         Src<real> s;
         if (interior) {
@@ -738,10 +749,6 @@ struct TileAcc {
         } else {
             mirror2d(*G, sine, i, j, s);
         }
-        const int o = (j - y0 + 2) * kVWS + (i - x0 + 2);
-        s.v[0] = xv[0][o];
-        s.v[1] = xv[1][o];
-        s.v[2] = xv[2][o];
         return s;
     }
     __device__ __forceinline__ real bed(int ci, int cj) const { return xb[(cj - y0 + 2) * kVCS + (ci - x0 + 2)]; }
@@ -753,65 +760,67 @@ struct TileAcc {
     {
         if (v == real(0)) return;
         const int li = i - x0 + 2, lj = j - y0 + 2;
-        if (li >= 0 && li < kVW && lj >= 0 && lj < kVW) atomicAdd(sv[var] + lj * kVWS + li, v);
+        if (li >= 0 && li < kVW && lj >= 0 && lj < kWH) atomicAdd(sv[var] + lj * kVWS + li, v);
         else atomicAdd(gv[var] + (size_t)j * nx + i, v);
     }
     __device__ __forceinline__ void ring(int i, int j, real v) const
     {
         if (v == real(0)) return;
         const int li = i - x0 + 2, lj = j - y0 + 2;
-        if (li >= 0 && li < kVW && lj >= 0 && lj < kVW) atomicAdd(sd + lj * kVWS + li, v);
+        if (li >= 0 && li < kVW && lj >= 0 && lj < kWH) atomicAdd(sd + lj * kVWS + li, v);
         else atomicAdd(gd + (size_t)(j + 1) * (nx + 2) + (i + 1), v);
     }
     __device__ __forceinline__ void corner(int ci, int cj, real v) const
     {
         if (v == real(0)) return;
         const int li = ci - x0 + 2, lj = cj - y0 + 2;
-        if (li >= 0 && li < kVC && lj >= 0 && lj < kVC) atomicAdd(sc + lj * kVCS + li, v);
+        if (li >= 0 && li < kVC && lj >= 0 && lj < kCH) atomicAdd(sc + lj * kVCS + li, v);
         else atomicAdd(gc + (size_t)(cj + 1) * pc + (ci + 1), v);
     }
 };
 
-template <typename real>
+template <typename real, int TY>
 constexpr size_t vjp_smem_bytes()
 {
-    return sizeof(real) * (size_t)(7 * kVW * kVWS + 2 * kVC * kVCS);
+    return sizeof(real) * (size_t)(7 * (TY + 4) * kVWS + 2 * (TY + 5) * kVCS);
 }
 
-template <typename real>
+template <typename real, int TY>
 __global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__ AdjArgs<real> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sm = reinterpret_cast<real *>(smem_raw);
     const Geo &G = A.geo;
-    const int x0 = blockIdx.x * kVT, y0 = blockIdx.y * kVT;
+    using Acc = TileAcc<real, TY>;
+    constexpr int kWH = Acc::kWH, kCH = Acc::kCH;
+    const int x0 = blockIdx.x * kVT, y0 = blockIdx.y * TY;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    constexpr int ntot = 4 * kVW * kVWS + kVC * kVCS;
+    constexpr int ntot = 4 * kWH * kVWS + kCH * kVCS;
     for (int k = tid; k < ntot; k += kVjpThreads) sm[k] = real(0);
-    TileAcc<real> acc;
-    for (int v = 0; v < 3; v++) acc.sv[v] = sm + v * kVW * kVWS;
-    acc.sd = sm + 3 * kVW * kVWS;
-    acc.sc = sm + 4 * kVW * kVWS;
+    Acc acc;
+    for (int v = 0; v < 3; v++) acc.sv[v] = sm + v * kWH * kVWS;
+    acc.sd = sm + 3 * kWH * kVWS;
+    acc.sc = sm + 4 * kWH * kVWS;
     real *xs = sm + ntot;
-    for (int v = 0; v < 3; v++) acc.xv[v] = xs + v * kVW * kVWS;
-    real *xb = xs + 3 * kVW * kVWS;
+    for (int v = 0; v < 3; v++) acc.xv[v] = xs + v * kWH * kVWS;
+    real *xb = xs + 3 * kWH * kVWS;
     acc.xb = xb;
     acc.G = &G;
     acc.sine = A.c.sine;
-    acc.interior = x0 >= 2 && y0 >= 2 && x0 + kVW - 2 <= G.nx && y0 + kVW - 2 <= G.ny;
+    acc.interior = x0 >= 2 && y0 >= 2 && x0 + kVW - 2 <= G.nx && y0 + kWH - 2 <= G.ny;
     acc.lg = A.lg;
     acc.tsel = A.tsel;
     acc.npos = A.c.npos;
     // the state with its ghosts (source2d) on cells within 2 of the grid,
     // and the bed corners, over the windows
-    for (int k = tid; k < kVW * kVW; k += kVjpThreads) {
+    for (int k = tid; k < kVW * kWH; k += kVjpThreads) {
         const int li = k % kVW, lj = k / kVW, i = x0 - 2 + li, j = y0 - 2 + lj, o = lj * kVWS + li;
         if (i >= -2 && i <= G.nx + 1 && j >= -2 && j <= G.ny + 1) {
             const Src<real> q = source2d(A, i, j);
-            for (int v = 0; v < 3; v++) xs[v * kVW * kVWS + o] = q.v[v];
+            for (int v = 0; v < 3; v++) xs[v * kWH * kVWS + o] = q.v[v];
         }
     }
-    for (int k = tid; k < kVC * kVC; k += kVjpThreads) {
+    for (int k = tid; k < kVC * kCH; k += kVjpThreads) {
         const int li = k % kVC, lj = k / kVC, ci = x0 - 2 + li, cj = y0 - 2 + lj;
         if (ci >= -1 && ci <= G.nx + 1 && cj >= -1 && cj <= G.ny + 1) xb[lj * kVCS + li] = corner(A.Bc, G, ci, cj);
     }
@@ -825,7 +834,7 @@ __global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__
     acc.nx = G.nx;
     acc.pc = G.pc;
     __syncthreads();
-    const int xe = min(x0 + kVT, G.nx), ye = min(y0 + kVT, G.ny);
+    const int xe = min(x0 + kVT, G.nx), ye = min(y0 + TY, G.ny);
     for (int j = y0 + ty; j < ye; j += kVjpThreads / 32) {
         const int i = x0 + tx;
         if (i < xe) {
@@ -842,7 +851,7 @@ __global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__
         if (i < xe) face_vjp(A, 1, gq, i, acc);
     }
     __syncthreads();
-    for (int k = tid; k < kVW * kVW; k += kVjpThreads) {
+    for (int k = tid; k < kVW * kWH; k += kVjpThreads) {
         const int li = k % kVW, lj = k / kVW, i = x0 - 2 + li, j = y0 - 2 + lj, o = lj * kVWS + li;
         if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) {
             const size_t c = (size_t)j * G.nx + i;
@@ -853,7 +862,7 @@ __global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__
             atomicAdd(A.ld + ring_index(G, i, j), acc.sd[o]);
     }
     if (A.lBc)
-        for (int k = tid; k < kVC * kVC; k += kVjpThreads) {
+        for (int k = tid; k < kVC * kCH; k += kVjpThreads) {
             const int li = k % kVC, lj = k / kVC, ci = x0 - 2 + li, cj = y0 - 2 + lj;
             const real v = acc.sc[lj * kVCS + li];
             if (v != real(0) && ci >= -1 && ci <= G.nx + 1 && cj >= -1 && cj <= G.ny + 1)
@@ -1053,19 +1062,45 @@ cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <typename real>
-cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st)
+template <typename real, int TY>
+cudaError_t launch_vjp_rows(const AdjArgs<real> &a, cudaStream_t st)
 {
-    constexpr size_t smem = vjp_smem_bytes<real>();
+    constexpr size_t smem = vjp_smem_bytes<real, TY>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_adj_vjp<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_adj_vjp<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 g((a.geo.nx + kVT - 1) / kVT, (a.geo.ny + kVT - 1) / kVT);
-    k_adj_vjp<real><<<g, kVjpThreads, smem, st>>>(a);
+    dim3 g((a.geo.nx + kVT - 1) / kVT, (a.geo.ny + TY - 1) / TY);
+    k_adj_vjp<real, TY><<<g, kVjpThreads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// Tile rows of the Jacobian kernel: 32 while 32 x 32 tiles give every SM
+// several blocks, else 16 or 8, so that small grids still fill the GPU.
+static int vjp_tile_rows(int nx, int ny)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 1;
+    }
+    const long cols = (nx + kVT - 1) / kVT, want = 4L * nsm;
+    if (cols * ((ny + 31) / 32) >= want) return 32;
+    if (cols * ((ny + 15) / 16) >= want) return 16;
+    return 8;
+}
+
+template <typename real>
+cudaError_t launch_adjoint_vjp(const AdjArgs<real> &a, cudaStream_t st)
+{
+    switch (vjp_tile_rows(a.geo.nx, a.geo.ny)) {
+    case 32: return launch_vjp_rows<real, 32>(a, st);
+    case 16: return launch_vjp_rows<real, 16>(a, st);
+    default: return launch_vjp_rows<real, 8>(a, st);
+    }
 }
 
 template <typename real>

@@ -1060,8 +1060,11 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
             rr[2 * tid + 1] = sR[ql];
         }
         __syncthreads();
-        // parallel cyclic reduction of the 2S interface rows
-        for (int s = 1; s < N2; s <<= 1) {
+        // parallel cyclic reduction of the 2S interface rows until they fall
+        // into P independent systems (rows r, r + P, r + 2P, ...), which one
+        // thread each then solves by elimination (fewer levels and barriers)
+        const int P = N2 > 64 ? 32 : N2;
+        for (int s = 1; s < P; s <<= 1) {
             real na[2], nb[2], nc[2], nr[2];
 #pragma unroll
             for (int u = 0; u < 2; u++) {
@@ -1095,6 +1098,27 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
                 rb[e] = nb[u];
                 rc[e] = nc[u];
                 rr[e] = nr[u];
+            }
+            __syncthreads();
+        }
+        if (P < N2) {
+            if (tid < P) {
+                real cprev = real(0), rprev = real(0);
+                int e = tid;
+                for (; e < N2; e += P) {
+                    const real ae = ra[e];
+                    const real inv = real(1) / (rb[e] - ae * cprev);
+                    cprev = rc[e] * inv;
+                    rprev = (rr[e] - ae * rprev) * inv;
+                    rc[e] = cprev;
+                    rr[e] = rprev;
+                    rb[e] = real(1);
+                }
+                real x = rprev;
+                for (e -= 2 * P; e >= 0; e -= P) {
+                    x = rr[e] - rc[e] * x;
+                    rr[e] = x;
+                }
             }
             __syncthreads();
         }
