@@ -433,29 +433,42 @@ __global__ void k_adj_mask(AdjArgs<real> A)
 
 // Step 3: the history.  The increments of w, U* and V* weigh R^n, R^{n-1},
 // R^{n-2} by c0, c1, c2 and (U*, V*) the mixed terms F*, G* by e0, e1, e2.
+// One 32 x 32 tile per block of 32 x 8 threads; the y-lines' solution
+// (column-major) is read along its columns and transposed in shared memory.
 template <typename real>
 __global__ void k_adj_hist(AdjArgs<real> A)
 {
+    __shared__ real tq[32][33];
     const Geo &G = A.geo;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    const int k = j * G.nx + i;
-    const real mu = A.muX ? A.muX[(size_t)j * G.px + i] : A.ldU[k];
-    const real mv = A.muY ? A.muY[(size_t)i * G.py + j] : A.ldV[k];
-    const real m[5] = {A.lw[k], mu, mv, mu, mv};
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-        if (v >= 3 && !A.bsnq) break;
-        const real c0 = v < 3 ? A.c0 : A.e0, c1 = v < 3 ? A.c1 : A.e1, c2 = v < 3 ? A.c2 : A.e2;
-        A.G0[v][k] += c0 * m[v];
-        if (A.G1[v]) A.G1[v][k] += c1 * m[v];
-        if (A.G2[v]) A.G2[v][k] += c2 * m[v];
-        if (A.H0[v]) A.H0[v][k] = (v < 3 ? A.hc : A.he) * m[v];
+    const int tx = threadIdx.x, ty = threadIdx.y, bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    if (A.muY) {
+        for (int r = ty; r < 32; r += 8) {
+            const int i = bx + r, j = by + tx;
+            tq[r][tx] = i < G.nx && j < G.ny ? A.muY[(size_t)i * G.py + j] : real(0);
+        }
+        __syncthreads();
     }
-    if (A.accw) {
-        A.accw[k] += m[0];
-        A.accP[k] += A.lP[k];
-        A.accQ[k] += A.lQ[k];
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bx + tx, j = by + r;
+        if (i >= G.nx || j >= G.ny) continue;
+        const int k = j * G.nx + i;
+        const real mu = A.muX ? A.muX[(size_t)j * G.px + i] : A.ldU[k];
+        const real mv = A.muY ? tq[tx][r] : A.ldV[k];
+        const real m[5] = {A.lw[k], mu, mv, mu, mv};
+#pragma unroll
+        for (int v = 0; v < 5; v++) {
+            if (v >= 3 && !A.bsnq) break;
+            const real c0 = v < 3 ? A.c0 : A.e0, c1 = v < 3 ? A.c1 : A.e1, c2 = v < 3 ? A.c2 : A.e2;
+            A.G0[v][k] += c0 * m[v];
+            if (A.G1[v]) A.G1[v][k] += c1 * m[v];
+            if (A.G2[v]) A.G2[v][k] += c2 * m[v];
+            if (A.H0[v]) A.H0[v][k] = (v < 3 ? A.hc : A.he) * m[v];
+        }
+        if (A.accw) {
+            A.accw[k] += m[0];
+            A.accP[k] += A.lP[k];
+            A.accQ[k] += A.lQ[k];
+        }
     }
 }
 
@@ -715,10 +728,9 @@ constexpr int kVC = kVT + 5;         // corner window: x0 - 2 .. x0 + 34
 constexpr int kVCS = kVC + 1;
 constexpr int kVjpThreads = 256;
 
-template <typename real, int TY>
-struct TileAcc {
-    static constexpr int kWH = TY + 4;   // cell window rows: y0 - 2 .. y0 + TY + 1
-    static constexpr int kCH = TY + 5;   // corner window rows
+// The accumulator's pointers and tile position.
+template <typename real>
+struct TileData {
     real *sv[3], *sd, *sc;   // shared windows: lw, lP, lQ, ld, lBc
     real *gv[3], *gd, *gc;   // global arrays
     const real *xv[3], *xb;  // shared windows: the state as source2d gives it, the bed corners
@@ -727,31 +739,44 @@ struct TileAcc {
     int interior;            // the whole cell window lies inside the grid: no ghosts
     real *lg;                // ghost adjoints (NULL: not wanted)
     int tsel, npos;
+    int x0, y0, nx, pc;
+};
+
+// kInt: a tile whose window lies inside the grid, where every source is the
+// cell itself and every target lies in the shared windows (no mapping, no
+// bounds checks, no global fallback).
+template <typename real, int TY, bool kInt>
+struct TileAcc : TileData<real> {
+    using D = TileData<real>;
+    static constexpr int kWH = TY + 4;   // cell window rows: y0 - 2 .. y0 + TY + 1
+    static constexpr int kCH = TY + 5;   // corner window rows
     __device__ __forceinline__ void ghost(const Src<real> &s, int var, real v) const
     {
-        if (lg && v != real(0)) atomicAdd(lg + ghost_index(tsel, s.gs, s.gl, var, s.gp, npos), v);
+        if (D::lg && v != real(0)) atomicAdd(D::lg + ghost_index(D::tsel, s.gs, s.gl, var, s.gp, D::npos), v);
     }
-    int x0, y0, nx, pc;
     __device__ __forceinline__ real val(int i, int j, int v) const
     {
-        return xv[v][(j - y0 + 2) * kVWS + (i - x0 + 2)];
+        return D::xv[v][(j - D::y0 + 2) * kVWS + (i - D::x0 + 2)];
     }
     // where the adjoint of window cell (i, j) goes: the cell it is or
     // mirrors, with the signs, or a sine-maker ghost (no values)
     __device__ __forceinline__ Src<real> map(int i, int j) const
     {
         Src<real> s;
-        if (interior) {
+        if (kInt || D::interior) {
             s.sgn[0] = s.sgn[1] = s.sgn[2] = real(1);
             s.ci = i;
             s.cj = j;
-            s.idx = j * nx + i;
+            s.idx = 0;   // a cell (its index is not needed here)
         } else {
-            mirror2d(*G, sine, i, j, s);
+            mirror2d(*D::G, D::sine, i, j, s);
         }
         return s;
     }
-    __device__ __forceinline__ real bed(int ci, int cj) const { return xb[(cj - y0 + 2) * kVCS + (ci - x0 + 2)]; }
+    __device__ __forceinline__ real bed(int ci, int cj) const
+    {
+        return D::xb[(cj - D::y0 + 2) * kVCS + (ci - D::x0 + 2)];
+    }
     __device__ __forceinline__ real bbar(int i, int j) const
     {
         return cell_bbar(bed(i, j), bed(i + 1, j), bed(i, j + 1), bed(i + 1, j + 1));
@@ -759,25 +784,51 @@ struct TileAcc {
     __device__ __forceinline__ void cell(int var, int i, int j, real v) const
     {
         if (v == real(0)) return;
-        const int li = i - x0 + 2, lj = j - y0 + 2;
-        if (li >= 0 && li < kVW && lj >= 0 && lj < kWH) atomicAdd(sv[var] + lj * kVWS + li, v);
-        else atomicAdd(gv[var] + (size_t)j * nx + i, v);
+        const int li = i - D::x0 + 2, lj = j - D::y0 + 2;
+        if (kInt || (li >= 0 && li < kVW && lj >= 0 && lj < kWH)) atomicAdd(D::sv[var] + lj * kVWS + li, v);
+        else atomicAdd(D::gv[var] + (size_t)j * D::nx + i, v);
     }
     __device__ __forceinline__ void ring(int i, int j, real v) const
     {
         if (v == real(0)) return;
-        const int li = i - x0 + 2, lj = j - y0 + 2;
-        if (li >= 0 && li < kVW && lj >= 0 && lj < kWH) atomicAdd(sd + lj * kVWS + li, v);
-        else atomicAdd(gd + (size_t)(j + 1) * (nx + 2) + (i + 1), v);
+        const int li = i - D::x0 + 2, lj = j - D::y0 + 2;
+        if (kInt || (li >= 0 && li < kVW && lj >= 0 && lj < kWH)) atomicAdd(D::sd + lj * kVWS + li, v);
+        else atomicAdd(D::gd + (size_t)(j + 1) * (D::nx + 2) + (i + 1), v);
     }
     __device__ __forceinline__ void corner(int ci, int cj, real v) const
     {
         if (v == real(0)) return;
-        const int li = ci - x0 + 2, lj = cj - y0 + 2;
-        if (li >= 0 && li < kVC && lj >= 0 && lj < kCH) atomicAdd(sc + lj * kVCS + li, v);
-        else atomicAdd(gc + (size_t)(cj + 1) * pc + (ci + 1), v);
+        const int li = ci - D::x0 + 2, lj = cj - D::y0 + 2;
+        if (kInt || (li >= 0 && li < kVC && lj >= 0 && lj < kCH)) atomicAdd(D::sc + lj * kVCS + li, v);
+        else atomicAdd(D::gc + (size_t)(cj + 1) * D::pc + (ci + 1), v);
     }
 };
+
+// The tile's cells and faces.
+template <typename real, int TY, bool kInt>
+__device__ __forceinline__ void vjp_tile_work(const AdjArgs<real> &A, const TileData<real> &td, int tx, int ty)
+{
+    TileAcc<real, TY, kInt> acc;
+    static_cast<TileData<real> &>(acc) = td;
+    const Geo &G = A.geo;
+    const int x0 = td.x0, y0 = td.y0;
+    const int xe = min(x0 + kVT, G.nx), ye = min(y0 + TY, G.ny);
+    for (int j = y0 + ty; j < ye; j += kVjpThreads / 32) {
+        const int i = x0 + tx;
+        if (i < xe) {
+            cell_vjp(A, i, j, acc);
+            if (A.bsnq) disp_vjp(A, i, j, acc);
+        }
+    }
+    const int fe = xe + (xe == G.nx ? 1 : 0);
+    for (int j = y0 + ty; j < ye; j += kVjpThreads / 32)
+        for (int f = x0 + tx; f < fe; f += 32) face_vjp(A, 0, f, j, acc);
+    const int ge = ye + (ye == G.ny ? 1 : 0);
+    for (int gq = y0 + ty; gq < ge; gq += kVjpThreads / 32) {
+        const int i = x0 + tx;
+        if (i < xe) face_vjp(A, 1, gq, i, acc);
+    }
+}
 
 template <typename real, int TY>
 constexpr size_t vjp_smem_bytes()
@@ -786,18 +837,17 @@ constexpr size_t vjp_smem_bytes()
 }
 
 template <typename real, int TY>
-__global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__ AdjArgs<real> A)
+__global__ void __launch_bounds__(kVjpThreads, sizeof(real) == 4 ? 4 : 2) k_adj_vjp(const __grid_constant__ AdjArgs<real> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sm = reinterpret_cast<real *>(smem_raw);
     const Geo &G = A.geo;
-    using Acc = TileAcc<real, TY>;
-    constexpr int kWH = Acc::kWH, kCH = Acc::kCH;
+    constexpr int kWH = TY + 4, kCH = TY + 5;
     const int x0 = blockIdx.x * kVT, y0 = blockIdx.y * TY;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     constexpr int ntot = 4 * kWH * kVWS + kCH * kVCS;
     for (int k = tid; k < ntot; k += kVjpThreads) sm[k] = real(0);
-    Acc acc;
+    TileData<real> acc;
     for (int v = 0; v < 3; v++) acc.sv[v] = sm + v * kWH * kVWS;
     acc.sd = sm + 3 * kWH * kVWS;
     acc.sc = sm + 4 * kWH * kVWS;
@@ -834,22 +884,8 @@ __global__ void __launch_bounds__(kVjpThreads) k_adj_vjp(const __grid_constant__
     acc.nx = G.nx;
     acc.pc = G.pc;
     __syncthreads();
-    const int xe = min(x0 + kVT, G.nx), ye = min(y0 + TY, G.ny);
-    for (int j = y0 + ty; j < ye; j += kVjpThreads / 32) {
-        const int i = x0 + tx;
-        if (i < xe) {
-            cell_vjp(A, i, j, acc);
-            if (A.bsnq) disp_vjp(A, i, j, acc);
-        }
-    }
-    const int fe = xe + (xe == G.nx ? 1 : 0);
-    for (int j = y0 + ty; j < ye; j += kVjpThreads / 32)
-        for (int f = x0 + tx; f < fe; f += 32) face_vjp(A, 0, f, j, acc);
-    const int ge = ye + (ye == G.ny ? 1 : 0);
-    for (int gq = y0 + ty; gq < ge; gq += kVjpThreads / 32) {
-        const int i = x0 + tx;
-        if (i < xe) face_vjp(A, 1, gq, i, acc);
-    }
+    if (acc.interior) vjp_tile_work<real, TY, true>(A, acc, tx, ty);
+    else vjp_tile_work<real, TY, false>(A, acc, tx, ty);
     __syncthreads();
     for (int k = tid; k < kVW * kWH; k += kVjpThreads) {
         const int li = k % kVW, lj = k / kVW, i = x0 - 2 + li, j = y0 - 2 + lj, o = lj * kVWS + li;
@@ -1057,7 +1093,7 @@ cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st)
 template <typename real>
 cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st)
 {
-    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
+    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 31) / 32);
     k_adj_hist<real><<<g, b, 0, st>>>(a);
     return cudaGetLastError();
 }
