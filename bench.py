@@ -347,13 +347,15 @@ def run_ensemble(args):
 
 def run_adjoint(args):
     """Cost of the discrete adjoint on the hump-on-beach workload (512^2, or
-    2048^2 for adjoint2048; Boussinesq, K = 1, 16 gauges, checkpoints every
-    100 steps): the time of
-    the gauge-misfit gradients with respect to the initial w and the bed
-    (forward with checkpoints, recomputation, reverse) against the time of
-    the forward steps alone, both with CUDA events on the solver's stream;
-    --steps is the run length.  The observations are the gauges of a target
-    run from a perturbed hump over a perturbed bed."""
+    2048^2 for adjoint2048; Boussinesq, K = 1, 16 gauges): the time of the
+    gauge-misfit gradients with respect to the initial w and the bed
+    (forward, reverse, and the recomputation where checkpoints are used)
+    against the time of the forward steps alone, both with CUDA events on
+    the solver's stream; --steps is the run length.  Every step of the
+    forward run is kept where that takes at most half the free device memory
+    (ckpt_every 0), else checkpoints every 100 steps; the scratch is
+    allocated before the timed region.  The observations are the gauges of
+    a target run from a perturbed hump over a perturbed bed."""
     import torch
 
     from paper_1611_05984_gb300 import celeris
@@ -370,6 +372,10 @@ def run_adjoint(args):
     obs = torch.as_tensor(t.read_gauges(args.steps)).to(device="cuda", dtype=dtype)
     t.close()
     g.step(args.warmup)
+    free, _ = torch.cuda.mem_get_info()
+    ckpt = 0 if celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), 0, bed=True) <= free // 2 else 100
+    scratch = torch.empty(celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), ckpt, bed=True),
+                          dtype=torch.uint8, device="cuda")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     g.set_state(*s.initial_state())
     torch.cuda.synchronize()
@@ -380,7 +386,8 @@ def run_adjoint(args):
     g.set_state(*s.initial_state())
     torch.cuda.synchronize()
     ev[2].record(stream)
-    loss, eta, grad, grad_z = celeris.gauge_misfit_gradient(g, args.steps, gauges, obs, ckpt_every=100, bed=True)
+    loss, eta, grad, grad_z = celeris.gauge_misfit_gradient(g, args.steps, gauges, obs, ckpt_every=ckpt, bed=True,
+                                                            scratch=scratch)
     ev[3].record(stream)
     torch.cuda.synchronize()
     fwd, adj = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
@@ -389,7 +396,7 @@ def run_adjoint(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic",
             "config": {"workload": s.name, "nx": s.nx, "ny": s.ny, "corrector_iters": s.K, "gauges": len(gauges),
-                       "ckpt_every": 100},
+                       "ckpt_every": ckpt, "scratch_gb": scratch.numel() / 1e9},
             "forward_ms_per_step": fwd / args.steps, "loss": loss,
             "grad_finite": bool(torch.isfinite(grad).all().item() and torch.isfinite(grad_z).all().item()),
             "grad_w_norm": float(torch.linalg.norm(grad.double()).item()),

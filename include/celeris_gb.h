@@ -232,7 +232,11 @@ cel_status cel_render(cel_solver *s, const cel_render_params *params, void *rgba
  * (cel_set_state just before); it runs N steps forward keeping a checkpoint
  * every ckpt_every steps, then the reverse sweep, recomputing one segment of
  * states at a time from its checkpoint; it ends holding the state after
- * step N.
+ * step N.  ckpt_every = 0 keeps every step's states, corrector iterates and
+ * line right sides from the forward run instead, with no recomputation
+ * (the scratch then grows with N: 3 (K + 1) values per cell and step, plus
+ * 2 (K + 1) with the bed on the Boussinesq model); a negative ckpt_every is
+ * CEL_ERR_INVALID_ARG.
  *
  * gij_host: ngauges (i, j) pairs; obs_dev: [N][ngauges] real, device;
  * scratch_dev: cel_adjoint_bytes(..., with_bed = grad_z_dev != NULL) bytes

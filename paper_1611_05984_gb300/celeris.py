@@ -453,26 +453,43 @@ class Ensemble:
             pass
 
 
+def adjoint_scratch_bytes(solver: "Solver", nsteps: int, ngauges: int, ckpt_every: int = 100,
+                          bed: bool = False) -> int:
+    """Bytes of the scratch tensor gauge_misfit_gradient needs (the
+    cel_adjoint_bytes figure plus 256 for alignment)."""
+    nb = ctypes.c_size_t()
+    solver._check(solver.L.cel_adjoint_bytes(solver._h, nsteps, ckpt_every, ngauges, int(bed), ctypes.byref(nb)),
+                  "adjoint_bytes")
+    return nb.value + 256
+
+
 def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every: int = 100, bed: bool = False,
-                          poison: bool = False):
+                          poison: bool = False, scratch=None):
     """Run nsteps from the solver's present (freshly set) state and return
     (L, eta, dL/dw0), plus dL/dz when bed is set: the gauge misfit
     L = 1/2 sum (eta - obs)^2 over steps 1..nsteps, the recorded eta
     ([nsteps, ngauges] tensor) and its gradients with respect to w at the
     start and to the cell-centre bed ([ny, nx] tensors), by the discrete
-    adjoint (cel_adjoint_gauge_misfit).  obs: [nsteps, ngauges].  poison:
-    fill the scratch with 0xFF bytes first (a test aid, as for Solver)."""
+    adjoint (cel_adjoint_gauge_misfit).  obs: [nsteps, ngauges].
+    ckpt_every: checkpoint spacing of the recomputation; 0 keeps every step
+    of the forward run instead (no recomputation; the scratch grows with
+    nsteps).  scratch: a uint8 CUDA tensor of at least
+    adjoint_scratch_bytes(...) bytes to use (else one is allocated).
+    poison: fill the scratch with 0xFF bytes first (a test aid, as for
+    Solver)."""
     torch = solver.torch
     ij = np.ascontiguousarray(np.asarray(gauges, dtype=np.int32).reshape(-1, 2))
     ng = len(ij)
     obs_t = torch.as_tensor(obs).to(device=solver.device, dtype=solver.dtype).contiguous()
     if tuple(obs_t.shape) != (nsteps, ng):
         raise ValueError("obs must be [nsteps, ngauges]")
-    nb = ctypes.c_size_t()
-    solver._check(solver.L.cel_adjoint_bytes(solver._h, nsteps, ckpt_every, ng, int(bed), ctypes.byref(nb)),
-                  "adjoint_bytes")
+    need = adjoint_scratch_bytes(solver, nsteps, ng, ckpt_every, bed)
+    nb = ctypes.c_size_t(need - 256)
     with torch.cuda.device(solver.device):
-        scratch = torch.empty(nb.value + 256, dtype=torch.uint8, device=solver.device)
+        if scratch is None:
+            scratch = torch.empty(need, dtype=torch.uint8, device=solver.device)
+        elif scratch.dtype != torch.uint8 or not scratch.is_cuda or scratch.numel() < need:
+            raise ValueError(f"scratch must be a uint8 CUDA tensor of at least {need} bytes")
         if poison:
             scratch.fill_(255)
         eta = torch.empty((nsteps, ng), dtype=solver.dtype, device=solver.device)

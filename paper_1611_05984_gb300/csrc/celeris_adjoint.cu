@@ -400,75 +400,82 @@ __device__ __forceinline__ size_t corner_index(const Geo &G, int ci, int cj)
     return (size_t)(cj + 1) * G.pc + (ci + 1);
 }
 
-// Step 1 of the reverse for one cell: the masks; the state's own path
-// (w^{n+1} = w^n + ...) passes the masked adjoint on unchanged.
+// Step 1 of the reverse: the masks; the state's own path (w^{n+1} = w^n +
+// ...) passes the masked adjoint on unchanged.  One 32 x 32 tile per block
+// of 32 x 32 threads, a cell per thread; the y-lines' right side
+// (column-major) is transposed in shared memory and written along columns.
 template <typename real>
-__global__ void k_adj_mask(AdjArgs<real> A)
+__global__ void __launch_bounds__(1024) k_adj_mask(AdjArgs<real> A)
 {
+    __shared__ real tq[32][33];
     const Geo &G = A.geo;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    const int k = j * G.nx + i;
-    const real Bb = bbar_at(A.Bc, G, i, j);
-    const real ws = A.c.ws;
-    const real d = fmax(ws - Bb, real(0));
-    const real gam = A.final_stage ? sponge_gamma<real>(A.c, G, i, j) : real(1);
-    const real wn = A.w_next[k];
-    const bool dry = wn - Bb <= real(0);
-    const bool spw = gam < real(1) && d > real(0);
-    const real w1 = spw ? ws + (wn - ws) / gam : wn;   // before the sponge
-    const real tol = (sizeof(real) == 8 ? real(1e-12) : real(1e-6)) * fmax(real(1), fabs(Bb));
-    const bool clamped = w1 - Bb <= tol;
-    if (clamped && A.lBb) A.lBb[ring_index(G, i, j)] += A.lw[k] * (spw ? gam : real(1));   // w = Bbar there
-    A.lw[k] = clamped ? real(0) : A.lw[k] * (spw ? gam : real(1));
-    const real lp = dry ? real(0) : A.lP[k] * gam, lq = dry ? real(0) : A.lQ[k] * gam;
-    A.lP[k] = lp;
-    A.lQ[k] = lq;
-    if (A.packX) {
-        A.packX[(size_t)j * G.px + i] = lp;
-        A.packY[(size_t)i * G.py + j] = lq;
+    const int tx = threadIdx.x, ty = threadIdx.y, bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const int i = bx + tx, j = by + ty;
+    real lq = real(0);
+    if (i < G.nx && j < G.ny) {
+        const int k = j * G.nx + i;
+        const real Bb = bbar_at(A.Bc, G, i, j);
+        const real ws = A.c.ws;
+        const real d = fmax(ws - Bb, real(0));
+        const real gam = A.final_stage ? sponge_gamma<real>(A.c, G, i, j) : real(1);
+        const real wn = A.w_next[k];
+        const bool dry = wn - Bb <= real(0);
+        const bool spw = gam < real(1) && d > real(0);
+        const real w1 = spw ? ws + (wn - ws) / gam : wn;   // before the sponge
+        const real tol = (sizeof(real) == 8 ? real(1e-12) : real(1e-6)) * fmax(real(1), fabs(Bb));
+        const bool clamped = w1 - Bb <= tol;
+        if (clamped && A.lBb) A.lBb[ring_index(G, i, j)] += A.lw[k] * (spw ? gam : real(1));   // w = Bbar there
+        A.lw[k] = clamped ? real(0) : A.lw[k] * (spw ? gam : real(1));
+        const real lp = dry ? real(0) : A.lP[k] * gam;
+        lq = dry ? real(0) : A.lQ[k] * gam;
+        A.lP[k] = lp;
+        A.lQ[k] = lq;
+        if (A.packX) A.packX[(size_t)j * G.px + i] = lp;
+        if (A.zero[0]) A.zero[0][k] = A.zero[1][k] = A.zero[2][k] = real(0);
     }
-    if (A.zero[0]) A.zero[0][k] = A.zero[1][k] = A.zero[2][k] = real(0);
+    if (A.packX) {
+        tq[ty][tx] = lq;
+        __syncthreads();
+        const int ic = bx + ty, jc = by + tx;
+        if (ic < G.nx && jc < G.ny) A.packY[(size_t)ic * G.py + jc] = tq[tx][ty];
+    }
 }
 
 // Step 3: the history.  The increments of w, U* and V* weigh R^n, R^{n-1},
 // R^{n-2} by c0, c1, c2 and (U*, V*) the mixed terms F*, G* by e0, e1, e2.
-// One 32 x 32 tile per block of 32 x 8 threads; the y-lines' solution
-// (column-major) is read along its columns and transposed in shared memory.
+// One 32 x 32 tile per block of 32 x 32 threads, a cell per thread; the
+// y-lines' solution (column-major) is read along its columns and transposed
+// in shared memory.
 template <typename real>
-__global__ void k_adj_hist(AdjArgs<real> A)
+__global__ void __launch_bounds__(1024) k_adj_hist(AdjArgs<real> A)
 {
     __shared__ real tq[32][33];
     const Geo &G = A.geo;
     const int tx = threadIdx.x, ty = threadIdx.y, bx = blockIdx.x * 32, by = blockIdx.y * 32;
     if (A.muY) {
-        for (int r = ty; r < 32; r += 8) {
-            const int i = bx + r, j = by + tx;
-            tq[r][tx] = i < G.nx && j < G.ny ? A.muY[(size_t)i * G.py + j] : real(0);
-        }
+        const int i = bx + ty, j = by + tx;
+        tq[ty][tx] = i < G.nx && j < G.ny ? A.muY[(size_t)i * G.py + j] : real(0);
         __syncthreads();
     }
-    for (int r = ty; r < 32; r += 8) {
-        const int i = bx + tx, j = by + r;
-        if (i >= G.nx || j >= G.ny) continue;
-        const int k = j * G.nx + i;
-        const real mu = A.muX ? A.muX[(size_t)j * G.px + i] : A.ldU[k];
-        const real mv = A.muY ? tq[tx][r] : A.ldV[k];
-        const real m[5] = {A.lw[k], mu, mv, mu, mv};
+    const int i = bx + tx, j = by + ty;
+    if (i >= G.nx || j >= G.ny) return;
+    const int k = j * G.nx + i;
+    const real mu = A.muX ? A.muX[(size_t)j * G.px + i] : A.ldU[k];
+    const real mv = A.muY ? tq[tx][ty] : A.ldV[k];
+    const real m[5] = {A.lw[k], mu, mv, mu, mv};
 #pragma unroll
-        for (int v = 0; v < 5; v++) {
-            if (v >= 3 && !A.bsnq) break;
-            const real c0 = v < 3 ? A.c0 : A.e0, c1 = v < 3 ? A.c1 : A.e1, c2 = v < 3 ? A.c2 : A.e2;
-            A.G0[v][k] += c0 * m[v];
-            if (A.G1[v]) A.G1[v][k] += c1 * m[v];
-            if (A.G2[v]) A.G2[v][k] += c2 * m[v];
-            if (A.H0[v]) A.H0[v][k] = (v < 3 ? A.hc : A.he) * m[v];
-        }
-        if (A.accw) {
-            A.accw[k] += m[0];
-            A.accP[k] += A.lP[k];
-            A.accQ[k] += A.lQ[k];
-        }
+    for (int v = 0; v < 5; v++) {
+        if (v >= 3 && !A.bsnq) break;
+        const real c0 = v < 3 ? A.c0 : A.e0, c1 = v < 3 ? A.c1 : A.e1, c2 = v < 3 ? A.c2 : A.e2;
+        A.G0[v][k] += c0 * m[v];
+        if (A.G1[v]) A.G1[v][k] += c1 * m[v];
+        if (A.G2[v]) A.G2[v][k] += c2 * m[v];
+        if (A.H0[v]) A.H0[v][k] = (v < 3 ? A.hc : A.he) * m[v];
+    }
+    if (A.accw) {
+        A.accw[k] += m[0];
+        A.accP[k] += A.lP[k];
+        A.accQ[k] += A.lQ[k];
     }
 }
 
@@ -1085,7 +1092,7 @@ __global__ void k_adj_misfit(AdjArgs<real> A, const int32_t *gij, int ng, const 
 template <typename real>
 cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st)
 {
-    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 7) / 8);
+    dim3 b(32, 32), g((a.geo.nx + 31) / 32, (a.geo.ny + 31) / 32);
     k_adj_mask<real><<<g, b, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -1093,7 +1100,7 @@ cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st)
 template <typename real>
 cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st)
 {
-    dim3 b(32, 8), g((a.geo.nx + 31) / 32, (a.geo.ny + 31) / 32);
+    dim3 b(32, 32), g((a.geo.nx + 31) / 32, (a.geo.ny + 31) / 32);
     k_adj_hist<real><<<g, b, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -1593,12 +1593,16 @@ struct AdjLayout {
     size_t rhs, xs, lBc, lBb, ld, ldl, lg;   // the bed's gradient (bed != 0)
     size_t ghost_bytes;
     int nseg, bed;
+    int keep;   // every step kept from the forward run: one segment, one slot, no recomputation
 };
 
 AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
 {
     AdjLayout L;
     L.bed = bed;
+    L.keep = C == 0;
+    if (L.keep) C = N;
+    const int slots = L.keep ? 1 : 2;
     L.ckpt_bytes = align256(ckpt_total(s));
     L.cells_bytes = align256((size_t)s->grid.nx * s->grid.ny * s->es);
     L.line_bytes = align256(std::max((size_t)s->geo.ny * s->geo.px, (size_t)s->geo.nx * s->geo.py) * s->es);
@@ -1612,9 +1616,9 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
     L.ckpt = take(L.ckpt_bytes * (size_t)(L.nseg + 1));   // + the final state
     const int K = s->params.corrector_iters;
     L.seg_slot = L.cells_bytes * 3 * (size_t)(C + 1);
-    L.seg = take(L.seg_slot * 2);
+    L.seg = take(L.seg_slot * slots);
     L.iter_slot = L.cells_bytes * 3 * (size_t)K * (size_t)(C + 1);   // the iterates of every step
-    L.iter = take(L.iter_slot * 2);
+    L.iter = take(L.iter_slot * slots);
     L.lam = take(L.cells_bytes * 9);   // 3 sets of (w, P, Q)
     L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
@@ -1627,7 +1631,7 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
     if (bed) {
         const bool lines = s->params.model == CEL_BSNQ;
         L.rhs_slot = lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0;   // every stage's right sides
-        L.rhs = take(L.rhs_slot * 2);
+        L.rhs = take(L.rhs_slot * slots);
         L.xs = take(lines ? L.line_bytes * 2 : 0);                                  // and their solutions
         L.ldl = take(lines ? L.line_bytes * 2 : 0);                                 // ld of the line systems
         L.lBc = take((size_t)s->geo.pc * (s->grid.ny + 3) * s->es);
@@ -1665,6 +1669,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                      const AdjLayout &L, real *eta_out, real *grad, real *grad_z, double *loss)
 {
     cudaStream_t st = s->stream;
+    if (L.keep) C = N;
     const size_t cells = (size_t)s->grid.nx * s->grid.ny;
     int32_t *gij = reinterpret_cast<int32_t *>(scr + L.gij);
     real *rec = reinterpret_cast<real *>(scr + L.rec);
@@ -1697,12 +1702,36 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         ~Range() { nvtxRangePop(); }
     };
     Range whole("cel adjoint");
+    // the state before step k of a segment, into slot sl
+    auto keep_state = [&](int sl, int k, cudaStream_t q) {
+        return launch_get_state<real>(s->geo, s->at<real>(s->lay.w[s->cur]), s->at<real>(s->lay.P[s->pcur]),
+                                      s->at<real>(s->lay.Qc[s->pcur]), segf_in(sl, k, 0), segf_in(sl, k, 1),
+                                      segf_in(sl, k, 2), q);
+    };
+    // one step, its corrector iterates and line right sides kept in slot sl
+    auto kept_step = [&](int sl, int k) -> cel_status {
+        s->capture = K > 0 ? reinterpret_cast<unsigned char *>(iterf_in(sl, k, 0, 0)) : nullptr;
+        s->capture_field = L.cells_bytes;
+        s->capture_rhs = bed_lines ? rhsf_in(sl, k, 0) : nullptr;
+        s->capture_line = L.line_bytes;
+        const cel_status r = step_t<real>(s, 1);
+        s->capture = nullptr;
+        s->capture_rhs = nullptr;
+        return r;
+    };
     for (int n = 0; n < N; n++) {
         if (n % C == 0 && (stt = cel_save_checkpoint(s, ckpt(n / C), L.ckpt_bytes)) != CEL_OK) return stt;
-        if ((stt = step_t<real>(s, 1)) != CEL_OK) return stt;
+        if (L.keep) {   // the forward run keeps what the reverse reads
+            CEL_CUDA(s, keep_state(0, n, st), "adjoint states");
+            stt = kept_step(0, n);
+        } else {
+            stt = step_t<real>(s, 1);
+        }
+        if (stt != CEL_OK) return stt;
         CEL_CUDA(s, launch_gauges<real>(s->geo, s->phy, s->at<real>(s->lay.w[s->cur]), gij, ng, rec + (size_t)n * ng, st),
                  "adjoint gauges");
     }
+    if (L.keep) CEL_CUDA(s, keep_state(0, N, st), "adjoint states");
     if ((stt = cel_save_checkpoint(s, ckpt(L.nseg), L.ckpt_bytes)) != CEL_OK) return stt;
     {
         std::vector<real> r((size_t)N * ng), o((size_t)N * ng);
@@ -1895,26 +1924,19 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     // recompute segment sg into slot sg & 1 on the solver's stream, once the
     // reverse of the segment that held the slot is done
     auto recompute = [&](int sg) -> cel_status {
+        const int sl = sg & 1;
+        if (L.keep) {   // kept by the forward run, which precedes on the solver's stream
+            CEL_CUDA(s, cudaEventRecord(ss.rec[sl], fst), "adjoint order");
+            return CEL_OK;
+        }
         Range r_("cel adjoint recompute");
-        const int sl = sg & 1, n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
+        const int n0 = sg * C, n1 = n0 + C < N ? n0 + C : N;
         if (used[sl]) CEL_CUDA(s, cudaStreamWaitEvent(fst, ss.rev[sl], 0), "adjoint order");
         cel_status r = cel_load_checkpoint(s, ckpt(sg), L.ckpt_bytes);
         if (r != CEL_OK) return r;
         for (int k = 0; k <= n1 - n0; k++) {
-            CEL_CUDA(s, launch_get_state<real>(s->geo, s->at<real>(s->lay.w[s->cur]), s->at<real>(s->lay.P[s->pcur]),
-                                               s->at<real>(s->lay.Qc[s->pcur]), segf_in(sl, k, 0), segf_in(sl, k, 1),
-                                               segf_in(sl, k, 2), fst),
-                     "adjoint states");
-            if (k < n1 - n0) {
-                s->capture = K > 0 ? reinterpret_cast<unsigned char *>(iterf_in(sl, k, 0, 0)) : nullptr;
-                s->capture_field = L.cells_bytes;
-                s->capture_rhs = bed_lines ? rhsf_in(sl, k, 0) : nullptr;
-                s->capture_line = L.line_bytes;
-                r = step_t<real>(s, 1);
-                s->capture = nullptr;
-                s->capture_rhs = nullptr;
-                if (r != CEL_OK) return r;
-            }
+            CEL_CUDA(s, keep_state(sl, k, fst), "adjoint states");
+            if (k < n1 - n0 && (r = kept_step(sl, k)) != CEL_OK) return r;
         }
         CEL_CUDA(s, cudaEventRecord(ss.rec[sl], fst), "adjoint order");
         used[sl] = true;
@@ -2049,8 +2071,8 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
 
 cel_status adjoint_check(const cel_solver *, int N, int C, int ng, std::string &why)
 {
-    if (N < 1 || C < 1 || ng < 1) {
-        why = "nsteps, ckpt_every and the gauge count must be positive";
+    if (N < 1 || C < 0 || ng < 1) {
+        why = "nsteps and the gauge count must be positive, ckpt_every positive or 0";
         return CEL_ERR_INVALID_ARG;
     }
     return CEL_OK;

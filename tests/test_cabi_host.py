@@ -97,7 +97,8 @@ def test_ensemble_rejects_empty_member_lists_without_gpu_work():
 
 def test_adjoint_entry_points_reject_bad_arguments_without_gpu_work():
     """The adjoint's calls validate on the host before any device work: a
-    NULL solver, non-positive step, checkpoint or gauge counts, and the
+    NULL solver, non-positive step or gauge counts, a negative checkpoint
+    spacing, and the
     face self-check's element size and counts."""
     L = celeris.load()
     nb = ctypes.c_size_t()

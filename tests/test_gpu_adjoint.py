@@ -142,10 +142,12 @@ def test_adjoint_checkpoint_spacing_and_fp32():
     _, _, g7, _ = _gpu_gradient(s, gauges, obs, ckpt=7)
     _, _, g40, _ = _gpu_gradient(s, gauges, obs, ckpt=40)
     _, _, g1, _ = _gpu_gradient(s, gauges, obs, ckpt=1)
+    _, _, g0, _ = _gpu_gradient(s, gauges, obs, ckpt=0)   # every step kept, no recomputation
     n = np.linalg.norm(g40)
     assert n > 0
     assert np.linalg.norm(g7 - g40) <= 1e-10 * n
     assert np.linalg.norm(g1 - g40) <= 1e-10 * n
+    assert np.linalg.norm(g0 - g40) <= 1e-10 * n
     # FP32 against FP64 where the branches are robust (on the beach the
     # hump's exponential tail flushes to zero in FP32 and sits on another,
     # equally valid branch of the limiter's kink)
@@ -377,6 +379,9 @@ def test_adjoint_corrector_beach_with_dry_land():
     _, _, g30, _, z30 = _gpu_gradient(s, gauges, obs, ckpt=30, bed=True)
     assert np.linalg.norm(g4 - g30) <= 1e-10 * np.linalg.norm(g30)
     assert np.linalg.norm(z4 - z30) <= 1e-10 * np.linalg.norm(z30)
+    _, _, g0, _, z0 = _gpu_gradient(s, gauges, obs, ckpt=0, bed=True)   # every step kept
+    assert np.linalg.norm(g0 - g30) <= 1e-10 * np.linalg.norm(g30)
+    assert np.linalg.norm(z0 - z30) <= 1e-10 * np.linalg.norm(z30)
     land = z > 0.5
     assert np.any(land) and np.all(g4[land] == 0.0) and np.all(z4[land] == 0.0)
     assert np.linalg.norm(g4) > 0 and np.all(np.isfinite(z4)) and np.linalg.norm(z4) > 0
