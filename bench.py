@@ -352,7 +352,7 @@ def run_adjoint(args):
     (forward, reverse, and the recomputation where checkpoints are used)
     against the time of the forward steps alone, both with CUDA events on
     the solver's stream; --steps is the run length.  Every step of the
-    forward run is kept where that takes at most half the free device memory
+    forward run is kept where that takes at most 70 % of the free device memory
     (ckpt_every 0), else checkpoints every 100 steps; the scratch is
     allocated before the timed region.  The observations are the gauges of
     a target run from a perturbed hump over a perturbed bed."""
@@ -373,7 +373,7 @@ def run_adjoint(args):
     t.close()
     g.step(args.warmup)
     free, _ = torch.cuda.mem_get_info()
-    ckpt = 0 if celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), 0, bed=True) <= free // 2 else 100
+    ckpt = 0 if celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), 0, bed=True) <= 0.7 * free else 100
     scratch = torch.empty(celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), ckpt, bed=True),
                           dtype=torch.uint8, device="cuda")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
