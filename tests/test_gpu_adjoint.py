@@ -355,6 +355,56 @@ def test_bed_gradient_vertical_shift_identity_with_dry_land():
     assert np.all(gz[land] == 0.0) and np.linalg.norm(gz) > 0
 
 
+def test_shift_identity_on_a_grid_of_16_row_tiles():
+    """The same identity on a 1024 x 512 grid, large enough that the
+    Jacobian pass takes its 32 x 16 tiles (the smaller grids above take
+    32 x 8): a gentle beach with dry land, humps across the water and 40
+    gauges spread over it, so that interior and boundary tiles of both
+    kinds carry adjoints."""
+    from paper_1611_05984_gb300 import scenarios as sc
+    nx, ny, dx = 1024, 512, 0.5
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
+    z = -0.5 + 1.5 * np.maximum(0.0, (X - 300.0) / 150.0)
+    dt = 0.1 * dx / math.sqrt(9.81 * 0.5)
+    s = sc.flat_basin(nx, ny, dx, 0.5, dt, model=1, K=1, friction=2, fcoef=0.02, eps=1e-8)
+    s.z = z
+    rng = np.random.default_rng(21)
+    hump = np.zeros_like(X)
+    for _ in range(12):
+        x0, y0 = rng.uniform(5.0, 345.0), rng.uniform(5.0, 250.0)
+        hump += 0.05 * np.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / 6.0)
+    s.w0 = np.maximum(z, hump)
+    s.steps = 30
+    gauges = [(int(rng.integers(2, 700)), int(rng.integers(2, ny - 2))) for _ in range(40)]
+    obs = 0.005 * rng.standard_normal((s.steps, len(gauges)))
+    loss, eta, gw, g, gz = _gpu_gradient(s, gauges, obs, ckpt=0, bed=True)
+    bed = g.field("Bbar").double().cpu().numpy()
+    wet = s.w0 > bed
+    want = float(np.sum(eta - obs))
+    assert abs(float(np.sum(gw[wet]) + np.sum(gz)) - want) <= 1e-9 * np.sum(np.abs(eta - obs))
+    assert np.count_nonzero(gw) > 40 * 100 and np.all(np.isfinite(gz))
+
+
+def test_caller_scratch():
+    """A caller-owned scratch tensor gives the gradients of an allocated
+    one; a scratch below adjoint_scratch_bytes is refused before any work."""
+    from paper_1611_05984_gb300 import celeris
+    s, gauges = _scenario(nsteps=12)
+    obs = torch.zeros((s.steps, len(gauges)), dtype=torch.float64)
+    g1 = celeris.from_scenario(s, dtype=torch.float64)
+    need = celeris.adjoint_scratch_bytes(g1, s.steps, len(gauges), 4, bed=True)
+    scratch = torch.empty(need + 4096, dtype=torch.uint8, device="cuda")
+    _, _, a_w, a_z = celeris.gauge_misfit_gradient(g1, s.steps, gauges, obs, 4, bed=True, scratch=scratch)
+    g2 = celeris.from_scenario(s, dtype=torch.float64)
+    _, _, b_w, b_z = celeris.gauge_misfit_gradient(g2, s.steps, gauges, obs, 4, bed=True)
+    assert torch.linalg.norm(a_w - b_w) <= 1e-12 * torch.linalg.norm(b_w)
+    assert torch.linalg.norm(a_z - b_z) <= 1e-12 * torch.linalg.norm(b_z)
+    g3 = celeris.from_scenario(s, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        celeris.gauge_misfit_gradient(g3, s.steps, gauges, obs, 4, bed=True,
+                                      scratch=torch.empty(need - 1, dtype=torch.uint8, device="cuda"))
+
+
 def test_adjoint_corrector_beach_with_dry_land():
     """K = 1 Boussinesq on a beach with dry land (dx = 0.5 m, depth/dx <=
     1): loss and records equal the oracle's, checkpoint spacing changes
