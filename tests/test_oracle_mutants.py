@@ -32,6 +32,10 @@ MUTANTS = [
      "(9.0 * o->Fc[c] + 18.0 * o->F[0][c] - 5.0 * o->F[1][c] + o->F[2][c])",
      "test_time_stepping_formulas_step_by_step"),
     ("wall_no_negate", "P[gc] = -P[sc];", "P[gc] = P[sc];", "test_mass_soliton_channel"),
+    ("sine_discharge_sign", "*Pg += c * cs * em;", "*Pg -= c * cs * em;", "test_sine_maker_progressive_wave"),
+    ("sine_celerity", "orc_real c = om / k;", "orc_real c = k / om;", "test_sine_maker_progressive_wave"),
+    ("desing_sqrt2", "return sqrt(2.0) * h / sqrt(h4 + fmax(h4, eps));", "return h / sqrt(h4 + fmax(h4, eps));",
+     "test_soliton_speed"),
     ("eq23_sign_s", "*a = s - r;", "*a = -s - r;", "test_symmetry_mirror_x"),
     ("tridiag_B", "*b = 1.0 + 2.0 * r;", "*b = 1.0 + r;", "test_dispersion_relation_1d"),
     ("hydrostatic_half", "FL1 = qnL * uL + 0.5 * g * hL * hL", "FL1 = qnL * uL + g * hL * hL",

@@ -16,6 +16,7 @@ an invariant, a textbook routine, a special case or a convergence order.
   dispersion terms, tridiagonal, F*, G*   linear dispersion relation test_dispersion_*
   ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
   soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36)  test_soliton_*
+  sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
   friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders   test_friction_*
   AB3 stability (Sec. 2.3)                real-axis bound -6/11     test_stability_*
 """
@@ -298,6 +299,50 @@ def test_friction_manning_ode(oracle_mod):
     ref = sol.y[0, -1]
     P, _ = _uniform_friction_error(oracle_mod, 0.002, f=n_m, P0=P0, h=h, T=T, kind=2)
     assert P == pytest.approx(ref, rel=1e-5)
+
+
+# ------------------------------------------------------------ sine maker
+
+def test_sine_maker_progressive_wave(oracle_mod):
+    """Eq. 25-29 at the west end of a channel with a sponge at the east end
+    (Boussinesq, K = 1, a/d = 0.005): what the maker sends in is a wave
+    travelling east, which mass conservation ties to P = c eta with c = w/k
+    of the model's own linear dispersion relation
+    c^2 = g d (1 + B (kd)^2) / (1 + (B + 1/3)(kd)^2) (Sec. 2.1); P in phase
+    with eta (a wave leaving the maker); an amplitude within 5 % of a (the
+    ghosts carry a and Eckart's c, within a few % of the model's)."""
+    from scipy.optimize import brentq
+    d, a, T, dx, ny = 1.0, 0.005, 4.0, 0.1, 2
+    w0 = 2 * math.pi / T
+    L = 2 * math.pi / oracle_mod.eckart_k(w0, d, G)
+    nx, sponge = int(round(6 * L / dx)), int(round(2 * L / dx))
+    z = np.full((ny, nx), -d)
+    dt = 0.2 * dx / math.sqrt(G * d)
+    o = oracle_mod.Oracle(z, dx, dx, dt, K=1)
+    o.set_boundary(oracle_mod.W, oracle_mod.SINE, 0, ((a, T, 0.0, 0.0),))
+    o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, sponge)
+    o.set_state(0 * z, 0 * z, 0 * z)
+    n_total, n_fit = int(round(7 * T / dt)), int(round(2 * T / dt))
+    o.step(n_total - n_fit)
+    gi = [int(round(f * L / dx)) for f in (0.5, 1.0, 1.5, 2.0)]
+    t, eta, P = [], [], []
+    for n in range(n_fit):
+        o.step(1)
+        w, p, _ = o.state()
+        t.append((n_total - n_fit + n + 1) * dt)
+        eta.append(w[0, gi])
+        P.append(p[0, gi])
+    t = np.array(t)
+    A = np.stack([np.cos(w0 * t), np.sin(w0 * t), np.ones_like(t)], 1)
+    ce = np.linalg.lstsq(A, np.array(eta), rcond=None)[0]
+    cp = np.linalg.lstsq(A, np.array(P), rcond=None)[0]
+    amp_eta, amp_P = np.hypot(ce[0], ce[1]), np.hypot(cp[0], cp[1])
+    lag = np.angle(np.exp(1j * (np.arctan2(cp[1], cp[0]) - np.arctan2(ce[1], ce[0]))))
+    km = brentq(lambda k: w0 ** 2 - G * d * k ** 2 * (1 + B * (k * d) ** 2) / (1 + (B + 1 / 3) * (k * d) ** 2),
+                1e-6, 10.0)
+    assert np.all(np.abs(amp_P / amp_eta / (w0 / km) - 1) <= 0.01)
+    assert np.all(np.abs(lag) <= 0.01)
+    assert np.all(np.abs(amp_eta / a - 1) <= 0.05)
 
 
 # --------------------------------------------------------------- symmetry
