@@ -17,8 +17,10 @@ each one are named in the test module docstrings):
   * friction + AB3 order: uniform-flow ODE -- pinned
   * Euler start-up, AB3 predictor and AM4 corrector iterations: each step's
     formula on the friction ODE, to rounding -- pinned
-  * sine-ghost timing, corner ghosts: parity unpinned (internal consistency
-    only).
+  * sine maker: the wave it sends into a sponged channel is progressive,
+    P = c eta with the model's dispersion relation, amplitude a -- pinned
+  * which of t^n, t^{n+1} each stage's sine ghosts are taken at, corner
+    ghosts: parity unpinned (internal consistency only).
   * run-up tracking: standing-mode maximum, dry threshold -- pinned
   * tangent-linear oracle (celeris_tlm.cpp: this source on dual numbers):
     values bit for bit the oracle's, tangents vs central differences,
