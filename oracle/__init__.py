@@ -18,9 +18,9 @@ each one are named in the test module docstrings):
   * Euler start-up, AB3 predictor and AM4 corrector iterations: each step's
     formula on the friction ODE, to rounding -- pinned
   * sine maker: the wave it sends into a sponged channel is progressive,
-    P = c eta with the model's dispersion relation, amplitude a -- pinned
-  * which of t^n, t^{n+1} each stage's sine ghosts are taken at, corner
-    ghosts: parity unpinned (internal consistency only).
+    P = c eta with the model's dispersion relation, amplitude a, and its
+    steady phase converged in dt (the stages' ghost times) -- pinned
+  * corner ghosts: parity unpinned (internal consistency only).
   * run-up tracking: standing-mode maximum, dry threshold -- pinned
   * tangent-linear oracle (celeris_tlm.cpp: this source on dual numbers):
     values bit for bit the oracle's, tangents vs central differences,

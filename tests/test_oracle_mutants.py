@@ -34,6 +34,12 @@ MUTANTS = [
     ("wall_no_negate", "P[gc] = -P[sc];", "P[gc] = P[sc];", "test_mass_soliton_channel"),
     ("sine_discharge_sign", "*Pg += c * cs * em;", "*Pg -= c * cs * em;", "test_sine_maker_progressive_wave"),
     ("sine_celerity", "orc_real c = om / k;", "orc_real c = k / om;", "test_sine_maker_progressive_wave"),
+    ("sine_corrector_time", "fill_ghosts(o, o->w1, o->P1, o->Q1, t1);", "fill_ghosts(o, o->w1, o->P1, o->Q1, t0);",
+     "test_sine_maker_progressive_wave"),
+    ("sine_predictor_time", "fill_ghosts(o, o->w, o->P, o->Q, t0);", "fill_ghosts(o, o->w, o->P, o->Q, t1);",
+     "test_sine_maker_progressive_wave"),
+    ("sine_line_rows_time", "solve_lines(o, 0, o->U1, o->P1, t1);", "solve_lines(o, 0, o->U1, o->P1, t0);",
+     "test_sine_maker_progressive_wave"),
     ("desing_sqrt2", "return sqrt(2.0) * h / sqrt(h4 + fmax(h4, eps));", "return h / sqrt(h4 + fmax(h4, eps));",
      "test_soliton_speed"),
     ("eq23_sign_s", "*a = s - r;", "*a = -s - r;", "test_symmetry_mirror_x"),
