@@ -32,6 +32,11 @@ MUTANTS = [
      "(9.0 * o->Fc[c] + 18.0 * o->F[0][c] - 5.0 * o->F[1][c] + o->F[2][c])",
      "test_time_stepping_formulas_step_by_step"),
     ("wall_no_negate", "P[gc] = -P[sc];", "P[gc] = P[sc];", "test_mass_soliton_channel"),
+    ("positivity_high_branch", "lo[0] = 2.0 * w[c] - Bhi;", "lo[0] = w[c];", "test_symmetry_mirror_x_wet_dry"),
+    ("positivity_low_branch", "hi[0] = 2.0 * w[c] - Blo;", "hi[0] = w[c];", "test_symmetry_mirror_x_wet_dry"),
+    ("sponge_skips_Q", "o->Q1[c] *= gam;", ";", "test_symmetry_transpose_with_sponges"),
+    ("sponge_to_zero_level", "o->w1[c] = o->p.ws + gam * (o->w1[c] - o->p.ws);", "o->w1[c] = gam * o->w1[c];",
+     "test_lake_at_rest_with_sponges_off_zero_level"),
     ("sine_discharge_sign", "*Pg += c * cs * em;", "*Pg -= c * cs * em;", "test_sine_maker_progressive_wave"),
     ("sine_celerity", "orc_real c = om / k;", "orc_real c = k / om;", "test_sine_maker_progressive_wave"),
     ("sine_corrector_time", "fill_ghosts(o, o->w1, o->P1, o->Q1, t1);", "fill_ghosts(o, o->w1, o->P1, o->Q1, t0);",

@@ -15,6 +15,8 @@ an invariant, a textbook routine, a special case or a convergence order.
   NLSW path, dry front                    Ritter closed form        test_ritter_*
   dispersion terms, tridiagonal, F*, G*   linear dispersion relation test_dispersion_*
   ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
+  positivity fix, dry clamp               symmetry with wet-dry fronts test_symmetry_mirror_x_wet_dry
+  sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
   soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36)  test_soliton_*
   sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
   friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders   test_friction_*
@@ -128,6 +130,22 @@ def test_lake_at_rest_submerged(oracle_mod):
     bound = 1e-12 * math.sqrt(G * dmax) * dmax
     assert np.max(np.abs(P)) <= bound and np.max(np.abs(Q)) <= bound
     assert np.max(np.abs(w)) <= 1e-13
+
+
+def test_lake_at_rest_with_sponges_off_zero_level(oracle_mod):
+    """Still water at a level w_s = 0.3 m (Sec. 2.1) over a submerged bed,
+    sponges on all four sides (Eq. 30): the sponge relaxes towards w_s, so
+    the lake stays exactly at rest."""
+    nx, ny, ws = 48, 40, 0.3
+    z = sc.random_bed(nx, ny, 7, -6.0, -0.5, smooth=2) + ws
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * 6.0), K=1, ws=ws)
+    for side in (oracle_mod.W, oracle_mod.E, oracle_mod.S, oracle_mod.N):
+        o.set_boundary(side, oracle_mod.SPONGE, 6)
+    o.set_state(np.full_like(z, ws), np.zeros_like(z), np.zeros_like(z))
+    o.step(300)
+    w, P, Q = o.state()
+    assert np.max(np.abs(w - ws)) <= 1e-13
+    assert np.max(np.abs(P)) <= 1e-12 and np.max(np.abs(Q)) <= 1e-12
 
 
 @pytest.mark.parametrize("K", [0, 2])
@@ -372,6 +390,46 @@ def test_symmetry_mirror_x(oracle_mod):
     assert np.max(np.abs(P + P[:, ::-1])) <= 1e-12 * max(np.max(np.abs(P)), 1e-30)
     assert np.all(Q == 0.0)
     assert np.max(np.abs(w - w[0:1])) == 0.0          # stays y-uniform
+
+
+def test_symmetry_mirror_x_wet_dry(oracle_mod):
+    """A parabolic basin dry at both ends with a centred hump: the shoreline
+    moves up both slopes, through both branches of the positivity fix
+    (Reading A-L2) and the dry clamp, and the run stays mirror-symmetric."""
+    nx, ny, dx = 120, 2, 0.05
+    x = (np.arange(nx) + 0.5) * dx
+    xc = nx * dx / 2
+    z = np.tile(-0.5 + 0.8 * ((x - xc) / xc) ** 2, (ny, 1))
+    eta = np.tile(0.08 * np.exp(-((x - xc) / 0.4) ** 2), (ny, 1))
+    o = oracle_mod.Oracle(z, dx, dx, 0.1 * dx / math.sqrt(G * 0.5), model=oracle_mod.NLSW, K=1, eps=1e-8)
+    o.set_state(np.maximum(eta, z), 0 * z, 0 * z)
+    o.step(800)
+    w, P, Q = o.state()
+    wet = w - z > 1e-6
+    assert np.any(~wet[0, :10]) and np.any(wet[0, 10:40])    # a shoreline on the slope
+    assert np.max(np.abs(w - w[:, ::-1])) <= 1e-12
+    assert np.max(np.abs(P + P[:, ::-1])) <= 1e-12 * max(np.max(np.abs(P)), 1e-30)
+    assert np.max(np.abs(P)) > 0
+
+
+def test_symmetry_transpose_with_sponges(oracle_mod):
+    """The transpose symmetry with sponges on all four sides (Eq. 30): each
+    damps w, P and Q alike, so the run stays symmetric under x <-> y with
+    P <-> Q."""
+    n = 48
+    z = sc.random_bed(n, n, 3, -3.0, -1.5, smooth=3)
+    z = 0.5 * (z + z.T)
+    X, Y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+    eta = 0.1 * np.exp(-((X - 14) ** 2 + (Y - 32) ** 2) / 20.0)
+    eta = eta + eta.T
+    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * 3.0), K=1)
+    for side in (oracle_mod.W, oracle_mod.E, oracle_mod.S, oracle_mod.N):
+        o.set_boundary(side, oracle_mod.SPONGE, 8)
+    o.set_state(eta, 0 * z, 0 * z)
+    o.step(300)
+    w, P, Q = o.state()
+    assert np.max(np.abs(w - w.T)) <= 1e-12 * np.max(np.abs(w))
+    assert np.max(np.abs(P - Q.T)) <= 1e-12 * np.max(np.abs(P))
 
 
 def test_symmetry_transpose(oracle_mod):
