@@ -20,7 +20,8 @@ each one are named in the test module docstrings):
   * sine maker: the wave it sends into a sponged channel is progressive,
     P = c eta with the model's dispersion relation, amplitude a, and its
     steady phase converged in dt (the stages' ghost times) -- pinned
-  * corner ghosts: parity unpinned (internal consistency only).
+  * corner ghosts where two sine makers meet: parity unpinned (internal
+    consistency only; a maker beside a wall transposes exactly -- pinned).
   * run-up tracking: standing-mode maximum, dry threshold -- pinned
   * tangent-linear oracle (celeris_tlm.cpp: this source on dual numbers):
     values bit for bit the oracle's, tangents vs central differences,

@@ -45,6 +45,9 @@ MUTANTS = [
      "test_sine_maker_progressive_wave"),
     ("sine_line_rows_time", "solve_lines(o, 0, o->U1, o->P1, t1);", "solve_lines(o, 0, o->U1, o->P1, t0);",
      "test_sine_maker_progressive_wave"),
+    ("sine_y_discharge_sign", "*Qg += c * sn * em;", "*Qg -= c * sn * em;", "test_symmetry_transpose_sine_makers"),
+    ("sine_y_line_rows_time", "solve_lines(o, 1, o->V1, o->Q1, t1);", "solve_lines(o, 1, o->V1, o->Q1, t0);",
+     "test_symmetry_transpose_sine_makers"),
     ("desing_sqrt2", "return sqrt(2.0) * h / sqrt(h4 + fmax(h4, eps));", "return h / sqrt(h4 + fmax(h4, eps));",
      "test_soliton_speed"),
     ("eq23_sign_s", "*a = s - r;", "*a = -s - r;", "test_symmetry_mirror_x"),

@@ -19,6 +19,7 @@ an invariant, a textbook routine, a special case or a convergence order.
   sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
   soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36)  test_soliton_*
   sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
+  sine maker on the y-sides               transposed runs           test_symmetry_transpose_sine_*
   friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders   test_friction_*
   AB3 stability (Sec. 2.3)                real-axis bound -6/11     test_stability_*
 """
@@ -430,6 +431,35 @@ def test_symmetry_transpose_with_sponges(oracle_mod):
     w, P, Q = o.state()
     assert np.max(np.abs(w - w.T)) <= 1e-12 * np.max(np.abs(w))
     assert np.max(np.abs(P - Q.T)) <= 1e-12 * np.max(np.abs(P))
+
+
+def test_symmetry_transpose_sine_makers(oracle_mod):
+    """A west maker at direction 0 beside a south wall, and the transposed
+    set-up, a south maker at direction pi/2 beside a west wall (Eq. 25-29,
+    sponges on the far sides), give transposed runs (x <-> y, P <-> Q): the
+    y-sides' maker ghosts, their discharge along y and the y-lines' maker
+    rows against the x-sides' (corner ghosts transpose too here, as each
+    corner touches one maker)."""
+    n = 64
+    z = sc.random_bed(n, n, 3, -3.0, -1.5, smooth=3)
+    z = 0.5 * (z + z.T)
+
+    def run(west):
+        o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * 3.0), K=1)
+        o.set_boundary(oracle_mod.W if west else oracle_mod.S, oracle_mod.SINE, 0,
+                       ((0.02, 6.0, 0.0 if west else math.pi / 2, 0.3),))
+        o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, 10)
+        o.set_boundary(oracle_mod.N, oracle_mod.SPONGE, 10)
+        o.set_state(0 * z, 0 * z, 0 * z)
+        o.step(600)
+        return o.state()
+
+    wa, Pa, Qa = run(True)
+    wb, Pb, Qb = run(False)
+    scale = np.max(np.abs(Pa))
+    assert np.max(np.abs(wa)) > 0.01
+    assert np.max(np.abs(wa - wb.T)) <= 1e-12 * np.max(np.abs(wa))
+    assert np.max(np.abs(Pa - Qb.T)) <= 1e-12 * scale and np.max(np.abs(Qa - Pb.T)) <= 1e-12 * scale
 
 
 def test_symmetry_transpose(oracle_mod):
