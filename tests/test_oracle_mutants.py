@@ -57,6 +57,8 @@ MUTANTS = [
     ("flux_mass_diffusion_sign", "ap * am * (wR - wL)", "ap * am * (wL - wR)", "test_ritter_dam_break"),
     ("friction_h_power", "f -= fc * P[c] * mag * hinv * hinv;", "f -= fc * P[c] * mag * hinv;",
      "test_friction_manning_ode"),
+    ("soliton_y_discharge_sign", "o->Q[c] += cs * es * st;", "o->Q[c] -= cs * es * st;",
+     "test_symmetry_transpose_solitons"),
     ("soliton_ks", "sqrt(3.0 * fabs(H) / (4.0 * ds * ds * ds))", "sqrt(3.0 * fabs(H) / (2.0 * ds * ds * ds))",
      "test_soliton_speed"),
     ("eckart", "return k0 * sqrt(1.0 / tanh(k0 * d));", "return k0 * (1.0 / tanh(k0 * d));",

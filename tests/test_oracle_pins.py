@@ -18,6 +18,7 @@ an invariant, a textbook routine, a special case or a convergence order.
   positivity fix, dry clamp               symmetry with wet-dry fronts test_symmetry_mirror_x_wet_dry
   sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
   soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36)  test_soliton_*
+  soliton direction                       transposed runs           test_symmetry_transpose_solitons
   sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
   sine maker on the y-sides               transposed runs           test_symmetry_transpose_sine_*
   friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders   test_friction_*
@@ -458,6 +459,31 @@ def test_symmetry_transpose_sine_makers(oracle_mod):
     wb, Pb, Qb = run(False)
     scale = np.max(np.abs(Pa))
     assert np.max(np.abs(wa)) > 0.01
+    assert np.max(np.abs(wa - wb.T)) <= 1e-12 * np.max(np.abs(wa))
+    assert np.max(np.abs(Pa - Qb.T)) <= 1e-12 * scale and np.max(np.abs(Qa - Pb.T)) <= 1e-12 * scale
+
+
+def test_symmetry_transpose_solitons(oracle_mod):
+    """A solitary wave heading along x (direction 0) and the transposed one
+    heading along y (pi/2) in a walled square basin (Eq. 33-36) give
+    transposed runs: the wave's discharge along its direction in y."""
+    n, dx, d = 64, 0.5, 1.0
+    z = np.full((n, n), -d)
+
+    def run(along_x):
+        o = oracle_mod.Oracle(z, dx, dx, 0.1 * dx / math.sqrt(G * d), K=1)
+        o.set_state(0 * z, 0 * z, 0 * z)
+        if along_x:
+            o.add_solitary(0.1, 0.0, 9.0, 17.0)
+        else:
+            o.add_solitary(0.1, math.pi / 2, 17.0, 9.0)
+        o.step(200)
+        return o.state()
+
+    wa, Pa, Qa = run(True)
+    wb, Pb, Qb = run(False)
+    scale = np.max(np.abs(Pa))
+    assert np.max(np.abs(wa)) > 0.05
     assert np.max(np.abs(wa - wb.T)) <= 1e-12 * np.max(np.abs(wa))
     assert np.max(np.abs(Pa - Qb.T)) <= 1e-12 * scale and np.max(np.abs(Qa - Pb.T)) <= 1e-12 * scale
 
