@@ -51,6 +51,10 @@ MUTANTS = [
     ("desing_sqrt2", "return sqrt(2.0) * h / sqrt(h4 + fmax(h4, eps));", "return h / sqrt(h4 + fmax(h4, eps));",
      "test_soliton_speed"),
     ("eq23_sign_s", "*a = s - r;", "*a = -s - r;", "test_symmetry_mirror_x"),
+    ("eta_depth_gradient_terms", "Bd * g * dd * dd * (dxd * (2.0 * exx + eyy) + dyd * exy);", "0.0;",
+     "test_linear_shoaling_on_a_slope"),
+    ("depth_gradient_sign", "(o->d[IX(o, i + 1, j)] - o->d[IX(o, i - 1, j)]) / (2.0 * o->p.dx)",
+     "(o->d[IX(o, i - 1, j)] - o->d[IX(o, i + 1, j)]) / (2.0 * o->p.dx)", "test_linear_shoaling_on_a_slope"),
     ("tridiag_B", "*b = 1.0 + 2.0 * r;", "*b = 1.0 + r;", "test_dispersion_relation_1d"),
     ("hydrostatic_half", "FL1 = qnL * uL + 0.5 * g * hL * hL", "FL1 = qnL * uL + g * hL * hL",
      "test_lake_at_rest_submerged"),

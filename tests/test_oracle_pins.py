@@ -14,6 +14,7 @@ an invariant, a textbook routine, a special case or a convergence order.
   flux form, walls, AB3 / AM4             mass conservation         test_mass_*
   NLSW path, dry front                    Ritter closed form        test_ritter_*
   dispersion terms, tridiagonal, F*, G*   linear dispersion relation test_dispersion_*
+  depth-gradient terms of Eq. 10-11       linear shoaling           test_linear_shoaling_*
   ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
   positivity fix, dry clamp               symmetry with wet-dry fronts test_symmetry_mirror_x_wet_dry
   sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
@@ -373,6 +374,56 @@ def test_sine_maker_progressive_wave(oracle_mod):
     assert np.all(np.abs(amp_eta - 1) <= 0.05)
     ph_half = _sine_channel(oracle_mod, 0.1)[2]
     assert np.all(np.abs(np.angle(np.exp(1j * (ph_half - ph_eta)))) <= 1e-5)
+
+
+def test_linear_shoaling_on_a_slope(oracle_mod):
+    """Sec. 2.1: the equations' linear shoaling is accurate for kd < 3.
+    Regular waves (a/d = 0.004, T = 2 s) from a sine maker run up a 1:20
+    slope from d = 1 m (kd 1.2) to 0.4 m (kd 0.68) into a sponge: the
+    amplitude grows as energy-flux conservation of linear theory says,
+    a2 / a1 = sqrt(Cg1 / Cg2) with Cg of w^2 = g k tanh(kd), within 3 %
+    (the oracle: -1.3 %; without the depth-gradient terms of Eq. 10-11,
+    -7 %; with d_x's sign flipped, +11 %)."""
+    from scipy.optimize import brentq
+
+    def k_of(w, d):
+        return brentq(lambda k: w * w - G * k * math.tanh(k * d), 1e-6, 50.0)
+
+    def cg(w, d):
+        k = k_of(w, d)
+        return 0.5 * w / k * (1 + 2 * k * d / math.sinh(2 * k * d))
+
+    d1, d2, T, a, dx, slope = 1.0, 0.4, 2.0, 0.004, 0.05, 1 / 20
+    w = 2 * math.pi / T
+    L1, L2 = 2 * math.pi / k_of(w, d1), 2 * math.pi / k_of(w, d2)
+    x1 = 2.5 * L1
+    x2 = x1 + (d1 - d2) / slope
+    nx = int(round((x2 + 6.0 * L2) / dx))
+    x = (np.arange(nx) + 0.5) * dx
+    z = np.tile(-np.where(x < x1, d1, np.where(x < x2, d1 - (x - x1) * slope, d2)), (2, 1))
+    dt = 0.2 * dx / math.sqrt(G * d1)
+    o = oracle_mod.Oracle(z, dx, dx, dt, K=1)
+    o.set_boundary(oracle_mod.W, oracle_mod.SINE, 0, ((a, T, 0.0, 0.0),))
+    o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, int(round(2.5 * L2 / dx)))
+    o.set_state(0 * z, 0 * z, 0 * z)
+    t_settled = x1 / (L1 / T) + (x2 - x1 + 3.5 * L2) / (L2 / T) + 8 * T
+    n_total, n_fit = int(round(t_settled / dt)), int(round(3 * T / dt))
+    o.step(n_total - n_fit)
+    # eight gauges over a wavelength on each flat part average out the
+    # partial standing wave of the slope's small reflection
+    gi = [int(round((0.8 * L1 + f * L1 / 8) / dx)) for f in range(8)] + \
+         [int(round((x2 + L2 + f * L2 / 8) / dx)) for f in range(8)]
+    t, eta = [], []
+    for n in range(n_fit):
+        o.step(1)
+        t.append((n_total - n_fit + n + 1) * dt)
+        eta.append(o.state()[0][0, gi])
+    t = np.array(t)
+    A = np.stack([np.cos(w * t), np.sin(w * t), np.ones_like(t)], 1)
+    ce = np.linalg.lstsq(A, np.array(eta), rcond=None)[0]
+    amp = np.hypot(ce[0], ce[1])
+    ratio = amp[8:].mean() / amp[:8].mean()
+    assert abs(ratio / math.sqrt(cg(w, d1) / cg(w, d2)) - 1) <= 0.03
 
 
 # --------------------------------------------------------------- symmetry
