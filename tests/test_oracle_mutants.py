@@ -58,6 +58,7 @@ MUTANTS = [
     ("tridiag_B", "*b = 1.0 + 2.0 * r;", "*b = 1.0 + r;", "test_dispersion_relation_1d"),
     ("hydrostatic_half", "FL1 = qnL * uL + 0.5 * g * hL * hL", "FL1 = qnL * uL + g * hL * hL",
      "test_lake_at_rest_submerged"),
+    ("tangential_flux_side", "FL2 = qnL * vL;", "FL2 = qnL * vR;", "test_central_upwind_consistency"),
     ("flux_mass_diffusion_sign", "ap * am * (wR - wL)", "ap * am * (wL - wR)", "test_ritter_dam_break"),
     ("friction_h_power", "f -= fc * P[c] * mag * hinv * hinv;", "f -= fc * P[c] * mag * hinv;",
      "test_friction_manning_ode"),

@@ -110,10 +110,14 @@ def test_central_upwind_consistency(oracle_mod):
     # lake at rest: hydrostatic momentum flux only
     H = cu(G, eps, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, -3.0)
     assert H == pytest.approx([0.0, 0.5 * G * 9.0, 0.0], abs=1e-13)
-    # supercritical to the right: pure upwinding, H = F(U_left)
-    hL, uL, hR, uR = 0.5, 10.0, 0.4, 9.0
-    H = cu(G, eps, hL, hL * uL, 0.0, hR, hR * uR, 0.0, 0.0)
-    assert H == pytest.approx([hL * uL, hL * uL * uL + 0.5 * G * hL * hL, 0.0], rel=1e-12)
+    # supercritical to the right: pure upwinding, H = F(U_left), the
+    # tangential velocity carried from the left as well
+    hL, uL, vL, hR, uR, vR = 0.5, 10.0, 1.5, 0.4, 9.0, -2.0
+    H = cu(G, eps, hL, hL * uL, hL * vL, hR, hR * uR, hR * vR, 0.0)
+    assert H == pytest.approx([hL * uL, hL * uL * uL + 0.5 * G * hL * hL, hL * uL * vL], rel=1e-12)
+    # and supercritical to the left: H = F(U_right)
+    H = cu(G, eps, hR, -hR * uR, hR * vR, hL, -hL * uL, hL * vL, 0.0)
+    assert H == pytest.approx([-hL * uL, hL * uL * uL + 0.5 * G * hL * hL, -hL * uL * vL], rel=1e-12)
     # both sides dry
     assert list(cu(G, eps, 1.0, 0.3, 0.1, 1.0, -0.2, 0.0, 1.0)) == [0.0, 0.0, 0.0]
 
