@@ -12,7 +12,8 @@ each one are named in the test module docstrings):
   * flux form, walls, AB3: mass conservation with solid walls -- pinned
   * KP07 NLSW path + dry front: Ritter dam-break closed form -- pinned
   * dispersion + tridiagonal + F*: linear dispersion relation -- pinned
-  * depth-gradient terms of Eq. 10-11: linear shoaling on a slope -- pinned;
+  * depth-gradient terms of Eq. 10-11 and Eq. 23: linear shoaling on a
+    slope -- pinned;
     those of F*, G* (Eq. 12-13): parity unpinned (they vanish in 1-D).
   * mirror / transpose symmetry -- pinned
   * Thomas solver: dense solve -- pinned; Eckart, sponge, soliton -- pinned

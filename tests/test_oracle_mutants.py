@@ -55,6 +55,8 @@ MUTANTS = [
      "test_linear_shoaling_on_a_slope"),
     ("depth_gradient_sign", "(o->d[IX(o, i + 1, j)] - o->d[IX(o, i - 1, j)]) / (2.0 * o->p.dx)",
      "(o->d[IX(o, i - 1, j)] - o->d[IX(o, i + 1, j)]) / (2.0 * o->p.dx)", "test_linear_shoaling_on_a_slope"),
+    ("eq23_depth_gradient_dropped", "orc_real s = dd * dda / (6.0 * h);", "orc_real s = 0.0;",
+     "test_linear_shoaling_on_a_slope"),
     ("tridiag_B", "*b = 1.0 + 2.0 * r;", "*b = 1.0 + r;", "test_dispersion_relation_1d"),
     ("hydrostatic_half", "FL1 = qnL * uL + 0.5 * g * hL * hL", "FL1 = qnL * uL + g * hL * hL",
      "test_lake_at_rest_submerged"),
