@@ -15,6 +15,7 @@ an invariant, a textbook routine, a special case or a convergence order.
   NLSW path, dry front                    Ritter closed form        test_ritter_*
   dispersion terms, tridiagonal, F*, G*   linear dispersion relation test_dispersion_*
   depth-gradient terms of Eq. 10-11       linear shoaling           test_linear_shoaling_*
+  NLSW reduction at d = 0 (Sec. 2.1)      the two models agree       test_boussinesq_reduces_*
   ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
   positivity fix, dry clamp               symmetry with wet-dry fronts test_symmetry_mirror_x_wet_dry
   sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
@@ -378,6 +379,29 @@ def test_sine_maker_progressive_wave(oracle_mod):
     assert np.all(np.abs(amp_eta - 1) <= 0.05)
     ph_half = _sine_channel(oracle_mod, 0.1)[2]
     assert np.all(np.abs(np.angle(np.exp(1j * (ph_half - ph_eta)))) <= 1e-5)
+
+
+def test_boussinesq_reduces_to_nlsw_where_d_is_zero(oracle_mod):
+    """Sec. 2.1: the equations reduce to the nonlinear shallow-water system
+    where d = 0.  With the still-water level below the whole bed (d = 0
+    everywhere) and water standing on it, the Boussinesq model steps
+    exactly as the NLSW model: every dispersive and mixed term carries a
+    factor d, and the rows of Eq. 23 become identity rows."""
+    nx, ny = 40, 32
+    z = sc.random_bed(nx, ny, 11, -1.0, -0.4, smooth=2)
+    X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
+    w0 = z + 0.3 + 0.1 * np.exp(-((X - 15) ** 2 + (Y - 12) ** 2) / 20.0)
+    runs = []
+    for model in (oracle_mod.BSNQ, oracle_mod.NLSW):
+        o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * 0.8), model=model, K=1, ws=-5.0,
+                              friction=2, fcoef=0.02, eps=1e-8)
+        o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, 6)
+        o.set_state(w0, 0 * z, 0 * z)
+        o.step(200)
+        runs.append(o.state())
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    assert np.max(np.abs(runs[0][1])) > 0
 
 
 def test_linear_shoaling_on_a_slope(oracle_mod):
