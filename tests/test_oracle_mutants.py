@@ -110,6 +110,10 @@ RENDER_MUTANTS = [
      "test_flat_lake_from_above"),
     ("speed_uses_P_twice", "v = sqrtf(u * u + vv * vv);", "v = sqrtf(u * u + u * u);",
      "test_speed_and_velocity_components"),
+    ("velocity_depth_floor", "float hd = h > p->h_min ? h : p->h_min;", "float hd = h;",
+     "test_speed_and_velocity_components"),
+    ("hillshade_unclamped", "float shade = 0.35f + 0.65f * (d > 0.0f ? d : 0.0f);", "float shade = 0.35f + 0.65f * d;",
+     "test_flat_land_hillshade"),
 ]
 
 

@@ -10,7 +10,8 @@ against closed forms and invariants, computed here in FP64:
 * flat land under a sun straight above is the bare terrain colour, and
   under a sun 60 degrees off the vertical the terrain colour times 0.675;
 * grid lines where x / spacing crosses an integer;
-* speed = |(P, Q)| / h;
+* speed = |(P, Q)| / h, with h at least h_min;
+* Lambert's law clamped at zero on land facing away from the sun;
 * mirror symmetry: a state mirrored in x, seen and lit from the mirrored
   directions, renders as the mirrored image, byte for byte.
 """
@@ -82,6 +83,15 @@ def test_flat_land_hillshade(oracle_mod):
     p = oracle_mod.render_params("eta", zmin=0.5, zmax=1.5, sun=(math.sin(math.pi / 3), 0.0, 0.5))
     img = oracle_mod.render(w, 0 * w, 0 * w, z, 1.0, 1.0, 0.0, p)
     assert np.all(np.abs(img[..., :3].astype(int) - _bytes(TERRAIN0 * (0.35 + 0.65 * 0.5))) <= 1)
+    # Lambert's law clamps at zero: land rising steeply towards a low sun
+    # faces away from it and keeps the ambient 0.35 of its terrain colour
+    zs = np.tile(0.5 + 0.002 * np.arange(5.0), (5, 1))
+    p = oracle_mod.render_params("eta", zmin=0.5, zmax=1.5, exaggeration=1000.0,
+                                 sun=(math.sin(math.radians(80)), 0.0, math.cos(math.radians(80))))
+    img = oracle_mod.render(zs, 0 * zs, 0 * zs, zs, 1.0, 1.0, 0.0, p)
+    t = (zs[2, 2] - 0.5) / 1.0
+    want = _bytes(oracle_mod.colormap(2, t).astype(np.float64) * 0.35)
+    assert np.all(np.abs(img[2, 2, :3].astype(int) - want) <= 1)
 
 
 def test_grid_lines(oracle_mod):
@@ -106,6 +116,12 @@ def test_speed_and_velocity_components(oracle_mod):
         img = oracle_mod.render(w, P, Q, B, 1.0, 1.0, 0.0, p)
         want = _bytes(oracle_mod.colormap(m, val / 10.0))
         np.testing.assert_array_equal(img[1, 1, :3], want)
+    # a film thinner than h_min (but wet) shows its velocity over h_min:
+    # P = 0.04 on 4 mm of water reads u = 2 (not 10)
+    Bf = np.full((3, 3), -0.004)
+    p = oracle_mod.render_params("u", vmin=0.0, vmax=10.0, dry_h=1e-3, h_min=0.02)
+    img = oracle_mod.render(w, np.full((3, 3), 0.04), 0 * w, Bf, 1.0, 1.0, 0.0, p)
+    np.testing.assert_array_equal(img[1, 1, :3], _bytes(oracle_mod.colormap(0, 0.2)))
 
 
 @pytest.mark.parametrize("mode", ["fresnel", "eta", "v", "speed"])
