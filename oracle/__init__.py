@@ -374,7 +374,8 @@ def tlm_lib():
     global _tlm
     with _lock:
         if _tlm is None:
-            L = ctypes.CDLL(build_tlm())
+            # TLM_ORACLE_LIB lets the mutation test load a deliberately broken copy
+            L = ctypes.CDLL(os.environ.get("TLM_ORACLE_LIB") or build_tlm())
             i, p = ctypes.c_int, ctypes.c_void_p
             dp = ctypes.POINTER(ctypes.c_double)
             L.tlm_create.restype = p

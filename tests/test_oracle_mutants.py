@@ -133,3 +133,36 @@ def test_render_pin_catches_mutant(tmp_path, name, orig, mut, pin):
                         os.path.join(ROOT, "tests", "test_render_oracle_pins.py"), "-k", pin],
                        cwd=ROOT, env=env, capture_output=True, text=True)
     assert r.returncode != 0, f"pin {pin} did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
+# The tangent-linear oracle's dual-number arithmetic (oracle/celeris_tlm.cpp):
+# a wrong derivative rule must break the match with central differences.
+TLM_SRC = os.path.join(ROOT, "oracle", "celeris_tlm.cpp")
+TLM_MUTANTS = [
+    ("product_rule", "static inline orc_dual operator*(orc_dual a, orc_dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }",
+     "static inline orc_dual operator*(orc_dual a, orc_dual b) { return {a.v * b.v, a.d * b.v}; }"),
+    ("quotient_rule", "return {q, (a.d - q * b.d) / b.v};", "return {q, (a.d + q * b.d) / b.v};"),
+    ("sqrt_rule", "return {s, s > 0.0 ? a.d / (2.0 * s) : 0.0};", "return {s, s > 0.0 ? a.d / s : 0.0};"),
+    ("cbrt_rule", "return {c, c != 0.0 ? a.d / (3.0 * c * c) : 0.0};", "return {c, c != 0.0 ? a.d / (3.0 * c) : 0.0};"),
+    ("tanh_rule", "return {t, (1.0 - t * t) * a.d};", "return {t, (1.0 + t * t) * a.d};"),
+    ("sin_rule", "return {::sin(a.v), ::cos(a.v) * a.d};", "return {::sin(a.v), -::cos(a.v) * a.d};"),
+]
+
+
+@pytest.mark.parametrize("name,orig,mut", TLM_MUTANTS, ids=[m[0] for m in TLM_MUTANTS])
+def test_tangent_pin_catches_mutant(tmp_path, name, orig, mut):
+    src = open(TLM_SRC).read()
+    assert src.count(orig) == 1, f"mutation site for {name} not found"
+    mdir = tmp_path / "tlm_mutant"
+    mdir.mkdir()
+    (mdir / "celeris_tlm.cpp").write_text(src.replace(orig, mut, 1))
+    for f in ("celeris_oracle.c", "celeris_oracle.h"):
+        (mdir / f).write_text(open(os.path.join(ROOT, "oracle", f)).read())
+    so = mdir / "libtlm_mutant.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                    str(mdir / "celeris_tlm.cpp")], check=True)
+    env = dict(os.environ, TLM_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_tlm_oracle.py"), "-k", "central_differences or manning_paths"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"the central-difference pin did not catch mutant {name}:\n{r.stdout[-2000:]}"

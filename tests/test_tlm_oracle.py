@@ -5,7 +5,9 @@ than itself:
 * its values are the oracle's, bit for bit (the same arithmetic on the
   value parts);
 * its tangents equal central differences of the plain oracle, in the bed
-  and in the initial state, on a state away from the method's kinks;
+  and in the initial state, on a state away from the method's kinks,
+  including where they run through the sine maker's and Manning's
+  dependence on the depth;
 * it is linear in the direction.
 """
 import numpy as np
@@ -62,3 +64,27 @@ def test_tangent_oracle_is_linear_in_the_direction():
     _, d2 = tangent_run(s, gauges, 1e-2 * b, 1e-4 * a)
     _, d3 = tangent_run(s, gauges, 1e-2 * (2 * a - 3 * b), 1e-4 * (2 * b - 3 * a))
     np.testing.assert_allclose(d3, 2 * d1 - 3 * d2, rtol=0, atol=1e-12 * np.max(np.abs(d3)))
+
+
+def test_tangent_oracle_maker_and_manning_paths():
+    """The same check where the tangent runs through the sine maker's
+    dependence on the depth beside it (Eckart's k, the celerity, Eq. 25-29)
+    and through Manning's depth-dependent coefficient (Eq. 32): bed
+    directions on the two columns next to the maker, gauges near it, a
+    2 cm maker and n = 0.05."""
+    import dataclasses
+    import math
+
+    from paper_1611_05984_gb300 import scenarios as sc
+    s, _, X, Y = tilted_bed_scenario(model=0, K=1, friction=2, sine=True, nsteps=12)
+    s = dataclasses.replace(s, fcoef=0.05)
+    s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.02, 3.0, 0.2, 0.3),))
+    gauges = [(i, j) for i in (1, 3, 6) for j in (8, 18, 27)]
+    for vz, vw in ((1e-2 * np.exp(-((X - 0.5) / 0.4) ** 2) * (1 + 0.3 * np.sin(2 * math.pi * Y / 9.0)), 0 * X),
+                   (0 * X, 1e-4 * np.exp(-((X - 2.0) ** 2 + (Y - 9.0) ** 2) / 4.0))):
+        _, deta = tangent_run(s, gauges, vz, vw)
+        eps = 1e-5
+        fd = (_oracle_eta(s, gauges, z=s.z + eps * vz, w0=s.w0 + eps * vw)
+              - _oracle_eta(s, gauges, z=s.z - eps * vz, w0=s.w0 - eps * vw)) / (2 * eps)
+        assert np.max(np.abs(fd)) > 0
+        assert np.max(np.abs(deta - fd)) <= 1e-6 * np.max(np.abs(fd))
