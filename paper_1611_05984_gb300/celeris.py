@@ -442,7 +442,8 @@ class Ensemble:
         self.L.cel_ensemble_profile_disable(self._h)
 
     def close(self):
-        if self._h is not None:
+        if getattr(self, "_h", None) is not None:
+            self.stream.synchronize()   # its launches read the argument tables this object owns
             self.L.cel_ensemble_destroy(self._h)
             self._h = None
 
