@@ -489,8 +489,9 @@ def gauge_misfit_gradient(solver: "Solver", nsteps: int, gauges, obs, ckpt_every
     with torch.cuda.device(solver.device):
         if scratch is None:
             scratch = torch.empty(need, dtype=torch.uint8, device=solver.device)
-        elif scratch.dtype != torch.uint8 or not scratch.is_cuda or scratch.numel() < need:
-            raise ValueError(f"scratch must be a uint8 CUDA tensor of at least {need} bytes")
+        elif (scratch.dtype != torch.uint8 or not scratch.is_cuda or scratch.numel() < need
+              or scratch.get_device() != torch.cuda.current_device()):
+            raise ValueError(f"scratch must be a uint8 tensor of at least {need} bytes on the solver's device")
         if poison:
             scratch.fill_(255)
         eta = torch.empty((nsteps, ng), dtype=solver.dtype, device=solver.device)
