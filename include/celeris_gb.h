@@ -362,8 +362,10 @@ void cel_ensemble_destroy(cel_ensemble *e);
  * corrector_iters >= 1, 256 x 256 in FP64); bad arguments give
  * CEL_ERR_INVALID_ARG.  A one-line reason is copied into msg (msg_len bytes,
  * may be NULL).  The first call on each device looks up the array's device
- * address (with that device current); make that first call before any stream
- * capture.  All calls share the one array and each call clears what must
+ * address (with that device current), and so does the first call after the
+ * device's CUDA context changed (cudaDeviceReset, or another context made
+ * current): the address is kept per device together with the context's unique
+ * id.  Make that first call before any stream capture.  All calls share the one array and each call clears what must
  * start at zero, so calls that overlap on the GPU (on different streams, or
  * from different threads) race and give wrong results: serialise them. */
 #define CEL_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)

@@ -1009,12 +1009,69 @@ namespace {
 // The scratch of cel_advance_noalloc: one array in device memory, defined
 // here so that the library never has to allocate it.  Host code must not use
 // the name as an address (it is a host-side stand-in); the device address is
-// looked up once per device with cudaGetSymbolAddress.
+// looked up with cudaGetSymbolAddress once per device and CUDA context, and
+// kept with the context's unique id: after cudaDeviceReset, or with another
+// context current on the device, the module is loaded again at another
+// address, so a changed id means a new lookup.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[CEL_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
-void *g_noalloc_ptr[kMaxDevices];
+struct NoallocSlot {
+    unsigned long long ctx_id;   // unique id of the context the address belongs to
+    void *ptr;                   // device address of g_noalloc_scratch there (null: none yet)
+};
+NoallocSlot g_noalloc_slot[kMaxDevices];
 std::mutex g_noalloc_mutex;
+
+// The driver's context queries, fetched through the runtime (the library
+// links no libcuda of its own).
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+// Unique id of the context current on this thread; the runtime binds the
+// device's primary context first when none is current.  False with a reason
+// in why on failure.
+bool current_context_id(unsigned long long *id, std::string *why)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            *why = "the driver's context queries (cuCtxGetCurrent, cuCtxGetId) are unavailable";
+            return false;
+        }
+        get_current = (CtxGetCurrentFn)f1;
+        get_id = (CtxGetIdFn)f2;
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0) {
+        *why = "cuCtxGetCurrent failed";
+        return false;
+    }
+    if (!ctx) {
+        // no context current yet: a runtime call binds the primary context
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return false;
+        }
+        if (get_current(&ctx) != 0 || !ctx) {
+            *why = "no CUDA context is current after binding the device";
+            return false;
+        }
+    }
+    if (get_id(ctx, id) != 0) {
+        *why = "cuCtxGetId failed";
+        return false;
+    }
+    return true;
+}
 
 void put_msg(char *msg, size_t len, const std::string &text)
 {
@@ -1049,23 +1106,37 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         put_msg(msg, msg_len, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        return CEL_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        char buf[120];
+        snprintf(buf, sizeof(buf), "device %d is beyond the %d devices this entry point serves", dev, kMaxDevices);
+        put_msg(msg, msg_len, buf);
         return CEL_ERR_CUDA;
     }
     void *scratch;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
+        unsigned long long ctx_id = 0;
+        std::string why;
+        if (!current_context_id(&ctx_id, &why)) {
+            put_msg(msg, msg_len, why);
+            return CEL_ERR_CUDA;
+        }
+        NoallocSlot &slot = g_noalloc_slot[dev];
+        if (!slot.ptr || slot.ctx_id != ctx_id) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
                 put_msg(msg, msg_len, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
                 return CEL_ERR_CUDA;
             }
-            g_noalloc_ptr[dev] = p;
+            slot.ptr = p;
+            slot.ctx_id = ctx_id;
         }
-        scratch = g_noalloc_ptr[dev];
+        scratch = slot.ptr;
     }
     // a handle on the stack, pointing at the fixed scratch; set up as
     // cel_create does (the scratch is cleared, so nothing of an earlier call

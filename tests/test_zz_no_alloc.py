@@ -10,10 +10,12 @@ library defines in device memory, shared by all calls.
 The test calls it twice in a row through the C ABI, each time from a
 different state, and compares each result with what cel_create +
 cel_set_boundary + cel_set_state + cel_step + cel_get_state give for the same
-input, within the parity tolerances of the other GPU tests (relative L2,
-FP64 1e-10, FP32 1e-4).  The second call also shows that nothing left in the
-shared scratch by the first call leaks into the second.  This file is named so
-that pytest collects it last.
+input.  Both paths launch the same kernels on the same inputs, so the results
+must be equal bit for bit (which is within any tolerance of the other GPU
+tests); a scratch value left over from the first call would show up in the
+second.  A third case starts at first_step = N, where the sine maker's phase
+depends on the start time.  This file is named so that pytest collects it
+last.
 """
 import ctypes
 
@@ -41,7 +43,7 @@ def _bcs(scenario, celeris):
     return arr
 
 
-def _noalloc(celeris, s, dtype, state, nsteps):
+def _noalloc(celeris, s, dtype, state, nsteps, first_step=0):
     L = celeris.load()
     es = 4 if dtype == torch.float32 else 8
     grid = celeris.CelGrid(s.nx, s.ny, s.dx, s.dy, es)
@@ -53,21 +55,33 @@ def _noalloc(celeris, s, dtype, state, nsteps):
     stream = torch.cuda.current_stream()
     st = L.cel_advance_noalloc(ctypes.byref(grid), ctypes.byref(params), _bcs(s, celeris), z.data_ptr(),
                                w.data_ptr(), P.data_ptr(), Q.data_ptr(), out[0].data_ptr(),
-                               out[1].data_ptr(), out[2].data_ptr(), nsteps, 0, stream.cuda_stream,
+                               out[1].data_ptr(), out[2].data_ptr(), nsteps, first_step, stream.cuda_stream,
                                msg, len(msg))
     assert st == 0, msg.value.decode()
     stream.synchronize()
     return out
 
 
-def _workspace_path(celeris, s, dtype, state, nsteps):
+def _workspace_path(celeris, s, dtype, state, nsteps, first_step=0):
     g = celeris.Solver(s.z, s.dx, s.dy, s.dt, dtype=dtype, model=s.model, g=s.g, Bd=s.Bd, theta=s.theta,
                        eps=s.eps, K=s.K, ws=s.ws, friction=s.friction, fcoef=s.fcoef)
     for side, sd in s.sides.items():
         g.set_boundary(side, sd.type, sd.width, sd.comps)
     g.set_state(*state)
+    if first_step:
+        # run to step first_step, then restart the history from the given
+        # state: set_state keeps the step count (the time), so the next steps
+        # start at first_step * dt with Euler steps, as the entry point does
+        g.step(first_step)
+        assert g.time()[1] == first_step
+        g.set_state(*state)
     g.step(nsteps)
     return list(g.state())
+
+
+def _same(a, b, dtype):
+    assert _rel(a, b) <= TOL[dtype]
+    assert torch.equal(a, b)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
@@ -80,7 +94,7 @@ def test_noalloc_matches_workspace_path_on_two_calls(dtype):
     first = _noalloc(celeris, s, dtype, rest, 120)
     ref1 = _workspace_path(celeris, s, dtype, rest, 120)
     for a, b in zip(first, ref1):
-        assert _rel(a, b) <= TOL[dtype]
+        _same(a, b, dtype)
 
     # second call in a row, from a different state (the first result with a
     # trough added), fewer steps
@@ -89,8 +103,24 @@ def test_noalloc_matches_workspace_path_on_two_calls(dtype):
     second = _noalloc(celeris, s, dtype, [w2, P2, Q2], 80)
     ref2 = _workspace_path(celeris, s, dtype, [w2, P2, Q2], 80)
     for a, b in zip(second, ref2):
-        assert _rel(a, b) <= TOL[dtype]
+        _same(a, b, dtype)
     assert not torch.equal(second[0], first[0])
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+def test_noalloc_start_step_sets_the_sine_makers_phase(dtype):
+    from paper_1611_05984_gb300 import celeris
+    from paper_1611_05984_gb300 import scenarios as sc
+
+    s = sc.beach(nx=160, ny=96, sponge=12)
+    rest = [torch.as_tensor(a, dtype=dtype) for a in s.initial_state()]
+    late = _noalloc(celeris, s, dtype, rest, 60, first_step=137)
+    ref = _workspace_path(celeris, s, dtype, rest, 60, first_step=137)
+    for a, b in zip(late, ref):
+        _same(a, b, dtype)
+    # the maker's phase moved with the start time: a run from step 0 differs
+    early = _noalloc(celeris, s, dtype, rest, 60)
+    assert not torch.equal(late[0], early[0])
 
 
 def test_noalloc_rejects_grids_beyond_the_fixed_scratch():
