@@ -37,6 +37,14 @@ sys.path.insert(0, ROOT)
 #   line solves (x-rows and y-columns in one launch): per family the right
 #     side, depth and P^n (or Q^n) read, P^{n+1} (or Q^{n+1}) written: 2 x 4.
 VALUES = {"stencil_pred_k": 14 + 11, "stencil_pred_0": 10 + 9, "stencil_corr": 7 + 3, "lines": 8}
+# The same split on the contract's count of algorithmic values per cell-update
+# (the method's minimum with the AB3 history held as two combined carries per
+# variable, K = 0: 25 values per step; each AM4 corrector iteration about 14
+# more).  The stencil's share of the predictor: w, P, Q, the bed corners, 2
+# carries read and 2 written for each of w, U*, V*, w^{n+1}, U*, V* written
+# (19); the line solves': U*, V* and the bed read (once per family), P, Q
+# written (6); a corrector's stencil: 14 - 6 = 8.
+CONTRACT = {"stencil_pred": 19, "stencil_corr": 8, "lines": 6}
 
 
 def parse():
@@ -52,6 +60,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ckpt", type=int, default=None,
+                    help="adjoint workloads: checkpoint spacing (0 keeps every step; default: every step kept "
+                         "where it fits in 70%% of the free memory, else 100)")
+    ap.add_argument("--ensemble-steps", type=int, default=50,
+                    help="default workload: steps of the ensemble measurement in the line (0: none)")
+    ap.add_argument("--adjoint-steps", type=int, default=2000,
+                    help="default workload: steps of the adjoint measurement in the line (0: none)")
     return ap.parse_args()
 
 
@@ -225,10 +240,6 @@ def run_ensemble(args):
     against the same members stepped one cel_step per scenario in turn, both
     timed with CUDA events on the one stream, after the same warm-up."""
     import torch
-
-    from paper_1611_05984_gb300 import celeris
-    from paper_1611_05984_gb300 import scenarios as sc
-
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -236,6 +247,26 @@ def run_ensemble(args):
     torch.cuda.set_device(local)
     if world > 1:   # scenarios are independent: each rank steps its share, no data-path collective
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = measure_ensemble(args.steps, args.warmup, args.precision, world, rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_ensemble(steps, warmup, precision, world=1, rank=0):
+    """One measurement of the ensemble against one launch per scenario (see
+    run_ensemble); returns the JSON object (every rank takes part)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1611_05984_gb300 import celeris
+    from paper_1611_05984_gb300 import scenarios as sc
+
+    class _A:
+        pass
+    args = _A()
+    args.steps, args.warmup, args.precision = steps, warmup, precision
 
     def barrier():
         if world > 1:
@@ -316,10 +347,9 @@ def run_ensemble(args):
     dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
     achieved = kernels[dominant]["gbs_algorithmic"]
     gbs = (bytes_of["stencil"] + bytes_of["lines"]) / (ms_ens / 1e3) / 1e9
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
+    ens.close()
+    for m in members:
+        m.close()
     line = {"metric": "ensemble cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ens / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
@@ -340,9 +370,7 @@ def run_ensemble(args):
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                          "per_kernel": kernels, "step_gbs_algorithmic": gbs},
             "finite": finite, "gpu_launches": launches, "clocks": clk}
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    return line
 
 
 def run_adjoint(args):
@@ -357,13 +385,26 @@ def run_adjoint(args):
     allocated before the timed region.  The observations are the gauges of
     a target run from a perturbed hump over a perturbed bed."""
     import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps(measure_adjoint(args.steps, args.warmup, args.precision,
+                                     2048 if args.workload == "adjoint2048" else 512, args.ckpt)), flush=True)
+
+
+def measure_adjoint(steps, warmup, precision, n=512, ckpt_request=None):
+    """One measurement of the adjoint's cost (see run_adjoint).  ckpt_request:
+    the checkpoint spacing (0 keeps every step); None picks every step kept
+    where it fits in 70 % of the free memory, else 100."""
+    import torch
 
     from paper_1611_05984_gb300 import celeris
     from paper_1611_05984_gb300 import scenarios as sc
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    class _A:
+        pass
+    args = _A()
+    args.steps, args.warmup, args.precision = steps, warmup, precision
     dtype = torch.float32 if args.precision == "f32" else torch.float64
-    s, gauges = sc.hump_beach(n=2048 if args.workload == "adjoint2048" else 512, steps=args.steps)
+    s, gauges = sc.hump_beach(n=n, steps=args.steps)
     g = celeris.from_scenario(s, dtype=dtype)
     stream = g.stream
     t = celeris.from_scenario(sc.hump_beach_target(s), dtype=dtype)
@@ -373,7 +414,10 @@ def run_adjoint(args):
     t.close()
     g.step(args.warmup)
     free, _ = torch.cuda.mem_get_info()
-    ckpt = 0 if celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), 0, bed=True) <= 0.7 * free else 100
+    if ckpt_request is None:
+        ckpt = 0 if celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), 0, bed=True) <= 0.7 * free else 100
+    else:
+        ckpt = ckpt_request
     scratch = torch.empty(celeris.adjoint_scratch_bytes(g, args.steps, len(gauges), ckpt, bed=True),
                           dtype=torch.uint8, device="cuda")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -401,7 +445,10 @@ def run_adjoint(args):
             "grad_finite": bool(torch.isfinite(grad).all().item() and torch.isfinite(grad_z).all().item()),
             "grad_w_norm": float(torch.linalg.norm(grad.double()).item()),
             "grad_z_norm": float(torch.linalg.norm(grad_z.double()).item())}
-    print(json.dumps(line), flush=True)
+    g.close()
+    del scratch
+    torch.cuda.empty_cache()
+    return line
 
 
 def main():
@@ -469,13 +516,21 @@ def main():
     kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items()}
     dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
     line_bytes = s.cells * es * VALUES["lines"] * (nstages_pred + nstages_corr)
-    bytes_of = {"stencil": st_bytes, "lines": line_bytes, "ghosts": 0}
+    # the contract's count (CONTRACT): achieved and frac are on it
+    c_st = s.cells * es * (nstages_pred * CONTRACT["stencil_pred"] + nstages_corr * CONTRACT["stencil_corr"])
+    c_ln = s.cells * es * CONTRACT["lines"] * (nstages_pred + nstages_corr)
+    bytes_of = {"stencil": c_st, "lines": c_ln, "ghosts": 0}
+    ring_of = {"stencil": st_bytes, "lines": line_bytes, "ghosts": 0}
     dk = kernels[dominant]
     achieved = bytes_of[dominant] / (dk["ms_total"] / 1e3) / 1e9 if dk["ms_total"] > 0 else 0.0
+    ring_achieved = ring_of[dominant] / (dk["ms_total"] / 1e3) / 1e9 if dk["ms_total"] > 0 else 0.0
     for k in kernels:
         kk = kernels[k]
+        kk["us_per_launch"] = 1e3 * kk["ms_total"] / kk["launches"] if kk["launches"] else None
         kk["gbs_algorithmic"] = (bytes_of[k] / (kk["ms_total"] / 1e3) / 1e9
                                  if kk["ms_total"] > 0 and bytes_of[k] else None)
+        kk["gbs_ring_history"] = (ring_of[k] / (kk["ms_total"] / 1e3) / 1e9
+                                  if kk["ms_total"] > 0 and ring_of[k] else None)
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -487,9 +542,17 @@ def main():
         traffic = None
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "count": "contract: 25 values per cell-update at K = 0, about 14 more per corrector "
+                         "(stencil 19 + 8 per corrector, line solves 6 per stage)",
+                "ring_history": {"achieved": ring_achieved, "frac": ring_achieved / peak,
+                                 "count": "values this implementation's kernels must move: stencil 25 (predictor "
+                                          "with the AB3/AM4 ring history) + 10 per corrector, line solves 8 "
+                                          "per stage (P^n read for the increment form)"},
                 "per_kernel": kernels,
-                "step_bytes_algorithmic": (st_bytes + line_bytes) / args.steps,
-                "step_gbs_algorithmic": (st_bytes + line_bytes) / (ms / 1e3) / 1e9 / world}
+                "step_bytes_algorithmic": (c_st + c_ln) / args.steps,
+                "step_gbs_algorithmic": (c_st + c_ln) / (ms / 1e3) / 1e9 / world,
+                "step_frac": (c_st + c_ln) / (ms / 1e3) / 1e9 / world / peak,
+                "step_bytes_ring_history": (st_bytes + line_bytes) / args.steps}
 
     # ---- headless rendering of the final state (Fresnel water, hillshaded land)
     rp = celeris.render_params("fresnel", zmin=-10.0, zmax=3.0, exaggeration=10.0, view=(0.5, 0.3, -0.8))
@@ -515,6 +578,36 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(s, args.cpu_seconds)
 
+    # ---- the two growth patterns the metric names, on one GPU: the
+    # ensemble's speed-up over one launch per scenario, and the adjoint's
+    # cost over the forward run at the configured checkpoint spacing (100),
+    # with the every-step-kept figure beside it
+    ensemble = adjoint = None
+    if world == 1 and args.workload == "beach2048" and args.precision == "f32":
+        sol.close()
+        if args.ensemble_steps > 0:
+            el = measure_ensemble(args.ensemble_steps, 5, "f32")
+            ensemble = {"workload": "ensemble256", "members": el["config"]["members"],
+                        "cells": el["config"]["cells"], "steps": el["steps"],
+                        "speedup_vs_single_launch": el["speedup_vs_single_launch"],
+                        "value": el["value"], "unit": "cell-updates/s", "ms_per_step": el["ms_per_step"],
+                        "single_launch": {"value": el["single_launch"]["value"],
+                                          "ms_per_step": el["single_launch"]["ms_per_step"]},
+                        "gpu_launches": el["gpu_launches"], "finite": el["finite"]}
+        if args.adjoint_steps > 0:
+            a100 = measure_adjoint(args.adjoint_steps, 5, "f32", 512, 100)
+            a0 = measure_adjoint(args.adjoint_steps, 5, "f32", 512, 0)
+            adjoint = {"workload": a100["config"]["workload"], "steps": args.adjoint_steps,
+                       "ckpt_every": 100, "cost_ratio": a100["value"],
+                       "forward_ms_per_step": a100["forward_ms_per_step"],
+                       "adjoint_ms_per_step": a100["ms_per_step"],
+                       "every_step_kept": {"ckpt_every": 0, "cost_ratio": a0["value"],
+                                           "adjoint_ms_per_step": a0["ms_per_step"],
+                                           "scratch_gb": a0["config"]["scratch_gb"]},
+                       "grad_finite": a100["grad_finite"] and a0["grad_finite"],
+                       "what": "dL/dw0 and dL/dz of the 16-gauge misfit (forward with checkpoints, "
+                               "recomputation and reverse) over the forward steps alone, CUDA events"}
+
     if rank == 0:
         line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -526,6 +619,7 @@ def main():
                            "l2": "inputs larger than L2 (workspace %.0f MB > 129 MB)"
                                  % (sol.workspace.numel() / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "render": render,
+                "ensemble": ensemble, "adjoint": adjoint,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -258,6 +258,17 @@ cel_status cel_adjoint_gauge_misfit(cel_solver *s, int32_t nsteps, int32_t ckpt_
                                     size_t scratch_bytes, void *eta_dev, void *grad_w_dev, void *grad_z_dev,
                                     double *loss);
 
+/* dL/dw_in from the dL/dw0 that cel_adjoint_gauge_misfit returns, for the
+ * caller's w_in before cel_set_state clamped it to the bed (w0 = max(w_in,
+ * Bbar), the reading of Sec. 2.2's dry cells used by cel_set_state): the
+ * derivative is 1 where w_in lies above the cell bed Bbar and 0 where the
+ * clamp holds w0 at the bed (the one-sided derivative at a tie).  w_in_dev:
+ * [ny][nx] real, device, the values passed to cel_set_state; grad_w_dev:
+ * [ny][nx] real, device, dL/dw0 on entry and dL/dw_in on return (in place).
+ * Uses the solver's present bed.  Asynchronous on the handle's stream;
+ * CEL_ERR_INVALID_ARG for a NULL argument, CEL_ERR_CUDA on a launch error. */
+cel_status cel_adjoint_input_gradient(cel_solver *s, const void *w_in_dev, void *grad_w_dev);
+
 /* Self-check of the adjoint's face-flux derivative (Sec. 2.2, Eq. 14): the
  * reverse sweep uses a hand-written vector-Jacobian product of the KP07
  * reconstruction and central-upwind flux; this evaluates it beside the

@@ -13,8 +13,9 @@ each one are named in the test module docstrings):
   * KP07 NLSW path + dry front: Ritter dam-break closed form -- pinned
   * dispersion + tridiagonal + F*: linear dispersion relation -- pinned
   * depth-gradient terms of Eq. 10-11 and Eq. 23: linear shoaling on a
-    slope -- pinned;
-    those of F*, G* (Eq. 12-13): parity unpinned (they vanish in 1-D).
+    slope -- pinned; those of F*, G* (Eq. 12-13) and the cross terms of
+    Eq. 10-11, which vanish in 1-D: isotropy over a round shoal (eta along
+    the diagonals converges to eta along the axes) -- pinned.
   * mirror / transpose symmetry -- pinned
   * Thomas solver: dense solve -- pinned; Eckart, sponge, soliton -- pinned
   * friction + AB3 order: uniform-flow ODE -- pinned
@@ -23,8 +24,10 @@ each one are named in the test module docstrings):
   * sine maker: the wave it sends into a sponged channel is progressive,
     P = c eta with the model's dispersion relation, amplitude a, and its
     steady phase converged in dt (the stages' ghost times) -- pinned
-  * corner ghosts where two sine makers meet: parity unpinned (internal
-    consistency only; a maker beside a wall transposes exactly -- pinned).
+  * corner ghosts: beside a wall, exact embedding in a run twice as high
+    -- pinned; where two sine makers meet, the plane wave both send is kept
+    at the corner (phase steps and amplitude within a few per cent) --
+    pinned.
   * run-up tracking: standing-mode maximum, dry threshold -- pinned
   * tangent-linear oracle (celeris_tlm.cpp: this source on dual numbers):
     values bit for bit the oracle's, tangents vs central differences,

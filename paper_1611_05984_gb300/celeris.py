@@ -32,7 +32,8 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
            "cel_load_checkpoint", "cel_runup_enable", "cel_render", "cel_adjoint_bytes",
-           "cel_adjoint_gauge_misfit", "cel_adjoint_face_selfcheck", "cel_get_stats", "cel_last_launch_count", "cel_profile_enable",
+           "cel_adjoint_gauge_misfit", "cel_adjoint_face_selfcheck", "cel_adjoint_input_gradient",
+           "cel_get_stats", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = True):
         L.cel_adjoint_gauge_misfit.argtypes = [vp, i32, i32, ctypes.POINTER(i32), i32, vp, vp, sz, vp, vp, vp,
                                                ctypes.POINTER(d)]
         L.cel_adjoint_face_selfcheck.argtypes = [i32, vp, i32, vp, vp]
+        L.cel_adjoint_input_gradient.argtypes = [vp, vp, vp]
         L.cel_get_stats.argtypes = [vp, ctypes.POINTER(CelStats)]
         L.cel_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_profile_enable.argtypes = [vp, i32]
@@ -541,8 +543,9 @@ def _gauge_misfit_function():
             solver.set_state(w0, P0, Q0)
             out = gauge_misfit_gradient(solver, nsteps, gauges, obs, ckpt_every, bed=z is not None)
             loss, grad = out[0], out[2]
-            bed = solver.field("Bbar").to(grad.dtype)
-            grad = torch.where(w0.to(device=grad.device, dtype=grad.dtype) > bed, grad, torch.zeros_like(grad))
+            w_in = w0.to(device=grad.device, dtype=grad.dtype).contiguous()
+            solver._check(solver.L.cel_adjoint_input_gradient(solver._h, w_in.data_ptr(), grad.data_ptr()),
+                          "adjoint_input_gradient")
             grad_z = out[3] if z is not None else torch.zeros_like(grad)
             ctx.has_z = z is not None
             ctx.save_for_backward(grad, grad_z)

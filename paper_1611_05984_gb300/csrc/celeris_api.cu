@@ -2201,4 +2201,16 @@ cel_status cel_adjoint_gauge_misfit(cel_solver *s, int32_t nsteps, int32_t ckpt_
                                           (double *)grad_z_dev, loss);
 }
 
+cel_status cel_adjoint_input_gradient(cel_solver *s, const void *w_in_dev, void *grad_w_dev)
+{
+    if (!s) return CEL_ERR_INVALID_ARG;
+    if (!w_in_dev || !grad_w_dev) return fail(s, CEL_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = s->es == 4 ? launch_clamp_adjoint<float>(s->geo, s->at<float>(s->lay.Bc), (const float *)w_in_dev,
+                                                             (float *)grad_w_dev, s->stream)
+                               : launch_clamp_adjoint<double>(s->geo, s->at<double>(s->lay.Bc),
+                                                              (const double *)w_in_dev, (double *)grad_w_dev, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "adjoint input gradient");
+    return CEL_OK;
+}
+
 }  // extern "C"

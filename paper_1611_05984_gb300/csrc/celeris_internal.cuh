@@ -202,6 +202,9 @@ cudaError_t launch_set_state(const Geo &g, const Phys &p, const real *Bc, const 
 template <typename real>
 cudaError_t launch_clamp_state(const Geo &g, const Phys &p, const real *Bc, real *w, real *P,
                                real *Qc, cudaStream_t st);
+// dL/dw_in from dL/dw0 for w0 = max(w_in, Bbar): zero where clamped.
+template <typename real>
+cudaError_t launch_clamp_adjoint(const Geo &g, const real *Bc, const real *w_in, real *grad, cudaStream_t st);
 template <typename real>
 cudaError_t launch_get_state(const Geo &g, const real *w, const real *P, const real *Qc,
                              real *w_out, real *P_out, real *Q_out, cudaStream_t st);

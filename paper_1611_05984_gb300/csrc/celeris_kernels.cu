@@ -98,6 +98,18 @@ __global__ void k_clamp_state(Geo g, Phys p, const real *__restrict__ Bc, real *
     }
 }
 
+// Reading A-J3: w0 = max(w_in, Bbar) has derivative 1 in w_in where w_in
+// lies above the cell bed and 0 where the clamp holds w0 at the bed (the
+// one-sided derivative at a tie); grad ([ny][nx]) is masked in place.
+template <typename real>
+__global__ void k_clamp_adjoint(Geo g, const real *__restrict__ Bc, const real *__restrict__ w_in, real *grad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    size_t k = (size_t)j * g.nx + i;
+    if (!(w_in[k] > bbar_at(Bc, g, i, j))) grad[k] = real(0);
+}
+
 template <typename real>
 __global__ void k_get_state(Geo g, const real *w, const real *P, const real *Qc, real *w_out,
                             real *P_out, real *Q_out)
@@ -1234,6 +1246,14 @@ cudaError_t launch_clamp_state(const Geo &g, const Phys &p, const real *Bc, real
 }
 
 template <typename real>
+cudaError_t launch_clamp_adjoint(const Geo &g, const real *Bc, const real *w_in, real *grad, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    k_clamp_adjoint<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, Bc, w_in, grad);
+    return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_get_state(const Geo &g, const real *w, const real *P, const real *Qc, real *w_out,
                              real *P_out, real *Q_out, cudaStream_t st)
 {
@@ -1486,6 +1506,8 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
                                                 cudaStream_t);                                          \
     template cudaError_t launch_clamp_state<real>(const Geo &, const Phys &, const real *, real *, real *, \
                                                   real *, cudaStream_t);                                \
+    template cudaError_t launch_clamp_adjoint<real>(const Geo &, const real *, const real *, real *,      \
+                                                    cudaStream_t);                                      \
     template cudaError_t launch_get_state<real>(const Geo &, const real *, const real *, const real *,   \
                                                 real *, real *, real *, cudaStream_t);                  \
     template cudaError_t launch_get_field<real>(const Geo &, const Phys &, int, const real *,            \

@@ -187,6 +187,17 @@ def test_autograd_function_and_rejections():
     _, _, _, _, refz = _gpu_gradient(s, gauges, obs, ckpt=5, bed=True)
     np.testing.assert_allclose(zt.grad.cpu().numpy(), 3.0 * refz, rtol=1e-9, atol=1e-14)
     np.testing.assert_allclose(w1.grad.cpu().numpy(), 3.0 * want, rtol=1e-9, atol=1e-14)
+    # the clamp's derivative by itself (cel_adjoint_input_gradient): 1 above
+    # the cell bed, 0 below it and at a tie (the one-sided derivative)
+    bed_t = torch.as_tensor(bed, device="cuda")
+    w_in = bed_t + torch.tensor([-0.5, 0.0, 0.25], dtype=torch.float64, device="cuda").repeat(bed.size)[:bed.size] \
+        .reshape(bed.shape)
+    gin = torch.arange(1, bed.size + 1, dtype=torch.float64, device="cuda").reshape(bed.shape)
+    gout = gin.clone()
+    assert g.L.cel_adjoint_input_gradient(g._h, w_in.data_ptr(), gout.data_ptr()) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(gout, torch.where(w_in > bed_t, gin, torch.zeros_like(gin)))
+    assert g.L.cel_adjoint_input_gradient(g._h, None, gout.data_ptr()) == 1
     b = celeris.from_scenario(sc.beach(nx=64, ny=48, sponge=8), dtype=torch.float64)
     with pytest.raises(celeris.CelerisError):                       # a gauge off the grid
         celeris.gauge_misfit_gradient(b, 5, [(64, 3)], torch.zeros((5, 1), dtype=torch.float64))

@@ -14,6 +14,15 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "celeris_oracle.c")
 
+_FS = ("fs = dd * dxd * Qy / 6.0 + dd * dyd * Qx / 6.0 + B3 * dd * dd * Qxy;\n"
+       "                gs = dd * dyd * Px / 6.0 + dd * dxd * Py / 6.0 + B3 * dd * dd * Pxy;")
+_ETA = ("Bd * g * dd * dd * (dxd * (2.0 * exx + eyy) + dyd * exy);\n"
+        "                gg += Bd * g * dd * dd * dd * (eyyy + exxy) +\n"
+        "                      Bd * g * dd * dd * (dyd * (2.0 * eyy + exx) + dxd * exy);")
+_CORNER = ("        for (int i = -2; i < nx + 2; i++)\n"
+           "            for (int k = 0; k < 2; k++) {\n"
+           "                int gj")
+
 MUTANTS = [
     # (name, original text, mutated text, pin that must fail)
     ("drop_Fstar", "fs = dd * dxd * Qy / 6.0 + dd * dyd * Qx / 6.0 + B3 * dd * dd * Qxy;",
@@ -76,6 +85,27 @@ MUTANTS = [
      "else if (wet) o->maxw[k] = o->w[c];", "test_runup_tracking_standing_mode"),
     ("runup_no_threshold", "int wet = o->w[c] - o->Bbar[c] > o->delta;", "int wet = 1;",
      "test_runup_tracking_threshold_and_dry_land"),
+    # depth-gradient terms that vanish in 1-D (F*, G* of Eq. 12-13; the
+    # cross terms of Eq. 10-11), changed alike in both momentum equations
+    # so that the transpose symmetry still holds: the isotropy pin
+    ("Fstar_dxQy_dyPx_dropped", _FS, _FS.replace("dd * dxd * Qy / 6.0 + ", "").replace("dd * dyd * Px / 6.0 + ", ""),
+     "test_isotropy_over_a_round_shoal"),
+    ("Fstar_dyQx_dxPy_dropped", _FS, _FS.replace(" + dd * dyd * Qx / 6.0", "").replace(" + dd * dxd * Py / 6.0", ""),
+     "test_isotropy_over_a_round_shoal"),
+    ("Fstar_sixth_as_third", _FS, _FS.replace("/ 6.0", "/ 3.0"), "test_isotropy_over_a_round_shoal"),
+    ("Fstar_dxd_dyd_swapped", "fs = dd * dxd * Qy / 6.0 + dd * dyd * Qx / 6.0",
+     "fs = dd * dyd * Qy / 6.0 + dd * dxd * Qx / 6.0", "test_isotropy_over_a_round_shoal"),
+    ("eta_dx_eyy_dropped", _ETA, _ETA.replace("(2.0 * exx + eyy)", "(2.0 * exx)").replace("(2.0 * eyy + exx)",
+                                                                                        "(2.0 * eyy)"),
+     "test_isotropy_over_a_round_shoal"),
+    ("eta_dy_exy_dropped", _ETA, _ETA.replace(" + dyd * exy)", ")").replace(" + dxd * exy)", ")"),
+     "test_isotropy_over_a_round_shoal"),
+    # corner ghosts (Reading A-B5): the y-sides filled over interior columns
+    # only, so the corner ghosts keep stale values
+    ("corner_ghosts_stale_two_makers", _CORNER, _CORNER.replace("int i = -2; i < nx + 2;", "int i = 0; i < nx;"),
+     "test_corner_ghosts_where_two_makers_meet"),
+    ("corner_ghosts_stale_beside_wall", _CORNER, _CORNER.replace("int i = -2; i < nx + 2;", "int i = 0; i < nx;"),
+     "test_corner_ghost_of_a_maker_beside_a_wall_by_embedding"),
 ]
 
 

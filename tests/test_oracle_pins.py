@@ -15,6 +15,10 @@ an invariant, a textbook routine, a special case or a convergence order.
   NLSW path, dry front                    Ritter closed form        test_ritter_*
   dispersion terms, tridiagonal, F*, G*   linear dispersion relation test_dispersion_*
   depth-gradient terms of Eq. 10-11       linear shoaling           test_linear_shoaling_*
+  depth-gradient terms of F*, G* and      isotropy over a round     test_isotropy_*
+  the cross terms of Eq. 10-11            shoal (axes vs diagonals)
+  corner ghosts (Reading A-B5)            embedding beside a wall;  test_corner_ghost*
+                                          plane wave of two makers
   NLSW reduction at d = 0 (Sec. 2.1)      the two models agree       test_boussinesq_reduces_*
   ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
   positivity fix, dry clamp               symmetry with wet-dry fronts test_symmetry_mirror_x_wet_dry
@@ -732,3 +736,143 @@ def test_time_stepping_formulas_step_by_step(oracle_mod, K):
     if K >= 1:   # and not the predictor alone: the corrector moved the value
         ab3 = P[2] + dt / 12 * (23 * F(P[2]) - 16 * F(P[1]) + 5 * F(P[0]))
         assert abs(P[3] - ab3) > 1e-9
+
+
+# ------------------------------------------------ isotropy and corner ghosts
+
+def _radial_anisotropy(oracle_mod, dx, R=4.0, dc=0.5, slope=0.3, sig=0.5, a=0.005, T=0.7):
+    """A Gaussian hump at rest over a round shoal whose depth grows with the
+    radius (d = dc + slope sqrt(r^2 + 1/4)), on a square grid centred on one
+    cell, walls far enough that the wave has not reached them at T.  Returns
+    (mismatch between eta along the diagonals and eta along the axes at the
+    same radius, relative L2; the largest spread between the four axes and
+    between the four diagonals, relative)."""
+    from scipy.interpolate import CubicSpline
+    n = int(round(2 * R / dx)) | 1
+    c = n // 2
+    x = (np.arange(n) - c) * dx
+    X, Y = np.meshgrid(x, x)
+    r = np.hypot(X, Y)
+    d = dc + slope * np.sqrt(r ** 2 + 0.25)
+    dt = 0.2 * dx / math.sqrt(G * d.max())
+    o = oracle_mod.Oracle(-d, dx, dx, dt, K=1, eps=1e-8)
+    o.set_state(a * np.exp(-r ** 2 / sig ** 2), 0 * r, 0 * r)
+    o.step(int(round(T / dt)))
+    w = o.state()[0]
+    k = np.arange(c + 1)
+    axes = [w[c, c + k], w[c, c - k], w[c + k, c], w[c - k, c]]
+    diags = [w[c + k, c + k], w[c - k, c - k], w[c + k, c - k], w[c - k, c + k]]
+    top = np.abs(axes[0]).max()
+    spread = max(max(np.abs(v - axes[0]).max() for v in axes), max(np.abs(v - diags[0]).max() for v in diags)) / top
+    ra, rd = k * dx, k * dx * math.sqrt(2.0)
+    along = CubicSpline(ra, axes[0])
+    m = rd <= 0.9 * ra[-1]
+    mismatch = np.linalg.norm(diags[0][m] - along(rd[m])) / np.linalg.norm(along(rd[m]))
+    return mismatch, spread
+
+
+def test_isotropy_over_a_round_shoal(oracle_mod):
+    """The equations are isotropic (Eq. 2-3, 7-13): with M = (P, Q) the
+    depth-gradient terms of the momentum equations are
+    d [grad d (div M) + (grad M)^T grad d] / 6 under the time derivative (the
+    1/3 of Eq. 7 and the two 1/6 of Eq. 12), and B g d^2 [grad d lap eta +
+    hess(eta) grad d] (Eq. 10-11).  So a radially symmetric problem has a
+    radially symmetric solution, and on the grid eta along the diagonals must
+    approach eta along the axes as the grid is refined.  On a round shoal
+    every depth-gradient term of F*, G* and of Eq. 10-11 is active: dropping
+    one, or weighting it 1/3 instead of 1/6, leaves an anisotropy that does
+    not shrink with the grid (measured: 0.013-0.026 at dx = 0.025, where this
+    oracle gives 0.004, converging from 0.008 at dx = 0.05).  The four axes
+    (and the four diagonals) agree to rounding by the grid's own symmetry."""
+    coarse, s1 = _radial_anisotropy(oracle_mod, 0.05)
+    fine, s2 = _radial_anisotropy(oracle_mod, 0.025)
+    assert s1 <= 1e-12 and s2 <= 1e-12
+    assert fine <= 6.5e-3, (coarse, fine)
+    assert fine <= 0.65 * coarse, (coarse, fine)
+
+
+def test_corner_ghost_of_a_maker_beside_a_wall_by_embedding(oracle_mod):
+    """Corner ghosts (Reading A-B5) where a sine maker meets a wall.  The
+    face-centred wall at y = 0 (Reading A-B1) is an even mirror: a run on
+    the upper half with a south wall is exactly the upper half of a run on a
+    domain twice as high whose bed, state and west maker are even about the
+    middle (two components at +-theta, phased so that their sum is even:
+    Eq. 25-28).  The corner ghost at (-1, -1) that the half run builds (the
+    mirror of the maker's ghost beside it, Q negated) is what the doubled run
+    holds there; cell (0, 0)'s mixed derivatives read it."""
+    nx, m, dx, d0, T, a, th = 64, 32, 0.25, 1.0, 3.0, 0.01, 0.5
+    rng = np.random.default_rng(21)
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(m) + 0.5) * dx)
+    # flat beside the maker (its wave number follows the depth there), a
+    # shoal, a slope and noise beyond
+    z = -d0 + (0.3 * np.exp(-((X - 9.0) ** 2 + (Y - 3.0) ** 2) / 4.0) + 0.02 * (X - 3.0)
+               + 0.05 * rng.standard_normal(X.shape)) * (X > 3.0)
+    z_big = np.vstack([z[::-1], z])
+    dt = 0.1 * dx / math.sqrt(G * d0)
+    k = oracle_mod.eckart_k(2 * math.pi / T, d0)
+    ymid = m * dx
+
+    def run(zz, comps, south):
+        o = oracle_mod.Oracle(zz, dx, dx, dt, K=1, eps=1e-8)
+        o.set_boundary(oracle_mod.W, oracle_mod.SINE, 0, comps)
+        o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, 12)
+        o.set_boundary(oracle_mod.S, south)
+        o.set_state(0 * zz, 0 * zz, 0 * zz)
+        o.step(400)
+        return o.state()
+
+    half = run(z, ((a, T, th, 0.0), (a, T, -th, 0.0)), oracle_mod.SOLID)
+    big = run(z_big, ((a, T, th, k * math.sin(th) * ymid), (a, T, -th, -k * math.sin(th) * ymid)),
+              oracle_mod.SOLID)
+    wh, Ph, Qh = half
+    wb, Pb, Qb = (v[m:] for v in big)
+    assert np.max(np.abs(wh)) > 0.005
+    scale = np.max(np.abs(Ph))
+    assert np.max(np.abs(wh - wb)) <= 1e-11 * np.max(np.abs(wh))
+    assert np.max(np.abs(Ph - Pb)) <= 1e-11 * scale and np.max(np.abs(Qh - Qb)) <= 1e-11 * scale
+
+
+def test_corner_ghosts_where_two_makers_meet(oracle_mod):
+    """Corner ghosts (Reading A-B5) where two sine makers meet: west and
+    south makers sending the same plane wave at 45 degrees over a flat bed
+    (Eq. 25-28), sponges east and north.  Both makers' formulas give the
+    same value at the corner ghost, the plane wave there.  The run is its
+    own transpose (x <-> y, P <-> Q) up to 1e-4: at the far corners, inside
+    the sponges, a maker meets a sponge side, and there the x-sides-first
+    composition gives the mirror of the west maker's ghost at the north-west
+    corner but the south maker's own value at the south-east one (measured
+    2.6e-5 of the amplitude).  The complex amplitude of eta near
+    the corner follows the plane wave: the phase step between neighbouring
+    cells and the amplitude at the corner cell stay within a few per cent of
+    the values far from the corner (what differs is the makers' boundary
+    layer, from Eckart's wave number against the model's).  A corner ghost
+    left unset (or set to still water) breaks both by 10-20 %: cell (0, 0)'s
+    mixed derivatives (Eq. 10-13) read it."""
+    n, dx, d0, T, a, th = 160, 0.05, 0.5, 1.5, 0.002, math.pi / 4
+    z = np.full((n, n), -d0)
+    dt = 0.2 * dx / math.sqrt(G * d0)
+    o = oracle_mod.Oracle(z, dx, dx, dt, K=1, eps=1e-8)
+    comps = ((a, T, th, 0.0),)
+    o.set_boundary(oracle_mod.W, oracle_mod.SINE, 0, comps)
+    o.set_boundary(oracle_mod.S, oracle_mod.SINE, 0, comps)
+    o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, 40)
+    o.set_boundary(oracle_mod.N, oracle_mod.SPONGE, 40)
+    m = 12
+    steps = int(round(8 * T / dt))
+    o.set_gauges([(i, j) for j in range(m) for i in range(m)], 1, steps)
+    o.step(steps)
+    w, P, Q = o.state()
+    assert np.max(np.abs(w - w.T)) <= 1e-4 * np.max(np.abs(w))
+    assert np.max(np.abs(P - Q.T)) <= 1e-4 * np.max(np.abs(P))
+    rec = o.read_gauges(steps)
+    t = dt * np.arange(1, steps + 1)
+    last = t > 5 * T
+    om = 2 * math.pi / T
+    M = np.stack([np.sin(om * t[last]), np.cos(om * t[last]), np.ones(last.sum())], 1)
+    coef = np.linalg.lstsq(M, rec[last], rcond=None)[0]
+    A = (coef[0] + 1j * coef[1]).reshape(m, m)        # A[j, i]
+    rx, ry = A[:, 1:] / A[:, :-1], A[1:, :] / A[:-1, :]
+    far_rx, far_ry = rx[6:, 6:].mean(), ry[6:, 6:].mean()
+    assert np.abs(rx[6:, 6:] - far_rx).max() <= 0.01          # a plane wave far from the corner
+    assert np.abs(rx[:3, :3] - far_rx).max() <= 0.05 and np.abs(ry[:3, :3] - far_ry).max() <= 0.05
+    assert abs(A[0, 0]) >= 0.87 * np.abs(A[6:, 6:]).mean()
