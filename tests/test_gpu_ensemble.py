@@ -189,3 +189,33 @@ def test_ensemble_256_uneven_scenarios_stay_finite():
     ens.step(300)
     for m in members:
         assert m.check_finite()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_ensemble_members_match_the_oracle(prec):
+    """Members of the ensemble against the FP64 oracle directly (not only
+    against single-grid runs): four uneven beaches of the seeded ensemble
+    generator and the soliton channel, stepped together 300 steps, each
+    compared with its own oracle run every 100 steps (relative L2 of eta,
+    FP64 <= 1e-10, FP32 <= 1e-4; P and Q within ten times that)."""
+    from paper_1611_05984_gb300 import celeris
+    from tests.helpers import oracle_from, rel_l2
+    tol = {"f64": 1e-10, "f32": 1e-4}[prec]
+    scens = sc.ensemble(n=4, seed=13, K=1, nx_range=(96, 420), ny_range=(64, 260))
+    scens.append(sc.soliton_channel(nx=250, ny=30, K=1, x0=5.0))
+    members = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    oracles = [oracle_from(s) for s in scens]
+    ens = celeris.Ensemble(members, stream=members[0].stream)
+    for done in (100, 200, 300):
+        ens.step(100)
+        torch.cuda.synchronize()
+        for k, (s, m, o) in enumerate(zip(scens, members, oracles)):
+            o.step(100)
+            wo, Po, Qo = o.state()
+            wg, Pg, Qg = (a.double().cpu().numpy() for a in m.state())
+            e = rel_l2(wg - s.ws, wo - s.ws)
+            assert e <= tol, f"member {k} ({s.name}): eta rel-L2 {e:.3e} at step {done}"
+            for a, b, name in ((Pg, Po, "P"), (Qg, Qo, "Q")):
+                if np.linalg.norm(b) > 1e-12:
+                    assert rel_l2(a, b) <= 10 * tol, f"member {k}: {name} at step {done}"
+    ens.close()

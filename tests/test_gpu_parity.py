@@ -308,3 +308,86 @@ def test_poisoned_workspace_reads_nothing_unwritten(prec, case):
     wo, _, _ = o.state()
     wg = _np(g.state()[0])
     assert rel_l2(wg - s.ws, wo - s.ws) <= TOL[prec]
+
+
+def _waves_everywhere(s, seed):
+    """A smooth seeded wave field over the whole wet domain (so that every
+    line's solve has a non-zero right side), with the discharge of waves
+    travelling both ways."""
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid((np.arange(s.nx) + 0.5) * s.dx, (np.arange(s.ny) + 0.5) * s.dy)
+    w = np.zeros_like(X)
+    P = np.zeros_like(X)
+    Q = np.zeros_like(X)
+    for _ in range(4):
+        L = rng.uniform(40.0, 120.0)
+        th = rng.uniform(0.0, 2 * math.pi)
+        ph = rng.uniform(0.0, 2 * math.pi)
+        e = 0.05 * np.sin(2 * math.pi * (X * math.cos(th) + Y * math.sin(th)) / L + ph)
+        w += e
+        P += 0.3 * math.cos(th) * e
+        Q += 0.3 * math.sin(th) * e
+    wet = s.z < -0.5
+    s.w0 = np.where(wet, w, s.ws)
+    s.P0 = np.where(wet, P, 0.0)
+    s.Q0 = np.where(wet, Q, 0.0)
+    return s
+
+
+def _transposed(s):
+    """The same problem with x and y exchanged (bed, state, sides, the
+    makers' directions)."""
+    import copy
+    t = copy.copy(s)
+    t.nx, t.ny, t.dx, t.dy = s.ny, s.nx, s.dy, s.dx
+    t.z = np.ascontiguousarray(s.z.T)
+    t.w0 = None if s.w0 is None else np.ascontiguousarray(s.w0.T)
+    t.P0 = None if s.Q0 is None else np.ascontiguousarray(s.Q0.T)
+    t.Q0 = None if s.P0 is None else np.ascontiguousarray(s.P0.T)
+    swap = {sc.W: sc.S, sc.E: sc.N, sc.S: sc.W, sc.N: sc.E}
+    t.sides = {}
+    for side, sd in s.sides.items():
+        comps = tuple((a, T, math.pi / 2 - th, ph) for (a, T, th, ph) in sd.comps)
+        t.sides[swap[side]] = sc.Side(sd.type, sd.width, comps)
+    t.name = s.name + "_T"
+    return t
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("shape", ["5000x8", "8x5000", "4500x40"])
+def test_long_lines_32_row_segments(prec, shape):
+    """Lines longer than 4096 cells (Eq. 21-22), which the line solver cuts
+    into 32-row segments with two threads per segment: x-lines of 5000 and
+    4500 cells, y-lines of 5000 (the transposed beach), against the oracle.
+    Beach and shoals with the west (south) sine maker, sponges on the short
+    sides, Manning friction, K = 1, and a seeded wave field over the whole
+    wet domain so that every line has work from the first step."""
+    nx, ny = (int(v) for v in shape.split("x"))
+    long_x = nx >= ny
+    L, Wd = (nx, ny) if long_x else (ny, nx)
+    s = sc.beach(nx=L, ny=Wd, sponge=2 if Wd < 16 else 5, nshoal=3, seed=11)
+    s = _waves_everywhere(s, 5)
+    if not long_x:
+        s = _transposed(s)
+    assert (s.nx, s.ny) == (nx, ny)
+    _lockstep(s, prec, 300, every=100)
+
+
+def test_full_size_beach_from_rest():
+    """The 2048 x 2048 beach (the benchmark's workload and launch
+    configuration) from t = 0, FP64 and FP32 against one oracle run over 300
+    steps, eta, P and Q compared every 100 steps."""
+    s = sc.beach(nx=2048, ny=2048)
+    o = oracle_from(s)
+    g = {p: _solver(s, p) for p in ("f64", "f32")}
+    for done in (100, 200, 300):
+        o.step(100)
+        wo, Po, Qo = o.state()
+        for p, sol in g.items():
+            sol.step(100)
+            wg, Pg, Qg = (_np(a) for a in sol.state())
+            e = rel_l2(wg - s.ws, wo - s.ws)
+            assert e <= TOL[p], f"{p}: eta rel-L2 {e:.3e} at step {done}"
+            assert rel_l2(Pg, Po) <= 10 * TOL[p], f"{p}: P at step {done}"
+            assert rel_l2(Qg, Qo) <= 10 * TOL[p], f"{p}: Q at step {done}"
+    assert np.max(np.abs(wo[:, :40])) > 0.1            # the maker's waves are in
