@@ -326,13 +326,29 @@ cel_status cel_profile_disable(cel_solver *s);
  * checkpoints, cel_set_boundary: the ensemble rebuilds its tables when a
  * boundary or bed changed).  Gauges of members are logged as under cel_step.
  * Two ensembles (or an ensemble and cel_step) that share a member must not
- * overlap on the GPU. */
+ * overlap on the GPU.
+ *
+ * Captured cycles: once the members' history is full (two steps after the
+ * state was set), the argument blocks of a step repeat every 6 steps.  Where
+ * no member logs gauges or tracks run-up and profiling is off,
+ * cel_ensemble_step records 6 steps as one CUDA graph (on a stream of the
+ * library's own, the first time a cycle starts at a given phase; every
+ * argument block of the cycle uploaded beforehand) and replays it on
+ * cuda_stream for each further 6 steps: the same kernels with the same
+ * arguments, so the results are bit for bit those of launching them one by
+ * one.  The ghost tables' step index then comes from a counter in the table
+ * that the graph advances.  A change of boundary or bed, or a new argument
+ * block, discards the graphs.  cel_ensemble_use_graphs(e, 0) launches every
+ * step one kernel at a time (the default is 1). */
 typedef struct cel_ensemble cel_ensemble;     /* opaque, owned by the library (host) */
 cel_status cel_ensemble_table_bytes(cel_solver *const *members, int32_t n, size_t *bytes);
 cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *table_dev,
                                size_t table_bytes, void *cuda_stream,
                                cel_ensemble **out, char *msg, size_t msg_len);
 cel_status cel_ensemble_step(cel_ensemble *e, int32_t nsteps);
+cel_status cel_ensemble_use_graphs(cel_ensemble *e, int32_t enable);
+/* Steps taken by replaying a captured cycle since cel_ensemble_create. */
+cel_status cel_ensemble_graph_steps(const cel_ensemble *e, int64_t *steps);
 /* Kernel launches issued by the most recent cel_ensemble_step call. */
 cel_status cel_ensemble_last_launch_count(const cel_ensemble *e, int64_t *launches);
 /* Per-kernel event timing of the ensemble's launches, as cel_profile_* for a

@@ -35,7 +35,8 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_adjoint_gauge_misfit", "cel_adjoint_face_selfcheck", "cel_adjoint_input_gradient",
            "cel_get_stats", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
-           "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_last_launch_count",
+           "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_use_graphs", "cel_ensemble_graph_steps",
+           "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
            "cel_ensemble_last_error", "cel_ensemble_destroy", "cel_advance_noalloc", "cel_status_string",
            "cel_last_error", "cel_destroy"]
@@ -119,6 +120,8 @@ def load(build_if_missing: bool = True):
         L.cel_ensemble_create.argtypes = [ctypes.POINTER(vp), i32, vp, sz, vp, ctypes.POINTER(vp),
                                           ctypes.c_char_p, sz]
         L.cel_ensemble_step.argtypes = [vp, i32]
+        L.cel_ensemble_use_graphs.argtypes = [vp, i32]
+        L.cel_ensemble_graph_steps.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_ensemble_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_ensemble_profile_enable.argtypes = [vp, i32]
         L.cel_ensemble_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
@@ -421,9 +424,22 @@ class Ensemble:
         if st != CEL_OK:
             raise CelerisError(st, self.L.cel_ensemble_last_error(self._h).decode())
 
+    def use_graphs(self, enable: bool = True):
+        """Replay captured 6-step cycles (the default) or launch every step
+        kernel by kernel (cel_ensemble_use_graphs)."""
+        st = self.L.cel_ensemble_use_graphs(self._h, int(bool(enable)))
+        if st != CEL_OK:
+            raise CelerisError(st, "cel_ensemble_use_graphs failed")
+
     def last_launch_count(self) -> int:
         v = ctypes.c_int64()
         self.L.cel_ensemble_last_launch_count(self._h, ctypes.byref(v))
+        return v.value
+
+    def graph_steps(self) -> int:
+        """Steps taken by replaying a captured 6-step cycle since creation."""
+        v = ctypes.c_int64()
+        self.L.cel_ensemble_graph_steps(self._h, ctypes.byref(v))
         return v.value
 
     def profile_enable(self, capacity: int):

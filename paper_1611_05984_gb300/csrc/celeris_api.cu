@@ -206,7 +206,6 @@ struct cel_solver {
     int cur;      // w buffer of the state (w alternates per stage)
     int pcur;     // P / Q buffer of the state (alternates per step)
     int64_t step, nh;
-    int nseg_x, nseg_y;
     // gauges
     int32_t *gij;
     unsigned char *gring;
@@ -361,9 +360,11 @@ LineArgs<real> line_args(const cel_solver *s, const Coef<real> &coef, int dir, i
     l.nlines = dir == 0 ? s->geo.ny : s->geo.nx;
     l.pitch = dir == 0 ? s->geo.px : s->geo.py;
     l.nwords = dir == 0 ? s->geo.nwx : s->geo.nwy;
-    l.nseg = dir == 0 ? s->nseg_x : s->nseg_y;
-    l.mshift = line_seg_shift(l.n, s->es);
-    l.sp = line_seg_stride(l.nseg);
+    const LineCfg lc = line_config(l.n, s->es);
+    l.algo = lc.algo;
+    l.nseg = lc.nseg;
+    l.mshift = lc.mshift;
+    l.sp = lc.sp;
     l.final_stage = stage == Kn;
     l.identity = s->params.model == CEL_NLSW;
     return l;
@@ -440,8 +441,7 @@ cel_status step_t(cel_solver *s, int nsteps)
             int pl = prof_begin(s, 1);
             CEL_CUDA(s, launch_lines<real>(lp, s->stream), "line solves");
             prof_end(s, pl);
-            if (lp.L[0].mshift != lp.L[1].mshift) launches += 1;   // two segment lengths: two launches
-            launches += 2;
+            launches += 1 + line_launches(lp.L[0].nlines, lp.L[0].n, lp.L[1].nlines, lp.L[1].n, s->es);
             if (s->capture && stage < Kn) {
                 real *dst = reinterpret_cast<real *>(s->capture + s->capture_field * 3 * stage);
                 const size_t f = s->capture_field / sizeof(real);
@@ -569,8 +569,6 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->phy.fcoef = params->fric_coef;
     memset(&s->bnd, 0, sizeof(s->bnd));
     for (int k = 0; k < 4; k++) s->bnd.s[k].type = kSolid;
-    s->nseg_x = line_segments(G.nx, s->es);
-    s->nseg_y = line_segments(G.ny, s->es);
     s->gij = nullptr;
     s->gring = nullptr;
     s->ng = s->log_every = s->cap = s->nrec = s->head = 0;
@@ -1161,8 +1159,6 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.phy.fcoef = params->fric_coef;
     memset(&s.bnd, 0, sizeof(s.bnd));
     for (int k = 0; k < 4; k++) s.bnd.s[k].type = kSolid;
-    s.nseg_x = line_segments(G.nx, s.es);
-    s.nseg_y = line_segments(G.ny, s.es);
     s.gij = nullptr;
     s.gring = nullptr;
     s.ng = s.log_every = s.cap = s.nrec = s.head = 0;
@@ -1207,9 +1203,10 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
 // were stepped alone.
 
 struct cel_ensemble {
-    struct Group {            // line families of one segment length and block size
-        int mshift, first, nfam, blocks, threads;
-        size_t smem, off_desc;
+    struct Group {            // line families of one line-solver configuration
+        LineCfg cfg;
+        int first, nfam, blocks;
+        size_t off_desc;
     };
     std::vector<cel_solver *> m;
     int es, K;
@@ -1232,6 +1229,26 @@ struct cel_ensemble {
     int64_t launches;
     EventProf prof;
     std::string err;
+    // Captured cycles: once the history is full the argument blocks repeat
+    // every 6 steps, so 6 steps captured as one graph replay as they are;
+    // one graph per phase of the cycle it starts at (key of member 0).
+    struct Graph {
+        uint64_t key;
+        cudaGraphExec_t exec;
+        int64_t launches;
+    };
+    std::vector<Graph> graphs;
+    bool use_graphs = true;
+    int64_t graph_steps = 0;             // steps taken by replaying a graph, since creation
+    cudaStream_t cap_stream = nullptr;   // the library's own stream, for capture only
+    size_t off_kdev = 0;                 // device step counter of the ghost tables
+    int64_t kdev_val = 0;                // its value once the queued work has run
+    bool kdev_known = false;
+    void drop_graphs()
+    {
+        for (Graph &g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+    }
 };
 
 namespace {
@@ -1241,7 +1258,8 @@ struct EnsPlan {
     std::vector<std::pair<int, int>> fam;
     std::vector<cel_ensemble::Group> groups;
     std::vector<int> gmem;
-    size_t off_tile_desc = 0, off_gargs = 0, off_gstart = 0, sarg_bytes = 0, entry_bytes = 0, off_entries = 0;
+    size_t off_tile_desc = 0, off_gargs = 0, off_gstart = 0, off_kdev = 0, sarg_bytes = 0, entry_bytes = 0,
+           off_entries = 0;
     int cap = 0;
     size_t total = 0;
 };
@@ -1259,40 +1277,45 @@ void plan_t(cel_solver *const *ms, int n, EnsPlan &P)
     for (int e = 0; e < n; e++)
         P.tiles += ((ms[e]->geo.nx + kTile - 1) / kTile) * ((ms[e]->geo.ny + kTile - 1) / kTile);
     P.off_tile_desc = take(sizeof(int2) * (size_t)P.tiles);
-    // line families grouped by segment length and block size (one launch
+    // line families grouped by their solver configuration (one launch
     // each), longest lines first within a group
     P.fam.clear();
     P.groups.clear();
     auto len_of = [&](const std::pair<int, int> &f) { return f.second == 0 ? ms[f.first]->geo.nx : ms[f.first]->geo.ny; };
-    auto seg_of = [&](const std::pair<int, int> &f) { return f.second == 0 ? ms[f.first]->nseg_x : ms[f.first]->nseg_y; };
-    for (int sh = 1; sh <= 5; sh++)
-        for (int th = 32; th <= 1024; th += 32) {
-            std::vector<std::pair<int, int>> g;
-            for (int e = 0; e < n; e++)
-                for (int dir = 0; dir < 2; dir++) {
-                    const std::pair<int, int> f(e, dir);
-                    if (line_seg_shift(len_of(f), ms[e]->es) == sh && line_threads(len_of(f), ms[e]->es) == th)
-                        g.push_back(f);
-                }
-            if (g.empty()) continue;
-            std::stable_sort(g.begin(), g.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
-                return len_of(a) > len_of(b);
-            });
-            cel_ensemble::Group G;
-            G.mshift = sh;
-            G.threads = th;
-            G.first = (int)P.fam.size();
-            G.nfam = (int)g.size();
-            G.blocks = 0;
-            G.smem = 0;
-            for (auto &f : g) {
-                G.blocks += f.second == 0 ? ms[f.first]->geo.ny : ms[f.first]->geo.nx;
-                G.smem = std::max(G.smem, line_smem_bytes<real>(len_of(f), seg_of(f)));
-                P.fam.push_back(f);
+    // register-path lines of one block size share a launch whatever their
+    // segment length; shared-memory ones need one segment length too
+    auto same = [](const LineCfg &a, const LineCfg &b) {
+        return a.algo == b.algo && a.threads == b.threads && (a.algo == 0 || a.mshift == b.mshift);
+    };
+    std::vector<std::pair<int, int>> all;
+    for (int e = 0; e < n; e++)
+        for (int dir = 0; dir < 2; dir++) all.push_back(std::pair<int, int>(e, dir));
+    std::vector<char> taken(all.size(), 0);
+    for (size_t a = 0; a < all.size(); a++) {
+        if (taken[a]) continue;
+        const LineCfg ca = line_config(len_of(all[a]), (int)sizeof(real));
+        std::vector<std::pair<int, int>> g;
+        for (size_t b = a; b < all.size(); b++)
+            if (!taken[b] && same(ca, line_config(len_of(all[b]), (int)sizeof(real)))) {
+                g.push_back(all[b]);
+                taken[b] = 1;
             }
-            G.off_desc = take(sizeof(int2) * (size_t)G.blocks);
-            P.groups.push_back(G);
+        std::stable_sort(g.begin(), g.end(), [&](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+            return len_of(x) > len_of(y);
+        });
+        cel_ensemble::Group G;
+        G.cfg = ca;
+        G.first = (int)P.fam.size();
+        G.nfam = (int)g.size();
+        G.blocks = 0;
+        for (auto &f : g) {
+            G.blocks += f.second == 0 ? ms[f.first]->geo.ny : ms[f.first]->geo.nx;
+            G.cfg.smem = std::max(G.cfg.smem, line_config(len_of(f), (int)sizeof(real)).smem);
+            P.fam.push_back(f);
         }
+        G.off_desc = take(sizeof(int2) * (size_t)G.blocks);
+        P.groups.push_back(G);
+    }
     P.gmem.clear();
     P.gblocks = 0;
     for (int e = 0; e < n; e++) {
@@ -1305,6 +1328,7 @@ void plan_t(cel_solver *const *ms, int n, EnsPlan &P)
     }
     P.off_gargs = take(sizeof(GhostArgs<real>) * (size_t)n);
     P.off_gstart = take(sizeof(int) * (size_t)(n + 1));
+    P.off_kdev = take(sizeof(int64_t));
     P.sarg_bytes = align256(sizeof(StencilArgs<real>) * (size_t)n);
     P.entry_bytes = P.sarg_bytes + align256(sizeof(LineArgs<real>) * P.fam.size());
     // the argument blocks repeat every 6 steps once the AB3 history is full
@@ -1357,11 +1381,13 @@ cel_status ens_fail(cel_ensemble *e, cel_status st, const std::string &msg)
         if (e_ != cudaSuccess) return ens_fail(e, CEL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-uint64_t ens_key(const cel_solver *s, int stage)
+uint64_t ens_key_of(int64_t nh, int cur, int pcur, int stage)
 {
-    const uint64_t nhk = s->nh < 2 ? (uint64_t)s->nh : 2 + (uint64_t)((s->nh - 2) % 6);
-    return (nhk << 16) | ((uint64_t)s->cur << 9) | ((uint64_t)s->pcur << 8) | (uint64_t)stage;
+    const uint64_t nhk = nh < 2 ? (uint64_t)nh : 2 + (uint64_t)((nh - 2) % 6);
+    return (nhk << 16) | ((uint64_t)cur << 9) | ((uint64_t)pcur << 8) | (uint64_t)stage;
 }
+
+uint64_t ens_key(const cel_solver *s, int stage) { return ens_key_of(s->nh, s->cur, s->pcur, stage); }
 
 // Index of the table entry holding the arguments of this stage for the
 // members' present state; built and uploaded if missing (stream-ordered, so
@@ -1376,6 +1402,7 @@ cel_status ens_entry(cel_ensemble *e, int stage, int Kn, int *idx)
             return CEL_OK;
         }
     if ((int)e->keys.size() >= e->cap) e->keys.clear();
+    e->drop_graphs();   // the captured graphs read entries by their index
     const int k = (int)e->keys.size();
     const int n = (int)e->m.size();
     std::vector<unsigned char> host(e->entry_bytes, 0);
@@ -1396,111 +1423,245 @@ cel_status ens_entry(cel_ensemble *e, int stage, int Kn, int *idx)
     return CEL_OK;
 }
 
+// Before a step: the members in lockstep, the tables rebuilt after a change
+// of boundary or bed, the ghost tables' arguments and Eckart tables current.
+template <typename real>
+cel_status ens_prepare(cel_ensemble *e, int64_t &launches)
+{
+    const int n = (int)e->m.size();
+    const cel_solver *m0 = e->m[0];
+    uint64_t gsum = 0;
+    for (int j = 0; j < n; j++) {
+        const cel_solver *s = e->m[j];
+        if (s->nh != m0->nh || s->cur != m0->cur || s->pcur != m0->pcur)
+            return ens_fail(e, CEL_ERR_INVALID_ARG,
+                            "members are not in lockstep (set their states together, then step the ensemble)");
+        gsum += s->gen;
+    }
+    if (gsum != e->gen_sum) {      // a boundary or bed changed: rebuild every table
+        e->keys.clear();
+        e->drop_graphs();
+        e->gvalid = false;
+        e->gen_sum = gsum;
+    }
+    if (e->gvalid && !e->gmem.empty()) {        // members moved on outside the ensemble?
+        const int64_t k0 = e->m[e->gmem[0]]->step - e->gstep0[0];
+        for (size_t g = 0; g < e->gmem.size(); g++)
+            if (e->m[e->gmem[g]]->step - e->gstep0[g] != k0) e->gvalid = false;
+    }
+    if (!e->gvalid) {                           // members with a sine maker, their ghost arguments
+        e->drop_graphs();
+        e->gmem.clear();
+        for (int j = 0; j < n; j++)
+            if (make_coef<real>(e->m[j]->geo, e->m[j]->phy, e->m[j]->bnd).sine) e->gmem.push_back(j);
+        e->gstep0.assign(e->gmem.size(), 0);
+        std::vector<GhostArgs<real>> ga(e->gmem.size());
+        std::vector<int> start(e->gmem.size() + 1, 0);
+        for (size_t g = 0; g < e->gmem.size(); g++) {
+            const cel_solver *s = e->m[e->gmem[g]];
+            GhostArgs<real> &a = ga[g];
+            memset(&a, 0, sizeof(a));
+            a.g = s->geo;
+            a.p = s->phy;
+            a.b = s->bnd;
+            a.d_r = s->at<real>(s->lay.dr);
+            a.ktab = s->at<double>(s->lay.ktab);
+            a.tab = s->at<real>(s->lay.ghost);
+            a.npos = make_coef<real>(s->geo, s->phy, s->bnd).npos;
+            a.step0 = s->step;
+            a.dt = s->params.dt;
+            e->gstep0[g] = s->step;
+            start[g + 1] = start[g] + ((a.npos + 127) / 128) * 16;
+        }
+        e->gblocks = start.back();
+        if (!ga.empty()) {
+            ENS_CUDA(e, cudaMemcpyAsync(e->tab + e->off_gargs, ga.data(), sizeof(GhostArgs<real>) * ga.size(),
+                                        cudaMemcpyHostToDevice, e->stream), "ensemble ghost arguments");
+            ENS_CUDA(e, cudaMemcpyAsync(e->tab + e->off_gstart, start.data(), sizeof(int) * start.size(),
+                                        cudaMemcpyHostToDevice, e->stream), "ensemble ghost arguments");
+        }
+        e->gvalid = true;
+    }
+    for (int j : e->gmem) {
+        cel_solver *s = e->m[j];
+        if (!s->ktab_dirty) continue;
+        const Coef<real> c = make_coef<real>(s->geo, s->phy, s->bnd);
+        ENS_CUDA(e, launch_eckart_table<real>(s->geo, s->phy, s->bnd, s->at<real>(s->lay.dr),
+                                              s->at<double>(s->lay.ktab), c.npos, e->stream), "Eckart table");
+        s->ktab_dirty = 0;
+        launches += 1;
+    }
+    return CEL_OK;
+}
+
+// One step's launches on stream st: the ghost tables (their step index k,
+// plus *kdev where given), then per stage the stencil over every member's
+// tiles and the line solves; the members' bookkeeping moves on a step.
+template <typename real>
+cel_status ens_launch_step(cel_ensemble *e, cudaStream_t st, const int64_t *kdev, int64_t k, int64_t &launches)
+{
+    const int n = (int)e->m.size();
+    const int Kn = stages_of(e->m[0]) - 1;
+    if (!e->gmem.empty()) {
+        const int pg = e->prof.begin(2, st);
+        ENS_CUDA(e, launch_ghost_batch<real>(reinterpret_cast<const GhostArgs<real> *>(e->tab + e->off_gargs),
+                                             reinterpret_cast<const int *>(e->tab + e->off_gstart),
+                                             (int)e->gmem.size(), e->gblocks, k, kdev, st), "ensemble ghost tables");
+        e->prof.finish(pg, st);
+        launches += 1;
+    }
+    for (int stage = 0; stage <= Kn; stage++) {
+        int idx = 0;
+        cel_status cs = ens_entry<real>(e, stage, Kn, &idx);
+        if (cs != CEL_OK) return cs;
+        const unsigned char *ent = e->tab + e->off_entries + (size_t)idx * e->entry_bytes;
+        // the members step in lockstep: member 0's stage kind is every member's
+        const Coef<real> c0 = make_coef<real>(e->m[0]->geo, e->m[0]->phy, e->m[0]->bnd);
+        const int spec = stencil_spec(stencil_args<real>(e->m[0], c0, stage, Kn));
+        const int pe = e->prof.begin(0, st);
+        ENS_CUDA(e, launch_stencil_batch<real>(reinterpret_cast<const StencilArgs<real> *>(ent),
+                                               reinterpret_cast<const int2 *>(e->tab + e->off_tile_desc),
+                                               e->tiles, spec, st), "ensemble stencil");
+        e->prof.finish(pe, st);
+        launches += 1;
+        const LineArgs<real> *la = reinterpret_cast<const LineArgs<real> *>(ent + e->sarg_bytes);
+        for (const cel_ensemble::Group &G : e->groups) {
+            const int pl = e->prof.begin(1, st);
+            ENS_CUDA(e, launch_lines_batch<real>(la + G.first, reinterpret_cast<const int2 *>(e->tab + G.off_desc),
+                                                 G.blocks, G.cfg, st),
+                     "ensemble line solves");
+            e->prof.finish(pl, st);
+            launches += 1;
+        }
+    }
+    for (int j = 0; j < n; j++) {
+        cel_solver *s = e->m[j];
+        finish_step(s, Kn);
+        int64_t lg = 0;
+        cel_status gs = log_gauges<real>(s, st, lg);
+        if (gs != CEL_OK) return ens_fail(e, gs, s->err);
+        launches += lg;
+    }
+    return CEL_OK;
+}
+
+// Six steps as one captured graph, replayed on the ensemble's stream: only
+// where nothing in those steps differs between repetitions of the cycle (the
+// history full, no gauges, run-up tracking or profiling, every argument
+// block of the cycle already uploaded).  *done: the six steps were taken.
+template <typename real>
+cel_status ens_graph_cycle(cel_ensemble *e, int64_t &launches, bool *done)
+{
+    *done = false;
+    const int n = (int)e->m.size();
+    const cel_solver *m0 = e->m[0];
+    if (!e->use_graphs || m0->nh < 2 || e->prof.cap > 0) return CEL_OK;
+    for (int j = 0; j < n; j++) {
+        const cel_solver *s = e->m[j];
+        if (s->runup || (s->ng > 0 && s->log_every > 0 && s->cap > 0)) return CEL_OK;
+    }
+    const int Kn = stages_of(m0) - 1;
+    // the cycle's argument blocks must all be in the table already
+    {
+        int64_t nh = m0->nh;
+        int cur = m0->cur, pcur = m0->pcur;
+        for (int i = 0; i < 6; i++) {   // as finish_step moves them on
+            for (int stage = 0; stage <= Kn; stage++)
+                if (std::find(e->keys.begin(), e->keys.end(), ens_key_of(nh, cur, pcur, stage)) == e->keys.end())
+                    return CEL_OK;
+            cur = (cur + Kn + 1) & 1;
+            pcur = 1 - pcur;
+            nh++;
+        }
+    }
+    const int64_t k = e->gmem.empty() ? 0 : e->m[e->gmem[0]]->step - e->gstep0[0];
+    int64_t *kdev = reinterpret_cast<int64_t *>(e->tab + e->off_kdev);
+    const uint64_t key = ens_key(m0, 0);
+    cel_ensemble::Graph *g = nullptr;
+    for (cel_ensemble::Graph &h : e->graphs)
+        if (h.key == key) g = &h;
+    if (!g) {
+        // capture the cycle on the library's own stream (the caller's may be
+        // the legacy default stream, which cannot be captured); the members'
+        // bookkeeping moves on as the launches are recorded, and is put back
+        // if the capture fails
+        if (!e->cap_stream && cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            e->cap_stream = nullptr;
+            cudaGetLastError();
+            return CEL_OK;
+        }
+        struct Saved {
+            int cur, pcur;
+            int64_t step, nh;
+        };
+        std::vector<Saved> saved(n);
+        for (int j = 0; j < n; j++) saved[j] = {e->m[j]->cur, e->m[j]->pcur, e->m[j]->step, e->m[j]->nh};
+        auto restore = [&]() {
+            for (int j = 0; j < n; j++) {
+                e->m[j]->cur = saved[j].cur;
+                e->m[j]->pcur = saved[j].pcur;
+                e->m[j]->step = saved[j].step;
+                e->m[j]->nh = saved[j].nh;
+            }
+        };
+        if (cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return CEL_OK;
+        }
+        int64_t lc = 0;
+        cel_status cs = CEL_OK;
+        for (int i = 0; i < 6 && cs == CEL_OK; i++) cs = ens_launch_step<real>(e, e->cap_stream, kdev, i, lc);
+        if (cs == CEL_OK && launch_counter(kdev, 6, 1, e->cap_stream) != cudaSuccess) cs = CEL_ERR_CUDA;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (cs == CEL_OK && ce == cudaSuccess && graph &&
+            cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+            cudaGraphDestroy(graph);
+            e->graphs.push_back(cel_ensemble::Graph{key, exec, lc});
+            g = &e->graphs.back();
+            restore();   // the replay below moves the bookkeeping on
+        } else {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            restore();
+            e->err.clear();
+            return CEL_OK;   // the steps are taken one at a time instead
+        }
+    }
+    if (!e->kdev_known || e->kdev_val != k)
+        ENS_CUDA(e, launch_counter(kdev, k, 0, e->stream), "ensemble step counter");
+    ENS_CUDA(e, cudaGraphLaunch(g->exec, e->stream), "ensemble graph");
+    e->kdev_val = k + 6;
+    e->kdev_known = true;
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < n; j++) finish_step(e->m[j], Kn);
+    launches += g->launches;
+    e->graph_steps += 6;
+    *done = true;
+    return CEL_OK;
+}
+
 template <typename real>
 cel_status ens_step_t(cel_ensemble *e, int nsteps)
 {
-    const int n = (int)e->m.size();
     int64_t launches = 0;
-    for (int it = 0; it < nsteps; it++) {
-        const cel_solver *m0 = e->m[0];
-        uint64_t gsum = 0;
-        for (int j = 0; j < n; j++) {
-            const cel_solver *s = e->m[j];
-            if (s->nh != m0->nh || s->cur != m0->cur || s->pcur != m0->pcur)
-                return ens_fail(e, CEL_ERR_INVALID_ARG,
-                                "members are not in lockstep (set their states together, then step the ensemble)");
-            gsum += s->gen;
-        }
-        if (gsum != e->gen_sum) {      // a boundary or bed changed: rebuild every table
-            e->keys.clear();
-            e->gvalid = false;
-            e->gen_sum = gsum;
-        }
-        const int Kn = stages_of(m0) - 1;
-        if (e->gvalid && !e->gmem.empty()) {        // members moved on outside the ensemble?
-            const int64_t k0 = e->m[e->gmem[0]]->step - e->gstep0[0];
-            for (size_t g = 0; g < e->gmem.size(); g++)
-                if (e->m[e->gmem[g]]->step - e->gstep0[g] != k0) e->gvalid = false;
-        }
-        if (!e->gvalid) {                           // members with a sine maker, their ghost arguments
-            e->gmem.clear();
-            for (int j = 0; j < n; j++)
-                if (make_coef<real>(e->m[j]->geo, e->m[j]->phy, e->m[j]->bnd).sine) e->gmem.push_back(j);
-            e->gstep0.assign(e->gmem.size(), 0);
-            std::vector<GhostArgs<real>> ga(e->gmem.size());
-            std::vector<int> start(e->gmem.size() + 1, 0);
-            for (size_t g = 0; g < e->gmem.size(); g++) {
-                const cel_solver *s = e->m[e->gmem[g]];
-                GhostArgs<real> &a = ga[g];
-                memset(&a, 0, sizeof(a));
-                a.g = s->geo;
-                a.p = s->phy;
-                a.b = s->bnd;
-                a.d_r = s->at<real>(s->lay.dr);
-                a.ktab = s->at<double>(s->lay.ktab);
-                a.tab = s->at<real>(s->lay.ghost);
-                a.npos = make_coef<real>(s->geo, s->phy, s->bnd).npos;
-                a.step0 = s->step;
-                a.dt = s->params.dt;
-                e->gstep0[g] = s->step;
-                start[g + 1] = start[g] + ((a.npos + 127) / 128) * 16;
-            }
-            e->gblocks = start.back();
-            if (!ga.empty()) {
-                ENS_CUDA(e, cudaMemcpyAsync(e->tab + e->off_gargs, ga.data(), sizeof(GhostArgs<real>) * ga.size(),
-                                            cudaMemcpyHostToDevice, e->stream), "ensemble ghost arguments");
-                ENS_CUDA(e, cudaMemcpyAsync(e->tab + e->off_gstart, start.data(), sizeof(int) * start.size(),
-                                            cudaMemcpyHostToDevice, e->stream), "ensemble ghost arguments");
-            }
-            e->gvalid = true;
-        }
-        if (!e->gmem.empty()) {
-            for (int j : e->gmem) {
-                cel_solver *s = e->m[j];
-                if (!s->ktab_dirty) continue;
-                const Coef<real> c = make_coef<real>(s->geo, s->phy, s->bnd);
-                ENS_CUDA(e, launch_eckart_table<real>(s->geo, s->phy, s->bnd, s->at<real>(s->lay.dr),
-                                                      s->at<double>(s->lay.ktab), c.npos, e->stream), "Eckart table");
-                s->ktab_dirty = 0;
-                launches += 1;
-            }
-            const int64_t k = e->m[e->gmem[0]]->step - e->gstep0[0];
-            const int pg = e->prof.begin(2, e->stream);
-            ENS_CUDA(e, launch_ghost_batch<real>(reinterpret_cast<const GhostArgs<real> *>(e->tab + e->off_gargs),
-                                                 reinterpret_cast<const int *>(e->tab + e->off_gstart),
-                                                 (int)e->gmem.size(), e->gblocks, k, e->stream), "ensemble ghost tables");
-            e->prof.finish(pg, e->stream);
-            launches += 1;
-        }
-        for (int stage = 0; stage <= Kn; stage++) {
-            int idx = 0;
-            cel_status st = ens_entry<real>(e, stage, Kn, &idx);
+    for (int it = 0; it < nsteps;) {
+        cel_status st = ens_prepare<real>(e, launches);
+        if (st != CEL_OK) return st;
+        if (nsteps - it >= 6) {
+            bool done = false;
+            st = ens_graph_cycle<real>(e, launches, &done);
             if (st != CEL_OK) return st;
-            const unsigned char *ent = e->tab + e->off_entries + (size_t)idx * e->entry_bytes;
-            const int pe = e->prof.begin(0, e->stream);
-            ENS_CUDA(e, launch_stencil_batch<real>(reinterpret_cast<const StencilArgs<real> *>(ent),
-                                                   reinterpret_cast<const int2 *>(e->tab + e->off_tile_desc),
-                                                   e->tiles, e->stream), "ensemble stencil");
-            e->prof.finish(pe, e->stream);
-            launches += 1;
-            const LineArgs<real> *la = reinterpret_cast<const LineArgs<real> *>(ent + e->sarg_bytes);
-            for (const cel_ensemble::Group &G : e->groups) {
-                const int pl = e->prof.begin(1, e->stream);
-                ENS_CUDA(e, launch_lines_batch<real>(la + G.first, reinterpret_cast<const int2 *>(e->tab + G.off_desc),
-                                                     G.blocks, G.mshift, G.threads, G.smem, e->stream),
-                         "ensemble line solves");
-                e->prof.finish(pl, e->stream);
-                launches += 1;
+            if (done) {
+                it += 6;
+                continue;
             }
         }
-        for (int j = 0; j < n; j++) {
-            cel_solver *s = e->m[j];
-            finish_step(s, Kn);
-            int64_t lg = 0;
-            cel_status st = log_gauges<real>(s, e->stream, lg);
-            if (st != CEL_OK) return ens_fail(e, st, s->err);
-            launches += lg;
-        }
+        const int64_t k = e->gmem.empty() ? 0 : e->m[e->gmem[0]]->step - e->gstep0[0];
+        st = ens_launch_step<real>(e, e->stream, nullptr, k, launches);
+        if (st != CEL_OK) return st;
+        it += 1;
     }
     e->launches = launches;
     return CEL_OK;
@@ -1557,6 +1718,7 @@ cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *tabl
     e->gblocks = P.gblocks;
     e->off_gargs = P.off_gargs;
     e->off_gstart = P.off_gstart;
+    e->off_kdev = P.off_kdev;
     e->gstep0.assign(P.gmem.size(), 0);
     e->gvalid = false;
     e->sarg_bytes = P.sarg_bytes;
@@ -1635,10 +1797,27 @@ cel_status cel_ensemble_profile_disable(cel_ensemble *e)
 
 const char *cel_ensemble_last_error(const cel_ensemble *e) { return e ? e->err.c_str() : ""; }
 
+cel_status cel_ensemble_graph_steps(const cel_ensemble *e, int64_t *steps)
+{
+    if (!e || !steps) return CEL_ERR_INVALID_ARG;
+    *steps = e->graph_steps;
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_use_graphs(cel_ensemble *e, int32_t enable)
+{
+    if (!e) return CEL_ERR_INVALID_ARG;
+    e->use_graphs = enable != 0;
+    if (!e->use_graphs) e->drop_graphs();
+    return CEL_OK;
+}
+
 void cel_ensemble_destroy(cel_ensemble *e)
 {
     if (!e) return;
     e->prof.release();
+    e->drop_graphs();
+    if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
     delete e;
 }
 

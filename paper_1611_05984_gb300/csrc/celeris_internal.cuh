@@ -168,9 +168,10 @@ struct LineArgs {
     real *sol;             // P^{n+1} = P^n + solution, line-major
     int dir;               // 0: x-lines (rows), 1: y-lines (columns)
     int n, nlines, pitch, nwords;
-    int nseg;              // segments per line (threads doing sweeps)
+    int algo;              // 0: segments in registers, one per thread; 1: segments in shared memory
+    int nseg;              // segments per line (algo 0: one per thread, the block size)
     int mshift;            // log2 of the rows per segment (lines padded to nseg << mshift)
-    int sp;                // odd shared-memory stride between rows of the segments
+    int sp;                // algo 1: odd shared-memory stride between rows of the segments
     int final_stage;       // apply the sponge
     int identity;          // NLSW model: no dispersive solve, P = U*, Q = V*
     real rh, rh2, hrh, srh; // 1/h, 1/h^2, 1/(2h), 1/(6h) along the line
@@ -239,6 +240,24 @@ cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const 
                                cudaStream_t st);
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st);
+// The stencil kernel's stage specialisation: 1 for the AB3 predictor with
+// the ring history, 2 for the AM4 corrector, 0 for the other stages.
+template <typename real>
+inline int stencil_spec(const StencilArgs<real> &a)
+{
+    return a.kind == kAM4 ? 2 : (a.ring && a.kind == kAB3 ? 1 : 0);
+}
+// How a line of n rows is solved: the algorithm, rows per segment, segments,
+// the odd shared-memory stride (algo 1), threads per block and dynamic
+// shared memory.  Lines of one launch share algo, mshift and threads.
+struct LineCfg {
+    int algo, mshift, nseg, sp, threads;
+    size_t smem;
+};
+LineCfg line_config(int n, int real_bytes);
+// Launches that launch_lines and its kin issue for the two families.
+int line_launches(int nx_lines, int n_x, int ny_lines, int n_y, int real_bytes);
+
 // The x-line and the y-line solves of one stage are independent (P from
 // the increment of U*, Q from that of V*) and run in one launch.
 template <typename real>
@@ -274,21 +293,22 @@ struct GhostArgs {
     double dt;
 };
 
+// k: the lockstep step index, plus *kdev where kdev is given (a device
+// counter that a captured graph advances between its replays).
 template <typename real>
 cudaError_t launch_ghost_batch(const GhostArgs<real> *args, const int *start, int n, int nblocks, int64_t k,
+                               const int64_t *kdev, cudaStream_t st);
+// *p = v (add 0) or *p += v (add 1), one thread.
+cudaError_t launch_counter(int64_t *p, int64_t v, int add, cudaStream_t st);
+// spec: the stencil's stage specialisation (stencil_spec of the members'
+// arguments, which step in lockstep and share it).
+template <typename real>
+cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, int spec,
+                                 cudaStream_t st);
+// All families of one launch share cfg (line_config of their length): the
+// algorithm, the segment length 1 << mshift and the block size.
+template <typename real>
+cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int nblocks, const LineCfg &cfg,
                                cudaStream_t st);
-template <typename real>
-cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, cudaStream_t st);
-// All families of one launch share the segment length 1 << mshift; threads
-// (a multiple of 32) is at least the segment count of every family.
-template <typename real>
-cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int nblocks, int mshift, int threads,
-                               size_t smem, cudaStream_t st);
-template <typename real>
-size_t line_smem_bytes(int n, int nseg);
-int line_segments(int n, int real_bytes);
-int line_seg_shift(int n, int real_bytes);
-int line_seg_stride(int nseg);
-int line_threads(int n, int real_bytes);
 
 }  // namespace cel

@@ -325,13 +325,13 @@ __global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r
 // step0 + k.
 template <typename real>
 __global__ void k_ghost_batch(const GhostArgs<real> *__restrict__ args, const int *__restrict__ start, int n,
-                              int64_t k)
+                              int64_t k, const int64_t *__restrict__ kdev)
 {
     const int e = find_owner(start, n, blockIdx.x);
     const GhostArgs<real> &A = args[e];
     const int b = blockIdx.x - start[e];
     const int nbx = (A.npos + 127) / 128;
-    const int64_t step = A.step0 + k;
+    const int64_t step = A.step0 + (kdev ? *kdev : 0) + k;
     ghost_entry(A.g, A.p, A.b, A.d_r, A.ktab, (double)step * A.dt, (double)(step + 1) * A.dt, A.tab, A.npos,
                 (b % nbx) * 128 + threadIdx.x, b / nbx);
 }
@@ -394,42 +394,62 @@ struct Carry {
 
 // The history a stage reads, loaded at the top of a cell's iteration so the
 // loads are in flight while the cell's right side is computed.
-template <typename real>
+// Stage specialisations of the stencil (kSpec): 0, any stage, its kind and
+// history layout read at run time; 1, the AB3 predictor with the ring
+// history (K >= 1); 2, the AM4 corrector.  The two hot stages then carry no
+// branches on the stage kind.
+template <int kSpec, typename real>
+__device__ __forceinline__ int stage_kind(const StencilArgs<real> &A)
+{
+    return kSpec == 1 ? kAB3 : (kSpec == 2 ? kAM4 : A.kind);
+}
+
+template <int kSpec, typename real>
+__device__ __forceinline__ bool stage_ring(const StencilArgs<real> &A)
+{
+    return kSpec == 1 ? true : (kSpec == 2 ? true : A.ring != 0);
+}
+
+template <typename real, int kSpec>
 __device__ __forceinline__ Carry<real> load_carry(const StencilArgs<real> &A, int v, size_t k)
 {
+    const int kind = stage_kind<kSpec>(A);
+    const bool ring = stage_ring<kSpec>(A);
     Carry<real> c;
     c.a = c.b = c.r1 = c.r2 = c.p1 = c.p2 = c.Y = real(0);
-    if (A.kind == kAM4) {
+    if (kind == kAM4) {
         c.Y = A.Y[v][k];
-    } else if (A.ring) {
-        if (A.kind == kAB3) {
+    } else if (ring) {
+        if (kind == kAB3) {
             c.r1 = A.R1[v][k];
             c.r2 = A.R2[v][k];
         }
-        if (v > 0 && A.kind != kEuler0) {
+        if (v > 0 && kind != kEuler0) {
             c.p1 = A.F1[v][k];
-            if (A.kind == kAB3) c.p2 = A.F2[v][k];
+            if (kind == kAB3) c.p2 = A.F2[v][k];
         }
-    } else if (A.kind == kEuler1) {
+    } else if (kind == kEuler1) {
         c.a = A.a[v][k];
-    } else if (A.kind == kAB3) {
+    } else if (kind == kAB3) {
         c.a = A.a[v][k];
         c.b = A.b[v][k];
     }
     return c;
 }
 
-template <typename real>
+template <typename real, int kSpec>
 __device__ __forceinline__ real advance(const StencilArgs<real> &A, int v, real X0, real R, real Phi, size_t k,
                                         const Carry<real> &c)
 {
+    const int kind = stage_kind<kSpec>(A);
+    const bool ring = stage_ring<kSpec>(A);
     const real dt = A.c.dt, c12 = dt / real(12), c24 = dt / real(24);
-    if (A.kind == kAM4) return c.Y + real(9) * c24 * R + Phi;
-    if (A.ring) {
+    if (kind == kAM4) return c.Y + real(9) * c24 * R + Phi;
+    if (ring) {
         real D;
-        if (A.kind == kEuler0) {
+        if (kind == kEuler0) {
             D = dt * R;
-        } else if (A.kind == kEuler1) {
+        } else if (kind == kEuler1) {
             D = dt * R + (Phi - c.p1);
         } else {
             D = c12 * (real(23) * R - real(16) * c.r1 + real(5) * c.r2) + real(2) * Phi - real(3) * c.p1 + c.p2;
@@ -440,10 +460,10 @@ __device__ __forceinline__ real advance(const StencilArgs<real> &A, int v, real 
         return D;
     }
     real D;
-    if (A.kind == kEuler0) {
+    if (kind == kEuler0) {
         D = dt * R;
         A.a[v][k] = Phi;
-    } else if (A.kind == kEuler1) {
+    } else if (kind == kEuler1) {
         D = dt * R + (Phi - c.a);
         A.a[v][k] = real(-16) * c12 * R - real(3) * Phi;
     } else {
@@ -549,7 +569,7 @@ struct SharedOrigin {
 };
 
 // One 32 x 32 tile of one grid, at the origin O gives: the whole stencil stage.
-template <typename real, typename Origin>
+template <typename real, int kSpec, typename Origin>
 __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const Origin &O, unsigned char *smem_raw)
 {
     StencilSmem<real> &sm = *reinterpret_cast<StencilSmem<real> *>(smem_raw);
@@ -653,25 +673,39 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
         const int lane = tid & 31, wq = (tid >> 5) & 3;
         const int f0 = wq * 8, f1 = wq == 3 ? kTile + 1 : f0 + 8;
         real lo[3], hiL[3], hiR[3];
+        // the three cells a reconstruction reads slide along the row (or
+        // column) one cell per face, so each face loads one new cell and one
+        // new pair of corners
+        real wq3[3], Pq[3], Qq[3];
         if (tid < 4 * 32) {
             const int r = lane;
             const int rowo = (r + kHalo) * kStride;
             const real *cb = sm.Bc + (r + 1) * kCornerStride;
+            real Bf;   // bed at the face about to be computed
             {
                 const int o = rowo + f0 + 1;
-                const real wq3[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
-                const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
-                const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
-                recon(th, wq3, Pq, Qq, real(0.5) * (cb[f0] + cb[f0 + kCornerStride]),
-                      real(0.5) * (cb[f0 + 1] + cb[f0 + 1 + kCornerStride]), lo, hiL);
+#pragma unroll
+                for (int u = 0; u < 3; u++) {
+                    wq3[u] = sm.w[o - 1 + u];
+                    Pq[u] = sm.P[o - 1 + u];
+                    Qq[u] = sm.Q[o - 1 + u];
+                }
+                Bf = real(0.5) * (cb[f0 + 1] + cb[f0 + 1 + kCornerStride]);
+                recon(th, wq3, Pq, Qq, real(0.5) * (cb[f0] + cb[f0 + kCornerStride]), Bf, lo, hiL);
             }
             for (int f = f0; f < f1; f++) {
                 const int o = rowo + f + 2;           // right cell of face f
-                const real wq3[3] = {sm.w[o - 1], sm.w[o], sm.w[o + 1]};
-                const real Pq[3] = {sm.P[o - 1], sm.P[o], sm.P[o + 1]};
-                const real Qq[3] = {sm.Q[o - 1], sm.Q[o], sm.Q[o + 1]};
-                const real Bf = real(0.5) * (cb[f + 1] + cb[f + 1 + kCornerStride]);
-                recon(th, wq3, Pq, Qq, Bf, real(0.5) * (cb[f + 2] + cb[f + 2 + kCornerStride]), lo, hiR);
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    wq3[u] = wq3[u + 1];
+                    Pq[u] = Pq[u + 1];
+                    Qq[u] = Qq[u + 1];
+                }
+                wq3[2] = sm.w[o + 1];
+                Pq[2] = sm.P[o + 1];
+                Qq[2] = sm.Q[o + 1];
+                const real Bn = real(0.5) * (cb[f + 2] + cb[f + 2 + kCornerStride]);
+                recon(th, wq3, Pq, Qq, Bf, Bn, lo, hiR);
                 real H[3];
                 cu_flux(g, eps, hiL[0], hiL[1], hiL[2], lo[0], lo[1], lo[2], Bf, H);
                 sm.Fx[0][r][f] = H[0];
@@ -680,27 +714,38 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
                 hiL[0] = hiR[0];
                 hiL[1] = hiR[1];
                 hiL[2] = hiR[2];
+                Bf = Bn;
             }
         } else {
             const int c = lane;
             const int tx = c + kHalo;
             const real *cb = sm.Bc + c + 1;
+            real Bf;
             {
                 const int o = (f0 + 1) * kStride + tx;
-                const real wq3[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
-                const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
-                const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
-                recon(th, wq3, Pq, Qq, real(0.5) * (cb[f0 * kCornerStride] + cb[f0 * kCornerStride + 1]),
-                      real(0.5) * (cb[(f0 + 1) * kCornerStride] + cb[(f0 + 1) * kCornerStride + 1]), lo, hiL);
+#pragma unroll
+                for (int u = 0; u < 3; u++) {
+                    wq3[u] = sm.w[o + (u - 1) * kStride];
+                    Pq[u] = sm.P[o + (u - 1) * kStride];
+                    Qq[u] = sm.Q[o + (u - 1) * kStride];
+                }
+                Bf = real(0.5) * (cb[(f0 + 1) * kCornerStride] + cb[(f0 + 1) * kCornerStride + 1]);
+                recon(th, wq3, Pq, Qq, real(0.5) * (cb[f0 * kCornerStride] + cb[f0 * kCornerStride + 1]), Bf, lo,
+                      hiL);
             }
             for (int gq = f0; gq < f1; gq++) {
                 const int o = (gq + 2) * kStride + tx;  // north cell of face gq
-                const real wq3[3] = {sm.w[o - kStride], sm.w[o], sm.w[o + kStride]};
-                const real Pq[3] = {sm.P[o - kStride], sm.P[o], sm.P[o + kStride]};
-                const real Qq[3] = {sm.Q[o - kStride], sm.Q[o], sm.Q[o + kStride]};
-                const real Bf = real(0.5) * (cb[(gq + 1) * kCornerStride] + cb[(gq + 1) * kCornerStride + 1]);
-                recon(th, wq3, Pq, Qq, Bf,
-                      real(0.5) * (cb[(gq + 2) * kCornerStride] + cb[(gq + 2) * kCornerStride + 1]), lo, hiR);
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    wq3[u] = wq3[u + 1];
+                    Pq[u] = Pq[u + 1];
+                    Qq[u] = Qq[u + 1];
+                }
+                wq3[2] = sm.w[o + kStride];
+                Pq[2] = sm.P[o + kStride];
+                Qq[2] = sm.Q[o + kStride];
+                const real Bn = real(0.5) * (cb[(gq + 2) * kCornerStride] + cb[(gq + 2) * kCornerStride + 1]);
+                recon(th, wq3, Pq, Qq, Bf, Bn, lo, hiR);
                 real H[3];
                 // normal discharge is Q, tangential is P
                 cu_flux(g, eps, hiL[0], hiL[2], hiL[1], lo[0], lo[2], lo[1], Bf, H);
@@ -710,6 +755,7 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
                 hiL[0] = hiR[0];
                 hiL[1] = hiR[1];
                 hiL[2] = hiR[2];
+                Bf = Bn;
             }
         }
     }
@@ -735,9 +781,9 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
         // occupancy than it saves latency)
         Carry<real> cw, cu, cv;
         if (valid) {
-            cw = load_carry(A, 0, kr);
-            cu = load_carry(A, 1, kr);
-            cv = load_carry(A, 2, kr);
+            cw = load_carry<real, kSpec>(A, 0, kr);
+            cu = load_carry<real, kSpec>(A, 1, kr);
+            cv = load_carry<real, kSpec>(A, 2, kr);
         }
         const real *cb = sm.Bc + (cy + 1) * kCornerStride + cx + 1;
         real c00 = cb[0], c10 = cb[1], c01 = cb[kCornerStride], c11 = cb[kCornerStride + 1];
@@ -790,10 +836,10 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
         }
         real w1 = w0, dU = real(0), dV = real(0);
         if (valid) {
-            real dw = advance(A, 0, w0, E, real(0), kr, cw);
-            w1 = A.kind == kAM4 ? dw : w0 + dw;   // the AM4 base of w holds w^n
-            dU = advance(A, 1, real(0), F, Fs, kr, cu);
-            dV = advance(A, 2, real(0), Gq, Gs, kr, cv);
+            real dw = advance<real, kSpec>(A, 0, w0, E, real(0), kr, cw);
+            w1 = stage_kind<kSpec>(A) == kAM4 ? dw : w0 + dw;   // the AM4 base of w holds w^n
+            dU = advance<real, kSpec>(A, 1, real(0), F, Fs, kr, cu);
+            dV = advance<real, kSpec>(A, 2, real(0), Gq, Gs, kr, cv);
             if (w1 < Bb) w1 = Bb;   // Reading A-D1
             if (A.final_stage) {
                 real gam = sponge_gamma<real>(C, G, i, j);
@@ -817,11 +863,11 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
     if (tid < kTile && O.x0() + tid < nx) A.mask_c[(size_t)(O.x0() + tid) * G.nwy + (O.y0() >> 5)] = sm.colbits[tid];
 }
 
-template <typename real>
+template <typename real, int kSpec>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_stencil(const __grid_constant__ StencilArgs<real> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stencil_tile(A, GridOrigin(), smem_raw);
+    stencil_tile<real, kSpec>(A, GridOrigin(), smem_raw);
 }
 
 // Copy a scenario's argument block (device memory) into shared memory.
@@ -837,7 +883,7 @@ __device__ __forceinline__ void load_args(T &dst, const T *src)
 // Ensemble: the tiles of every member in one launch.  desc[b] names block
 // b's member (x) and tile (y: row << 16 | column); the member's arguments
 // are copied to shared memory.
-template <typename real>
+template <typename real, int kSpec>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
     k_stencil_batch(const StencilArgs<real> *__restrict__ args, const int2 *__restrict__ desc)
 {
@@ -851,7 +897,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
     }
     load_args(A, args + d.x);
     __syncthreads();
-    stencil_tile(A, SharedOrigin{origin}, smem_raw);
+    stencil_tile<real, kSpec>(A, SharedOrigin{origin}, smem_raw);
 }
 
 // ------------------------------------------------------------ line solves
@@ -894,13 +940,408 @@ __device__ __forceinline__ int seg_slot(int k, int mshift, int sp)
     return (k & ((1 << mshift) - 1)) * sp + (k >> mshift);
 }
 
-// One line of one family (x-row or y-column): the whole solve and epilogue.
+// ------------------------------------------- line solves, segments in registers
+//
+// A line of n rows (Eq. 21-23) is cut into T = blockDim.x segments of M
+// consecutive rows, one per thread; rows from n on are identity rows.  The
+// last row of segment t is its separator s_t.  Thread t eliminates the M - 1
+// rows before it by Thomas against three right sides (the data, and the
+// couplings to s_{t-1} and s_t), so that each of them is y + u s_{t-1} +
+// v s_t, and the separators' rows form a tridiagonal system with one row per
+// thread.  Lane 31 of each warp holds the warp's separator S_w: a warp
+// reduces its other 31 rows by cyclic reduction in registers (shuffles)
+// against the same three right sides, and the warps' separators form a
+// system of one row per warp, which warp 0 solves the same way.  Two
+// barriers per line; the system is strictly diagonally dominant (|d_x| below
+// about 5), so no pivoting.
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Cyclic reduction of a warp's 32 rows a x_{i-1} + b x_i + c x_{i+1} = r
+// (rows beyond the warp decoupled), NR right sides at once: afterwards row i
+// reads b x_i = r.
+template <typename real, int NR>
+__device__ __forceinline__ void warp_cr(real &a, real &b, real &c, real (&r)[NR], int lane)
+{
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const real ib = real(1) / b;   // each row's reciprocal, once, to both neighbours
+        const real am = __shfl_up_sync(kFull, a, s), ibm = __shfl_up_sync(kFull, ib, s);
+        const real cm = __shfl_up_sync(kFull, c, s);
+        const real ap = __shfl_down_sync(kFull, a, s), ibp = __shfl_down_sync(kFull, ib, s);
+        const real cp = __shfl_down_sync(kFull, c, s);
+        real rm[NR], rp[NR];
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            rm[q] = __shfl_up_sync(kFull, r[q], s);
+            rp[q] = __shfl_down_sync(kFull, r[q], s);
+        }
+        const real k1 = lane >= s ? a * ibm : real(0);
+        const real k2 = lane + s < 32 ? c * ibp : real(0);
+        b = b - cm * k1 - ap * k2;
+#pragma unroll
+        for (int q = 0; q < NR; q++) r[q] = r[q] - rm[q] * k1 - rp[q] * k2;
+        a = -am * k1;
+        c = -cp * k2;
+    }
+}
+
+// M consecutive reals at p (16-byte aligned when M * sizeof(real) >= 16)
+template <typename real, int M>
+__device__ __forceinline__ void load_run(real (&v)[M], const real *p)
+{
+    if constexpr (M * sizeof(real) >= 16) {
+        using V = typename Vec2<real>::type;
+        if constexpr (sizeof(real) == 4) {
+#pragma unroll
+            for (int u = 0; u < M / 4; u++) {
+                const float4 q = reinterpret_cast<const float4 *>(p)[u];
+                v[4 * u] = q.x;
+                v[4 * u + 1] = q.y;
+                v[4 * u + 2] = q.z;
+                v[4 * u + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < M / 2; u++) {
+                const V q = reinterpret_cast<const V *>(p)[u];
+                v[2 * u] = q.x;
+                v[2 * u + 1] = q.y;
+            }
+        }
+    } else if constexpr (M == 2) {
+        const typename Vec2<real>::type q = *reinterpret_cast<const typename Vec2<real>::type *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < M; u++) v[u] = p[u];
+    }
+}
+
+template <typename real, int M>
+__device__ __forceinline__ void store_run(real *p, const real (&v)[M])
+{
+    if constexpr (sizeof(real) == 4 && M % 4 == 0) {
+#pragma unroll
+        for (int u = 0; u < M / 4; u++)
+            reinterpret_cast<float4 *>(p)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+    } else if constexpr (M % 2 == 0) {
+        using V = typename Vec2<real>::type;
+#pragma unroll
+        for (int u = 0; u < M / 2; u++) {
+            V q;
+            q.x = v[2 * u];
+            q.y = v[2 * u + 1];
+            reinterpret_cast<V *>(p)[u] = q;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < M; u++) p[u] = v[u];
+    }
+}
+
+// Row k of the line's system T: Eq. 23 from the depths dm, dd, dp of rows
+// k - 1, k, k + 1, with the boundary rows of Reading A-B2 (a solid or sponge
+// end folds the mirrored neighbour into b; at a maker end the known ghost
+// increment moves to the right side, *rk -= a * inc, when rk is given);
+// identity rows beyond the line.
+template <typename real>
+__device__ __forceinline__ void t_row(const LineArgs<real> &A, int k, real dm, real dd, real dp, bool lo_sine,
+                                      bool hi_sine, real lo_inc, real hi_inc, real &a, real &b, real &c,
+                                      real *rk)
+{
+    if (k < 0 || k >= A.n) {
+        a = c = real(0);
+        b = real(1);
+        return;
+    }
+    coef23(A.c.B3, A.hrh, A.srh, A.rh2, dd, dm, dp, a, b, c);
+    if (k == 0) {
+        if (!lo_sine) b -= a;
+        else if (rk) *rk -= a * lo_inc;
+        a = real(0);
+    }
+    if (k == A.n - 1) {
+        if (!hi_sine) b -= c;
+        else if (rk) *rk -= c * hi_inc;
+        c = real(0);
+    }
+}
+
+// The values that cross warps, per warp: lane 0's first interior row
+// (y, u, v) and its separator's (Y, U, V); lane 31's row and its last
+// interior row; lane 30's (Y, U, V); the warps' separators.
+template <typename real>
+struct LineShared {
+    real sh0[32][3], sh1[32][3], sh31[32][7], sh30[32][3], shS[32];
+};
+
+// One line of one family: kMode 0, the step's solve with P^n + x, the sponge
+// on the last stage and the dry mask; 1, the transposed system T^T y = r
+// (row k of T^T is (c_{k-1}, b_k, a_{k+1}) of T's rows), y alone; 2, T x = r,
+// x alone.  The line's own segment count A.nseg (a multiple of 32, at most
+// the block size) sets the reduction, so the result does not depend on the
+// block size: warps beyond it only pass the barriers.
+template <typename real, int M, int kMode>
+__device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line, LineShared<real> &L)
+{
+    static_assert(M >= 2 && M <= 8, "rows per thread");
+    constexpr int m1 = M - 1;
+    auto &sh0 = L.sh0;
+    auto &sh1 = L.sh1;
+    auto &sh31 = L.sh31;
+    auto &sh30 = L.sh30;
+    auto &shS = L.shS;
+    const int n = A.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = A.nseg >> 5;
+    const bool act = warp < nw;            // whole warps: the segment count is a multiple of 32
+    const int f = tid * M;
+    const int lo_side = A.dir == 0 ? 0 : 2, hi_side = A.dir == 0 ? 1 : 3;
+    const bool lo_sine = (A.c.sine >> lo_side) & 1, hi_sine = (A.c.sine >> hi_side) & 1;
+    const int gvar = A.dir == 0 ? 1 : 2;   // ghost discharge: P on x-lines, Q on y-lines
+    const size_t lo = (size_t)line * A.pitch;
+    real *out = A.sol + lo;
+    const bool any = act && f < n;         // the segment holds rows of the line
+
+    real r[M];
+    if (any) {
+        if (kMode == 0) {   // P^n and the dry bits are read in the epilogue: to L1 now
+#pragma unroll
+            for (int u = 0; u < M; u += 32 / (int)sizeof(real))
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.base + lo + f + u));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.mask + (size_t)line * A.nwords + (f >> 5)));
+        }
+        load_run<real, M>(r, A.rhs + lo + f);
+#pragma unroll
+        for (int j = 0; j < M; j++)
+            if (f + j >= n) r[j] = real(0);
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; j++) r[j] = real(0);
+    }
+    real x[M];
+    if (A.identity) {   // NLSW: P = U*
+#pragma unroll
+        for (int j = 0; j < M; j++) x[j] = r[j];
+    } else {
+        // depths of rows f - 2 .. f + M + 1 (mirrored at the ends)
+        real dv[M + 4];
+        const real *dl = A.d + lo;
+        if (any) {
+            real mid[M];
+            load_run<real, M>(mid, dl + f);
+#pragma unroll
+            for (int j = 0; j < M; j++) dv[j + 2] = f + j < n ? mid[j] : dl[n - 1];
+            dv[0] = dl[f >= 2 ? f - 2 : 0];
+            dv[1] = dl[f >= 1 ? f - 1 : 0];
+            dv[M + 2] = dl[f + M < n ? f + M : n - 1];
+            dv[M + 3] = dl[f + M + 1 < n ? f + M + 1 : n - 1];
+        } else {
+#pragma unroll
+            for (int j = 0; j < M + 4; j++) dv[j] = real(0);
+        }
+        // rows f .. f + M - 1 of the system solved (T, or T^T in mode 1):
+        // Eq. 23 on every row, then the rows at the line's ends (Reading
+        // A-B2) and beyond it (identity), in the segments that hold them
+        real ra[M], rb[M], rc[M];
+        const bool at_end = f + M > n - 1;   // holds row n - 1 (or lies beyond)
+        if (kMode == 1) {
+            real ta[M + 2], tb[M + 2], tc[M + 2];   // T's rows f - 1 .. f + M
+#pragma unroll
+            for (int j = 0; j < M + 2; j++)
+                coef23(A.c.B3, A.hrh, A.srh, A.rh2, dv[j + 1], dv[j], dv[j + 2], ta[j], tb[j], tc[j]);
+            if (f == 0 || at_end) {
+#pragma unroll
+                for (int j = 0; j < M + 2; j++)
+                    t_row(A, f - 1 + j, dv[j], dv[j + 1], dv[j + 2], lo_sine, hi_sine, real(0), real(0), ta[j],
+                          tb[j], tc[j], (real *)nullptr);
+            }
+#pragma unroll
+            for (int j = 0; j < M; j++) {
+                ra[j] = tc[j];
+                rb[j] = tb[j + 1];
+                rc[j] = ta[j + 2];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; j++)
+                coef23(A.c.B3, A.hrh, A.srh, A.rh2, dv[j + 2], dv[j + 1], dv[j + 3], ra[j], rb[j], rc[j]);
+            if (f == 0 || at_end) {
+                // the makers' ghost increments (t^{n+1} - t^n) at the line's ends
+                real lo_inc = real(0), hi_inc = real(0);
+                if (lo_sine && f == 0)
+                    lo_inc = A.ghost[ghost_index(1, lo_side, 0, gvar, line + 2, A.c.npos)] -
+                             A.ghost[ghost_index(0, lo_side, 0, gvar, line + 2, A.c.npos)];
+                if (hi_sine && at_end && f <= n - 1)
+                    hi_inc = A.ghost[ghost_index(1, hi_side, 0, gvar, line + 2, A.c.npos)] -
+                             A.ghost[ghost_index(0, hi_side, 0, gvar, line + 2, A.c.npos)];
+#pragma unroll
+                for (int j = 0; j < M; j++)
+                    t_row(A, f + j, dv[j + 1], dv[j + 2], dv[j + 3], lo_sine, hi_sine, lo_inc, hi_inc, ra[j], rb[j],
+                          rc[j], &r[j]);
+            }
+        }
+        // Thomas on rows f .. f + M - 2 against (r, -a_f e_0, -c e_last)
+        real g[m1], y[m1], uu[m1], vv[m1];
+        real Y = real(0), U = real(0), V = real(0);
+        {
+            real gp = real(0), yp = real(0), up = real(0);
+#pragma unroll
+            for (int j = 0; j < m1; j++) {
+                const real inv = real(1) / (rb[j] - ra[j] * gp);
+                g[j] = j + 1 < m1 ? rc[j] * inv : real(0);
+                y[j] = (r[j] - ra[j] * yp) * inv;
+                uu[j] = (j == 0 ? -ra[0] : -ra[j] * up) * inv;
+                vv[j] = j + 1 == m1 ? -rc[j] * inv : real(0);
+                gp = g[j];
+                yp = y[j];
+                up = uu[j];
+            }
+#pragma unroll
+            for (int j = m1 - 2; j >= 0; j--) {
+                y[j] -= g[j] * y[j + 1];
+                uu[j] -= g[j] * uu[j + 1];
+                vv[j] = -g[j] * vv[j + 1];
+            }
+        }
+        // the separator's row in (s_{t-1}, s_t, s_{t+1}): the next thread's
+        // first interior row by shuffle (lane 31: later, from shared memory)
+        const real al = ra[m1], bl = rb[m1], cl = rc[m1], rl = r[m1];
+        if (act) {
+        const real ny0 = __shfl_down_sync(kFull, y[0], 1), nu0 = __shfl_down_sync(kFull, uu[0], 1);
+        const real nv0 = __shfl_down_sync(kFull, vv[0], 1);
+        real a1 = al * uu[m1 - 1];
+        real b1 = al * vv[m1 - 1] + bl + cl * nu0;
+        real c1 = cl * nv0;
+        real rr1[3] = {rl - al * y[m1 - 1] - cl * ny0, real(0), real(0)};
+        // lanes 0..30 reduced against (S_{w-1}, S_w): lane 0's coupling to
+        // the previous warp's separator and lane 30's to lane 31 move to the
+        // right sides; lane 31 is the warp's separator
+        if (lane == 0) {
+            rr1[1] = -a1;
+            a1 = real(0);
+        }
+        if (lane == 30) {
+            rr1[2] = -c1;
+            c1 = real(0);
+        }
+        if (lane == 31) {
+            a1 = c1 = real(0);
+            b1 = real(1);
+            rr1[0] = real(0);
+        }
+        warp_cr<real, 3>(a1, b1, c1, rr1, lane);
+        const real ib = real(1) / b1;
+        Y = rr1[0] * ib;
+        U = rr1[1] * ib;
+        V = rr1[2] * ib;
+        const real Y30 = __shfl_up_sync(kFull, Y, 1), U30 = __shfl_up_sync(kFull, U, 1);
+        const real V30 = __shfl_up_sync(kFull, V, 1);
+        if (lane == 0) {
+            sh0[warp][0] = y[0];
+            sh0[warp][1] = uu[0];
+            sh0[warp][2] = vv[0];
+            sh1[warp][0] = Y;
+            sh1[warp][1] = U;
+            sh1[warp][2] = V;
+        }
+        if (lane == 31) {
+            sh31[warp][0] = al;
+            sh31[warp][1] = bl;
+            sh31[warp][2] = cl;
+            sh31[warp][3] = rl;
+            sh31[warp][4] = y[m1 - 1];
+            sh31[warp][5] = uu[m1 - 1];
+            sh31[warp][6] = vv[m1 - 1];
+            sh30[warp][0] = Y30;
+            sh30[warp][1] = U30;
+            sh30[warp][2] = V30;
+        }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // row of separator S_w in (S_{w-1}, S_w, S_{w+1})
+            real A2 = real(0), B2 = real(1), C2 = real(0), R2[1] = {real(0)};
+            if (lane < nw) {
+                const bool nx = lane + 1 < nw;
+                const real p0 = nx ? sh0[lane + 1][0] : real(0), p1 = nx ? sh0[lane + 1][1] : real(0);
+                const real p2 = nx ? sh0[lane + 1][2] : real(0);
+                const real q0 = nx ? sh1[lane + 1][0] : real(0), q1 = nx ? sh1[lane + 1][1] : real(0);
+                const real q2 = nx ? sh1[lane + 1][2] : real(0);
+                const real la = sh31[lane][0], lb = sh31[lane][1], lc = sh31[lane][2], lr = sh31[lane][3];
+                const real ly = sh31[lane][4], lu = sh31[lane][5], lv = sh31[lane][6];
+                // lane 31's separator row in (x_{lane 30}, S_w, x_{next warp's lane 0})
+                const real A1 = la * lu, B1 = la * lv + lb + lc * p1, C1 = lc * p2, R1 = lr - la * ly - lc * p0;
+                A2 = A1 * sh30[lane][1];
+                B2 = A1 * sh30[lane][2] + B1 + C1 * q1;
+                C2 = C1 * q2;
+                R2[0] = R1 - A1 * sh30[lane][0] - C1 * q0;
+            }
+            warp_cr<real, 1>(A2, B2, C2, R2, lane);
+            if (lane < nw) shS[lane] = R2[0] / B2;
+        }
+        __syncthreads();
+        if (!act) return;
+        const real Sw = shS[warp], Sm = warp > 0 ? shS[warp - 1] : real(0);
+        const real st = lane == 31 ? Sw : Y + U * Sm + V * Sw;      // this thread's separator
+        const real up1 = __shfl_up_sync(kFull, st, 1);
+        const real sm = lane == 0 ? Sm : up1;                          // the previous thread's
+#pragma unroll
+        for (int j = 0; j < m1; j++) x[j] = y[j] + uu[j] * sm + vv[j] * st;
+        x[m1] = st;
+    }
+    if (!any) return;
+    real o[M];
+    if (kMode != 0) {
+#pragma unroll
+        for (int j = 0; j < M; j++) o[j] = x[j];
+    } else {
+        // epilogue: P^n + increment, sponge (Eq. 30) on the last stage, zero
+        // discharge where dry
+        load_run<real, M>(o, A.base + lo + f);
+        const uint32_t bits = A.mask[(size_t)line * A.nwords + (f >> 5)] >> (f & 31);
+        // the sponge only where the segment reaches into one (Eq. 30)
+        bool sponge = false;
+        if (A.final_stage) {
+            const int *w = A.c.spw;
+            const int lo_w = w[A.dir == 0 ? 0 : 2], hi_w = w[A.dir == 0 ? 1 : 3];
+            const int ac_lo = w[A.dir == 0 ? 2 : 0], ac_hi = w[A.dir == 0 ? 3 : 1];
+            const int across = A.dir == 0 ? A.geo.ny : A.geo.nx;
+            sponge = f < lo_w || f + M > n - hi_w || line < ac_lo || line >= across - ac_hi;
+        }
+#pragma unroll
+        for (int j = 0; j < M; j++) {
+            real v = o[j] + x[j];
+            if (sponge) {
+                const int k = f + j;
+                const int i = A.dir == 0 ? k : line, jj = A.dir == 0 ? line : k;
+                if (k < n) v *= sponge_gamma<real>(A.c, A.geo, i, jj);
+            }
+            if ((bits >> j) & 1u) v = real(0);
+            o[j] = v;
+        }
+    }
+    if (f + M <= n) {
+        store_run<real, M>(out + f, o);
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; j++)
+            if (f + j < n) out[f + j] = o[j];
+    }
+}
+
+// ----------------------------------------- line solves, segments in shared memory
+//
+// Lines too long for one segment per thread in registers (FP32 beyond 8192
+// rows, FP64 beyond 4096).
+//
+// One line of one family, segments in shared memory (x-row or y-column): the whole solve and epilogue.
 // kMode 0: the step's solve, P^n + x with the sponge and the dry mask;
 // 1: the transposed system T^T y = r (the adjoint), whose row k is
 // (c_{k-1}, b_k, a_{k+1}) of T's rows with T's boundary rows, y alone;
 // 2: the step's system T x = r, x alone.
 template <typename real, int M, int kMode = 0>
-__device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, unsigned char *smem_raw)
+__device__ __forceinline__ void line_solve_seg(const LineArgs<real> &A, int line, unsigned char *smem_raw)
 {
     const int n = A.n, S = A.nseg, N2 = 2 * S;
     constexpr int m = M;                             // rows per segment
@@ -1168,39 +1609,61 @@ __device__ __forceinline__ void line_solve(const LineArgs<real> &A, int line, un
     }
 }
 
-template <typename real, int M>
-__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(const __grid_constant__ LinePair<real> PA)
+// The segment length of the line's family picks the instance.
+template <typename real, int kMode>
+__device__ __forceinline__ void line_solve_any(const LineArgs<real> &A, int line, LineShared<real> &L)
 {
-    // blocks [0, ny) solve x-rows, the rest y-columns
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
-    const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
-    line_solve<real, M>(PA.L[fam], line, smem_raw);
+    if (A.mshift == 3)
+        line_solve_reg<real, 8, kMode>(A, line, L);
+    else if (A.mshift == 2)
+        line_solve_reg<real, 4, kMode>(A, line, L);
+    else
+        line_solve_reg<real, 2, kMode>(A, line, L);
 }
 
-// The adjoint's solves (kMode 1: transposed, 2: plain), solutions alone:
-// x-rows and y-columns in one launch.
+template <typename real, int kMode>
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(const __grid_constant__ LinePair<real> PA)
+{
+    // blocks [0, nlines of x) solve x-rows, the rest y-columns
+    __shared__ LineShared<real> L;
+    const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
+    const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
+    line_solve_any<real, kMode>(PA.L[fam], line, L);
+}
+
 template <typename real, int M, int kMode>
-__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines_t(const __grid_constant__ LinePair<real> PA)
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines_seg(const __grid_constant__ LinePair<real> PA)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
     const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
-    line_solve<real, M, kMode>(PA.L[fam], line, smem_raw);
+    line_solve_seg<real, M, kMode>(PA.L[fam], line, smem_raw);
 }
 
 // Ensemble: lines of many members and both families in one launch, all of
-// one segment length M.  desc[b] names block b's family (x) and line (y).
-template <typename real, int M>
+// one configuration.  desc[b] names block b's family (x) and line (y).
+template <typename real>
 __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512)
     k_lines_batch(const LineArgs<real> *__restrict__ args, const int2 *__restrict__ desc)
+{
+    __shared__ __align__(16) LineArgs<real> A;
+    __shared__ LineShared<real> L;
+    const int2 d = desc[blockIdx.x];
+    load_args(A, args + d.x);
+    __syncthreads();
+    line_solve_any<real, 0>(A, d.y, L);
+}
+
+template <typename real, int M>
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512)
+    k_lines_batch_seg(const LineArgs<real> *__restrict__ args, const int2 *__restrict__ desc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) LineArgs<real> A;
     const int2 d = desc[blockIdx.x];
     load_args(A, args + d.x);
     __syncthreads();
-    line_solve<real, M>(A, d.y, smem_raw);
+    line_solve_seg<real, M>(A, d.y, smem_raw);
 }
 
 }  // namespace
@@ -1333,82 +1796,108 @@ cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const 
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
 {
-    static bool configured = false;
+    static bool configured[3] = {false, false, false};
     const size_t smem = sizeof(StencilSmem<real>);
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    const int spec = stencil_spec(a);
+    auto *kern = spec == 1 ? k_stencil<real, 1> : spec == 2 ? k_stencil<real, 2> : k_stencil<real, 0>;
+    if (!configured[spec]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured[spec] = true;
     }
     dim3 grid((a.geo.nx + kTile - 1) / kTile, (a.geo.ny + kTile - 1) / kTile);
-    k_stencil<real><<<grid, kStencilThreads, smem, st>>>(a);
+    kern<<<grid, kStencilThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_ghost_batch(const GhostArgs<real> *args, const int *start, int n, int nblocks, int64_t k,
-                               cudaStream_t st)
+                               const int64_t *kdev, cudaStream_t st)
 {
-    if (nblocks > 0) k_ghost_batch<real><<<nblocks, 128, 0, st>>>(args, start, n, k);
+    if (nblocks > 0) k_ghost_batch<real><<<nblocks, 128, 0, st>>>(args, start, n, k, kdev);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_counter(int64_t *p, int64_t v, int add) { *p = add ? *p + v : v; }
+}  // namespace
+
+cudaError_t launch_counter(int64_t *p, int64_t v, int add, cudaStream_t st)
+{
+    k_counter<<<1, 1, 0, st>>>(p, v, add);
     return cudaGetLastError();
 }
 
 template <typename real>
-cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, cudaStream_t st)
+cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, int spec,
+                                 cudaStream_t st)
 {
-    static bool configured = false;
+    static bool configured[3] = {false, false, false};
+    if (spec < 0 || spec > 2) return cudaErrorInvalidValue;
     const size_t smem = sizeof(StencilSmem<real>);
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil_batch<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    auto *kern = spec == 1 ? k_stencil_batch<real, 1> : spec == 2 ? k_stencil_batch<real, 2> : k_stencil_batch<real, 0>;
+    if (!configured[spec]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured[spec] = true;
     }
-    if (nblocks > 0) k_stencil_batch<real><<<nblocks, kStencilThreads, smem, st>>>(args, desc);
+    if (nblocks > 0) kern<<<nblocks, kStencilThreads, smem, st>>>(args, desc);
     return cudaGetLastError();
 }
 
-int line_seg_shift(int n, int real_bytes)
+namespace {
+
+// The shared-memory solver's segments: 8 rows up to 1024 rows, 16 up to
+// 4096, 32 above (at most 512 segments, and two 8192-row FP32 lines fit one
+// SM's shared memory); fewer for short lines so that there are at least 2
+// segments of >= 2 rows
+int seg_shift(int n)
 {
-    // 8 rows per segment up to 1024 rows, 16 up to 4096, 32 above (at most
-    // 512 segments, and two 8192-row FP32 lines fit one SM's shared memory);
-    // fewer for short lines so that there are at least 2 segments of >= 2
-    // rows
-    (void)real_bytes;
     int sh = n > 4096 ? 5 : (n > 1024 ? 4 : 3);
     while (sh > 1 && (n >> sh) < 2) sh--;
     return sh;
 }
 
-int line_segments(int n, int real_bytes)
+template <typename real>
+size_t seg_smem_bytes(int n, int nseg)
 {
-    const int m = 1 << line_seg_shift(n, real_bytes);
-    return (n + m - 1) / m;
+    const int m = 1 << seg_shift(n);
+    return sizeof(real) * ((size_t)3 * m * (nseg | 1) + (size_t)8 * nseg) + sizeof(uint32_t) * (size_t)((n + 31) / 32);
 }
 
-int line_seg_stride(int nseg) { return nseg | 1; }
+}  // namespace
 
-// Block size of a line solve: a thread per segment, and at most 8 elements
-// of P^n per thread held through the solve (16 with 32-row segments, so that
-// the longest lines stay within 1024 threads): segments of 16 or 32 rows get
-// two threads each, which hides more of the loads' latency.
-int line_threads(int n, int real_bytes)
+LineCfg line_config(int n, int real_bytes)
 {
-    const int m = 1 << line_seg_shift(n, real_bytes);
+    LineCfg c;
+    if (real_bytes == 4 ? n <= 8192 : n <= 4096) {
+        // one segment per thread in registers: 8 rows (2 or 4 on lines of at
+        // most 64 or 128 rows, which one warp then holds), a multiple of 32
+        // threads, at most 1024 (FP32) or 512 (FP64)
+        c.algo = 0;
+        c.mshift = n <= 64 ? 1 : (n <= 128 ? 2 : 3);
+        const int m = 1 << c.mshift;
+        c.nseg = round_up((n + m - 1) / m, 32);
+        c.threads = c.nseg;
+        c.sp = 0;
+        c.smem = 0;
+        return c;
+    }
+    // segments in shared memory: a thread per segment, and at most 8
+    // elements of P^n per thread held through the solve (16 with 32-row
+    // segments, so that the longest lines stay within 1024 threads)
+    c.algo = 1;
+    c.mshift = seg_shift(n);
+    const int m = 1 << c.mshift;
+    c.nseg = (n + m - 1) / m;
+    c.sp = c.nseg | 1;
     const int own = m == 32 ? 16 : (m < 8 ? m : 8);
-    int t = line_segments(n, real_bytes);
+    int t = c.nseg;
     if ((n + own - 1) / own > t) t = (n + own - 1) / own;
     t = round_up(t, 32);
-    return t < 32 ? 32 : t;
-}
-
-template <typename real>
-size_t line_smem_bytes(int n, int nseg)
-{
-    const int m = 1 << line_seg_shift(n, (int)sizeof(real));
-    return sizeof(real) * ((size_t)3 * m * line_seg_stride(nseg) + (size_t)8 * nseg) +
-           sizeof(uint32_t) * (size_t)((n + 31) / 32);
+    c.threads = t < 32 ? 32 : t;
+    c.smem = real_bytes == 4 ? seg_smem_bytes<float>(n, c.nseg) : seg_smem_bytes<double>(n, c.nseg);
+    return c;
 }
 
 template <typename real>
@@ -1433,67 +1922,92 @@ cudaError_t launch_lines_solution(const LinePair<real> &p, cudaStream_t st)
 }
 
 template <typename real, int kMode>
-auto lines_kernel(int sh)
+auto seg_kernel(int sh)
 {
-    return sh == 1 ? k_lines_t<real, 2, kMode> : sh == 2 ? k_lines_t<real, 4, kMode> : sh == 3 ? k_lines_t<real, 8, kMode>
-         : sh == 4 ? k_lines_t<real, 16, kMode> : k_lines_t<real, 32, kMode>;
+    return sh == 1 ? k_lines_seg<real, 2, kMode> : sh == 2 ? k_lines_seg<real, 4, kMode>
+         : sh == 3 ? k_lines_seg<real, 8, kMode> : sh == 4 ? k_lines_seg<real, 16, kMode>
+                   : k_lines_seg<real, 32, kMode>;
+}
+
+int line_launches(int nx_lines, int n_x, int ny_lines, int n_y, int real_bytes)
+{
+    if (nx_lines <= 0 || ny_lines <= 0) return nx_lines > 0 || ny_lines > 0 ? 1 : 0;
+    const LineCfg a = line_config(n_x, real_bytes), b = line_config(n_y, real_bytes);
+    if (a.algo != b.algo) return 2;
+    return a.algo == 1 && (a.mshift != b.mshift || a.threads != b.threads) ? 2 : 1;
 }
 
 template <typename real>
 cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, int mode)
 {
-    size_t smem = 0;
-    int threads = 32;
+    if (mode < 0 || mode > 2) return cudaErrorInvalidValue;
+    LineCfg cf[2];
+    for (int f = 0; f < 2; f++) {
+        const LineArgs<real> &a = p.L[f];
+        if (a.nlines <= 0) continue;
+        cf[f] = line_config(a.n, (int)sizeof(real));
+        if (a.algo != cf[f].algo || a.mshift != cf[f].mshift || a.nseg != cf[f].nseg ||
+            (a.algo == 1 && a.sp != cf[f].sp))
+            return cudaErrorInvalidValue;
+    }
     const bool both = p.L[0].nlines > 0 && p.L[1].nlines > 0;
-    if (both && p.L[0].mshift != p.L[1].mshift) {   // one segment length per launch
-        LinePair<real> a = p, b = p;
+    // register-path families share a launch (each uses its own segment
+    // length and count); shared-memory ones need one segment length
+    if (both && (cf[0].algo != cf[1].algo ||
+                 (cf[0].algo == 1 && (cf[0].mshift != cf[1].mshift || cf[0].threads != cf[1].threads)))) {
+        LinePair<real> a = p, b = p;   // one configuration per launch
         a.L[1].nlines = 0;
         b.L[0].nlines = 0;
         cudaError_t e = launch_lines_impl<real>(a, st, mode);
         return e != cudaSuccess ? e : launch_lines_impl<real>(b, st, mode);
     }
-    for (int f = 0; f < 2; f++) {
-        const LineArgs<real> &a = p.L[f];
-        if (a.nlines <= 0) continue;
-        if (a.nseg * (1 << a.mshift) < a.n || a.sp != line_seg_stride(a.nseg)) return cudaErrorInvalidValue;
-        size_t b = line_smem_bytes<real>(a.n, a.nseg);
-        if (b > smem) smem = b;
-        int t = line_threads(a.n, (int)sizeof(real));
-        if (t > threads) threads = t;
+    const int blocks = p.L[0].nlines + p.L[1].nlines;
+    if (blocks <= 0) return cudaSuccess;
+    const LineCfg &c = p.L[0].nlines > 0 ? cf[0] : cf[1];
+    const int sh = c.mshift;
+    if (c.algo == 0) {
+        int threads = c.threads;
+        if (both && cf[1].threads > threads) threads = cf[1].threads;
+        auto *kern = mode == 1 ? k_lines<real, 1> : mode == 2 ? k_lines<real, 2> : k_lines<real, 0>;
+        kern<<<blocks, threads, 0, st>>>(p);
+        return cudaGetLastError();
     }
+    if (sh < 1 || sh > 5) return cudaErrorInvalidValue;
+    size_t smem = c.smem;
+    if (both && cf[1].smem > smem) smem = cf[1].smem;
     static int configured[3][6] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
-    const int sh = p.L[0].nlines > 0 ? p.L[0].mshift : p.L[1].mshift;
-    if (sh < 1 || sh > 5 || mode < 0 || mode > 2) return cudaErrorInvalidValue;
-    auto *kern = mode == 1 ? lines_kernel<real, 1>(sh)
-               : mode == 2 ? lines_kernel<real, 2>(sh)
-                           : (sh == 1 ? k_lines<real, 2> : sh == 2 ? k_lines<real, 4> : sh == 3 ? k_lines<real, 8>
-                                                       : sh == 4 ? k_lines<real, 16> : k_lines<real, 32>);
+    auto *kern = mode == 1 ? seg_kernel<real, 1>(sh) : mode == 2 ? seg_kernel<real, 2>(sh) : seg_kernel<real, 0>(sh);
     if ((int)smem > configured[mode][sh]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured[mode][sh] = (int)smem;
     }
-    const int blocks = p.L[0].nlines + p.L[1].nlines;
-    if (blocks > 0) kern<<<blocks, threads, smem, st>>>(p);
+    kern<<<blocks, c.threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 template <typename real>
-cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int nblocks, int mshift, int threads,
-                               size_t smem, cudaStream_t st)
+cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int nblocks, const LineCfg &cfg,
+                               cudaStream_t st)
 {
-    static int configured[6] = {0, 0, 0, 0, 0, 0};
-    if (mshift < 1 || mshift > 5 || threads < 32 || threads % 32 || threads > (sizeof(real) == 4 ? 1024 : 512))
-        return cudaErrorInvalidValue;
-    auto *kern = mshift == 1 ? k_lines_batch<real, 2> : mshift == 2 ? k_lines_batch<real, 4>
-               : mshift == 3 ? k_lines_batch<real, 8> : mshift == 4 ? k_lines_batch<real, 16>
-                             : k_lines_batch<real, 32>;
-    if ((int)smem > configured[mshift]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured[mshift] = (int)smem;
+    const int sh = cfg.mshift, threads = cfg.threads;
+    if (threads < 32 || threads % 32 || threads > (sizeof(real) == 4 ? 1024 : 512)) return cudaErrorInvalidValue;
+    if (nblocks <= 0) return cudaSuccess;
+    if (cfg.algo == 0) {
+        k_lines_batch<real><<<nblocks, threads, 0, st>>>(args, desc);
+        return cudaGetLastError();
     }
-    if (nblocks > 0) kern<<<nblocks, threads, smem, st>>>(args, desc);
+    static int configured[6] = {0, 0, 0, 0, 0, 0};
+    if (sh < 1 || sh > 5) return cudaErrorInvalidValue;
+    auto *kern = sh == 1 ? k_lines_batch_seg<real, 2> : sh == 2 ? k_lines_batch_seg<real, 4>
+               : sh == 3 ? k_lines_batch_seg<real, 8> : sh == 4 ? k_lines_batch_seg<real, 16>
+                         : k_lines_batch_seg<real, 32>;
+    if ((int)cfg.smem > configured[sh]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+        if (e != cudaSuccess) return e;
+        configured[sh] = (int)cfg.smem;
+    }
+    kern<<<nblocks, threads, cfg.smem, st>>>(args, desc);
     return cudaGetLastError();
 }
 
@@ -1533,11 +2047,10 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
     template cudaError_t launch_lines<real>(const LinePair<real> &, cudaStream_t);                       \
     template cudaError_t launch_lines_transposed<real>(const LinePair<real> &, cudaStream_t);            \
     template cudaError_t launch_lines_solution<real>(const LinePair<real> &, cudaStream_t);              \
-    template size_t line_smem_bytes<real>(int, int);                                                    \
     template cudaError_t launch_ghost_batch<real>(const GhostArgs<real> *, const int *, int, int, int64_t, \
-                                                  cudaStream_t);                                        \
-    template cudaError_t launch_stencil_batch<real>(const StencilArgs<real> *, const int2 *, int, cudaStream_t); \
-    template cudaError_t launch_lines_batch<real>(const LineArgs<real> *, const int2 *, int, int, int, size_t, \
+                                                  const int64_t *, cudaStream_t);                                        \
+    template cudaError_t launch_stencil_batch<real>(const StencilArgs<real> *, const int2 *, int, int, cudaStream_t); \
+    template cudaError_t launch_lines_batch<real>(const LineArgs<real> *, const int2 *, int, const LineCfg &, \
                                                   cudaStream_t);
 
 CEL_INSTANTIATE(float)

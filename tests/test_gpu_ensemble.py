@@ -45,17 +45,15 @@ def _members(K):
 
 
 def _line_launch_class(n, es):
-    # segment length and block size of the line solver: 2**shift rows per
-    # segment (8 up to 1024 rows, 16 up to 4096, 32 above, fewer for short
-    # lines), a thread per segment and at most 8 elements per thread (16 with
-    # 32-row segments), rounded up to a warp
-    sh = 5 if n > 4096 else (4 if n > 1024 else 3)
-    while sh > 1 and (n >> sh) < 2:
-        sh -= 1
-    m = 1 << sh
-    nseg = -(-n // m)
-    t = max(nseg, -(-n // (16 if m == 32 else min(m, 8))))
-    return sh, max(32, -(-t // 32) * 32)
+    # the line solver's configuration of a line of n rows: up to 8192 rows
+    # (FP32) or 4096 (FP64), one segment per thread in registers, of 2 rows
+    # up to 64, 4 up to 128, 8 above, in a multiple of 32 threads; longer
+    # lines in shared-memory segments of 32 rows, a thread per 16 elements
+    # (register-path lines of one block size share a launch)
+    if n <= (8192 if es == 4 else 4096):
+        sh = 1 if n <= 64 else (2 if n <= 128 else 3)
+        return 0, 0, -(-(-(-n // (1 << sh))) // 32) * 32
+    return 1, 5, -(-(-(-n // 16)) // 32) * 32
 
 
 def _pairs(scens, prec):
@@ -219,3 +217,45 @@ def test_ensemble_members_match_the_oracle(prec):
                 if np.linalg.norm(b) > 1e-12:
                     assert rel_l2(a, b) <= 10 * tol, f"member {k}: {name} at step {done}"
     ens.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_captured_cycles_equal_launches_one_by_one(prec):
+    """Once the history is full, cel_ensemble_step replays captured 6-step
+    cycles: the members must equal, bit for bit, those of the same ensemble
+    launching every kernel one by one, and the members stepped alone.  Steps
+    in uneven chunks start the cycles at several phases; a change of
+    boundary in between discards the graphs, which are captured again."""
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)
+    ga = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    gb = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    alone = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    ea = celeris.Ensemble(ga)
+    eb = celeris.Ensemble(gb)
+    eb.use_graphs(False)
+    total = 0
+    for n in (3, 13, 7, 20, 1, 12):
+        ea.step(n)
+        eb.step(n)
+        total += n
+    assert ea.graph_steps() >= 36 and eb.graph_steps() == 0
+    for m in alone:
+        m.step(total)
+    torch.cuda.synchronize()
+    _assert_equal(ga, gb)
+    _assert_equal(ga, alone)
+    # a boundary change: tables and graphs rebuilt
+    for grp in (ga, gb, alone):
+        grp[0].set_boundary(sc.N, sc.SOLID)
+    before = ea.graph_steps()
+    ea.step(14)
+    eb.step(14)
+    for m in alone:
+        m.step(14)
+    torch.cuda.synchronize()
+    assert ea.graph_steps() >= before + 6
+    _assert_equal(ga, gb)
+    _assert_equal(ga, alone)
+    ea.close()
+    eb.close()
