@@ -67,6 +67,8 @@ def parse():
                     help="default workload: steps of the ensemble measurement in the line (0: none)")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="default workload: steps of the adjoint measurement in the line (0: none)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the line solver's built-in split instead of autotuning it first")
     return ap.parse_args()
 
 
@@ -378,7 +380,7 @@ def measure_ensemble(steps, warmup, precision, world=1, rank=0):
                          "per_kernel": kernels, "per_kernel_from": f"a profiled run of {prof_steps} steps after "
                                                                   "the timed ones, kernel by kernel",
                          "step_gbs_algorithmic": gbs},
-            "graph_steps": graph_steps,
+            "graph_steps": graph_steps, "line_splits": TUNED,
             "finite": finite, "gpu_launches": launches, "clocks": clk}
     return line
 
@@ -461,11 +463,28 @@ def measure_adjoint(steps, warmup, precision, n=512, ckpt_request=None):
     return line
 
 
+TUNED = None
+
+
+def tune_lines(args):
+    """The line solver's split per class of line lengths, picked by the
+    project's autotuner on this GPU before anything is measured (every
+    measurement below runs under it)."""
+    global TUNED
+    if args.no_tune:
+        return
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1611_05984_gb300 import autotune
+    TUNED = autotune.tune(args.precision, cells=1 << 21, steps=4)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
         return
+    tune_lines(args)
     if args.workload == "ensemble256":
         run_ensemble(args)
         return
@@ -630,7 +649,7 @@ def main():
                            "l2": "inputs larger than L2 (workspace %.0f MB > 129 MB)"
                                  % (sol.workspace.numel() / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "render": render,
-                "ensemble": ensemble, "adjoint": adjoint,
+                "ensemble": ensemble, "adjoint": adjoint, "line_splits": TUNED,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

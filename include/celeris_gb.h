@@ -233,7 +233,7 @@ cel_status cel_render(cel_solver *s, const cel_render_params *params, void *rgba
  * every ckpt_every steps, then the reverse sweep, recomputing one segment of
  * states at a time from its checkpoint; it ends holding the state after
  * step N.  ckpt_every = 0 keeps every step's states, corrector iterates and
- * line right sides from the forward run instead, with no recomputation
+ * line solutions from the forward run instead, with no recomputation
  * (the scratch then grows with N: 3 (K + 1) values per cell and step, plus
  * 2 (K + 1) with the bed on the Boussinesq model); a negative ckpt_every is
  * CEL_ERR_INVALID_ARG.
@@ -282,6 +282,27 @@ cel_status cel_adjoint_input_gradient(cel_solver *s, const void *w_in_dev, void 
  * CEL_ERR_CUDA on a CUDA error, CEL_ERR_INVALID_ARG on bad arguments. */
 cel_status cel_adjoint_face_selfcheck(int32_t real_bytes, const void *in_dev, int32_t n, void *out_dev,
                                       void *cuda_stream);
+
+/* Line-solver splits (the per-line tridiagonal solves of Eq. 21-23).  A
+ * line of up to 8192 rows (FP32) or 4096 (FP64) is cut into segments of 2, 4
+ * or 8 rows, one per thread: the built-in rule takes 2 rows on lines of at
+ * most 64, 4 up to 128 and 8 above.  cel_set_line_split(real_bytes,
+ * max_rows, rows_per_thread) sets the rows per thread for the class of line
+ * lengths up to max_rows (above the next smaller class's bound), where the
+ * block of ceil(n / rows) threads, rounded up to 32, fits (1024 FP32, 512
+ * FP64); rows_per_thread 0 removes the class.  It is meant for an autotuner:
+ * the results of a line solve depend on its split at rounding level, so
+ * cel_step and ensembles that are to agree bit for bit must run under the
+ * same table.  The table is process-wide and applies to every later launch;
+ * an ensemble created before a change refuses to step (create it again).
+ * cel_reset_line_splits returns to the built-in rule.  cel_line_config
+ * reports the rows per thread and the block size a line of `rows` rows gets.
+ * CEL_ERR_INVALID_ARG for sizes or rows out of range.  The paper has one
+ * line solver (a cyclic reduction on the GPU, Sec. 3.3); the splits are this
+ * library's own. */
+cel_status cel_set_line_split(int32_t real_bytes, int32_t max_rows, int32_t rows_per_thread);
+cel_status cel_reset_line_splits(void);
+cel_status cel_line_config(int32_t real_bytes, int32_t rows, int32_t *rows_per_thread, int32_t *threads);
 
 /* Kernel launches issued by the most recent cel_step call. */
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);

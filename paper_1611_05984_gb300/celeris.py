@@ -38,7 +38,8 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_use_graphs", "cel_ensemble_graph_steps",
            "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
-           "cel_ensemble_last_error", "cel_ensemble_destroy", "cel_advance_noalloc", "cel_status_string",
+           "cel_ensemble_last_error", "cel_ensemble_destroy", "cel_advance_noalloc", "cel_set_line_split",
+           "cel_reset_line_splits", "cel_line_config", "cel_status_string",
            "cel_last_error", "cel_destroy"]
 
 
@@ -126,6 +127,9 @@ def load(build_if_missing: bool = True):
         L.cel_ensemble_profile_enable.argtypes = [vp, i32]
         L.cel_ensemble_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
         L.cel_ensemble_profile_disable.argtypes = [vp]
+        L.cel_set_line_split.argtypes = [i32, i32, i32]
+        L.cel_reset_line_splits.argtypes = []
+        L.cel_line_config.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.cel_ensemble_last_error.restype = ctypes.c_char_p
         L.cel_ensemble_last_error.argtypes = [vp]
         L.cel_ensemble_destroy.argtypes = [vp]
@@ -470,6 +474,28 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+def set_line_split(real_bytes: int, max_rows: int, rows_per_thread: int):
+    """The line solver's rows per thread for lines of up to max_rows rows
+    (cel_set_line_split; 0 removes the class)."""
+    st = load().cel_set_line_split(int(real_bytes), int(max_rows), int(rows_per_thread))
+    if st != CEL_OK:
+        raise CelerisError(st, "cel_set_line_split: bad size or rows per thread")
+
+
+def reset_line_splits():
+    """Back to the built-in rule (cel_reset_line_splits)."""
+    load().cel_reset_line_splits()
+
+
+def line_config(real_bytes: int, rows: int):
+    """(rows per thread, threads per block) of a line of `rows` rows."""
+    m, t = ctypes.c_int32(), ctypes.c_int32()
+    st = load().cel_line_config(int(real_bytes), int(rows), ctypes.byref(m), ctypes.byref(t))
+    if st != CEL_OK:
+        raise CelerisError(st, "cel_line_config: bad size")
+    return m.value, t.value
 
 
 def adjoint_scratch_bytes(solver: "Solver", nsteps: int, ngauges: int, ckpt_every: int = 100,

@@ -217,7 +217,7 @@ struct cel_solver {
     // the last ([stage][w, P, Q][ny][nx] dense), or NULL
     unsigned char *capture;
     size_t capture_field;
-    // and where to copy the line solves' right sides of every stage
+    // and where the line solves write their solutions of every stage
     // ([stage][U*, V* increments][line layout], capture_line bytes each), or NULL
     unsigned char *capture_rhs;
     size_t capture_line;
@@ -438,6 +438,11 @@ cel_status step_t(cel_solver *s, int nsteps)
             prof_end(s, pe);
             LinePair<real> lp;
             for (int dir = 0; dir < 2; dir++) lp.L[dir] = line_args<real>(s, coef, dir, stage, Kn);
+            if (s->capture_rhs) {   // the adjoint keeps each stage's line solutions (line layout)
+                unsigned char *dst = s->capture_rhs + s->capture_line * 2 * stage;
+                lp.L[0].xcap = reinterpret_cast<real *>(dst);
+                lp.L[1].xcap = reinterpret_cast<real *>(dst + s->capture_line);
+            }
             int pl = prof_begin(s, 1);
             CEL_CUDA(s, launch_lines<real>(lp, s->stream), "line solves");
             prof_end(s, pl);
@@ -449,14 +454,6 @@ cel_status step_t(cel_solver *s, int nsteps)
                                                    s->at<real>(L.P[1 - s->pcur]), s->at<real>(L.Qc[1 - s->pcur]), dst,
                                                    dst + f, dst + 2 * f, s->stream),
                          "iterate capture");
-            }
-            if (s->capture_rhs) {
-                unsigned char *dst = s->capture_rhs + s->capture_line * 2 * stage;
-                CEL_CUDA(s, cudaMemcpyAsync(dst, s->at<real>(L.U), sizeof(real) * (size_t)s->geo.ny * s->geo.px,
-                                            cudaMemcpyDeviceToDevice, s->stream), "right-side capture");
-                CEL_CUDA(s, cudaMemcpyAsync(dst + s->capture_line, s->at<real>(L.Vc),
-                                            sizeof(real) * (size_t)s->geo.nx * s->geo.py, cudaMemcpyDeviceToDevice,
-                                            s->stream), "right-side capture");
             }
         }
         finish_step(s, Kn);
@@ -991,6 +988,28 @@ cel_status cel_render(cel_solver *s, const cel_render_params *p, void *rgba_dev)
     return CEL_OK;
 }
 
+cel_status cel_set_line_split(int32_t real_bytes, int32_t max_rows, int32_t rows_per_thread)
+{
+    return line_split_set(real_bytes, max_rows, rows_per_thread) == 0 ? CEL_OK : CEL_ERR_INVALID_ARG;
+}
+
+cel_status cel_reset_line_splits(void)
+{
+    line_split_reset();
+    return CEL_OK;
+}
+
+cel_status cel_line_config(int32_t real_bytes, int32_t rows, int32_t *rows_per_thread, int32_t *threads)
+{
+    if ((real_bytes != 4 && real_bytes != 8) || rows < 2 ||
+        rows > (real_bytes == 4 ? CEL_MAX_LINE_F32 : CEL_MAX_LINE_F64) || !rows_per_thread || !threads)
+        return CEL_ERR_INVALID_ARG;
+    const LineCfg c = line_config(rows, real_bytes);
+    *rows_per_thread = 1 << c.mshift;
+    *threads = c.threads;
+    return CEL_OK;
+}
+
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches)
 {
     if (!s || !launches) return CEL_ERR_INVALID_ARG;
@@ -1240,6 +1259,7 @@ struct cel_ensemble {
     std::vector<Graph> graphs;
     bool use_graphs = true;
     int64_t graph_steps = 0;             // steps taken by replaying a graph, since creation
+    int split_gen = 0;                   // line-split table generation the plan was made with
     cudaStream_t cap_stream = nullptr;   // the library's own stream, for capture only
     size_t off_kdev = 0;                 // device step counter of the ghost tables
     int64_t kdev_val = 0;                // its value once the queued work has run
@@ -1430,6 +1450,9 @@ cel_status ens_prepare(cel_ensemble *e, int64_t &launches)
 {
     const int n = (int)e->m.size();
     const cel_solver *m0 = e->m[0];
+    if (line_split_generation() != e->split_gen)
+        return ens_fail(e, CEL_ERR_INVALID_ARG,
+                        "the line-solver splits changed after the ensemble was created (create it again)");
     uint64_t gsum = 0;
     for (int j = 0; j < n; j++) {
         const cel_solver *s = e->m[j];
@@ -1517,7 +1540,13 @@ cel_status ens_launch_step(cel_ensemble *e, cudaStream_t st, const int64_t *kdev
         const unsigned char *ent = e->tab + e->off_entries + (size_t)idx * e->entry_bytes;
         // the members step in lockstep: member 0's stage kind is every member's
         const Coef<real> c0 = make_coef<real>(e->m[0]->geo, e->m[0]->phy, e->m[0]->bnd);
-        const int spec = stencil_spec(stencil_args<real>(e->m[0], c0, stage, Kn));
+        int spec = stencil_spec(stencil_args<real>(e->m[0], c0, stage, Kn));
+        if (spec >= 3)   // the model and friction law too, where every member shares them
+            for (const cel_solver *s : e->m)
+                if (s->phy.model != e->m[0]->phy.model || s->phy.friction != e->m[0]->phy.friction) {
+                    spec -= 2;
+                    break;
+                }
         const int pe = e->prof.begin(0, st);
         ENS_CUDA(e, launch_stencil_batch<real>(reinterpret_cast<const StencilArgs<real> *>(ent),
                                                reinterpret_cast<const int2 *>(e->tab + e->off_tile_desc),
@@ -1690,6 +1719,7 @@ cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *tabl
     *out = nullptr;
     EnsPlan P;
     std::string why;
+    const int split_gen = line_split_generation();
     cel_status st = plan(members, n, P, why);
     if (st != CEL_OK) {
         put_msg(msg, msg_len, why);
@@ -1704,6 +1734,7 @@ cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *tabl
         return CEL_ERR_WORKSPACE_TOO_SMALL;
     }
     cel_ensemble *e = new cel_ensemble();
+    e->split_gen = split_gen;
     e->m.assign(members, members + n);
     e->es = members[0]->es;
     e->K = members[0]->params.corrector_iters;
@@ -1840,7 +1871,7 @@ struct AdjLayout {
     size_t ckpt, seg, iter, lam, G, rec, gij, total;
     size_t seg_slot, iter_slot, rhs_slot;   // two slots each: one segment recomputed while the next is reversed
     size_t gtab, xy;                        // the reverse's own ghost table and line-layout scratch
-    size_t rhs, xs, lBc, lBb, ld, ldl, lg;   // the bed's gradient (bed != 0)
+    size_t rhs, lBc, lBb, ld, ldl, lg;       // the bed's gradient (bed != 0)
     size_t ghost_bytes;
     int nseg, bed;
     int keep;   // every step kept from the forward run: one segment, one slot, no recomputation
@@ -1873,16 +1904,15 @@ AdjLayout adj_layout(const cel_solver *s, int N, int C, int ng, int bed)
     L.G = take(L.cells_bytes * 20);    // 3 steps x (E, F, G, F*, G*), and the corrector's
     L.rec = take((size_t)N * ng * s->es);
     L.gij = take((size_t)ng * 2 * sizeof(int32_t));
-    L.rhs = L.xs = L.lBc = L.lBb = L.ld = L.ldl = L.lg = 0;
+    L.rhs = L.lBc = L.lBb = L.ld = L.ldl = L.lg = 0;
     L.rhs_slot = 0;
     L.ghost_bytes = ghost_index(2, 0, 0, 0, 0, (s->geo.nx > s->geo.ny ? s->geo.nx : s->geo.ny) + 4) * s->es;
     L.gtab = take(L.ghost_bytes);
     L.xy = take(L.line_bytes * 2);
     if (bed) {
         const bool lines = s->params.model == CEL_BSNQ;
-        L.rhs_slot = lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0;   // every stage's right sides
+        L.rhs_slot = lines ? L.line_bytes * 2 * (size_t)(K + 1) * (size_t)C : 0;   // every stage's line solutions
         L.rhs = take(L.rhs_slot * slots);
-        L.xs = take(lines ? L.line_bytes * 2 : 0);                                  // and their solutions
         L.ldl = take(lines ? L.line_bytes * 2 : 0);                                 // ld of the line systems
         L.lBc = take((size_t)s->geo.pc * (s->grid.ny + 3) * s->es);
         L.lBb = take((size_t)(s->grid.nx + 2) * (s->grid.ny + 2) * s->es);
@@ -1940,7 +1970,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
     };
     auto iterf = [&](int k, int stage, int v) { return iterf_in(slot, k, stage, v); };
     const bool bed = grad_z != nullptr, bed_lines = bed && s->params.model == CEL_BSNQ;
-    auto rhsf_in = [&](int sl, int k, int stage) {   // right sides of `stage` of step k of the segment
+    auto rhsf_in = [&](int sl, int k, int stage) {   // line solutions of `stage` of step k of the segment
         return scr + L.rhs + L.rhs_slot * sl + L.line_bytes * 2 * ((size_t)k * (K + 1) + stage);
     };
     auto rhsf = [&](int k, int stage) { return rhsf_in(slot, k, stage); };
@@ -1958,7 +1988,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
                                       s->at<real>(s->lay.Qc[s->pcur]), segf_in(sl, k, 0), segf_in(sl, k, 1),
                                       segf_in(sl, k, 2), q);
     };
-    // one step, its corrector iterates and line right sides kept in slot sl
+    // one step, its corrector iterates and line solutions kept in slot sl
     auto kept_step = [&](int sl, int k) -> cel_status {
         s->capture = K > 0 ? reinterpret_cast<unsigned char *>(iterf_in(sl, k, 0, 0)) : nullptr;
         s->capture_field = L.cells_bytes;
@@ -2124,24 +2154,16 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
         return launch_lines_transposed<real>(lp, st);
     };
     // the line systems' dependence on d: the stage's solutions again from
-    // its captured right sides, with the transposed solves' still in Xr, Yr
+    // its line solutions kept by the forward run, with the transposed solves' still in Xr, Yr
     auto tri_bed = [&](const AdjArgs<real> &x, int k, int stage) -> cudaError_t {
         if (!bed_lines) return cudaSuccess;
         cudaError_t e = cudaEventRecord(ss.mu, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.ts, ss.mu, 0);
         if (e != cudaSuccess) return e;
-        real *Rx = reinterpret_cast<real *>(rhsf(k, stage)), *Ry = reinterpret_cast<real *>(rhsf(k, stage) + L.line_bytes);
-        real *Xs = reinterpret_cast<real *>(scr + L.xs), *Ys = reinterpret_cast<real *>(scr + L.xs + L.line_bytes);
-        LinePair<real> lp;
-        for (int dir = 0; dir < 2; dir++) {
-            lp.L[dir] = rline(x, dir);
-            lp.L[dir].rhs = dir == 0 ? Rx : Ry;
-            lp.L[dir].base = dir == 0 ? Rx : Ry;
-            lp.L[dir].sol = dir == 0 ? Xs : Ys;
-        }
-        e = launch_lines_solution<real>(lp, ss.ts);
-        if (e == cudaSuccess)
-            e = launch_adjoint_tri_bed<real>(x, Xs, Ys, Xr, Yr, s->at<real>(s->lay.dr), s->at<real>(s->lay.dc), ss.ts);
+        // the stage's line solutions, kept by the forward run's line solves
+        const real *Xs = reinterpret_cast<const real *>(rhsf(k, stage));
+        const real *Ys = reinterpret_cast<const real *>(rhsf(k, stage) + L.line_bytes);
+        e = launch_adjoint_tri_bed<real>(x, Xs, Ys, Xr, Yr, s->at<real>(s->lay.dr), s->at<real>(s->lay.dc), ss.ts);
         if (e == cudaSuccess) e = cudaEventRecord(ss.tri, ss.ts);
         tri_pending = e == cudaSuccess;
         return e;
@@ -2300,7 +2322,7 @@ cel_status adjoint_t(cel_solver *s, int N, int C, const int32_t *gij_host, int n
             CEL_CUDA(s, cudaMemsetAsync(Gb(sn, 0), 0, L.cells_bytes * 5, st), "adjoint");
         }
         nvtxRangePop();
-        CEL_CUDA(s, wait_tri(), "adjoint order");   // the captured right sides of this slot
+        CEL_CUDA(s, wait_tri(), "adjoint order");   // the captured line solutions of this slot
         CEL_CUDA(s, cudaEventRecord(ss.rev[slot], st), "adjoint order");
         if (sg > 0 && (stt = recompute(sg - 1)) != CEL_OK) return stt;   // overlaps this segment's reverse
     }

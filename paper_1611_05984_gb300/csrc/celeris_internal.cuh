@@ -166,6 +166,7 @@ struct LineArgs {
     const uint32_t *mask;  // dry bits, line-major words
     const real *base;      // P^n or Q^n, line-major
     real *sol;             // P^{n+1} = P^n + solution, line-major
+    real *xcap;            // or NULL: the step's solution itself as well (line-major), for the adjoint
     int dir;               // 0: x-lines (rows), 1: y-lines (columns)
     int n, nlines, pitch, nwords;
     int algo;              // 0: segments in registers, one per thread; 1: segments in shared memory
@@ -241,11 +242,13 @@ cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const 
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st);
 // The stencil kernel's stage specialisation: 1 for the AB3 predictor with
-// the ring history, 2 for the AM4 corrector, 0 for the other stages.
+// the ring history, 2 for the AM4 corrector, 3 and 4 for those of the
+// Boussinesq model with Manning friction, 0 for the other stages.
 template <typename real>
 inline int stencil_spec(const StencilArgs<real> &a)
 {
-    return a.kind == kAM4 ? 2 : (a.ring && a.kind == kAB3 ? 1 : 0);
+    const int s = a.kind == kAM4 ? 2 : (a.ring && a.kind == kAB3 ? 1 : 0);
+    return s > 0 && a.phy.model == kBsnq && a.phy.friction == kFricManning ? s + 2 : s;
 }
 // How a line of n rows is solved: the algorithm, rows per segment, segments,
 // the odd shared-memory stride (algo 1), threads per block and dynamic
@@ -255,6 +258,11 @@ struct LineCfg {
     size_t smem;
 };
 LineCfg line_config(int n, int real_bytes);
+// The register path's rows per thread per class of line lengths (0: the
+// built-in rule); the generation counts changes (ensembles plan with it).
+int line_split_set(int real_bytes, int max_rows, int rows_per_thread);
+void line_split_reset();
+int line_split_generation();
 // Launches that launch_lines and its kin issue for the two families.
 int line_launches(int nx_lines, int n_x, int ny_lines, int n_y, int real_bytes);
 

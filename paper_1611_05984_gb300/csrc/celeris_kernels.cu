@@ -22,6 +22,10 @@
 #include "celeris_internal.cuh"
 #include "celeris_physics.cuh"
 
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include <math.h>
 
 namespace cel {
@@ -396,18 +400,19 @@ struct Carry {
 // loads are in flight while the cell's right side is computed.
 // Stage specialisations of the stencil (kSpec): 0, any stage, its kind and
 // history layout read at run time; 1, the AB3 predictor with the ring
-// history (K >= 1); 2, the AM4 corrector.  The two hot stages then carry no
-// branches on the stage kind.
+// history (K >= 1); 2, the AM4 corrector; 3 and 4, the same two stages of
+// the Boussinesq model with Manning friction.  The hot stages then carry no
+// branches on the stage kind (nor on the model and friction law).
 template <int kSpec, typename real>
 __device__ __forceinline__ int stage_kind(const StencilArgs<real> &A)
 {
-    return kSpec == 1 ? kAB3 : (kSpec == 2 ? kAM4 : A.kind);
+    return kSpec == 1 || kSpec == 3 ? kAB3 : (kSpec == 2 || kSpec == 4 ? kAM4 : A.kind);
 }
 
 template <int kSpec, typename real>
 __device__ __forceinline__ bool stage_ring(const StencilArgs<real> &A)
 {
-    return kSpec == 1 ? true : (kSpec == 2 ? true : A.ring != 0);
+    return kSpec != 0 ? true : A.ring != 0;
 }
 
 template <typename real, int kSpec>
@@ -766,8 +771,13 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
     const real rdx = C.rdx, rdy = C.rdy, rdx2 = C.rdx2, rdy2 = C.rdy2, rdxdy4 = C.rdxdy4;
     const real rdx3h = C.rdx3h, rdy3h = C.rdy3h, rdxdy2h = C.rdxdy2h, rdx2dyh = C.rdx2dyh;
     const real Bd = C.Bd, B3 = C.B3, sixth = C.sixth;
-    const bool bsnq = A.phy.model == kBsnq;
+    const bool bsnq = kSpec >= 3 ? true : A.phy.model == kBsnq;
+    const int friction = kSpec >= 3 ? (int)kFricManning : A.phy.friction;
     const int lane = tid & 31;
+    // the sponge (Eq. 30) on the last stage, where the tile reaches into one
+    const bool sponge_tile = A.final_stage &&
+                             (O.x0() < C.spw[0] || O.x0() + kTile > nx - C.spw[1] || O.y0() < C.spw[2] ||
+                              O.y0() + kTile > ny - C.spw[3]);
     constexpr int kRows = kTile / (kStencilThreads / 32);   // rows per thread
 #pragma unroll 1
     for (int rr = 0; rr < kRows; rr++) {
@@ -797,9 +807,9 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
                  g * hb * (BxE - BxW) * rdx;
         real Gq = -(sm.Fx[2][cy][cx + 1] - sm.Fx[2][cy][cx]) * rdx - (sm.Fy[2][cy + 1][cx] - sm.Fy[2][cy][cx]) * rdy -
                   g * hb * (ByN - ByS) * rdy;
-        if (A.phy.friction != kFricNone) {   // Eq. 31-32 with the Eq. 14 device
+        if (friction != kFricNone) {   // Eq. 31-32 with the Eq. 14 device
             real hinv = desing(fmax(hb, real(0)), eps);
-            real fc = A.phy.friction == kFricManning ? C.fric * cbrt_r(hinv) : C.fric;
+            real fc = friction == kFricManning ? C.fric * cbrt_r(hinv) : C.fric;
             real mag = sqrt(P0 * P0 + Q0 * Q0);
             F -= fc * P0 * mag * hinv * hinv;
             Gq -= fc * Q0 * mag * hinv * hinv;
@@ -841,7 +851,7 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
             dU = advance<real, kSpec>(A, 1, real(0), F, Fs, kr, cu);
             dV = advance<real, kSpec>(A, 2, real(0), Gq, Gs, kr, cv);
             if (w1 < Bb) w1 = Bb;   // Reading A-D1
-            if (A.final_stage) {
+            if (sponge_tile) {
                 real gam = sponge_gamma<real>(C, G, i, j);
                 if (gam < real(1) && dd > real(0)) w1 = ws + gam * (w1 - ws);
             }
@@ -1292,6 +1302,16 @@ __device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line
     }
     if (!any) return;
     real o[M];
+    if (kMode == 0 && A.xcap) {   // the solution itself, for the adjoint's depth term
+        real *xc = A.xcap + lo;
+        if (f + M <= n) {
+            store_run<real, M>(xc + f, x);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; j++)
+                if (f + j < n) xc[f + j] = x[j];
+        }
+    }
     if (kMode != 0) {
 #pragma unroll
         for (int j = 0; j < M; j++) o[j] = x[j];
@@ -1598,7 +1618,9 @@ __device__ __forceinline__ void line_solve_seg(const LineArgs<real> &A, int line
         for (int u = 0; u < kMaxOwn; u++) {
             const int k = tid + u * T;
             if (k >= n) continue;
-            real v = own[u] + sR[seg_slot(k, mshift, sp)];
+            const real xk = sR[seg_slot(k, mshift, sp)];
+            if (A.xcap) A.xcap[(size_t)line * A.pitch + k] = xk;
+            real v = own[u] + xk;
             if (A.final_stage) {
                 int i = A.dir == 0 ? k : line, j = A.dir == 0 ? line : k;
                 v *= sponge_gamma<real>(A.c, G, i, j);
@@ -1796,10 +1818,11 @@ cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const 
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
 {
-    static bool configured[3] = {false, false, false};
+    static bool configured[5] = {false, false, false, false, false};
     const size_t smem = sizeof(StencilSmem<real>);
     const int spec = stencil_spec(a);
-    auto *kern = spec == 1 ? k_stencil<real, 1> : spec == 2 ? k_stencil<real, 2> : k_stencil<real, 0>;
+    auto *kern = spec == 1 ? k_stencil<real, 1> : spec == 2 ? k_stencil<real, 2> : spec == 3 ? k_stencil<real, 3>
+               : spec == 4 ? k_stencil<real, 4> : k_stencil<real, 0>;
     if (!configured[spec]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1832,10 +1855,12 @@ template <typename real>
 cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, int spec,
                                  cudaStream_t st)
 {
-    static bool configured[3] = {false, false, false};
-    if (spec < 0 || spec > 2) return cudaErrorInvalidValue;
+    static bool configured[5] = {false, false, false, false, false};
+    if (spec < 0 || spec > 4) return cudaErrorInvalidValue;
     const size_t smem = sizeof(StencilSmem<real>);
-    auto *kern = spec == 1 ? k_stencil_batch<real, 1> : spec == 2 ? k_stencil_batch<real, 2> : k_stencil_batch<real, 0>;
+    auto *kern = spec == 1 ? k_stencil_batch<real, 1> : spec == 2 ? k_stencil_batch<real, 2>
+               : spec == 3 ? k_stencil_batch<real, 3> : spec == 4 ? k_stencil_batch<real, 4>
+                           : k_stencil_batch<real, 0>;
     if (!configured[spec]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1867,15 +1892,79 @@ size_t seg_smem_bytes(int n, int nseg)
 
 }  // namespace
 
+// Rows per thread of the register path, per class of line lengths and per
+// precision, as set by cel_set_line_split (an autotuner's choices); a class
+// covers the lengths above the previous class's bound up to its own.
+namespace {
+struct SplitTable {
+    std::mutex mu;
+    std::vector<std::pair<int, int>> cls[2];   // (largest rows, rows per thread), ascending
+    int generation = 0;
+};
+SplitTable &split_table()
+{
+    static SplitTable t;
+    return t;
+}
+int max_line_threads(int real_bytes) { return real_bytes == 4 ? 1024 : 512; }
+}  // namespace
+
+int line_split_set(int real_bytes, int max_rows, int rows_per_thread)
+{
+    if ((real_bytes != 4 && real_bytes != 8) || max_rows < 2) return -1;
+    if (rows_per_thread != 0 && rows_per_thread != 2 && rows_per_thread != 4 && rows_per_thread != 8) return -1;
+    SplitTable &t = split_table();
+    std::lock_guard<std::mutex> lock(t.mu);
+    auto &v = t.cls[real_bytes == 8];
+    for (size_t k = 0; k < v.size(); k++)
+        if (v[k].first == max_rows) {
+            v.erase(v.begin() + k);
+            break;
+        }
+    if (rows_per_thread != 0) {
+        v.push_back(std::make_pair(max_rows, rows_per_thread));
+        std::sort(v.begin(), v.end());
+    }
+    t.generation++;
+    return 0;
+}
+
+void line_split_reset()
+{
+    SplitTable &t = split_table();
+    std::lock_guard<std::mutex> lock(t.mu);
+    t.cls[0].clear();
+    t.cls[1].clear();
+    t.generation++;
+}
+
+int line_split_generation()
+{
+    SplitTable &t = split_table();
+    std::lock_guard<std::mutex> lock(t.mu);
+    return t.generation;
+}
+
 LineCfg line_config(int n, int real_bytes)
 {
     LineCfg c;
     if (real_bytes == 4 ? n <= 8192 : n <= 4096) {
         // one segment per thread in registers: 8 rows (2 or 4 on lines of at
         // most 64 or 128 rows, which one warp then holds), a multiple of 32
-        // threads, at most 1024 (FP32) or 512 (FP64)
+        // threads, at most 1024 (FP32) or 512 (FP64); a class set by
+        // cel_set_line_split overrides the rows where its block fits
         c.algo = 0;
         c.mshift = n <= 64 ? 1 : (n <= 128 ? 2 : 3);
+        {
+            SplitTable &t = split_table();
+            std::lock_guard<std::mutex> lock(t.mu);
+            for (const auto &e : t.cls[real_bytes == 8])
+                if (n <= e.first) {
+                    const int m = e.second, tt = round_up((n + m - 1) / m, 32);
+                    if (tt <= max_line_threads(real_bytes)) c.mshift = m == 2 ? 1 : (m == 4 ? 2 : 3);
+                    break;
+                }
+        }
         const int m = 1 << c.mshift;
         c.nseg = round_up((n + m - 1) / m, 32);
         c.threads = c.nseg;

@@ -110,3 +110,38 @@ def test_adjoint_entry_points_reject_bad_arguments_without_gpu_work():
     assert L.cel_adjoint_face_selfcheck(4, None, -1, None, None) == 1    # a negative count
     assert L.cel_adjoint_face_selfcheck(8, None, 5, None, None) == 1     # NULL buffers
     assert L.cel_adjoint_face_selfcheck(4, None, 0, None, None) == 0     # nothing to do
+
+
+def test_line_split_table():
+    """The line solver's split per class of line lengths (cel_set_line_split,
+    the autotuner's setting): the built-in rule, a class overriding it where
+    the block fits, removal, reset, and the argument checks.  Host logic."""
+    L = celeris.load()
+    celeris.reset_line_splits()
+    try:
+        assert celeris.line_config(4, 50) == (2, 32)
+        assert celeris.line_config(4, 100) == (4, 32)
+        assert celeris.line_config(4, 2048) == (8, 256)
+        assert celeris.line_config(4, 8192) == (8, 1024)
+        assert celeris.line_config(8, 4096) == (8, 512)
+        celeris.set_line_split(4, 256, 4)          # lines of 129..256 rows: 4 rows per thread
+        assert celeris.line_config(4, 200) == (4, 64)
+        assert celeris.line_config(4, 100) == (4, 32)   # below the class: the same class (the first that fits)
+        assert celeris.line_config(4, 300) == (8, 64)   # above it: the built-in rule
+        assert celeris.line_config(8, 200) == (8, 32)   # the other precision is untouched
+        celeris.set_line_split(4, 8192, 2)         # 4096 threads would not fit: the built-in rule
+        assert celeris.line_config(4, 8192) == (8, 1024)
+        assert celeris.line_config(4, 300) == (2, 160)  # where it fits, the class 257..8192 applies
+        celeris.set_line_split(4, 256, 0)          # removed: lines of 200 rows fall in the 8192 class
+        assert celeris.line_config(4, 200) == (2, 128)
+        celeris.set_line_split(4, 8192, 0)
+        assert celeris.line_config(4, 200) == (8, 32)
+        with pytest.raises(celeris.CelerisError):
+            celeris.set_line_split(4, 256, 3)
+        with pytest.raises(celeris.CelerisError):
+            celeris.set_line_split(2, 256, 4)
+        with pytest.raises(celeris.CelerisError):
+            celeris.line_config(4, 20000)
+    finally:
+        celeris.reset_line_splits()
+    assert celeris.line_config(4, 200) == (8, 32)

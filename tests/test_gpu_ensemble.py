@@ -259,3 +259,27 @@ def test_captured_cycles_equal_launches_one_by_one(prec):
     _assert_equal(ga, alone)
     ea.close()
     eb.close()
+
+
+def test_ensemble_under_a_tuned_split():
+    """With a line split set (as the autotuner sets it), the ensemble and the
+    members stepped alone still agree bit for bit; an ensemble planned before
+    the split changed refuses to step."""
+    from paper_1611_05984_gb300 import celeris
+    celeris.reset_line_splits()
+    try:
+        celeris.set_line_split(4, 512, 4)
+        scens = _members(1)
+        alone, together = _pairs(scens, "f32")
+        ens = celeris.Ensemble(together)
+        ens.step(15)
+        for m in alone:
+            m.step(15)
+        torch.cuda.synchronize()
+        _assert_equal(alone, together)
+        celeris.set_line_split(4, 512, 2)
+        with pytest.raises(celeris.CelerisError, match="splits changed"):
+            ens.step(1)
+        ens.close()
+    finally:
+        celeris.reset_line_splits()

@@ -391,3 +391,22 @@ def test_full_size_beach_from_rest():
             assert rel_l2(Pg, Po) <= 10 * TOL[p], f"{p}: P at step {done}"
             assert rel_l2(Qg, Qo) <= 10 * TOL[p], f"{p}: Q at step {done}"
     assert np.max(np.abs(wo[:, :40])) > 0.1            # the maker's waves are in
+
+
+@pytest.mark.parametrize("m", [2, 4, 8])
+def test_line_splits_match_oracle(m):
+    """Every split the line-solver autotuner may pick (2, 4 or 8 rows per
+    thread: blocks of 128, 64 or 32 threads for the 200-row x-lines and
+    96, 64 or 32 for the 150-row y-lines) against the oracle, FP64 and FP32:
+    the beach crop with its sine maker, sponges and moving shoreline."""
+    from paper_1611_05984_gb300 import celeris
+    celeris.reset_line_splits()
+    try:
+        for rb in (4, 8):
+            celeris.set_line_split(rb, 256, m)
+        assert celeris.line_config(4, 200)[0] == m and celeris.line_config(8, 150)[0] == m
+        s = sc.beach(nx=200, ny=150, sponge=20)
+        _lockstep(s, "f64", 300)
+        _lockstep(s, "f32", 300)
+    finally:
+        celeris.reset_line_splits()
