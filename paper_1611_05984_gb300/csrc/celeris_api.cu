@@ -1540,13 +1540,7 @@ cel_status ens_launch_step(cel_ensemble *e, cudaStream_t st, const int64_t *kdev
         const unsigned char *ent = e->tab + e->off_entries + (size_t)idx * e->entry_bytes;
         // the members step in lockstep: member 0's stage kind is every member's
         const Coef<real> c0 = make_coef<real>(e->m[0]->geo, e->m[0]->phy, e->m[0]->bnd);
-        int spec = stencil_spec(stencil_args<real>(e->m[0], c0, stage, Kn));
-        if (spec >= 3)   // the model and friction law too, where every member shares them
-            for (const cel_solver *s : e->m)
-                if (s->phy.model != e->m[0]->phy.model || s->phy.friction != e->m[0]->phy.friction) {
-                    spec -= 2;
-                    break;
-                }
+        const int spec = stencil_spec(stencil_args<real>(e->m[0], c0, stage, Kn));
         const int pe = e->prof.begin(0, st);
         ENS_CUDA(e, launch_stencil_batch<real>(reinterpret_cast<const StencilArgs<real> *>(ent),
                                                reinterpret_cast<const int2 *>(e->tab + e->off_tile_desc),

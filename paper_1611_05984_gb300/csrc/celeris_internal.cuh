@@ -242,13 +242,11 @@ cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const 
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st);
 // The stencil kernel's stage specialisation: 1 for the AB3 predictor with
-// the ring history, 2 for the AM4 corrector, 3 and 4 for those of the
-// Boussinesq model with Manning friction, 0 for the other stages.
+// the ring history, 2 for the AM4 corrector, 0 for the other stages.
 template <typename real>
 inline int stencil_spec(const StencilArgs<real> &a)
 {
-    const int s = a.kind == kAM4 ? 2 : (a.ring && a.kind == kAB3 ? 1 : 0);
-    return s > 0 && a.phy.model == kBsnq && a.phy.friction == kFricManning ? s + 2 : s;
+    return a.kind == kAM4 ? 2 : (a.ring && a.kind == kAB3 ? 1 : 0);
 }
 // How a line of n rows is solved: the algorithm, rows per segment, segments,
 // the odd shared-memory stride (algo 1), threads per block and dynamic

@@ -400,13 +400,12 @@ struct Carry {
 // loads are in flight while the cell's right side is computed.
 // Stage specialisations of the stencil (kSpec): 0, any stage, its kind and
 // history layout read at run time; 1, the AB3 predictor with the ring
-// history (K >= 1); 2, the AM4 corrector; 3 and 4, the same two stages of
-// the Boussinesq model with Manning friction.  The hot stages then carry no
-// branches on the stage kind (nor on the model and friction law).
+// history (K >= 1); 2, the AM4 corrector.  The two hot stages then carry no
+// branches on the stage kind.
 template <int kSpec, typename real>
 __device__ __forceinline__ int stage_kind(const StencilArgs<real> &A)
 {
-    return kSpec == 1 || kSpec == 3 ? kAB3 : (kSpec == 2 || kSpec == 4 ? kAM4 : A.kind);
+    return kSpec == 1 ? kAB3 : (kSpec == 2 ? kAM4 : A.kind);
 }
 
 template <int kSpec, typename real>
@@ -771,8 +770,8 @@ __device__ __forceinline__ void stencil_tile(const StencilArgs<real> &A, const O
     const real rdx = C.rdx, rdy = C.rdy, rdx2 = C.rdx2, rdy2 = C.rdy2, rdxdy4 = C.rdxdy4;
     const real rdx3h = C.rdx3h, rdy3h = C.rdy3h, rdxdy2h = C.rdxdy2h, rdx2dyh = C.rdx2dyh;
     const real Bd = C.Bd, B3 = C.B3, sixth = C.sixth;
-    const bool bsnq = kSpec >= 3 ? true : A.phy.model == kBsnq;
-    const int friction = kSpec >= 3 ? (int)kFricManning : A.phy.friction;
+    const bool bsnq = A.phy.model == kBsnq;
+    const int friction = A.phy.friction;
     const int lane = tid & 31;
     // the sponge (Eq. 30) on the last stage, where the tile reaches into one
     const bool sponge_tile = A.final_stage &&
@@ -969,12 +968,14 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Cyclic reduction of a warp's 32 rows a x_{i-1} + b x_i + c x_{i+1} = r
 // (rows beyond the warp decoupled), NR right sides at once: afterwards row i
-// reads b x_i = r.
+// reads b x_i = r.  Where only the first `rows` rows couple (the rest are
+// identity rows), ceil(log2(rows)) levels decouple them.
 template <typename real, int NR>
-__device__ __forceinline__ void warp_cr(real &a, real &b, real &c, real (&r)[NR], int lane)
+__device__ __forceinline__ void warp_cr(real &a, real &b, real &c, real (&r)[NR], int lane, int rows = 32)
 {
 #pragma unroll
     for (int s = 1; s < 32; s <<= 1) {
+        if (s >= rows) break;
         const real ib = real(1) / b;   // each row's reciprocal, once, to both neighbours
         const real am = __shfl_up_sync(kFull, a, s), ibm = __shfl_up_sync(kFull, ib, s);
         const real cm = __shfl_up_sync(kFull, c, s);
@@ -1287,7 +1288,7 @@ __device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line
                 C2 = C1 * q2;
                 R2[0] = R1 - A1 * sh30[lane][0] - C1 * q0;
             }
-            warp_cr<real, 1>(A2, B2, C2, R2, lane);
+            warp_cr<real, 1>(A2, B2, C2, R2, lane, nw);
             if (lane < nw) shS[lane] = R2[0] / B2;
         }
         __syncthreads();
@@ -1643,8 +1644,12 @@ __device__ __forceinline__ void line_solve_any(const LineArgs<real> &A, int line
         line_solve_reg<real, 2, kMode>(A, line, L);
 }
 
-template <typename real, int kMode>
-__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines(const __grid_constant__ LinePair<real> PA)
+// kOcc: blocks of at most 256 threads held to 48 registers, so that 5 of
+// them fit an SM (the register path is latency-bound); else up to 1024
+// (FP32) or 512 (FP64) threads.
+template <typename real, int kMode, int kOcc = 0>
+__global__ void __launch_bounds__(kOcc ? 256 : (sizeof(real) == 4 ? 1024 : 512), kOcc ? 5 : 1)
+    k_lines(const __grid_constant__ LinePair<real> PA)
 {
     // blocks [0, nlines of x) solve x-rows, the rest y-columns
     __shared__ LineShared<real> L;
@@ -1664,8 +1669,8 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines_seg(co
 
 // Ensemble: lines of many members and both families in one launch, all of
 // one configuration.  desc[b] names block b's family (x) and line (y).
-template <typename real>
-__global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512)
+template <typename real, int kOcc = 0>
+__global__ void __launch_bounds__(kOcc ? 256 : (sizeof(real) == 4 ? 1024 : 512), kOcc ? 5 : 1)
     k_lines_batch(const LineArgs<real> *__restrict__ args, const int2 *__restrict__ desc)
 {
     __shared__ __align__(16) LineArgs<real> A;
@@ -1818,11 +1823,10 @@ cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const 
 template <typename real>
 cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
 {
-    static bool configured[5] = {false, false, false, false, false};
+    static bool configured[3] = {false, false, false};
     const size_t smem = sizeof(StencilSmem<real>);
     const int spec = stencil_spec(a);
-    auto *kern = spec == 1 ? k_stencil<real, 1> : spec == 2 ? k_stencil<real, 2> : spec == 3 ? k_stencil<real, 3>
-               : spec == 4 ? k_stencil<real, 4> : k_stencil<real, 0>;
+    auto *kern = spec == 1 ? k_stencil<real, 1> : spec == 2 ? k_stencil<real, 2> : k_stencil<real, 0>;
     if (!configured[spec]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1855,12 +1859,10 @@ template <typename real>
 cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, int spec,
                                  cudaStream_t st)
 {
-    static bool configured[5] = {false, false, false, false, false};
-    if (spec < 0 || spec > 4) return cudaErrorInvalidValue;
+    static bool configured[3] = {false, false, false};
+    if (spec < 0 || spec > 2) return cudaErrorInvalidValue;
     const size_t smem = sizeof(StencilSmem<real>);
-    auto *kern = spec == 1 ? k_stencil_batch<real, 1> : spec == 2 ? k_stencil_batch<real, 2>
-               : spec == 3 ? k_stencil_batch<real, 3> : spec == 4 ? k_stencil_batch<real, 4>
-                           : k_stencil_batch<real, 0>;
+    auto *kern = spec == 1 ? k_stencil_batch<real, 1> : spec == 2 ? k_stencil_batch<real, 2> : k_stencil_batch<real, 0>;
     if (!configured[spec]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -2057,7 +2059,10 @@ cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, int mode
     if (c.algo == 0) {
         int threads = c.threads;
         if (both && cf[1].threads > threads) threads = cf[1].threads;
-        auto *kern = mode == 1 ? k_lines<real, 1> : mode == 2 ? k_lines<real, 2> : k_lines<real, 0>;
+        const bool occ = sizeof(real) == 4 && threads <= 256;
+        auto *kern = mode == 1 ? (occ ? k_lines<real, 1, 1> : k_lines<real, 1>)
+                   : mode == 2 ? (occ ? k_lines<real, 2, 1> : k_lines<real, 2>)
+                               : (occ ? k_lines<real, 0, 1> : k_lines<real, 0>);
         kern<<<blocks, threads, 0, st>>>(p);
         return cudaGetLastError();
     }
@@ -2083,7 +2088,10 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
     if (threads < 32 || threads % 32 || threads > (sizeof(real) == 4 ? 1024 : 512)) return cudaErrorInvalidValue;
     if (nblocks <= 0) return cudaSuccess;
     if (cfg.algo == 0) {
-        k_lines_batch<real><<<nblocks, threads, 0, st>>>(args, desc);
+        if (sizeof(real) == 4 && threads <= 256)
+            k_lines_batch<real, 1><<<nblocks, threads, 0, st>>>(args, desc);
+        else
+            k_lines_batch<real><<<nblocks, threads, 0, st>>>(args, desc);
         return cudaGetLastError();
     }
     static int configured[6] = {0, 0, 0, 0, 0, 0};
