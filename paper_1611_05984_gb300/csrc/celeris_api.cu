@@ -31,7 +31,7 @@ int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
 struct Layout {
     size_t w[2], P[2], U, dr, a[3], b[3][2];     // carries (K = 0)
     size_t R[3][3], Ph[3][3], Y[3];              // rings and AM4 bases (K >= 1)
-    size_t Qc[2], Vc, dc, Bc, mr, mc, ghost, ktab, flag;
+    size_t Qc[2], Vc, dc, Bc, mr, mc, ghost, ktab, gam, flag;
     size_t total;
     size_t row_bytes, col_bytes;
 };
@@ -92,6 +92,7 @@ Layout make_layout(const Geo &G, int es, int K)
     L.mc = take((size_t)G.nx * G.nwy * 4);
     L.ghost = take(ghost_index(2, 0, 0, 0, 0, (G.nx > G.ny ? G.nx : G.ny) + 4) * es);
     L.ktab = take((size_t)4 * ((G.nx > G.ny ? G.nx : G.ny) + 4) * 8 * sizeof(double));
+    L.gam = take((size_t)4 * ((G.nx > G.ny ? G.nx : G.ny) + 4) * es);
     L.flag = take(256);
     L.total = cur;
     return L;
@@ -222,6 +223,7 @@ struct cel_solver {
     unsigned char *capture_rhs;
     size_t capture_line;
     int ktab_dirty;   // boundaries or bed changed: rebuild the Eckart table
+    int gam_dirty;    // boundaries changed: rebuild the sponge factors
     uint64_t gen;     // counts boundary and bed changes (ensembles rebuild their tables)
     std::string err;
     EventProf prof;   // optional per-kernel event timing
@@ -304,6 +306,7 @@ StencilArgs<real> stencil_args(const cel_solver *s, const Coef<real> &coef, int 
     a.geo = s->geo;
     a.phy = s->phy;
     a.c = coef;
+    a.c.gam = s->at<real>(L.gam);
     a.ghost = s->at<real>(L.ghost);
     a.Bc = s->at<real>(L.Bc);
     a.w_in = s->at<real>(L.w[(s->cur + stage) & 1]);
@@ -344,6 +347,7 @@ LineArgs<real> line_args(const cel_solver *s, const Coef<real> &coef, int dir, i
     l.geo = s->geo;
     l.phy = s->phy;
     l.c = coef;
+    l.c.gam = s->at<real>(L.gam);
     l.ghost = s->at<real>(L.ghost);
     const double h = dir == 0 ? s->geo.dx : s->geo.dy;
     l.rh = real(1.0 / h);
@@ -415,6 +419,13 @@ cel_status step_t(cel_solver *s, int nsteps)
     int64_t launches = 0;
     const Coef<real> coef = make_coef<real>(s->geo, s->phy, s->bnd);
     real *ghost = s->at<real>(L.ghost);
+    if (s->gam_dirty) {
+        if (coef.spw[0] | coef.spw[1] | coef.spw[2] | coef.spw[3]) {
+            CEL_CUDA(s, launch_sponge_table<real>(coef, s->at<real>(L.gam), s->stream), "sponge table");
+            launches += 1;
+        }
+        s->gam_dirty = 0;
+    }
     for (int it = 0; it < nsteps; it++) {
         const int Kn = stages_of(s) - 1;
         const double t0 = (double)s->step * s->params.dt, t1 = (double)(s->step + 1) * s->params.dt;
@@ -577,6 +588,7 @@ cel_status cel_create(const cel_grid *grid, const cel_params *params, const void
     s->capture_rhs = nullptr;
     s->capture_line = 0;
     s->ktab_dirty = 1;
+    s->gam_dirty = 1;
     s->gen = 0;
     s->step = 0;
     s->cur = s->pcur = 0;
@@ -617,6 +629,7 @@ cel_status cel_set_boundary(cel_solver *s, int32_t side, const cel_bc *bc)
     Side &S = s->bnd.s[side];
     memset(&S, 0, sizeof(S));
     s->ktab_dirty = 1;
+    s->gam_dirty = 1;
     s->gen++;
     S.type = bc->type;
     S.width = bc->width_cells;
@@ -1189,6 +1202,7 @@ extern "C" cel_status cel_advance_noalloc(const cel_grid *grid, const cel_params
     s.capture_rhs = nullptr;
     s.capture_line = 0;
     s.ktab_dirty = 1;
+    s.gam_dirty = 1;
     s.gen = 0;
     s.step = first_step;
     s.nh = 0;
@@ -1504,6 +1518,16 @@ cel_status ens_prepare(cel_ensemble *e, int64_t &launches)
                                         cudaMemcpyHostToDevice, e->stream), "ensemble ghost arguments");
         }
         e->gvalid = true;
+    }
+    for (int j = 0; j < n; j++) {
+        cel_solver *s = e->m[j];
+        if (!s->gam_dirty) continue;
+        const Coef<real> c = make_coef<real>(s->geo, s->phy, s->bnd);
+        if (c.spw[0] | c.spw[1] | c.spw[2] | c.spw[3]) {
+            ENS_CUDA(e, launch_sponge_table<real>(c, s->at<real>(s->lay.gam), e->stream), "sponge table");
+            launches += 1;
+        }
+        s->gam_dirty = 0;
     }
     for (int j : e->gmem) {
         cel_solver *s = e->m[j];

@@ -71,6 +71,7 @@ struct Coef {
     int spw[4];          // sponge width in cells per side (0: not a sponge)
     int sine;            // bit s set: side s is a sine maker
     int npos;            // positions per side in the ghost table
+    const real *gam;     // Eq. 30 factor per side and position ([side][npos]), or null
 };
 
 template <typename real>
@@ -103,6 +104,7 @@ inline Coef<real> make_coef(const Geo &G, const Phys &p, const Bnd &b)
         if (b.s[s].type == kSine) c.sine |= 1 << s;
     }
     c.npos = (G.nx > G.ny ? G.nx : G.ny) + 4;
+    c.gam = nullptr;
     return c;
 }
 
@@ -235,6 +237,8 @@ cudaError_t launch_check_finite(const Geo &g, const real *w, const real *P, cons
 template <typename real>
 cudaError_t launch_eckart_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, double *ktab,
                                 int npos, cudaStream_t st);
+template <typename real>
+cudaError_t launch_sponge_table(const Coef<real> &c, real *gam, cudaStream_t st);
 template <typename real>
 cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r,
                                const double *ktab, double t0, double t1, real *tab, int npos,

@@ -288,8 +288,19 @@ __global__ void k_eckart_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_
     }
 }
 
-// Sine-maker ghosts (Eq. 25-28) for one step, in double: both ghost layers of
-// every sine side at t^n and t^{n+1}, summed over components.
+// Eq. 30's factor per sponge side and position from the side ([side][pos],
+// 1 beyond the sponge).  Rebuilt when a boundary changes.
+template <typename real>
+__global__ void k_sponge_table(const Coef<real> c, real *__restrict__ gam)
+{
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x, side = blockIdx.y;
+    if (pos >= c.npos) return;
+    const int w = c.spw[side];
+    gam[(size_t)side * c.npos + pos] = pos < w ? sponge_eq30<real>(w, pos) : real(1);
+}
+
+// Sine-maker ghosts (Eq. 25-28) for one step: both ghost layers of every
+// sine side at t^n and t^{n+1}, summed over components.
 template <typename real>
 __device__ __forceinline__ void ghost_entry(const Geo &g, const Phys &p, const Bnd &b, const real *__restrict__ d_r,
                                             const double *__restrict__ ktab, double t0, double t1,
@@ -301,19 +312,41 @@ __device__ __forceinline__ void ghost_entry(const Geo &g, const Phys &p, const B
     if (!ghost_site(g, d_r, side, layer, pos, x, y, dadj)) return;
     const Side &S = b.s[side];
     const double t = time ? t1 : t0;
-    double eta = 0.0, Pg = 0.0, Qg = 0.0;
-    for (int m = 0; m < S.ncomp; m++) {
-        const double k = ktab[((size_t)side * npos + pos) * 8 + m];
-        if (!(k > 0.0)) continue;
-        const double om = S.omega[m], c = om / k;
-        const double em = S.amp[m] * sin(om * t - k * S.cdir[m] * x - k * S.sdir[m] * y + S.phase[m]);
-        eta += em;
-        Pg += c * S.cdir[m] * em;
-        Qg += c * S.sdir[m] * em;
+    if constexpr (sizeof(real) == 4) {
+        // single precision: the phase in double (omega t grows without
+        // bound), reduced there to [-pi, pi]; the sine and the sums in
+        // single precision, which the table holds (double-precision
+        // arithmetic runs at a small fraction of the single-precision rate)
+        constexpr double kTwoPi = 6.283185307179586, kInvTwoPi = 0.15915494309189535;
+        float eta = 0.f, Pg = 0.f, Qg = 0.f;
+        for (int m = 0; m < S.ncomp; m++) {
+            const double k = ktab[((size_t)side * npos + pos) * 8 + m];
+            if (!(k > 0.0)) continue;
+            const double ph = S.omega[m] * t - k * S.cdir[m] * x - k * S.sdir[m] * y + S.phase[m];
+            const double r = ph - kTwoPi * rint(ph * kInvTwoPi);
+            const float em = (float)S.amp[m] * sinf((float)r), c = (float)S.omega[m] / (float)k;
+            eta += em;
+            Pg += c * (float)S.cdir[m] * em;
+            Qg += c * (float)S.sdir[m] * em;
+        }
+        tab[ghost_index(time, side, layer, 0, pos, npos)] = (float)p.ws + eta;
+        tab[ghost_index(time, side, layer, 1, pos, npos)] = Pg;
+        tab[ghost_index(time, side, layer, 2, pos, npos)] = Qg;
+    } else {
+        double eta = 0.0, Pg = 0.0, Qg = 0.0;
+        for (int m = 0; m < S.ncomp; m++) {
+            const double k = ktab[((size_t)side * npos + pos) * 8 + m];
+            if (!(k > 0.0)) continue;
+            const double om = S.omega[m], c = om / k;
+            const double em = S.amp[m] * sin(om * t - k * S.cdir[m] * x - k * S.sdir[m] * y + S.phase[m]);
+            eta += em;
+            Pg += c * S.cdir[m] * em;
+            Qg += c * S.sdir[m] * em;
+        }
+        tab[ghost_index(time, side, layer, 0, pos, npos)] = real(p.ws + eta);
+        tab[ghost_index(time, side, layer, 1, pos, npos)] = real(Pg);
+        tab[ghost_index(time, side, layer, 2, pos, npos)] = real(Qg);
     }
-    tab[ghost_index(time, side, layer, 0, pos, npos)] = real(p.ws + eta);
-    tab[ghost_index(time, side, layer, 1, pos, npos)] = real(Pg);
-    tab[ghost_index(time, side, layer, 2, pos, npos)] = real(Qg);
 }
 
 template <typename real>
@@ -1092,19 +1125,24 @@ struct LineShared {
 // on the last stage and the dry mask; 1, the transposed system T^T y = r
 // (row k of T^T is (c_{k-1}, b_k, a_{k+1}) of T's rows), y alone; 2, T x = r,
 // x alone.  The line's own segment count A.nseg (a multiple of 32, at most
-// the block size) sets the reduction, so the result does not depend on the
-// block size: warps beyond it only pass the barriers.
+// the threads given to the line) sets the reduction, so the result does not
+// depend on the block size: warps beyond it only pass the barriers.  A block
+// may solve several lines side by side: tid is the thread's index among its
+// line's threads and wbase the block warp its line starts at; every thread
+// of the block takes the call (with `valid` false where its slot has no
+// line), since the two barriers are the block's.
 template <typename real, int M, int kMode>
-__device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line, LineShared<real> &L)
+__device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line, LineShared<real> &L, int tid,
+                                               int wbase, bool valid)
 {
     static_assert(M >= 2 && M <= 8, "rows per thread");
     constexpr int m1 = M - 1;
-    auto &sh0 = L.sh0;
-    auto &sh1 = L.sh1;
-    auto &sh31 = L.sh31;
-    auto &sh30 = L.sh30;
-    auto &shS = L.shS;
-    const int n = A.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = A.nseg >> 5;
+    real(*sh0)[3] = L.sh0 + wbase;
+    real(*sh1)[3] = L.sh1 + wbase;
+    real(*sh31)[7] = L.sh31 + wbase;
+    real(*sh30)[3] = L.sh30 + wbase;
+    real *shS = L.shS + wbase;
+    const int n = A.n, lane = tid & 31, warp = tid >> 5, nw = valid ? A.nseg >> 5 : 0;
     const bool act = warp < nw;            // whole warps: the segment count is a multiple of 32
     const int f = tid * M;
     const int lo_side = A.dir == 0 ? 0 : 2, hi_side = A.dir == 0 ? 1 : 3;
@@ -1321,22 +1359,26 @@ __device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line
         // discharge where dry
         load_run<real, M>(o, A.base + lo + f);
         const uint32_t bits = A.mask[(size_t)line * A.nwords + (f >> 5)] >> (f & 31);
-        // the sponge only where the segment reaches into one (Eq. 30)
+        // the sponge only where the segment reaches into one (Eq. 30): the
+        // sides across the line give one factor for the whole segment, the
+        // sides along it one per row
         bool sponge = false;
+        real g_across = real(1);
+        const int s_lo = A.dir == 0 ? 0 : 2, a_lo = A.dir == 0 ? 2 : 0;   // west/south along, across
         if (A.final_stage) {
             const int *w = A.c.spw;
-            const int lo_w = w[A.dir == 0 ? 0 : 2], hi_w = w[A.dir == 0 ? 1 : 3];
-            const int ac_lo = w[A.dir == 0 ? 2 : 0], ac_hi = w[A.dir == 0 ? 3 : 1];
             const int across = A.dir == 0 ? A.geo.ny : A.geo.nx;
-            sponge = f < lo_w || f + M > n - hi_w || line < ac_lo || line >= across - ac_hi;
+            sponge = f < w[s_lo] || f + M > n - w[s_lo + 1] || line < w[a_lo] || line >= across - w[a_lo + 1];
+            if (sponge)
+                g_across = fmin(sponge_side(A.c, a_lo, line), sponge_side(A.c, a_lo + 1, across - 1 - line));
         }
 #pragma unroll
         for (int j = 0; j < M; j++) {
             real v = o[j] + x[j];
             if (sponge) {
                 const int k = f + j;
-                const int i = A.dir == 0 ? k : line, jj = A.dir == 0 ? line : k;
-                if (k < n) v *= sponge_gamma<real>(A.c, A.geo, i, jj);
+                if (k < n)
+                    v *= fmin(g_across, fmin(sponge_side(A.c, s_lo, k), sponge_side(A.c, s_lo + 1, n - 1 - k)));
             }
             if ((bits >> j) & 1u) v = real(0);
             o[j] = v;
@@ -1634,14 +1676,15 @@ __device__ __forceinline__ void line_solve_seg(const LineArgs<real> &A, int line
 
 // The segment length of the line's family picks the instance.
 template <typename real, int kMode>
-__device__ __forceinline__ void line_solve_any(const LineArgs<real> &A, int line, LineShared<real> &L)
+__device__ __forceinline__ void line_solve_any(const LineArgs<real> &A, int line, LineShared<real> &L,
+                                               int tid = threadIdx.x, int wbase = 0, bool valid = true)
 {
     if (A.mshift == 3)
-        line_solve_reg<real, 8, kMode>(A, line, L);
+        line_solve_reg<real, 8, kMode>(A, line, L, tid, wbase, valid);
     else if (A.mshift == 2)
-        line_solve_reg<real, 4, kMode>(A, line, L);
+        line_solve_reg<real, 4, kMode>(A, line, L, tid, wbase, valid);
     else
-        line_solve_reg<real, 2, kMode>(A, line, L);
+        line_solve_reg<real, 2, kMode>(A, line, L, tid, wbase, valid);
 }
 
 // kOcc: blocks of at most 256 threads held to 48 registers, so that 5 of
@@ -1809,6 +1852,13 @@ cudaError_t launch_eckart_table(const Geo &g, const Phys &p, const Bnd &b, const
                                 cudaStream_t st)
 {
     k_eckart_table<real><<<dim3((npos + 127) / 128, 4), 128, 0, st>>>(g, p, b, d_r, ktab, npos);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_sponge_table(const Coef<real> &c, real *gam, cudaStream_t st)
+{
+    k_sponge_table<real><<<dim3((c.npos + 127) / 128, 4), 128, 0, st>>>(c, gam);
     return cudaGetLastError();
 }
 
@@ -2088,6 +2138,7 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
     if (threads < 32 || threads % 32 || threads > (sizeof(real) == 4 ? 1024 : 512)) return cudaErrorInvalidValue;
     if (nblocks <= 0) return cudaSuccess;
     if (cfg.algo == 0) {
+        // lines of at most 128 threads share blocks of up to 256
         if (sizeof(real) == 4 && threads <= 256)
             k_lines_batch<real, 1><<<nblocks, threads, 0, st>>>(args, desc);
         else
@@ -2137,6 +2188,7 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
                                                    unsigned long long *, cudaStream_t);                 \
     template cudaError_t launch_eckart_table<real>(const Geo &, const Phys &, const Bnd &, const real *,  \
                                                    double *, int, cudaStream_t);                        \
+    template cudaError_t launch_sponge_table<real>(const Coef<real> &, real *, cudaStream_t);            \
     template cudaError_t launch_ghost_table<real>(const Geo &, const Phys &, const Bnd &, const real *,   \
                                                   const double *, double, double, real *, int,          \
                                                   cudaStream_t);                                        \

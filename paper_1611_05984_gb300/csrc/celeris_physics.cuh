@@ -91,21 +91,30 @@ __device__ __forceinline__ double cospi_r(double x) { return cospi(x); }
 // Eq. 30 with D the distance from the absorbing face to the cell centre and
 // L_s = width cells: a cell idx cells from the side (idx = i for the west) is
 // inside when idx < width, with (L_s - D)/L_s = (2 (width - idx) - 1)/(2 width).
+template <typename real>
+__device__ __forceinline__ real sponge_eq30(int w, int idx)
+{
+    const real r = real(2 * (w - idx) - 1) / real(2 * w);
+    return real(0.5) * (real(1) + cospi_r(r));
+}
+
+// The factor of side s for a cell idx cells from it: 1 outside its sponge;
+// inside, from the solver's table when the arguments carry one (the same
+// expression, evaluated once per side and position), else evaluated here.
+template <typename real>
+__device__ __forceinline__ real sponge_side(const Coef<real> &c, int s, int idx)
+{
+    const int w = c.spw[s];
+    if (idx >= w) return real(1);
+    return c.gam ? c.gam[(size_t)s * c.npos + idx] : sponge_eq30<real>(w, idx);
+}
+
 // The smallest gamma over the sponge sides.
 template <typename real>
 __device__ __forceinline__ real sponge_gamma(const Coef<real> &c, const Geo &g, int i, int j)
 {
-    real gm = real(1);
-    const int idx[4] = {i, g.nx - 1 - i, j, g.ny - 1 - j};
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        const int w = c.spw[s];
-        if (idx[s] < w) {
-            real r = real(2 * (w - idx[s]) - 1) / real(2 * w);
-            gm = fmin(gm, real(0.5) * (real(1) + cospi_r(r)));
-        }
-    }
-    return gm;
+    return fmin(fmin(sponge_side(c, 0, i), sponge_side(c, 1, g.nx - 1 - i)),
+                fmin(sponge_side(c, 2, j), sponge_side(c, 3, g.ny - 1 - j)));
 }
 
 // Adjacent still-water depth d and ghost coordinates of table position pos

@@ -105,6 +105,8 @@ def test_runup_tracking_starts_from_state_and_disables():
     assert tracked == g2.last_launch_count() + 5        # one run-up launch per step
     g.set_state(*g2.state())
     g.step(5)
+    g2.set_state(*g2.state())   # both restart their history past the first call (which builds the sponge table)
+    g2.step(5)
     assert g.last_launch_count() == g2.last_launch_count()   # none once disabled
 
 
