@@ -308,6 +308,24 @@ def measure_ensemble(steps, warmup, precision, world=1, rank=0):
     barrier()
     launches = ens.last_launch_count()
     graph_steps = ens.graph_steps() - g0
+    # the same steps as one persistent cooperative launch per call
+    ens.use_persistent(True)
+    ens.step(1)
+    torch.cuda.synchronize()
+    ep = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    p0 = ens.persistent_steps()
+    barrier()
+    torch.cuda.synchronize()
+    ep[0].record(stream)
+    ens.step(args.steps)
+    ep[1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ens.check()
+    persistent_steps = ens.persistent_steps() - p0
+    persistent_launches = ens.last_launch_count()
+    ens.use_persistent(False)
+    ms_pers = max_over_ranks(ep[0].elapsed_time(ep[1]))
     # the per-kernel split, from a short profiled run after the timed one
     # (profiling launches every kernel on its own, without graphs)
     ens.profile_enable(8 * (scens[0].K + 1) * 12 + 16)
@@ -381,6 +399,12 @@ def measure_ensemble(steps, warmup, precision, world=1, rank=0):
                                                                   "the timed ones, kernel by kernel",
                          "step_gbs_algorithmic": gbs},
             "graph_steps": graph_steps, "line_splits": TUNED,
+            "persistent": {"ms_per_step": ms_pers / args.steps,
+                           "value": total_cells * args.steps / (ms_pers / 1e3),
+                           "speedup_vs_single_launch": ms_one / ms_pers, "steps": persistent_steps,
+                           "gpu_launches": persistent_launches,
+                           "what": "the same steps as one persistent cooperative launch per call "
+                                   "(cel_ensemble_use_persistent), grid-wide barriers between phases"},
             "finite": finite, "gpu_launches": launches, "clocks": clk}
     return line
 
@@ -623,6 +647,8 @@ def main():
                         "single_launch": {"value": el["single_launch"]["value"],
                                           "ms_per_step": el["single_launch"]["ms_per_step"]},
                         "gpu_launches": el["gpu_launches"], "graph_steps": el["graph_steps"],
+                        "persistent": {k: el["persistent"][k] for k in
+                                       ("ms_per_step", "speedup_vs_single_launch", "steps", "gpu_launches")},
                         "finite": el["finite"]}
         if args.adjoint_steps > 0:
             a100 = measure_adjoint(args.adjoint_steps, 5, "f32", 512, 100)

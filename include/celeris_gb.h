@@ -370,6 +370,30 @@ cel_status cel_ensemble_step(cel_ensemble *e, int32_t nsteps);
 cel_status cel_ensemble_use_graphs(cel_ensemble *e, int32_t enable);
 /* Steps taken by replaying a captured cycle since cel_ensemble_create. */
 cel_status cel_ensemble_graph_steps(const cel_ensemble *e, int64_t *steps);
+/* Persistent launch.  With enable != 0, where a captured cycle could be used
+ * (above) and every line family takes the register solver in blocks of at
+ * most 256 threads, cel_ensemble_step takes all its remaining steps in ONE
+ * cooperative launch (as many 256-thread blocks as fit the GPU at once):
+ * the blocks work through the ghost tables, then per stage the stencil
+ * tiles and the line solves (several short lines side by side per block),
+ * with a grid-wide barrier where a batched launch would end.  The arguments
+ * are the batched launches' argument blocks, so the results are bit for bit
+ * the same.  Every barrier wait is bounded by timeout_ms (in (0, 60000];
+ * CEL_ERR_INVALID_ARG otherwise): a block whose wait runs out sets a status
+ * word and the launch ends at the next barrier, leaving the members' states
+ * undefined.  cel_ensemble_check synchronises the ensemble's stream and
+ * returns CEL_ERR_TIMEOUT if that happened (the words are cleared).
+ * CEL_ERR_CUDA if no block of the launch fits an SM.  Off by default. */
+cel_status cel_ensemble_use_persistent(cel_ensemble *e, int32_t enable, double timeout_ms);
+/* Steps taken by persistent launches since cel_ensemble_create. */
+cel_status cel_ensemble_persistent_steps(const cel_ensemble *e, int64_t *steps);
+cel_status cel_ensemble_check(cel_ensemble *e);
+/* A check of the barrier's bound: one persistent launch that takes a single
+ * barrier expecting `missing` more arrivals than it has blocks (0..1024),
+ * waits at most timeout_ms, synchronises, and sets *timed_out to 1 if the
+ * wait ran out (it must, for missing > 0) or 0 if the barrier completed.
+ * The members are not touched. */
+cel_status cel_ensemble_barrier_check(cel_ensemble *e, int32_t missing, double timeout_ms, int32_t *timed_out);
 /* Kernel launches issued by the most recent cel_ensemble_step call. */
 cel_status cel_ensemble_last_launch_count(const cel_ensemble *e, int64_t *launches);
 /* Per-kernel event timing of the ensemble's launches, as cel_profile_* for a

@@ -36,7 +36,8 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_get_stats", "cel_last_launch_count", "cel_profile_enable",
            "cel_profile_read", "cel_profile_disable", "cel_ensemble_table_bytes",
            "cel_ensemble_create", "cel_ensemble_step", "cel_ensemble_use_graphs", "cel_ensemble_graph_steps",
-           "cel_ensemble_last_launch_count",
+           "cel_ensemble_use_persistent", "cel_ensemble_persistent_steps", "cel_ensemble_check",
+           "cel_ensemble_barrier_check", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
            "cel_ensemble_last_error", "cel_ensemble_destroy", "cel_advance_noalloc", "cel_set_line_split",
            "cel_reset_line_splits", "cel_line_config", "cel_status_string",
@@ -123,6 +124,10 @@ def load(build_if_missing: bool = True):
         L.cel_ensemble_step.argtypes = [vp, i32]
         L.cel_ensemble_use_graphs.argtypes = [vp, i32]
         L.cel_ensemble_graph_steps.argtypes = [vp, ctypes.POINTER(i64)]
+        L.cel_ensemble_use_persistent.argtypes = [vp, i32, ctypes.c_double]
+        L.cel_ensemble_persistent_steps.argtypes = [vp, ctypes.POINTER(i64)]
+        L.cel_ensemble_check.argtypes = [vp]
+        L.cel_ensemble_barrier_check.argtypes = [vp, i32, ctypes.c_double, ctypes.POINTER(i32)]
         L.cel_ensemble_last_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.cel_ensemble_profile_enable.argtypes = [vp, i32]
         L.cel_ensemble_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
@@ -434,6 +439,36 @@ class Ensemble:
         st = self.L.cel_ensemble_use_graphs(self._h, int(bool(enable)))
         if st != CEL_OK:
             raise CelerisError(st, "cel_ensemble_use_graphs failed")
+
+    def use_persistent(self, enable: bool = True, timeout_ms: float = 1000.0):
+        """Take each call's steps in one persistent cooperative launch where
+        the captured cycle's conditions hold (cel_ensemble_use_persistent);
+        every grid-wide wait is bounded by timeout_ms."""
+        st = self.L.cel_ensemble_use_persistent(self._h, int(bool(enable)), float(timeout_ms))
+        if st != CEL_OK:
+            raise CelerisError(st, self.L.cel_ensemble_last_error(self._h).decode())
+
+    def persistent_steps(self) -> int:
+        """Steps taken by persistent launches since creation."""
+        v = ctypes.c_int64()
+        self.L.cel_ensemble_persistent_steps(self._h, ctypes.byref(v))
+        return v.value
+
+    def check(self):
+        """Synchronise; raises CelerisError (CEL_ERR_TIMEOUT) if a wait of a
+        persistent launch ran out."""
+        st = self.L.cel_ensemble_check(self._h)
+        if st != CEL_OK:
+            raise CelerisError(st, self.L.cel_ensemble_last_error(self._h).decode())
+
+    def barrier_check(self, missing: int, timeout_ms: float) -> bool:
+        """One persistent launch of a single barrier that expects `missing`
+        more blocks than run; True if its wait ran out."""
+        v = ctypes.c_int32()
+        st = self.L.cel_ensemble_barrier_check(self._h, int(missing), float(timeout_ms), ctypes.byref(v))
+        if st != CEL_OK:
+            raise CelerisError(st, self.L.cel_ensemble_last_error(self._h).decode())
+        return bool(v.value)
 
     def last_launch_count(self) -> int:
         v = ctypes.c_int64()

@@ -1278,6 +1278,12 @@ struct cel_ensemble {
     size_t off_kdev = 0;                 // device step counter of the ghost tables
     int64_t kdev_val = 0;                // its value once the queued work has run
     bool kdev_known = false;
+    // The persistent launch (cel_ensemble_use_persistent): one cooperative
+    // launch for a call's steps once the cycle's argument blocks are in place.
+    bool use_persist = false;
+    double persist_timeout_ms = 1000.0;
+    int64_t persist_steps = 0;           // steps taken by persistent launches, since creation
+    size_t off_bar = 0;                  // the launch's barrier words
     void drop_graphs()
     {
         for (Graph &g : graphs) cudaGraphExecDestroy(g.exec);
@@ -1292,8 +1298,8 @@ struct EnsPlan {
     std::vector<std::pair<int, int>> fam;
     std::vector<cel_ensemble::Group> groups;
     std::vector<int> gmem;
-    size_t off_tile_desc = 0, off_gargs = 0, off_gstart = 0, off_kdev = 0, sarg_bytes = 0, entry_bytes = 0,
-           off_entries = 0;
+    size_t off_tile_desc = 0, off_gargs = 0, off_gstart = 0, off_kdev = 0, off_bar = 0, sarg_bytes = 0,
+           entry_bytes = 0, off_entries = 0;
     int cap = 0;
     size_t total = 0;
 };
@@ -1363,6 +1369,7 @@ void plan_t(cel_solver *const *ms, int n, EnsPlan &P)
     P.off_gargs = take(sizeof(GhostArgs<real>) * (size_t)n);
     P.off_gstart = take(sizeof(int) * (size_t)(n + 1));
     P.off_kdev = take(sizeof(int64_t));
+    P.off_bar = take(4 * sizeof(unsigned));
     P.sarg_bytes = align256(sizeof(StencilArgs<real>) * (size_t)n);
     P.entry_bytes = P.sarg_bytes + align256(sizeof(LineArgs<real>) * P.fam.size());
     // the argument blocks repeat every 6 steps once the AB3 history is full
@@ -1689,6 +1696,111 @@ cel_status ens_graph_cycle(cel_ensemble *e, int64_t &launches, bool *done)
     return CEL_OK;
 }
 
+// The remaining nsteps steps as one persistent cooperative launch, where the
+// captured cycle's conditions hold (history full, no gauges, run-up tracking
+// or profiling, every argument block of the 6-step cycle in the table) and
+// every line family takes the register path in blocks of at most 256
+// threads.  *done: the steps were taken.
+template <typename real>
+cel_status ens_persistent(cel_ensemble *e, int nsteps, int64_t &launches, bool *done)
+{
+    *done = false;
+    const int n = (int)e->m.size();
+    const cel_solver *m0 = e->m[0];
+    if (!e->use_persist || nsteps < 1 || m0->nh < 2 || e->prof.cap > 0) return CEL_OK;
+    for (int j = 0; j < n; j++) {
+        const cel_solver *s = e->m[j];
+        if (s->runup || (s->ng > 0 && s->log_every > 0 && s->cap > 0)) return CEL_OK;
+    }
+    const int Kn = stages_of(m0) - 1;
+    if (Kn + 1 > kPersistMaxStages) return CEL_OK;
+    PersistArgs<real> P;
+    memset(&P, 0, sizeof(P));
+    {
+        int64_t nh = m0->nh;
+        int cur = m0->cur, pcur = m0->pcur;
+        for (int i = 0; i < 6; i++) {
+            for (int stage = 0; stage <= Kn; stage++) {
+                auto it = std::find(e->keys.begin(), e->keys.end(), ens_key_of(nh, cur, pcur, stage));
+                if (it == e->keys.end()) return CEL_OK;
+                P.ent[i][stage] = (int)(it - e->keys.begin());
+            }
+            cur = (cur + Kn + 1) & 1;
+            pcur = 1 - pcur;
+            nh++;
+        }
+    }
+    // line runs: families of one group with one segment length and one model,
+    // in table order (the solver's barriers are taken by Boussinesq lines
+    // alone, so lines of both models never share a block)
+    int nruns = 0;
+    for (const cel_ensemble::Group &G : e->groups) {
+        if (G.cfg.algo != 0 || G.cfg.threads > kStencilThreads) return CEL_OK;
+        size_t off = G.off_desc;
+        int prev = -1;
+        for (int f = 0; f < G.nfam; f++) {
+            const std::pair<int, int> &fm = e->fam[G.first + f];
+            const cel_solver *s = e->m[fm.first];
+            const int len = fm.second == 0 ? s->geo.nx : s->geo.ny, nl = fm.second == 0 ? s->geo.ny : s->geo.nx;
+            const int ident = s->params.model == CEL_NLSW;
+            const int msh = line_config(len, (int)sizeof(real)).mshift;
+            if (msh * 2 + ident != prev) {
+                if (nruns == kPersistMaxRuns) return CEL_OK;
+                P.run_desc[nruns] = reinterpret_cast<const int2 *>(e->tab + off);
+                P.run_first[nruns] = G.first;
+                P.run_lines[nruns] = 0;
+                P.run_threads[nruns] = G.cfg.threads;
+                P.run_mshift[nruns] = msh;
+                P.run_identity[nruns] = ident;
+                P.run_nfam[nruns] = G.nfam;
+                nruns++;
+                prev = msh * 2 + ident;
+            }
+            P.run_lines[nruns - 1] += nl;
+            off += sizeof(int2) * (size_t)nl;
+        }
+    }
+    const int grid = persistent_grid<real>();
+    if (grid <= 0) return CEL_OK;
+    P.nruns = nruns;
+    P.nmembers = n;
+    P.nent = (int)e->keys.size();
+    P.entries = e->tab + e->off_entries;
+    P.entry_bytes = e->entry_bytes;
+    P.sarg_bytes = e->sarg_bytes;
+    for (int stage = 0; stage <= Kn; stage++) {
+        StencilArgs<real> a;
+        memset(&a, 0, sizeof(a));
+        a.kind = stage == 0 ? kAB3 : kAM4;
+        a.ring = e->K > 0;
+        P.spec[stage] = stencil_spec(a);
+    }
+    P.nstages = Kn + 1;
+    P.phase0 = 0;
+    P.nsteps = nsteps;
+    P.tile_desc = reinterpret_cast<const int2 *>(e->tab + e->off_tile_desc);
+    P.tiles = e->tiles;
+    if (!e->gmem.empty()) {
+        P.gargs = reinterpret_cast<const GhostArgs<real> *>(e->tab + e->off_gargs);
+        P.gstart = reinterpret_cast<const int *>(e->tab + e->off_gstart);
+        P.ngm = (int)e->gmem.size();
+        P.gblocks = e->gblocks;
+        P.k0 = e->m[e->gmem[0]]->step - e->gstep0[0];
+    }
+    P.bar = reinterpret_cast<unsigned *>(e->tab + e->off_bar);
+    P.expect = (unsigned)grid;
+    P.timeout_ns = (long long)(e->persist_timeout_ms * 1e6);
+    ENS_CUDA(e, cudaMemsetAsync(P.bar, 0, 4 * sizeof(unsigned), e->stream), "persistent barrier words");
+    ENS_CUDA(e, launch_persistent<real>(P, grid, e->stream), "persistent ensemble launch");
+    for (int i = 0; i < nsteps; i++)
+        for (int j = 0; j < n; j++) finish_step(e->m[j], Kn);
+    e->kdev_known = false;   // the device step counter was not advanced
+    launches += 1;
+    e->persist_steps += nsteps;
+    *done = true;
+    return CEL_OK;
+}
+
 template <typename real>
 cel_status ens_step_t(cel_ensemble *e, int nsteps)
 {
@@ -1696,6 +1808,12 @@ cel_status ens_step_t(cel_ensemble *e, int nsteps)
     for (int it = 0; it < nsteps;) {
         cel_status st = ens_prepare<real>(e, launches);
         if (st != CEL_OK) return st;
+        {
+            bool done = false;
+            st = ens_persistent<real>(e, nsteps - it, launches, &done);
+            if (st != CEL_OK) return st;
+            if (done) break;
+        }
         if (nsteps - it >= 6) {
             bool done = false;
             st = ens_graph_cycle<real>(e, launches, &done);
@@ -1768,6 +1886,7 @@ cel_status cel_ensemble_create(cel_solver *const *members, int32_t n, void *tabl
     e->off_gargs = P.off_gargs;
     e->off_gstart = P.off_gstart;
     e->off_kdev = P.off_kdev;
+    e->off_bar = P.off_bar;
     e->gstep0.assign(P.gmem.size(), 0);
     e->gvalid = false;
     e->sarg_bytes = P.sarg_bytes;
@@ -1858,6 +1977,87 @@ cel_status cel_ensemble_use_graphs(cel_ensemble *e, int32_t enable)
     if (!e) return CEL_ERR_INVALID_ARG;
     e->use_graphs = enable != 0;
     if (!e->use_graphs) e->drop_graphs();
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_use_persistent(cel_ensemble *e, int32_t enable, double timeout_ms)
+{
+    if (!e) return CEL_ERR_INVALID_ARG;
+    if (!(timeout_ms > 0.0) || timeout_ms > 60000.0)
+        return ens_fail(e, CEL_ERR_INVALID_ARG, "the barrier timeout must lie in (0, 60000] ms");
+    if (enable && (e->es == 4 ? persistent_grid<float>() : persistent_grid<double>()) <= 0)
+        return ens_fail(e, CEL_ERR_CUDA, "no block of the persistent launch fits an SM");
+    e->use_persist = enable != 0;
+    e->persist_timeout_ms = timeout_ms;
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_persistent_steps(const cel_ensemble *e, int64_t *steps)
+{
+    if (!e || !steps) return CEL_ERR_INVALID_ARG;
+    *steps = e->persist_steps;
+    return CEL_OK;
+}
+
+namespace {
+// Reads the barrier status after the stream's work and clears the words.
+cel_status ens_read_barrier(cel_ensemble *e, unsigned *status)
+{
+    unsigned w[4] = {0, 0, 0, 0};
+    ENS_CUDA(e, cudaStreamSynchronize(e->stream), "ensemble stream");
+    ENS_CUDA(e, cudaMemcpy(w, e->tab + e->off_bar, sizeof(w), cudaMemcpyDeviceToHost), "persistent barrier words");
+    ENS_CUDA(e, cudaMemset(e->tab + e->off_bar, 0, sizeof(w)), "persistent barrier words");
+    *status = w[2];
+    if (w[3] != 0)
+        return ens_fail(e, CEL_ERR_INVALID_ARG,
+                        "the persistent launch met a descriptor out of range (code " + std::to_string(w[3] >> 24) +
+                            ", index " + std::to_string(w[3] & 0xffffffu) + ") and skipped its work");
+    return CEL_OK;
+}
+}  // namespace
+
+cel_status cel_ensemble_check(cel_ensemble *e)
+{
+    if (!e) return CEL_ERR_INVALID_ARG;
+    unsigned status = 0;
+    cel_status st = ens_read_barrier(e, &status);
+    if (st != CEL_OK) return st;
+    if (status != 0)
+        return ens_fail(e, CEL_ERR_TIMEOUT,
+                        "a wait of the persistent launch ran out: the members' states are undefined (set them again)");
+    return CEL_OK;
+}
+
+cel_status cel_ensemble_barrier_check(cel_ensemble *e, int32_t missing, double timeout_ms, int32_t *timed_out)
+{
+    if (!e || !timed_out || missing < 0 || missing > 1024 || !(timeout_ms > 0.0) || timeout_ms > 60000.0)
+        return CEL_ERR_INVALID_ARG;
+    const int grid = e->es == 4 ? persistent_grid<float>() : persistent_grid<double>();
+    if (grid <= 0) return ens_fail(e, CEL_ERR_CUDA, "no block of the persistent launch fits an SM");
+    ENS_CUDA(e, cudaMemsetAsync(e->tab + e->off_bar, 0, 4 * sizeof(unsigned), e->stream), "persistent barrier words");
+    cudaError_t ce;
+    if (e->es == 4) {
+        PersistArgs<float> P;
+        memset(&P, 0, sizeof(P));
+        P.barrier_only = 1;
+        P.bar = reinterpret_cast<unsigned *>(e->tab + e->off_bar);
+        P.expect = (unsigned)(grid + missing);
+        P.timeout_ns = (long long)(timeout_ms * 1e6);
+        ce = launch_persistent<float>(P, grid, e->stream);
+    } else {
+        PersistArgs<double> P;
+        memset(&P, 0, sizeof(P));
+        P.barrier_only = 1;
+        P.bar = reinterpret_cast<unsigned *>(e->tab + e->off_bar);
+        P.expect = (unsigned)(grid + missing);
+        P.timeout_ns = (long long)(timeout_ms * 1e6);
+        ce = launch_persistent<double>(P, grid, e->stream);
+    }
+    ENS_CUDA(e, ce, "persistent barrier check");
+    unsigned status = 0;
+    cel_status st = ens_read_barrier(e, &status);
+    if (st != CEL_OK) return st;
+    *timed_out = status != 0;
     return CEL_OK;
 }
 

@@ -303,6 +303,41 @@ struct GhostArgs {
     double dt;
 };
 
+// The persistent ensemble launch: one cooperative launch runs nsteps steps
+// of every member, its phases (ghost tables, then per stage the stencil
+// tiles and the line solves) separated by grid-wide barriers.  The argument
+// entries of the 6-step cycle are the ones the batched launches use.  Line
+// solves run in runs of one block size and one segment length each, as many
+// lines side by side per block as fit 256 threads.
+constexpr int kPersistMaxStages = 4, kPersistMaxRuns = 48;
+
+template <typename real>
+struct PersistArgs {
+    const unsigned char *entries;      // argument entries (stencil arguments, then line arguments)
+    size_t entry_bytes, sarg_bytes;
+    int ent[6][kPersistMaxStages];     // entry per step of the cycle and stage
+    int spec[kPersistMaxStages];       // stencil instance per stage (stencil_spec)
+    int nstages, phase0, nsteps;
+    const int2 *tile_desc;             // as for the batched stencil launch
+    int tiles;
+    int nruns;
+    const int2 *run_desc[kPersistMaxRuns];   // (family, line) per line, as for the batched line launch
+    int run_first[kPersistMaxRuns];    // the run's first family in the entry's line arguments
+    int run_lines[kPersistMaxRuns], run_threads[kPersistMaxRuns];
+    int run_mshift[kPersistMaxRuns];   // log2 rows per segment of every line of the run
+    int run_identity[kPersistMaxRuns]; // 1: the run's lines are shallow-water ones (P = U*, no solve)
+    int run_nfam[kPersistMaxRuns];     // families of the run's group (descriptor x below it)
+    int nmembers, nent;                // members; argument entries in the table
+    const GhostArgs<real> *gargs;      // as for the batched ghost launch
+    const int *gstart;
+    int ngm, gblocks;
+    int64_t k0;                        // lockstep step index of the first step
+    unsigned *bar;                     // barrier words: arrivals, generation, status (0 at launch)
+    unsigned expect;                   // arrivals a barrier waits for: the grid size
+    long long timeout_ns;              // bound of every wait
+    int barrier_only;                  // 1: one barrier and nothing else (a check of the waits' bound)
+};
+
 // k: the lockstep step index, plus *kdev where kdev is given (a device
 // counter that a captured graph advances between its replays).
 template <typename real>
@@ -312,6 +347,11 @@ cudaError_t launch_ghost_batch(const GhostArgs<real> *args, const int *start, in
 cudaError_t launch_counter(int64_t *p, int64_t v, int add, cudaStream_t st);
 // spec: the stencil's stage specialisation (stencil_spec of the members'
 // arguments, which step in lockstep and share it).
+template <typename real>
+cudaError_t launch_persistent(const PersistArgs<real> &p, int grid, cudaStream_t st);
+// Blocks of the persistent launch that fit the GPU at once (0 on an error).
+template <typename real>
+int persistent_grid();
 template <typename real>
 cudaError_t launch_stencil_batch(const StencilArgs<real> *args, const int2 *desc, int nblocks, int spec,
                                  cudaStream_t st);

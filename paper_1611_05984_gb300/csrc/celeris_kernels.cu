@@ -361,16 +361,23 @@ __global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r
 // owns blocks [start[e], start[e+1]), 16 per 128 positions, and is at step
 // step0 + k.
 template <typename real>
+__device__ __forceinline__ void ghost_batch_block(const GhostArgs<real> *__restrict__ args,
+                                                  const int *__restrict__ start, int n, int blk, int t, int64_t k)
+{
+    const int e = find_owner(start, n, blk);
+    const GhostArgs<real> &A = args[e];
+    const int b = blk - start[e];
+    const int nbx = (A.npos + 127) / 128;
+    const int64_t step = A.step0 + k;
+    ghost_entry(A.g, A.p, A.b, A.d_r, A.ktab, (double)step * A.dt, (double)(step + 1) * A.dt, A.tab, A.npos,
+                (b % nbx) * 128 + t, b / nbx);
+}
+
+template <typename real>
 __global__ void k_ghost_batch(const GhostArgs<real> *__restrict__ args, const int *__restrict__ start, int n,
                               int64_t k, const int64_t *__restrict__ kdev)
 {
-    const int e = find_owner(start, n, blockIdx.x);
-    const GhostArgs<real> &A = args[e];
-    const int b = blockIdx.x - start[e];
-    const int nbx = (A.npos + 127) / 128;
-    const int64_t step = A.step0 + (kdev ? *kdev : 0) + k;
-    ghost_entry(A.g, A.p, A.b, A.d_r, A.ktab, (double)step * A.dt, (double)(step + 1) * A.dt, A.tab, A.npos,
-                (b % nbx) * 128 + threadIdx.x, b / nbx);
+    ghost_batch_block(args, start, n, blockIdx.x, threadIdx.x, (kdev ? *kdev : 0) + k);
 }
 
 // ------------------------------------------------------------ the stencil
@@ -1736,6 +1743,195 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512)
     line_solve_seg<real, M>(A, d.y, smem_raw);
 }
 
+// ------------------------------------------------- persistent ensemble launch
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of the persistent launch (a cooperative launch: every
+// block is resident).  bar[0] counts arrivals, bar[1] is the generation,
+// bar[2] the status.  Each wait is bounded by timeout_ns of the global
+// timer: a block that gives up sets the status to 1, and every block ends
+// the launch at its next barrier.  Returns false when the launch must end.
+__device__ __noinline__ bool grid_sync(unsigned *bar, unsigned expect, long long timeout_ns)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vb = bar;
+        int good = vb[2] == 0u;
+        if (good) {
+            const unsigned gen = vb[1];
+            __threadfence();   // the block's writes (ordered by the block barrier) before its arrival
+            if (atomicAdd(bar, 1u) + 1u == expect) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                while (vb[1] == gen) {
+                    if (vb[2] != 0u) {
+                        good = 0;
+                        break;
+                    }
+                    if ((long long)(global_ns() - t0) > timeout_ns) {
+                        atomicExch(bar + 2, 1u);
+                        good = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+            __threadfence();   // the others' writes after the release
+        }
+        ok = good && vb[2] == 0u;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// The phases' work as calls of their own, so that each gets the register
+// file to itself instead of sharing one allocation with the launch's loops.
+template <typename real, int kSpec>
+__device__ __noinline__ void persist_tile(const StencilArgs<real> &A, const int *origin, unsigned char *smem_raw)
+{
+    stencil_tile<real, kSpec>(A, SharedOrigin{origin}, smem_raw);
+}
+
+template <typename real, int M>
+__device__ __noinline__ void persist_line(const LineArgs<real> &A, int line, LineShared<real> &L, int tid, int wbase,
+                                          bool valid)
+{
+    line_solve_reg<real, M, 0>(A, line, L, tid, wbase, valid);
+}
+
+// A descriptor or entry index out of range: recorded once in bar[3] (code
+// in the top byte, the index below), and the work it names is skipped.
+__device__ __forceinline__ void persist_flag(unsigned *bar, unsigned code, unsigned info)
+{
+    atomicCAS(bar + 3, 0u, (code << 24) | (info & 0xffffffu));
+}
+
+// One launch for nsteps lockstep steps of an ensemble: the work of each
+// batched launch (ghost tables; per stage the stencil tiles, then the line
+// solves) spread over the resident blocks, a grid-wide barrier where a
+// batched launch would end.  Every block runs the same loop, so each takes
+// every barrier.
+template <typename real>
+__global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
+    k_ensemble_persistent(const __grid_constant__ PersistArgs<real> P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) StencilArgs<real> As;
+    __shared__ int origin[2];
+    // the line phases reuse the stencil's shared memory: a slot's arguments,
+    // then the values that cross warps
+    static_assert(sizeof(LineArgs<real>) * (kStencilThreads / 32) + sizeof(LineShared<real>) <=
+                      sizeof(StencilSmem<real>),
+                  "line phase shared memory");
+    LineArgs<real> *Al = reinterpret_cast<LineArgs<real> *>(smem_raw);
+    LineShared<real> &L =
+        *reinterpret_cast<LineShared<real> *>(smem_raw + sizeof(LineArgs<real>) * (kStencilThreads / 32));
+    if (P.barrier_only) {
+        grid_sync(P.bar, P.expect, P.timeout_ns);
+        return;
+    }
+    for (int s = 0; s < P.nsteps; s++) {
+        const int ph = (P.phase0 + s) % 6;
+        if (P.gblocks > 0) {
+            // ghost tables: two 128-position blocks per pass
+            for (int b = 2 * blockIdx.x; b < P.gblocks; b += 2 * gridDim.x) {
+                const int blk = b + (threadIdx.x >> 7);
+                if (blk < P.gblocks) ghost_batch_block(P.gargs, P.gstart, P.ngm, blk, threadIdx.x & 127, P.k0 + s);
+            }
+            if (!grid_sync(P.bar, P.expect, P.timeout_ns)) return;
+        }
+        for (int stage = 0; stage < P.nstages; stage++) {
+            const int ei = P.ent[ph][stage];
+            if (ei < 0 || ei >= P.nent) {
+                if (threadIdx.x == 0) persist_flag(P.bar, 3u, (unsigned)(ph * 16 + stage));
+                return;   // every block returns here: no barrier is left waiting
+            }
+            const unsigned char *ent = P.entries + (size_t)ei * P.entry_bytes;
+            const StencilArgs<real> *sa = reinterpret_cast<const StencilArgs<real> *>(ent);
+            const int spec = P.spec[stage];
+            for (int t = blockIdx.x; t < P.tiles; t += gridDim.x) {
+                __syncthreads();   // the previous tile is done with shared memory
+                const int2 d = P.tile_desc[t];
+                if (d.x < 0 || d.x >= P.nmembers) {
+                    if (threadIdx.x == 0) persist_flag(P.bar, 1u, (unsigned)t);
+                    continue;
+                }
+                if (threadIdx.x == 0) {
+                    origin[0] = (d.y & 0xffff) * kTile;
+                    origin[1] = (d.y >> 16) * kTile;
+                }
+                load_args(As, sa + d.x);
+                __syncthreads();
+                if ((d.y & 0xffff) * kTile >= As.geo.nx || (d.y >> 16) * kTile >= As.geo.ny) {
+                    if (threadIdx.x == 0) persist_flag(P.bar, 2u, (unsigned)t);
+                    continue;
+                }
+                if (spec == 1)
+                    persist_tile<real, 1>(As, origin, smem_raw);
+                else if (spec == 2)
+                    persist_tile<real, 2>(As, origin, smem_raw);
+                else
+                    persist_tile<real, 0>(As, origin, smem_raw);
+            }
+            if (!grid_sync(P.bar, P.expect, P.timeout_ns)) return;
+            const LineArgs<real> *la = reinterpret_cast<const LineArgs<real> *>(ent + P.sarg_bytes);
+            for (int r = 0; r < P.nruns; r++) {
+                // G lines of T threads side by side; threads past G T only pass the barriers
+                const int T = P.run_threads[r], G = kStencilThreads / T, nl = P.run_lines[r];
+                const int slot = threadIdx.x / T, tid = threadIdx.x - slot * T;
+                const int passes = (nl + G - 1) / G;
+                for (int q = blockIdx.x; q < passes; q += gridDim.x) {
+                    const int line_q = q * G + slot;
+                    const bool valid = slot < G && line_q < nl;
+                    const int own = valid ? slot : 0;   // a spare slot takes slot 0's arguments
+                    __syncthreads();   // the previous pass is done with the arguments
+                    bool bad = false;
+                    if (slot < G) {
+                        const int2 d = P.run_desc[r][valid ? line_q : q * G];
+                        bad = d.x < 0 || d.x >= P.run_nfam[r];
+                        if (bad && tid == 0) persist_flag(P.bar, 4u, (unsigned)(r * 65536 + q));
+                        if ((valid || slot == 0) && !bad) {
+                            const int nw = (int)(sizeof(LineArgs<real>) / sizeof(int));
+                            int *dst = reinterpret_cast<int *>(&Al[slot]);
+                            const int *src = reinterpret_cast<const int *>(la + P.run_first[r] + d.x);
+                            for (int k = tid; k < nw; k += T) dst[k] = src[k];
+                        }
+                    }
+                    if (__syncthreads_or(bad)) continue;   // skip the pass (the block's decision)
+                    // the run's segment length picks the instance, the same
+                    // for every slot, and the run's lines are all of one
+                    // model: the solve's barriers are the block's, and the
+                    // shallow-water model takes none
+                    const int2 d = P.run_desc[r][valid ? line_q : q * G];
+                    const bool bad2 = slot < G && (d.y < 0 || d.y >= Al[own].nlines || Al[own].nseg > T ||
+                                                   (Al[own].nseg & 31) != 0 || Al[own].mshift != P.run_mshift[r] ||
+                                                   Al[own].identity != P.run_identity[r]);
+                    if (bad2 && tid == 0) persist_flag(P.bar, 5u, (unsigned)(r * 65536 + q));
+                    if (__syncthreads_or(bad2)) continue;
+                    const int wb = slot * (T >> 5);
+                    if (P.run_mshift[r] == 3)
+                        persist_line<real, 8>(Al[own], d.y, L, tid, wb, valid);
+                    else if (P.run_mshift[r] == 2)
+                        persist_line<real, 4>(Al[own], d.y, L, tid, wb, valid);
+                    else
+                        persist_line<real, 2>(Al[own], d.y, L, tid, wb, valid);
+                }
+            }
+            if (!grid_sync(P.bar, P.expect, P.timeout_ns)) return;
+        }
+    }
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------- launchers
@@ -2159,6 +2355,37 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
     return cudaGetLastError();
 }
 
+template <typename real>
+int persistent_grid()
+{
+    static int grid[2] = {-1, -1};
+    int &g = grid[sizeof(real) == 8];
+    if (g >= 0) return g;
+    const size_t smem = sizeof(StencilSmem<real>);
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_ensemble_persistent<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ensemble_persistent<real>, kStencilThreads, smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    g = sms * per;
+    return g;
+}
+
+template <typename real>
+cudaError_t launch_persistent(const PersistArgs<real> &p, int grid, cudaStream_t st)
+{
+    if (grid <= 0 || p.nstages > kPersistMaxStages || p.nruns > kPersistMaxRuns) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(StencilSmem<real>);
+    void *params[] = {const_cast<PersistArgs<real> *>(&p)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_ensemble_persistent<real>), dim3(grid),
+                                       dim3(kStencilThreads), params, smem, st);
+}
+
 #define CEL_INSTANTIATE(real)                                                                           \
     template cudaError_t launch_corners<real>(const Geo &, const real *, real *, cudaStream_t);           \
     template cudaError_t launch_static_cells<real>(const Geo &, const Phys &, const real *, real *,      \
@@ -2200,7 +2427,9 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
                                                   const int64_t *, cudaStream_t);                                        \
     template cudaError_t launch_stencil_batch<real>(const StencilArgs<real> *, const int2 *, int, int, cudaStream_t); \
     template cudaError_t launch_lines_batch<real>(const LineArgs<real> *, const int2 *, int, const LineCfg &, \
-                                                  cudaStream_t);
+                                                  cudaStream_t);                                          \
+    template int persistent_grid<real>();                                                                  \
+    template cudaError_t launch_persistent<real>(const PersistArgs<real> &, int, cudaStream_t);
 
 CEL_INSTANTIATE(float)
 CEL_INSTANTIATE(double)

@@ -261,6 +261,89 @@ def test_captured_cycles_equal_launches_one_by_one(prec):
     eb.close()
 
 
+@pytest.mark.parametrize("prec,K", [("f32", 1), ("f64", 1), ("f32", 2)])
+def test_persistent_launch_equals_launches_one_by_one(prec, K):
+    """With the persistent launch on, each call's steps (once the cycle's
+    argument blocks are in the table) run as one cooperative launch whose
+    blocks work through every phase between grid-wide barriers: the members
+    must equal, bit for bit, the same ensemble launching every kernel one by
+    one and the members stepped alone, over calls of uneven length and a
+    boundary change.  (With two corrector iterations the random beaches grow
+    unstable after about 60 steps, as even K does on such grids: that case
+    runs fewer steps.)"""
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(K)
+    ga = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    gb = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    alone = [celeris.from_scenario(s, dtype=_dtype(prec)) for s in scens]
+    ea = celeris.Ensemble(ga)
+    ea.use_persistent(True, timeout_ms=2000.0)
+    eb = celeris.Ensemble(gb)
+    eb.use_graphs(False)
+    first, second = ((8, 1, 13, 5, 20), (9, 11)) if K == 1 else ((8, 1, 7), (8, 3))
+    total = 0
+    for n in first:
+        ea.step(n)
+        eb.step(n)
+        total += n
+    taken = total - 8
+    assert ea.persistent_steps() == taken, ea.persistent_steps()   # every call after the first 8 steps
+    assert eb.persistent_steps() == 0
+    ea.check()
+    for m in alone:
+        m.step(total)
+    torch.cuda.synchronize()
+    _assert_equal(ga, gb)
+    _assert_equal(ga, alone)
+    for grp in (ga, gb, alone):
+        grp[1].set_boundary(sc.S, sc.SOLID)
+    for n in second:
+        ea.step(n)
+        eb.step(n)
+        for m in alone:
+            m.step(n)
+    ea.check()
+    torch.cuda.synchronize()
+    assert ea.persistent_steps() > taken
+    _assert_equal(ga, gb)
+    _assert_equal(ga, alone)
+    ea.close()
+    eb.close()
+
+
+def test_persistent_barrier_wait_is_bounded():
+    """Every wait of the persistent launch's grid-wide barrier has a bound: a
+    barrier that expects one block more than the launch has runs out after
+    the bound and reports it, and the GPU stays usable (a complete barrier,
+    then persistent steps equal to launches one by one)."""
+    import time
+
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)[:3]
+    ga = [celeris.from_scenario(s, dtype=torch.float32) for s in scens]
+    gb = [celeris.from_scenario(s, dtype=torch.float32) for s in scens]
+    ea = celeris.Ensemble(ga)
+    eb = celeris.Ensemble(gb)
+    eb.use_graphs(False)
+    assert not ea.barrier_check(0, 1000.0)
+    t0 = time.perf_counter()
+    assert ea.barrier_check(1, 200.0)
+    took = time.perf_counter() - t0
+    assert 0.15 <= took < 10.0, took
+    assert not ea.barrier_check(0, 1000.0)
+    ea.use_persistent(True, timeout_ms=2000.0)
+    ea.step(20)
+    eb.step(20)
+    ea.check()
+    torch.cuda.synchronize()
+    assert ea.persistent_steps() == 12
+    _assert_equal(ga, gb)
+    with pytest.raises(celeris.CelerisError):
+        ea.use_persistent(True, timeout_ms=0.0)
+    ea.close()
+    eb.close()
+
+
 def test_ensemble_under_a_tuned_split():
     """With a line split set (as the autotuner sets it), the ensemble and the
     members stepped alone still agree bit for bit; an ensemble planned before
