@@ -277,7 +277,7 @@ def measure_ensemble(steps, warmup, precision, world=1, rank=0):
     dtype = torch.float32 if args.precision == "f32" else torch.float64
     es = 4 if args.precision == "f32" else 8
     every = sc.ensemble()
-    share = sc.partition([s.cells for s in every], world)[rank]
+    share = celeris.ensemble_share([s.cells for s in every], rank, world)
     scens = [every[k] for k in share]
     members = [celeris.from_scenario(s, dtype=dtype) for s in scens]
     cells = sum(s.cells for s in scens)

@@ -643,6 +643,34 @@ def gauge_misfit(w0, solver, P0, Q0, nsteps, gauges, obs, ckpt_every=100, z=None
     return _gauge_misfit_function().apply(w0, z, solver, P0, Q0, nsteps, gauges, obs, ckpt_every)
 
 
+def ensemble_share(cells: Sequence[int], rank: Optional[int] = None, world: Optional[int] = None) -> list:
+    """Indices of the scenarios one rank steps when an ensemble is sharded
+    over ranks (one GPU each, no data exchanged between them): the split of
+    scenarios.partition, largest first to the rank with the fewest cells.
+    cells: the scenarios' cell counts.  rank and world default to those of
+    torch.distributed when it is initialised, else 0 and 1."""
+    from . import scenarios as _sc
+    if rank is None or world is None:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            rank, world = dist.get_rank(), dist.get_world_size()
+        else:
+            rank, world = 0, 1
+    if not 0 <= rank < world:
+        raise ValueError(f"rank {rank} outside a world of {world}")
+    return _sc.partition(list(cells), world)[rank]
+
+
+def sharded_ensemble(scenarios, dtype=None, rank: Optional[int] = None, world: Optional[int] = None,
+                     stream=None, **kw):
+    """This rank's share of an ensemble sharded over ranks: (Ensemble of its
+    members, the scenarios' indices).  Each rank steps its share alone; the
+    members' results do not depend on the sharding."""
+    share = ensemble_share([s.cells for s in scenarios], rank, world)
+    members = [from_scenario(scenarios[k], dtype=dtype, **kw) for k in share]
+    return Ensemble(members, stream=stream), share
+
+
 def from_scenario(s, dtype=None, K: Optional[int] = None, **kw) -> Solver:
     """A Solver set up with a scenario's bed, boundaries, state and solitons."""
     sol = Solver(s.z, s.dx, s.dy, s.dt, dtype=dtype, model=s.model, g=s.g, Bd=s.Bd, theta=s.theta,

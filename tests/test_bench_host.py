@@ -61,3 +61,43 @@ def test_ensemble_partition_covers_and_balances():
         loads = [sum(cells[k] for k in p) for p in parts]
         assert max(loads) - min(loads) <= max(cells)
     assert sc.partition([5, 4, 3, 3, 2, 1], 2) == [[0, 3, 5], [1, 2, 4]]   # loads 9 and 9
+
+
+def _share_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    from paper_1611_05984_gb300 import celeris
+    from paper_1611_05984_gb300 import scenarios as sc
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        cells = [s.cells for s in sc.ensemble()]
+        q.put((rank, celeris.ensemble_share(cells)))     # rank and world from the process group
+    finally:
+        dist.destroy_process_group()
+
+
+def test_ensemble_share_under_a_process_group():
+    """The library's sharding call, with rank and world taken from a gloo
+    process group of two ranks: the two shares are disjoint, cover every
+    scenario, and their cell totals differ by at most one scenario."""
+    from paper_1611_05984_gb300 import celeris
+    from paper_1611_05984_gb300 import scenarios as sc
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_share_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    cells = [s.cells for s in sc.ensemble()]
+    assert sorted(got[0] + got[1]) == list(range(len(cells)))
+    t0, t1 = (sum(cells[k] for k in got[r]) for r in (0, 1))
+    assert abs(t0 - t1) <= max(cells)
+    assert got[1] == celeris.ensemble_share(cells, 1, 2)       # explicit rank and world agree
+    assert celeris.ensemble_share(cells) == list(range(len(cells)))   # no process group: everything
+    with pytest.raises(ValueError):
+        celeris.ensemble_share(cells, 2, 2)

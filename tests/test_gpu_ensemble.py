@@ -344,6 +344,27 @@ def test_persistent_barrier_wait_is_bounded():
     eb.close()
 
 
+def test_sharded_ensemble_shares_step_like_the_members_alone():
+    """An ensemble sharded over two ranks (both shares built here, as each
+    rank would build its own): the shares cover the scenarios once, and
+    every member of either share equals, bit for bit, the member stepped
+    alone."""
+    from paper_1611_05984_gb300 import celeris
+    scens = _members(1)
+    e0, s0 = celeris.sharded_ensemble(scens, dtype=torch.float32, rank=0, world=2)
+    e1, s1 = celeris.sharded_ensemble(scens, dtype=torch.float32, rank=1, world=2)
+    assert sorted(s0 + s1) == list(range(len(scens))) and s0 and s1
+    alone = [celeris.from_scenario(s, dtype=torch.float32) for s in scens]
+    e0.step(11)
+    e1.step(11)
+    for m in alone:
+        m.step(11)
+    torch.cuda.synchronize()
+    _assert_equal(e0.members + e1.members, [alone[k] for k in s0 + s1])
+    e0.close()
+    e1.close()
+
+
 def test_ensemble_under_a_tuned_split():
     """With a line split set (as the autotuner sets it), the ensemble and the
     members stepped alone still agree bit for bit; an ensemble planned before
