@@ -1369,7 +1369,7 @@ void plan_t(cel_solver *const *ms, int n, EnsPlan &P)
     P.off_gargs = take(sizeof(GhostArgs<real>) * (size_t)n);
     P.off_gstart = take(sizeof(int) * (size_t)(n + 1));
     P.off_kdev = take(sizeof(int64_t));
-    P.off_bar = take(4 * sizeof(unsigned));
+    P.off_bar = take(8 * sizeof(unsigned));   // barrier words, then the work counters
     P.sarg_bytes = align256(sizeof(StencilArgs<real>) * (size_t)n);
     P.entry_bytes = P.sarg_bytes + align256(sizeof(LineArgs<real>) * P.fam.size());
     // the argument blocks repeat every 6 steps once the AB3 history is full
@@ -1763,6 +1763,11 @@ cel_status ens_persistent(cel_ensemble *e, int nsteps, int64_t &launches, bool *
     const int grid = persistent_grid<real>();
     if (grid <= 0) return CEL_OK;
     P.nruns = nruns;
+    P.run_pass0[0] = 0;
+    for (int r = 0; r < nruns; r++) {
+        const int G = kStencilThreads / P.run_threads[r];
+        P.run_pass0[r + 1] = P.run_pass0[r] + (P.run_lines[r] + G - 1) / G;
+    }
     P.nmembers = n;
     P.nent = (int)e->keys.size();
     P.entries = e->tab + e->off_entries;
@@ -1788,9 +1793,10 @@ cel_status ens_persistent(cel_ensemble *e, int nsteps, int64_t &launches, bool *
         P.k0 = e->m[e->gmem[0]]->step - e->gstep0[0];
     }
     P.bar = reinterpret_cast<unsigned *>(e->tab + e->off_bar);
+    P.work = reinterpret_cast<int *>(P.bar + 4);
     P.expect = (unsigned)grid;
     P.timeout_ns = (long long)(e->persist_timeout_ms * 1e6);
-    ENS_CUDA(e, cudaMemsetAsync(P.bar, 0, 4 * sizeof(unsigned), e->stream), "persistent barrier words");
+    ENS_CUDA(e, cudaMemsetAsync(P.bar, 0, 8 * sizeof(unsigned), e->stream), "persistent barrier words");
     ENS_CUDA(e, launch_persistent<real>(P, grid, e->stream), "persistent ensemble launch");
     for (int i = 0; i < nsteps; i++)
         for (int j = 0; j < n; j++) finish_step(e->m[j], Kn);
@@ -2006,7 +2012,7 @@ cel_status ens_read_barrier(cel_ensemble *e, unsigned *status)
     unsigned w[4] = {0, 0, 0, 0};
     ENS_CUDA(e, cudaStreamSynchronize(e->stream), "ensemble stream");
     ENS_CUDA(e, cudaMemcpy(w, e->tab + e->off_bar, sizeof(w), cudaMemcpyDeviceToHost), "persistent barrier words");
-    ENS_CUDA(e, cudaMemset(e->tab + e->off_bar, 0, sizeof(w)), "persistent barrier words");
+    ENS_CUDA(e, cudaMemset(e->tab + e->off_bar, 0, 8 * sizeof(unsigned)), "persistent barrier words");
     *status = w[2];
     if (w[3] != 0)
         return ens_fail(e, CEL_ERR_INVALID_ARG,
@@ -2034,7 +2040,7 @@ cel_status cel_ensemble_barrier_check(cel_ensemble *e, int32_t missing, double t
         return CEL_ERR_INVALID_ARG;
     const int grid = e->es == 4 ? persistent_grid<float>() : persistent_grid<double>();
     if (grid <= 0) return ens_fail(e, CEL_ERR_CUDA, "no block of the persistent launch fits an SM");
-    ENS_CUDA(e, cudaMemsetAsync(e->tab + e->off_bar, 0, 4 * sizeof(unsigned), e->stream), "persistent barrier words");
+    ENS_CUDA(e, cudaMemsetAsync(e->tab + e->off_bar, 0, 8 * sizeof(unsigned), e->stream), "persistent barrier words");
     cudaError_t ce;
     if (e->es == 4) {
         PersistArgs<float> P;

@@ -327,12 +327,14 @@ struct PersistArgs {
     int run_mshift[kPersistMaxRuns];   // log2 rows per segment of every line of the run
     int run_identity[kPersistMaxRuns]; // 1: the run's lines are shallow-water ones (P = U*, no solve)
     int run_nfam[kPersistMaxRuns];     // families of the run's group (descriptor x below it)
+    int run_pass0[kPersistMaxRuns + 1];   // first pass of each run in the phase's pass order (prefix sums)
     int nmembers, nent;                // members; argument entries in the table
     const GhostArgs<real> *gargs;      // as for the batched ghost launch
     const int *gstart;
     int ngm, gblocks;
     int64_t k0;                        // lockstep step index of the first step
-    unsigned *bar;                     // barrier words: arrivals, generation, status (0 at launch)
+    unsigned *bar;                     // barrier words: arrivals, generation, status, check (0 at launch)
+    int *work;                         // three work counters, used by the phases in turn (0 at launch)
     unsigned expect;                   // arrivals a barrier waits for: the grid size
     long long timeout_ns;              // bound of every wait
     int barrier_only;                  // 1: one barrier and nothing else (a check of the waits' bound)

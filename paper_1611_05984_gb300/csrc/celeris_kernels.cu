@@ -1756,8 +1756,10 @@ __device__ __forceinline__ unsigned long long global_ns()
 // block is resident).  bar[0] counts arrivals, bar[1] is the generation,
 // bar[2] the status.  Each wait is bounded by timeout_ns of the global
 // timer: a block that gives up sets the status to 1, and every block ends
-// the launch at its next barrier.  Returns false when the launch must end.
-__device__ __noinline__ bool grid_sync(unsigned *bar, unsigned expect, long long timeout_ns)
+// the launch at its next barrier.  The last block to arrive clears *reset
+// (a work counter no block uses until after the next barrier) before it
+// releases the others.  Returns false when the launch must end.
+__device__ __noinline__ bool grid_sync(unsigned *bar, unsigned expect, long long timeout_ns, int *reset = nullptr)
 {
     __shared__ int ok;
     __syncthreads();
@@ -1769,6 +1771,7 @@ __device__ __noinline__ bool grid_sync(unsigned *bar, unsigned expect, long long
             __threadfence();   // the block's writes (ordered by the block barrier) before its arrival
             if (atomicAdd(bar, 1u) + 1u == expect) {
                 atomicExch(bar, 0u);
+                if (reset) atomicExch(reset, 0);
                 __threadfence();
                 atomicAdd(bar + 1, 1u);
             } else {
@@ -1796,16 +1799,22 @@ __device__ __noinline__ bool grid_sync(unsigned *bar, unsigned expect, long long
 
 // The phases' work as calls of their own, so that each gets the register
 // file to itself instead of sharing one allocation with the launch's loops.
+// The arguments sit in shared memory and nothing the work stores aliases
+// them, which the compiler is told so that it keeps them in registers
+// across the global stores.
 template <typename real, int kSpec>
-__device__ __noinline__ void persist_tile(const StencilArgs<real> &A, const int *origin, unsigned char *smem_raw)
+__device__ __noinline__ void persist_tile(const StencilArgs<real> &__restrict__ A, const int *origin,
+                                          unsigned char *smem_raw)
 {
+    __builtin_assume(__isShared(&A));
     stencil_tile<real, kSpec>(A, SharedOrigin{origin}, smem_raw);
 }
 
 template <typename real, int M>
-__device__ __noinline__ void persist_line(const LineArgs<real> &A, int line, LineShared<real> &L, int tid, int wbase,
-                                          bool valid)
+__device__ __noinline__ void persist_line(const LineArgs<real> &__restrict__ A, int line, LineShared<real> &L, int tid,
+                                          int wbase, bool valid)
 {
+    __builtin_assume(__isShared(&A));
     line_solve_reg<real, M, 0>(A, line, L, tid, wbase, valid);
 }
 
@@ -1828,6 +1837,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) StencilArgs<real> As;
     __shared__ int origin[2];
+    __shared__ int item;
     // the line phases reuse the stencil's shared memory: a slot's arguments,
     // then the values that cross warps
     static_assert(sizeof(LineArgs<real>) * (kStencilThreads / 32) + sizeof(LineShared<real>) <=
@@ -1840,6 +1850,22 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
         grid_sync(P.bar, P.expect, P.timeout_ns);
         return;
     }
+    // Tiles and line passes go to blocks as they free up (a counter per
+    // phase, three used in turn), as the hardware hands out the blocks of a
+    // launch, so that a phase ends when its work does and not with its
+    // slowest block's fixed share.
+    int phase = 0;
+    auto next_item = [&]() -> int {
+        __syncthreads();   // the block is done with its previous item
+        if (threadIdx.x == 0) item = atomicAdd(P.work + phase % 3, 1);
+        __syncthreads();
+        return item;
+    };
+    auto end_phase = [&]() -> bool {
+        const bool ok = grid_sync(P.bar, P.expect, P.timeout_ns, P.work + (phase + 2) % 3);
+        phase++;
+        return ok;
+    };
     for (int s = 0; s < P.nsteps; s++) {
         const int ph = (P.phase0 + s) % 6;
         if (P.gblocks > 0) {
@@ -1848,7 +1874,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
                 const int blk = b + (threadIdx.x >> 7);
                 if (blk < P.gblocks) ghost_batch_block(P.gargs, P.gstart, P.ngm, blk, threadIdx.x & 127, P.k0 + s);
             }
-            if (!grid_sync(P.bar, P.expect, P.timeout_ns)) return;
+            if (!end_phase()) return;
         }
         for (int stage = 0; stage < P.nstages; stage++) {
             const int ei = P.ent[ph][stage];
@@ -1859,8 +1885,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
             const unsigned char *ent = P.entries + (size_t)ei * P.entry_bytes;
             const StencilArgs<real> *sa = reinterpret_cast<const StencilArgs<real> *>(ent);
             const int spec = P.spec[stage];
-            for (int t = blockIdx.x; t < P.tiles; t += gridDim.x) {
-                __syncthreads();   // the previous tile is done with shared memory
+            for (int t = next_item(); t < P.tiles; t = next_item()) {
                 const int2 d = P.tile_desc[t];
                 if (d.x < 0 || d.x >= P.nmembers) {
                     if (threadIdx.x == 0) persist_flag(P.bar, 1u, (unsigned)t);
@@ -1883,18 +1908,19 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
                 else
                     persist_tile<real, 0>(As, origin, smem_raw);
             }
-            if (!grid_sync(P.bar, P.expect, P.timeout_ns)) return;
+            if (!end_phase()) return;
             const LineArgs<real> *la = reinterpret_cast<const LineArgs<real> *>(ent + P.sarg_bytes);
-            for (int r = 0; r < P.nruns; r++) {
-                // G lines of T threads side by side; threads past G T only pass the barriers
-                const int T = P.run_threads[r], G = kStencilThreads / T, nl = P.run_lines[r];
-                const int slot = threadIdx.x / T, tid = threadIdx.x - slot * T;
-                const int passes = (nl + G - 1) / G;
-                for (int q = blockIdx.x; q < passes; q += gridDim.x) {
+            for (int p = next_item(); p < P.run_pass0[P.nruns]; p = next_item()) {
+                int r = 0;
+                while (P.run_pass0[r + 1] <= p) r++;
+                const int q = p - P.run_pass0[r];
+                {
+                    // G lines of T threads side by side; threads past G T only pass the barriers
+                    const int T = P.run_threads[r], G = kStencilThreads / T, nl = P.run_lines[r];
+                    const int slot = threadIdx.x / T, tid = threadIdx.x - slot * T;
                     const int line_q = q * G + slot;
                     const bool valid = slot < G && line_q < nl;
                     const int own = valid ? slot : 0;   // a spare slot takes slot 0's arguments
-                    __syncthreads();   // the previous pass is done with the arguments
                     bool bad = false;
                     if (slot < G) {
                         const int2 d = P.run_desc[r][valid ? line_q : q * G];
@@ -1927,7 +1953,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
                         persist_line<real, 2>(Al[own], d.y, L, tid, wb, valid);
                 }
             }
-            if (!grid_sync(P.bar, P.expect, P.timeout_ns)) return;
+            if (!end_phase()) return;
         }
     }
 }
