@@ -45,6 +45,14 @@ VALUES = {"stencil_pred_k": 14 + 11, "stencil_pred_0": 10 + 9, "stencil_corr": 7
 # (19); the line solves': U*, V* and the bed read (once per family), P, Q
 # written (6); a corrector's stencil: 14 - 6 = 8.
 CONTRACT = {"stencil_pred": 19, "stencil_corr": 8, "lines": 6}
+# FP64: the kernels are bound by the FP64 pipe, not by memory, so the FP64
+# line's roofline is arithmetic.  Double-precision operations per cell of one
+# launch, 2 DFMA + DADD + DMUL, counted by ncu on the 2048^2 beach
+# (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum / cells):
+# the AB3 predictor stencil, the AM4 corrector stencil, one line-solve launch
+# (both families).  The peak: 2 DFMA per clock per SM x 2 x 152 SMs x 2.07 GHz.
+FP64_FLOPS = {"stencil_pred": 562.6, "stencil_corr": 517.5, "lines": 117.9}
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 
 def parse():
@@ -606,6 +614,22 @@ def main():
                 "step_gbs_algorithmic": (c_st + c_ln) / (ms / 1e3) / 1e9 / world,
                 "step_frac": (c_st + c_ln) / (ms / 1e3) / 1e9 / world / peak,
                 "step_bytes_ring_history": (st_bytes + line_bytes) / args.steps}
+    if args.precision == "f64" and s.K > 0:
+        # the FP64 pipe bounds the FP64 kernels: the line's roofline is
+        # arithmetic, with the memory figures beside it
+        fl_of = {"stencil": s.cells * (nstages_pred * FP64_FLOPS["stencil_pred"] +
+                                       nstages_corr * FP64_FLOPS["stencil_corr"]),
+                 "lines": s.cells * FP64_FLOPS["lines"] * (nstages_pred + nstages_corr), "ghosts": 0}
+        dk = kernels[dominant]
+        tf = fl_of[dominant] / (dk["ms_total"] / 1e3) / 1e12 if dk["ms_total"] > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": dominant, "achieved": tf, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+                    "peak_source": "derived: 2 DFMA per clock per SM x 2 FLOP x 152 SMs x 2.07 GHz (the nominal "
+                                   "1.25 TFLOP/s FP64)",
+                    "count": "FP64 operations per cell counted by ncu (2 DFMA + DADD + DMUL): stencil 562.6 "
+                             "(predictor) / 517.5 (corrector), line solves 117.9 per stage",
+                    "hbm": {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "peak_source", "count")},
+                    "per_kernel": kernels}
 
     # ---- headless rendering of the final state (Fresnel water, hillshaded land)
     rp = celeris.render_params("fresnel", zmin=-10.0, zmax=3.0, exaggeration=10.0, view=(0.5, 0.3, -0.8))
