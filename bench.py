@@ -77,6 +77,8 @@ def parse():
                     help="default workload: steps of the adjoint measurement in the line (0: none)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the line solver's built-in split instead of autotuning it first")
+    ap.add_argument("--dependent-launch", default="on", choices=["on", "off"],
+                    help="programmatic dependent launch of the step's kernels (cel_set_dependent_launch)")
     return ap.parse_args()
 
 
@@ -362,11 +364,24 @@ def measure_ensemble(steps, warmup, precision, world=1, rank=0):
     e5.record(stream)
     torch.cuda.synchronize()
     barrier()
+    # the same one-at-a-time loop with plain launches (no programmatic
+    # dependent launch between the members' kernels)
+    dl = celeris.dependent_launch()
+    celeris.set_dependent_launch(False)
+    e6, e7 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e6.record(stream)
+    for m in members:
+        m.step(args.steps)
+    e7.record(stream)
+    torch.cuda.synchronize()
+    celeris.set_dependent_launch(dl)
+    barrier()
     clk = clocks.stop()
     ms_ens = max_over_ranks(e[0].elapsed_time(e[1]))
     ms_runs = max_over_ranks(e[2].elapsed_time(e[3]))
     ms_inter = max_over_ranks(e4.elapsed_time(e5))
     ms_one = min(ms_runs, ms_inter)
+    ms_plain = max_over_ranks(e6.elapsed_time(e7))
     finite = all(m.check_finite() for m in members)
     value = total_cells * args.steps / (ms_ens / 1e3)
     one = total_cells * args.steps / (ms_one / 1e3)
@@ -401,6 +416,9 @@ def measure_ensemble(steps, warmup, precision, world=1, rank=0):
                               "ms_per_step_interleaved": ms_inter / args.steps,
                               "gpu_launches": single_launches},
             "speedup_vs_single_launch": value / one,
+            "single_launch_plain": {"ms_per_step": ms_plain / args.steps, "speedup": ms_plain / ms_ens,
+                                    "what": "one cel_step(K steps) per member in turn with plain launches "
+                                            "(cel_set_dependent_launch(0))"},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                          "per_kernel": kernels, "per_kernel_from": f"a profiled run of {prof_steps} steps after "
@@ -516,6 +534,8 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    from paper_1611_05984_gb300 import celeris
+    celeris.set_dependent_launch(args.dependent_launch == "on")
     tune_lines(args)
     if args.workload == "ensemble256":
         run_ensemble(args)
@@ -547,25 +567,35 @@ def main():
     sol.step(args.warmup)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, inputs resident in HBM
+    # ---- timed region: K steps, inputs resident in HBM, nothing recorded
+    # between the kernels (an event between two kernels costs the step about
+    # 7 %: the next launch waits for it)
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.4)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sol.profile_enable(3 * (s.K + 1) * args.steps + 16)
     e0.record(stream)
     sol.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
     launches = sol.last_launch_count()
-    prof = sol.profile_read()
-    sol.profile_disable()
     ms = max_over_ranks(e0.elapsed_time(e1))
     value = whole_job_rate(s.cells, args.steps, ms)
+    # ---- the per-kernel split: the same K steps again, right after, with
+    # CUDA events around every kernel on the solver's stream
+    sol.profile_enable(3 * (s.K + 1) * args.steps + 16)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    sol.step(args.steps)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = sol.profile_read()
+    sol.profile_disable()
+    ms_profiled = max_over_ranks(p0.elapsed_time(p1))
 
     # ---- roofline of the dominant kernel (bytes per launch / event time)
     peak, peak_src = peaks()
@@ -610,6 +640,9 @@ def main():
                                           "with the AB3/AM4 ring history) + 10 per corrector, line solves 8 "
                                           "per stage (P^n read for the increment form)"},
                 "per_kernel": kernels,
+                "per_kernel_from": "the same K steps run again right after the timed ones, with CUDA events "
+                                   "around every kernel on the solver's stream (%.4f ms per step with them)"
+                                   % (ms_profiled / args.steps),
                 "step_bytes_algorithmic": (c_st + c_ln) / args.steps,
                 "step_gbs_algorithmic": (c_st + c_ln) / (ms / 1e3) / 1e9 / world,
                 "step_frac": (c_st + c_ln) / (ms / 1e3) / 1e9 / world / peak,
@@ -670,6 +703,7 @@ def main():
                         "value": el["value"], "unit": "cell-updates/s", "ms_per_step": el["ms_per_step"],
                         "single_launch": {"value": el["single_launch"]["value"],
                                           "ms_per_step": el["single_launch"]["ms_per_step"]},
+                        "single_launch_plain": el["single_launch_plain"],
                         "gpu_launches": el["gpu_launches"], "graph_steps": el["graph_steps"],
                         "persistent": {k: el["persistent"][k] for k in
                                        ("ms_per_step", "speedup_vs_single_launch", "steps", "gpu_launches")},
@@ -677,6 +711,10 @@ def main():
         if args.adjoint_steps > 0:
             a100 = measure_adjoint(args.adjoint_steps, 5, "f32", 512, 100)
             a0 = measure_adjoint(args.adjoint_steps, 5, "f32", 512, 0)
+            dl = celeris.dependent_launch()
+            celeris.set_dependent_launch(False)
+            ap = measure_adjoint(args.adjoint_steps, 5, "f32", 512, 100)
+            celeris.set_dependent_launch(dl)
             adjoint = {"workload": a100["config"]["workload"], "steps": args.adjoint_steps,
                        "ckpt_every": 100, "cost_ratio": a100["value"],
                        "forward_ms_per_step": a100["forward_ms_per_step"],
@@ -684,6 +722,10 @@ def main():
                        "every_step_kept": {"ckpt_every": 0, "cost_ratio": a0["value"],
                                            "adjoint_ms_per_step": a0["ms_per_step"],
                                            "scratch_gb": a0["config"]["scratch_gb"]},
+                       "plain_launches": {"ckpt_every": 100, "cost_ratio": ap["value"],
+                                          "forward_ms_per_step": ap["forward_ms_per_step"],
+                                          "adjoint_ms_per_step": ap["ms_per_step"],
+                                          "what": "the same with cel_set_dependent_launch(0)"},
                        "grad_finite": a100["grad_finite"] and a0["grad_finite"],
                        "what": "dL/dw0 and dL/dz of the 16-gauge misfit (forward with checkpoints, "
                                "recomputation and reverse) over the forward steps alone, CUDA events"}
@@ -695,7 +737,7 @@ def main():
                 "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": s.name, "nx": s.nx, "ny": s.ny, "cells": s.cells,
                            "corrector_iters": s.K, "dt": s.dt, "courant": 0.1,
-                           "parallelism": f"replicas{world}",
+                           "parallelism": f"replicas{world}", "dependent_launch": args.dependent_launch,
                            "l2": "inputs larger than L2 (workspace %.0f MB > 129 MB)"
                                  % (sol.workspace.numel() / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "render": render,

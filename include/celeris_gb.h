@@ -304,6 +304,17 @@ cel_status cel_set_line_split(int32_t real_bytes, int32_t max_rows, int32_t rows
 cel_status cel_reset_line_splits(void);
 cel_status cel_line_config(int32_t real_bytes, int32_t rows, int32_t *rows_per_thread, int32_t *threads);
 
+/* Programmatic dependent launch of the step's kernels (ghost tables,
+ * stencil, line solves, gauges, state captures; single grids and the
+ * adjoint's reverse; the ensembles' batched launches stay plain),
+ * process-wide, on by default: each is launched so that it
+ * may start while the kernel before it on the stream drains its last
+ * blocks, and waits on the device for that kernel's completion before it
+ * touches memory.  The results do not depend on the setting; 0 launches
+ * every kernel after the previous one has completed. */
+cel_status cel_set_dependent_launch(int32_t enable);
+cel_status cel_get_dependent_launch(int32_t *enabled);
+
 /* Kernel launches issued by the most recent cel_step call. */
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches);
 

@@ -40,7 +40,8 @@ EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_sta
            "cel_ensemble_barrier_check", "cel_ensemble_last_launch_count",
            "cel_ensemble_profile_enable", "cel_ensemble_profile_read", "cel_ensemble_profile_disable",
            "cel_ensemble_last_error", "cel_ensemble_destroy", "cel_advance_noalloc", "cel_set_line_split",
-           "cel_reset_line_splits", "cel_line_config", "cel_status_string",
+           "cel_reset_line_splits", "cel_line_config", "cel_set_dependent_launch", "cel_get_dependent_launch",
+           "cel_status_string",
            "cel_last_error", "cel_destroy"]
 
 
@@ -135,6 +136,8 @@ def load(build_if_missing: bool = True):
         L.cel_set_line_split.argtypes = [i32, i32, i32]
         L.cel_reset_line_splits.argtypes = []
         L.cel_line_config.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.cel_set_dependent_launch.argtypes = [i32]
+        L.cel_get_dependent_launch.argtypes = [ctypes.POINTER(i32)]
         L.cel_ensemble_last_error.restype = ctypes.c_char_p
         L.cel_ensemble_last_error.argtypes = [vp]
         L.cel_ensemble_destroy.argtypes = [vp]
@@ -522,6 +525,18 @@ def set_line_split(real_bytes: int, max_rows: int, rows_per_thread: int):
 def reset_line_splits():
     """Back to the built-in rule (cel_reset_line_splits)."""
     load().cel_reset_line_splits()
+
+
+def set_dependent_launch(enable: bool = True):
+    """Programmatic dependent launch of the step's kernels (process-wide;
+    cel_set_dependent_launch).  The results do not depend on it."""
+    load().cel_set_dependent_launch(int(bool(enable)))
+
+
+def dependent_launch() -> bool:
+    v = ctypes.c_int32()
+    load().cel_get_dependent_launch(ctypes.byref(v))
+    return bool(v.value)
 
 
 def line_config(real_bytes: int, rows: int):

@@ -407,6 +407,7 @@ __device__ __forceinline__ size_t corner_index(const Geo &G, int ci, int cj)
 template <typename real>
 __global__ void __launch_bounds__(1024) k_adj_mask(AdjArgs<real> A)
 {
+    dependent_launch_wait_then_release();
     __shared__ real tq[32][33];
     const Geo &G = A.geo;
     const int tx = threadIdx.x, ty = threadIdx.y, bx = blockIdx.x * 32, by = blockIdx.y * 32;
@@ -449,6 +450,7 @@ __global__ void __launch_bounds__(1024) k_adj_mask(AdjArgs<real> A)
 template <typename real>
 __global__ void __launch_bounds__(1024) k_adj_hist(AdjArgs<real> A)
 {
+    dependent_launch_wait_then_release();
     __shared__ real tq[32][33];
     const Geo &G = A.geo;
     const int tx = threadIdx.x, ty = threadIdx.y, bx = blockIdx.x * 32, by = blockIdx.y * 32;
@@ -846,6 +848,7 @@ constexpr size_t vjp_smem_bytes()
 template <typename real, int TY>
 __global__ void __launch_bounds__(kVjpThreads, sizeof(real) == 4 ? 4 : 2) k_adj_vjp(const __grid_constant__ AdjArgs<real> A)
 {
+    dependent_launch_wait_then_release();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sm = reinterpret_cast<real *>(smem_raw);
     const Geo &G = A.geo;
@@ -933,6 +936,7 @@ template <typename real>
 __global__ void k_adj_tri_bed(AdjArgs<real> A, const real *X, const real *Yc, const real *MUx, const real *MUy,
                               const real *dr, const real *dc, LineConst<real> K)
 {
+    dependent_launch_wait_then_release();
     const Geo &G = A.geo;
     const int dir = blockIdx.z;
     const int n = dir == 0 ? G.nx : G.ny, nl = dir == 0 ? G.ny : G.nx;
@@ -1001,6 +1005,7 @@ __global__ void k_adj_tri_bed(AdjArgs<real> A, const real *X, const real *Yc, co
 template <typename real>
 __global__ void k_adj_ghost_bed(AdjArgs<real> A, Bnd b, const double *ktab, const real *d_r, double t0, double t1)
 {
+    dependent_launch_wait_then_release();
     const int pos = blockIdx.x * blockDim.x + threadIdx.x, yb = blockIdx.y;
     const int time = yb & 1, layer = (yb >> 1) & 1, side = yb >> 2;
     const int npos = A.c.npos;
@@ -1082,6 +1087,7 @@ __global__ void k_adj_bed_z(AdjArgs<real> A, real *grad_z)
 template <typename real>
 __global__ void k_adj_misfit(AdjArgs<real> A, const int32_t *gij, int ng, const real *rec, const real *obs)
 {
+    dependent_launch_wait_then_release();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ng) return;
     atomicAdd(A.lw + gij[2 * k + 1] * A.geo.nx + gij[2 * k], rec[k] - obs[k]);
@@ -1093,16 +1099,16 @@ template <typename real>
 cudaError_t launch_adjoint_mask(const AdjArgs<real> &a, cudaStream_t st)
 {
     dim3 b(32, 32), g((a.geo.nx + 31) / 32, (a.geo.ny + 31) / 32);
-    k_adj_mask<real><<<g, b, 0, st>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = launch_step_kernel(k_adj_mask<real>, g, b, 0, st, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_adjoint_hist(const AdjArgs<real> &a, cudaStream_t st)
 {
     dim3 b(32, 32), g((a.geo.nx + 31) / 32, (a.geo.ny + 31) / 32);
-    k_adj_hist<real><<<g, b, 0, st>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = launch_step_kernel(k_adj_hist<real>, g, b, 0, st, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename real, int TY>
@@ -1116,8 +1122,8 @@ cudaError_t launch_vjp_rows(const AdjArgs<real> &a, cudaStream_t st)
         configured = true;
     }
     dim3 g((a.geo.nx + kVT - 1) / kVT, (a.geo.ny + TY - 1) / TY);
-    k_adj_vjp<real, TY><<<g, kVjpThreads, smem, st>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = launch_step_kernel(k_adj_vjp<real, TY>, g, dim3(kVjpThreads), smem, st, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Tile rows of the Jacobian kernel: 32 while 32 x 32 tiles give every SM
@@ -1165,7 +1171,9 @@ cudaError_t launch_adjoint_tri_bed(const AdjArgs<real> &a, const real *X, const 
         K.hrh[d] = real(0.5 / h);
         K.srh[d] = real(1.0 / (6.0 * h));
     }
-    k_adj_tri_bed<real><<<dim3((n + 127) / 128, nl, 2), 128, 0, st>>>(a, X, Yc, MUx, MUy, dr, dc, K);
+    cudaError_t e = launch_step_kernel(k_adj_tri_bed<real>, dim3((n + 127) / 128, nl, 2), dim3(128), 0, st, a, X, Yc,
+                                       MUx, MUy, dr, dc, K);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1174,7 +1182,9 @@ cudaError_t launch_adjoint_ghost_bed(const AdjArgs<real> &a, const Bnd &b, const
                                      double t0, double t1, cudaStream_t st)
 {
     if (!a.lg || !a.c.sine) return cudaSuccess;
-    k_adj_ghost_bed<real><<<dim3((a.c.npos + 127) / 128, 16), 128, 0, st>>>(a, b, ktab, d_r, t0, t1);
+    cudaError_t e = launch_step_kernel(k_adj_ghost_bed<real>, dim3((a.c.npos + 127) / 128, 16), dim3(128), 0, st, a,
+                                       b, ktab, d_r, t0, t1);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1194,7 +1204,9 @@ template <typename real>
 cudaError_t launch_adjoint_misfit(const AdjArgs<real> &a, const int32_t *gij, int ng, const real *rec, const real *obs,
                                   cudaStream_t st)
 {
-    k_adj_misfit<real><<<(ng + 127) / 128, 128, 0, st>>>(a, gij, ng, rec, obs);
+    cudaError_t e = launch_step_kernel(k_adj_misfit<real>, dim3((ng + 127) / 128), dim3(128), 0, st, a, gij, ng, rec,
+                                       obs);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -1023,6 +1023,19 @@ cel_status cel_line_config(int32_t real_bytes, int32_t rows, int32_t *rows_per_t
     return CEL_OK;
 }
 
+cel_status cel_set_dependent_launch(int32_t enable)
+{
+    set_dependent_launch(enable != 0);
+    return CEL_OK;
+}
+
+cel_status cel_get_dependent_launch(int32_t *enabled)
+{
+    if (!enabled) return CEL_ERR_INVALID_ARG;
+    *enabled = dependent_launch();
+    return CEL_OK;
+}
+
 cel_status cel_last_launch_count(const cel_solver *s, int64_t *launches)
 {
     if (!s || !launches) return CEL_ERR_INVALID_ARG;

@@ -265,6 +265,41 @@ LineCfg line_config(int n, int real_bytes);
 int line_split_set(int real_bytes, int max_rows, int rows_per_thread);
 void line_split_reset();
 int line_split_generation();
+// Programmatic dependent launch of the step kernels (process-wide, on by default).
+void set_dependent_launch(int on);
+int dependent_launch();
+
+// A kernel launched with programmatic stream serialisation may start while
+// the kernel before it on the stream drains its last blocks.  Each such
+// kernel first waits for that kernel to complete (its writes visible),
+// before any access to memory, then lets the kernel after it launch: the
+// kernels overlap only in their launch and block scheduling, never in their
+// memory accesses.  Without the launch attribute the wait returns at once.
+__device__ __forceinline__ void dependent_launch_wait_then_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// A step kernel's launch, with programmatic stream serialisation where it is
+// switched on (the kernel's own wait keeps its memory accesses after the
+// previous kernel's).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_step_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                      Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = dependent_launch() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 // Launches that launch_lines and its kin issue for the two families.
 int line_launches(int nx_lines, int n_x, int ny_lines, int n_y, int real_bytes);
 

@@ -23,6 +23,7 @@
 #include "celeris_physics.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -118,6 +119,7 @@ template <typename real>
 __global__ void k_get_state(Geo g, const real *w, const real *P, const real *Qc, real *w_out,
                             real *P_out, real *Q_out)
 {
+    dependent_launch_wait_then_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
     size_t k = (size_t)j * g.nx + i;
@@ -187,6 +189,7 @@ __global__ void k_add_solitary(Geo g, Phys p, const real *Bc, real *w, real *P, 
 template <typename real>
 __global__ void k_gauges(Geo g, Phys p, const real *w, const int32_t *ij, int n, real *slot)
 {
+    dependent_launch_wait_then_release();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int i = ij[2 * k], j = ij[2 * k + 1];
@@ -354,6 +357,7 @@ __global__ void k_ghost_table(Geo g, Phys p, Bnd b, const real *__restrict__ d_r
                               const double *__restrict__ ktab, double t0, double t1, real *__restrict__ tab,
                               int npos)
 {
+    dependent_launch_wait_then_release();
     ghost_entry(g, p, b, d_r, ktab, t0, t1, tab, npos, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
 }
 
@@ -916,6 +920,7 @@ template <typename real, int kSpec>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2) k_stencil(const __grid_constant__ StencilArgs<real> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    dependent_launch_wait_then_release();
     stencil_tile<real, kSpec>(A, GridOrigin(), smem_raw);
 }
 
@@ -1703,6 +1708,7 @@ __global__ void __launch_bounds__(kOcc ? 256 : (sizeof(real) == 4 ? 1024 : 512),
 {
     // blocks [0, nlines of x) solve x-rows, the rest y-columns
     __shared__ LineShared<real> L;
+    dependent_launch_wait_then_release();
     const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
     const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
     line_solve_any<real, kMode>(PA.L[fam], line, L);
@@ -1712,6 +1718,7 @@ template <typename real, int M, int kMode>
 __global__ void __launch_bounds__(sizeof(real) == 4 ? 1024 : 512) k_lines_seg(const __grid_constant__ LinePair<real> PA)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    dependent_launch_wait_then_release();
     const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
     const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
     line_solve_seg<real, M, kMode>(PA.L[fam], line, smem_raw);
@@ -1964,6 +1971,13 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(real) == 4 ? 4 : 2)
 
 static dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
+namespace {
+std::atomic<int> g_dependent_launch{1};
+}  // namespace
+
+void set_dependent_launch(int on) { g_dependent_launch.store(on ? 1 : 0); }
+int dependent_launch() { return g_dependent_launch.load(); }
+
 template <typename real>
 cudaError_t launch_corners(const Geo &g, const real *z, real *Bc, cudaStream_t st)
 {
@@ -2013,8 +2027,9 @@ cudaError_t launch_get_state(const Geo &g, const real *w, const real *P, const r
                              real *P_out, real *Q_out, cudaStream_t st)
 {
     dim3 b(32, 8);
-    k_get_state<real><<<grid2(g.nx, g.ny, b), b, 0, st>>>(g, w, P, Qc, w_out, P_out, Q_out);
-    return cudaGetLastError();
+    cudaError_t e = launch_step_kernel(k_get_state<real>, grid2(g.nx, g.ny, b), b, 0, st, g, w, P, Qc, w_out, P_out,
+                                       Q_out);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename real>
@@ -2049,8 +2064,8 @@ template <typename real>
 cudaError_t launch_gauges(const Geo &g, const Phys &p, const real *w, const int32_t *ij, int n, real *slot,
                           cudaStream_t st)
 {
-    k_gauges<real><<<(n + 127) / 128, 128, 0, st>>>(g, p, w, ij, n, slot);
-    return cudaGetLastError();
+    cudaError_t e = launch_step_kernel(k_gauges<real>, dim3((n + 127) / 128), dim3(128), 0, st, g, p, w, ij, n, slot);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename real>
@@ -2088,7 +2103,9 @@ template <typename real>
 cudaError_t launch_ghost_table(const Geo &g, const Phys &p, const Bnd &b, const real *d_r, const double *ktab,
                                double t0, double t1, real *tab, int npos, cudaStream_t st)
 {
-    k_ghost_table<real><<<dim3((npos + 127) / 128, 16), 128, 0, st>>>(g, p, b, d_r, ktab, t0, t1, tab, npos);
+    cudaError_t e = launch_step_kernel(k_ghost_table<real>, dim3((npos + 127) / 128, 16), dim3(128), 0, st, g, p, b,
+                                       d_r, ktab, t0, t1, tab, npos);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -2105,10 +2122,13 @@ cudaError_t launch_stencil(const StencilArgs<real> &a, cudaStream_t st)
         configured[spec] = true;
     }
     dim3 grid((a.geo.nx + kTile - 1) / kTile, (a.geo.ny + kTile - 1) / kTile);
-    kern<<<grid, kStencilThreads, smem, st>>>(a);
+    cudaError_t e = launch_step_kernel(kern, grid, dim3(kStencilThreads), smem, st, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
+// The ensemble's batched launches are plain launches: replayed as captured
+// graphs, programmatic dependent launch made the ensemble's step 3 % slower.
 template <typename real>
 cudaError_t launch_ghost_batch(const GhostArgs<real> *args, const int *start, int n, int nblocks, int64_t k,
                                const int64_t *kdev, cudaStream_t st)
@@ -2335,8 +2355,8 @@ cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, int mode
         auto *kern = mode == 1 ? (occ ? k_lines<real, 1, 1> : k_lines<real, 1>)
                    : mode == 2 ? (occ ? k_lines<real, 2, 1> : k_lines<real, 2>)
                                : (occ ? k_lines<real, 0, 1> : k_lines<real, 0>);
-        kern<<<blocks, threads, 0, st>>>(p);
-        return cudaGetLastError();
+        cudaError_t e = launch_step_kernel(kern, dim3(blocks), dim3(threads), 0, st, p);
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     if (sh < 1 || sh > 5) return cudaErrorInvalidValue;
     size_t smem = c.smem;
@@ -2348,8 +2368,8 @@ cudaError_t launch_lines_impl(const LinePair<real> &p, cudaStream_t st, int mode
         if (e != cudaSuccess) return e;
         configured[mode][sh] = (int)smem;
     }
-    kern<<<blocks, c.threads, smem, st>>>(p);
-    return cudaGetLastError();
+    cudaError_t e = launch_step_kernel(kern, dim3(blocks), dim3(c.threads), smem, st, p);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename real>
@@ -2360,7 +2380,6 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
     if (threads < 32 || threads % 32 || threads > (sizeof(real) == 4 ? 1024 : 512)) return cudaErrorInvalidValue;
     if (nblocks <= 0) return cudaSuccess;
     if (cfg.algo == 0) {
-        // lines of at most 128 threads share blocks of up to 256
         if (sizeof(real) == 4 && threads <= 256)
             k_lines_batch<real, 1><<<nblocks, threads, 0, st>>>(args, desc);
         else

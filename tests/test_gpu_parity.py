@@ -410,3 +410,24 @@ def test_line_splits_match_oracle(m):
         _lockstep(s, "f32", 300)
     finally:
         celeris.reset_line_splits()
+
+
+def test_dependent_launch_changes_nothing():
+    """The step's kernels launched with programmatic dependent launch (each
+    waiting on the device for the previous kernel before it touches memory)
+    give the results of plain launches bit for bit, in FP32 and FP64."""
+    from paper_1611_05984_gb300 import celeris
+    s = sc.beach(nx=300, ny=200, sponge=20, nshoal=3)
+    try:
+        for prec in ("f32", "f64"):
+            out = []
+            for on in (True, False):
+                celeris.set_dependent_launch(on)
+                assert celeris.dependent_launch() == on
+                g = _solver(s, prec)
+                g.step(25)
+                out.append(g.state())
+            for a, b in zip(*out):
+                assert torch.equal(a, b)
+    finally:
+        celeris.set_dependent_launch(True)
