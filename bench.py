@@ -411,7 +411,8 @@ def measure_ensemble(steps, warmup, precision, world=1, rank=0):
                              % (sum(m.workspace.numel() for m in members) / 1e9)},
             "single_launch": {"value": one, "ms_per_step": ms_one / args.steps,
                               "what": "the same members one at a time, the faster of: one cel_step(K steps) "
-                                      "per member in turn, and every member one cel_step(1) per step",
+                                      "per member in turn, and every member one cel_step(1) per step "
+                                      "(the library's default launches: programmatic dependent launch)",
                               "ms_per_step_per_member_runs": ms_runs / args.steps,
                               "ms_per_step_interleaved": ms_inter / args.steps,
                               "gpu_launches": single_launches},
