@@ -150,6 +150,13 @@ cel_status cel_set_gauges(cel_solver *s, const int32_t *ij_host, int32_t n,
  * drop them from the ring; *n_rec = records written.  Synchronises. */
 cel_status cel_read_gauges(cel_solver *s, void *eta_host, int32_t max_rec,
                            int32_t *n_rec);
+/* The same without synchronising: the copies are queued on the handle's
+ * stream (asynchronous where eta_host is pinned), so the next steps can be
+ * queued behind them; *n_rec is known at once, the values are in eta_host
+ * once the stream has reached the copies (cudaStreamSynchronize or an event
+ * recorded after this call).  eta_host must stay valid until then. */
+cel_status cel_read_gauges_async(cel_solver *s, void *eta_host, int32_t max_rec,
+                                 int32_t *n_rec);
 
 /* Simulated time t = step * dt and the step count since create.  Host only. */
 cel_status cel_get_time(cel_solver *s, double *t, int64_t *step);

@@ -29,7 +29,7 @@ FIELDS = {"Bbar": 0, "d": 1, "U": 2, "V": 3}
 
 EXPORTS = ["cel_workspace_bytes", "cel_create", "cel_set_boundary", "cel_set_state",
            "cel_add_solitary", "cel_set_bathymetry", "cel_step", "cel_get_state", "cel_get_field",
-           "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_get_time",
+           "cel_gauge_bytes", "cel_set_gauges", "cel_read_gauges", "cel_read_gauges_async", "cel_get_time",
            "cel_check_finite", "cel_checkpoint_bytes", "cel_save_checkpoint",
            "cel_load_checkpoint", "cel_runup_enable", "cel_render", "cel_adjoint_bytes",
            "cel_adjoint_gauge_misfit", "cel_adjoint_face_selfcheck", "cel_adjoint_input_gradient",
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
         L.cel_gauge_bytes.argtypes = [i32, i32, i32, ctypes.POINTER(sz)]
         L.cel_set_gauges.argtypes = [vp, ctypes.POINTER(i32), i32, i32, i32, vp, sz]
         L.cel_read_gauges.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+        L.cel_read_gauges_async.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
         L.cel_get_time.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64)]
         L.cel_check_finite.argtypes = [vp]
         L.cel_checkpoint_bytes.argtypes = [vp, ctypes.POINTER(sz)]
@@ -322,6 +323,21 @@ class Solver:
         n = ctypes.c_int32()
         self._check(self.L.cel_read_gauges(self._h, out.ctypes.data, max_rec, ctypes.byref(n)), "read_gauges")
         return out[: n.value]
+
+    def read_gauges_async(self, out) -> int:
+        """Queue the copy of up to len(out) oldest gauge records into `out`
+        (a pinned host tensor [records, gauges] of the solver's dtype) on the
+        solver's stream without synchronising (cel_read_gauges_async);
+        returns the records queued.  The values are there once the stream has
+        passed this point."""
+        if out.device.type != "cpu" or out.dim() != 2 or out.shape[1] != self.ng or not out.is_contiguous():
+            raise ValueError("out must be a contiguous host tensor [records, gauges]")
+        if out.element_size() != self.es:
+            raise ValueError("out must have the solver's precision")
+        n = ctypes.c_int32()
+        self._check(self.L.cel_read_gauges_async(self._h, out.data_ptr(), out.shape[0], ctypes.byref(n)),
+                    "read_gauges_async")
+        return n.value
 
     def time(self):
         t, s = ctypes.c_double(), ctypes.c_int64()

@@ -774,7 +774,10 @@ cel_status cel_set_gauges(cel_solver *s, const int32_t *ij_host, int32_t n, int3
     return CEL_OK;
 }
 
-cel_status cel_read_gauges(cel_solver *s, void *eta_host, int32_t max_rec, int32_t *n_rec)
+namespace {
+// Copies of up to max_rec oldest gauge records to eta_host, queued on the
+// handle's stream, and the records dropped from the ring.
+cel_status queue_gauge_read(cel_solver *s, void *eta_host, int32_t max_rec, int32_t *n_rec)
 {
     if (!s || !n_rec || max_rec < 0 || (max_rec > 0 && !eta_host)) return fail(s, CEL_ERR_INVALID_ARG, "bad read");
     int n = s->nrec < max_rec ? s->nrec : max_rec;
@@ -784,11 +787,24 @@ cel_status cel_read_gauges(cel_solver *s, void *eta_host, int32_t max_rec, int32
         CEL_CUDA(s, cudaMemcpyAsync((unsigned char *)eta_host + (size_t)r * rec, s->gring + (size_t)slot * rec, rec,
                                     cudaMemcpyDeviceToHost, s->stream), "read gauges");
     }
-    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "read gauges");
     if (s->cap) s->head = (s->head + n) % s->cap;
     s->nrec -= n;
     *n_rec = n;
     return CEL_OK;
+}
+}  // namespace
+
+cel_status cel_read_gauges(cel_solver *s, void *eta_host, int32_t max_rec, int32_t *n_rec)
+{
+    cel_status st = queue_gauge_read(s, eta_host, max_rec, n_rec);
+    if (st != CEL_OK) return st;
+    CEL_CUDA(s, cudaStreamSynchronize(s->stream), "read gauges");
+    return CEL_OK;
+}
+
+cel_status cel_read_gauges_async(cel_solver *s, void *eta_host, int32_t max_rec, int32_t *n_rec)
+{
+    return queue_gauge_read(s, eta_host, max_rec, n_rec);
 }
 
 cel_status cel_get_time(cel_solver *s, double *t, int64_t *step)

@@ -174,6 +174,27 @@ def test_gauges_match_oracle():
     assert g.read_gauges(10).shape[0] == 0
 
 
+def test_queued_gauge_reads_equal_synchronous_reads():
+    """cel_read_gauges_async queues the records' copies on the stream: read
+    every step into a pinned buffer without synchronising, they equal the
+    records read synchronously from a twin solver, and the ring is empty."""
+    s = sc.soliton_channel(K=0)
+    a, b = _solver(s, "f64"), _solver(s, "f64")
+    ij = [(10, 3), (128, 16), (255, 31)]
+    a.set_gauges(ij, 1, 2)
+    b.set_gauges(ij, 1, 2)
+    buf = torch.empty((20, 3), dtype=torch.float64).pin_memory()
+    sync = []
+    for k in range(20):
+        a.step(1)
+        assert a.read_gauges_async(buf[k:k + 1]) == 1
+        b.step(1)
+        sync.append(b.read_gauges(2))
+    a.stream.synchronize()
+    np.testing.assert_array_equal(buf.numpy(), np.concatenate(sync))
+    assert a.read_gauges(2).shape[0] == 0
+
+
 def test_check_finite_and_launch_count():
     s = sc.soliton_channel(K=2)
     g = _solver(s, "f32")
