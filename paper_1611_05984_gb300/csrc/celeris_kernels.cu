@@ -2403,13 +2403,22 @@ cudaError_t launch_lines_batch(const LineArgs<real> *args, const int2 *desc, int
 template <typename real>
 int persistent_grid()
 {
-    static int grid[2] = {-1, -1};
-    int &g = grid[sizeof(real) == 8];
-    if (g >= 0) return g;
+    // per device (the SM count and the function attribute are the device's)
+    constexpr int kDevices = 64;
+    static std::atomic<int> grid[kDevices];
+    static std::once_flag init;
+    std::call_once(init, [] {
+        for (auto &g : grid) g.store(-1);
+    });
     const size_t smem = sizeof(StencilSmem<real>);
     int dev = 0, sms = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int known = grid[dev].load();
+    if (known >= 0) return known;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(k_ensemble_persistent<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ensemble_persistent<real>, kStencilThreads, smem) !=
@@ -2417,8 +2426,8 @@ int persistent_grid()
         cudaGetLastError();
         return 0;
     }
-    g = sms * per;
-    return g;
+    grid[dev].store(sms * per);
+    return sms * per;
 }
 
 template <typename real>
