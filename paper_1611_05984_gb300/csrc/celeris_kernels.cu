@@ -1164,24 +1164,33 @@ __device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line
     real *out = A.sol + lo;
     const bool any = act && f < n;         // the segment holds rows of the line
 
-    real r[M];
-    if (any) {
-        if (kMode == 0) {   // P^n and the dry bits are read in the epilogue: to L1 now
+    // What the kernel before this one on the stream does not write comes
+    // first: P^n (read in the epilogue: to L1 now), the depths, the rows of
+    // the system and the makers' ghost increments.  Then the wait for that
+    // kernel (a stencil launch), and the right side it wrote.
+    if (any && kMode == 0) {
 #pragma unroll
-            for (int u = 0; u < M; u += 32 / (int)sizeof(real))
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.base + lo + f + u));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.mask + (size_t)line * A.nwords + (f >> 5)));
-        }
-        load_run<real, M>(r, A.rhs + lo + f);
-#pragma unroll
-        for (int j = 0; j < M; j++)
-            if (f + j >= n) r[j] = real(0);
-    } else {
-#pragma unroll
-        for (int j = 0; j < M; j++) r[j] = real(0);
+        for (int u = 0; u < M; u += 32 / (int)sizeof(real))
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.base + lo + f + u));
     }
+    real r[M];
+    auto load_rhs = [&]() {
+        dependent_launch_wait_then_release();
+        if (any) {
+            if (kMode == 0)   // the dry bits, read in the epilogue
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.mask + (size_t)line * A.nwords + (f >> 5)));
+            load_run<real, M>(r, A.rhs + lo + f);
+#pragma unroll
+            for (int j = 0; j < M; j++)
+                if (f + j >= n) r[j] = real(0);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; j++) r[j] = real(0);
+        }
+    };
     real x[M];
     if (A.identity) {   // NLSW: P = U*
+        load_rhs();
 #pragma unroll
         for (int j = 0; j < M; j++) x[j] = r[j];
     } else {
@@ -1223,23 +1232,38 @@ __device__ __forceinline__ void line_solve_reg(const LineArgs<real> &A, int line
                 rb[j] = tb[j + 1];
                 rc[j] = ta[j + 2];
             }
+            load_rhs();
         } else {
 #pragma unroll
             for (int j = 0; j < M; j++)
                 coef23(A.c.B3, A.hrh, A.srh, A.rh2, dv[j + 2], dv[j + 1], dv[j + 3], ra[j], rb[j], rc[j]);
+            // the makers' ghost increments (t^{n+1} - t^n) at the line's ends
+            // and the coefficients that carry them to the right side
+            real lo_inc = real(0), hi_inc = real(0), a_lo = real(0), c_hi = real(0);
             if (f == 0 || at_end) {
-                // the makers' ghost increments (t^{n+1} - t^n) at the line's ends
-                real lo_inc = real(0), hi_inc = real(0);
-                if (lo_sine && f == 0)
+                if (lo_sine && f == 0) {
                     lo_inc = A.ghost[ghost_index(1, lo_side, 0, gvar, line + 2, A.c.npos)] -
                              A.ghost[ghost_index(0, lo_side, 0, gvar, line + 2, A.c.npos)];
-                if (hi_sine && at_end && f <= n - 1)
+                    a_lo = ra[0];
+                }
+                if (hi_sine && at_end && f <= n - 1) {
                     hi_inc = A.ghost[ghost_index(1, hi_side, 0, gvar, line + 2, A.c.npos)] -
                              A.ghost[ghost_index(0, hi_side, 0, gvar, line + 2, A.c.npos)];
 #pragma unroll
+                    for (int j = 0; j < M; j++)
+                        if (f + j == n - 1) c_hi = rc[j];
+                }
+#pragma unroll
                 for (int j = 0; j < M; j++)
                     t_row(A, f + j, dv[j + 1], dv[j + 2], dv[j + 3], lo_sine, hi_sine, lo_inc, hi_inc, ra[j], rb[j],
-                          rc[j], &r[j]);
+                          rc[j], (real *)nullptr);
+            }
+            load_rhs();
+            if (lo_sine && f == 0) r[0] -= a_lo * lo_inc;   // Reading A-B2: the known ghost increment moves to the right side
+            if (hi_sine && at_end && f <= n - 1) {
+#pragma unroll
+                for (int j = 0; j < M; j++)
+                    if (f + j == n - 1) r[j] -= c_hi * hi_inc;
             }
         }
         // Thomas on rows f .. f + M - 2 against (r, -a_f e_0, -c e_last)
@@ -1706,9 +1730,10 @@ template <typename real, int kMode, int kOcc = 0>
 __global__ void __launch_bounds__(kOcc ? 256 : (sizeof(real) == 4 ? 1024 : 512), kOcc ? 5 : 1)
     k_lines(const __grid_constant__ LinePair<real> PA)
 {
-    // blocks [0, nlines of x) solve x-rows, the rest y-columns
+    // blocks [0, nlines of x) solve x-rows, the rest y-columns (the solve
+    // waits for the kernel before this one once it has read what that
+    // kernel does not write)
     __shared__ LineShared<real> L;
-    dependent_launch_wait_then_release();
     const int fam = blockIdx.x < PA.L[0].nlines ? 0 : 1;
     const int line = fam == 0 ? blockIdx.x : blockIdx.x - PA.L[0].nlines;
     line_solve_any<real, kMode>(PA.L[fam], line, L);
