@@ -106,6 +106,34 @@ MUTANTS = [
      "test_corner_ghosts_where_two_makers_meet"),
     ("corner_ghosts_stale_beside_wall", _CORNER, _CORNER.replace("int i = -2; i < nx + 2;", "int i = 0; i < nx;"),
      "test_corner_ghost_of_a_maker_beside_a_wall_by_embedding"),
+    # time stepping (Sec. 2.3, Eq. 15-20)
+    ("am4_E_coef", "(9.0 * o->Ec[c] + 19.0 * o->E[0][c] - 5.0 * o->E[1][c] + o->E[2][c])",
+     "(9.0 * o->Ec[c] + 19.0 * o->E[0][c] - 5.0 * o->E[1][c] - o->E[2][c])",
+     "test_dispersion_relation_1d_with_corrector"),
+    ("am4_E_coef_oblique", "(9.0 * o->Ec[c] + 19.0 * o->E[0][c] - 5.0 * o->E[1][c] + o->E[2][c])",
+     "(9.0 * o->Ec[c] + 19.0 * o->E[0][c] - 5.0 * o->E[1][c] - o->E[2][c])",
+     "test_standing_mode_started_from_its_discharges"),
+    ("euler_Fstar_increment", "(o->Fs[0][c] - o->Fs[1][c]);", "(o->Fs[0][c]);",
+     "test_standing_mode_started_from_its_discharges"),
+    ("euler_Gstar_increment", "(o->Gs[0][c] - o->Gs[1][c]);", "(o->Gs[0][c]);",
+     "test_standing_mode_started_from_its_discharges"),
+    ("ab3_Fstar_first_order", "2.0 * o->Fs[0][c] - 3.0 * o->Fs[1][c] + o->Fs[2][c]", "o->Fs[0][c] - o->Fs[1][c]",
+     "test_isotropy_over_a_round_shoal"),
+    ("am4_Fstar_increment", "o->Fsc[c] - o->Fs[0][c];", "o->Fsc[c] - o->Fs[1][c];",
+     "test_dispersion_relation_2d_oblique"),
+    # pieces: limiter, local speeds, friction law, sponge, Thomas
+    ("minmod_drop_central", "return fmin(a, fmin(b, c));", "return fmin(a, c);", "test_minmod_cases"),
+    ("minmod_theta_ignored", "orc_real a = theta * (q0 - qm), b = 0.5 * (qp - qm), c = theta * (qp - q0);",
+     "orc_real a = (q0 - qm), b = 0.5 * (qp - qm), c = (qp - q0);", "test_minmod_cases"),
+    ("wave_speed_am_side", "orc_real am = fmin(fmin(uL - sL, uR - sR), 0.0);",
+     "orc_real am = fmin(fmin(uL - sL, uL - sR), 0.0);", "test_central_upwind_mirror_symmetry"),
+    ("wave_speed_ap_side", "orc_real ap = fmax(fmax(uL + sL, uR + sR), 0.0);",
+     "orc_real ap = fmax(fmax(uL + sL, uR + sL), 0.0);", "test_central_upwind_mirror_symmetry"),
+    ("manning_cube_root", "cbrt(hinv)", "hinv", "test_friction_manning_ode"),
+    ("sponge_cos_sign", "return 0.5 * (1.0 + cos(ORC_PI * (Ls - D) / Ls));",
+     "return 0.5 * (1.0 - cos(ORC_PI * (Ls - D) / Ls));", "test_sponge_gamma"),
+    ("thomas_back_sub_sign", "x[i] = dp[i] - cp[i] * x[i + 1];", "x[i] = dp[i] + cp[i] * x[i + 1];",
+     "test_thomas_vs_dense"),
 ]
 
 

@@ -9,7 +9,8 @@ an invariant, a textbook routine, a special case or a convergence order.
   minmod (KP07 step 1)                    hand cases                test_minmod_*
   Eckart k (Eq. 29)                       Newton on w^2 = gk tanh kd test_eckart_*
   sponge gamma (Eq. 30)                   end values, monotone      test_sponge_*
-  central-upwind flux (KP07 step 3)       consistency, upwinding    test_central_*
+  central-upwind flux (KP07 step 3)       consistency, upwinding,   test_central_*
+                                          mirror symmetry
   reconstruction + flux + bed slope       lake at rest              test_lake_*
   flux form, walls, AB3 / AM4             mass conservation         test_mass_*
   NLSW path, dry front                    Ritter closed form        test_ritter_*
@@ -28,6 +29,9 @@ an invariant, a textbook routine, a special case or a convergence order.
   sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
   sine maker on the y-sides               transposed runs           test_symmetry_transpose_sine_*
   friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders   test_friction_*
+  AM4 weights of w, start-up F*, G*       1-D mode with corrector;  test_dispersion_relation_1d_with_*
+  increments (Sec. 2.3, Eq. 18)           mode started from its     test_standing_mode_started_*
+                                          discharges
   AB3 stability (Sec. 2.3)                real-axis bound -6/11     test_stability_*
 """
 import math
@@ -127,6 +131,28 @@ def test_central_upwind_consistency(oracle_mod):
     assert list(cu(G, eps, 1.0, 0.3, 0.1, 1.0, -0.2, 0.0, 1.0)) == [0.0, 0.0, 0.0]
 
 
+def test_central_upwind_mirror_symmetry(oracle_mod):
+    """KP07 step 3 is unchanged by the reflection x -> -x: the face's sides
+    trade places, the normal discharges change sign, the one-sided speeds
+    a+ and a- trade places with a sign, so the flux through the reflected
+    face is (-H0, H1, -H2).  A speed taken from the wrong side, or a sign
+    slip in one of the two fluxes, breaks it.  Seeded random states, some
+    sides dry."""
+    cu = oracle_mod.central_upwind
+    rng = np.random.default_rng(1611)
+    for _ in range(400):
+        Bf = rng.uniform(-2.0, 0.5)
+        hL, hR = (0.0 if rng.random() < 0.15 else rng.uniform(0.0, 3.0) for _ in range(2))
+        nL, tL, nR, tR = rng.uniform(-6.0, 6.0, 4)
+        wL, wR = Bf + hL, Bf + hR
+        H = cu(G, 5e-12, wL, nL, tL, wR, nR, tR, Bf)
+        Hm = cu(G, 5e-12, wR, -nR, tR, wL, -nL, tL, Bf)
+        scale = max(1.0, max(abs(v) for v in H))
+        assert Hm[0] == pytest.approx(-H[0], rel=1e-13, abs=1e-13 * scale)
+        assert Hm[1] == pytest.approx(H[1], rel=1e-13, abs=1e-13 * scale)
+        assert Hm[2] == pytest.approx(-H[2], rel=1e-13, abs=1e-13 * scale)
+
+
 # -------------------------------------------------------------- invariants
 
 def test_lake_at_rest_submerged(oracle_mod):
@@ -217,10 +243,11 @@ def _omega(k, d):
     return k * math.sqrt(G * d * (1 + B * (k * d) ** 2) / (1 + (B + 1 / 3) * (k * d) ** 2))
 
 
-def _standing_period_error(oracle_mod, kd, cpl, twod=False, periods=3):
+def _standing_period_error(oracle_mod, kd, cpl, twod=False, periods=3, K=None):
     """Standing mode eta = a cos(kx x)[cos(ky y)] in a walled basin; period
     from the zero crossings of eta at the corner cell vs the linear
-    dispersion relation of Eq. 2 / 7 / 10 (flat bed)."""
+    dispersion relation of Eq. 2 / 7 / 10 (flat bed).  K defaults to 1 for
+    the oblique mode and 0 for the 1-D one."""
     d = 1.0
     k = kd / d
     if twod:
@@ -233,7 +260,7 @@ def _standing_period_error(oracle_mod, kd, cpl, twod=False, periods=3):
     eta = 1e-4 * d * np.cos(kx * X) * (np.cos(ky * Y) if twod else 1.0)
     z = np.full((ny, nx), -d)
     dt = 0.2 * dx / math.sqrt(G * d)
-    o = oracle_mod.Oracle(z, dx, dx, dt, K=1 if twod else 0)
+    o = oracle_mod.Oracle(z, dx, dx, dt, K=(1 if twod else 0) if K is None else K)
     o.set_state(eta, 0 * z, 0 * z)
     T = 2 * math.pi / _omega(k, d)
     n = int(periods * T / dt) + 2
@@ -256,12 +283,68 @@ def test_dispersion_relation_1d(oracle_mod, kd):
 
 
 @pytest.mark.parametrize("kd", [1.0, 2.0])
+def test_dispersion_relation_1d_with_corrector(oracle_mod, kd):
+    """The same 1-D mode with one AM4 corrector iteration (Eq. 18-20): the
+    corrector's weights of w and of U must keep the period, to second order
+    in space."""
+    e64 = _standing_period_error(oracle_mod, kd, 64, K=1)
+    e128 = _standing_period_error(oracle_mod, kd, 128, K=1)
+    assert e64 <= 5e-3
+    assert e128 <= e64 / 3.0
+
+
+@pytest.mark.parametrize("kd", [1.0, 2.0])
 def test_dispersion_relation_2d_oblique(oracle_mod, kd):
     """An oblique mode needs the mixed terms of Eq. 10-13 (F*, G*, eta_xyy)."""
     e32 = _standing_period_error(oracle_mod, kd, 32, twod=True)
     e64 = _standing_period_error(oracle_mod, kd, 64, twod=True)
     assert e64 <= 5e-3
     assert e64 <= e32 / 3.0
+
+
+def _moving_standing_mode(oracle_mod, kd, cpl, periods=2.0):
+    """The oblique standing mode of the test above, started a quarter period
+    later: eta = 0 and the discharges (P, Q) = grad phi that continuity
+    (eta_t + P_x + Q_y = 0) gives for eta = a cos(kx x) cos(ky y) cos(omega t),
+    omega from the dispersion relation of Eq. 2 / 7 / 10.  Then
+    eta = -a cos(kx x) cos(ky y) sin(omega t).  Returns the fitted sine and
+    cosine amplitudes of eta at the corner cell, over a (1 and 0 exactly)."""
+    d = 1.0
+    k = kd / d
+    kx = ky = k / math.sqrt(2)
+    dx = 2 * math.pi / kx / cpl
+    X, Y = np.meshgrid((np.arange(cpl) + 0.5) * dx, (np.arange(cpl) + 0.5) * dx)
+    a, om = 1e-4 * d, _omega(k, d)
+    P = a * om * kx / k ** 2 * np.sin(kx * X) * np.cos(ky * Y)
+    Q = a * om * ky / k ** 2 * np.cos(kx * X) * np.sin(ky * Y)
+    z = np.full((cpl, cpl), -d)
+    dt = 0.2 * dx / math.sqrt(G * d)
+    o = oracle_mod.Oracle(z, dx, dx, dt, K=1)
+    o.set_state(0 * z, P, Q)
+    n = int(periods * 2 * math.pi / om / dt) + 2
+    sig = np.empty(n)
+    for s in range(n):
+        o.step(1)
+        sig[s] = o.state()[0][0, 0]
+    t = (np.arange(n) + 1) * dt
+    corner = a * math.cos(kx * 0.5 * dx) * math.cos(ky * 0.5 * dx)
+    A = np.stack([np.sin(om * t), np.cos(om * t)], 1)
+    cs, cc = np.linalg.lstsq(A, sig, rcond=None)[0]
+    return -cs / corner, cc / corner
+
+
+@pytest.mark.parametrize("kd", [1.0, 2.0])
+def test_standing_mode_started_from_its_discharges(oracle_mod, kd):
+    """With discharges at t = 0 the mixed terms F*, G* (Eq. 12-13) are not
+    zero at the start, so the start-up steps' F* and G* increments (Sec. 2.3:
+    none on the first step, F*^1 - F*^0 on the second) and the AM4 weights
+    of w (Eq. 18) all shape the first periods: eta must come back with the
+    amplitude and phase of the linear mode, converging in space."""
+    s32, c32 = _moving_standing_mode(oracle_mod, kd, 32)
+    s64, c64 = _moving_standing_mode(oracle_mod, kd, 64)
+    assert abs(s64 - 1) <= 5e-3
+    assert abs(c64) <= 1e-2
+    assert abs(s64 - 1) <= abs(s32 - 1) / 3.0
 
 
 def test_soliton_speed(oracle_mod):
