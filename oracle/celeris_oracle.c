@@ -518,8 +518,11 @@ static void solve_lines(orc *o, int dir, const orc_real *R, orc_real *X, orc_rea
 }
 
 /* Reading A-D1: AB3 is not positivity preserving, so w is clamped to the
- * bed after each update and P, Q are zeroed where the depth is zero. */
-static void clamp_w(orc *o, orc_real *w)
+ * bed after each update and P, Q are zeroed where the depth is zero.  The
+ * mass the clamp adds is recorded for the last stage only (count = 1): each
+ * corrector starts again from w^n, so what an earlier stage's clamp added
+ * never reaches w^{n+1}. */
+static void clamp_w(orc *o, orc_real *w, int count)
 {
     orc_real added = 0.0;
     for (int j = 0; j < o->ny; j++)
@@ -530,7 +533,7 @@ static void clamp_w(orc *o, orc_real *w)
                 w[c] = o->Bbar[c];
             }
         }
-    o->clamp_mass += added * o->p.dx * o->p.dy;
+    if (count) o->clamp_mass += added * o->p.dx * o->p.dy;
 }
 
 static void dry_zero(orc *o, const orc_real *w, orc_real *P, orc_real *Q)
@@ -641,7 +644,7 @@ int orc_step(orc *o, int nsteps)
                             o->Gsc[c] - o->Gs[0][c];
                     }
             }
-            clamp_w(o, o->w1);
+            clamp_w(o, o->w1, stage == Kn);
             if (bsnq) {
                 solve_lines(o, 0, o->U1, o->P1, t1);
                 solve_lines(o, 1, o->V1, o->Q1, t1);

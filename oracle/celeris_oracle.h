@@ -70,7 +70,7 @@ void orc_get_state(const orc *o, orc_real *w, orc_real *P, orc_real *Q);
 int orc_get_field(const orc *o, int which, orc_real *out);
 void orc_get_time(const orc *o, orc_real *t, long long *step);
 orc_real orc_mass(const orc *o);        /* sum (w - Bbar) dx dy over interior */
-orc_real orc_clamp_mass(const orc *o);  /* mass added by the w >= Bbar clamp */
+orc_real orc_clamp_mass(const orc *o);  /* mass the w >= Bbar clamp added to w^{n+1} */
 int orc_set_gauges(orc *o, const int *ij, int n, int log_every, int capacity);
 int orc_read_gauges(orc *o, orc_real *eta, int max_rec, int *n_rec);
 int orc_num_threads(void);

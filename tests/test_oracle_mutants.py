@@ -134,6 +134,17 @@ MUTANTS = [
      "return 0.5 * (1.0 - cos(ORC_PI * (Ls - D) / Ls));", "test_sponge_gamma"),
     ("thomas_back_sub_sign", "x[i] = dp[i] - cp[i] * x[i + 1];", "x[i] = dp[i] + cp[i] * x[i + 1];",
      "test_thomas_vs_dense"),
+    ("friction_speed_from_P_only", "orc_real mag = sqrt(P[c] * P[c] + Q[c] * Q[c]);", "orc_real mag = fabs(P[c]);",
+     "test_friction_quadratic_oblique_flow"),
+    # dry cells (Reading A-D1) and gauges
+    ("dry_zero_strict", "if (w[c] - o->Bbar[c] <= 0.0) {", "if (w[c] - o->Bbar[c] < 0.0) {",
+     "test_dry_land_holds_no_water_and_no_discharge"),
+    ("clamp_to_zero_level", "                w[c] = o->Bbar[c];\n", "                w[c] = 0.0;\n",
+     "test_dry_land_holds_no_water_and_no_discharge"),
+    ("clamp_mass_every_stage", "if (count) o->clamp_mass +=", "o->clamp_mass +=",
+     "test_dry_land_holds_no_water_and_no_discharge"),
+    ("gauge_records_w", "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)] - o->p.ws;",
+     "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)];", "test_gauges_record_eta_about_the_still_water_level"),
 ]
 
 

@@ -23,12 +23,17 @@ an invariant, a textbook routine, a special case or a convergence order.
   NLSW reduction at d = 0 (Sec. 2.1)      the two models agree       test_boussinesq_reduces_*
   ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
   positivity fix, dry clamp               symmetry with wet-dry fronts test_symmetry_mirror_x_wet_dry
+  dry clamp and dry discharges (A-D1)     w >= bed, P = Q = 0 dry,  test_dry_land_*
+                                          mass less the clamp's
+                                          addition conserved
+  gauges                                  eta about w_s, ring       test_gauges_*, test_gauge_ring
   sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
   soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36)  test_soliton_*
   soliton direction                       transposed runs           test_symmetry_transpose_solitons
   sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
   sine maker on the y-sides               transposed runs           test_symmetry_transpose_sine_*
-  friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders   test_friction_*
+  friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders;  test_friction_*
+                                          oblique uniform flow
   AM4 weights of w, start-up F*, G*       1-D mode with corrector;  test_dispersion_relation_1d_with_*
   increments (Sec. 2.3, Eq. 18)           mode started from its     test_standing_mode_started_*
                                           discharges
@@ -414,6 +419,26 @@ def test_friction_manning_ode(oracle_mod):
     assert P == pytest.approx(ref, rel=1e-5)
 
 
+def test_friction_quadratic_oblique_flow(oracle_mod):
+    """Eq. 31 acts on the discharge vector M = (P, Q) through its length:
+    M' = -f M |M| / h^2 on a uniform flow, so the direction of M stays put
+    and |M| follows the 1-D solution |M0| / (1 + f |M0| t / h^2), less the
+    forward-Euler start-up term of the test above."""
+    f, h, T, dt = 0.5, 1.0, 2.0, 0.004
+    P0, Q0 = 0.4, 0.3
+    M0, a = math.hypot(P0, Q0), f / h ** 2
+    nx, ny, dx = 200, 200, 0.1
+    z = np.full((ny, nx), -h)
+    o = oracle_mod.Oracle(z, dx, dx, dt, model=oracle_mod.NLSW, friction=1, fcoef=f)
+    o.set_state(0 * z, P0 + 0 * z, Q0 + 0 * z)
+    o.step(int(round(T / dt)))
+    _, P, Q = o.state()
+    p, q = P[ny // 2, nx // 2], Q[ny // 2, nx // 2]
+    assert q / p == pytest.approx(Q0 / P0, rel=1e-12)
+    startup = -2 * a * a * M0 ** 3 * dt * dt / (1 + a * M0 * T) ** 2
+    assert math.hypot(p, q) - M0 / (1 + a * M0 * T) == pytest.approx(startup, rel=0.05)
+
+
 # ------------------------------------------------------------ sine maker
 
 def _sine_channel(oracle_mod, courant, d=1.0, a=0.005, T=4.0, dx=0.1, ny=2):
@@ -737,6 +762,56 @@ def test_gauge_ring(oracle_mod):
             etas.append([w[5, 10], w[16, 200]])
     np.testing.assert_array_equal(rec, np.array(etas[-4:]))
     assert o.read_gauges(10).shape == (0, 2)
+
+
+def test_gauges_record_eta_about_the_still_water_level(oracle_mod):
+    """Gauges record the free surface's elevation eta = w - w_s (Sec. 2.1's
+    eta over the still-water level): still water at w_s = 0.3 m over a
+    random bed records zero at every gauge, and a raised lake records its
+    rise."""
+    nx, ny = 40, 30
+    rng = np.random.default_rng(5)
+    z = -1.0 - 0.5 * rng.random((ny, nx))
+    for rise in (0.0, 0.02):
+        o = oracle_mod.Oracle(z, 1.0, 1.0, 0.05, K=1, ws=0.3)
+        o.set_state(np.full_like(z, 0.3 + rise), 0 * z, 0 * z)
+        o.set_gauges([(3, 4), (20, 15), (37, 27)], log_every=1, capacity=8)
+        o.step(5)
+        rec = o.read_gauges(8)
+        assert rec.shape == (5, 3)
+        np.testing.assert_allclose(rec, rise, rtol=0, atol=1e-12)
+
+
+def test_dry_land_holds_no_water_and_no_discharge(oracle_mod):
+    """A 0.2 m hump of water runs up a steep planar beach (1:2) and back
+    (Boussinesq, K = 1), far enough that the dry clamp of Reading A-D1 has
+    to act.  Checked every 50 steps: the surface never lies below the bed;
+    wherever the depth is zero the discharges are zero; and the flux form
+    conserves mass (Eq. 1, walls all round), so the mass changes by exactly
+    what the clamp reports it added.  Land the wave never reaches keeps w
+    equal to its bed, which on a plane is the input z away from the mirrored
+    edge cells and the beach's toe."""
+    nx, ny, dx = 160, 4, 0.05
+    x = (np.arange(nx) + 0.5) * dx
+    z = np.tile(-0.4 + 0.5 * np.maximum(x - 2.5, 0.0), (ny, 1))     # shoreline at x = 3.3 m
+    eta = 0.2 * np.exp(-((x - 1.5) / 0.3) ** 2)
+    o = oracle_mod.Oracle(z, dx, dx, 0.2 * dx / math.sqrt(G * 0.6), K=1)
+    o.set_state(np.tile(eta, (ny, 1)), 0 * z, 0 * z)     # land: w clamped up to its bed
+    Bbar = o.field("Bbar")
+    plane = (np.abs(x - 2.5) > 2 * dx) & (np.arange(nx) > 0) & (np.arange(nx) < nx - 1)
+    np.testing.assert_allclose(Bbar[:, plane], z[:, plane], rtol=0, atol=1e-14)
+    m0 = o.mass()
+    for _ in range(20):
+        o.step(50)
+        w, P, Q = o.state()
+        assert np.all(w >= Bbar)
+        dry = w - Bbar <= 0.0
+        assert dry.any()
+        assert np.all(P[dry] == 0.0) and np.all(Q[dry] == 0.0)
+        assert o.mass() - o.clamp_mass() == pytest.approx(m0, rel=1e-12)
+    assert o.clamp_mass() > 0.0                  # the clamp acted
+    far = plane & (x > 5.5)
+    np.testing.assert_allclose(w[:, far], z[:, far], rtol=0, atol=1e-14)
 
 
 def test_runup_tracking_standing_mode(oracle_mod):
