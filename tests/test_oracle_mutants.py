@@ -143,6 +143,9 @@ MUTANTS = [
      "test_dry_land_holds_no_water_and_no_discharge"),
     ("clamp_mass_every_stage", "if (count) o->clamp_mass +=", "o->clamp_mass +=",
      "test_dry_land_holds_no_water_and_no_discharge"),
+    ("sponge_relaxes_land", "if (o->d[c] > 0.0) o->w1[c] = o->p.ws + gam * (o->w1[c] - o->p.ws);",
+     "o->w1[c] = o->p.ws + gam * (o->w1[c] - o->p.ws);", "test_sponge_leaves_dry_land_at_its_bed"),
+    ("soliton_sech_not_sech2", "orc_real es = H * sh * sh;", "orc_real es = H * sh;", "test_soliton_speed"),
     ("gauge_records_w", "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)] - o->p.ws;",
      "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)];", "test_gauges_record_eta_about_the_still_water_level"),
 ]

@@ -28,7 +28,9 @@ an invariant, a textbook routine, a special case or a convergence order.
                                           addition conserved
   gauges                                  eta about w_s, ring       test_gauges_*, test_gauge_ring
   sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
-  soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36)  test_soliton_*
+  sponge on dry land                      land stays on its bed     test_sponge_leaves_dry_land_*
+  soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36), test_soliton_*
+                                          the profile's volume
   soliton direction                       transposed runs           test_symmetry_transpose_solitons
   sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
   sine maker on the y-sides               transposed runs           test_symmetry_transpose_sine_*
@@ -189,6 +191,25 @@ def test_lake_at_rest_with_sponges_off_zero_level(oracle_mod):
     w, P, Q = o.state()
     assert np.max(np.abs(w - ws)) <= 1e-13
     assert np.max(np.abs(P)) <= 1e-12 and np.max(np.abs(Q)) <= 1e-12
+
+
+def test_sponge_leaves_dry_land_at_its_bed(oracle_mod):
+    """Eq. 30 damps the free surface towards the still-water level w_s; land
+    above w_s inside the layer holds no water, so its surface stays on its
+    bed (a relaxation of w there would pull it 0.2 m below the bed).  A lake
+    against a cliff to land 0.2 m above w_s, the land inside an east sponge."""
+    nx, ny = 60, 8
+    z = np.full((ny, nx), -0.5)
+    z[:, 50:] = 0.2
+    o = oracle_mod.Oracle(z, 0.1, 0.1, 0.01, K=1)
+    o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, 15)
+    o.set_state(0 * z, 0 * z, 0 * z)
+    o.step(50)
+    w, P, Q = o.state()
+    Bbar = o.field("Bbar")
+    assert np.all(w >= Bbar)
+    np.testing.assert_array_equal(w[:, 51:], Bbar[:, 51:])
+    assert np.all(P[:, 51:] == 0.0) and np.all(Q[:, 51:] == 0.0)
 
 
 @pytest.mark.parametrize("K", [0, 2])
@@ -377,6 +398,13 @@ def test_soliton_speed(oracle_mod):
     c = (xb - xa) / ((n2 - n1) * dt)
     assert abs(c / math.sqrt(G * (H + d)) - 1) <= 0.03
     assert hb >= 0.95 * H
+    # the volume of Eq. 33's sech^2 profile over the channel, per unit crest
+    # length: the integral of H sech^2(k (x - x0)) from 0 to L (the flux form
+    # keeps it while the wave travels)
+    k = math.sqrt(3 * H / (4 * d ** 3))
+    vol = o.state()[0][0].sum() * dx
+    exact = H / k * (math.tanh(k * (nx * dx - 15.0)) + math.tanh(k * 15.0))
+    assert vol == pytest.approx(exact, rel=1e-4)
 
 
 def _uniform_friction_error(oracle_mod, dt, f=0.5, P0=0.5, h=1.0, T=2.0, kind=1):
