@@ -2,7 +2,7 @@
 // start-up and the AM4 corrector stages (Eq. 15-20, Sec. 2.3) -- for the
 // Boussinesq model and the nonlinear shallow-water model (Sec. 3.2), and the
 // gradient of a gauge misfit.  The reverse of one stage, given the adjoint
-// lambda of the state after it (the driver in celeris_api.cu orders the
+// lambda of the state after it (the host code in celeris_api.cu orders the
 // stages, the checkpoints and the recomputation):
 //   1. the masks of the update: the dry clamp w >= Bbar (Reading A-D1), the
 //      sponge (Eq. 30), the zero discharge of dry cells;

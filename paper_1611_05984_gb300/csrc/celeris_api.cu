@@ -1082,8 +1082,8 @@ struct NoallocSlot {
 NoallocSlot g_noalloc_slot[kMaxDevices];
 std::mutex g_noalloc_mutex;
 
-// The driver's context queries, fetched through the runtime (the library
-// links no libcuda of its own).
+// The CUDA driver API's context queries, fetched through the runtime (the
+// library links no libcuda of its own).
 typedef int (*CtxGetCurrentFn)(void **ctx);
 typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
 
@@ -1101,7 +1101,7 @@ bool current_context_id(unsigned long long *id, std::string *why)
         cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
         if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
             q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
-            *why = "the driver's context queries (cuCtxGetCurrent, cuCtxGetId) are unavailable";
+            *why = "the CUDA driver API's context queries (cuCtxGetCurrent, cuCtxGetId) are unavailable";
             return false;
         }
         get_current = (CtxGetCurrentFn)f1;
