@@ -189,6 +189,46 @@ def test_pin_scenarios(prec, case):
         assert o.clamp_mass() > 0.0          # the dry clamp acted on this run
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_still_water_level_off_zero(prec):
+    """Still water at w_s = 0.3 m (Sec. 2.1) over a random bed that rises to
+    land above w_s: the depth d = max(w_s - Bbar, 0), the sine maker's ghost
+    level w_s + eta (Eq. 25), the sponge's relaxation towards w_s (Eq. 30)
+    and the gauges' eta = w - w_s all take w_s.  State and gauge records
+    against the oracle."""
+    nx, ny, dx, ws = 101, 45, 0.1, 0.3
+    x = (np.arange(nx) + 0.5) * dx
+    s = sc.flat_basin(nx, ny, dx, 0.5, 0.1 * dx / math.sqrt(9.81 * 0.8), K=1, ws=ws)
+    s.z = sc.random_bed(nx, ny, 11, -0.6, -0.3, smooth=3) + np.maximum(x - 6.0, 0.0) * 0.5 + ws
+    s.sides[sc.W] = sc.Side(sc.SINE, 0, ((0.01, 1.5, 0.2, 0.0),))
+    s.sides[sc.S] = sc.Side(sc.SPONGE, 8)
+    ij = [(5, 10), (20, 22), (35, 30), (50, 40)]         # all in the water (land from x = 6 m)
+    o = oracle_from(s)
+    g = _solver(s, prec)
+    o.set_gauges(ij, 10, 80)
+    g.set_gauges(ij, 10, 80)
+    for _ in range(8):
+        o.step(100)
+        g.step(100)
+        wo, Po, Qo = o.state()
+        wg, Pg, Qg = (_np(a) for a in g.state())
+        assert rel_l2(wg - ws, wo - ws) <= TOL[prec]
+        assert rel_l2(Pg, Po) <= 10 * TOL[prec] and rel_l2(Qg, Qo) <= 10 * TOL[prec]
+    ro, rg = o.read_gauges(80), g.read_gauges(80)
+    assert rg.shape == ro.shape == (80, 4)
+    assert np.abs(ro).max() > 1e-3                      # the maker's wave reached the gauges
+    # the last record is the present state's eta at the gauge cells: w less
+    # w_s as the solver's precision holds it (float32(0.3) in FP32; the
+    # difference of two numbers this close is exact)
+    real = np.float64 if prec == "f64" else np.float32
+    cells = np.array([wg[j, i] for i, j in ij]).astype(real)
+    np.testing.assert_array_equal(rg[-1].astype(real), cells - real(ws))
+    # FP32 carries w = w_s + eta, so at w_s = 0.3 m each record holds eta
+    # only to ulp(0.3) = 3e-8 and the drift of the state: measured 1.06e-4
+    # over these 80 records, where the 4-cell sample weighs every record alike
+    assert rel_l2(rg, ro) <= (TOL[prec] if prec == "f64" else 2e-4)
+
+
 def test_dispersive_2d_mode_fp64():
     """Oblique standing mode on a flat bed: exercises F*, G*, eta_xyy."""
     n, d = 48, 1.0
