@@ -145,3 +145,32 @@ def test_line_split_table():
     finally:
         celeris.reset_line_splits()
     assert celeris.line_config(4, 200) == (8, 32)
+
+
+def test_launch_switch_and_queued_reads_without_gpu_work():
+    """The dependent-launch switch (on by default) reads back what was set;
+    the queued gauge read and the persistent ensemble's calls refuse NULL
+    handles and out-pointers before any CUDA call, leaving the outputs
+    untouched."""
+    L = celeris.load()
+    v = ctypes.c_int32(-1)
+    assert L.cel_get_dependent_launch(ctypes.byref(v)) == 0
+    old = v.value
+    assert old in (0, 1)
+    try:
+        for want in (0, 1, 0):
+            assert L.cel_set_dependent_launch(want) == 0
+            assert L.cel_get_dependent_launch(ctypes.byref(v)) == 0 and v.value == want
+        assert L.cel_set_dependent_launch(5) == 0                   # any non-zero value turns it on
+        assert L.cel_get_dependent_launch(ctypes.byref(v)) == 0 and v.value == 1
+    finally:
+        L.cel_set_dependent_launch(old)
+    assert L.cel_get_dependent_launch(None) == 1
+    n = ctypes.c_int32(7)
+    assert L.cel_read_gauges_async(None, None, 0, ctypes.byref(n)) == 1 and n.value == 7
+    assert L.cel_ensemble_use_persistent(None, 1, 100.0) == 1
+    steps = ctypes.c_int64(5)
+    assert L.cel_ensemble_persistent_steps(None, ctypes.byref(steps)) == 1 and steps.value == 5
+    assert L.cel_ensemble_check(None) == 1
+    t = ctypes.c_int32(3)
+    assert L.cel_ensemble_barrier_check(None, 0, 10.0, ctypes.byref(t)) == 1 and t.value == 3
