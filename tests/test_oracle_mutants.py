@@ -146,6 +146,14 @@ MUTANTS = [
     ("sponge_relaxes_land", "if (o->d[c] > 0.0) o->w1[c] = o->p.ws + gam * (o->w1[c] - o->p.ws);",
      "o->w1[c] = o->p.ws + gam * (o->w1[c] - o->p.ws);", "test_sponge_leaves_dry_land_at_its_bed"),
     ("soliton_sech_not_sech2", "orc_real es = H * sh * sh;", "orc_real es = H * sh;", "test_soliton_speed"),
+    ("east_maker_depth_cell", "orc_real dadj = o->d[IX(o, side == ORC_W ? 0 : nx - 1, j)];",
+     "orc_real dadj = o->d[IX(o, side == ORC_W ? 0 : nx + 1, j)];", "test_symmetry_mirror_sine_makers"),
+    ("north_maker_depth_cell", "orc_real dadj = o->d[IX(o, ic, side == ORC_S ? 0 : ny - 1)];",
+     "orc_real dadj = o->d[IX(o, ic, side == ORC_S ? 0 : ny + 1)];", "test_symmetry_mirror_sine_makers"),
+    ("west_sponge_width_in_cells_over_dx", "L = bc->width * o->p.dx; }", "L = bc->width / o->p.dx; }",
+     "test_sponge_profile_in_metres"),
+    ("west_sponge_distance_over_dx", "if (s == ORC_W) { D = (i + 0.5) * o->p.dx;", "if (s == ORC_W) { D = (i + 0.5) / o->p.dx;",
+     "test_symmetry_transpose_with_sponges"),
     ("gauge_records_w", "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)] - o->p.ws;",
      "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)];", "test_gauges_record_eta_about_the_still_water_level"),
 ]

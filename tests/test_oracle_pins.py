@@ -29,6 +29,8 @@ an invariant, a textbook routine, a special case or a convergence order.
   gauges                                  eta about w_s, ring       test_gauges_*, test_gauge_ring
   sponge relaxation to w_s                still water stays still   test_lake_at_rest_with_sponges_*
   sponge on dry land                      land stays on its bed     test_sponge_leaves_dry_land_*
+  sponge distances and widths in metres   one step of a raised lake test_sponge_profile_in_metres
+  east and north makers                   mirrored runs             test_symmetry_mirror_sine_makers
   soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36), test_soliton_*
                                           the profile's volume
   soliton direction                       transposed runs           test_symmetry_transpose_solitons
@@ -643,7 +645,7 @@ def test_symmetry_transpose_with_sponges(oracle_mod):
     X, Y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
     eta = 0.1 * np.exp(-((X - 14) ** 2 + (Y - 32) ** 2) / 20.0)
     eta = eta + eta.T
-    o = oracle_mod.Oracle(z, 1.0, 1.0, 0.1 / math.sqrt(G * 3.0), K=1)
+    o = oracle_mod.Oracle(z, 0.5, 0.5, 0.05 / math.sqrt(G * 3.0), K=1)
     for side in (oracle_mod.W, oracle_mod.E, oracle_mod.S, oracle_mod.N):
         o.set_boundary(side, oracle_mod.SPONGE, 8)
     o.set_state(eta, 0 * z, 0 * z)
@@ -651,6 +653,73 @@ def test_symmetry_transpose_with_sponges(oracle_mod):
     w, P, Q = o.state()
     assert np.max(np.abs(w - w.T)) <= 1e-12 * np.max(np.abs(w))
     assert np.max(np.abs(P - Q.T)) <= 1e-12 * np.max(np.abs(P))
+
+
+def test_sponge_profile_in_metres(oracle_mod):
+    """Eq. 30 on every side, in metres: a lake raised by eps over a flat bed
+    is at rest (no flux), so one step leaves w - w_s = eps gamma(D) exactly,
+    with D the distance from the side's face to the cell centre and the
+    layer width L = cells x spacing of that direction (dx != dy), the
+    smallest gamma where layers overlap."""
+    nx, ny, dx, dy, eps = 40, 30, 0.5, 0.25, 1e-3
+    widths = {oracle_mod.W: 6, oracle_mod.E: 9, oracle_mod.S: 5, oracle_mod.N: 7}
+    z = np.full((ny, nx), -1.0)
+    o = oracle_mod.Oracle(z, dx, dy, 0.01, K=1)
+    for side, wd in widths.items():
+        o.set_boundary(side, oracle_mod.SPONGE, wd)
+    o.set_state(np.full_like(z, eps), 0 * z, 0 * z)
+    o.step(1)
+    w = o.state()[0]
+    xc, yc = (np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dy
+    gam = np.ones((ny, nx))
+    for side, wd in widths.items():
+        if side in (oracle_mod.W, oracle_mod.E):
+            D, L = (xc if side == oracle_mod.W else nx * dx - xc), wd * dx
+            g = np.array([oracle_mod.sponge_gamma(v, L) for v in D])[None, :]
+        else:
+            D, L = (yc if side == oracle_mod.S else ny * dy - yc), wd * dy
+            g = np.array([oracle_mod.sponge_gamma(v, L) for v in D])[:, None]
+        gam = np.minimum(gam, g)
+    np.testing.assert_allclose(w, eps * gam, rtol=1e-12, atol=1e-18)
+    assert (gam < 1).sum() > 0 and (gam == 1).sum() > 0
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_symmetry_mirror_sine_makers(oracle_mod, axis):
+    """A west maker (direction 0) over a bed that varies along x, and an east
+    maker (direction pi) over the mirrored bed, give mirrored runs (Eq.
+    25-29): the east maker takes its depth, hence k (Eq. 29), from the cell
+    beside it and its ghosts at their own x; its phase is set back by k L
+    so that both makers send the same wave.  axis "y": the same with south
+    and north makers over a bed that varies along y."""
+    n, m, dx = 72, 6, 0.5
+    s = np.arange(n)
+    bed = -2.0 + 0.8 * np.exp(-((s - 60) / 8.0) ** 2) + 0.2 * np.cos(s / 5.0)
+    a, T, phi = 0.01, 3.0, 0.4
+    om = 2 * math.pi / T
+
+    def run(far):
+        z1 = bed[::-1] if far else bed
+        z = np.tile(z1, (m, 1)) if axis == "x" else np.tile(z1[:, None], (1, m))
+        o = oracle_mod.Oracle(z, dx, dx, 0.1 * dx / math.sqrt(G * 2.0), K=1)
+        near_side, far_side = (oracle_mod.W, oracle_mod.E) if axis == "x" else (oracle_mod.S, oracle_mod.N)
+        d = o.field("d")
+        dadj = (d[0, -1] if axis == "x" else d[-1, 0]) if far else d[0, 0]     # the cell beside the maker
+        k = oracle_mod.eckart_k(om, dadj, G)
+        base = 0.0 if axis == "x" else math.pi / 2
+        comp = (a, T, base + math.pi, phi - k * n * dx) if far else (a, T, base, phi)
+        o.set_boundary(far_side if far else near_side, oracle_mod.SINE, 0, (comp,))
+        o.set_state(0 * z, 0 * z, 0 * z)
+        o.step(300)
+        return o.state()
+
+    wa, Pa, Qa = run(False)
+    wb, Pb, Qb = run(True)
+    flip = (lambda v: v[:, ::-1]) if axis == "x" else (lambda v: v[::-1, :])
+    Na, Nb = (Pa, Pb) if axis == "x" else (Qa, Qb)
+    assert np.max(np.abs(wa)) > 1e-3
+    assert np.max(np.abs(wa - flip(wb))) <= 1e-10 * np.max(np.abs(wa))
+    assert np.max(np.abs(Na + flip(Nb))) <= 1e-10 * np.max(np.abs(Na))
 
 
 def test_symmetry_transpose_sine_makers(oracle_mod):
