@@ -194,6 +194,32 @@ RENDER_MUTANTS = [
      "test_speed_and_velocity_components"),
     ("hillshade_unclamped", "float shade = 0.35f + 0.65f * (d > 0.0f ? d : 0.0f);", "float shade = 0.35f + 0.65f * d;",
      "test_flat_land_hillshade"),
+    ("north_neighbour_index", "jn = j < ny - 1 ? j + 1 : j;", "jn = j < ny - 1 ? j - 1 : j;",
+     "test_tilted_plane_both_directions_grazing_view"),
+    ("y_span_over_dy", "spany = (float)(jn - js) * dy;", "spany = (float)(jn - js) / dy;",
+     "test_tilted_plane_both_directions_grazing_view"),
+    ("west_neighbour_eta_sign", "float eW = AT(w, iw, j) - AT(Bbar, iw, j) > p->dry_h ? AT(w, iw, j) - ws : ec;",
+     "float eW = AT(w, iw, j) - AT(Bbar, iw, j) > p->dry_h ? AT(w, iw, j) + ws : ec;",
+     "test_tilted_plane_both_directions_grazing_view"),
+    ("dry_neighbour_level", "const float ec = wc - ws;", "const float ec = wc + ws;", "test_lake_shore_is_level"),
+    ("incidence_dot_sign", "float idn = I[0] * n[0] + I[1] * n[1] + I[2] * n[2];",
+     "float idn = I[0] * n[0] - I[1] * n[1] + I[2] * n[2];", "test_tilted_plane_both_directions_grazing_view"),
+    ("reflected_height", "float rz = I[2] - 2.0f * idn * n[2];", "float rz = I[2] - 2.0f * idn / n[2];",
+     "test_tilted_plane_both_directions_grazing_view"),
+    ("normalise_y", "    v[1] = v[1] / n;\n", "    v[1] = v[1] * n;\n", "test_tilted_plane_both_directions_grazing_view"),
+    ("value_range", "return (v - lo) / (hi - lo);", "return (v - lo) / (hi + lo);", "test_colormap_range_of_the_value"),
+    ("colormap_quarters", "float s = t * 4.0f;", "float s = t / 4.0f;", "test_colormap_control_points_and_linearity"),
+    ("grid_rows_off_by_one", "int ly = floorf((float)(j + 1) * dy / p->grid)", "int ly = floorf((float)(j - 1) * dy / p->grid)",
+     "test_grid_lines"),
+    ("hillshade_y_term", "float d = nb[0] * L[0] + nb[1] * L[1] + nb[2] * L[2];",
+     "float d = nb[0] * L[0] - nb[1] * L[1] + nb[2] * L[2];", "test_hillshade_of_a_plane_in_both_directions"),
+    ("dry_threshold_inclusive", "const int wet = h > p->dry_h;", "const int wet = h >= p->dry_h;",
+     "test_depth_equal_to_dry_h_is_land"),
+    ("east_neighbour_threshold", "float eE = AT(w, ie, j) - AT(Bbar, ie, j) > p->dry_h",
+     "float eE = AT(w, ie, j) - AT(Bbar, ie, j) >= p->dry_h", "test_depth_equal_to_dry_h_is_land"),
+    ("land_span_guard", "float gx = spanx > 0.0f ? (AT(Bbar, ie, j) - AT(Bbar, iw, j)) / spanx : 0.0f;",
+     "float gx = spanx >= 0.0f ? (AT(Bbar, ie, j) - AT(Bbar, iw, j)) / spanx : 0.0f;",
+     "test_one_cell_wide_strips_see_a_level_surface"),
 ]
 
 
