@@ -45,13 +45,6 @@ struct orc_dual {
         v *= b.v;
         return *this;
     }
-    orc_dual &operator/=(orc_dual b)
-    {
-        const double q = v / b.v;
-        d = (d - q * b.d) / b.v;
-        v = q;
-        return *this;
-    }
 };
 
 static inline orc_dual operator+(orc_dual a, orc_dual b) { return {a.v + b.v, a.d + b.d}; }

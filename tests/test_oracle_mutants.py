@@ -252,6 +252,9 @@ TLM_MUTANTS = [
     ("cbrt_rule", "return {c, c != 0.0 ? a.d / (3.0 * c * c) : 0.0};", "return {c, c != 0.0 ? a.d / (3.0 * c) : 0.0};"),
     ("tanh_rule", "return {t, (1.0 - t * t) * a.d};", "return {t, (1.0 + t * t) * a.d};"),
     ("sin_rule", "return {::sin(a.v), ::cos(a.v) * a.d};", "return {::sin(a.v), -::cos(a.v) * a.d};"),
+    ("difference_rule", "static inline orc_dual operator-(orc_dual a, orc_dual b) { return {a.v - b.v, a.d - b.d}; }",
+     "static inline orc_dual operator-(orc_dual a, orc_dual b) { return {a.v - b.v, a.d + b.d}; }"),
+    ("scaling_in_place", "        d = d * b.v + v * b.d;\n", "        d = d + v * b.d;\n"),
 ]
 
 
