@@ -134,6 +134,8 @@ MUTANTS = [
      "return 0.5 * (1.0 - cos(ORC_PI * (Ls - D) / Ls));", "test_sponge_gamma"),
     ("thomas_back_sub_sign", "x[i] = dp[i] - cp[i] * x[i + 1];", "x[i] = dp[i] + cp[i] * x[i + 1];",
      "test_thomas_vs_dense"),
+    ("friction_y_without_depth", "gg -= fc * Q[c] * mag * hinv * hinv;", "gg -= fc * Q[c] * mag * hinv / hinv;",
+     "test_friction_quadratic_oblique_flow"),
     ("friction_speed_from_P_only", "orc_real mag = sqrt(P[c] * P[c] + Q[c] * Q[c]);", "orc_real mag = fabs(P[c]);",
      "test_friction_quadratic_oblique_flow"),
     # dry cells (Reading A-D1) and gauges

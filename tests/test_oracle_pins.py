@@ -453,8 +453,9 @@ def test_friction_quadratic_oblique_flow(oracle_mod):
     """Eq. 31 acts on the discharge vector M = (P, Q) through its length:
     M' = -f M |M| / h^2 on a uniform flow, so the direction of M stays put
     and |M| follows the 1-D solution |M0| / (1 + f |M0| t / h^2), less the
-    forward-Euler start-up term of the test above."""
-    f, h, T, dt = 0.5, 1.0, 2.0, 0.004
+    forward-Euler start-up term of the test above (h = 0.6 m, so the
+    1/h^2 of Eq. 31 shows in both components)."""
+    f, h, T, dt = 0.5, 0.6, 2.0, 0.004
     P0, Q0 = 0.4, 0.3
     M0, a = math.hypot(P0, Q0), f / h ** 2
     nx, ny, dx = 200, 200, 0.1
