@@ -83,6 +83,8 @@ MUTANTS = [
      "coef23(o->p.Bd, o->p.dy, o->d[c], o->ddx[c], &a, &b, &cc);", "test_lake_at_rest_submerged"),
     ("runup_keeps_last", "else if (wet && o->w[c] > o->maxw[k]) o->maxw[k] = o->w[c];",
      "else if (wet) o->maxw[k] = o->w[c];", "test_runup_tracking_standing_mode"),
+    ("runup_threshold_inclusive", "int wet = o->w[c] - o->Bbar[c] > o->delta;", "int wet = o->w[c] - o->Bbar[c] >= o->delta;",
+     "test_runup_tracking_threshold_and_dry_land"),
     ("runup_no_threshold", "int wet = o->w[c] - o->Bbar[c] > o->delta;", "int wet = 1;",
      "test_runup_tracking_threshold_and_dry_land"),
     # depth-gradient terms that vanish in 1-D (F*, G* of Eq. 12-13; the

@@ -941,7 +941,8 @@ def test_runup_tracking_standing_mode(oracle_mod):
 
 def test_runup_tracking_threshold_and_dry_land(oracle_mod):
     """Cells never deeper than the threshold keep -inf: dry land behind a
-    lake, and the whole lake once the threshold exceeds its depth."""
+    lake, the whole lake once the threshold exceeds its depth, and a lake
+    exactly as deep as the threshold."""
     z = np.full((4, 12), -0.05)
     z[:, 8:] = 0.4
     o = oracle_mod.Oracle(z, 1.0, 1.0, 0.01)
@@ -955,6 +956,16 @@ def test_runup_tracking_threshold_and_dry_land(oracle_mod):
     o.runup_enable(0.06)
     o.step(2)
     assert np.all(np.isneginf(o.runup()))
+    # the threshold is strict: a lake exactly delta deep (a power of two, so
+    # w - Bbar = delta exactly, and exactly at rest) never exceeded it
+    zf = np.full((4, 12), -0.0625)
+    of = oracle_mod.Oracle(zf, 1.0, 1.0, 0.01)
+    of.runup_enable(0.0625)
+    of.step(3)
+    assert np.all(np.isneginf(of.runup()))
+    of.runup_enable(0.0624)
+    of.step(1)
+    np.testing.assert_array_equal(of.runup(), 0.0)
 
 
 def _uniform_flow_states(oracle_mod, K, nsteps, dt=0.01, f=0.5, P0=0.5):
