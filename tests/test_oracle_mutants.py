@@ -158,6 +158,13 @@ MUTANTS = [
      "test_sponge_profile_in_metres"),
     ("west_sponge_distance_over_dx", "if (s == ORC_W) { D = (i + 0.5) * o->p.dx;", "if (s == ORC_W) { D = (i + 0.5) / o->p.dx;",
      "test_symmetry_transpose_with_sponges"),
+    ("y_face_low_bed_of_south_cell", "recon_cell(th, w, P, Q, IX(o, i, gq - 1), ex, By(o, i, gq - 1), By(o, i, gq), loS, hiS);",
+     "recon_cell(th, w, P, Q, IX(o, i, gq - 1), ex, By(o, i, gq + 1), By(o, i, gq), loS, hiS);",
+     "test_symmetry_transpose_wet_dry"),
+    ("y_face_high_bed_of_north_cell", "recon_cell(th, w, P, Q, IX(o, i, gq), ex, By(o, i, gq), By(o, i, gq + 1), loN, hiN);",
+     "recon_cell(th, w, P, Q, IX(o, i, gq), ex, By(o, i, gq), By(o, i, gq - 1), loN, hiN);",
+     "test_symmetry_transpose_wet_dry"),
+    ("maker_beside_dry_cell", "if (!(dadj > 0.0)) return;", "if (!(dadj >= 0.0)) return;", "test_sine_maker_beside_dry_land"),
     ("gauge_records_w", "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)] - o->p.ws;",
      "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)];", "test_gauges_record_eta_about_the_still_water_level"),
 ]

@@ -23,6 +23,8 @@ an invariant, a textbook routine, a special case or a convergence order.
   NLSW reduction at d = 0 (Sec. 2.1)      the two models agree       test_boussinesq_reduces_*
   ghosts, x/y treatment                   mirror / transpose symmetry test_symmetry_*
   positivity fix, dry clamp               symmetry with wet-dry fronts test_symmetry_mirror_x_wet_dry
+  positivity fix on the y-faces           the wet-dry basin along y  test_symmetry_transpose_wet_dry
+  maker beside dry land (d = 0)           sends nothing, stays dry  test_sine_maker_beside_dry_land
   dry clamp and dry discharges (A-D1)     w >= bed, P = Q = 0 dry,  test_dry_land_*
                                           mass less the clamp's
                                           addition conserved
@@ -636,6 +638,34 @@ def test_symmetry_mirror_x_wet_dry(oracle_mod):
     assert np.max(np.abs(P)) > 0
 
 
+def test_symmetry_transpose_wet_dry(oracle_mod):
+    """The basin of the test above with its hump off centre, run along x and
+    along y: the shoreline climbs the slopes through both branches of the
+    positivity fix on the y-faces as on the x-faces, and the two runs are
+    transposes of each other (w, and P against Q)."""
+    n, m, dx = 120, 2, 0.05
+    x = (np.arange(n) + 0.5) * dx
+    xc = n * dx / 2
+    z1 = -0.5 + 0.8 * ((x - xc) / xc) ** 2
+    eta1 = 0.08 * np.exp(-((x - 0.8 * xc) / 0.4) ** 2)
+
+    def run(along_x):
+        z = np.tile(z1, (m, 1)) if along_x else np.tile(z1[:, None], (1, m))
+        eta = np.tile(eta1, (m, 1)) if along_x else np.tile(eta1[:, None], (1, m))
+        o = oracle_mod.Oracle(z, dx, dx, 0.1 * dx / math.sqrt(G * 0.5), model=oracle_mod.NLSW, K=1, eps=1e-8)
+        o.set_state(np.maximum(eta, z), 0 * z, 0 * z)
+        o.step(800)
+        return o.state(), z
+
+    (wa, Pa, Qa), za = run(True)
+    (wb, Pb, Qb), _ = run(False)
+    wet = wa - za > 1e-6
+    assert np.any(~wet[0, :10]) and np.any(wet[0, 10:40]) and np.any(~wet[0, -10:])
+    assert np.max(np.abs(wa - wb.T)) <= 1e-12
+    assert np.max(np.abs(Pa - Qb.T)) <= 1e-12 * np.max(np.abs(Pa))
+    assert np.max(np.abs(Pa)) > 0 and np.all(Qa == 0.0) and np.all(Pb == 0.0)
+
+
 def test_symmetry_transpose_with_sponges(oracle_mod):
     """The transpose symmetry with sponges on all four sides (Eq. 30): each
     damps w, P and Q alike, so the run stays symmetric under x <-> y with
@@ -721,6 +751,28 @@ def test_symmetry_mirror_sine_makers(oracle_mod, axis):
     assert np.max(np.abs(wa)) > 1e-3
     assert np.max(np.abs(wa - flip(wb))) <= 1e-10 * np.max(np.abs(wa))
     assert np.max(np.abs(Na + flip(Nb))) <= 1e-10 * np.max(np.abs(Na))
+
+
+def test_sine_maker_beside_dry_land(oracle_mod):
+    """Eq. 25-29 take the still-water depth of the cell beside the maker; in
+    rows where that cell is land (d = 0) there is no depth to set k from and
+    the maker sends nothing: its ghosts hold still water.  A west maker along
+    a coast whose upper rows start on land 0.3 m above w_s: the run stays
+    finite and the land there stays dry, with no discharge."""
+    nx, ny, dx = 40, 16, 0.1
+    z = np.full((ny, nx), -0.5)
+    z[10:, :5] = 0.3
+    o = oracle_mod.Oracle(z, dx, dx, 0.1 * dx / math.sqrt(G * 0.5), K=1)
+    o.set_boundary(oracle_mod.W, oracle_mod.SINE, 0, ((0.01, 1.0, 0.0, 0.0),))
+    o.set_boundary(oracle_mod.E, oracle_mod.SPONGE, 10)
+    o.set_state(0 * z, 0 * z, 0 * z)
+    assert np.all(o.field("d")[10:, 0] == 0.0) and np.all(o.field("d")[:10, 0] > 0.0)
+    o.step(300)
+    w, P, Q = o.state()
+    Bbar = o.field("Bbar")
+    assert np.all(np.isfinite(w)) and np.max(np.abs(w[:10, :10])) > 1e-3     # the wave went in below
+    np.testing.assert_array_equal(w[11:, :4], Bbar[11:, :4])
+    assert np.all(P[11:, :4] == 0.0) and np.all(Q[11:, :4] == 0.0)
 
 
 def test_symmetry_transpose_sine_makers(oracle_mod):
