@@ -165,6 +165,15 @@ MUTANTS = [
      "recon_cell(th, w, P, Q, IX(o, i, gq), ex, By(o, i, gq), By(o, i, gq - 1), loN, hiN);",
      "test_symmetry_transpose_wet_dry"),
     ("maker_beside_dry_cell", "if (!(dadj > 0.0)) return;", "if (!(dadj >= 0.0)) return;", "test_sine_maker_beside_dry_land"),
+    ("soliton_crest_orientation", "orc_real xi = ((i + 0.5) * o->p.dx - x0) * ct + ((j + 0.5) * o->p.dy - y0) * st;",
+     "orc_real xi = ((i + 0.5) * o->p.dx - x0) * ct - ((j + 0.5) * o->p.dy - y0) * st;",
+     "test_solitary_wave_heading_and_depth"),
+    ("soliton_width_depth_power", "orc_real ks = sqrt(3.0 * fabs(H) / (4.0 * ds * ds * ds));",
+     "orc_real ks = sqrt(3.0 * fabs(H) / (4.0 * ds / ds * ds));", "test_solitary_wave_heading_and_depth"),
+    ("accepts_zero_eps", "!(p->dt > 0) || p->K < 0 || !(p->eps > 0))", "!(p->dt > 0) || p->K < 0 || !(p->eps >= 0))",
+     "test_oracle_refuses_invalid_parameters"),
+    ("accepts_zero_dx", "p->nx < 2 || p->ny < 2 || !(p->dx > 0)", "p->nx < 2 || p->ny < 2 || !(p->dx >= 0)",
+     "test_oracle_refuses_invalid_parameters"),
     ("gauge_records_w", "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)] - o->p.ws;",
      "o->grec[(size_t)slot * o->ng + gk] = o->w[IX(o, i, j)];", "test_gauges_record_eta_about_the_still_water_level"),
 ]

@@ -36,6 +36,9 @@ an invariant, a textbook routine, a special case or a convergence order.
   soliton (Eq. 33-36) + propagation       crest speed c_s (Eq. 36), test_soliton_*
                                           the profile's volume
   soliton direction                       transposed runs           test_symmetry_transpose_solitons
+  soliton heading, width at d != 1        M parallel to grad eta,   test_solitary_wave_heading_*
+                                          volume at d = 0.5 m
+  parameter checks                        refusals                  test_oracle_refuses_*
   sine maker (Eq. 25-29)                  progressive wave P = c eta test_sine_maker_*
   sine maker on the y-sides               transposed runs           test_symmetry_transpose_sine_*
   friction (Eq. 31-32) + start-up + AB3   ODE closed form, orders;  test_friction_*
@@ -409,6 +412,52 @@ def test_soliton_speed(oracle_mod):
     vol = o.state()[0][0].sum() * dx
     exact = H / k * (math.tanh(k * (nx * dx - 15.0)) + math.tanh(k * 15.0))
     assert vol == pytest.approx(exact, rel=1e-4)
+
+
+def test_solitary_wave_heading_and_depth(oracle_mod):
+    """Eq. 33-36 describe a wave travelling along its heading n = (cos
+    theta, sin theta): its discharge c eta n is normal to its crest, so M
+    is parallel to grad eta wherever the wave stands out (a heading of 30
+    degrees, where neither component vanishes); and its width follows the
+    still-water depth d at the crest: at d = 0.5 m the channel holds the
+    volume of H sech^2(k (x - x0)), k = sqrt(3 H / (4 d^3))."""
+    n, dx, d, H = 120, 0.1, 0.5, 0.025
+    z = np.full((n, n), -d)
+    o = oracle_mod.Oracle(z, dx, dx, 0.01, K=1)
+    o.set_state(0 * z, 0 * z, 0 * z)
+    o.add_solitary(H, math.radians(30), 6.0, 6.0)
+    w, P, Q = o.state()
+    ex = (w[1:-1, 2:] - w[1:-1, :-2]) / (2 * dx)
+    ey = (w[2:, 1:-1] - w[:-2, 1:-1]) / (2 * dx)
+    Pi, Qi = P[1:-1, 1:-1], Q[1:-1, 1:-1]
+    m = w[1:-1, 1:-1] > 0.2 * H
+    cross = np.abs(Pi * ey - Qi * ex)[m]
+    scale = (np.hypot(Pi, Qi) * np.hypot(ex, ey))[m]
+    assert m.sum() > 1000 and np.max(cross / np.maximum(scale, 1e-300)) <= 1e-2
+    assert np.all(Qi[m] > 0) and np.all(Pi[m] > 0)
+    # the width at d = 0.5 m: a straight crest across a channel
+    nx, ny = 400, 4
+    zc = np.full((ny, nx), -d)
+    oc = oracle_mod.Oracle(zc, dx, dx, 0.01)
+    oc.set_state(0 * zc, 0 * zc, 0 * zc)
+    oc.add_solitary(H, 0.0, 15.0, ny * dx / 2)
+    k = math.sqrt(3 * H / (4 * d ** 3))
+    vol = oc.state()[0][0].sum() * dx
+    assert vol == pytest.approx(H / k * (math.tanh(k * (nx * dx - 15.0)) + math.tanh(k * 15.0)), rel=1e-4)
+
+
+def test_oracle_refuses_invalid_parameters(oracle_mod):
+    """orc_create refuses a grid of fewer than 2 x 2 cells and spacings,
+    a step or an epsilon that are not positive, and a negative K."""
+    z = np.full((4, 4), -1.0)
+    good = dict(dx=0.5, dy=0.5, dt=0.01)
+    oracle_mod.Oracle(z, good["dx"], good["dy"], good["dt"])
+    for dx, dy, dt, kw in ((0.0, 0.5, 0.01, {}), (0.5, 0.0, 0.01, {}), (0.5, 0.5, 0.0, {}),
+                           (0.5, 0.5, 0.01, {"eps": 0.0}), (0.5, 0.5, 0.01, {"K": -1})):
+        with pytest.raises(ValueError):
+            oracle_mod.Oracle(z, dx, dy, dt, **kw)
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle(np.full((1, 4), -1.0), 0.5, 0.5, 0.01)
 
 
 def _uniform_friction_error(oracle_mod, dt, f=0.5, P0=0.5, h=1.0, T=2.0, kind=1):
